@@ -1,0 +1,337 @@
+"""PolyMinHash benchmark: one step = one pass of the whole signature path over one batch.
+
+Step (device-resident inputs): upload + preprocessing of the database polygons (A0),
+MinHash signatures (A1), band keys + bucket index (A2, A3), the same for the query
+batch, bucket join (A4), agreement estimate (A5), top-m by agreement (A6), exact
+fp64 refinement to the top-10 (A8).  Workload: 1,000,000 star polygons (16-256 vertices,
+area fraction log-uniform 1e-4..1e-2), K = 128, 16 bands x 8 rows, 10,000 perturbed-copy
+queries, synthetic and seeded.
+
+value = (N + Q) * K polygon-hashes per second of step time.  `e2e` is the same step
+through the C ABI from pinned HOST buffers (host-to-device copies and the device-to-host
+read of the top-10 inside the timed region).  `roofline` is the dominant kernel (A1
+signing) against the measured integer-ALU peak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# 32-bit integer operations the definition needs per stream point: 64-bit counter add (2),
+# two xor-shift rounds (4 + 4), two low-64-bit 64x64 multiplies (4 + 4), final xor-shift
+# of the low word (2), field extraction and half-open bbox test (6).
+INT_OPS_PER_POINT = 26
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale")
+    ap.add_argument("--n-polys", type=int, default=None, help="override database size")
+    ap.add_argument("--n-queries", type=int, default=None)
+    ap.add_argument("--topm", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=None, help="polygons in the CPU sample")
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def algorithmic_points(hashes_np: np.ndarray, T: int) -> int:
+    """Stream points the definition examines: h + 1 for a hit, T for the sentinel."""
+    h = hashes_np.astype(np.int64)
+    return int(np.where(h < T, h + 1, T).sum())
+
+
+def run_reference(args, w):
+    """The oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    from paper_2511_16576_gb300 import synth
+    oracle.build()
+    n_sample = args.cpu_sample or 2000
+    db = synth.make_database(w, args.n_polys)
+    rng = np.random.default_rng(7)
+    cores = os.cpu_count() or 1
+    times = []
+    for step in range(args.warmup + args.steps):
+        ids = np.sort(rng.choice(db.n, n_sample, replace=False))
+        sub = db.subset(ids)
+        t0 = time.perf_counter()
+        h = oracle.sign(sub.xy, sub.offsets, w.seed, w.K, w.T, nthreads=cores)
+        oracle.band_keys(h, w.bands, w.rows, w.T, w.lsh_seed)
+        t1 = time.perf_counter()
+        if step >= args.warmup:
+            times.append(t1 - t0)
+    t = float(np.mean(times))
+    value = n_sample * w.K / t
+    line = {
+        "impl": "reference", "metric": "polygon-hashes/s (N*K/s)", "value": value,
+        "unit": "hashes/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"{w.name}: {w.n_polys} star polygons, K={w.K}, "
+                               f"{w.bands}x{w.rows} bands", "sample_polygons": n_sample},
+        "cpu_baseline": {"value": value, "unit": "hashes/s", "cores": cores, "kind": "oracle",
+                         "sample": f"oracle sign + band keys of {n_sample} random polygons of the "
+                                   f"{w.n_polys}-polygon workload per step"},
+        "e2e": {"value": value, "unit": "hashes/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, db, seconds_target=15.0, n_sample=None):
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(11)
+    n = n_sample or 256
+    # grow the sample until it takes a few seconds, then size it for the target
+    while True:
+        ids = np.sort(rng.choice(db.n, min(n, db.n), replace=False))
+        sub = db.subset(ids)
+        t0 = time.perf_counter()
+        oracle.sign(sub.xy, sub.offsets, w.seed, w.K, w.T, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if n_sample or dt > 2.0 or n >= db.n:
+            break
+        n = min(db.n, int(n * max(2.0, min(8.0, seconds_target / 4 / max(dt, 1e-3)))))
+    return {"value": len(ids) * w.K / dt, "unit": "hashes/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle sign of {len(ids)} random polygons x K={w.K} of the "
+                      f"{db.n}-polygon workload ({dt:.1f} s, {cores} threads)"}
+
+
+def main():
+    args = parse()
+    from paper_2511_16576_gb300 import synth
+    w = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+    assert args.warmup >= 3 or os.environ.get("PMH_BENCH_ALLOW_SHORT"), "warm-up >= 3"
+
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2511_16576_gb300 import binding as B
+    from paper_2511_16576_gb300 import build as cuda_build
+    cuda_build.build()
+
+    dev = torch.device("cuda", local)
+    # every rank signs its own shard of the same size (weak scaling)
+    gen_w = w if rank == 0 else synth.Workload(**{**w.__dict__, "gen_seed": w.gen_seed + 1000 * rank})
+    db = synth.make_database(gen_w, args.n_polys)
+    qs = synth.make_queries(gen_w, db, args.n_queries)
+    N, Q, K = db.n, qs.n, w.K
+    P = B.make_params(K, w.bands, w.T, w.seed, w.lsh_seed)
+    ctx = B.Context(local)
+    stream = torch.cuda.current_stream()
+
+    d_xy = torch.from_numpy(db.xy).to(dev)
+    d_off = torch.from_numpy(db.offsets).to(dev)
+    q_xy = torch.from_numpy(qs.xy).to(dev)
+    q_off = torch.from_numpy(qs.offsets).to(dev)
+    ev = {}
+
+    def step(host: bool, record: bool):
+        if host:
+            dbp = B.poly_upload_pinned(ctx, h_xy, h_off)
+        else:
+            dbp = B.poly_upload(ctx, d_xy, d_off)
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        h = B.minhash_sign(ctx, dbp, P)
+        if record:
+            e1.record(stream)
+            ev.setdefault("sign", []).append((e0, e1))
+        index = B.lsh_build(ctx, h, P)
+        qp = B.poly_upload_pinned(ctx, hq_xy, hq_off) if host else B.poly_upload(ctx, q_xy, q_off)
+        qh = B.minhash_sign(ctx, qp, P)
+        row_ptr, cand = B.lsh_query(ctx, index, qh)
+        count, _ = B.jaccard_estimate(ctx, qh, h, row_ptr, cand, P, bandmask=False)
+        ids, nn = B.topm(ctx, row_ptr, cand, count, args.topm)
+        top_ids, top_j = B.refine_topk(ctx, qp, dbp, ids, nn, 10)
+        out = (h, cand, top_ids, top_j)
+        if host:
+            res_ids.copy_(top_ids, non_blocking=True)
+            res_j.copy_(top_j, non_blocking=True)
+        index.close()
+        qp.close()
+        dbp.close()
+        return out
+
+    h_xy = torch.from_numpy(db.xy).pin_memory()
+    h_off = torch.from_numpy(db.offsets).pin_memory()
+    hq_xy = torch.from_numpy(qs.xy).pin_memory()
+    hq_off = torch.from_numpy(qs.offsets).pin_memory()
+    res_ids = torch.empty((Q, 10), dtype=torch.int32).pin_memory()
+    res_j = torch.empty((Q, 10), dtype=torch.float64).pin_memory()
+
+    def timed(host: bool, steps: int, warmup: int, record: bool):
+        for _ in range(warmup):
+            out = step(host, False)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev.clear()
+        l0 = B.launch_count()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            out = step(host, record)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches = B.launch_count() - l0
+        ms = t0.elapsed_time(t1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches, out
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms, launches, out = timed(False, args.steps, args.warmup, True)
+    clk = clocks.stop()
+    h = out[0]
+    sign_ms = float(np.mean([a.elapsed_time(b) for a, b in ev.get("sign", [])]))
+    e2e = None
+    if not args.no_e2e:
+        ms_e2e, _, _ = timed(True, args.steps, max(3, args.warmup // 2 + 1), False)
+        h2d = db.xy.nbytes + db.offsets.nbytes + qs.xy.nbytes + qs.offsets.nbytes
+        d2h = res_ids.numel() * 4 + res_j.numel() * 8
+        e2e = {"value": world * (N + Q) * K / (ms_e2e * 1e-3), "unit": "hashes/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": ms_e2e}
+
+    # roofline of the dominant kernel: integer ops of the definition / sign kernel time
+    hashes_np = h.cpu().numpy().view(np.uint32)
+    G = algorithmic_points(hashes_np, w.T)
+    peak = B.probe_int_peak(ctx)
+    achieved = INT_OPS_PER_POINT * G / (sign_ms * 1e-3)
+    roofline = {"bound": "alu", "kernel": "sign_kernel", "achieved": achieved / 1e12,
+                "peak": peak / 1e12, "unit": "Tintop/s", "frac": achieved / peak,
+                "traffic": None, "points_per_launch": G,
+                "int_ops_per_point": INT_OPS_PER_POINT,
+                "peak_source": "measured: pmh_probe_int_peak (integer mad/add/xor/shl mix, all SMs)",
+                "sign_ms": sign_ms, "points_per_s": G / (sign_ms * 1e-3)}
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(w, db, n_sample=args.cpu_sample)
+
+    value = world * (N + Q) * K / (ms * 1e-3)
+    line = {
+        "metric": "polygon-hashes/s (N*K/s)", "value": value, "unit": "hashes/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": f"{w.name}: {N} star polygons ({db.n_vertices} vertices), K={K}, "
+                               f"{w.bands}x{w.rows} bands, {Q} perturbed-copy queries, "
+                               f"top-{args.topm} refined to top-10",
+                   "l2": f"inputs larger than L2 ({db.xy.nbytes / 1e6:.0f} MB of vertices)",
+                   "parallelism": f"{world} independent shard(s)"},
+        "sign_hashes_per_s": world * N * K / (sign_ms * 1e-3),
+        "candidates_per_query": float(out[1].numel()) / Q,
+        "roofline": roofline,
+        "cpu_baseline": base,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * polyminhash.h -- C ABI of the GB300 (sm_103a) PolyMinHash library.
+ *
+ * PolyMinHash (arXiv 2511.16576) signs a polygon P with m = K MinHash values:
+ * h_k(P) is the index of the first point of hash k's seeded uniform point
+ * stream that lands inside P (Definition 2, Algorithm 1).  Two polygons agree
+ * on one hash with probability J(P, Q) = area(P n Q) / area(P u Q)
+ * (Theorem 1), so signatures bucket similar polygons together (hashmap
+ * filtering, Sec. 3.2 after Theorem 1 and Sec. 5.2) and estimate Jaccard.
+ *
+ * Conventions
+ *  - Every call returns PMH_OK (0) or a negative PMH_ERR_* code; the message
+ *    of the last failure on the calling thread is pmh_last_error().
+ *  - Array arguments named d_* are DEVICE pointers owned by the caller
+ *    (for example torch tensors); h_* are host pointers.  Handles
+ *    (pmh_ctx, pmh_polys, pmh_index) are owned by the library and released by
+ *    their *_destroy call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls enqueue their kernels on it and return without waiting,
+ *    unless the description says "synchronises".
+ *  - There is no CPU fallback: on a machine without a usable sm_103a GPU every
+ *    compute call fails with PMH_ERR_CUDA.
+ *
+ * Geometry and the readings of the paper used by every call
+ *  - A polygon is a simple ring of n >= 3 int32 vertices (x, y) given once
+ *    (the closing vertex is not repeated); edges are (v_i, v_{(i+1) mod n}).
+ *    Coordinates must satisfy |x|, |y| <= 2^20.
+ *  - The sampling domain is the integer lattice [0, 65536)^2 (the paper's
+ *    global MBR, Sec. 3.1, fixed for all data sets).  Point i of stream k is
+ *    v = mix64(s_k + (i+1) * G) with G = 0x9E3779B97F4A7C15,
+ *    s_k = mix64(seed + (k+1) * G) and mix64 the SplitMix64 output function;
+ *    x = v & 0xFFFF, y = (v >> 16) & 0xFFFF.
+ *  - A lattice point p is inside P iff p + (e1, e2), 0 < e2 << e1
+ *    infinitesimal, lies inside P (even-odd rule); this makes membership
+ *    exact, monotone under containment and additive over tilings.
+ *  - h_k(P) = min{ i in [0, T) : point i of stream k is inside P }, else T
+ *    (0-based count of rejected attempts, capped at T <= 2^31).
+ */
+#ifndef POLYMINHASH_H
+#define POLYMINHASH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PMH_OK 0
+#define PMH_ERR_ARG (-1)      /* invalid argument (null, size, shape) */
+#define PMH_ERR_RANGE (-2)    /* input data out of the supported range */
+#define PMH_ERR_CAPACITY (-3) /* an output buffer is too small */
+#define PMH_ERR_CUDA (-4)     /* a CUDA runtime call or kernel failed */
+#define PMH_ERR_TIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define PMH_ERR_STATE (-6)    /* handle used in the wrong state */
+#define PMH_ERR_NOMEM (-7)    /* device or host allocation failed */
+
+#define PMH_INVALID_KEY 0xFFFFFFFFFFFFFFFFull
+
+typedef struct pmh_ctx_s* pmh_ctx;
+typedef struct pmh_polys_s* pmh_polys;
+typedef struct pmh_index_s* pmh_index;
+
+/* Signature and banding parameters.
+ *   seed      global stream seed (Sec. 3.2: fixed seeds per hash function)
+ *   K         signature length m (Definition 2), 1 <= K <= 4096
+ *   T         stream cap, 1 <= T <= 2^31; a hash that never hits is T
+ *   bands     number of LSH bands b, rows = K / bands (K % bands == 0),
+ *             1 <= bands <= 128
+ *   rows      r, must equal K / bands
+ *   lsh_seed  seed of the band-key fingerprint
+ *   flags     0 (reserved) */
+typedef struct {
+    uint64_t seed;
+    uint32_t K;
+    uint32_t T;
+    uint32_t bands;
+    uint32_t rows;
+    uint64_t lsh_seed;
+    uint32_t flags;
+    uint32_t reserved;
+} pmh_params;
+
+/* Message of the last failure on this thread ("" if none).  Never NULL. */
+const char* pmh_last_error(void);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int pmh_version(void);
+
+/* Create a context on CUDA device `device`: it owns scratch buffers and a
+ * device status word.  Not thread-safe: use one context per host thread.
+ * Errors: PMH_ERR_ARG (null out), PMH_ERR_CUDA (no such device / not sm_103). */
+int pmh_create(pmh_ctx* out, int device);
+int pmh_destroy(pmh_ctx ctx);
+
+/* A0 -- upload polygons (Sec. 3.1 preprocessing: local MBRs).
+ * Copies n_polys polygons into library-owned device memory and computes each
+ * polygon's half-open bounding box clipped to the domain, twice its signed
+ * area (exact int64 shoelace) and a work estimate.
+ *   d_xy       int32 [n_vertices][2], interleaved (x, y), device
+ *   d_offsets  int64 [n_polys + 1], offsets[0] = 0, offsets[n_polys] =
+ *              n_vertices, polygon p = vertices offsets[p] .. offsets[p+1]-1
+ * Synchronises `stream` once to report validation failures.
+ * Errors: PMH_ERR_ARG (null, n_polys < 0, n_polys >= 2^31),
+ *         PMH_ERR_RANGE (offsets not increasing, a polygon with < 3 vertices,
+ *         a coordinate beyond 2^20), PMH_ERR_NOMEM, PMH_ERR_CUDA. */
+int pmh_poly_upload(pmh_ctx ctx, const int32_t* d_xy, const int64_t* d_offsets,
+                    int64_t n_polys, int64_t n_vertices, pmh_polys* out, void* stream);
+
+/* Same as pmh_poly_upload with HOST arrays (pageable or pinned); the
+ * host-to-device copies run on `stream` inside the call. */
+int pmh_poly_upload_host(pmh_ctx ctx, const int32_t* h_xy, const int64_t* h_offsets,
+                         int64_t n_polys, int64_t n_vertices, pmh_polys* out, void* stream);
+
+/* Number of polygons and vertices of an uploaded set. */
+int pmh_polys_info(pmh_polys polys, int64_t* n_polys, int64_t* n_vertices);
+
+/* Copy the per-polygon preprocessing out (for inspection):
+ *   d_bbox   int32 [n_polys][4] = x0, y0, x1, y1: lattice points inside P
+ *            satisfy x0 <= x < x1, y0 <= y < y1 (already clipped to the domain)
+ *   d_area2  int64 [n_polys] twice the signed area
+ * Either pointer may be NULL. */
+int pmh_polys_prep(pmh_polys polys, int32_t* d_bbox, int64_t* d_area2, void* stream);
+int pmh_polys_destroy(pmh_polys polys);
+
+/* A1 -- MinHash signatures (Definition 2, Algorithm 1; 0-based, cap T).
+ *   d_hashes  uint32 [n_polys][K] row-major, written completely.
+ * Hashes are exact: bit-identical to the definition above.
+ * Errors: PMH_ERR_ARG (null, bad K/T), PMH_ERR_CUDA. */
+int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* params,
+                     uint32_t* d_hashes, void* stream);
+
+/* A2 -- band keys (hashmap keys of Sec. 3.2 after Theorem 1, one per band).
+ * Band j covers hashes j*r .. j*r+r-1; a = mix64(lsh_seed + (j+1)*G), then
+ * a = mix64(a ^ h) for each of its r hashes; a band holding T has key
+ * PMH_INVALID_KEY, a valid key equal to it is replaced by it minus one.
+ *   d_hashes uint32 [n][K]; d_keys uint64 [n][bands]. */
+int pmh_band_keys(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n, const pmh_params* params,
+                  uint64_t* d_keys, void* stream);
+
+/* A3 -- build the bucket index of n database signatures (one hashmap per
+ * band): band keys plus a stable radix sort of (band, key) with ids.  The
+ * index keeps its own copy of the hashes it needs, so d_hashes may be freed
+ * afterwards.  Errors: PMH_ERR_ARG, PMH_ERR_NOMEM, PMH_ERR_CUDA. */
+int pmh_lsh_build(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n, const pmh_params* params,
+                  pmh_index* out, void* stream);
+int pmh_index_destroy(pmh_index index);
+
+/* A4 -- bucket join.  Candidates of query q: every database id p with some
+ * band j whose r-tuple is valid (no T) in both and equal in both, ascending,
+ * without duplicates, as CSR:
+ *   d_row_ptr int64 [Q + 1] (device), d_cand int32 [cand_capacity] (device)
+ *   h_total   (host) receives the number of candidates over all queries.
+ * Synchronises `stream` once (to learn the total).  With cand_capacity <
+ * total, d_cand is left unwritten, d_row_ptr is still written, and the call
+ * returns PMH_ERR_CAPACITY: call again with a larger buffer. */
+int pmh_lsh_query(pmh_ctx ctx, pmh_index index, const uint32_t* d_qhashes, int64_t Q,
+                  int64_t* d_row_ptr, int32_t* d_cand, int64_t cand_capacity, int64_t* h_total,
+                  void* stream);
+
+/* A5 -- agreement estimate (Theorem 1: Pr[h_k(q) = h_k(p)] = J(q, p)).
+ * For every CSR pair (q, d_cand[e]): d_count[e] = #{k : h_k(q) = h_k(p) != T}
+ * (J estimate = count / K) and, if d_bandmask is not NULL, bit j of
+ * d_bandmask[e] set iff band j (j < 32) is valid and equal in both.
+ *   d_qhashes uint32 [Q][K], d_dbhashes uint32 [N][K], d_row_ptr int64 [Q+1],
+ *   d_cand int32 [row_ptr[Q]] (ids < N; not checked). */
+int pmh_jaccard_estimate(pmh_ctx ctx, const uint32_t* d_qhashes, const uint32_t* d_dbhashes,
+                         const int64_t* d_row_ptr, const int32_t* d_cand, int64_t Q,
+                         const pmh_params* params, uint16_t* d_count, uint32_t* d_bandmask,
+                         void* stream);
+
+/* A6 -- top-m of every candidate row.  Order: (count desc, id asc), or with
+ * d_score != NULL (float per pair, e.g. a learned Jaccard) (score desc, id
+ * asc).  d_out_ids int32 [Q][m] (-1 padded), d_out_n int32 [Q]. 1 <= m <= 1024. */
+int pmh_topm(pmh_ctx ctx, const int64_t* d_row_ptr, const int32_t* d_cand,
+             const uint16_t* d_count, const float* d_score, int64_t Q, int32_t m,
+             int32_t* d_out_ids, int32_t* d_out_n, void* stream);
+
+/* A8 -- exact refinement (Sec. 5.2 refinement phase): for every query q and
+ * each of its d_n[q] listed ids (d_ids [Q][m]), the exact Jaccard
+ * J = area(q n p) / area(q u p) in fp64; keeps the best k by (J desc, id asc).
+ *   d_top_ids int32 [Q][k] (-1 padded), d_top_j double [Q][k].
+ * 1 <= k <= m <= 1024. */
+int pmh_refine_topk(pmh_ctx ctx, pmh_polys queries, pmh_polys db, const int32_t* d_ids,
+                    const int32_t* d_n, int64_t Q, int32_t m, int32_t k, int32_t* d_top_ids,
+                    double* d_top_j, void* stream);
+
+/* Exact Jaccard of explicit pairs (d_qid[e], d_pid[e]) -> d_j[e] (fp64). */
+int pmh_pair_jaccard(pmh_ctx ctx, pmh_polys queries, pmh_polys db, const int32_t* d_qid,
+                     const int32_t* d_pid, int64_t n_pairs, double* d_j, void* stream);
+
+/* Integer-ALU throughput probe used as the roofline denominator: runs a
+ * fixed mix of 32-bit integer instructions (add, logic, shift, multiply-add)
+ * on every SM and reports integer instructions per second (thread level).
+ * Synchronises. */
+int pmh_probe_int_peak(pmh_ctx ctx, double* h_int_ops_per_s, double* h_seconds);
+
+/* Number of kernels this library has launched in this process (all
+ * contexts); used to count launches inside a timed region. */
+int64_t pmh_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

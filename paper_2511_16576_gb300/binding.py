@@ -1,0 +1,319 @@
+"""Thin ctypes binding of libpolyminhash.so (the C ABI in include/polyminhash.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.  torch
+provides device memory and streams.  uint32 / uint16 arrays are carried in int32 /
+int16 tensors (same bits); uint64 keys in int64 tensors.  There is no CPU fallback:
+if the library is missing or no sm_103 GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpolyminhash.so")
+_lib = None
+
+PMH_OK = 0
+PMH_ERR_CAPACITY = -3
+INVALID_KEY = 0xFFFFFFFFFFFFFFFF
+
+
+class PmhError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"polyminhash error {code}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("K", ctypes.c_uint32), ("T", ctypes.c_uint32),
+                ("bands", ctypes.c_uint32), ("rows", ctypes.c_uint32),
+                ("lsh_seed", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+def make_params(K: int, bands: int, T: int = 1 << 24, seed: int = 0x5EED,
+                lsh_seed: int = 0x15A) -> Params:
+    return Params(seed, K, T, bands, K // bands, lsh_seed, 0, 0)
+
+
+# entry points: name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_SIGS = {
+    "pmh_last_error": (ctypes.c_char_p, []),
+    "pmh_version": (ctypes.c_int, []),
+    "pmh_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int]),
+    "pmh_destroy": (ctypes.c_int, [_P]),
+    "pmh_poly_upload": (ctypes.c_int, [_P, _P, _P, _i64, _i64, ctypes.POINTER(_P), _P]),
+    "pmh_poly_upload_host": (ctypes.c_int, [_P, _P, _P, _i64, _i64, ctypes.POINTER(_P), _P]),
+    "pmh_polys_info": (ctypes.c_int, [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "pmh_polys_prep": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pmh_polys_destroy": (ctypes.c_int, [_P]),
+    "pmh_minhash_sign": (ctypes.c_int, [_P, _P, ctypes.POINTER(Params), _P, _P]),
+    "pmh_band_keys": (ctypes.c_int, [_P, _P, _i64, ctypes.POINTER(Params), _P, _P]),
+    "pmh_lsh_build": (ctypes.c_int, [_P, _P, _i64, ctypes.POINTER(Params), ctypes.POINTER(_P), _P]),
+    "pmh_index_destroy": (ctypes.c_int, [_P]),
+    "pmh_lsh_query": (ctypes.c_int, [_P, _P, _P, _i64, _P, _P, _i64, ctypes.POINTER(_i64), _P]),
+    "pmh_jaccard_estimate": (ctypes.c_int, [_P, _P, _P, _P, _P, _i64, ctypes.POINTER(Params), _P,
+                                            _P, _P]),
+    "pmh_topm": (ctypes.c_int, [_P, _P, _P, _P, _P, _i64, _i32, _P, _P, _P]),
+    "pmh_refine_topk": (ctypes.c_int, [_P, _P, _P, _P, _P, _i64, _i32, _i32, _P, _P, _P]),
+    "pmh_pair_jaccard": (ctypes.c_int, [_P, _P, _P, _P, _P, _i64, _P, _P]),
+    "pmh_probe_int_peak": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "pmh_launch_count": (_i64, []),
+}
+
+
+def exported_names() -> list[str]:
+    return sorted(_SIGS)
+
+
+def load():
+    """Load the library (built by paper_2511_16576_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != PMH_OK:
+        raise PmhError(rc, load().pmh_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Context:
+    """A library context on one CUDA device (owns scratch memory)."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        h = _P()
+        _check(lib.pmh_create(ctypes.byref(h), device))
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            load().pmh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Polys:
+    """Polygons uploaded to library-owned device memory (step A0)."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.handle = handle
+        n, nv = _i64(), _i64()
+        _check(load().pmh_polys_info(handle, ctypes.byref(n), ctypes.byref(nv)))
+        self.n, self.n_vertices = n.value, nv.value
+
+    def prep(self, stream=None):
+        dev = torch.device("cuda", self.ctx.device)
+        bbox = torch.empty((max(self.n, 1), 4), dtype=torch.int32, device=dev)
+        area2 = torch.empty(max(self.n, 1), dtype=torch.int64, device=dev)
+        _check(load().pmh_polys_prep(self.handle, _ptr(bbox), _ptr(area2), _stream(stream)))
+        return bbox[:self.n], area2[:self.n]
+
+    def close(self):
+        if self.handle:
+            load().pmh_polys_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def poly_upload(ctx: Context, xy: torch.Tensor, offsets: torch.Tensor, stream=None) -> Polys:
+    """Upload device arrays xy int32 [V, 2] and offsets int64 [N + 1]."""
+    assert xy.dtype == torch.int32 and offsets.dtype == torch.int64
+    assert xy.is_cuda and offsets.is_cuda and xy.is_contiguous() and offsets.is_contiguous()
+    h = _P()
+    n = offsets.numel() - 1
+    _check(load().pmh_poly_upload(ctx.handle, _ptr(xy), _ptr(offsets), n, xy.shape[0],
+                                  ctypes.byref(h), _stream(stream)))
+    return Polys(ctx, h)
+
+
+def poly_upload_host(ctx: Context, xy, offsets, stream=None) -> Polys:
+    """Upload host arrays (numpy or CPU tensors, pinned or pageable)."""
+    import numpy as np
+    xy_np = np.ascontiguousarray(np.asarray(xy), dtype=np.int32)
+    off_np = np.ascontiguousarray(np.asarray(offsets), dtype=np.int64)
+    h = _P()
+    _check(load().pmh_poly_upload_host(ctx.handle, xy_np.ctypes.data, off_np.ctypes.data,
+                                       len(off_np) - 1, xy_np.shape[0], ctypes.byref(h),
+                                       _stream(stream)))
+    return Polys(ctx, h)
+
+
+def poly_upload_pinned(ctx: Context, xy: torch.Tensor, offsets: torch.Tensor,
+                       stream=None) -> Polys:
+    """Upload pinned CPU tensors without an extra host copy."""
+    assert not xy.is_cuda and not offsets.is_cuda
+    h = _P()
+    _check(load().pmh_poly_upload_host(ctx.handle, _ptr(xy), _ptr(offsets), offsets.numel() - 1,
+                                       xy.shape[0], ctypes.byref(h), _stream(stream)))
+    return Polys(ctx, h)
+
+
+def minhash_sign(ctx: Context, polys: Polys, params: Params, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """A1: uint32 hashes [N, K] (carried in an int32 tensor)."""
+    if out is None:
+        out = torch.empty((polys.n, params.K), dtype=torch.int32,
+                          device=torch.device("cuda", ctx.device))
+    _check(load().pmh_minhash_sign(ctx.handle, polys.handle, ctypes.byref(params), _ptr(out),
+                                   _stream(stream)))
+    return out
+
+
+def band_keys(ctx: Context, hashes: torch.Tensor, params: Params, out=None, stream=None):
+    """A2: uint64 band keys [N, bands] (carried in an int64 tensor)."""
+    n = hashes.shape[0]
+    if out is None:
+        out = torch.empty((n, params.bands), dtype=torch.int64, device=hashes.device)
+    _check(load().pmh_band_keys(ctx.handle, _ptr(hashes), n, ctypes.byref(params), _ptr(out),
+                                _stream(stream)))
+    return out
+
+
+class Index:
+    """A3: bucket index of database signatures."""
+
+    def __init__(self, ctx: Context, hashes: torch.Tensor, params: Params, stream=None):
+        h = _P()
+        _check(load().pmh_lsh_build(ctx.handle, _ptr(hashes), hashes.shape[0],
+                                    ctypes.byref(params), ctypes.byref(h), _stream(stream)))
+        self.ctx, self.handle, self.params, self.n = ctx, h, params, hashes.shape[0]
+
+    def close(self):
+        if self.handle:
+            load().pmh_index_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lsh_build(ctx: Context, hashes: torch.Tensor, params: Params, stream=None) -> Index:
+    return Index(ctx, hashes, params, stream)
+
+
+def lsh_query(ctx: Context, index: Index, qhashes: torch.Tensor, capacity: int | None = None,
+              stream=None):
+    """A4: CSR (row_ptr int64 [Q+1], cand int32 [total]); sizes the buffer itself."""
+    Q = qhashes.shape[0]
+    dev = qhashes.device
+    row_ptr = torch.empty(Q + 1, dtype=torch.int64, device=dev)
+    total = _i64()
+    cap = 0 if capacity is None else capacity
+    cand = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    lib = load()
+    rc = lib.pmh_lsh_query(ctx.handle, index.handle, _ptr(qhashes), Q, _ptr(row_ptr), _ptr(cand),
+                           cap, ctypes.byref(total), _stream(stream))
+    if rc == PMH_ERR_CAPACITY and capacity is None:
+        cand = torch.empty(max(total.value, 1), dtype=torch.int32, device=dev)
+        rc = lib.pmh_lsh_query(ctx.handle, index.handle, _ptr(qhashes), Q, _ptr(row_ptr),
+                               _ptr(cand), total.value, ctypes.byref(total), _stream(stream))
+    _check(rc)
+    return row_ptr, cand[:total.value]
+
+
+def jaccard_estimate(ctx: Context, qhashes, dbhashes, row_ptr, cand, params: Params,
+                     bandmask: bool = True, stream=None):
+    """A5: agreement counts (int16 carrying uint16) and band-match bits (int32 carrying uint32)."""
+    E = cand.numel()
+    dev = qhashes.device
+    count = torch.empty(max(E, 1), dtype=torch.int16, device=dev)
+    mask = torch.empty(max(E, 1), dtype=torch.int32, device=dev) if bandmask else None
+    _check(load().pmh_jaccard_estimate(ctx.handle, _ptr(qhashes), _ptr(dbhashes), _ptr(row_ptr),
+                                       _ptr(cand), qhashes.shape[0], ctypes.byref(params),
+                                       _ptr(count), _ptr(mask), _stream(stream)))
+    return count[:E], (mask[:E] if mask is not None else None)
+
+
+def topm(ctx: Context, row_ptr, cand, count, m: int, score=None, stream=None):
+    """A6: top-m ids per query ([Q, m], -1 padded) and kept counts [Q]."""
+    Q = row_ptr.numel() - 1
+    dev = row_ptr.device
+    ids = torch.empty((max(Q, 1), m), dtype=torch.int32, device=dev)
+    nn = torch.empty(max(Q, 1), dtype=torch.int32, device=dev)
+    _check(load().pmh_topm(ctx.handle, _ptr(row_ptr), _ptr(cand), _ptr(count), _ptr(score), Q, m,
+                           _ptr(ids), _ptr(nn), _stream(stream)))
+    return ids[:Q], nn[:Q]
+
+
+def refine_topk(ctx: Context, queries: Polys, db: Polys, ids, nn, k: int, stream=None):
+    """A8: exact top-k by Jaccard among each query's listed ids."""
+    Q, m = ids.shape
+    dev = ids.device
+    top_ids = torch.empty((max(Q, 1), k), dtype=torch.int32, device=dev)
+    top_j = torch.empty((max(Q, 1), k), dtype=torch.float64, device=dev)
+    _check(load().pmh_refine_topk(ctx.handle, queries.handle, db.handle, _ptr(ids), _ptr(nn), Q, m,
+                                  k, _ptr(top_ids), _ptr(top_j), _stream(stream)))
+    return top_ids[:Q], top_j[:Q]
+
+
+def pair_jaccard(ctx: Context, queries: Polys, db: Polys, qid, pid, stream=None):
+    """Exact Jaccard of explicit (query, database) pairs, fp64."""
+    n = qid.numel()
+    out = torch.empty(max(n, 1), dtype=torch.float64, device=qid.device)
+    _check(load().pmh_pair_jaccard(ctx.handle, queries.handle, db.handle, _ptr(qid), _ptr(pid), n,
+                                   _ptr(out), _stream(stream)))
+    return out[:n]
+
+
+def probe_int_peak(ctx: Context) -> float:
+    """Measured integer instructions per second (thread level) of this GPU."""
+    ops, sec = ctypes.c_double(), ctypes.c_double()
+    _check(load().pmh_probe_int_peak(ctx.handle, ctypes.byref(ops), ctypes.byref(sec)))
+    return ops.value
+
+
+def launch_count() -> int:
+    return int(load().pmh_launch_count())
+
+
+@dataclass
+class Signed:
+    polys: Polys
+    hashes: torch.Tensor

@@ -1,0 +1,278 @@
+// lsh.cu -- steps A2 (band keys), A3 (bucket index) and A4 (bucket join).
+//
+// The paper inserts every polygon into a hashmap keyed on its MinHash code and
+// takes the bucket members as refinement candidates (Sec. 3.2 after Theorem 1,
+// Sec. 5.2; "2 hashmaps", Sec. 5.3).  Here one hashmap per band is a sorted
+// array: entry (band j, polygon p) gets a 32-bit composite sort key
+// (j in the top band_bits bits, the top bits of the 64-bit band key below),
+// stable-radix-sorted so that equal composites keep ascending ids.  A query
+// binary-searches its composite per band and walks the equal range, keeping
+// entries whose full 64-bit key AND r-tuple equal its own (exact bucket
+// membership).  The per-band id lists are ascending, so a warp merges them
+// (min over lanes) into the sorted, duplicate-free candidate row.
+#include <algorithm>
+
+#include "pmh_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ uint64_t band_key(const uint32_t* __restrict__ h, int j, int rows,
+                                             uint32_t T, uint64_t lsh_seed)
+{
+    uint64_t a = pmh_mix64(lsh_seed + (uint64_t)(j + 1) * PMH_GAMMA);
+    bool valid = true;
+    for (int t = 0; t < rows; ++t) {
+        uint32_t v = h[j * rows + t];
+        valid &= v != T;
+        a = pmh_mix64(a ^ (uint64_t)v);
+    }
+    if (a == PMH_INVALID_KEY) a = PMH_INVALID_KEY - 1;
+    return valid ? a : PMH_INVALID_KEY;
+}
+
+__global__ void band_key_kernel(const uint32_t* __restrict__ hashes, int64_t n, int K, int bands,
+                                int rows, uint32_t T, uint64_t lsh_seed, uint64_t* __restrict__ keys)
+{
+    int64_t total = n * bands;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = t / bands;
+        int j = (int)(t - p * bands);
+        keys[t] = band_key(hashes + p * K, j, rows, T, lsh_seed);
+    }
+}
+
+__device__ __forceinline__ uint32_t composite(uint64_t key, int j, int band_bits)
+{
+    if (key == PMH_INVALID_KEY) return 0xFFFFFFFFu;
+    return ((uint32_t)j << (32 - band_bits)) | (uint32_t)(key >> (32 + band_bits));
+}
+
+// entries in band-major order: e = j * n + p
+__global__ void fill_entries_kernel(const uint64_t* __restrict__ keys, int64_t n, int bands,
+                                    int band_bits, uint32_t* __restrict__ comp,
+                                    int32_t* __restrict__ ids)
+{
+    int64_t total = n * bands;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int j = (int)(e / n);
+        int64_t p = e - (int64_t)j * n;
+        comp[e] = composite(keys[p * bands + j], j, band_bits);
+        ids[e] = (int32_t)p;
+    }
+}
+
+constexpr int kMaxBandsPerLane = 4;  // bands <= 128
+constexpr int32_t kNone = 0x7FFFFFFF;
+
+struct BandCursor {
+    int64_t cur;
+    uint32_t comp;
+    uint64_t key;
+    int j;
+    int32_t head;
+};
+
+__device__ __forceinline__ bool tuple_equal(const uint32_t* __restrict__ a,
+                                            const uint32_t* __restrict__ b, int j, int rows)
+{
+    for (int t = 0; t < rows; ++t)
+        if (a[j * rows + t] != b[j * rows + t]) return false;
+    return true;
+}
+
+// advance c to the next entry of its band that is an exact bucket member
+__device__ __forceinline__ void advance(BandCursor& c, const uint32_t* __restrict__ comp,
+                                        const int32_t* __restrict__ ids,
+                                        const uint64_t* __restrict__ keys,
+                                        const uint32_t* __restrict__ dbh,
+                                        const uint32_t* __restrict__ qh, int64_t m, int K,
+                                        int bands, int rows)
+{
+    c.head = kNone;
+    while (c.cur < m && comp[c.cur] == c.comp) {
+        int32_t p = ids[c.cur];
+        ++c.cur;
+        if (keys[(int64_t)p * bands + c.j] == c.key &&
+            tuple_equal(qh, dbh + (int64_t)p * K, c.j, rows)) {
+            c.head = p;
+            return;
+        }
+    }
+}
+
+template <bool kWrite>
+__global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands,
+                             int rows, uint32_t T, uint64_t lsh_seed, int band_bits,
+                             const uint32_t* __restrict__ comp, const int32_t* __restrict__ ids,
+                             const uint64_t* __restrict__ keys, const uint32_t* __restrict__ dbh,
+                             int64_t m, int64_t* __restrict__ counts,
+                             const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= Q) return;
+    const uint32_t* qh = qhashes + q * K;
+    BandCursor cur[kMaxBandsPerLane];
+#pragma unroll
+    for (int t = 0; t < kMaxBandsPerLane; ++t) {
+        int j = lane + 32 * t;
+        cur[t].head = kNone;
+        cur[t].j = j;
+        if (j >= bands) continue;
+        uint64_t key = band_key(qh, j, rows, T, lsh_seed);
+        if (key == PMH_INVALID_KEY) continue;
+        cur[t].key = key;
+        cur[t].comp = composite(key, j, band_bits);
+        // lower bound of comp in the sorted composite array
+        int64_t lo = 0, hi = m;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (comp[mid] < cur[t].comp) lo = mid + 1;
+            else hi = mid;
+        }
+        cur[t].cur = lo;
+        advance(cur[t], comp, ids, keys, dbh, qh, m, K, bands, rows);
+    }
+    int64_t out = kWrite ? row_ptr[q] : 0;
+    int64_t cnt = 0;
+    for (;;) {
+        int32_t mine = kNone;
+#pragma unroll
+        for (int t = 0; t < kMaxBandsPerLane; ++t) mine = min(mine, cur[t].head);
+        int32_t best = __reduce_min_sync(0xffffffffu, mine);
+        if (best == kNone) break;
+        if (kWrite && lane == 0) cand[out + cnt] = best;
+        ++cnt;
+#pragma unroll
+        for (int t = 0; t < kMaxBandsPerLane; ++t)
+            if (cur[t].head == best) advance(cur[t], comp, ids, keys, dbh, qh, m, K, bands, rows);
+    }
+    if (!kWrite && lane == 0) counts[q] = cnt;
+}
+
+}  // namespace
+
+extern "C" int pmh_band_keys(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
+                             const pmh_params* params, uint64_t* d_keys, void* stream)
+{
+    PMH_TRY(pmh_check_device(ctx));
+    PMH_TRY(pmh_check_params(params));
+    if (n < 0 || (n > 0 && (!d_hashes || !d_keys))) return pmh_set_error(PMH_ERR_ARG, "bad arguments");
+    if (n == 0) return PMH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t total = n * params->bands;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)ctx->sm_count * 32);
+    band_key_kernel<<<blocks, 256, 0, s>>>(d_hashes, n, (int)params->K, (int)params->bands,
+                                           (int)params->rows, params->T, params->lsh_seed, d_keys);
+    PMH_LAUNCHED("band_key_kernel");
+    return PMH_OK;
+}
+
+extern "C" int pmh_lsh_build(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
+                             const pmh_params* params, pmh_index* out, void* stream)
+{
+    if (!out) return pmh_set_error(PMH_ERR_ARG, "null out");
+    *out = nullptr;
+    PMH_TRY(pmh_check_device(ctx));
+    PMH_TRY(pmh_check_params(params));
+    if (n < 0 || n >= (1ll << 31) || (n > 0 && !d_hashes))
+        return pmh_set_error(PMH_ERR_ARG, "bad arguments (n=%lld)", (long long)n);
+    cudaStream_t s = (cudaStream_t)stream;
+    pmh_index X = new pmh_index_s();
+    X->ctx = ctx;
+    X->n = n;
+    X->params = *params;
+    int bb = 1;
+    while ((1u << bb) - 1 < params->bands) ++bb;  // band index < 2^bb - 1: comp never all ones
+    X->band_bits = bb;
+    const int64_t entries = n * params->bands;
+    const size_t nn = (size_t)std::max<int64_t>(n, 1), ne = (size_t)std::max<int64_t>(entries, 1);
+    if (cudaMalloc(&X->hashes, sizeof(uint32_t) * nn * params->K) != cudaSuccess ||
+        cudaMalloc(&X->keys, sizeof(uint64_t) * nn * params->bands) != cudaSuccess ||
+        cudaMalloc(&X->sorted_comp, sizeof(uint32_t) * ne) != cudaSuccess ||
+        cudaMalloc(&X->sorted_id, sizeof(int32_t) * ne) != cudaSuccess) {
+        cudaGetLastError();
+        pmh_index_destroy(X);
+        return pmh_set_error(PMH_ERR_NOMEM, "index allocation failed (n=%lld)", (long long)n);
+    }
+    int rc = PMH_OK;
+    if (n > 0) {
+        cudaError_t e = cudaMemcpyAsync(X->hashes, d_hashes, sizeof(uint32_t) * n * params->K,
+                                        cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
+        if (rc == PMH_OK) rc = pmh_band_keys(ctx, X->hashes, n, params, X->keys, stream);
+        if (rc == PMH_OK) {
+            int blocks = (int)std::min<int64_t>((entries + 255) / 256, (int64_t)ctx->sm_count * 32);
+            fill_entries_kernel<<<blocks, 256, 0, s>>>(X->keys, n, (int)params->bands, bb,
+                                                        X->sorted_comp, X->sorted_id);
+            g_pmh_launches.fetch_add(1);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "fill: %s", cudaGetErrorString(e));
+        }
+        if (rc == PMH_OK) rc = pmh_radix_sort_u32(ctx, X->sorted_comp, X->sorted_id, entries, 32, s);
+    }
+    if (rc != PMH_OK) {
+        pmh_index_destroy(X);
+        return rc;
+    }
+    *out = X;
+    return PMH_OK;
+}
+
+extern "C" int pmh_index_destroy(pmh_index X)
+{
+    if (!X) return PMH_OK;
+    if (X->ctx) cudaSetDevice(X->ctx->device);
+    cudaDeviceSynchronize();
+    if (X->hashes) cudaFree(X->hashes);
+    if (X->keys) cudaFree(X->keys);
+    if (X->sorted_comp) cudaFree(X->sorted_comp);
+    if (X->sorted_id) cudaFree(X->sorted_id);
+    delete X;
+    return PMH_OK;
+}
+
+extern "C" int pmh_lsh_query(pmh_ctx ctx, pmh_index X, const uint32_t* d_qhashes, int64_t Q,
+                             int64_t* d_row_ptr, int32_t* d_cand, int64_t cand_capacity,
+                             int64_t* h_total, void* stream)
+{
+    PMH_TRY(pmh_check_device(ctx));
+    if (!X || !d_row_ptr || !h_total || Q < 0 || (Q > 0 && !d_qhashes) || cand_capacity < 0)
+        return pmh_set_error(PMH_ERR_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    *h_total = 0;
+    if (Q == 0) {
+        PMH_CUDA_TRY(cudaMemsetAsync(d_row_ptr, 0, sizeof(int64_t), s));
+        return PMH_OK;
+    }
+    const pmh_params& P = X->params;
+    int64_t* counts = nullptr;
+    PMH_TRY(pmh_scratch(ctx, SCR_QUERY, sizeof(int64_t) * (size_t)Q, (void**)&counts));
+    const int64_t m = X->n * P.bands;
+    const int wpb = 8;
+    unsigned blocks = (unsigned)((Q + wpb - 1) / wpb);
+    query_kernel<false><<<blocks, wpb * 32, 0, s>>>(d_qhashes, Q, (int)P.K, (int)P.bands,
+                                                    (int)P.rows, P.T, P.lsh_seed, X->band_bits,
+                                                    X->sorted_comp, X->sorted_id, X->keys,
+                                                    X->hashes, m, counts, nullptr, nullptr);
+    PMH_LAUNCHED("query_kernel<count>");
+    PMH_TRY(pmh_exclusive_scan_i64(ctx, counts, d_row_ptr, Q, s));
+    PMH_CUDA_TRY(cudaMemcpyAsync(ctx->h_pinned, d_row_ptr + Q, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+    PMH_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t total = ctx->h_pinned[0];
+    *h_total = total;
+    if (total > cand_capacity)
+        return pmh_set_error(PMH_ERR_CAPACITY, "%lld candidates > capacity %lld", (long long)total,
+                             (long long)cand_capacity);
+    if (total == 0) return PMH_OK;
+    if (!d_cand) return pmh_set_error(PMH_ERR_ARG, "null candidate buffer");
+    query_kernel<true><<<blocks, wpb * 32, 0, s>>>(d_qhashes, Q, (int)P.K, (int)P.bands,
+                                                   (int)P.rows, P.T, P.lsh_seed, X->band_bits,
+                                                   X->sorted_comp, X->sorted_id, X->keys,
+                                                   X->hashes, m, nullptr, d_row_ptr, d_cand);
+    PMH_LAUNCHED("query_kernel<fill>");
+    return PMH_OK;
+}

@@ -1,0 +1,132 @@
+// pmh_internal.cuh -- internal declarations of the PolyMinHash CUDA library.
+//
+// Shared by the library's translation units only (never by the CPU oracle).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "../../include/polyminhash.h"
+
+// ---------------------------------------------------------------------------
+// Error reporting
+// ---------------------------------------------------------------------------
+int pmh_set_error(int code, const char* fmt, ...);
+#define PMH_CUDA_TRY(call)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return pmh_set_error(PMH_ERR_CUDA, "%s failed: %s (%s:%d)", #call,         \
+                                 cudaGetErrorString(e_), __FILE__, __LINE__);          \
+    } while (0)
+#define PMH_TRY(expr)              \
+    do {                           \
+        int rc_ = (expr);          \
+        if (rc_ != PMH_OK) return rc_; \
+    } while (0)
+
+extern std::atomic<int64_t> g_pmh_launches;
+// launch bookkeeping: count every kernel launch and check the launch status
+#define PMH_LAUNCHED(name)                                                              \
+    do {                                                                                \
+        g_pmh_launches.fetch_add(1, std::memory_order_relaxed);                         \
+        cudaError_t e_ = cudaGetLastError();                                            \
+        if (e_ != cudaSuccess)                                                          \
+            return pmh_set_error(PMH_ERR_CUDA, "launch of %s failed: %s", name,         \
+                                 cudaGetErrorString(e_));                               \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------
+enum ScratchSlot {
+    SCR_SORT_A = 0,
+    SCR_SORT_B,
+    SCR_SORT_HIST,
+    SCR_SCAN,
+    SCR_QUERY,
+    SCR_REFINE,
+    SCR_MISC,
+    SCR_COUNT
+};
+
+struct pmh_ctx_s {
+    int device = 0;
+    int sm_count = 0;
+    int* d_status = nullptr;              // device status word (0 = ok)
+    unsigned long long* d_tickets = nullptr;  // work-queue tickets [64]
+    void* scratch[SCR_COUNT] = {};
+    size_t scratch_bytes[SCR_COUNT] = {};
+    int64_t* h_pinned = nullptr;          // small pinned host buffer [64]
+};
+
+struct pmh_polys_s {
+    pmh_ctx ctx = nullptr;
+    int64_t n = 0, nv = 0;
+    int2* xy = nullptr;
+    int64_t* offsets = nullptr;
+    int4* bbox = nullptr;      // x0, y0, x1, y1 half-open, clipped to the domain
+    int64_t* area2 = nullptr;  // twice the signed area
+    int32_t max_n = 0;         // largest vertex count
+};
+
+struct pmh_index_s {
+    pmh_ctx ctx = nullptr;
+    int64_t n = 0;
+    pmh_params params{};
+    int band_bits = 0;
+    uint32_t* hashes = nullptr;     // [n][K]
+    uint64_t* keys = nullptr;       // [n][bands]
+    uint32_t* sorted_comp = nullptr;  // [n * bands] composite (band, key) sort keys
+    int32_t* sorted_id = nullptr;     // [n * bands]
+};
+
+// grow-only scratch buffer of the context
+int pmh_scratch(pmh_ctx ctx, int slot, size_t bytes, void** out);
+int pmh_check_params(const pmh_params* p);
+int pmh_check_device(pmh_ctx ctx);
+
+// ---------------------------------------------------------------------------
+// Stream points (SplitMix64, Steele/Lea/Flood 2014)
+// ---------------------------------------------------------------------------
+#define PMH_GAMMA 0x9E3779B97F4A7C15ull
+#define PMH_M1 0xBF58476D1CE4E5B9ull
+#define PMH_M2 0x94D049BB133111EBull
+
+__host__ __device__ __forceinline__ uint64_t pmh_mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * PMH_M1;
+    z = (z ^ (z >> 27)) * PMH_M2;
+    return z ^ (z >> 31);
+}
+
+// low 32 bits of the mix: all a lattice point needs (x = bits 0..15, y = 16..31)
+__device__ __forceinline__ uint32_t pmh_mix64_lo(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * PMH_M1;
+    z = (z ^ (z >> 27)) * PMH_M2;
+    return (uint32_t)(z ^ (z >> 31));
+}
+
+// ---------------------------------------------------------------------------
+// Scans (scan.cu)
+// ---------------------------------------------------------------------------
+// exclusive prefix sum of n int64 values in place-able form: out[i] = sum in[0..i-1],
+// out[n] = total (out has n + 1 entries).  in may alias out.
+int pmh_exclusive_scan_i64(pmh_ctx ctx, const int64_t* in, int64_t* out, int64_t n,
+                           cudaStream_t s);
+
+// stable LSD radix sort of (uint32 key, int32 value) pairs; result in keys/vals.
+int pmh_radix_sort_u32(pmh_ctx ctx, uint32_t* keys, int32_t* vals, int64_t n, int key_bits,
+                       cudaStream_t s);
+
+// warp helpers
+__device__ __forceinline__ unsigned pmh_lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}

@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads and exports every entry point of include/*.h (CPU only:
+no compute call is made without a GPU)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(pmh_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_16576_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("pmh_poly_upload", "pmh_minhash_sign", "pmh_lsh_build", "pmh_lsh_query",
+                     "pmh_jaccard_estimate"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header():
+    from paper_2511_16576_gb300 import binding
+    assert set(declared_functions()) <= set(binding.exported_names())
+
+
+def test_error_path_without_gpu_or_bad_args(lib):
+    lib.pmh_last_error.restype = ctypes.c_char_p
+    lib.pmh_version.restype = ctypes.c_int
+    assert lib.pmh_version() >= 10000
+    # null out-pointer is rejected before any CUDA call
+    assert lib.pmh_create(None, 0) == -1
+    assert b"null" in lib.pmh_last_error()
+    assert lib.pmh_polys_destroy(None) == 0
+    assert lib.pmh_index_destroy(None) == 0
+
+
+def test_params_struct_layout():
+    from paper_2511_16576_gb300 import binding
+    assert ctypes.sizeof(binding.Params) == 40
+    p = binding.make_params(128, 16)
+    assert (p.K, p.bands, p.rows, p.T) == (128, 16, 8, 1 << 24)

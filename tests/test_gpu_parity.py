@@ -1,0 +1,290 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle, through the C ABI.
+
+Hashes, band keys, candidate sets, agreement counts, band bits and top-m lists must be
+bit-identical; exact Jaccard (fp64, different algorithms on the two sides) agrees to a
+relative 1e-9.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2511_16576_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda", 0)
+SEED = 0x5EED
+T24 = 1 << 24
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2511_16576_gb300 import binding, build
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def upload(B, ctx, ps):
+    return B.poly_upload(ctx, torch.from_numpy(ps.xy).to(DEV), torch.from_numpy(ps.offsets).to(DEV))
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def from_polys(polys):
+    xy = np.concatenate([np.asarray(p, np.int32).reshape(-1, 2) for p in polys])
+    off = np.zeros(len(polys) + 1, np.int64)
+    off[1:] = np.cumsum([len(p) for p in polys])
+    return synth.PolySet(xy, off, np.zeros((len(polys), 2), np.int64), np.ones(len(polys)))
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = synth.WORKLOADS["small"]
+    db = synth.make_database(w)
+    qs = synth.make_queries(w, db)
+    return w, db, qs
+
+
+def test_prep_bbox_and_area(B, ctx, orc, small):
+    _, db, _ = small
+    P = upload(B, ctx, db)
+    bbox, area2 = P.prep()
+    bbox, area2 = bbox.cpu().numpy(), area2.cpu().numpy()
+    for i in range(db.n):
+        ref = orc.bbox(db.poly(i))
+        assert list(bbox[i]) == [max(ref[0], 0), max(ref[1], 0), min(ref[2], 65536), min(ref[3], 65536)]
+        assert area2[i] == orc.area2(db.poly(i))
+
+
+def test_upload_rejects_bad_input(B, ctx):
+    ps = from_polys([[[0, 0], [5, 0], [0, 5]], [[1, 1], [2, 2]]])   # second has 2 vertices
+    with pytest.raises(B.PmhError):
+        upload(B, ctx, ps)
+    ps = from_polys([[[0, 0], [5, 0], [0, 1 << 22]]])
+    with pytest.raises(B.PmhError):
+        upload(B, ctx, ps)
+
+
+def test_sign_small_bit_exact(B, ctx, orc, small):
+    w, db, qs = small
+    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed)
+    h = u32(B.minhash_sign(ctx, upload(B, ctx, db), P))
+    ref = orc.sign(db.xy, db.offsets, w.seed, w.K, w.T, nthreads=8)
+    assert np.array_equal(h, ref)
+
+
+@pytest.mark.parametrize("K,T", [(40, 1 << 24), (32, 100), (7, 3000), (64, 1)])
+def test_sign_ragged_K_and_cap(B, ctx, orc, K, T):
+    db = synth.star_polygons(300, 11, (3, 40), "uniform", (1e-3, 2e-2))
+    P = B.make_params(K, 1, T)
+    h = u32(B.minhash_sign(ctx, upload(B, ctx, db), P))
+    ref = orc.sign(db.xy, db.offsets, SEED, K, T, nthreads=8)
+    assert np.array_equal(h, ref)
+
+
+def test_sign_edge_cases(B, ctx, orc):
+    polys = [
+        [[0, 0], [65536, 0], [65536, 65536], [0, 65536]],          # covers the domain: all 0
+        [[-100, -100], [70000, -50], [70000, 70000], [-90, 70000]],  # beyond the domain
+        [[5, 5], [9, 5], [7, 5]],                                   # zero area: all T
+        [[60000, 60000], [70000, 60000], [70000, 70000]],            # partly outside
+        [[1000, 1000], [1010, 1000], [1010, 1010], [1000, 1010]][::-1],  # clockwise square
+        [[200, 200], [300, 200], [300, 250], [250, 250], [250, 300], [200, 300]],  # L shape
+    ]
+    # a 2000-vertex star exercises the global-memory edge path (> 256 vertices)
+    big = synth.star_polygons(1, 5, (2000, 2000), "uniform", (2e-3, 2e-3))
+    polys.append(big.poly(0))
+    ps = from_polys(polys)
+    K, T = 64, 200000
+    P = B.make_params(K, 1, T)
+    h = u32(B.minhash_sign(ctx, upload(B, ctx, ps), P))
+    ref = orc.sign(ps.xy, ps.offsets, SEED, K, T)
+    assert np.array_equal(h, ref)
+    assert (h[0] == 0).all() and (h[2] == T).all()
+
+
+def test_sign_scale_workload_sampled(B, ctx, orc):
+    """The 1,000,000-polygon, K = 128 workload in the benchmark's launch, sampled rows."""
+    w = synth.WORKLOADS["scale"]
+    db = synth.make_database(w)
+    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed)
+    h = B.minhash_sign(ctx, upload(B, ctx, db), P)
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(db.n, 96, replace=False))
+    rows = np.concatenate([rows, [0, db.n - 1]])
+    sub = db.subset(rows)
+    ref = orc.sign(sub.xy, sub.offsets, w.seed, w.K, w.T, nthreads=16)
+    assert np.array_equal(u32(h[torch.from_numpy(rows).to(DEV)]), ref)
+    # property at every size: all hashes below the cap (every polygon is large enough)
+    assert int(torch.max(h.view(torch.int32))) < w.T
+
+
+def test_band_keys_bit_exact(B, ctx, orc):
+    rng = np.random.default_rng(3)
+    for K, b in ((32, 8), (128, 16), (256, 32), (128, 128)):
+        h = rng.integers(0, 5000, size=(500, K)).astype(np.uint32)
+        h[rng.random(h.shape) < 0.02] = T24
+        P = B.make_params(K, b)
+        keys = B.band_keys(ctx, torch.from_numpy(h.view(np.int32)).to(DEV), P)
+        ref = orc.band_keys(h, b, K // b, T24, 0x15A)
+        assert np.array_equal(keys.cpu().numpy().view(np.uint64), ref)
+
+
+def run_pipeline(B, ctx, w, db, qs, K, b, T):
+    P = B.make_params(K, b, T, w.seed, w.lsh_seed)
+    dbp, qp = upload(B, ctx, db), upload(B, ctx, qs)
+    h = B.minhash_sign(ctx, dbp, P)
+    qh = B.minhash_sign(ctx, qp, P)
+    index = B.lsh_build(ctx, h, P)
+    row_ptr, cand = B.lsh_query(ctx, index, qh)
+    return P, dbp, qp, h, qh, index, row_ptr, cand
+
+
+@pytest.mark.parametrize("K,b,T", [(32, 8, T24), (32, 16, T24), (32, 32, 60), (128, 128, T24)])
+def test_candidates_bit_exact(B, ctx, orc, small, K, b, T):
+    w, db, qs = small
+    P, dbp, qp, h, qh, index, row_ptr, cand = run_pipeline(B, ctx, w, db, qs, K, b, T)
+    h_ref = orc.sign(db.xy, db.offsets, w.seed, K, T, nthreads=8)
+    qh_ref = orc.sign(qs.xy, qs.offsets, w.seed, K, T, nthreads=8)
+    assert np.array_equal(u32(h), h_ref) and np.array_equal(u32(qh), qh_ref)
+    rp_ref, cand_ref = orc.candidates(qh_ref, h_ref, b, K // b, T)
+    assert np.array_equal(row_ptr.cpu().numpy(), rp_ref)
+    assert np.array_equal(cand.cpu().numpy(), cand_ref)
+    # agreement counts and band bits
+    count, mask = B.jaccard_estimate(ctx, qh, h, row_ptr, cand, P)
+    c_ref, m_ref = orc.agree(qh_ref, h_ref, b, K // b, T, rp_ref, cand_ref)
+    assert np.array_equal(count.cpu().numpy().view(np.uint16), c_ref)
+    assert np.array_equal(mask.cpu().numpy().view(np.uint32), m_ref)
+    # top-m by (count desc, id asc)
+    for m in (1, 5, 64):
+        ids, nn = B.topm(ctx, row_ptr, cand, count, m)
+        ids_ref, nn_ref = orc.topm_by_count(rp_ref, cand_ref, c_ref, m)
+        assert np.array_equal(ids.cpu().numpy(), ids_ref)
+        assert np.array_equal(nn.cpu().numpy(), nn_ref)
+
+
+def test_query_capacity_and_empty(B, ctx, small):
+    w, db, qs = small
+    P, dbp, qp, h, qh, index, row_ptr, cand = run_pipeline(B, ctx, w, db, qs, 32, 8, T24)
+    total = cand.numel()
+    assert total > 0
+    with pytest.raises(B.PmhError) as ei:
+        B.lsh_query(ctx, index, qh, capacity=total - 1)
+    assert ei.value.code == B.PMH_ERR_CAPACITY
+    rp0, c0 = B.lsh_query(ctx, index, qh[:0])
+    assert rp0.cpu().tolist() == [0] and c0.numel() == 0
+
+
+def test_agreement_on_dense_pairs_with_sentinels(B, ctx, orc):
+    rng = np.random.default_rng(9)
+    for K, b in ((128, 16), (256, 32), (36, 4), (30, 5)):
+        ph = rng.integers(0, 3, size=(40, K)).astype(np.uint32)
+        ph[rng.random(ph.shape) < 0.1] = T24
+        qh = ph[:7].copy()
+        qh[:, ::3] = rng.integers(0, 3, size=qh[:, ::3].shape)
+        row_ptr = np.arange(8, dtype=np.int64) * 40
+        cand = np.tile(np.arange(40, dtype=np.int32), 7)
+        P = B.make_params(K, b)
+        count, mask = B.jaccard_estimate(ctx, torch.from_numpy(qh.view(np.int32)).to(DEV),
+                                         torch.from_numpy(ph.view(np.int32)).to(DEV),
+                                         torch.from_numpy(row_ptr).to(DEV),
+                                         torch.from_numpy(cand).to(DEV), P)
+        c_ref, m_ref = orc.agree(qh, ph, b, K // b, T24, row_ptr, cand)
+        assert np.array_equal(count.cpu().numpy().view(np.uint16), c_ref)
+        assert np.array_equal(mask.cpu().numpy().view(np.uint32), m_ref)
+
+
+def test_topm_large_rows_and_scores(B, ctx):
+    rng = np.random.default_rng(4)
+    lens = [0, 1, 7, 3000, 5000]
+    row_ptr = np.zeros(len(lens) + 1, np.int64)
+    row_ptr[1:] = np.cumsum(lens)
+    E = int(row_ptr[-1])
+    cand = rng.integers(0, 1 << 30, E).astype(np.int32)
+    count = rng.integers(0, 40, E).astype(np.uint16)
+    score = rng.random(E).astype(np.float32)
+    score[::5] = score[1::5][: len(score[::5])] if E > 5 else score[::5]
+    t = lambda a: torch.from_numpy(a).to(DEV)
+    for m in (1, 10, 1024):
+        ids, nn = B.topm(ctx, t(row_ptr), t(cand), t(count.view(np.int16)), m)
+        ids_s, nn_s = B.topm(ctx, t(row_ptr), t(cand), t(count.view(np.int16)), m, score=t(score))
+        for q in range(len(lens)):
+            seg = slice(row_ptr[q], row_ptr[q + 1])
+            exp = [c for _, c in sorted(zip(-count[seg].astype(int), cand[seg]))][:m]
+            exp_s = [c for _, c in sorted(zip(-score[seg].astype(np.float64), cand[seg]))][:m]
+            got = ids.cpu().numpy()[q]
+            got_s = ids_s.cpu().numpy()[q]
+            assert list(got[:len(exp)]) == exp and (got[len(exp):] == -1).all()
+            assert list(got_s[:len(exp_s)]) == exp_s
+            assert nn.cpu().numpy()[q] == len(exp)
+
+
+def test_pair_jaccard_matches_oracle(B, ctx, orc, small):
+    w, db, qs = small
+    dbp, qp = upload(B, ctx, db), upload(B, ctx, qs)
+    rng = np.random.default_rng(2)
+    qid = np.repeat(np.arange(qs.n, dtype=np.int32), 6)
+    pid = np.empty_like(qid)
+    for q in range(qs.n):
+        pid[q * 6] = qs.source[q]
+        pid[q * 6 + 1:q * 6 + 6] = rng.integers(0, db.n, 5)
+    j = B.pair_jaccard(ctx, qp, dbp, torch.from_numpy(qid).to(DEV), torch.from_numpy(pid).to(DEV))
+    j = j.cpu().numpy()
+    for e in range(len(qid)):
+        ref = orc.jaccard(qs.poly(int(qid[e])), db.poly(int(pid[e])))
+        assert abs(j[e] - ref) <= 1e-9 * max(ref, 1e-300) + 1e-12, (e, j[e], ref)
+
+
+def test_pair_jaccard_degenerate_contacts(B, ctx, orc):
+    """Identical polygons, shared edges, vertex-on-edge, nested, golden closed forms."""
+    import os
+    from test_oracle_area import load_golden
+    pairs = [(a, b) for _, a, b, _, _ in load_golden()]
+    sq = [[0, 0], [10, 0], [10, 10], [0, 10]]
+    pairs += [
+        (sq, sq),
+        (sq, [[10, 0], [20, 0], [20, 10], [10, 10]]),            # shared edge, disjoint
+        (sq, [[5, 0], [15, 0], [15, 10], [5, 10]]),              # overlapping collinear edges
+        (sq, [[5, 5], [10, 0], [10, 10]]),                       # vertex on edge, inside
+        (sq, [[0, 0], [10, 10], [0, 10]]),                       # diagonal half
+        (sq[::-1], [[2, 2], [8, 2], [8, 8], [2, 8]]),            # orientation mix, nested
+        ([[0, 0], [4, 0], [4, 2], [2, 2], [2, 4], [0, 4]], [[2, 2], [6, 2], [6, 6], [2, 6]]),
+    ]
+    ps_a = from_polys([a for a, _ in pairs])
+    ps_b = from_polys([b for _, b in pairs])
+    pa, pb = upload(B, ctx, ps_a), upload(B, ctx, ps_b)
+    idx = torch.arange(len(pairs), dtype=torch.int32, device=DEV)
+    j = B.pair_jaccard(ctx, pa, pb, idx, idx).cpu().numpy()
+    for e, (a, b) in enumerate(pairs):
+        ref = orc.jaccard(np.asarray(a, np.int32), np.asarray(b, np.int32))
+        assert abs(j[e] - ref) <= 1e-12 + 1e-9 * ref, (e, j[e], ref)
+
+
+def test_refine_topk_matches_oracle(B, ctx, orc, small):
+    w, db, qs = small
+    P, dbp, qp, h, qh, index, row_ptr, cand = run_pipeline(B, ctx, w, db, qs, 32, 32, T24)
+    count, _ = B.jaccard_estimate(ctx, qh, h, row_ptr, cand, P)
+    m, k = 32, 10
+    ids, nn = B.topm(ctx, row_ptr, cand, count, m)
+    top_ids, top_j = B.refine_topk(ctx, qp, dbp, ids, nn, k)
+    ids, nn = ids.cpu().numpy(), nn.cpu().numpy()
+    top_ids, top_j = top_ids.cpu().numpy(), top_j.cpu().numpy()
+    for q in range(qs.n):
+        js = [(orc.jaccard(qs.poly(q), db.poly(int(p))), int(p)) for p in ids[q, :nn[q]]]
+        js.sort(key=lambda t: (-t[0], t[1]))
+        exp = js[:k]
+        for s, (jr, pr) in enumerate(exp):
+            assert abs(top_j[q, s] - jr) <= 1e-9 * max(jr, 1e-300) + 1e-12
+            # ids equal unless the Jaccard values tie within rounding
+            if top_ids[q, s] != pr:
+                assert abs(orc.jaccard(qs.poly(q), db.poly(int(top_ids[q, s]))) - jr) < 1e-9
+        assert (top_ids[q, len(exp):] == -1).all()
