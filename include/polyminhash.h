@@ -189,6 +189,34 @@ int pmh_refine_topk(pmh_ctx ctx, pmh_polys queries, pmh_polys db, const int32_t*
 int pmh_pair_jaccard(pmh_ctx ctx, pmh_polys queries, pmh_polys db, const int32_t* d_qid,
                      const int32_t* d_pid, int64_t n_pairs, double* d_j, void* stream);
 
+/* Allocation-free signing (the paper has no counterpart: this is a deployment
+ * entry point).  Same hashes as pmh_minhash_sign, for callers that must not
+ * let a library allocate device memory: processes that reserve their whole
+ * device-memory budget up front, hosts whose memory is owned by a caching
+ * allocator that a side cudaMalloc would fragment or starve, and
+ * latency-critical loops that cannot absorb the device-wide synchronisation of
+ * cudaFree.  It takes raw device arrays instead of a pmh_polys handle and needs
+ * no pmh_ctx:
+ *   d_xy       int32 [n_vertices][2] interleaved (x, y), device
+ *   d_offsets  int64 [n_polys + 1], device (same layout as pmh_poly_upload)
+ *   d_hashes   uint32 [n_polys][K], device, written completely
+ * It runs on the current device and calls no cudaMalloc, cudaFree or
+ * allocating library routine.  Its scratch (work-queue ticket, validation
+ * word, one bounding box per polygon) is a fixed device array of
+ * PMH_NOALLOC_MAX_POLYS + 1 16-byte entries (4 MiB) that every GPU loading
+ * the library holds until the process exits; n_polys above
+ * PMH_NOALLOC_MAX_POLYS is rejected with PMH_ERR_RANGE before any GPU work.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call
+ * shares the one array and clears its ticket and flags itself, so calls that
+ * overlap on the GPU (two streams, two threads) race: serialise them.
+ * Synchronises `stream` once to report validation failures, like
+ * pmh_poly_upload, with the same error codes. */
+#define PMH_NOALLOC_MAX_POLYS 262144
+int pmh_minhash_sign_noalloc(const int32_t* d_xy, const int64_t* d_offsets, int64_t n_polys,
+                             int64_t n_vertices, const pmh_params* params, uint32_t* d_hashes,
+                             void* stream);
+
 /* Integer-ALU throughput probe used as the roofline denominator: runs a
  * fixed mix of 32-bit integer instructions (add, logic, shift, multiply-add)
  * on every SM and reports integer instructions per second (thread level).

@@ -67,6 +67,8 @@ _SIGS = {
     "pmh_probe_int_peak": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]),
     "pmh_launch_count": (_i64, []),
+    "pmh_minhash_sign_noalloc": (ctypes.c_int, [_P, _P, _i64, _i64, ctypes.POINTER(Params), _P,
+                                                _P]),
 }
 
 
@@ -200,6 +202,26 @@ def minhash_sign(ctx: Context, polys: Polys, params: Params, out: torch.Tensor |
                           device=torch.device("cuda", ctx.device))
     _check(load().pmh_minhash_sign(ctx.handle, polys.handle, ctypes.byref(params), _ptr(out),
                                    _stream(stream)))
+    return out
+
+
+NOALLOC_MAX_POLYS = 262144
+
+
+def minhash_sign_noalloc(xy: torch.Tensor, offsets: torch.Tensor, params: Params,
+                         out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Allocation-free A1 on raw device arrays (no context, no polygon handle).
+
+    The library allocates nothing for this call (its scratch is a fixed device array of
+    NOALLOC_MAX_POLYS bounding boxes); `out` is allocated here by torch only when the caller
+    does not pass one.  Calls that overlap on the GPU share that array and race.
+    """
+    assert xy.dtype == torch.int32 and offsets.dtype == torch.int64
+    n = offsets.numel() - 1
+    if out is None:
+        out = torch.empty((n, params.K), dtype=torch.int32, device=xy.device)
+    _check(load().pmh_minhash_sign_noalloc(_ptr(xy), _ptr(offsets), n, xy.shape[0],
+                                           ctypes.byref(params), _ptr(out), _stream(stream)))
     return out
 
 

@@ -21,6 +21,7 @@
 // SM count), which balances polygons whose expected work differs by 100x
 // (Theorem 2: E[h] = 1/S_p).
 #include <algorithm>
+#include <mutex>
 
 #include "pmh_internal.cuh"
 
@@ -147,5 +148,167 @@ extern "C" int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* 
                                                     params->seed, (int)params->K, params->T,
                                                     chunks, n_items, ticket, d_hashes);
     PMH_LAUNCHED("sign_kernel");
+    return PMH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the signing entry point.
+//
+// Some callers cannot let a library call cudaMalloc: a process that reserves
+// its whole device-memory budget at start-up, a host whose memory belongs to a
+// caching allocator that a side allocation would fragment or starve, or a
+// latency-critical loop that cannot absorb the device-wide synchronisation
+// cudaFree implies.  For them the scratch this path needs -- the work-queue
+// ticket, a validation word and every polygon's bounding box -- lives in one
+// file-scope device array, reserved when the library is loaded on a GPU and
+// held by every GPU that loads the library until the process exits.
+// ---------------------------------------------------------------------------
+// element 0: .x/.y = 64-bit work ticket, .z = validation flags; elements 1..:
+// clipped bounding boxes of polygons 0 .. PMH_NOALLOC_MAX_POLYS-1 (4 MiB in all)
+static __device__ __align__(256) int4 g_sign_scratch[PMH_NOALLOC_MAX_POLYS + 1];
+
+namespace {
+
+__global__ void noalloc_prep_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
+                                    int64_t n_polys, int64_t n_vertices, int4* __restrict__ scratch)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int LIM = 1 << 20;
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < n_polys;
+         p += nwarps) {
+        int64_t b = off[p], e = off[p + 1];
+        int flags = (b < 0 || e > n_vertices || e < b) ? 1 : 0;
+        if (e - b < 3) flags |= 2;
+        int x0 = 0x7fffffff, y0 = 0x7fffffff, x1 = -0x7fffffff - 1, y1 = -0x7fffffff - 1;
+        if (!flags)
+            for (int64_t i = b + lane; i < e; i += 32) {
+                int2 v = xy[i];
+                if (v.x < -LIM || v.x > LIM || v.y < -LIM || v.y > LIM) flags |= 4;
+                x0 = min(x0, v.x);
+                x1 = max(x1, v.x);
+                y0 = min(y0, v.y);
+                y1 = max(y1, v.y);
+            }
+        x0 = __reduce_min_sync(0xffffffffu, x0);
+        y0 = __reduce_min_sync(0xffffffffu, y0);
+        x1 = __reduce_max_sync(0xffffffffu, x1);
+        y1 = __reduce_max_sync(0xffffffffu, y1);
+        flags = __reduce_or_sync(0xffffffffu, flags);
+        if (lane == 0) {
+            if (flags) {
+                atomicOr(&scratch[0].z, flags);
+                scratch[1 + p] = make_int4(0, 0, 0, 0);
+            } else {
+                int cx0 = max(x0, 0), cy0 = max(y0, 0), cx1 = min(x1, 65536), cy1 = min(y1, 65536);
+                scratch[1 + p] = make_int4(cx0, cy0, max(cx1, cx0), max(cy1, cy0));
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kWarps * 32)
+noalloc_sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off, uint64_t seed,
+                    int K, uint32_t T, int chunks, int64_t n_items, int4* __restrict__ scratch,
+                    uint32_t* __restrict__ out)
+{
+    __shared__ __align__(16) int2 sv[kWarps][kSmemVerts];
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
+    unsigned long long* ticket = reinterpret_cast<unsigned long long*>(&scratch[0]);
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(ticket, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if ((int64_t)item >= n_items) break;
+        const int64_t p = (int64_t)(item / (unsigned)chunks);
+        const int k0 = (int)(item % (unsigned)chunks) * 32;
+        const int64_t b = off[p];
+        const int n = (int)(off[p + 1] - b);
+        const int4 bb = scratch[1 + p];
+        const int2* v = xy + b;
+        if (n <= kSmemVerts) {
+            for (int i = lane; i < n; i += 32) sv[wid][i] = v[i];
+            __syncwarp();
+            v = sv[wid];
+        }
+        const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
+        uint32_t mine = T;
+        const int kend = min(K, k0 + 32);
+        for (int k = k0; k < kend; ++k) {
+            uint64_t sk = pmh_mix64(seed + (uint64_t)(k + 1) * PMH_GAMMA);
+            uint32_t hk = sign_one(v, n, bb.x, bb.y, w, h, sk, T, lane);
+            if (lane == k - k0) mine = hk;
+        }
+        if (k0 + lane < kend) out[p * (int64_t)K + k0 + lane] = mine;
+        __syncwarp();
+    }
+}
+
+struct NoallocDevice {
+    int4* scratch = nullptr;  // device address of g_sign_scratch on this device
+    int sm_count = 0;
+    int blocks_per_sm = 0;
+};
+std::mutex g_noalloc_mutex;
+NoallocDevice g_noalloc_dev[64];
+
+}  // namespace
+
+extern "C" int pmh_minhash_sign_noalloc(const int32_t* d_xy, const int64_t* d_offsets,
+                                        int64_t n_polys, int64_t n_vertices,
+                                        const pmh_params* params, uint32_t* d_hashes, void* stream)
+{
+    PMH_TRY(pmh_check_params(params));
+    if (n_polys < 0 || n_vertices < 0 || !d_offsets || (n_polys > 0 && (!d_xy || !d_hashes)))
+        return pmh_set_error(PMH_ERR_ARG, "bad arguments (n_polys=%lld n_vertices=%lld)",
+                             (long long)n_polys, (long long)n_vertices);
+    if (n_polys > PMH_NOALLOC_MAX_POLYS)
+        return pmh_set_error(PMH_ERR_RANGE,
+                             "pmh_minhash_sign_noalloc handles at most %d polygons per call "
+                             "(got %lld); split the batch or use pmh_minhash_sign",
+                             PMH_NOALLOC_MAX_POLYS, (long long)n_polys);
+    if (n_polys == 0) return PMH_OK;
+    int dev = 0;
+    PMH_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return pmh_set_error(PMH_ERR_ARG, "device %d out of range", dev);
+    NoallocDevice nd;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        NoallocDevice& slot = g_noalloc_dev[dev];
+        if (!slot.scratch) {  // once per device, with that device current
+            void* p = nullptr;
+            PMH_CUDA_TRY(cudaGetSymbolAddress(&p, g_sign_scratch));
+            int sms = 0, per_sm = 0;
+            PMH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, noalloc_sign_kernel,
+                                                                       kWarps * 32, 0));
+            slot.sm_count = sms;
+            slot.blocks_per_sm = per_sm > 0 ? per_sm : 1;
+            slot.scratch = static_cast<int4*>(p);
+        }
+        nd = slot;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: clear the ticket and the flags
+    PMH_CUDA_TRY(cudaMemsetAsync(nd.scratch, 0, sizeof(int4), s));
+    int prep_blocks = (int)std::min<int64_t>((n_polys + kWarps - 1) / kWarps, (int64_t)nd.sm_count * 16);
+    noalloc_prep_kernel<<<prep_blocks, kWarps * 32, 0, s>>>(
+        reinterpret_cast<const int2*>(d_xy), d_offsets, n_polys, n_vertices, nd.scratch);
+    PMH_LAUNCHED("noalloc_prep_kernel");
+    int4 head;
+    PMH_CUDA_TRY(cudaMemcpyAsync(&head, nd.scratch, sizeof(int4), cudaMemcpyDeviceToHost, s));
+    PMH_CUDA_TRY(cudaStreamSynchronize(s));
+    if (head.z & 1) return pmh_set_error(PMH_ERR_RANGE, "offsets are not increasing / in range");
+    if (head.z & 2) return pmh_set_error(PMH_ERR_RANGE, "a polygon has fewer than 3 vertices");
+    if (head.z & 4) return pmh_set_error(PMH_ERR_RANGE, "a coordinate exceeds |2^20|");
+    const int chunks = (int)((params->K + 31) / 32);
+    const int64_t n_items = n_polys * chunks;
+    int64_t blocks = (int64_t)nd.sm_count * nd.blocks_per_sm;
+    blocks = std::min<int64_t>(blocks, (n_items + kWarps - 1) / kWarps);
+    noalloc_sign_kernel<<<(int)blocks, kWarps * 32, 0, s>>>(
+        reinterpret_cast<const int2*>(d_xy), d_offsets, params->seed, (int)params->K, params->T,
+        chunks, n_items, nd.scratch, d_hashes);
+    PMH_LAUNCHED("noalloc_sign_kernel");
     return PMH_OK;
 }
