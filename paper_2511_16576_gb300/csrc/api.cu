@@ -227,6 +227,9 @@ static int upload_common(pmh_ctx ctx, const int32_t* xy, const int64_t* offsets,
     if (st[0] & 2) return fail(pmh_set_error(PMH_ERR_RANGE, "a polygon has fewer than 3 vertices"));
     if (st[0] & 4) return fail(pmh_set_error(PMH_ERR_RANGE, "a coordinate exceeds |2^20|"));
     P->max_n = st[1];
+    int rc = pmh_build_slabs(P, s);
+    if (rc == PMH_OK) rc = pmh_build_cost_order(P, s);
+    if (rc != PMH_OK) return fail(rc);
     *out = P;
     return PMH_OK;
 }
@@ -270,10 +273,10 @@ extern "C" int pmh_polys_destroy(pmh_polys p)
     if (!p) return PMH_OK;
     if (p->ctx) cudaSetDevice(p->ctx->device);
     if (p->xy || p->offsets || p->bbox || p->area2) cudaDeviceSynchronize();
-    if (p->xy) cudaFree(p->xy);
-    if (p->offsets) cudaFree(p->offsets);
-    if (p->bbox) cudaFree(p->bbox);
-    if (p->area2) cudaFree(p->area2);
+    void* bufs[] = {p->xy, p->offsets, p->bbox, p->area2, p->slab_info, p->slab_ptr,
+                    p->slab_edges, p->order};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
     delete p;
     return PMH_OK;
 }

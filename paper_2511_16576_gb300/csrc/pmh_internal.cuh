@@ -63,6 +63,16 @@ struct pmh_ctx_s {
     int64_t* h_pinned = nullptr;          // small pinned host buffer [64]
 };
 
+// per-polygon y-slab edge index (slabs.cu); S == 0 for polygons without one
+struct SlabInfo {
+    int64_t slab_base;  // first entry of the polygon's slab table in slab_ptr
+    int64_t edge_base;  // first entry of its edge lists in slab_edges
+    int32_t S;          // number of slabs
+    int32_t slab_h;     // slab height (rows)
+    int32_t ymin;       // lowest vertex y
+};
+constexpr int kSlabMinVerts = 256;  // polygons above this size get a slab index
+
 struct pmh_polys_s {
     pmh_ctx ctx = nullptr;
     int64_t n = 0, nv = 0;
@@ -71,7 +81,14 @@ struct pmh_polys_s {
     int4* bbox = nullptr;      // x0, y0, x1, y1 half-open, clipped to the domain
     int64_t* area2 = nullptr;  // twice the signed area
     int32_t max_n = 0;         // largest vertex count
+    SlabInfo* slab_info = nullptr;  // [n]
+    int32_t* slab_ptr = nullptr;
+    int32_t* slab_edges = nullptr;
+    int32_t* order = nullptr;       // polygons by expected signing cost, largest first
 };
+
+int pmh_build_slabs(pmh_polys P, cudaStream_t s);
+int pmh_build_cost_order(pmh_polys P, cudaStream_t s);
 
 struct pmh_index_s {
     pmh_ctx ctx = nullptr;

@@ -7,7 +7,8 @@
 // almost every point, and the exact point-in-polygon test runs ~2-3 times per
 // hash.  One warp owns a work item (polygon p, 32 consecutive hashes):
 //   * the polygon's vertices are staged once into the warp's shared-memory
-//     slice with 16-byte loads;
+//     slice (polygons of more than 256 vertices are read from global memory
+//     through their y-slab edge index instead, see slabs.cu);
 //   * per round every lane draws U points (indices i0 + j*32 + lane), so one
 //     round covers 32*U consecutive stream indices; the counter-based stream
 //     lets each lane jump straight to its own index;
@@ -18,8 +19,9 @@
 //   * lane j keeps the hash of k0 + j and the warp writes 32 hashes with one
 //     coalesced store.
 // Items are handed out by a global atomic ticket (persistent grid sized to the
-// SM count), which balances polygons whose expected work differs by 100x
-// (Theorem 2: E[h] = 1/S_p).
+// SM count) in decreasing order of expected cost (2^32 / area per hash,
+// Theorem 2: E[h] = 1/S_p), which balances polygons whose work differs by
+// orders of magnitude.
 #include <algorithm>
 #include <mutex>
 
@@ -50,10 +52,54 @@ __device__ __forceinline__ bool warp_inside(const int2* __restrict__ v, int n, i
     return __popc(__ballot_sync(0xffffffffu, par)) & 1;
 }
 
+// Exact membership through the polygon's y-slab index: only the edges listed
+// for the slab holding py can straddle the line y = py.
+__device__ __forceinline__ bool warp_inside_slab(const int2* __restrict__ v, int n,
+                                                 const int32_t* __restrict__ sp,
+                                                 const int32_t* __restrict__ se, int slab_h,
+                                                 int ymin, int px, int py, int lane)
+{
+    const int s = (py - ymin) / slab_h;
+    const int lo = sp[s], hi = sp[s + 1];
+    unsigned par = 0;
+    for (int i = lo + lane; i < hi; i += 32) {
+        int e = se[i];
+        int2 a = v[e];
+        int2 b = v[e + 1 == n ? 0 : e + 1];
+        bool st = (a.y > py) != (b.y > py);
+        if (st) {
+            long long cr = (long long)(b.x - a.x) * (py - a.y) - (long long)(px - a.x) * (b.y - a.y);
+            par ^= (cr != 0) & ((cr > 0) == (b.y > a.y));
+        }
+    }
+    return __popc(__ballot_sync(0xffffffffu, par)) & 1;
+}
+
+struct AllEdges {
+    const int2* v;
+    int n;
+    __device__ __forceinline__ bool operator()(int px, int py, int lane) const
+    {
+        return warp_inside(v, n, px, py, lane);
+    }
+};
+
+struct SlabEdges {
+    const int2* v;
+    int n;
+    const int32_t* sp;
+    const int32_t* se;
+    int slab_h, ymin;
+    __device__ __forceinline__ bool operator()(int px, int py, int lane) const
+    {
+        return warp_inside_slab(v, n, sp, se, slab_h, ymin, px, py, lane);
+    }
+};
+
 // One hash of one polygon; every lane returns the same value.
-__device__ __forceinline__ uint32_t sign_one(const int2* __restrict__ v, int n, int x0, int y0,
-                                             uint32_t w, uint32_t h, uint64_t sk, uint32_t T,
-                                             int lane)
+template <class Inside>
+__device__ __forceinline__ uint32_t sign_one_t(const Inside& inside, int x0, int y0, uint32_t w,
+                                               uint32_t h, uint64_t sk, uint32_t T, int lane)
 {
     if (w == 0 || h == 0) return T;
     uint64_t z = sk + (uint64_t)(lane + 1) * PMH_GAMMA;
@@ -80,16 +126,40 @@ __device__ __forceinline__ uint32_t sign_one(const int2* __restrict__ v, int n, 
                 uint32_t i = i0 + (uint32_t)(j * 32 + l);
                 if (i >= T) return T;
                 uint32_t r = __shfl_sync(0xffffffffu, pts[j], l);
-                if (warp_inside(v, n, (int)(r & 0xFFFFu), (int)(r >> 16), lane)) return i;
+                if (inside((int)(r & 0xFFFFu), (int)(r >> 16), lane)) return i;
             }
         }
     }
     return T;
 }
 
+__device__ __forceinline__ uint32_t sign_one(const int2* __restrict__ v, int n, int x0, int y0,
+                                             uint32_t w, uint32_t h, uint64_t sk, uint32_t T,
+                                             int lane)
+{
+    return sign_one_t(AllEdges{v, n}, x0, y0, w, h, sk, T, lane);
+}
+
+// the hashes k0 .. k0+31 of one polygon; lane j returns hash k0 + j
+template <class Inside>
+__device__ __forceinline__ uint32_t sign_chunk(const Inside& inside, int4 bb, uint64_t seed, int k0,
+                                               int kend, uint32_t T, int lane)
+{
+    const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
+    uint32_t mine = T;
+    for (int k = k0; k < kend; ++k) {
+        uint64_t sk = pmh_mix64(seed + (uint64_t)(k + 1) * PMH_GAMMA);
+        uint32_t hk = sign_one_t(inside, bb.x, bb.y, w, h, sk, T, lane);
+        if (lane == k - k0) mine = hk;
+    }
+    return mine;
+}
+
 __global__ void __launch_bounds__(kWarps * 32)
 sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
-            const int4* __restrict__ bbox, uint64_t seed, int K, uint32_t T, int chunks,
+            const int4* __restrict__ bbox, const SlabInfo* __restrict__ slabs,
+            const int32_t* __restrict__ slab_ptr, const int32_t* __restrict__ slab_edges,
+            const int32_t* __restrict__ order, uint64_t seed, int K, uint32_t T, int chunks,
             int64_t n_items, unsigned long long* __restrict__ ticket, uint32_t* __restrict__ out)
 {
     __shared__ __align__(16) int2 sv[kWarps][kSmemVerts];
@@ -100,25 +170,26 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
         if (lane == 0) item = atomicAdd(ticket, 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
         if ((int64_t)item >= n_items) break;
-        const int64_t p = (int64_t)(item / (unsigned)chunks);
+        const int64_t slot = (int64_t)(item / (unsigned)chunks);
+        const int64_t p = order ? (int64_t)order[slot] : slot;
         const int k0 = (int)(item % (unsigned)chunks) * 32;
+        const int kend = min(K, k0 + 32);
         const int64_t b = off[p];
         const int n = (int)(off[p + 1] - b);
         const int4 bb = bbox[p];
-        const int2* v = xy + b;
+        uint32_t mine;
         if (n <= kSmemVerts) {
-            // stage vertices: 8-byte aligned source, so copy int2 by int2 (coalesced)
-            for (int i = lane; i < n; i += 32) sv[wid][i] = v[i];
+            // stage the vertices in this warp's shared-memory slice (coalesced 8-byte loads)
+            for (int i = lane; i < n; i += 32) sv[wid][i] = xy[b + i];
             __syncwarp();
-            v = sv[wid];
-        }
-        const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
-        uint32_t mine = T;
-        const int kend = min(K, k0 + 32);
-        for (int k = k0; k < kend; ++k) {
-            uint64_t sk = pmh_mix64(seed + (uint64_t)(k + 1) * PMH_GAMMA);
-            uint32_t hk = sign_one(v, n, bb.x, bb.y, w, h, sk, T, lane);
-            if (lane == k - k0) mine = hk;
+            mine = sign_chunk(AllEdges{sv[wid], n}, bb, seed, k0, kend, T, lane);
+        } else if (slabs && slabs[p].S > 0) {
+            const SlabInfo si = slabs[p];
+            mine = sign_chunk(SlabEdges{xy + b, n, slab_ptr + si.slab_base, slab_edges + si.edge_base,
+                                        si.slab_h, si.ymin},
+                              bb, seed, k0, kend, T, lane);
+        } else {
+            mine = sign_chunk(AllEdges{xy + b, n}, bb, seed, k0, kend, T, lane);
         }
         if (k0 + lane < kend) out[p * (int64_t)K + k0 + lane] = mine;
         __syncwarp();
@@ -144,9 +215,10 @@ extern "C" int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* 
     PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sign_kernel, kWarps * 32, 0));
     int64_t blocks = (int64_t)ctx->sm_count * std::max(per_sm, 1);
     blocks = std::min<int64_t>(blocks, (n_items + kWarps - 1) / kWarps);
-    sign_kernel<<<(int)blocks, kWarps * 32, 0, s>>>(polys->xy, polys->offsets, polys->bbox,
-                                                    params->seed, (int)params->K, params->T,
-                                                    chunks, n_items, ticket, d_hashes);
+    sign_kernel<<<(int)blocks, kWarps * 32, 0, s>>>(
+        polys->xy, polys->offsets, polys->bbox, polys->slab_info, polys->slab_ptr,
+        polys->slab_edges, polys->order, params->seed, (int)params->K, params->T, chunks, n_items,
+        ticket, d_hashes);
     PMH_LAUNCHED("sign_kernel");
     return PMH_OK;
 }

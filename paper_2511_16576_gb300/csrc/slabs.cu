@@ -1,0 +1,227 @@
+// slabs.cu -- per-polygon y-slab edge index and cost order (part of step A0,
+// used by the batching path of A1).
+//
+// The exact membership test of a point at height py only involves edges that
+// straddle the horizontal line through it.  For a polygon with many vertices
+// (coastline-like boundaries with up to 65,536 vertices) the y-range of its
+// bounding box is cut into S equal slabs and every slab lists the edges whose
+// row range [min(ay,by), max(ay,by)) meets it.  A test then reads one slab's
+// list instead of all n edges; the parity of the crossings is order-independent,
+// so the order inside a list does not matter.
+//
+// Layout (only polygons with n > kSlabMinVerts get slabs):
+//   slab_info[p] = {slab_base, edge_base, S, slab_h | ymin}: see SlabInfo
+//   slab_ptr[slab_base .. slab_base + S]  int32 offsets into the edge list
+//   slab_edges[edge_base + ...]           int32 local edge ids (edge e = v_e -> v_e+1)
+//
+// The cost order sorts polygons by the expected number of stream points per
+// hash, 2^32 / area (Theorem 2, E[h] = 1/S_p), largest first, so that the
+// persistent signing grid starts the longest items first.
+#include <algorithm>
+
+#include "pmh_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ int slab_count_for(int n, int height)
+{
+    int s = n / 4;
+    s = max(s, 1);
+    s = min(s, max(height, 1));
+    return min(s, 1 << 16);
+}
+
+// pass 1: sizes of every polygon's slab table and edge list
+__global__ void slab_size_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
+                                 int64_t n_polys, int min_verts, SlabInfo* __restrict__ info,
+                                 int64_t* __restrict__ ptr_sizes, int64_t* __restrict__ edge_sizes)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < n_polys;
+         p += nwarps) {
+        const int64_t b = off[p];
+        const int n = (int)(off[p + 1] - b);
+        if (n <= min_verts) {
+            if (lane == 0) {
+                info[p] = SlabInfo{0, 0, 0, 1, 0};
+                ptr_sizes[p] = 0;
+                edge_sizes[p] = 0;
+            }
+            continue;
+        }
+        int y0 = 0x7fffffff, y1 = -0x7fffffff - 1;
+        for (int i = lane; i < n; i += 32) {
+            int y = xy[b + i].y;
+            y0 = min(y0, y);
+            y1 = max(y1, y);
+        }
+        y0 = __reduce_min_sync(0xffffffffu, y0);
+        y1 = __reduce_max_sync(0xffffffffu, y1);
+        const int height = y1 - y0;
+        const int S = slab_count_for(n, height);
+        const int h = max((height + S - 1) / S, 1);
+        long long entries = 0;
+        for (int e = lane; e < n; e += 32) {
+            int ay = xy[b + e].y, by = xy[b + (e + 1 == n ? 0 : e + 1)].y;
+            if (ay == by) continue;
+            int lo = min(ay, by) - y0, hi = max(ay, by) - 1 - y0;
+            entries += hi / h - lo / h + 1;
+        }
+        for (int o = 16; o > 0; o >>= 1) entries += __shfl_xor_sync(0xffffffffu, entries, o);
+        if (lane == 0) {
+            info[p] = SlabInfo{0, 0, S, h, y0};
+            ptr_sizes[p] = S + 1;
+            edge_sizes[p] = entries;
+        }
+    }
+}
+
+// pass 2: per polygon (one warp) count, prefix-sum and fill the slab lists
+__global__ void slab_fill_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
+                                 int64_t n_polys, int min_verts, SlabInfo* __restrict__ info,
+                                 const int64_t* __restrict__ ptr_base,
+                                 const int64_t* __restrict__ edge_base, int32_t* __restrict__ slab_ptr,
+                                 int32_t* __restrict__ cursor, int32_t* __restrict__ slab_edges)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < n_polys;
+         p += nwarps) {
+        const int64_t b = off[p];
+        const int n = (int)(off[p + 1] - b);
+        if (n <= min_verts) continue;
+        SlabInfo si = info[p];
+        const int S = si.S, h = si.slab_h, y0 = si.ymin;
+        const int64_t pb = ptr_base[p], eb = edge_base[p];
+        if (lane == 0) {
+            info[p].slab_base = pb;
+            info[p].edge_base = eb;
+        }
+        int32_t* sp = slab_ptr + pb;
+        int32_t* cur = cursor + pb;
+        for (int s = lane; s <= S; s += 32) cur[s] = 0;
+        __syncwarp();
+        for (int e = lane; e < n; e += 32) {
+            int ay = xy[b + e].y, by = xy[b + (e + 1 == n ? 0 : e + 1)].y;
+            if (ay == by) continue;
+            int lo = (min(ay, by) - y0) / h, hi = (max(ay, by) - 1 - y0) / h;
+            for (int s = lo; s <= hi; ++s) atomicAdd(&cur[s], 1);
+        }
+        __syncwarp();
+        __threadfence_block();
+        // exclusive prefix over S + 1 entries, 32 at a time
+        int carry = 0;
+        for (int base = 0; base <= S; base += 32) {
+            int s = base + lane;
+            int v = s < S ? cur[s] : 0;
+            int x = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (s <= S) sp[s] = carry + x - v;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+        __syncwarp();
+        for (int s = lane; s <= S; s += 32) cur[s] = sp[s];
+        __syncwarp();
+        for (int e = lane; e < n; e += 32) {
+            int ay = xy[b + e].y, by = xy[b + (e + 1 == n ? 0 : e + 1)].y;
+            if (ay == by) continue;
+            int lo = (min(ay, by) - y0) / h, hi = (max(ay, by) - 1 - y0) / h;
+            for (int s = lo; s <= hi; ++s) slab_edges[eb + atomicAdd(&cur[s], 1)] = e;
+        }
+        __syncwarp();
+    }
+}
+
+// cost key: expected stream points per hash ~ 2^33 / |area2|, as orderable float bits,
+// complemented so that an ascending sort puts the most expensive polygon first
+__global__ void cost_key_kernel(const int64_t* __restrict__ area2, int64_t n,
+                                uint32_t* __restrict__ keys, int32_t* __restrict__ ids)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        long long a = area2[p];
+        double aa = (double)(a < 0 ? -a : a);
+        float cost = (float)(8589934592.0 / fmax(aa, 1.0));
+        keys[p] = ~__float_as_uint(cost);  // positive floats order like their bits
+        ids[p] = (int32_t)p;
+    }
+}
+
+}  // namespace
+
+int pmh_build_slabs(pmh_polys P, cudaStream_t s)
+{
+    pmh_ctx ctx = P->ctx;
+    if (P->n == 0) return PMH_OK;
+    const int64_t n = P->n;
+    if (cudaMalloc(&P->slab_info, sizeof(SlabInfo) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return pmh_set_error(PMH_ERR_NOMEM, "slab info allocation failed");
+    }
+    if (P->max_n <= kSlabMinVerts) {
+        PMH_CUDA_TRY(cudaMemsetAsync(P->slab_info, 0, sizeof(SlabInfo) * n, s));
+        return PMH_OK;
+    }
+    int64_t* sizes = nullptr;
+    PMH_TRY(pmh_scratch(ctx, SCR_MISC, sizeof(int64_t) * (size_t)(2 * (n + 1)), (void**)&sizes));
+    int64_t* ptr_sizes = sizes;
+    int64_t* edge_sizes = sizes + (n + 1);
+    int blocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)ctx->sm_count * 16);
+    slab_size_kernel<<<blocks, 256, 0, s>>>(P->xy, P->offsets, n, kSlabMinVerts, P->slab_info,
+                                            ptr_sizes, edge_sizes);
+    PMH_LAUNCHED("slab_size_kernel");
+    PMH_TRY(pmh_exclusive_scan_i64(ctx, ptr_sizes, ptr_sizes, n, s));
+    PMH_TRY(pmh_exclusive_scan_i64(ctx, edge_sizes, edge_sizes, n, s));
+    PMH_CUDA_TRY(cudaMemcpyAsync(ctx->h_pinned, ptr_sizes + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    PMH_CUDA_TRY(cudaMemcpyAsync(ctx->h_pinned + 1, edge_sizes + n, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+    PMH_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t n_ptr = ctx->h_pinned[0], n_edges = ctx->h_pinned[1];
+    int32_t* cursor = nullptr;
+    if (cudaMalloc(&P->slab_ptr, sizeof(int32_t) * std::max<int64_t>(n_ptr, 1)) != cudaSuccess ||
+        cudaMalloc(&P->slab_edges, sizeof(int32_t) * std::max<int64_t>(n_edges, 1)) != cudaSuccess ||
+        cudaMalloc(&cursor, sizeof(int32_t) * std::max<int64_t>(n_ptr, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        if (cursor) cudaFree(cursor);
+        return pmh_set_error(PMH_ERR_NOMEM, "slab index allocation failed (%lld entries)",
+                             (long long)n_edges);
+    }
+    slab_fill_kernel<<<blocks, 256, 0, s>>>(P->xy, P->offsets, n, kSlabMinVerts, P->slab_info,
+                                            ptr_sizes, edge_sizes, P->slab_ptr, cursor,
+                                            P->slab_edges);
+    cudaError_t e = cudaGetLastError();
+    g_pmh_launches.fetch_add(1);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(cursor);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return pmh_set_error(PMH_ERR_CUDA, "slab fill failed: %s",
+                             cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return PMH_OK;
+}
+
+int pmh_build_cost_order(pmh_polys P, cudaStream_t s)
+{
+    pmh_ctx ctx = P->ctx;
+    const int64_t n = P->n;
+    if (n == 0) return PMH_OK;
+    uint32_t* keys = nullptr;
+    if (cudaMalloc(&P->order, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMalloc(&keys, sizeof(uint32_t) * n) != cudaSuccess) {
+        cudaGetLastError();
+        if (keys) cudaFree(keys);
+        return pmh_set_error(PMH_ERR_NOMEM, "cost order allocation failed");
+    }
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sm_count * 32);
+    cost_key_kernel<<<blocks, 256, 0, s>>>(P->area2, n, keys, P->order);
+    cudaError_t e = cudaGetLastError();
+    g_pmh_launches.fetch_add(1);
+    int rc = e == cudaSuccess ? pmh_radix_sort_u32(ctx, keys, P->order, n, 32, s)
+                              : pmh_set_error(PMH_ERR_CUDA, "cost key: %s", cudaGetErrorString(e));
+    cudaStreamSynchronize(s);
+    cudaFree(keys);
+    return rc;
+}

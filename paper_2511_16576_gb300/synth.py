@@ -133,8 +133,9 @@ def _fractal_radius(rng, pid: np.ndarray, pos: np.ndarray, n: np.ndarray, amp0: 
                     decay: float = 0.6) -> np.ndarray:
     """Midpoint-displacement radius profile r(t) on t in [0,1), amplitude x decay per level.
 
-    Level l adds 2^l new random offsets; every vertex takes the linear interpolation of each
-    level's periodic control values at its angle, so the sum is a periodic fractal profile.
+    Level l adds 2^l periodic control offsets; a vertex takes the linear interpolation of
+    each level's controls at its angle, so the sum is a periodic fractal profile.  A
+    polygon only receives the levels its own vertex count can resolve (2^l <= 2n).
     """
     t = pos / n[pid]
     r = np.ones(len(pid))
@@ -142,12 +143,19 @@ def _fractal_radius(rng, pid: np.ndarray, pos: np.ndarray, n: np.ndarray, amp0: 
     amp = amp0
     for lev in range(2, levels + 1):
         m = 1 << lev
-        ctrl = rng.uniform(-amp, amp, size=(len(n), m))
-        u = t * m
+        elig = np.nonzero(2 * n >= m)[0]
+        if len(elig) == 0:
+            break
+        row = np.full(len(n), -1, np.int64)
+        row[elig] = np.arange(len(elig))
+        ctrl = rng.uniform(-amp, amp, size=(len(elig), m))
+        sel = row[pid] >= 0
+        u = t[sel] * m
         i0 = np.floor(u).astype(np.int64) % m
         w = u - np.floor(u)
         i1 = (i0 + 1) % m
-        r += (1 - w) * ctrl[pid, i0] + w * ctrl[pid, i1]
+        rr = row[pid[sel]]
+        r[sel] += (1 - w) * ctrl[rr, i0] + w * ctrl[rr, i1]
         amp *= decay
         if amp < 1e-4:
             break

@@ -288,3 +288,44 @@ def test_refine_topk_matches_oracle(B, ctx, orc, small):
             if top_ids[q, s] != pr:
                 assert abs(orc.jaccard(qs.poly(q), db.poly(int(top_ids[q, s]))) - jr) < 1e-9
         assert (top_ids[q, len(exp):] == -1).all()
+
+
+def test_sign_batching_workload_sampled(B, ctx, orc):
+    """Fractal coastline-like polygons with 4..65,536 vertices (slab-index edge path), K = 256."""
+    w = synth.WORKLOADS["batching"]
+    db = synth.make_database(w, 600)
+    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed)
+    h = B.minhash_sign(ctx, upload(B, ctx, db), P)
+    n = np.diff(db.offsets)
+    order = np.argsort(n)
+    rng = np.random.default_rng(1)
+    rows = np.unique(np.concatenate([order[-10:], order[:4], rng.choice(db.n, 10, replace=False)]))
+    sub = db.subset(rows)
+    ref = orc.sign(sub.xy, sub.offsets, w.seed, w.K, w.T, nthreads=16)
+    assert n[rows].max() > 30000
+    assert np.array_equal(u32(h[torch.from_numpy(rows).to(DEV)]), ref)
+
+
+def test_sign_slab_index_degenerate(B, ctx, orc):
+    """Large polygons whose slab lists hold horizontal edges, vertical runs and spikes."""
+    polys = []
+    # comb: 300 teeth, horizontal edges on every tooth, vertices on slab boundaries
+    pts = [[1000, 1000]]
+    for i in range(300):
+        x = 1000 + 20 * i
+        pts += [[x, 3000], [x + 10, 3000], [x + 10, 1200], [x + 20, 1200]]
+    pts += [[1000 + 20 * 300, 1000]]
+    polys.append(pts)
+    # a 65,536-vertex fractal star
+    big = synth.star_polygons(1, 17, (65536, 65536), "uniform", (5e-2, 5e-2), fractal=True)
+    polys.append(big.poly(0))
+    # a 1,000-vertex regular polygon (many slabs, short edges)
+    ang = np.arange(1000) * 2 * np.pi / 1000
+    polys.append(np.stack([np.rint(30000 + 9000 * np.cos(ang)),
+                           np.rint(30000 + 9000 * np.sin(ang))], 1).astype(np.int32))
+    ps = from_polys(polys)
+    K, T = 64, 1 << 24
+    P = B.make_params(K, 1, T)
+    h = u32(B.minhash_sign(ctx, upload(B, ctx, ps), P))
+    ref = orc.sign(ps.xy, ps.offsets, SEED, K, T, nthreads=4)
+    assert np.array_equal(h, ref)
