@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=None, help="polygons in the CPU sample")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default sign variant")
     return ap.parse_args()
 
 
@@ -207,6 +208,17 @@ def main():
     ctx = B.Context(local)
     stream = torch.cuda.current_stream()
 
+    autotune = None
+    if not args.no_autotune:
+        # pick the signing-kernel shape on a 2 % sample of the workload (cached per GPU/K/workload)
+        sample = db.subset(np.linspace(0, db.n - 1, max(1, min(db.n, 20000)), dtype=np.int64))
+        sp = B.poly_upload(ctx, torch.from_numpy(sample.xy).to(dev),
+                           torch.from_numpy(sample.offsets).to(dev))
+        best, ms = B.sign_autotune(ctx, sp, P, cache_key=f"{w.name}:{N}")
+        autotune = {"variant": best, "points_per_lane_x_warps": B.sign_variant_info(best),
+                    "sample_ms": [round(t, 3) for t in ms]}
+        sp.close()
+
     d_xy = torch.from_numpy(db.xy).to(dev)
     d_off = torch.from_numpy(db.offsets).to(dev)
     q_xy = torch.from_numpy(qs.xy).to(dev)
@@ -324,6 +336,7 @@ def main():
         "cpu_baseline": base,
         "e2e": e2e,
         "gpu_launches": int(launches),
+        "autotune": autotune,
         "clocks": clk,
     }
     if rank == 0:

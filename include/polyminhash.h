@@ -91,6 +91,8 @@ int pmh_version(void);
  * device status word.  Not thread-safe: use one context per host thread.
  * Errors: PMH_ERR_ARG (null out), PMH_ERR_CUDA (no such device / not sm_103). */
 int pmh_create(pmh_ctx* out, int device);
+/* Release a context.  Handles made with it (polygons, indexes, graphs) stay
+ * releasable afterwards but may no longer be used in compute calls. */
 int pmh_destroy(pmh_ctx ctx);
 
 /* A0 -- upload polygons (Sec. 3.1 preprocessing: local MBRs).
@@ -188,6 +190,51 @@ int pmh_refine_topk(pmh_ctx ctx, pmh_polys queries, pmh_polys db, const int32_t*
 /* Exact Jaccard of explicit pairs (d_qid[e], d_pid[e]) -> d_j[e] (fp64). */
 int pmh_pair_jaccard(pmh_ctx ctx, pmh_polys queries, pmh_polys db, const int32_t* d_qid,
                      const int32_t* d_pid, int64_t n_pairs, double* d_j, void* stream);
+
+/* A9 -- batching: signing-kernel variants and their autotuner.
+ * The signing kernel exists in PMH_SIGN_VARIANTS shapes (points per lane per
+ * round x warps per block).  pmh_sign_autotune times every variant on the
+ * polygons of `sample` (typically a few thousand polygons of the workload),
+ * stores the fastest in the context (later pmh_minhash_sign calls use it) and
+ * returns its index; h_ms (optional, PMH_SIGN_VARIANTS floats) receives each
+ * variant's time.  Synchronises.  pmh_sign_set_variant(ctx, -1) restores the
+ * default.  Hashes do not depend on the variant. */
+#define PMH_SIGN_VARIANTS 6
+int pmh_sign_autotune(pmh_ctx ctx, pmh_polys sample, const pmh_params* params, int* h_best,
+                      float* h_ms);
+int pmh_sign_set_variant(pmh_ctx ctx, int variant);
+int pmh_sign_variant_info(int variant, int* points_per_lane, int* warps_per_block);
+
+/* A9 -- batching: the query pipeline as one CUDA graph.
+ * pmh_qgraph_create captures, on buffers the graph owns, the chain
+ * A0 prep -> A1 sign -> A4 join -> A5 agreement -> A6 top-m (m per query) for
+ * batches of at most max_queries polygons holding at most max_vertices
+ * vertices, against `index` (which must outlive the graph).  The signing
+ * variant in force in ctx is baked in.
+ * pmh_qgraph_run copies one batch (xy int32 [n_vertices][2], offsets int64
+ * [n_queries + 1], HOST arrays if host_memory != 0, else device) into the
+ * graph's inputs and replays the graph on `stream`: it neither allocates nor
+ * synchronises.  Batches beyond the graph's sizes fail with PMH_ERR_RANGE.
+ * pmh_qgraph_outputs returns device pointers (owned by the graph, valid until
+ * pmh_qgraph_destroy, rewritten by every run): hashes uint32 [max_queries][K],
+ * row_ptr int64 [max_queries + 1], cand int32 [cand_capacity], count uint16
+ * [cand_capacity], top_ids int32 [max_queries][m] (-1 padded), top_n int32
+ * [max_queries]; rows past the batch are empty.
+ * pmh_qgraph_status synchronises `stream` and reports the last run's status
+ * bits (1, 2, 4: invalid polygons -- offsets, fewer than 3 vertices,
+ * coordinate range -- nothing computed; 8: more candidates than
+ * cand_capacity, rows not written, agreement and top-m skipped) and its
+ * candidate total. */
+typedef struct pmh_qgraph_s* pmh_qgraph;
+int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, int64_t max_queries, int64_t max_vertices,
+                      int64_t cand_capacity, int32_t m, pmh_qgraph* out);
+int pmh_qgraph_run(pmh_qgraph graph, const int32_t* xy, const int64_t* offsets, int64_t n_queries,
+                   int64_t n_vertices, int host_memory, void* stream);
+int pmh_qgraph_outputs(pmh_qgraph graph, uint32_t** d_hashes, int64_t** d_row_ptr,
+                       int32_t** d_cand, uint16_t** d_count, int32_t** d_top_ids,
+                       int32_t** d_top_n);
+int pmh_qgraph_status(pmh_qgraph graph, int* h_flags, int64_t* h_total, void* stream);
+int pmh_qgraph_destroy(pmh_qgraph graph);
 
 /* Allocation-free signing (the paper has no counterpart: this is a deployment
  * entry point).  Same hashes as pmh_minhash_sign, for callers that must not

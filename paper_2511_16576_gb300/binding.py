@@ -69,6 +69,16 @@ _SIGS = {
     "pmh_launch_count": (_i64, []),
     "pmh_minhash_sign_noalloc": (ctypes.c_int, [_P, _P, _i64, _i64, ctypes.POINTER(Params), _P,
                                                 _P]),
+    "pmh_sign_autotune": (ctypes.c_int, [_P, _P, ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int),
+                                         _P]),
+    "pmh_sign_set_variant": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pmh_sign_variant_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_int)]),
+    "pmh_qgraph_create": (ctypes.c_int, [_P, _P, _i64, _i64, _i64, _i32, ctypes.POINTER(_P)]),
+    "pmh_qgraph_run": (ctypes.c_int, [_P, _P, _P, _i64, _i64, ctypes.c_int, _P]),
+    "pmh_qgraph_outputs": (ctypes.c_int, [_P] + [ctypes.POINTER(_P)] * 6),
+    "pmh_qgraph_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), _P]),
+    "pmh_qgraph_destroy": (ctypes.c_int, [_P]),
 }
 
 
@@ -111,17 +121,26 @@ def _stream(stream) -> int | None:
 
 
 class Context:
-    """A library context on one CUDA device (owns scratch memory)."""
+    """A library context on one CUDA device (owns scratch memory).
+
+    Closing it first closes every handle (polygons, index, graph) made with it."""
 
     def __init__(self, device: int = 0):
+        import weakref
         lib = load()
         h = _P()
         _check(lib.pmh_create(ctypes.byref(h), device))
         self.handle = h
         self.device = device
+        self._children = weakref.WeakSet()
+
+    def _adopt(self, child):
+        self._children.add(child)
 
     def close(self):
         if self.handle:
+            for child in list(self._children):
+                child.close()
             load().pmh_destroy(self.handle)
             self.handle = None
 
@@ -138,6 +157,7 @@ class Polys:
     def __init__(self, ctx: Context, handle):
         self.ctx = ctx
         self.handle = handle
+        ctx._adopt(self)
         n, nv = _i64(), _i64()
         _check(load().pmh_polys_info(handle, ctypes.byref(n), ctypes.byref(nv)))
         self.n, self.n_vertices = n.value, nv.value
@@ -243,6 +263,7 @@ class Index:
         _check(load().pmh_lsh_build(ctx.handle, _ptr(hashes), hashes.shape[0],
                                     ctypes.byref(params), ctypes.byref(h), _stream(stream)))
         self.ctx, self.handle, self.params, self.n = ctx, h, params, hashes.shape[0]
+        ctx._adopt(self)
 
     def close(self):
         if self.handle:
@@ -339,3 +360,118 @@ def launch_count() -> int:
 class Signed:
     polys: Polys
     hashes: torch.Tensor
+
+
+# --------------------------------------------------------------------------- A9
+SIGN_VARIANTS = 6
+_AUTOTUNE_CACHE = os.path.join(_HERE, "_build", "autotune.json")
+
+
+def sign_variant_info(v: int):
+    u, w = ctypes.c_int(), ctypes.c_int()
+    _check(load().pmh_sign_variant_info(v, ctypes.byref(u), ctypes.byref(w)))
+    return u.value, w.value
+
+
+def sign_set_variant(ctx: Context, v: int):
+    _check(load().pmh_sign_set_variant(ctx.handle, v))
+
+
+def sign_autotune(ctx: Context, sample: Polys, params: Params, cache_key: str | None = None):
+    """Time every signing-kernel variant on `sample`, keep the fastest in the context.
+
+    With a cache_key the choice is cached in _build/autotune.json per GPU name, K and key,
+    and a cached choice is applied without timing."""
+    import json
+    gpu = torch.cuda.get_device_name(ctx.device)
+    key = f"{gpu}|K={params.K}|{cache_key}" if cache_key else None
+    cache = {}
+    if key and os.path.exists(_AUTOTUNE_CACHE):
+        try:
+            cache = json.load(open(_AUTOTUNE_CACHE))
+        except ValueError:
+            cache = {}
+        if key in cache:
+            sign_set_variant(ctx, int(cache[key]["best"]))
+            return int(cache[key]["best"]), cache[key]["ms"]
+    best = ctypes.c_int()
+    ms = (ctypes.c_float * SIGN_VARIANTS)()
+    _check(load().pmh_sign_autotune(ctx.handle, sample.handle, ctypes.byref(params),
+                                    ctypes.byref(best), ms))
+    times = [float(v) for v in ms]
+    if key:
+        cache[key] = {"best": best.value, "ms": times,
+                      "shapes": [sign_variant_info(v) for v in range(SIGN_VARIANTS)]}
+        os.makedirs(os.path.dirname(_AUTOTUNE_CACHE), exist_ok=True)
+        json.dump(cache, open(_AUTOTUNE_CACHE, "w"), indent=1)
+    return best.value, times
+
+
+class _DeviceArray:
+    """__cuda_array_interface__ view of library-owned device memory (no copy)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def _view(ptr, shape, typestr, device):
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device=device)
+
+
+class QueryGraph:
+    """A9: captured query pipeline (prep, sign, join, agreement, top-m) replayed per batch."""
+
+    def __init__(self, ctx: Context, index: Index, max_queries: int, max_vertices: int,
+                 cand_capacity: int, m: int):
+        h = _P()
+        _check(load().pmh_qgraph_create(ctx.handle, index.handle, max_queries, max_vertices,
+                                        cand_capacity, m, ctypes.byref(h)))
+        self.ctx, self.index, self.handle = ctx, index, h
+        ctx._adopt(self)
+        self.max_queries, self.m, self.K = max_queries, m, index.params.K
+        ptrs = [_P() for _ in range(6)]
+        _check(load().pmh_qgraph_outputs(h, *[ctypes.byref(p) for p in ptrs]))
+        dev = torch.device("cuda", ctx.device)
+        Q = max_queries
+        self.hashes = _view(ptrs[0].value, (Q, self.K), "<i4", dev)
+        self.row_ptr = _view(ptrs[1].value, (Q + 1,), "<i8", dev)
+        self.cand = _view(ptrs[2].value, (cand_capacity,), "<i4", dev)
+        self.count = _view(ptrs[3].value, (cand_capacity,), "<i2", dev)
+        self.top_ids = _view(ptrs[4].value, (Q, m), "<i4", dev)
+        self.top_n = _view(ptrs[5].value, (Q,), "<i4", dev)
+
+    def run(self, xy, offsets, stream=None):
+        """Replay on one batch: device tensors, or pinned/pageable CPU tensors / numpy arrays."""
+        n = len(offsets) - 1
+        if isinstance(xy, torch.Tensor) and xy.is_cuda:
+            _check(load().pmh_qgraph_run(self.handle, _ptr(xy), _ptr(offsets), n, xy.shape[0], 0,
+                                         _stream(stream)))
+        else:
+            import numpy as np
+            if isinstance(xy, torch.Tensor):
+                xp, op = xy.data_ptr(), offsets.data_ptr()
+                nv = xy.shape[0]
+            else:
+                self._keep = (np.ascontiguousarray(xy, np.int32), np.ascontiguousarray(offsets, np.int64))
+                xp, op = self._keep[0].ctypes.data, self._keep[1].ctypes.data
+                nv = self._keep[0].shape[0]
+            _check(load().pmh_qgraph_run(self.handle, xp, op, n, nv, 1, _stream(stream)))
+        return n
+
+    def status(self, stream=None):
+        f, t = ctypes.c_int(), _i64()
+        _check(load().pmh_qgraph_status(self.handle, ctypes.byref(f), ctypes.byref(t),
+                                        _stream(stream)))
+        return f.value, t.value
+
+    def close(self):
+        if self.handle:
+            load().pmh_qgraph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

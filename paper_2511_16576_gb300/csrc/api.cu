@@ -32,6 +32,7 @@ extern "C" int64_t pmh_launch_count(void) { return g_pmh_launches.load(); }
 int pmh_check_device(pmh_ctx ctx)
 {
     if (!ctx) return pmh_set_error(PMH_ERR_ARG, "null context");
+    cudaGetLastError();  // a stale error of an earlier, unrelated call must not fail this one
     PMH_CUDA_TRY(cudaSetDevice(ctx->device));
     return PMH_OK;
 }
@@ -120,10 +121,12 @@ extern "C" int pmh_destroy(pmh_ctx ctx)
 // status[1] = max vertex count.
 // ---------------------------------------------------------------------------
 __global__ void prep_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
-                            int64_t n_polys, int64_t n_vertices, int4* __restrict__ bbox,
-                            int64_t* __restrict__ area2, int* __restrict__ status)
+                            int64_t n_polys, const int64_t* __restrict__ d_n, int64_t n_vertices,
+                            int4* __restrict__ bbox, int64_t* __restrict__ area2,
+                            int* __restrict__ status)
 {
     const int lane = threadIdx.x & 31;
+    if (d_n) n_polys = min(n_polys, *d_n);
     int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int LIM = 1 << 20;
@@ -172,6 +175,17 @@ __global__ void prep_kernel(const int2* __restrict__ xy, const int64_t* __restri
     }
 }
 
+int pmh_launch_prep(int sm_count, const int2* xy, const int64_t* off, int64_t n_polys,
+                    const int64_t* d_n, int64_t n_vertices, int4* bbox, int64_t* area2,
+                    int* status, cudaStream_t s)
+{
+    if (n_polys <= 0) return PMH_OK;
+    int blocks = (int)std::min<int64_t>((n_polys + 7) / 8, (int64_t)sm_count * 16);
+    prep_kernel<<<blocks, 256, 0, s>>>(xy, off, n_polys, d_n, n_vertices, bbox, area2, status);
+    PMH_LAUNCHED("prep_kernel");
+    return PMH_OK;
+}
+
 static int upload_common(pmh_ctx ctx, const int32_t* xy, const int64_t* offsets, int64_t n_polys,
                          int64_t n_vertices, bool host, pmh_polys* out, void* stream)
 {
@@ -185,6 +199,7 @@ static int upload_common(pmh_ctx ctx, const int32_t* xy, const int64_t* offsets,
     cudaStream_t s = (cudaStream_t)stream;
     pmh_polys P = new pmh_polys_s();
     P->ctx = ctx;
+    P->device = ctx->device;
     P->n = n_polys;
     P->nv = n_vertices;
     auto fail = [&](int code) {
@@ -209,13 +224,9 @@ static int upload_common(pmh_ctx ctx, const int32_t* xy, const int64_t* offsets,
         return fail(pmh_set_error(PMH_ERR_CUDA, "upload copy failed: %s", cudaGetErrorString(e)));
     // offsets[0] and offsets[n] are checked by the kernel through b/e bounds
     if (n_polys > 0) {
-        int blocks = (int)std::min<int64_t>((n_polys + 7) / 8, (int64_t)ctx->sm_count * 16);
-        prep_kernel<<<blocks, 256, 0, s>>>(P->xy, P->offsets, n_polys, n_vertices, P->bbox,
-                                           P->area2, ctx->d_status);
-        g_pmh_launches.fetch_add(1);
-        e = cudaGetLastError();
-        if (e != cudaSuccess)
-            return fail(pmh_set_error(PMH_ERR_CUDA, "prep launch: %s", cudaGetErrorString(e)));
+        int rc = pmh_launch_prep(ctx->sm_count, P->xy, P->offsets, n_polys, nullptr, n_vertices,
+                                 P->bbox, P->area2, ctx->d_status, s);
+        if (rc != PMH_OK) return fail(rc);
     }
     int st[2] = {0, 0};
     e = cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -271,7 +282,7 @@ extern "C" int pmh_polys_prep(pmh_polys p, int32_t* d_bbox, int64_t* d_area2, vo
 extern "C" int pmh_polys_destroy(pmh_polys p)
 {
     if (!p) return PMH_OK;
-    if (p->ctx) cudaSetDevice(p->ctx->device);
+    cudaSetDevice(p->device);
     if (p->xy || p->offsets || p->bbox || p->area2) cudaDeviceSynchronize();
     void* bufs[] = {p->xy, p->offsets, p->bbox, p->area2, p->slab_info, p->slab_ptr,
                     p->slab_edges, p->order};

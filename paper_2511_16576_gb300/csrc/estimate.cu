@@ -20,12 +20,14 @@ constexpr int kMaxK = 4096;
 
 __global__ void agree_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ ph,
                              const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cand,
-                             int64_t Q, int K, int bands, int rows, uint32_t T,
-                             uint16_t* __restrict__ count, uint32_t* __restrict__ bandmask)
+                             int64_t Q, int64_t cap, int K, int bands, int rows, uint32_t T,
+                             uint16_t* __restrict__ count, uint32_t* __restrict__ bandmask,
+                             const int* __restrict__ d_flags)
 {
     __shared__ uint32_t eqbits[8][kMaxK / 32];  // per warp: equality bit per hash
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t E = row_ptr[Q];
+    if (d_flags && *d_flags) return;  // failed validation or candidate overflow
+    const int64_t E = min(row_ptr[Q], cap);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; e < E; e += nwarps) {
         // find the query of pair e (binary search over row_ptr)
@@ -124,11 +126,12 @@ __global__ void __launch_bounds__(kTopThreads)
 topm_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cand,
             const uint16_t* __restrict__ count, const float* __restrict__ score, int K, int m,
             int cap /* power of two >= m + kTopChunk */, int32_t* __restrict__ out_ids,
-            int32_t* __restrict__ out_n)
+            int32_t* __restrict__ out_n, const int* __restrict__ d_flags)
 {
     extern __shared__ uint64_t s[];
     const int64_t q = blockIdx.x;
-    const int64_t b = row_ptr[q], e = row_ptr[q + 1];
+    const bool failed = d_flags && *d_flags;
+    const int64_t b = failed ? 0 : row_ptr[q], e = failed ? 0 : row_ptr[q + 1];
     int kept = 0;
     for (int64_t base = b; base < e; base += kTopChunk) {
         int take = (int)(e - base < kTopChunk ? e - base : kTopChunk);
@@ -154,6 +157,34 @@ topm_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ can
 
 }  // namespace
 
+int pmh_launch_agree(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph, const int64_t* row_ptr,
+                     const int32_t* cand, int64_t Q, int64_t cap, const pmh_params* P,
+                     uint16_t* count, uint32_t* bandmask, const int* d_flags, cudaStream_t s)
+{
+    if (Q <= 0) return PMH_OK;
+    int blocks = ctx->sm_count * 8;
+    agree_kernel<<<blocks, 256, 0, s>>>(qh, ph, row_ptr, cand, Q, cap, (int)P->K, (int)P->bands,
+                                        (int)P->rows, P->T, count, bandmask, d_flags);
+    PMH_LAUNCHED("agree_kernel");
+    return PMH_OK;
+}
+
+int pmh_launch_topm(const int64_t* row_ptr, const int32_t* cand, const uint16_t* count,
+                    const float* score, int64_t Q, int32_t m, int32_t* out_ids, int32_t* out_n,
+                    const int* d_flags, cudaStream_t s)
+{
+    if (Q <= 0) return PMH_OK;
+    int cap = 1;
+    while (cap < m + kTopChunk) cap <<= 1;
+    size_t smem = sizeof(uint64_t) * cap;
+    PMH_CUDA_TRY(cudaFuncSetAttribute(topm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    topm_kernel<<<(unsigned)Q, kTopThreads, smem, s>>>(row_ptr, cand, count, score, 4096, m, cap,
+                                                       out_ids, out_n, d_flags);
+    PMH_LAUNCHED("topm_kernel");
+    return PMH_OK;
+}
+
 extern "C" int pmh_jaccard_estimate(pmh_ctx ctx, const uint32_t* d_qhashes,
                                     const uint32_t* d_dbhashes, const int64_t* d_row_ptr,
                                     const int32_t* d_cand, int64_t Q, const pmh_params* params,
@@ -163,14 +194,8 @@ extern "C" int pmh_jaccard_estimate(pmh_ctx ctx, const uint32_t* d_qhashes,
     PMH_TRY(pmh_check_params(params));
     if (Q < 0 || (Q > 0 && (!d_qhashes || !d_dbhashes || !d_row_ptr || !d_count)))
         return pmh_set_error(PMH_ERR_ARG, "bad arguments");
-    if (Q == 0) return PMH_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    int blocks = ctx->sm_count * 8;
-    agree_kernel<<<blocks, 256, 0, s>>>(d_qhashes, d_dbhashes, d_row_ptr, d_cand, Q, (int)params->K,
-                                        (int)params->bands, (int)params->rows, params->T, d_count,
-                                        d_bandmask);
-    PMH_LAUNCHED("agree_kernel");
-    return PMH_OK;
+    return pmh_launch_agree(ctx, d_qhashes, d_dbhashes, d_row_ptr, d_cand, Q, INT64_MAX, params,
+                            d_count, d_bandmask, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" int pmh_topm(pmh_ctx ctx, const int64_t* d_row_ptr, const int32_t* d_cand,
@@ -181,16 +206,7 @@ extern "C" int pmh_topm(pmh_ctx ctx, const int64_t* d_row_ptr, const int32_t* d_
     if (Q < 0 || m < 1 || m > 1024 || (Q > 0 && (!d_row_ptr || !d_out_ids || !d_out_n)) ||
         (!d_count && !d_score))
         return pmh_set_error(PMH_ERR_ARG, "bad arguments (m in [1,1024])");
-    if (Q == 0) return PMH_OK;
     if (Q > 0x7FFFFFFF) return pmh_set_error(PMH_ERR_ARG, "too many queries");
-    cudaStream_t s = (cudaStream_t)stream;
-    int cap = 1;
-    while (cap < m + kTopChunk) cap <<= 1;
-    size_t smem = sizeof(uint64_t) * cap;
-    PMH_CUDA_TRY(cudaFuncSetAttribute(topm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-    topm_kernel<<<(unsigned)Q, kTopThreads, smem, s>>>(d_row_ptr, d_cand, d_count, d_score, 4096, m,
-                                                       cap, d_out_ids, d_out_n);
-    PMH_LAUNCHED("topm_kernel");
-    return PMH_OK;
+    return pmh_launch_topm(d_row_ptr, d_cand, d_count, d_score, Q, m, d_out_ids, d_out_n, nullptr,
+                           (cudaStream_t)stream);
 }

@@ -1,0 +1,203 @@
+// graph.cu -- A9: the query pipeline captured once as a CUDA graph.
+//
+// For query batches of up to max_queries polygons (at most max_vertices
+// vertices in all), the steps prep (A0), sign (A1), bucket join (A4, count +
+// scan + fill), agreement (A5) and top-m (A6) are captured on fixed,
+// graph-owned buffers.  A replay copies the batch into the input buffers,
+// writes the batch size into a device word and launches the graph: no host
+// synchronisation, no allocation.  Data-dependent sizes stay on the device:
+// kernels read the batch size from the device word, the join writes its rows
+// only if the candidate total fits the capacity, and a device status word
+// records failures (bits 0-2 invalid polygons, bit 3 candidate overflow) which
+// make the later stages do nothing; pmh_qgraph_status reads it.
+#include <algorithm>
+
+#include "pmh_internal.cuh"
+
+struct pmh_qgraph_s {
+    pmh_ctx ctx = nullptr;
+    int device = 0;
+    pmh_index index = nullptr;
+    pmh_params P{};
+    int64_t maxQ = 0, maxV = 0, cap = 0;
+    int m = 0;
+    int2* xy = nullptr;
+    int64_t* off = nullptr;
+    int4* bbox = nullptr;
+    int64_t* area2 = nullptr;
+    uint32_t* hashes = nullptr;
+    int64_t* counts = nullptr;
+    int64_t* row_ptr = nullptr;
+    int32_t* cand = nullptr;
+    uint16_t* count16 = nullptr;
+    int32_t* top_ids = nullptr;
+    int32_t* top_n = nullptr;
+    int* flags = nullptr;
+    int64_t* d_n = nullptr;
+    unsigned long long* ticket = nullptr;
+    int64_t* scan_sums = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+__global__ void set_batch_kernel(int64_t* d_n, int64_t n) { *d_n = n; }
+
+}  // namespace
+
+extern "C" int pmh_qgraph_destroy(pmh_qgraph g)
+{
+    if (!g) return PMH_OK;
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    void* bufs[] = {g->xy,     g->off,     g->bbox,    g->area2, g->hashes, g->counts,
+                    g->row_ptr, g->cand,   g->count16, g->top_ids, g->top_n, g->flags,
+                    g->d_n,    g->ticket, g->scan_sums};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete g;
+    return PMH_OK;
+}
+
+extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, int64_t max_queries,
+                                 int64_t max_vertices, int64_t cand_capacity, int32_t m,
+                                 pmh_qgraph* out)
+{
+    if (!out) return pmh_set_error(PMH_ERR_ARG, "null out");
+    *out = nullptr;
+    PMH_TRY(pmh_check_device(ctx));
+    if (!index || max_queries < 1 || max_queries >= (1ll << 31) || max_vertices < 3 ||
+        cand_capacity < 1 || m < 1 || m > 1024)
+        return pmh_set_error(PMH_ERR_ARG, "bad graph sizes");
+    pmh_qgraph g = new pmh_qgraph_s();
+    g->ctx = ctx;
+    g->device = ctx->device;
+    g->index = index;
+    g->P = index->params;
+    g->maxQ = max_queries;
+    g->maxV = max_vertices;
+    g->cap = cand_capacity;
+    g->m = m;
+    const int64_t Q = max_queries, K = g->P.K;
+    bool ok = cudaMalloc(&g->xy, sizeof(int2) * max_vertices) == cudaSuccess &&
+              cudaMalloc(&g->off, sizeof(int64_t) * (Q + 1)) == cudaSuccess &&
+              cudaMalloc(&g->bbox, sizeof(int4) * Q) == cudaSuccess &&
+              cudaMalloc(&g->area2, sizeof(int64_t) * Q) == cudaSuccess &&
+              cudaMalloc(&g->hashes, sizeof(uint32_t) * Q * K) == cudaSuccess &&
+              cudaMalloc(&g->counts, sizeof(int64_t) * Q) == cudaSuccess &&
+              cudaMalloc(&g->row_ptr, sizeof(int64_t) * (Q + 1)) == cudaSuccess &&
+              cudaMalloc(&g->cand, sizeof(int32_t) * cand_capacity) == cudaSuccess &&
+              cudaMalloc(&g->count16, sizeof(uint16_t) * cand_capacity) == cudaSuccess &&
+              cudaMalloc(&g->top_ids, sizeof(int32_t) * Q * m) == cudaSuccess &&
+              cudaMalloc(&g->top_n, sizeof(int32_t) * Q) == cudaSuccess &&
+              cudaMalloc(&g->flags, sizeof(int) * 4) == cudaSuccess &&
+              cudaMalloc(&g->d_n, sizeof(int64_t)) == cudaSuccess &&
+              cudaMalloc(&g->ticket, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&g->scan_sums, sizeof(int64_t) * pmh_scan_sums_size(Q)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        pmh_qgraph_destroy(g);
+        return pmh_set_error(PMH_ERR_NOMEM, "graph buffer allocation failed");
+    }
+    cudaMemset(g->d_n, 0, sizeof(int64_t));
+    cudaMemset(g->off, 0, sizeof(int64_t) * (Q + 1));
+    cudaStream_t cs;
+    PMH_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    int rc = PMH_OK;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+    if (rc == PMH_OK && cudaMemsetAsync(g->flags, 0, sizeof(int) * 4, cs) != cudaSuccess)
+        rc = pmh_set_error(PMH_ERR_CUDA, "capture memset failed");
+    if (rc == PMH_OK)
+        rc = pmh_launch_prep(ctx->sm_count, g->xy, g->off, Q, g->d_n, max_vertices, g->bbox, g->area2,
+                             g->flags, cs);
+    if (rc == PMH_OK)
+        rc = pmh_launch_sign(ctx, g->xy, g->off, g->bbox, nullptr, nullptr, nullptr, nullptr, &g->P,
+                             Q, g->d_n, g->flags, g->ticket, g->hashes, cs);
+    if (rc == PMH_OK)
+        rc = pmh_launch_query(index, g->hashes, Q, g->d_n, g->counts, nullptr, nullptr, 0, g->flags,
+                              false, cs);
+    if (rc == PMH_OK) rc = pmh_exclusive_scan_i64(ctx, g->counts, g->row_ptr, Q, cs, g->scan_sums);
+    if (rc == PMH_OK)
+        rc = pmh_launch_query(index, g->hashes, Q, g->d_n, nullptr, g->row_ptr, g->cand, g->cap,
+                              g->flags, true, cs);
+    if (rc == PMH_OK)
+        rc = pmh_launch_agree(ctx, g->hashes, index->hashes, g->row_ptr, g->cand, Q, g->cap, &g->P,
+                              g->count16, nullptr, g->flags, cs);
+    if (rc == PMH_OK)
+        rc = pmh_launch_topm(g->row_ptr, g->cand, g->count16, nullptr, Q, m, g->top_ids, g->top_n,
+                             g->flags, cs);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cs, &graph);
+    if (rc == PMH_OK && e != cudaSuccess)
+        rc = pmh_set_error(PMH_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+    g->graph = graph;
+    if (rc == PMH_OK) {
+        e = cudaGraphInstantiate(&g->exec, graph, 0);
+        if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+    }
+    cudaStreamDestroy(cs);
+    if (rc != PMH_OK) {
+        cudaGetLastError();
+        pmh_qgraph_destroy(g);
+        return rc;
+    }
+    PMH_CUDA_TRY(cudaDeviceSynchronize());
+    *out = g;
+    return PMH_OK;
+}
+
+extern "C" int pmh_qgraph_run(pmh_qgraph g, const int32_t* xy, const int64_t* offsets,
+                              int64_t n_queries, int64_t n_vertices, int host_memory, void* stream)
+{
+    if (!g) return pmh_set_error(PMH_ERR_ARG, "null graph");
+    PMH_TRY(pmh_check_device(g->ctx));
+    if (n_queries < 0 || n_queries > g->maxQ || n_vertices < 0 || n_vertices > g->maxV ||
+        (n_queries > 0 && (!xy || !offsets)))
+        return pmh_set_error(PMH_ERR_RANGE, "batch of %lld queries / %lld vertices exceeds the "
+                             "graph's %lld / %lld", (long long)n_queries, (long long)n_vertices,
+                             (long long)g->maxQ, (long long)g->maxV);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemcpyKind kind = host_memory ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (n_vertices > 0) PMH_CUDA_TRY(cudaMemcpyAsync(g->xy, xy, sizeof(int2) * n_vertices, kind, s));
+    if (n_queries > 0)
+        PMH_CUDA_TRY(cudaMemcpyAsync(g->off, offsets, sizeof(int64_t) * (n_queries + 1), kind, s));
+    set_batch_kernel<<<1, 1, 0, s>>>(g->d_n, n_queries);
+    PMH_LAUNCHED("set_batch_kernel");
+    PMH_CUDA_TRY(cudaGraphLaunch(g->exec, s));
+    g_pmh_launches.fetch_add(9);  // kernels in the graph: prep, sign, 2 x join, 3 x scan, agree, top-m
+    return PMH_OK;
+}
+
+extern "C" int pmh_qgraph_outputs(pmh_qgraph g, uint32_t** d_hashes, int64_t** d_row_ptr,
+                                  int32_t** d_cand, uint16_t** d_count, int32_t** d_top_ids,
+                                  int32_t** d_top_n)
+{
+    if (!g) return pmh_set_error(PMH_ERR_ARG, "null graph");
+    if (d_hashes) *d_hashes = g->hashes;
+    if (d_row_ptr) *d_row_ptr = g->row_ptr;
+    if (d_cand) *d_cand = g->cand;
+    if (d_count) *d_count = g->count16;
+    if (d_top_ids) *d_top_ids = g->top_ids;
+    if (d_top_n) *d_top_n = g->top_n;
+    return PMH_OK;
+}
+
+extern "C" int pmh_qgraph_status(pmh_qgraph g, int* h_flags, int64_t* h_total, void* stream)
+{
+    if (!g) return pmh_set_error(PMH_ERR_ARG, "null graph");
+    PMH_TRY(pmh_check_device(g->ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    int flags = 0;
+    int64_t total = 0;
+    PMH_CUDA_TRY(cudaMemcpyAsync(&flags, g->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PMH_CUDA_TRY(cudaMemcpyAsync(&total, g->row_ptr + g->maxQ, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+    PMH_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h_flags) *h_flags = flags;
+    if (h_total) *h_total = total;
+    return PMH_OK;
+}

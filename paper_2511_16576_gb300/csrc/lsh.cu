@@ -102,17 +102,34 @@ __device__ __forceinline__ void advance(BandCursor& c, const uint32_t* __restric
     }
 }
 
+// One warp per query.  The count pass writes the row length (0 for rows past the
+// device-side batch size d_n or after a failed validation, flag bits 0-2); the
+// fill pass writes the row, unless the total exceeds the capacity (then it
+// raises flag bit 3).
 template <bool kWrite>
 __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands,
                              int rows, uint32_t T, uint64_t lsh_seed, int band_bits,
                              const uint32_t* __restrict__ comp, const int32_t* __restrict__ ids,
                              const uint64_t* __restrict__ keys, const uint32_t* __restrict__ dbh,
                              int64_t m, int64_t* __restrict__ counts,
-                             const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand)
+                             const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand,
+                             int64_t cap, const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
 {
     const int lane = threadIdx.x & 31;
     int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (q >= Q) return;
+    const bool skip = (d_n && q >= *d_n) || (d_flags && (*d_flags & 7));
+    if (!kWrite && skip) {
+        if (lane == 0) counts[q] = 0;
+        return;
+    }
+    if (kWrite) {
+        if (skip) return;
+        if (row_ptr[Q] > cap) {
+            if (lane == 0 && d_flags) atomicOr(d_flags, 8);
+            return;
+        }
+    }
     const uint32_t* qh = qhashes + q * K;
     BandCursor cur[kMaxBandsPerLane];
 #pragma unroll
@@ -182,6 +199,7 @@ extern "C" int pmh_lsh_build(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
     cudaStream_t s = (cudaStream_t)stream;
     pmh_index X = new pmh_index_s();
     X->ctx = ctx;
+    X->device = ctx->device;
     X->n = n;
     X->params = *params;
     int bb = 1;
@@ -224,13 +242,38 @@ extern "C" int pmh_lsh_build(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
 extern "C" int pmh_index_destroy(pmh_index X)
 {
     if (!X) return PMH_OK;
-    if (X->ctx) cudaSetDevice(X->ctx->device);
+    cudaSetDevice(X->device);
     cudaDeviceSynchronize();
     if (X->hashes) cudaFree(X->hashes);
     if (X->keys) cudaFree(X->keys);
     if (X->sorted_comp) cudaFree(X->sorted_comp);
     if (X->sorted_id) cudaFree(X->sorted_id);
     delete X;
+    return PMH_OK;
+}
+
+int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
+                     int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
+                     int* d_flags, bool write, cudaStream_t s)
+{
+    if (Q <= 0) return PMH_OK;
+    const pmh_params& P = X->params;
+    const int64_t m = X->n * P.bands;
+    const int wpb = 8;
+    unsigned blocks = (unsigned)((Q + wpb - 1) / wpb);
+    if (write) {
+        query_kernel<true><<<blocks, wpb * 32, 0, s>>>(
+            qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T, P.lsh_seed, X->band_bits,
+            X->sorted_comp, X->sorted_id, X->keys, X->hashes, m, nullptr, row_ptr, cand, cap, d_n,
+            d_flags);
+        PMH_LAUNCHED("query_kernel<fill>");
+    } else {
+        query_kernel<false><<<blocks, wpb * 32, 0, s>>>(
+            qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T, P.lsh_seed, X->band_bits,
+            X->sorted_comp, X->sorted_id, X->keys, X->hashes, m, counts, nullptr, nullptr, 0, d_n,
+            d_flags);
+        PMH_LAUNCHED("query_kernel<count>");
+    }
     return PMH_OK;
 }
 
@@ -247,17 +290,9 @@ extern "C" int pmh_lsh_query(pmh_ctx ctx, pmh_index X, const uint32_t* d_qhashes
         PMH_CUDA_TRY(cudaMemsetAsync(d_row_ptr, 0, sizeof(int64_t), s));
         return PMH_OK;
     }
-    const pmh_params& P = X->params;
     int64_t* counts = nullptr;
     PMH_TRY(pmh_scratch(ctx, SCR_QUERY, sizeof(int64_t) * (size_t)Q, (void**)&counts));
-    const int64_t m = X->n * P.bands;
-    const int wpb = 8;
-    unsigned blocks = (unsigned)((Q + wpb - 1) / wpb);
-    query_kernel<false><<<blocks, wpb * 32, 0, s>>>(d_qhashes, Q, (int)P.K, (int)P.bands,
-                                                    (int)P.rows, P.T, P.lsh_seed, X->band_bits,
-                                                    X->sorted_comp, X->sorted_id, X->keys,
-                                                    X->hashes, m, counts, nullptr, nullptr);
-    PMH_LAUNCHED("query_kernel<count>");
+    PMH_TRY(pmh_launch_query(X, d_qhashes, Q, nullptr, counts, nullptr, nullptr, 0, nullptr, false, s));
     PMH_TRY(pmh_exclusive_scan_i64(ctx, counts, d_row_ptr, Q, s));
     PMH_CUDA_TRY(cudaMemcpyAsync(ctx->h_pinned, d_row_ptr + Q, sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, s));
@@ -269,10 +304,6 @@ extern "C" int pmh_lsh_query(pmh_ctx ctx, pmh_index X, const uint32_t* d_qhashes
                              (long long)cand_capacity);
     if (total == 0) return PMH_OK;
     if (!d_cand) return pmh_set_error(PMH_ERR_ARG, "null candidate buffer");
-    query_kernel<true><<<blocks, wpb * 32, 0, s>>>(d_qhashes, Q, (int)P.K, (int)P.bands,
-                                                   (int)P.rows, P.T, P.lsh_seed, X->band_bits,
-                                                   X->sorted_comp, X->sorted_id, X->keys,
-                                                   X->hashes, m, nullptr, d_row_ptr, d_cand);
-    PMH_LAUNCHED("query_kernel<fill>");
-    return PMH_OK;
+    return pmh_launch_query(X, d_qhashes, Q, nullptr, nullptr, d_row_ptr, d_cand, cand_capacity,
+                            nullptr, true, s);
 }

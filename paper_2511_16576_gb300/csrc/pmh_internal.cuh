@@ -61,6 +61,7 @@ struct pmh_ctx_s {
     void* scratch[SCR_COUNT] = {};
     size_t scratch_bytes[SCR_COUNT] = {};
     int64_t* h_pinned = nullptr;          // small pinned host buffer [64]
+    int sign_variant = -1;                // autotuned signing kernel (-1 = default)
 };
 
 // per-polygon y-slab edge index (slabs.cu); S == 0 for polygons without one
@@ -73,8 +74,10 @@ struct SlabInfo {
 };
 constexpr int kSlabMinVerts = 256;  // polygons above this size get a slab index
 
+// Handles record their device so that they can be released after their context.
 struct pmh_polys_s {
     pmh_ctx ctx = nullptr;
+    int device = 0;
     int64_t n = 0, nv = 0;
     int2* xy = nullptr;
     int64_t* offsets = nullptr;
@@ -92,6 +95,7 @@ int pmh_build_cost_order(pmh_polys P, cudaStream_t s);
 
 struct pmh_index_s {
     pmh_ctx ctx = nullptr;
+    int device = 0;
     int64_t n = 0;
     pmh_params params{};
     int band_bits = 0;
@@ -133,8 +137,41 @@ __device__ __forceinline__ uint32_t pmh_mix64_lo(uint64_t z)
 // ---------------------------------------------------------------------------
 // exclusive prefix sum of n int64 values in place-able form: out[i] = sum in[0..i-1],
 // out[n] = total (out has n + 1 entries).  in may alias out.
+// sums_buffer (optional, pmh_scan_sums_size(n) entries) replaces the context scratch,
+// so that a captured graph owns every buffer it touches.
 int pmh_exclusive_scan_i64(pmh_ctx ctx, const int64_t* in, int64_t* out, int64_t n,
-                           cudaStream_t s);
+                           cudaStream_t s, int64_t* sums_buffer = nullptr);
+int64_t pmh_scan_sums_size(int64_t n);
+
+// ---------------------------------------------------------------------------
+// Internal launchers shared by the public calls and the captured query graph.
+// d_n (optional): device-side count that caps the launch-time size n, so a graph
+// captured for a maximum batch serves any smaller batch.  d_flags (optional):
+// device status word; bits 0-2 = invalid polygons (set by prep: 1 offsets,
+// 2 fewer than 3 vertices, 4 coordinate range), bit 3 = candidate overflow (set
+// by the join).  Kernels after a failed stage do nothing.
+// ---------------------------------------------------------------------------
+int pmh_launch_prep(int sm_count, const int2* xy, const int64_t* off, int64_t n_polys,
+                    const int64_t* d_n, int64_t n_vertices, int4* bbox, int64_t* area2,
+                    int* status, cudaStream_t s);
+int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4* bbox,
+                    const SlabInfo* slabs, const int32_t* slab_ptr, const int32_t* slab_edges,
+                    const int32_t* order, const pmh_params* P, int64_t n_polys,
+                    const int64_t* d_n, const int* d_flags, unsigned long long* ticket,
+                    uint32_t* out, cudaStream_t s);
+int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
+                     int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
+                     int* d_flags, bool write, cudaStream_t s);
+int pmh_launch_agree(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph, const int64_t* row_ptr,
+                     const int32_t* cand, int64_t Q, int64_t cap, const pmh_params* P,
+                     uint16_t* count, uint32_t* bandmask, const int* d_flags, cudaStream_t s);
+int pmh_launch_topm(const int64_t* row_ptr, const int32_t* cand, const uint16_t* count,
+                    const float* score, int64_t Q, int32_t m, int32_t* out_ids, int32_t* out_n,
+                    const int* d_flags, cudaStream_t s);
+
+// signing kernel variants (points per lane per round x warps per block)
+int pmh_sign_variant_count();
+void pmh_sign_variant_shape(int v, int* points_per_lane, int* warps);
 
 // stable LSD radix sort of (uint32 key, int32 value) pairs; result in keys/vals.
 int pmh_radix_sort_u32(pmh_ctx ctx, uint32_t* keys, int32_t* vals, int64_t n, int key_bits,

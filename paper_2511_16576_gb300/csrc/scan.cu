@@ -185,15 +185,19 @@ radix_scatter_kernel(const uint32_t* __restrict__ kin, const int32_t* __restrict
 
 }  // namespace
 
-int pmh_exclusive_scan_i64(pmh_ctx ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t s)
+int64_t pmh_scan_sums_size(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+int pmh_exclusive_scan_i64(pmh_ctx ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t s,
+                           int64_t* sums_buffer)
 {
     if (n <= 0) {
         PMH_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
         return PMH_OK;
     }
     int64_t nb = (n + kScanTile - 1) / kScanTile;
-    int64_t* sums = nullptr;
-    PMH_TRY(pmh_scratch(ctx, SCR_SCAN, sizeof(int64_t) * (size_t)(nb + 1), (void**)&sums));
+    int64_t* sums = sums_buffer;
+    if (!sums)
+        PMH_TRY(pmh_scratch(ctx, SCR_SCAN, sizeof(int64_t) * (size_t)(nb + 1), (void**)&sums));
     scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
     PMH_LAUNCHED("scan_reduce_kernel");
     scan_sums_kernel<<<1, 1024, 0, s>>>(sums, nb);

@@ -96,29 +96,30 @@ struct SlabEdges {
     }
 };
 
-// One hash of one polygon; every lane returns the same value.
-template <class Inside>
+// One hash of one polygon; every lane returns the same value.  U points per
+// lane per round: one round covers 32 * U consecutive stream indices.
+template <int U, class Inside>
 __device__ __forceinline__ uint32_t sign_one_t(const Inside& inside, int x0, int y0, uint32_t w,
                                                uint32_t h, uint64_t sk, uint32_t T, int lane)
 {
     if (w == 0 || h == 0) return T;
     uint64_t z = sk + (uint64_t)(lane + 1) * PMH_GAMMA;
     const uint64_t step = 32ull * PMH_GAMMA;
-    for (uint32_t i0 = 0; i0 < T; i0 += 32u * kU) {
-        uint32_t pts[kU];
+    for (uint32_t i0 = 0; i0 < T; i0 += 32u * U) {
+        uint32_t pts[U];
         unsigned m = 0;
 #pragma unroll
-        for (int j = 0; j < kU; ++j) {
+        for (int j = 0; j < U; ++j) {
             uint32_t r = pmh_mix64_lo(z + (uint64_t)j * step);
             pts[j] = r;
             uint32_t dx = (r & 0xFFFFu) - (uint32_t)x0;
             uint32_t dy = (r >> 16) - (uint32_t)y0;
             m |= (unsigned)((dx < w) & (dy < h)) << j;
         }
-        z += (uint64_t)kU * step;
+        z += (uint64_t)U * step;
         if (!__any_sync(0xffffffffu, m)) continue;
 #pragma unroll
-        for (int j = 0; j < kU; ++j) {
+        for (int j = 0; j < U; ++j) {
             unsigned b = __ballot_sync(0xffffffffu, (m >> j) & 1u);
             while (b) {
                 int l = __ffs(b) - 1;
@@ -137,11 +138,11 @@ __device__ __forceinline__ uint32_t sign_one(const int2* __restrict__ v, int n, 
                                              uint32_t w, uint32_t h, uint64_t sk, uint32_t T,
                                              int lane)
 {
-    return sign_one_t(AllEdges{v, n}, x0, y0, w, h, sk, T, lane);
+    return sign_one_t<kU>(AllEdges{v, n}, x0, y0, w, h, sk, T, lane);
 }
 
 // the hashes k0 .. k0+31 of one polygon; lane j returns hash k0 + j
-template <class Inside>
+template <int U, class Inside>
 __device__ __forceinline__ uint32_t sign_chunk(const Inside& inside, int4 bb, uint64_t seed, int k0,
                                                int kend, uint32_t T, int lane)
 {
@@ -149,20 +150,25 @@ __device__ __forceinline__ uint32_t sign_chunk(const Inside& inside, int4 bb, ui
     uint32_t mine = T;
     for (int k = k0; k < kend; ++k) {
         uint64_t sk = pmh_mix64(seed + (uint64_t)(k + 1) * PMH_GAMMA);
-        uint32_t hk = sign_one_t(inside, bb.x, bb.y, w, h, sk, T, lane);
+        uint32_t hk = sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane);
         if (lane == k - k0) mine = hk;
     }
     return mine;
 }
 
-__global__ void __launch_bounds__(kWarps * 32)
+template <int U, int W>
+__global__ void __launch_bounds__(W * 32)
 sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
             const int4* __restrict__ bbox, const SlabInfo* __restrict__ slabs,
             const int32_t* __restrict__ slab_ptr, const int32_t* __restrict__ slab_edges,
             const int32_t* __restrict__ order, uint64_t seed, int K, uint32_t T, int chunks,
-            int64_t n_items, unsigned long long* __restrict__ ticket, uint32_t* __restrict__ out)
+            int64_t n_polys, const int64_t* __restrict__ d_n, const int* __restrict__ d_flags,
+            unsigned long long* __restrict__ ticket, uint32_t* __restrict__ out)
 {
-    __shared__ __align__(16) int2 sv[kWarps][kSmemVerts];
+    __shared__ __align__(16) int2 sv[W][kSmemVerts];
+    if (d_flags && *d_flags) return;  // the batch failed validation
+    if (d_n) n_polys = min(n_polys, *d_n);
+    const int64_t n_items = n_polys * chunks;
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
     for (;;) {
@@ -182,21 +188,65 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
             // stage the vertices in this warp's shared-memory slice (coalesced 8-byte loads)
             for (int i = lane; i < n; i += 32) sv[wid][i] = xy[b + i];
             __syncwarp();
-            mine = sign_chunk(AllEdges{sv[wid], n}, bb, seed, k0, kend, T, lane);
+            mine = sign_chunk<U>(AllEdges{sv[wid], n}, bb, seed, k0, kend, T, lane);
         } else if (slabs && slabs[p].S > 0) {
             const SlabInfo si = slabs[p];
-            mine = sign_chunk(SlabEdges{xy + b, n, slab_ptr + si.slab_base, slab_edges + si.edge_base,
-                                        si.slab_h, si.ymin},
-                              bb, seed, k0, kend, T, lane);
+            mine = sign_chunk<U>(SlabEdges{xy + b, n, slab_ptr + si.slab_base,
+                                           slab_edges + si.edge_base, si.slab_h, si.ymin},
+                                 bb, seed, k0, kend, T, lane);
         } else {
-            mine = sign_chunk(AllEdges{xy + b, n}, bb, seed, k0, kend, T, lane);
+            mine = sign_chunk<U>(AllEdges{xy + b, n}, bb, seed, k0, kend, T, lane);
         }
         if (k0 + lane < kend) out[p * (int64_t)K + k0 + lane] = mine;
         __syncwarp();
     }
 }
 
+using SignFn = void (*)(const int2*, const int64_t*, const int4*, const SlabInfo*, const int32_t*,
+                        const int32_t*, const int32_t*, uint64_t, int, uint32_t, int, int64_t,
+                        const int64_t*, const int*, unsigned long long*, uint32_t*);
+struct SignVariant {
+    int U, W;
+    SignFn fn;
+};
+// index 0 is the default; the autotuner may pick any of them
+const SignVariant kSignVariants[] = {
+    {4, 8, sign_kernel<4, 8>},  {2, 8, sign_kernel<2, 8>},   {8, 8, sign_kernel<8, 8>},
+    {4, 4, sign_kernel<4, 4>},  {4, 16, sign_kernel<4, 16>}, {2, 16, sign_kernel<2, 16>},
+};
+constexpr int kNumSignVariants = sizeof(kSignVariants) / sizeof(kSignVariants[0]);
+
 }  // namespace
+
+int pmh_sign_variant_count() { return kNumSignVariants; }
+
+void pmh_sign_variant_shape(int v, int* points_per_lane, int* warps)
+{
+    *points_per_lane = kSignVariants[v].U;
+    *warps = kSignVariants[v].W;
+}
+
+int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4* bbox,
+                    const SlabInfo* slabs, const int32_t* slab_ptr, const int32_t* slab_edges,
+                    const int32_t* order, const pmh_params* P, int64_t n_polys,
+                    const int64_t* d_n, const int* d_flags, unsigned long long* ticket,
+                    uint32_t* out, cudaStream_t s)
+{
+    if (n_polys <= 0) return PMH_OK;
+    const SignVariant& v = kSignVariants[ctx->sign_variant >= 0 ? ctx->sign_variant : 0];
+    const int chunks = (int)((P->K + 31) / 32);
+    const int64_t n_items = n_polys * chunks;
+    int per_sm = 0;
+    PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, v.W * 32, 0));
+    int64_t blocks = (int64_t)ctx->sm_count * std::max(per_sm, 1);
+    blocks = std::min<int64_t>(blocks, (n_items + v.W - 1) / v.W);
+    PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
+    v.fn<<<(int)blocks, v.W * 32, 0, s>>>(xy, off, bbox, slabs, slab_ptr, slab_edges, order,
+                                          P->seed, (int)P->K, P->T, chunks, n_polys, d_n, d_flags,
+                                          ticket, out);
+    PMH_LAUNCHED("sign_kernel");
+    return PMH_OK;
+}
 
 extern "C" int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* params,
                                 uint32_t* d_hashes, void* stream)
@@ -206,21 +256,74 @@ extern "C" int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* 
     if (!polys || (!d_hashes && polys->n > 0))
         return pmh_set_error(PMH_ERR_ARG, "null polygons or output");
     if (polys->n == 0) return PMH_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int chunks = (int)((params->K + 31) / 32);
-    const int64_t n_items = polys->n * chunks;
-    unsigned long long* ticket = ctx->d_tickets + 0;
-    PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
-    int per_sm = 0;
-    PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sign_kernel, kWarps * 32, 0));
-    int64_t blocks = (int64_t)ctx->sm_count * std::max(per_sm, 1);
-    blocks = std::min<int64_t>(blocks, (n_items + kWarps - 1) / kWarps);
-    sign_kernel<<<(int)blocks, kWarps * 32, 0, s>>>(
-        polys->xy, polys->offsets, polys->bbox, polys->slab_info, polys->slab_ptr,
-        polys->slab_edges, polys->order, params->seed, (int)params->K, params->T, chunks, n_items,
-        ticket, d_hashes);
-    PMH_LAUNCHED("sign_kernel");
+    return pmh_launch_sign(ctx, polys->xy, polys->offsets, polys->bbox, polys->slab_info,
+                           polys->slab_ptr, polys->slab_edges, polys->order, params, polys->n,
+                           nullptr, nullptr, ctx->d_tickets + 0, d_hashes, (cudaStream_t)stream);
+}
+
+extern "C" int pmh_sign_variant_info(int variant, int* points_per_lane, int* warps_per_block)
+{
+    if (variant < 0 || variant >= kNumSignVariants)
+        return pmh_set_error(PMH_ERR_ARG, "variant %d not in [0,%d)", variant, kNumSignVariants);
+    if (points_per_lane) *points_per_lane = kSignVariants[variant].U;
+    if (warps_per_block) *warps_per_block = kSignVariants[variant].W;
     return PMH_OK;
+}
+
+extern "C" int pmh_sign_set_variant(pmh_ctx ctx, int variant)
+{
+    if (!ctx) return pmh_set_error(PMH_ERR_ARG, "null context");
+    if (variant < -1 || variant >= kNumSignVariants)
+        return pmh_set_error(PMH_ERR_ARG, "variant %d not in [-1,%d)", variant, kNumSignVariants);
+    ctx->sign_variant = variant;
+    return PMH_OK;
+}
+
+extern "C" int pmh_sign_autotune(pmh_ctx ctx, pmh_polys sample, const pmh_params* params,
+                                 int* h_best, float* h_ms)
+{
+    PMH_TRY(pmh_check_device(ctx));
+    PMH_TRY(pmh_check_params(params));
+    if (!sample || sample->n <= 0 || !h_best)
+        return pmh_set_error(PMH_ERR_ARG, "empty sample or null output");
+    uint32_t* out = nullptr;
+    if (cudaMalloc(&out, sizeof(uint32_t) * (size_t)sample->n * params->K) != cudaSuccess) {
+        cudaGetLastError();
+        return pmh_set_error(PMH_ERR_NOMEM, "autotune output allocation failed");
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved = ctx->sign_variant;
+    int best = 0, rc = PMH_OK;
+    float best_ms = 1e30f;
+    for (int v = 0; v < kNumSignVariants && rc == PMH_OK; ++v) {
+        ctx->sign_variant = v;
+        float ms_v = 1e30f;
+        for (int r = 0; r < 3 && rc == PMH_OK; ++r) {  // first run is a warm-up
+            cudaEventRecord(e0, 0);
+            rc = pmh_launch_sign(ctx, sample->xy, sample->offsets, sample->bbox, sample->slab_info,
+                                 sample->slab_ptr, sample->slab_edges, sample->order, params,
+                                 sample->n, nullptr, nullptr, ctx->d_tickets + 1, out, 0);
+            cudaEventRecord(e1, 0);
+            if (cudaEventSynchronize(e1) != cudaSuccess)
+                rc = pmh_set_error(PMH_ERR_CUDA, "autotune run failed");
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) ms_v = std::min(ms_v, ms);
+        }
+        if (h_ms) h_ms[v] = ms_v;
+        if (ms_v < best_ms) {
+            best_ms = ms_v;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    ctx->sign_variant = rc == PMH_OK ? best : saved;
+    *h_best = best;
+    return rc;
 }
 
 // ---------------------------------------------------------------------------

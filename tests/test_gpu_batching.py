@@ -1,0 +1,127 @@
+"""GPU parity of the batching pieces (A9): signing-kernel variants and their autotuner,
+and the CUDA-graph query pipeline, against the plain calls and the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2511_16576_gb300 import synth
+from test_gpu_parity import DEV, from_polys, u32, upload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2511_16576_gb300 import binding, build
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def test_every_sign_variant_is_bit_exact(B, ctx, orc):
+    db = synth.star_polygons(400, 21, (3, 600), "loguniform", (1e-3, 3e-2))
+    P = B.make_params(96, 12, 1 << 24)
+    ref = orc.sign(db.xy, db.offsets, P.seed, 96, P.T, nthreads=8)
+    polys = upload(B, ctx, db)
+    for v in range(B.SIGN_VARIANTS):
+        B.sign_set_variant(ctx, v)
+        assert np.array_equal(u32(B.minhash_sign(ctx, polys, P)), ref), B.sign_variant_info(v)
+    B.sign_set_variant(ctx, -1)
+
+
+def test_autotune_picks_a_variant(B, ctx, tmp_path, monkeypatch):
+    monkeypatch.setattr(B, "_AUTOTUNE_CACHE", str(tmp_path / "autotune.json"))
+    w = synth.WORKLOADS["scale"]
+    db = synth.make_database(w, 4000)
+    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed)
+    polys = upload(B, ctx, db)
+    best, ms = B.sign_autotune(ctx, polys, P, cache_key="test")
+    assert 0 <= best < B.SIGN_VARIANTS and len(ms) == B.SIGN_VARIANTS
+    assert ms[best] == min(ms) and all(t > 0 for t in ms)
+    # a cached choice is applied without timing
+    best2, ms2 = B.sign_autotune(ctx, polys, P, cache_key="test")
+    assert best2 == best and ms2 == ms
+    B.sign_set_variant(ctx, -1)
+
+
+@pytest.fixture(scope="module")
+def small_index(B, ctx):
+    w = synth.WORKLOADS["small"]
+    db = synth.make_database(w)
+    qs = synth.make_queries(w, db, 300)
+    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed)
+    h = B.minhash_sign(ctx, upload(B, ctx, db), P)
+    index = B.lsh_build(ctx, h, P)
+    return w, db, qs, P, h, index
+
+
+def plain_outputs(B, ctx, qs, P, h, index, m):
+    qh = B.minhash_sign(ctx, upload(B, ctx, qs), P)
+    row_ptr, cand = B.lsh_query(ctx, index, qh)
+    count, _ = B.jaccard_estimate(ctx, qh, h, row_ptr, cand, P, bandmask=False)
+    ids, nn = B.topm(ctx, row_ptr, cand, count, m)
+    return qh, row_ptr, cand, count, ids, nn
+
+
+def test_query_graph_matches_plain_calls(B, ctx, orc, small_index):
+    w, db, qs, P, h, index = small_index
+    m = 8
+    g = B.QueryGraph(ctx, index, max_queries=128, max_vertices=20000, cand_capacity=200000, m=m)
+    try:
+        for lo, n, host in ((0, 1, False), (1, 7, False), (8, 100, True), (108, 128, False),
+                            (0, 0, False)):
+            batch = qs.subset(np.arange(lo, lo + n))
+            if host:
+                g.run(batch.xy, batch.offsets)
+            else:
+                g.run(torch.from_numpy(batch.xy).to(DEV), torch.from_numpy(batch.offsets).to(DEV))
+            flags, total = g.status()
+            assert flags == 0
+            if n == 0:
+                assert total == 0
+                continue
+            qh, row_ptr, cand, count, ids, nn = plain_outputs(B, ctx, batch, P, h, index, m)
+            assert torch.equal(g.hashes[:n], qh)
+            assert torch.equal(g.row_ptr[:n + 1], row_ptr) and total == cand.numel()
+            assert (g.row_ptr[n:] == total).all()
+            assert torch.equal(g.cand[:total], cand)
+            assert torch.equal(g.count[:total], count)
+            assert torch.equal(g.top_ids[:n], ids) and torch.equal(g.top_n[:n], nn)
+            # and against the oracle on this batch
+            qh_ref = orc.sign(batch.xy, batch.offsets, w.seed, w.K, w.T)
+            assert np.array_equal(u32(g.hashes[:n]), qh_ref)
+    finally:
+        g.close()
+
+
+def test_query_graph_overflow_invalid_and_recovery(B, ctx, small_index):
+    w, db, qs, P, h, index = small_index
+    g = B.QueryGraph(ctx, index, max_queries=64, max_vertices=10000, cand_capacity=3, m=4)
+    try:
+        batch = qs.subset(np.arange(0, 64))
+        g.run(torch.from_numpy(batch.xy).to(DEV), torch.from_numpy(batch.offsets).to(DEV))
+        flags, total = g.status()
+        assert flags == 8 and total > 3
+        assert (g.top_n[:64] == 0).all() and (g.top_ids[:64] == -1).all()
+        bad = from_polys([[[0, 0], [5, 0], [0, 5]], [[1, 1], [2, 2]]])
+        g.run(bad.xy, bad.offsets)
+        flags, total = g.status()
+        assert flags == 2 and total == 0   # fewer than 3 vertices
+        one = qs.subset([0])
+        g.run(one.xy, one.offsets)
+        flags, total = g.status()
+        assert flags in (0, 8)
+        if flags == 0:
+            qh, row_ptr, cand, count, ids, nn = plain_outputs(B, ctx, one, P, h, index, 4)
+            assert torch.equal(g.top_ids[:1], ids)
+        with pytest.raises(B.PmhError):
+            big = qs.subset(np.arange(0, 65))
+            g.run(big.xy, big.offsets)
+    finally:
+        g.close()
