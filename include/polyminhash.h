@@ -236,6 +236,42 @@ int pmh_qgraph_outputs(pmh_qgraph graph, uint32_t** d_hashes, int64_t** d_row_pt
 int pmh_qgraph_status(pmh_qgraph graph, int* h_flags, int64_t* h_total, void* stream);
 int pmh_qgraph_destroy(pmh_qgraph graph);
 
+/* A7 -- learned reranker (not in the paper): an MLP 37 -> 64 -> 64 -> 1
+ * (ReLU, ReLU, sigmoid) predicting the Jaccard similarity of a (query,
+ * candidate) pair, trained on the GPU by mean squared error against exact
+ * Jaccard.  bf16 weights and activations on the tensor cores, fp32
+ * accumulation and fp32 master weights (Adam).
+ * Packed parameter layout (PMH_RERANK_PARAMS floats): w1 [64][37] (out, in),
+ * b1 [64], w2 [64][64], b2 [64], w3 [64], b3 [1].
+ * Features (pmh_rerank_features): bf16 [E][48] per CSR pair, columns
+ *   0..31 group-match bits (group j = hashes j*K/32 .. (j+1)*K/32-1 all equal
+ *          and not T), 32 agreement count / K, 33-34 log2(area) / 32 of query
+ *          and candidate, 35-36 log2(vertex count) / 16, 37..47 zero.
+ *   K must be a multiple of 32.
+ * pmh_rerank_forward writes a score in (0, 1) per feature row (feed it to
+ * pmh_topm as d_score).  pmh_rerank_gradients computes the loss (mean over
+ * n_rows) and the packed gradients of one batch into the reranker (and
+ * copies them to d_grads / d_loss when not NULL); pmh_rerank_adam_step
+ * applies them.  set/get move the packed fp32 master weights (synchronise). */
+#define PMH_RERANK_IN 37
+#define PMH_RERANK_HIDDEN 64
+#define PMH_RERANK_PARAMS 6657
+typedef struct pmh_rerank_s* pmh_rerank;
+int pmh_rerank_create(pmh_ctx ctx, pmh_rerank* out);
+int pmh_rerank_destroy(pmh_rerank r);
+int pmh_rerank_set_weights(pmh_rerank r, const float* h_params);
+int pmh_rerank_get_weights(pmh_rerank r, float* h_params);
+int pmh_rerank_features(pmh_ctx ctx, pmh_polys queries, pmh_polys db, const uint32_t* d_qhashes,
+                        const uint32_t* d_dbhashes, const int64_t* d_row_ptr,
+                        const int32_t* d_cand, int64_t Q, const pmh_params* params,
+                        uint16_t* d_feat, void* stream);
+int pmh_rerank_forward(pmh_rerank r, const uint16_t* d_feat, int64_t n_rows, float* d_score,
+                       void* stream);
+int pmh_rerank_gradients(pmh_rerank r, const uint16_t* d_feat, const float* d_label,
+                         int64_t n_rows, float* d_grads, float* d_loss, void* stream);
+int pmh_rerank_adam_step(pmh_rerank r, float lr, float beta1, float beta2, float eps,
+                         void* stream);
+
 /* Allocation-free signing (the paper has no counterpart: this is a deployment
  * entry point).  Same hashes as pmh_minhash_sign, for callers that must not
  * let a library allocate device memory: processes that reserve their whole

@@ -79,6 +79,16 @@ _SIGS = {
     "pmh_qgraph_outputs": (ctypes.c_int, [_P] + [ctypes.POINTER(_P)] * 6),
     "pmh_qgraph_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), _P]),
     "pmh_qgraph_destroy": (ctypes.c_int, [_P]),
+    "pmh_rerank_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "pmh_rerank_destroy": (ctypes.c_int, [_P]),
+    "pmh_rerank_set_weights": (ctypes.c_int, [_P, _P]),
+    "pmh_rerank_get_weights": (ctypes.c_int, [_P, _P]),
+    "pmh_rerank_features": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _i64, ctypes.POINTER(Params),
+                                           _P, _P]),
+    "pmh_rerank_forward": (ctypes.c_int, [_P, _P, _i64, _P, _P]),
+    "pmh_rerank_gradients": (ctypes.c_int, [_P, _P, _P, _i64, _P, _P, _P]),
+    "pmh_rerank_adam_step": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                            ctypes.c_float, _P]),
 }
 
 
@@ -468,6 +478,104 @@ class QueryGraph:
     def close(self):
         if self.handle:
             load().pmh_qgraph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------- A7
+RERANK_IN, RERANK_HIDDEN, RERANK_PARAMS, RERANK_FEAT_COLS = 37, 64, 6657, 48
+
+
+def unpack_params(flat):
+    """Split packed reranker parameters into (w1, b1, w2, b2, w3, b3)."""
+    import numpy as np
+    flat = np.asarray(flat)
+    h, d = RERANK_HIDDEN, RERANK_IN
+    o = np.cumsum([0, h * d, h, h * h, h, h, 1])
+    return (flat[o[0]:o[1]].reshape(h, d), flat[o[1]:o[2]], flat[o[2]:o[3]].reshape(h, h),
+            flat[o[3]:o[4]], flat[o[4]:o[5]], flat[o[5]:o[6]])
+
+
+def init_rerank_params(seed: int = 0):
+    """Packed fp32 initial weights: He-normal layers, zero biases, small output layer."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    h, d = RERANK_HIDDEN, RERANK_IN
+    parts = [rng.normal(0, np.sqrt(2.0 / d), (h, d)), np.zeros(h),
+             rng.normal(0, np.sqrt(2.0 / h), (h, h)), np.zeros(h),
+             rng.normal(0, np.sqrt(1.0 / h), h), np.zeros(1)]
+    return np.concatenate([p.reshape(-1) for p in parts]).astype(np.float32)
+
+
+def rerank_features(ctx: Context, queries: Polys, db: Polys, qhashes, dbhashes, row_ptr, cand,
+                    params: Params, stream=None):
+    """A7 features: bf16 bits [E, 48] (int16 tensor) of every CSR pair."""
+    E = cand.numel()
+    out = torch.empty((max(E, 1), RERANK_FEAT_COLS), dtype=torch.int16, device=qhashes.device)
+    _check(load().pmh_rerank_features(ctx.handle, queries.handle, db.handle, _ptr(qhashes),
+                                      _ptr(dbhashes), _ptr(row_ptr), _ptr(cand),
+                                      row_ptr.numel() - 1, ctypes.byref(params), _ptr(out),
+                                      _stream(stream)))
+    return out[:E]
+
+
+class Reranker:
+    """A7: the MLP reranker (training and inference kernels on the GPU)."""
+
+    def __init__(self, ctx: Context, weights=None, seed: int = 0):
+        h = _P()
+        _check(load().pmh_rerank_create(ctx.handle, ctypes.byref(h)))
+        self.ctx, self.handle = ctx, h
+        ctx._adopt(self)
+        dev = torch.device("cuda", ctx.device)
+        self._loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.set_weights(init_rerank_params(seed) if weights is None else weights)
+
+    def set_weights(self, flat):
+        import numpy as np
+        w = np.ascontiguousarray(flat, dtype=np.float32)
+        assert w.size == RERANK_PARAMS
+        _check(load().pmh_rerank_set_weights(self.handle, w.ctypes.data))
+
+    def get_weights(self):
+        import numpy as np
+        w = np.empty(RERANK_PARAMS, np.float32)
+        _check(load().pmh_rerank_get_weights(self.handle, w.ctypes.data))
+        return w
+
+    def forward(self, feat, out=None, stream=None):
+        n = feat.shape[0]
+        if out is None:
+            out = torch.empty(max(n, 1), dtype=torch.float32, device=feat.device)
+        _check(load().pmh_rerank_forward(self.handle, _ptr(feat), n, _ptr(out), _stream(stream)))
+        return out[:n]
+
+    def gradients(self, feat, label, stream=None):
+        """(packed gradients [6657] fp32 tensor, loss tensor) of the mean squared error."""
+        grads = torch.empty(RERANK_PARAMS, dtype=torch.float32, device=feat.device)
+        _check(load().pmh_rerank_gradients(self.handle, _ptr(feat), _ptr(label), feat.shape[0],
+                                           _ptr(grads), _ptr(self._loss), _stream(stream)))
+        return grads, self._loss
+
+    def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                  stream=None):
+        _check(load().pmh_rerank_adam_step(self.handle, lr, beta1, beta2, eps, _stream(stream)))
+
+    def train_step(self, feat, label, lr: float, stream=None):
+        """One Adam step on one batch; returns the batch loss tensor (device)."""
+        _check(load().pmh_rerank_gradients(self.handle, _ptr(feat), _ptr(label), feat.shape[0],
+                                           None, _ptr(self._loss), _stream(stream)))
+        self.adam_step(lr, stream=stream)
+        return self._loss
+
+    def close(self):
+        if self.handle:
+            load().pmh_rerank_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,625 @@
+// rerank.cu -- A7: learned reranker of bucket candidates (not in the paper).
+//
+// A small MLP maps features of a (query, candidate) pair to a predicted
+// Jaccard similarity; candidates are then ordered by it (A6) so the exact
+// refinement (A8) touches fewer of them.  Network 37 -> 64 -> 64 -> 1, ReLU,
+// ReLU, sigmoid, mean squared error against the exact Jaccard.
+//
+// Features (bf16, padded to 48 columns):
+//   0..31  group-match bits: bit j = all K/32 hashes of group j agree (and are
+//          not the sentinel) -- the band-match pattern of a 32-band split;
+//   32     agreement fraction c / K (Theorem 1 estimate of J);
+//   33, 34 log2 of the query's and the candidate's area / 32;
+//   35, 36 log2 of the query's and the candidate's vertex count / 16.
+//
+// GEMMs run on the tensor cores with mma.sync m16n8k16 (bf16 operands, fp32
+// accumulation).  One warp owns 16 rows; the accumulator fragment of one
+// layer is, element for element, the A fragment of the next, so activations
+// stay in registers.  Training fuses forward and backward per 128-row chunk:
+// activations and back-propagated gradients go to shared memory, weight
+// gradients are tensor-core GEMMs over the chunk's rows (K = rows), kept in
+// registers across chunks and added to global memory once per CTA.  Operand
+// rounding points follow the fp64 reference exactly: weights, layer inputs and
+// the back-propagated gradients feeding a GEMM are bf16; sums are fp32.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "pmh_internal.cuh"
+
+namespace {
+
+constexpr int kIn = PMH_RERANK_IN;      // 37
+constexpr int kInPad = 48;
+constexpr int kH = PMH_RERANK_HIDDEN;   // 64
+constexpr int kWarpsMlp = 8;
+constexpr int kChunk = kWarpsMlp * 16;  // rows per CTA iteration
+constexpr int XS = 56;                  // shared row strides (bf16), bank-conflict padding
+constexpr int HS = 72;
+
+// packed parameter / gradient layout
+constexpr int OFF_W1 = 0;
+constexpr int OFF_B1 = OFF_W1 + kH * kIn;
+constexpr int OFF_W2 = OFF_B1 + kH;
+constexpr int OFF_B2 = OFF_W2 + kH * kH;
+constexpr int OFF_W3 = OFF_B2 + kH;
+constexpr int OFF_B3 = OFF_W3 + kH;
+constexpr int N_PARAMS = OFF_B3 + 1;
+static_assert(N_PARAMS == PMH_RERANK_PARAMS, "packed layout");
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_raw(__nv_bfloat16 lo, __nv_bfloat16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ float bfr(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p)
+{
+    return *reinterpret_cast<const uint32_t*>(p);
+}
+
+struct MlpSmem {
+    __nv_bfloat16 w1[kH][XS];   // [out][in]   B operand of layer 1
+    __nv_bfloat16 w2[kH][HS];   // [out][in]   B operand of layer 2
+    __nv_bfloat16 w2t[kH][HS];  // [in][out]   B operand of dh1 = d2 . W2
+    __nv_bfloat16 w3[8][HS];    // row 0 = w3, rows 1..7 zero
+    float b1[kH], b2[kH], w3f[kH], b3;
+    __nv_bfloat16 x[kChunk][XS];
+    __nv_bfloat16 h1[kChunk][HS];
+    __nv_bfloat16 d2[kChunk][HS];
+    __nv_bfloat16 d1[kChunk][HS];
+    float g3[kChunk];
+    float gb1[kH], gb2[kH], gw3[kH], gb3, loss;
+};
+
+// features of pair e = (q, cand[e])
+__global__ void features_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ ph,
+                                const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cand,
+                                int64_t Q, int K, uint32_t T, const int64_t* __restrict__ q_area2,
+                                const int64_t* __restrict__ q_off, const int64_t* __restrict__ p_area2,
+                                const int64_t* __restrict__ p_off, __nv_bfloat16* __restrict__ feat)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t E = row_ptr[Q];
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int g = K / 32;  // hashes per group
+    for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < E; e += nwarps) {
+        int64_t lo = 0, hi = Q;
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (row_ptr[mid] <= e) lo = mid;
+            else hi = mid;
+        }
+        const int64_t q = lo;
+        const int64_t p = cand[e];
+        const uint32_t* a = qh + q * K;
+        const uint32_t* b = ph + p * K;
+        // lane j handles group j
+        int agree = 0;
+        bool all = true;
+        for (int i = 0; i < g; ++i) {
+            uint32_t x = a[lane * g + i], y = b[lane * g + i];
+            bool eq = (x == y) & (x != T);
+            agree += eq;
+            all &= eq;
+        }
+        agree = __reduce_add_sync(0xffffffffu, agree);
+        __nv_bfloat16* f = feat + e * kInPad;
+        f[lane] = __float2bfloat16_rn(all ? 1.f : 0.f);
+        if (lane < kInPad - 32) {
+            float v = 0.f;
+            if (lane == 0) v = (float)agree / (float)K;
+            if (lane == 1 || lane == 2) {
+                long long a2 = lane == 1 ? q_area2[q] : p_area2[p];
+                double ar = 0.5 * (double)(a2 < 0 ? -a2 : a2);
+                v = (float)(log2(fmax(ar, 1.0)) / 32.0);
+            }
+            if (lane == 3 || lane == 4) {
+                int64_t n = lane == 3 ? q_off[q + 1] - q_off[q] : p_off[p + 1] - p_off[p];
+                v = (float)(log2((double)n) / 16.0);
+            }
+            f[32 + lane] = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+// load the bf16 weights into shared memory (padding zeroed)
+__device__ void load_weights(MlpSmem& s, const __nv_bfloat16* __restrict__ w1b,
+                             const __nv_bfloat16* __restrict__ w2b,
+                             const __nv_bfloat16* __restrict__ w3b, const float* __restrict__ master)
+{
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    for (int i = threadIdx.x; i < kH * XS; i += blockDim.x) {
+        int o = i / XS, c = i % XS;
+        s.w1[o][c] = c < kInPad ? w1b[o * kInPad + c] : zero;
+    }
+    for (int i = threadIdx.x; i < kH * HS; i += blockDim.x) {
+        int o = i / HS, c = i % HS;
+        s.w2[o][c] = c < kH ? w2b[o * kH + c] : zero;
+        s.w2t[o][c] = c < kH ? w2b[c * kH + o] : zero;
+    }
+    for (int i = threadIdx.x; i < 8 * HS; i += blockDim.x) {
+        int r = i / HS, c = i % HS;
+        s.w3[r][c] = (r == 0 && c < kH) ? w3b[c] : zero;
+    }
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+        s.b1[i] = master[OFF_B1 + i];
+        s.b2[i] = master[OFF_B2 + i];
+        s.w3f[i] = __bfloat162float(w3b[i]);
+        s.gb1[i] = 0.f;
+        s.gb2[i] = 0.f;
+        s.gw3[i] = 0.f;
+    }
+    if (threadIdx.x == 0) {
+        s.b3 = master[OFF_B3];
+        s.gb3 = 0.f;
+        s.loss = 0.f;
+    }
+}
+
+// Forward (kTrain = false: writes scores) or forward + backward (kTrain = true:
+// accumulates gradients of the mean squared error over n_total rows).
+template <bool kTrain>
+__global__ void __launch_bounds__(kWarpsMlp * 32, 1)
+mlp_kernel(const __nv_bfloat16* __restrict__ feat, const float* __restrict__ label, int64_t n_rows,
+           int64_t n_total, const __nv_bfloat16* __restrict__ w1b,
+           const __nv_bfloat16* __restrict__ w2b, const __nv_bfloat16* __restrict__ w3b,
+           const float* __restrict__ master, float* __restrict__ score, float* __restrict__ grads,
+           float* __restrict__ loss_out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MlpSmem& s = *reinterpret_cast<MlpSmem*>(smem_raw);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    load_weights(s, w1b, w2b, w3b, master);
+    __syncthreads();
+
+    // weight-gradient accumulators of this warp, kept across chunks:
+    // gW2 slice: out units 16*(wid/2).., in units 32*(wid%2).. (4 n-tiles);
+    // gW1 slice: out units 16*(wid/2).., in units 24*(wid%2).. (3 n-tiles)
+    float acc_w2[4][4] = {};
+    float acc_w1[3][4] = {};
+    const float inv_n = 1.f / (float)(n_total > 1 ? n_total : 1);
+
+    for (int64_t base = (int64_t)blockIdx.x * kChunk; base < n_rows; base += (int64_t)gridDim.x * kChunk) {
+        // stage the chunk's features (rows past n_rows are zero)
+        for (int i = threadIdx.x; i < kChunk * (kInPad / 2); i += blockDim.x) {
+            int r = i / (kInPad / 2), c2 = i % (kInPad / 2);
+            uint32_t v = 0;
+            if (base + r < n_rows) v = ld32(feat + (base + r) * kInPad + 2 * c2);
+            *reinterpret_cast<uint32_t*>(&s.x[r][2 * c2]) = v;
+        }
+        __syncthreads();
+        const int r0 = wid * 16;  // this warp's rows within the chunk
+
+        // ---- layer 1: [16 x 48] x [48 x 64]
+        float acc1[8][4] = {};
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+            uint32_t a[4] = {ld32(&s.x[r0 + g][16 * kk + 2 * t]), ld32(&s.x[r0 + g + 8][16 * kk + 2 * t]),
+                             ld32(&s.x[r0 + g][16 * kk + 2 * t + 8]),
+                             ld32(&s.x[r0 + g + 8][16 * kk + 2 * t + 8])};
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                uint32_t b[2] = {ld32(&s.w1[nt * 8 + g][16 * kk + 2 * t]),
+                                 ld32(&s.w1[nt * 8 + g][16 * kk + 2 * t + 8])};
+                mma_bf16(acc1[nt], a, b);
+            }
+        }
+        uint32_t a2f[4][4];
+        uint32_t mask1 = 0;  // bit (nt*4 + i): z1 > 0 for element i of n-tile nt
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float h[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float z = acc1[nt][i] + s.b1[nt * 8 + 2 * t + (i & 1)];
+                mask1 |= (uint32_t)(z > 0.f) << (nt * 4 + i);
+                h[i] = z > 0.f ? z : 0.f;
+            }
+            uint32_t lo = pack2(h[0], h[1]), hi = pack2(h[2], h[3]);
+            a2f[nt >> 1][(nt & 1) * 2 + 0] = lo;
+            a2f[nt >> 1][(nt & 1) * 2 + 1] = hi;
+            if (kTrain) {
+                *reinterpret_cast<uint32_t*>(&s.h1[r0 + g][nt * 8 + 2 * t]) = lo;
+                *reinterpret_cast<uint32_t*>(&s.h1[r0 + g + 8][nt * 8 + 2 * t]) = hi;
+            }
+        }
+        // ---- layer 2: [16 x 64] x [64 x 64]
+        float acc2[8][4] = {};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                uint32_t b[2] = {ld32(&s.w2[nt * 8 + g][16 * kk + 2 * t]),
+                                 ld32(&s.w2[nt * 8 + g][16 * kk + 2 * t + 8])};
+                mma_bf16(acc2[nt], a2f[kk], b);
+            }
+        }
+        uint32_t a3f[4][4];
+        uint32_t mask2 = 0;
+        float h2v[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float z = acc2[nt][i] + s.b2[nt * 8 + 2 * t + (i & 1)];
+                mask2 |= (uint32_t)(z > 0.f) << (nt * 4 + i);
+                h2v[nt][i] = bfr(z > 0.f ? z : 0.f);
+            }
+            uint32_t lo = pack2(h2v[nt][0], h2v[nt][1]), hi = pack2(h2v[nt][2], h2v[nt][3]);
+            a3f[nt >> 1][(nt & 1) * 2 + 0] = lo;
+            a3f[nt >> 1][(nt & 1) * 2 + 1] = hi;
+        }
+        // ---- layer 3: [16 x 64] x [64 x 8] (column 0 = w3)
+        float acc3[4] = {};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            uint32_t b[2] = {ld32(&s.w3[g][16 * kk + 2 * t]), ld32(&s.w3[g][16 * kk + 2 * t + 8])};
+            mma_bf16(acc3, a3f[kk], b);
+        }
+        // rows r0+g (acc3[0]) and r0+g+8 (acc3[2]) live in lanes with t == 0
+        const int64_t rowA = base + r0 + g, rowB = rowA + 8;
+        float pA = 1.f / (1.f + expf(-(acc3[0] + s.b3)));
+        float pB = 1.f / (1.f + expf(-(acc3[2] + s.b3)));
+        if (!kTrain) {
+            if (t == 0) {
+                if (rowA < n_rows) score[rowA] = pA;
+                if (rowB < n_rows) score[rowB] = pB;
+            }
+            __syncthreads();
+            continue;
+        }
+        // ---- backward
+        if (t == 0) {
+            float gA = 0.f, gB = 0.f, l = 0.f;
+            if (rowA < n_rows) {
+                float err = pA - label[rowA];
+                l += err * err;
+                gA = 2.f * err * inv_n * pA * (1.f - pA);
+            }
+            if (rowB < n_rows) {
+                float err = pB - label[rowB];
+                l += err * err;
+                gB = 2.f * err * inv_n * pB * (1.f - pB);
+            }
+            s.g3[r0 + g] = gA;
+            s.g3[r0 + g + 8] = gB;
+            atomicAdd(&s.loss, l);
+            atomicAdd(&s.gb3, gA + gB);
+        }
+        __syncwarp();
+        const float g3A = s.g3[r0 + g], g3B = s.g3[r0 + g + 8];
+        const float g3rA = bfr(g3A), g3rB = bfr(g3B);
+        // d2 = bf16(relu'(z2) * w3 * g3r); gb2 += relu'(z2) * w3 * g3r; gw3 += g3r * h2
+        uint32_t a4f[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float d[4], gw[2], gb[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int col = nt * 8 + 2 * t + c;
+                const float w3 = s.w3f[col];
+                const bool mA = (mask2 >> (nt * 4 + c)) & 1u, mB = (mask2 >> (nt * 4 + 2 + c)) & 1u;
+                d[c] = mA ? w3 * g3rA : 0.f;
+                d[2 + c] = mB ? w3 * g3rB : 0.f;
+                gb[c] = d[c] + d[2 + c];
+                gw[c] = g3rA * h2v[nt][c] + g3rB * h2v[nt][2 + c];
+            }
+            // reduce over the 8 row groups g (lanes with equal t)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) {
+                    gb[c] += __shfl_xor_sync(0xffffffffu, gb[c], o);
+                    gw[c] += __shfl_xor_sync(0xffffffffu, gw[c], o);
+                }
+            }
+            if (g == 0) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    atomicAdd(&s.gb2[nt * 8 + 2 * t + c], gb[c]);
+                    atomicAdd(&s.gw3[nt * 8 + 2 * t + c], gw[c]);
+                }
+            }
+            uint32_t lo = pack2(d[0], d[1]), hi = pack2(d[2], d[3]);
+            a4f[nt >> 1][(nt & 1) * 2 + 0] = lo;
+            a4f[nt >> 1][(nt & 1) * 2 + 1] = hi;
+            *reinterpret_cast<uint32_t*>(&s.d2[r0 + g][nt * 8 + 2 * t]) = lo;
+            *reinterpret_cast<uint32_t*>(&s.d2[r0 + g + 8][nt * 8 + 2 * t]) = hi;
+        }
+        // dh1 = d2 . W2 : [16 x 64 out] x [64 out x 64 in]
+        float acc4[8][4] = {};
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                uint32_t b[2] = {ld32(&s.w2t[nt * 8 + g][16 * kk + 2 * t]),
+                                 ld32(&s.w2t[nt * 8 + g][16 * kk + 2 * t + 8])};
+                mma_bf16(acc4[nt], a4f[kk], b);
+            }
+        }
+        // d1 = relu'(z1) * dh1; gb1 += d1; d1 (bf16) to shared memory
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float d[4], gb[2];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) d[i] = ((mask1 >> (nt * 4 + i)) & 1u) ? acc4[nt][i] : 0.f;
+            gb[0] = d[0] + d[2];
+            gb[1] = d[1] + d[3];
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) gb[c] += __shfl_xor_sync(0xffffffffu, gb[c], o);
+            if (g == 0) {
+                atomicAdd(&s.gb1[nt * 8 + 2 * t], gb[0]);
+                atomicAdd(&s.gb1[nt * 8 + 2 * t + 1], gb[1]);
+            }
+            *reinterpret_cast<uint32_t*>(&s.d1[r0 + g][nt * 8 + 2 * t]) = pack2(d[0], d[1]);
+            *reinterpret_cast<uint32_t*>(&s.d1[r0 + g + 8][nt * 8 + 2 * t]) = pack2(d[2], d[3]);
+        }
+        __syncthreads();
+        // weight gradients over the chunk's 128 rows (K = rows)
+        const int m0 = 16 * (wid >> 1);
+#pragma unroll
+        for (int kk = 0; kk < kChunk / 16; ++kk) {
+            const int k0 = 16 * kk;
+            // A[m = out][k = row] = d2[row][out]
+            uint32_t a[4] = {pack_raw(s.d2[k0 + 2 * t][m0 + g], s.d2[k0 + 2 * t + 1][m0 + g]),
+                             pack_raw(s.d2[k0 + 2 * t][m0 + g + 8], s.d2[k0 + 2 * t + 1][m0 + g + 8]),
+                             pack_raw(s.d2[k0 + 2 * t + 8][m0 + g], s.d2[k0 + 2 * t + 9][m0 + g]),
+                             pack_raw(s.d2[k0 + 2 * t + 8][m0 + g + 8], s.d2[k0 + 2 * t + 9][m0 + g + 8])};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n0 = 32 * (wid & 1) + 8 * j;
+                // B[k = row][n = in] = h1[row][in]
+                uint32_t b[2] = {pack_raw(s.h1[k0 + 2 * t][n0 + g], s.h1[k0 + 2 * t + 1][n0 + g]),
+                                 pack_raw(s.h1[k0 + 2 * t + 8][n0 + g], s.h1[k0 + 2 * t + 9][n0 + g])};
+                mma_bf16(acc_w2[j], a, b);
+            }
+            uint32_t a1[4] = {pack_raw(s.d1[k0 + 2 * t][m0 + g], s.d1[k0 + 2 * t + 1][m0 + g]),
+                              pack_raw(s.d1[k0 + 2 * t][m0 + g + 8], s.d1[k0 + 2 * t + 1][m0 + g + 8]),
+                              pack_raw(s.d1[k0 + 2 * t + 8][m0 + g], s.d1[k0 + 2 * t + 9][m0 + g]),
+                              pack_raw(s.d1[k0 + 2 * t + 8][m0 + g + 8], s.d1[k0 + 2 * t + 9][m0 + g + 8])};
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int n0 = 24 * (wid & 1) + 8 * j;
+                uint32_t b[2] = {pack_raw(s.x[k0 + 2 * t][n0 + g], s.x[k0 + 2 * t + 1][n0 + g]),
+                                 pack_raw(s.x[k0 + 2 * t + 8][n0 + g], s.x[k0 + 2 * t + 9][n0 + g])};
+                mma_bf16(acc_w1[j], a1, b);
+            }
+        }
+        __syncthreads();
+    }
+    if (!kTrain) return;
+    // flush: this warp's weight-gradient slices and the CTA's small partials
+    const int m0 = 16 * (wid >> 1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int n0 = 32 * (wid & 1) + 8 * j;
+        atomicAdd(&grads[OFF_W2 + (m0 + g) * kH + n0 + 2 * t], acc_w2[j][0]);
+        atomicAdd(&grads[OFF_W2 + (m0 + g) * kH + n0 + 2 * t + 1], acc_w2[j][1]);
+        atomicAdd(&grads[OFF_W2 + (m0 + g + 8) * kH + n0 + 2 * t], acc_w2[j][2]);
+        atomicAdd(&grads[OFF_W2 + (m0 + g + 8) * kH + n0 + 2 * t + 1], acc_w2[j][3]);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int n0 = 24 * (wid & 1) + 8 * j;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int o = m0 + g + (i >= 2 ? 8 : 0), c = n0 + 2 * t + (i & 1);
+            if (c < kIn) atomicAdd(&grads[OFF_W1 + o * kIn + c], acc_w1[j][i]);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+        atomicAdd(&grads[OFF_B1 + i], s.gb1[i]);
+        atomicAdd(&grads[OFF_B2 + i], s.gb2[i]);
+        atomicAdd(&grads[OFF_W3 + i], s.gw3[i]);
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&grads[OFF_B3], s.gb3);
+        atomicAdd(loss_out, s.loss * inv_n);
+    }
+}
+
+// Adam on the fp32 master weights (the bf16 operand copies are refreshed after it)
+__global__ void adam_kernel(float* __restrict__ master, float* __restrict__ m1,
+                            float* __restrict__ m2, const float* __restrict__ grads, float lr,
+                            float beta1, float beta2, float eps, float bc1, float bc2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N_PARAMS; i += gridDim.x * blockDim.x) {
+        float gr = grads[i];
+        float a = beta1 * m1[i] + (1.f - beta1) * gr;
+        float b = beta2 * m2[i] + (1.f - beta2) * gr * gr;
+        m1[i] = a;
+        m2[i] = b;
+        float w = master[i] - lr * (a / bc1) / (sqrtf(b / bc2) + eps);
+        master[i] = w;
+    }
+}
+
+__global__ void refresh_bf16_kernel(const float* __restrict__ master, __nv_bfloat16* __restrict__ w1b,
+                                    __nv_bfloat16* __restrict__ w2b, __nv_bfloat16* __restrict__ w3b)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kH * kInPad; i += gridDim.x * blockDim.x) {
+        int o = i / kInPad, c = i % kInPad;
+        w1b[i] = __float2bfloat16_rn(c < kIn ? master[OFF_W1 + o * kIn + c] : 0.f);
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kH * kH; i += gridDim.x * blockDim.x)
+        w2b[i] = __float2bfloat16_rn(master[OFF_W2 + i]);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kH; i += gridDim.x * blockDim.x)
+        w3b[i] = __float2bfloat16_rn(master[OFF_W3 + i]);
+}
+
+}  // namespace
+
+struct pmh_rerank_s {
+    pmh_ctx ctx = nullptr;
+    int device = 0;
+    float* master = nullptr;  // packed fp32 weights
+    float* m1 = nullptr;      // Adam moments
+    float* m2 = nullptr;
+    float* grads = nullptr;
+    float* loss = nullptr;
+    __nv_bfloat16* w1b = nullptr;  // [64][48] bf16 operand copies
+    __nv_bfloat16* w2b = nullptr;  // [64][64]
+    __nv_bfloat16* w3b = nullptr;  // [64]
+    int64_t steps = 0;
+};
+
+extern "C" int pmh_rerank_destroy(pmh_rerank r)
+{
+    if (!r) return PMH_OK;
+    cudaSetDevice(r->device);
+    cudaDeviceSynchronize();
+    void* bufs[] = {r->master, r->m1, r->m2, r->grads, r->loss, r->w1b, r->w2b, r->w3b};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete r;
+    return PMH_OK;
+}
+
+extern "C" int pmh_rerank_create(pmh_ctx ctx, pmh_rerank* out)
+{
+    if (!out) return pmh_set_error(PMH_ERR_ARG, "null out");
+    *out = nullptr;
+    PMH_TRY(pmh_check_device(ctx));
+    pmh_rerank r = new pmh_rerank_s();
+    r->ctx = ctx;
+    r->device = ctx->device;
+    bool ok = cudaMalloc(&r->master, sizeof(float) * N_PARAMS) == cudaSuccess &&
+              cudaMalloc(&r->m1, sizeof(float) * N_PARAMS) == cudaSuccess &&
+              cudaMalloc(&r->m2, sizeof(float) * N_PARAMS) == cudaSuccess &&
+              cudaMalloc(&r->grads, sizeof(float) * N_PARAMS) == cudaSuccess &&
+              cudaMalloc(&r->loss, sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&r->w1b, sizeof(__nv_bfloat16) * kH * kInPad) == cudaSuccess &&
+              cudaMalloc(&r->w2b, sizeof(__nv_bfloat16) * kH * kH) == cudaSuccess &&
+              cudaMalloc(&r->w3b, sizeof(__nv_bfloat16) * kH) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        pmh_rerank_destroy(r);
+        return pmh_set_error(PMH_ERR_NOMEM, "reranker allocation failed");
+    }
+    cudaMemset(r->master, 0, sizeof(float) * N_PARAMS);
+    cudaMemset(r->m1, 0, sizeof(float) * N_PARAMS);
+    cudaMemset(r->m2, 0, sizeof(float) * N_PARAMS);
+    refresh_bf16_kernel<<<8, 256>>>(r->master, r->w1b, r->w2b, r->w3b);
+    g_pmh_launches.fetch_add(1);
+    PMH_CUDA_TRY(cudaDeviceSynchronize());
+    *out = r;
+    return PMH_OK;
+}
+
+extern "C" int pmh_rerank_set_weights(pmh_rerank r, const float* h_params)
+{
+    if (!r || !h_params) return pmh_set_error(PMH_ERR_ARG, "null argument");
+    PMH_TRY(pmh_check_device(r->ctx));
+    PMH_CUDA_TRY(cudaMemcpy(r->master, h_params, sizeof(float) * N_PARAMS, cudaMemcpyHostToDevice));
+    PMH_CUDA_TRY(cudaMemset(r->m1, 0, sizeof(float) * N_PARAMS));
+    PMH_CUDA_TRY(cudaMemset(r->m2, 0, sizeof(float) * N_PARAMS));
+    r->steps = 0;
+    refresh_bf16_kernel<<<8, 256>>>(r->master, r->w1b, r->w2b, r->w3b);
+    PMH_LAUNCHED("refresh_bf16_kernel");
+    PMH_CUDA_TRY(cudaDeviceSynchronize());
+    return PMH_OK;
+}
+
+extern "C" int pmh_rerank_get_weights(pmh_rerank r, float* h_params)
+{
+    if (!r || !h_params) return pmh_set_error(PMH_ERR_ARG, "null argument");
+    PMH_TRY(pmh_check_device(r->ctx));
+    PMH_CUDA_TRY(cudaDeviceSynchronize());
+    PMH_CUDA_TRY(cudaMemcpy(h_params, r->master, sizeof(float) * N_PARAMS, cudaMemcpyDeviceToHost));
+    return PMH_OK;
+}
+
+extern "C" int pmh_rerank_features(pmh_ctx ctx, pmh_polys queries, pmh_polys db,
+                                   const uint32_t* d_qhashes, const uint32_t* d_dbhashes,
+                                   const int64_t* d_row_ptr, const int32_t* d_cand, int64_t Q,
+                                   const pmh_params* params, uint16_t* d_feat, void* stream)
+{
+    PMH_TRY(pmh_check_device(ctx));
+    PMH_TRY(pmh_check_params(params));
+    if (!queries || !db || Q < 0 || Q > queries->n || params->K % 32 != 0 ||
+        (Q > 0 && (!d_qhashes || !d_dbhashes || !d_row_ptr || !d_feat)))
+        return pmh_set_error(PMH_ERR_ARG, "bad arguments (K must be a multiple of 32)");
+    if (Q == 0) return PMH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    features_kernel<<<ctx->sm_count * 8, 256, 0, s>>>(
+        d_qhashes, d_dbhashes, d_row_ptr, d_cand, Q, (int)params->K, params->T, queries->area2,
+        queries->offsets, db->area2, db->offsets, reinterpret_cast<__nv_bfloat16*>(d_feat));
+    PMH_LAUNCHED("features_kernel");
+    return PMH_OK;
+}
+
+static int mlp_launch(pmh_rerank r, bool train, const uint16_t* d_feat, const float* d_label,
+                      int64_t n, float* d_score, cudaStream_t s)
+{
+    const size_t smem = sizeof(MlpSmem);
+    auto fn = train ? mlp_kernel<true> : mlp_kernel<false>;
+    PMH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int blocks = (int)std::min<int64_t>((n + kChunk - 1) / kChunk, (int64_t)r->ctx->sm_count);
+    fn<<<std::max(blocks, 1), kWarpsMlp * 32, smem, s>>>(
+        reinterpret_cast<const __nv_bfloat16*>(d_feat), d_label, n, n, r->w1b, r->w2b, r->w3b,
+        r->master, d_score, r->grads, r->loss);
+    PMH_LAUNCHED(train ? "mlp_kernel<train>" : "mlp_kernel<forward>");
+    return PMH_OK;
+}
+
+extern "C" int pmh_rerank_forward(pmh_rerank r, const uint16_t* d_feat, int64_t n_rows,
+                                  float* d_score, void* stream)
+{
+    if (!r || n_rows < 0 || (n_rows > 0 && (!d_feat || !d_score)))
+        return pmh_set_error(PMH_ERR_ARG, "bad arguments");
+    PMH_TRY(pmh_check_device(r->ctx));
+    if (n_rows == 0) return PMH_OK;
+    return mlp_launch(r, false, d_feat, nullptr, n_rows, d_score, (cudaStream_t)stream);
+}
+
+extern "C" int pmh_rerank_gradients(pmh_rerank r, const uint16_t* d_feat, const float* d_label,
+                                    int64_t n_rows, float* d_grads, float* d_loss, void* stream)
+{
+    if (!r || n_rows < 1 || !d_feat || !d_label) return pmh_set_error(PMH_ERR_ARG, "bad arguments");
+    PMH_TRY(pmh_check_device(r->ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    PMH_CUDA_TRY(cudaMemsetAsync(r->grads, 0, sizeof(float) * N_PARAMS, s));
+    PMH_CUDA_TRY(cudaMemsetAsync(r->loss, 0, sizeof(float), s));
+    PMH_TRY(mlp_launch(r, true, d_feat, d_label, n_rows, nullptr, s));
+    if (d_grads)
+        PMH_CUDA_TRY(cudaMemcpyAsync(d_grads, r->grads, sizeof(float) * N_PARAMS,
+                                     cudaMemcpyDeviceToDevice, s));
+    if (d_loss) PMH_CUDA_TRY(cudaMemcpyAsync(d_loss, r->loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return PMH_OK;
+}
+
+extern "C" int pmh_rerank_adam_step(pmh_rerank r, float lr, float beta1, float beta2, float eps,
+                                    void* stream)
+{
+    if (!r) return pmh_set_error(PMH_ERR_ARG, "null reranker");
+    PMH_TRY(pmh_check_device(r->ctx));
+    cudaStream_t s = (cudaStream_t)stream;
+    r->steps += 1;
+    float bc1 = 1.f - powf(beta1, (float)r->steps), bc2 = 1.f - powf(beta2, (float)r->steps);
+    adam_kernel<<<8, 256, 0, s>>>(r->master, r->m1, r->m2, r->grads, lr, beta1, beta2, eps, bc1, bc2);
+    PMH_LAUNCHED("adam_kernel");
+    refresh_bf16_kernel<<<8, 256, 0, s>>>(r->master, r->w1b, r->w2b, r->w3b);
+    PMH_LAUNCHED("refresh_bf16_kernel");
+    return PMH_OK;
+}

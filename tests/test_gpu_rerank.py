@@ -1,0 +1,153 @@
+"""GPU parity of the learned reranker (A7) against the fp64 oracle MLP.
+
+Features are compared with a recomputation from oracle hashes and areas; the forward
+pass and the gradients with the oracle network in which every GEMM operand is rounded to
+bf16 exactly where the GPU rounds it (the GPU accumulates in fp32, the oracle exactly);
+training with the GPU's Adam kernel lowers the loss like an Adam loop run on the oracle's
+gradients.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2511_16576_gb300 import synth
+from test_gpu_parity import DEV, u32, upload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2511_16576_gb300 import binding, build
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def bf16_bits_to_float(bits: np.ndarray) -> np.ndarray:
+    return (bits.astype(np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+@pytest.fixture(scope="module")
+def pairs(B, ctx, orc):
+    w = synth.WORKLOADS["small"]
+    db = synth.make_database(w)
+    qs = synth.make_queries(w, db)
+    K, bands = 64, 64          # one-hash bands: many candidates per query
+    P = B.make_params(K, bands, w.T, w.seed, w.lsh_seed)
+    dbp, qp = upload(B, ctx, db), upload(B, ctx, qs)
+    h = B.minhash_sign(ctx, dbp, P)
+    qh = B.minhash_sign(ctx, qp, P)
+    index = B.lsh_build(ctx, h, P)
+    row_ptr, cand = B.lsh_query(ctx, index, qh)
+    feat = B.rerank_features(ctx, qp, dbp, qh, h, row_ptr, cand, P)
+    return w, db, qs, P, dbp, qp, h, qh, row_ptr, cand, feat
+
+
+def test_features_match_oracle_values(B, ctx, orc, pairs):
+    w, db, qs, P, dbp, qp, h, qh, row_ptr, cand, feat = pairs
+    K = P.K
+    qh_ref = orc.sign(qs.xy, qs.offsets, w.seed, K, w.T, nthreads=8)
+    h_ref = orc.sign(db.xy, db.offsets, w.seed, K, w.T, nthreads=8)
+    rp, cd = row_ptr.cpu().numpy(), cand.cpu().numpy()
+    got = bf16_bits_to_float(feat.cpu().numpy())
+    assert got.shape == (len(cd), 48) and len(cd) > 1000
+    for q in range(qs.n):
+        for e in range(rp[q], rp[q + 1]):
+            p = int(cd[e])
+            eq = (qh_ref[q] == h_ref[p]) & (qh_ref[q] != w.T)
+            exp = np.zeros(48)
+            exp[:32] = eq.reshape(32, K // 32).all(axis=1)
+            exp[32] = eq.sum() / K
+            exp[33] = math.log2(max(abs(orc.area2(qs.poly(q))) / 2, 1)) / 32
+            exp[34] = math.log2(max(abs(orc.area2(db.poly(p))) / 2, 1)) / 32
+            exp[35] = math.log2(len(qs.poly(q))) / 16
+            exp[36] = math.log2(len(db.poly(p))) / 16
+            exp_b = np.array([orc.bf16_round(v) for v in exp])
+            assert np.array_equal(got[e, :33], exp_b[:33]), e
+            # log features: equal up to one bf16 step (the two log2 may round differently)
+            assert np.all(np.abs(got[e, 33:37] - exp_b[33:37]) <= 2 ** -8 * np.abs(exp_b[33:37]) + 1e-12)
+            assert np.all(got[e, 37:] == 0)
+
+
+def random_features(rng, n):
+    f = np.zeros((n, 48), np.float32)
+    f[:, :32] = rng.random((n, 32)) < 0.3
+    f[:, 32] = rng.random(n)
+    f[:, 33:37] = rng.uniform(0.2, 1.0, (n, 4))
+    bits = (f.view(np.uint32) + 0x7FFF + ((f.view(np.uint32) >> 16) & 1)) >> 16   # to bf16 (RNE)
+    return bits.astype(np.uint16).view(np.int16)
+
+
+def oracle_run(orc, B, feat_bits, label, flat, grads=True):
+    x = bf16_bits_to_float(feat_bits)[:, :37]
+    w1, b1, w2, b2, w3, b3 = B.unpack_params(flat.astype(np.float64))
+    return orc.mlp_forward_backward(x, label, w1, b1, w2, b2, w3, b3, grads=grads, bf16=True)
+
+
+@pytest.mark.parametrize("n", [1, 127, 129, 5000])
+def test_forward_and_gradients_match_oracle(B, ctx, orc, n):
+    rng = np.random.default_rng(n)
+    feat = random_features(rng, n)
+    label = rng.random(n).astype(np.float32)
+    flat = B.init_rerank_params(seed=n)
+    flat[B.RERANK_HIDDEN * B.RERANK_IN:B.RERANK_HIDDEN * B.RERANK_IN + 64] = rng.normal(0, 0.1, 64)
+    r = B.Reranker(ctx, flat)
+    try:
+        f_d = torch.from_numpy(feat).to(DEV)
+        l_d = torch.from_numpy(label).to(DEV)
+        score = r.forward(f_d).cpu().numpy()
+        pred, loss, g_ref = oracle_run(orc, B, feat, label, flat)
+        assert np.max(np.abs(score - pred)) < 5e-3
+        assert np.mean(np.abs(score - pred)) < 5e-4
+        grads, loss_d = r.gradients(f_d, l_d)
+        assert abs(float(loss_d.item()) - loss) <= 1e-3 * loss + 1e-7
+        g = grads.cpu().numpy().astype(np.float64)
+        for got, ref in zip(B.unpack_params(g), g_ref):
+            got, ref = got.reshape(-1), ref.reshape(-1)
+            assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref) + 1e-9
+    finally:
+        r.close()
+
+
+def test_training_tracks_oracle_adam(B, ctx, orc, pairs):
+    """20 Adam steps with GPU gradients vs 20 with oracle gradients (numpy Adam)."""
+    w, db, qs, P, dbp, qp, h, qh, row_ptr, cand, feat = pairs
+    rp, cd = row_ptr.cpu().numpy(), cand.cpu().numpy()
+    n = min(len(cd), 2048)
+    lab = np.empty(n, np.float32)
+    q_of = np.searchsorted(rp, np.arange(n), side="right") - 1
+    for e in range(n):
+        lab[e] = orc.jaccard(qs.poly(int(q_of[e])), db.poly(int(cd[e])))
+    fb = feat[:n].contiguous()
+    flat = B.init_rerank_params(seed=3)
+    r = B.Reranker(ctx, flat)
+    lr, b1, b2, eps = 3e-3, 0.9, 0.999, 1e-8
+    gpu_loss, ref_loss = [], []
+    m = np.zeros_like(flat, dtype=np.float64)
+    v = np.zeros_like(m)
+    wref = flat.astype(np.float64)
+    fnp = fb.cpu().numpy()
+    l_d = torch.from_numpy(lab).to(DEV)
+    try:
+        for step in range(1, 21):
+            gpu_loss.append(float(r.train_step(fb, l_d, lr).item()))
+            _, loss, g = oracle_run(orc, B, fnp, lab, wref.astype(np.float32))
+            ref_loss.append(loss)
+            gv = np.concatenate([x.reshape(-1) for x in g])
+            m = b1 * m + (1 - b1) * gv
+            v = b2 * v + (1 - b2) * gv * gv
+            wref = wref - lr * (m / (1 - b1 ** step)) / (np.sqrt(v / (1 - b2 ** step)) + eps)
+        assert gpu_loss[-1] < 0.8 * gpu_loss[0]
+        for a, b in zip(gpu_loss, ref_loss):
+            assert abs(a - b) <= 0.05 * b + 1e-5
+    finally:
+        r.close()
