@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=None, help="polygons in the CPU sample")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default sign variant")
+    ap.add_argument("--no-search", action="store_true", help="skip the recall / queries-per-s sweep")
+    ap.add_argument("--eval-queries", type=int, default=1000,
+                    help="queries whose recall@10 is checked against brute force")
+    ap.add_argument("--train-queries", type=int, default=4000)
     return ap.parse_args()
 
 
@@ -176,6 +180,52 @@ def cpu_baseline(w, db, seconds_target=15.0, n_sample=None):
     return {"value": len(ids) * w.K / dt, "unit": "hashes/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle sign of {len(ids)} random polygons x K={w.K} of the "
                       f"{db.n}-polygon workload ({dt:.1f} s, {cores} threads)"}
+
+
+def search_quality(args, w, B, ctx, db, qs, h, d_xy, d_off, q_xy, q_off, P):
+    """queries/s at recall@10 >= 0.9, plain (agreement count) vs learned (reranker) ranking.
+
+    Runs after the timed region.  Candidates come from a one-hash-per-band index
+    (bands = K) of the same signatures, so that every polygon sharing one MinHash value
+    with the query is a candidate; the headline 16x8 banding is reported beside it."""
+    import torch
+    from paper_2511_16576_gb300 import evaluate as ev
+    from paper_2511_16576_gb300 import synth
+    dev = d_xy.device
+    dbp = B.poly_upload(ctx, d_xy, d_off)
+    qp = B.poly_upload(ctx, q_xy, q_off)
+    n_eval = min(args.eval_queries, qs.n)
+    qe = qs.subset(np.arange(n_eval))
+    qep = B.poly_upload(ctx, torch.from_numpy(qe.xy).to(dev), torch.from_numpy(qe.offsets).to(dev))
+    truth, t_bf = ev.timed(lambda: ev.brute_force_topk(ctx, qep, dbp, 10))
+    out = {"eval_queries": n_eval, "timed_queries": qs.n, "k": 10, "target_recall": 0.9,
+           "bf_pairs_per_query": truth.pairs / n_eval, "bf_seconds_eval_queries": t_bf,
+           "forms": {}}
+    P1 = B.make_params(w.K, w.K, w.T, w.seed, w.lsh_seed)
+    for label, params in (("bands_KxA", P1), ("bands_config", P)):
+        index = B.lsh_build(ctx, h, params)
+        s = ev.Searcher(ctx, index, params, dbp, h)
+        key = f"{params.bands}x{params.rows}"
+        plain = ev.sweep(s, qp, truth, n_eval, learned=False)
+        res = {"bands": key, "plain_curve": plain, "plain": ev.best_at_recall(plain)}
+        if label == "bands_KxA":
+            tq = synth.perturbed_queries(db, args.train_queries, w.query_seed + 1000)
+            tp = B.poly_upload(ctx, torch.from_numpy(tq.xy).to(dev), torch.from_numpy(tq.offsets).to(dev))
+            feat, lab = ev.training_pairs(ctx, s, tp)
+            s.reranker = B.Reranker(ctx, seed=1)
+            (losses, t_train) = ev.timed(lambda: ev.train_reranker(s.reranker, feat, lab))
+            learned = ev.sweep(s, qp, truth, n_eval, learned=True)
+            res.update({"learned_curve": learned, "learned": ev.best_at_recall(learned),
+                        "train_pairs": int(feat.shape[0]), "train_loss_per_epoch": losses,
+                        "train_seconds": t_train})
+            s.reranker.close()
+            tp.close()
+        out["forms"][key] = res
+        index.close()
+    qep.close()
+    qp.close()
+    dbp.close()
+    return out
 
 
 def main():
@@ -315,6 +365,10 @@ def main():
                 "peak_source": "measured: pmh_probe_int_peak (integer mad/add/xor/shl mix, all SMs)",
                 "sign_ms": sign_ms, "points_per_s": G / (sign_ms * 1e-3)}
 
+    search = None
+    if not args.no_search:
+        search = search_quality(args, w, B, ctx, db, qs, h, d_xy, d_off, q_xy, q_off, P)
+
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(w, db, n_sample=args.cpu_sample)
@@ -337,6 +391,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": int(launches),
         "autotune": autotune,
+        "search": search,
         "clocks": clk,
     }
     if rank == 0:

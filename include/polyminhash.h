@@ -300,6 +300,13 @@ int pmh_minhash_sign_noalloc(const int32_t* d_xy, const int64_t* d_offsets, int6
                              int64_t n_vertices, const pmh_params* params, uint32_t* d_hashes,
                              void* stream);
 
+/* Brute-force candidates (the exact search the paper compares against,
+ * Sec. 5.2): CSR of every database polygon whose bounding box overlaps the
+ * query's with positive area (the only polygons with J > 0), ids ascending.
+ * Same two-pass capacity protocol and synchronisation as pmh_lsh_query. */
+int pmh_bbox_join(pmh_ctx ctx, pmh_polys queries, pmh_polys db, int64_t* d_row_ptr,
+                  int32_t* d_cand, int64_t cand_capacity, int64_t* h_total, void* stream);
+
 /* Integer-ALU throughput probe used as the roofline denominator: runs a
  * fixed mix of 32-bit integer instructions (add, logic, shift, multiply-add)
  * on every SM and reports integer instructions per second (thread level).

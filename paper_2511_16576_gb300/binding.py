@@ -79,6 +79,7 @@ _SIGS = {
     "pmh_qgraph_outputs": (ctypes.c_int, [_P] + [ctypes.POINTER(_P)] * 6),
     "pmh_qgraph_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), _P]),
     "pmh_qgraph_destroy": (ctypes.c_int, [_P]),
+    "pmh_bbox_join": (ctypes.c_int, [_P, _P, _P, _P, _P, _i64, ctypes.POINTER(_i64), _P]),
     "pmh_rerank_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "pmh_rerank_destroy": (ctypes.c_int, [_P]),
     "pmh_rerank_set_weights": (ctypes.c_int, [_P, _P]),
@@ -353,6 +354,23 @@ def pair_jaccard(ctx: Context, queries: Polys, db: Polys, qid, pid, stream=None)
     _check(load().pmh_pair_jaccard(ctx.handle, queries.handle, db.handle, _ptr(qid), _ptr(pid), n,
                                    _ptr(out), _stream(stream)))
     return out[:n]
+
+
+def bbox_join(ctx: Context, queries: Polys, db: Polys, stream=None):
+    """Brute-force candidates: CSR of bbox-overlapping database polygons per query."""
+    dev = torch.device("cuda", ctx.device)
+    row_ptr = torch.empty(queries.n + 1, dtype=torch.int64, device=dev)
+    total = _i64()
+    lib = load()
+    cand = torch.empty(1, dtype=torch.int32, device=dev)
+    rc = lib.pmh_bbox_join(ctx.handle, queries.handle, db.handle, _ptr(row_ptr), _ptr(cand), 0,
+                           ctypes.byref(total), _stream(stream))
+    if rc == PMH_ERR_CAPACITY:
+        cand = torch.empty(max(total.value, 1), dtype=torch.int32, device=dev)
+        rc = lib.pmh_bbox_join(ctx.handle, queries.handle, db.handle, _ptr(row_ptr), _ptr(cand),
+                               total.value, ctypes.byref(total), _stream(stream))
+    _check(rc)
+    return row_ptr, cand[:total.value]
 
 
 def probe_int_peak(ctx: Context) -> float:

@@ -309,3 +309,72 @@ extern "C" int pmh_pair_jaccard(pmh_ctx ctx, pmh_polys queries, pmh_polys db, co
     PMH_LAUNCHED("refine_pairs_kernel");
     return PMH_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Brute-force candidate set of the exact search (the paper's BF baseline,
+// Sec. 5.2): every database polygon whose bounding box overlaps the query's
+// with positive area -- the only ones with J > 0.  One warp per query scans
+// the database 32 polygons at a time; ballots keep ids ascending.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <bool kWrite>
+__global__ void bbox_join_kernel(const int4* __restrict__ qbox, int64_t Q, const int4* __restrict__ pbox,
+                                 int64_t N, int64_t* __restrict__ counts,
+                                 const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= Q) return;
+    const int4 a = qbox[q];
+    int64_t cnt = 0, out = kWrite ? row_ptr[q] : 0;
+    for (int64_t base = 0; base < N; base += 32) {
+        const int64_t p = base + lane;
+        bool hit = false;
+        if (p < N) {
+            const int4 b = pbox[p];
+            hit = a.x < b.z && b.x < a.z && a.y < b.w && b.y < a.w;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (kWrite && hit) cand[out + cnt + __popc(m & pmh_lanemask_lt())] = (int32_t)p;
+        cnt += __popc(m);
+    }
+    if (!kWrite && lane == 0) counts[q] = cnt;
+}
+
+}  // namespace
+
+extern "C" int pmh_bbox_join(pmh_ctx ctx, pmh_polys queries, pmh_polys db, int64_t* d_row_ptr,
+                             int32_t* d_cand, int64_t cand_capacity, int64_t* h_total, void* stream)
+{
+    PMH_TRY(pmh_check_device(ctx));
+    if (!queries || !db || !d_row_ptr || !h_total || cand_capacity < 0)
+        return pmh_set_error(PMH_ERR_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t Q = queries->n;
+    *h_total = 0;
+    if (Q == 0) {
+        PMH_CUDA_TRY(cudaMemsetAsync(d_row_ptr, 0, sizeof(int64_t), s));
+        return PMH_OK;
+    }
+    int64_t* counts = nullptr;
+    PMH_TRY(pmh_scratch(ctx, SCR_QUERY, sizeof(int64_t) * (size_t)Q, (void**)&counts));
+    const unsigned blocks = (unsigned)((Q + 7) / 8);
+    bbox_join_kernel<false><<<blocks, 256, 0, s>>>(queries->bbox, Q, db->bbox, db->n, counts, nullptr,
+                                                   nullptr);
+    PMH_LAUNCHED("bbox_join_kernel<count>");
+    PMH_TRY(pmh_exclusive_scan_i64(ctx, counts, d_row_ptr, Q, s));
+    PMH_CUDA_TRY(cudaMemcpyAsync(ctx->h_pinned, d_row_ptr + Q, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    PMH_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t total = ctx->h_pinned[0];
+    *h_total = total;
+    if (total > cand_capacity)
+        return pmh_set_error(PMH_ERR_CAPACITY, "%lld pairs > capacity %lld", (long long)total,
+                             (long long)cand_capacity);
+    if (total == 0) return PMH_OK;
+    if (!d_cand) return pmh_set_error(PMH_ERR_ARG, "null candidate buffer");
+    bbox_join_kernel<true><<<blocks, 256, 0, s>>>(queries->bbox, Q, db->bbox, db->n, nullptr, d_row_ptr,
+                                                  d_cand);
+    PMH_LAUNCHED("bbox_join_kernel<fill>");
+    return PMH_OK;
+}

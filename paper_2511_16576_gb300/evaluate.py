@@ -1,0 +1,162 @@
+"""Search-quality measurement: recall@k and queries/s of the plain and learned forms.
+
+The paper evaluates PolyMinHash by Recall@k against the exact brute-force search and by
+the time of hashmap lookup + refinement (Sec. 5.2, Table "Impact of MinHash lengths").
+Here, on the GPU:
+
+* brute force (the ground truth): every database polygon whose bounding box overlaps a
+  query's (pmh_bbox_join), exact fp64 Jaccard of all those pairs (pmh_pair_jaccard),
+  top-k by (J desc, id asc);
+* the approximate search: sign the queries, join the buckets, count agreements, keep the
+  top-m candidates -- by agreement count (plain form) or by the learned reranker's
+  predicted Jaccard (learned form) -- and refine them exactly to the top-k;
+* recall@k = |returned top-k among the exact top-k| / k (a returned polygon whose exact J
+  ties the k-th exact J within 1e-9 also counts; if fewer than k polygons have J > 0 the
+  denominator is that number).
+
+Every step runs in the library's kernels; this module only orchestrates and times.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+@dataclasses.dataclass
+class Truth:
+    ids: np.ndarray     # int32 [Q, k], -1 padded
+    j: np.ndarray       # float64 [Q, k]
+    n_pos: np.ndarray   # int [Q] number of polygons with J > 0 (capped at k)
+    pairs: int          # exact Jaccard evaluations done by the brute force
+
+
+def brute_force_topk(ctx: B.Context, qp: B.Polys, dbp: B.Polys, k: int = 10) -> Truth:
+    row_ptr, cand = B.bbox_join(ctx, qp, dbp)
+    Q = qp.n
+    counts = (row_ptr[1:] - row_ptr[:-1]).cpu().numpy()
+    qid = torch.repeat_interleave(torch.arange(Q, device=cand.device, dtype=torch.int32),
+                                  torch.from_numpy(counts).to(cand.device))
+    j = B.pair_jaccard(ctx, qp, dbp, qid, cand).cpu().numpy()
+    rp = row_ptr.cpu().numpy()
+    cd = cand.cpu().numpy()
+    ids = np.full((Q, k), -1, np.int32)
+    jj = np.full((Q, k), -1.0)
+    n_pos = np.zeros(Q, np.int64)
+    for q in range(Q):
+        seg_j = j[rp[q]:rp[q + 1]]
+        seg_i = cd[rp[q]:rp[q + 1]]
+        pos = seg_j > 0
+        seg_j, seg_i = seg_j[pos], seg_i[pos]
+        order = np.lexsort((seg_i, -seg_j))[:k]
+        ids[q, :len(order)] = seg_i[order]
+        jj[q, :len(order)] = seg_j[order]
+        n_pos[q] = len(order)
+    return Truth(ids, jj, n_pos, int(len(cd)))
+
+
+def recall_at_k(ann_ids: np.ndarray, ann_j: np.ndarray, truth: Truth, k: int = 10,
+                tol: float = 1e-9) -> float:
+    rec = []
+    for q in range(len(truth.ids)):
+        denom = int(truth.n_pos[q])
+        if denom == 0:
+            continue
+        exact = set(int(x) for x in truth.ids[q, :denom])
+        kth = truth.j[q, denom - 1] if denom == k else 0.0
+        good = 0
+        for i, jv in zip(ann_ids[q, :k], ann_j[q, :k]):
+            if i < 0:
+                continue
+            if int(i) in exact or (denom == k and jv >= kth - tol and jv > 0):
+                good += 1
+        rec.append(min(good, denom) / denom)
+    return float(np.mean(rec)) if rec else 1.0
+
+
+@dataclasses.dataclass
+class Searcher:
+    """The approximate search over one database index."""
+    ctx: B.Context
+    index: B.Index
+    params: B.Params
+    dbp: B.Polys
+    dbh: torch.Tensor
+    reranker: B.Reranker | None = None
+
+    def query(self, qp: B.Polys, m: int, k: int = 10, learned: bool = False, stream=None):
+        qh = B.minhash_sign(self.ctx, qp, self.params, stream=stream)
+        row_ptr, cand = B.lsh_query(self.ctx, self.index, qh, stream=stream)
+        count, _ = B.jaccard_estimate(self.ctx, qh, self.dbh, row_ptr, cand, self.params,
+                                      bandmask=False, stream=stream)
+        score = None
+        if learned:
+            feat = B.rerank_features(self.ctx, qp, self.dbp, qh, self.dbh, row_ptr, cand,
+                                     self.params, stream=stream)
+            score = self.reranker.forward(feat, stream=stream)
+        ids, nn = B.topm(self.ctx, row_ptr, cand, count, m, score=score, stream=stream)
+        top_ids, top_j = B.refine_topk(self.ctx, qp, self.dbp, ids, nn, k, stream=stream)
+        return top_ids, top_j, int(cand.numel())
+
+
+def training_pairs(ctx: B.Context, searcher: Searcher, tp: B.Polys):
+    """Features and exact-Jaccard labels of every bucket candidate of the training queries."""
+    qh = B.minhash_sign(ctx, tp, searcher.params)
+    row_ptr, cand = B.lsh_query(ctx, searcher.index, qh)
+    feat = B.rerank_features(ctx, tp, searcher.dbp, qh, searcher.dbh, row_ptr, cand, searcher.params)
+    counts = (row_ptr[1:] - row_ptr[:-1])
+    qid = torch.repeat_interleave(torch.arange(tp.n, device=cand.device, dtype=torch.int32), counts)
+    label = B.pair_jaccard(ctx, tp, searcher.dbp, qid, cand).to(torch.float32)
+    return feat, label
+
+
+def train_reranker(reranker: B.Reranker, feat: torch.Tensor, label: torch.Tensor, epochs: int = 4,
+                   batch: int = 8192, lr: float = 2e-3, seed: int = 0):
+    """Minibatch Adam on the GPU; returns the mean loss of each epoch."""
+    g = torch.Generator(device=feat.device)
+    g.manual_seed(seed)
+    n = feat.shape[0]
+    losses = []
+    for _ in range(epochs):
+        perm = torch.randperm(n, generator=g, device=feat.device)
+        tot = torch.zeros((), device=feat.device)
+        nb = 0
+        for s in range(0, n, batch):
+            idx = perm[s:s + batch]
+            tot += reranker.train_step(feat[idx].contiguous(), label[idx].contiguous(), lr)[0]
+            nb += 1
+        losses.append(float(tot.item()) / max(nb, 1))
+    return losses
+
+
+def timed(fn, stream=None):
+    stream = stream or torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return out, e0.elapsed_time(e1) * 1e-3
+
+
+def sweep(searcher: Searcher, qp: B.Polys, truth: Truth, n_eval: int, ms=(10, 16, 32, 64, 128, 256, 512),
+          k: int = 10, learned: bool = False):
+    """recall@k (first n_eval queries) and queries/s (whole batch) for each m."""
+    rows = []
+    for m in ms:
+        searcher.query(qp, m, k, learned)  # warm-up
+        (ids, j, ncand), t = timed(lambda: searcher.query(qp, m, k, learned))
+        r = recall_at_k(ids.cpu().numpy()[:n_eval], j.cpu().numpy()[:n_eval], truth, k)
+        rows.append({"m": m, "recall": r, "qps": qp.n / t, "seconds": t,
+                     "candidates_per_query": ncand / qp.n})
+    return rows
+
+
+def best_at_recall(rows, target: float = 0.9):
+    ok = [r for r in rows if r["recall"] >= target]
+    return max(ok, key=lambda r: r["qps"]) if ok else None

@@ -329,3 +329,27 @@ def test_sign_slab_index_degenerate(B, ctx, orc):
     h = u32(B.minhash_sign(ctx, upload(B, ctx, ps), P))
     ref = orc.sign(ps.xy, ps.offsets, SEED, K, T, nthreads=4)
     assert np.array_equal(h, ref)
+
+
+def test_bbox_join_and_brute_force_truth(B, ctx, orc, small):
+    """Brute-force candidates = bbox overlaps (oracle MBRs); exact top-10 = oracle Jaccard."""
+    from paper_2511_16576_gb300 import evaluate as ev
+    w, db, qs = small
+    dbp, qp = upload(B, ctx, db), upload(B, ctx, qs)
+    row_ptr, cand = B.bbox_join(ctx, qp, dbp)
+    rp, cd = row_ptr.cpu().numpy(), cand.cpu().numpy()
+    qb = np.array([orc.bbox(qs.poly(i)) for i in range(qs.n)])
+    pb = np.array([orc.bbox(db.poly(i)) for i in range(db.n)])
+    for q in range(qs.n):
+        a = qb[q]
+        exp = np.nonzero((a[0] < pb[:, 2]) & (pb[:, 0] < a[2]) & (a[1] < pb[:, 3]) & (pb[:, 1] < a[3]))[0]
+        assert list(cd[rp[q]:rp[q + 1]]) == list(exp)
+    truth = ev.brute_force_topk(ctx, qp, dbp, 10)
+    for q in range(0, qs.n, 7):
+        js = [(orc.jaccard(qs.poly(q), db.poly(int(p))), int(p)) for p in cd[rp[q]:rp[q + 1]]]
+        js = sorted([t for t in js if t[0] > 0], key=lambda t: (-t[0], t[1]))[:10]
+        assert truth.n_pos[q] == len(js)
+        for s, (jr, pr) in enumerate(js):
+            assert abs(truth.j[q, s] - jr) <= 1e-9 * jr + 1e-12
+    # the exact search finds itself: recall of the truth against itself is 1
+    assert ev.recall_at_k(truth.ids, truth.j, truth, 10) == 1.0
