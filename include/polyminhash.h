@@ -160,6 +160,14 @@ int pmh_lsh_query(pmh_ctx ctx, pmh_index index, const uint32_t* d_qhashes, int64
                   int64_t* d_row_ptr, int32_t* d_cand, int64_t cand_capacity, int64_t* h_total,
                   void* stream);
 
+/* Second half of pmh_lsh_query for callers that sized the candidate buffer
+ * from a first call (cand_capacity = 0 gives the total and writes d_row_ptr):
+ * fills d_cand from that d_row_ptr without recounting.  cand_capacity must be
+ * at least the total (else nothing is written).  Does not synchronise. */
+int pmh_lsh_query_fill(pmh_ctx ctx, pmh_index index, const uint32_t* d_qhashes, int64_t Q,
+                       const int64_t* d_row_ptr, int32_t* d_cand, int64_t cand_capacity,
+                       void* stream);
+
 /* A5 -- agreement estimate (Theorem 1: Pr[h_k(q) = h_k(p)] = J(q, p)).
  * For every CSR pair (q, d_cand[e]): d_count[e] = #{k : h_k(q) = h_k(p) != T}
  * (J estimate = count / K) and, if d_bandmask is not NULL, bit j of
@@ -177,6 +185,12 @@ int pmh_jaccard_estimate(pmh_ctx ctx, const uint32_t* d_qhashes, const uint32_t*
 int pmh_topm(pmh_ctx ctx, const int64_t* d_row_ptr, const int32_t* d_cand,
              const uint16_t* d_count, const float* d_score, int64_t Q, int32_t m,
              int32_t* d_out_ids, int32_t* d_out_n, void* stream);
+
+/* Fixed-width lists (d_ids [Q][m] as written by pmh_topm, d_n [Q] kept per
+ * row) to compact CSR: d_row_ptr int64 [Q + 1], d_cand int32 (capacity Q*m).
+ * Used to rerank a count-ordered shortlist with the learned scores. */
+int pmh_lists_to_csr(pmh_ctx ctx, const int32_t* d_ids, const int32_t* d_n, int64_t Q, int32_t m,
+                     int64_t* d_row_ptr, int32_t* d_cand, void* stream);
 
 /* A8 -- exact refinement (Sec. 5.2 refinement phase): for every query q and
  * each of its d_n[q] listed ids (d_ids [Q][m]), the exact Jaccard

@@ -59,6 +59,7 @@ _SIGS = {
     "pmh_lsh_build": (ctypes.c_int, [_P, _P, _i64, ctypes.POINTER(Params), ctypes.POINTER(_P), _P]),
     "pmh_index_destroy": (ctypes.c_int, [_P]),
     "pmh_lsh_query": (ctypes.c_int, [_P, _P, _P, _i64, _P, _P, _i64, ctypes.POINTER(_i64), _P]),
+    "pmh_lsh_query_fill": (ctypes.c_int, [_P, _P, _P, _i64, _P, _P, _i64, _P]),
     "pmh_jaccard_estimate": (ctypes.c_int, [_P, _P, _P, _P, _P, _i64, ctypes.POINTER(Params), _P,
                                             _P, _P]),
     "pmh_topm": (ctypes.c_int, [_P, _P, _P, _P, _P, _i64, _i32, _P, _P, _P]),
@@ -79,6 +80,7 @@ _SIGS = {
     "pmh_qgraph_outputs": (ctypes.c_int, [_P] + [ctypes.POINTER(_P)] * 6),
     "pmh_qgraph_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), _P]),
     "pmh_qgraph_destroy": (ctypes.c_int, [_P]),
+    "pmh_lists_to_csr": (ctypes.c_int, [_P, _P, _P, _i64, _i32, _P, _P, _P]),
     "pmh_bbox_join": (ctypes.c_int, [_P, _P, _P, _P, _P, _i64, ctypes.POINTER(_i64), _P]),
     "pmh_rerank_create": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "pmh_rerank_destroy": (ctypes.c_int, [_P]),
@@ -305,9 +307,10 @@ def lsh_query(ctx: Context, index: Index, qhashes: torch.Tensor, capacity: int |
     rc = lib.pmh_lsh_query(ctx.handle, index.handle, _ptr(qhashes), Q, _ptr(row_ptr), _ptr(cand),
                            cap, ctypes.byref(total), _stream(stream))
     if rc == PMH_ERR_CAPACITY and capacity is None:
+        # the count pass already wrote row_ptr: only the fill pass remains
         cand = torch.empty(max(total.value, 1), dtype=torch.int32, device=dev)
-        rc = lib.pmh_lsh_query(ctx.handle, index.handle, _ptr(qhashes), Q, _ptr(row_ptr),
-                               _ptr(cand), total.value, ctypes.byref(total), _stream(stream))
+        rc = lib.pmh_lsh_query_fill(ctx.handle, index.handle, _ptr(qhashes), Q, _ptr(row_ptr),
+                                    _ptr(cand), total.value, _stream(stream))
     _check(rc)
     return row_ptr, cand[:total.value]
 
@@ -334,6 +337,16 @@ def topm(ctx: Context, row_ptr, cand, count, m: int, score=None, stream=None):
     _check(load().pmh_topm(ctx.handle, _ptr(row_ptr), _ptr(cand), _ptr(count), _ptr(score), Q, m,
                            _ptr(ids), _ptr(nn), _stream(stream)))
     return ids[:Q], nn[:Q]
+
+
+def lists_to_csr(ctx: Context, ids, nn, stream=None):
+    """Fixed-width top-m lists to compact CSR (row_ptr int64 [Q+1], cand int32)."""
+    Q, m = ids.shape
+    row_ptr = torch.empty(Q + 1, dtype=torch.int64, device=ids.device)
+    cand = torch.empty(max(Q * m, 1), dtype=torch.int32, device=ids.device)
+    _check(load().pmh_lists_to_csr(ctx.handle, _ptr(ids), _ptr(nn), Q, m, _ptr(row_ptr), _ptr(cand),
+                                   _stream(stream)))
+    return row_ptr, cand
 
 
 def refine_topk(ctx: Context, queries: Polys, db: Polys, ids, nn, k: int, stream=None):

@@ -186,6 +186,19 @@ int pmh_launch_prep(int sm_count, const int2* xy, const int64_t* off, int64_t n_
     return PMH_OK;
 }
 
+// per-polygon reranker inputs: log2(area) / 32 and log2(vertex count) / 16
+__global__ void poly_feat_kernel(const int64_t* __restrict__ area2, const int64_t* __restrict__ off,
+                                 int64_t n, float2* __restrict__ out)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const long long a2 = area2[p];
+        const double a = 0.5 * (double)(a2 < 0 ? -a2 : a2);
+        out[p] = make_float2(log2f((float)(a > 1.0 ? a : 1.0)) / 32.f,
+                             log2f((float)(off[p + 1] - off[p])) / 16.f);
+    }
+}
+
 static int upload_common(pmh_ctx ctx, const int32_t* xy, const int64_t* offsets, int64_t n_polys,
                          int64_t n_vertices, bool host, pmh_polys* out, void* stream)
 {
@@ -238,6 +251,17 @@ static int upload_common(pmh_ctx ctx, const int32_t* xy, const int64_t* offsets,
     if (st[0] & 2) return fail(pmh_set_error(PMH_ERR_RANGE, "a polygon has fewer than 3 vertices"));
     if (st[0] & 4) return fail(pmh_set_error(PMH_ERR_RANGE, "a coordinate exceeds |2^20|"));
     P->max_n = st[1];
+    if (cudaMalloc(&P->feat, sizeof(float2) * (size_t)(n_polys > 0 ? n_polys : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(pmh_set_error(PMH_ERR_NOMEM, "feature allocation failed"));
+    }
+    if (n_polys > 0) {
+        int blocks = (int)std::min<int64_t>((n_polys + 255) / 256, (int64_t)ctx->sm_count * 32);
+        poly_feat_kernel<<<blocks, 256, 0, s>>>(P->area2, P->offsets, n_polys, P->feat);
+        g_pmh_launches.fetch_add(1);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return fail(pmh_set_error(PMH_ERR_CUDA, "feature kernel: %s", cudaGetErrorString(e)));
+    }
     int rc = pmh_build_slabs(P, s);
     if (rc == PMH_OK) rc = pmh_build_cost_order(P, s);
     if (rc != PMH_OK) return fail(rc);
@@ -284,7 +308,7 @@ extern "C" int pmh_polys_destroy(pmh_polys p)
     if (!p) return PMH_OK;
     cudaSetDevice(p->device);
     if (p->xy || p->offsets || p->bbox || p->area2) cudaDeviceSynchronize();
-    void* bufs[] = {p->xy, p->offsets, p->bbox, p->area2, p->slab_info, p->slab_ptr,
+    void* bufs[] = {p->xy, p->offsets, p->bbox, p->area2, p->feat, p->slab_info, p->slab_ptr,
                     p->slab_edges, p->order};
     for (void* b : bufs)
         if (b) cudaFree(b);

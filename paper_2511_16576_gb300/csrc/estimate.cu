@@ -1,15 +1,18 @@
 // estimate.cu -- steps A5 (agreement estimate) and A6 (top-m selection).
 //
 // A5 follows Theorem 1: Pr[h_k(q) = h_k(p)] = J(q, p), so the fraction of
-// agreeing positions estimates J.  One warp handles one (query, candidate)
-// pair: the K hashes of both rows are read as 16-byte vectors (coalesced, 512
-// bytes per row at K = 128), equality bits are gathered with ballots, the
-// count is a warp reduction and the per-band full-match bits come from the
-// same ballots.
+// agreeing positions estimates J.  One block handles one query row: the
+// query's hashes sit in shared memory, each warp takes one candidate at a
+// time and reads its K hashes as 16-byte vectors (512 bytes per row at
+// K = 128); equality bits are gathered with shuffles, the count is a warp
+// reduction, and the band-match bits and the reranker's features (A7) come
+// from the same bits.
 //
 // A6 sorts each candidate row by a 64-bit key in shared memory (bitonic),
 // keeping the first m: key = (K - count) << 32 | id for the plain form,
 // or (~orderable(score)) << 32 | id for a learned score.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "pmh_internal.cuh"
@@ -17,77 +20,98 @@
 namespace {
 
 constexpr int kMaxK = 4096;
+constexpr int kAgreeWarps = 4;
 
-__global__ void agree_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ ph,
-                             const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cand,
-                             int64_t Q, int64_t cap, int K, int bands, int rows, uint32_t T,
-                             uint16_t* __restrict__ count, uint32_t* __restrict__ bandmask,
-                             const int* __restrict__ d_flags)
+// One block per query (its hashes staged in shared memory once), warps stride
+// over the query's candidate row.  Per pair: equality bits of the K hashes
+// (16-byte loads when K % 4 == 0), the count (warp sum), the full-match bits
+// of the first 32 bands and, optionally, the reranker's feature row.
+__global__ void __launch_bounds__(kAgreeWarps * 32)
+agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ ph,
+                  const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cand, int64_t Q,
+                  int64_t cap, int K, int bands, int rows, uint32_t T, uint16_t* __restrict__ count,
+                  uint32_t* __restrict__ bandmask, __nv_bfloat16* __restrict__ feat,
+                  const float2* __restrict__ qfeat, const float2* __restrict__ pfeat,
+                  const int* __restrict__ d_flags)
 {
-    __shared__ uint32_t eqbits[8][kMaxK / 32];  // per warp: equality bit per hash
+    __shared__ __align__(16) uint32_t qs[kMaxK];
+    __shared__ uint32_t eqbits[kAgreeWarps][kMaxK / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (d_flags && *d_flags) return;  // failed validation or candidate overflow
-    const int64_t E = min(row_ptr[Q], cap);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; e < E; e += nwarps) {
-        // find the query of pair e (binary search over row_ptr)
-        int64_t lo = 0, hi = Q;
-        while (hi - lo > 1) {
-            int64_t mid = (lo + hi) >> 1;
-            if (row_ptr[mid] <= e) lo = mid;
-            else hi = mid;
-        }
-        const uint32_t* a = qh + lo * K;
-        const uint32_t* b = ph + (int64_t)cand[e] * K;
-        int c = 0;
-        if ((K & 3) == 0) {
-            const uint4* a4 = reinterpret_cast<const uint4*>(a);
-            const uint4* b4 = reinterpret_cast<const uint4*>(b);
-            for (int base = 0; base < K / 4; base += 32) {
-                int i = base + lane;
-                unsigned bits = 0;
-                if (i < K / 4) {
-                    uint4 x = __ldg(a4 + i), y = __ldg(b4 + i);
-                    bits = (unsigned)((x.x == y.x) & (x.x != T)) |
-                           ((unsigned)((x.y == y.y) & (x.y != T)) << 1) |
-                           ((unsigned)((x.z == y.z) & (x.z != T)) << 2) |
-                           ((unsigned)((x.w == y.w) & (x.w != T)) << 3);
+    for (int64_t q = blockIdx.x; q < Q; q += gridDim.x) {
+        const int64_t b = min(row_ptr[q], cap), e = min(row_ptr[q + 1], cap);
+        if (b >= e) continue;
+        __syncthreads();
+        for (int i = threadIdx.x; i < K; i += blockDim.x) qs[i] = qh[q * K + i];
+        __syncthreads();
+        for (int64_t x = b + wid; x < e; x += kAgreeWarps) {
+            const int64_t p = cand[x];
+            const uint32_t* bp = ph + p * K;
+            int c = 0;
+            if ((K & 3) == 0) {
+                const uint4* a4 = reinterpret_cast<const uint4*>(qs);
+                const uint4* b4 = reinterpret_cast<const uint4*>(bp);
+                for (int base = 0; base < K / 4; base += 32) {
+                    const int i = base + lane;
+                    unsigned bits = 0;
+                    if (i < K / 4) {
+                        const uint4 u = a4[i], v = __ldg(b4 + i);
+                        bits = (unsigned)((u.x == v.x) & (u.x != T)) |
+                               ((unsigned)((u.y == v.y) & (u.y != T)) << 1) |
+                               ((unsigned)((u.z == v.z) & (u.z != T)) << 2) |
+                               ((unsigned)((u.w == v.w) & (u.w != T)) << 3);
+                    }
+                    c += __popc(bits);
+                    // hash 4i+t is bit (4i+t) % 32 of word i / 8: OR eight lanes' nibbles
+                    unsigned w0 = bits << ((lane & 7) * 4);
+                    w0 |= __shfl_xor_sync(0xffffffffu, w0, 1);
+                    w0 |= __shfl_xor_sync(0xffffffffu, w0, 2);
+                    w0 |= __shfl_xor_sync(0xffffffffu, w0, 4);
+                    if ((lane & 7) == 0 && i < K / 4) eqbits[wid][i >> 3] = w0;
                 }
-                c += __popc(bits);
-                // hash 4*i + t is bit (4*i + t) % 32 of word (4*i + t) / 32 = i / 8 of the
-                // equality mask: OR the nibbles of each group of eight lanes together
-                unsigned w0 = bits << ((lane & 7) * 4);
-                w0 |= __shfl_xor_sync(0xffffffffu, w0, 1);
-                w0 |= __shfl_xor_sync(0xffffffffu, w0, 2);
-                w0 |= __shfl_xor_sync(0xffffffffu, w0, 4);
-                if ((lane & 7) == 0 && i < K / 4) eqbits[wid][i >> 3] = w0;
+            } else {
+                for (int base = 0; base < K; base += 32) {
+                    const int i = base + lane;
+                    const bool eq = i < K && qs[i] == bp[i] && qs[i] != T;
+                    const unsigned bal = __ballot_sync(0xffffffffu, eq);
+                    c += eq;
+                    if (lane == 0) eqbits[wid][base / 32] = bal;
+                }
             }
-        } else {
-            for (int base = 0; base < K; base += 32) {
-                int i = base + lane;
-                bool eq = i < K && a[i] == b[i] && a[i] != T;
-                unsigned bal = __ballot_sync(0xffffffffu, eq);
-                c += eq;
-                if (lane == 0) eqbits[wid][base / 32] = bal;
+            __syncwarp();
+            c = __reduce_add_sync(0xffffffffu, c);
+            if (count && lane == 0) count[x] = (uint16_t)c;
+            if (bandmask) {
+                bool all = lane < bands;
+                for (int t = 0; t < rows && all; ++t) {
+                    const int k = lane * rows + t;
+                    all = (eqbits[wid][k >> 5] >> (k & 31)) & 1u;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, all);
+                if (lane == 0) bandmask[x] = m;
             }
-        }
-        __syncwarp();
-        c = __reduce_add_sync(0xffffffffu, c);
-        if (lane == 0) count[e] = (uint16_t)c;
-        if (bandmask) {
-            unsigned ok = 0;
-            for (int j = lane; j < bands && j < 32; j += 32) {
+            if (feat) {
+                // group j = hashes j*g .. j*g+g-1 (g = K / 32) all equal
+                const int g = K / 32;
                 bool all = true;
-                for (int t = 0; t < rows; ++t) {
-                    int k = j * rows + t;
-                    all &= (eqbits[wid][k >> 5] >> (k & 31)) & 1u;
+                for (int t = 0; t < g && all; ++t) {
+                    const int k = lane * g + t;
+                    all = (eqbits[wid][k >> 5] >> (k & 31)) & 1u;
                 }
-                ok = all;
+                __nv_bfloat16* f = feat + x * 48;
+                f[lane] = __float2bfloat16_rn(all ? 1.f : 0.f);
+                if (lane < 16) {
+                    float v = 0.f;
+                    if (lane == 0) v = (float)c / (float)K;
+                    if (lane == 1) v = qfeat[q].x;
+                    if (lane == 2) v = pfeat[p].x;
+                    if (lane == 3) v = qfeat[q].y;
+                    if (lane == 4) v = pfeat[p].y;
+                    f[32 + lane] = __float2bfloat16_rn(v);
+                }
             }
-            unsigned m = __ballot_sync(0xffffffffu, ok);
-            if (lane == 0) bandmask[e] = m;
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
@@ -155,17 +179,70 @@ topm_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ can
     if (threadIdx.x == 0) out_n[q] = kept;
 }
 
+// fixed-width lists (ids [Q][m], -1 padded, counts n[Q]) to compact CSR
+__global__ void list_counts_kernel(const int32_t* __restrict__ n, int64_t Q, int64_t* __restrict__ c)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < Q;
+         q += (int64_t)gridDim.x * blockDim.x)
+        c[q] = n[q];
+}
+
+__global__ void list_copy_kernel(const int32_t* __restrict__ ids, const int32_t* __restrict__ n,
+                                 int64_t Q, int m, const int64_t* __restrict__ row_ptr,
+                                 int32_t* __restrict__ cand)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < Q * m;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = t / m;
+        const int i = (int)(t - q * m);
+        if (i < n[q]) cand[row_ptr[q] + i] = ids[t];
+    }
+}
+
 }  // namespace
+
+extern "C" int pmh_lists_to_csr(pmh_ctx ctx, const int32_t* d_ids, const int32_t* d_n, int64_t Q,
+                                int32_t m, int64_t* d_row_ptr, int32_t* d_cand, void* stream)
+{
+    PMH_TRY(pmh_check_device(ctx));
+    if (Q < 0 || m < 1 || !d_row_ptr || (Q > 0 && (!d_ids || !d_n || !d_cand)))
+        return pmh_set_error(PMH_ERR_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (Q == 0) {
+        PMH_CUDA_TRY(cudaMemsetAsync(d_row_ptr, 0, sizeof(int64_t), s));
+        return PMH_OK;
+    }
+    int64_t* counts = nullptr;
+    PMH_TRY(pmh_scratch(ctx, SCR_QUERY, sizeof(int64_t) * (size_t)Q, (void**)&counts));
+    const int blocks = (int)std::min<int64_t>((Q * m + 255) / 256, (int64_t)ctx->sm_count * 32);
+    list_counts_kernel<<<blocks, 256, 0, s>>>(d_n, Q, counts);
+    PMH_LAUNCHED("list_counts_kernel");
+    PMH_TRY(pmh_exclusive_scan_i64(ctx, counts, d_row_ptr, Q, s));
+    list_copy_kernel<<<blocks, 256, 0, s>>>(d_ids, d_n, Q, m, d_row_ptr, d_cand);
+    PMH_LAUNCHED("list_copy_kernel");
+    return PMH_OK;
+}
 
 int pmh_launch_agree(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph, const int64_t* row_ptr,
                      const int32_t* cand, int64_t Q, int64_t cap, const pmh_params* P,
                      uint16_t* count, uint32_t* bandmask, const int* d_flags, cudaStream_t s)
 {
+    return pmh_launch_agree_features(ctx, qh, ph, row_ptr, cand, Q, cap, P, count, bandmask, nullptr,
+                                     nullptr, nullptr, d_flags, s);
+}
+
+int pmh_launch_agree_features(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph,
+                              const int64_t* row_ptr, const int32_t* cand, int64_t Q, int64_t cap,
+                              const pmh_params* P, uint16_t* count, uint32_t* bandmask,
+                              uint16_t* feat, const float2* qfeat, const float2* pfeat,
+                              const int* d_flags, cudaStream_t s)
+{
     if (Q <= 0) return PMH_OK;
-    int blocks = ctx->sm_count * 8;
-    agree_kernel<<<blocks, 256, 0, s>>>(qh, ph, row_ptr, cand, Q, cap, (int)P->K, (int)P->bands,
-                                        (int)P->rows, P->T, count, bandmask, d_flags);
-    PMH_LAUNCHED("agree_kernel");
+    const int blocks = (int)std::min<int64_t>(Q, (int64_t)ctx->sm_count * 16);
+    agree_rows_kernel<<<blocks, kAgreeWarps * 32, 0, s>>>(
+        qh, ph, row_ptr, cand, Q, cap, (int)P->K, (int)P->bands, (int)P->rows, P->T, count, bandmask,
+        reinterpret_cast<__nv_bfloat16*>(feat), qfeat, pfeat, d_flags);
+    PMH_LAUNCHED("agree_rows_kernel");
     return PMH_OK;
 }
 

@@ -63,6 +63,19 @@ __global__ void fill_entries_kernel(const uint64_t* __restrict__ keys, int64_t n
     }
 }
 
+// full 64-bit key of every sorted entry (band from the composite's top bits)
+__global__ void gather_keys_kernel(const uint32_t* __restrict__ comp, const int32_t* __restrict__ ids,
+                                   const uint64_t* __restrict__ keys, int64_t m, int bands,
+                                   int band_bits, uint64_t* __restrict__ out)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c = comp[e];
+        out[e] = c == 0xFFFFFFFFu ? PMH_INVALID_KEY
+                                  : keys[(int64_t)ids[e] * bands + (int)(c >> (32 - band_bits))];
+    }
+}
+
 constexpr int kMaxBandsPerLane = 4;  // bands <= 128
 constexpr int32_t kNone = 0x7FFFFFFF;
 
@@ -82,20 +95,21 @@ __device__ __forceinline__ bool tuple_equal(const uint32_t* __restrict__ a,
     return true;
 }
 
-// advance c to the next entry of its band that is an exact bucket member
+// advance c to the next entry of its band that is an exact bucket member: the
+// walk reads the sorted arrays sequentially; only a key match gathers the tuple
 __device__ __forceinline__ void advance(BandCursor& c, const uint32_t* __restrict__ comp,
                                         const int32_t* __restrict__ ids,
-                                        const uint64_t* __restrict__ keys,
+                                        const uint64_t* __restrict__ skeys,
                                         const uint32_t* __restrict__ dbh,
                                         const uint32_t* __restrict__ qh, int64_t m, int K,
                                         int bands, int rows)
 {
     c.head = kNone;
     while (c.cur < m && comp[c.cur] == c.comp) {
-        int32_t p = ids[c.cur];
-        ++c.cur;
-        if (keys[(int64_t)p * bands + c.j] == c.key &&
-            tuple_equal(qh, dbh + (int64_t)p * K, c.j, rows)) {
+        const int64_t e = c.cur++;
+        if (skeys[e] != c.key) continue;
+        const int32_t p = ids[e];
+        if (tuple_equal(qh, dbh + (int64_t)p * K, c.j, rows)) {
             c.head = p;
             return;
         }
@@ -110,7 +124,7 @@ template <bool kWrite>
 __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands,
                              int rows, uint32_t T, uint64_t lsh_seed, int band_bits,
                              const uint32_t* __restrict__ comp, const int32_t* __restrict__ ids,
-                             const uint64_t* __restrict__ keys, const uint32_t* __restrict__ dbh,
+                             const uint64_t* __restrict__ skeys, const uint32_t* __restrict__ dbh,
                              int64_t m, int64_t* __restrict__ counts,
                              const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand,
                              int64_t cap, const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
@@ -150,7 +164,7 @@ __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, in
             else hi = mid;
         }
         cur[t].cur = lo;
-        advance(cur[t], comp, ids, keys, dbh, qh, m, K, bands, rows);
+        advance(cur[t], comp, ids, skeys, dbh, qh, m, K, bands, rows);
     }
     int64_t out = kWrite ? row_ptr[q] : 0;
     int64_t cnt = 0;
@@ -164,9 +178,158 @@ __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, in
         ++cnt;
 #pragma unroll
         for (int t = 0; t < kMaxBandsPerLane; ++t)
-            if (cur[t].head == best) advance(cur[t], comp, ids, keys, dbh, qh, m, K, bands, rows);
+            if (cur[t].head == best) advance(cur[t], comp, ids, skeys, dbh, qh, m, K, bands, rows);
     }
     if (!kWrite && lane == 0) counts[q] = cnt;
+}
+
+// Many-band join: one block per query.  Each warp takes one band at a time;
+// its lanes stride over the band's bucket (coalesced reads of the sorted
+// entries) and insert exact matches into a shared-memory open-addressing set,
+// which drops the duplicates (a candidate found in several bands).  The set is
+// then bitonic-sorted in place (empty slots sort last), which yields the same
+// ascending, duplicate-free row as the warp merge.  A row with more distinct
+// candidates than the set can hold falls back to the warp merge (warp 0).
+constexpr int kJoinThreads = 256;
+constexpr int kJoinTable = 16384;            // shared set slots (64 KiB)
+constexpr int kJoinMaxUnique = kJoinTable / 2;
+
+__device__ int64_t merge_row(const uint32_t* __restrict__ qh, int K, int bands, int rows, uint32_t T,
+                             uint64_t lsh_seed, int band_bits, const uint32_t* __restrict__ comp,
+                             const int32_t* __restrict__ ids, const uint64_t* __restrict__ skeys,
+                             const uint32_t* __restrict__ dbh, int64_t m, int32_t* __restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    BandCursor cur[kMaxBandsPerLane];
+#pragma unroll
+    for (int t = 0; t < kMaxBandsPerLane; ++t) {
+        int j = lane + 32 * t;
+        cur[t].head = kNone;
+        cur[t].j = j;
+        if (j >= bands) continue;
+        uint64_t key = band_key(qh, j, rows, T, lsh_seed);
+        if (key == PMH_INVALID_KEY) continue;
+        cur[t].key = key;
+        cur[t].comp = composite(key, j, band_bits);
+        int64_t lo = 0, hi = m;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (comp[mid] < cur[t].comp) lo = mid + 1;
+            else hi = mid;
+        }
+        cur[t].cur = lo;
+        advance(cur[t], comp, ids, skeys, dbh, qh, m, K, bands, rows);
+    }
+    int64_t cnt = 0;
+    for (;;) {
+        int32_t mine = kNone;
+#pragma unroll
+        for (int t = 0; t < kMaxBandsPerLane; ++t) mine = min(mine, cur[t].head);
+        int32_t best = __reduce_min_sync(0xffffffffu, mine);
+        if (best == kNone) break;
+        if (out && lane == 0) out[cnt] = best;
+        ++cnt;
+#pragma unroll
+        for (int t = 0; t < kMaxBandsPerLane; ++t)
+            if (cur[t].head == best) advance(cur[t], comp, ids, skeys, dbh, qh, m, K, bands, rows);
+    }
+    return cnt;
+}
+
+__device__ __forceinline__ uint32_t slot_hash(int32_t p)
+{
+    return ((uint32_t)p * 0x9E3779B1u) >> (32 - 14);  // 14 bits = log2(kJoinTable)
+}
+
+template <bool kWrite>
+__global__ void __launch_bounds__(kJoinThreads)
+join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, int rows, uint32_t T,
+            uint64_t lsh_seed, int band_bits, const uint32_t* __restrict__ comp,
+            const int32_t* __restrict__ ids, const uint64_t* __restrict__ skeys,
+            const uint32_t* __restrict__ dbh, int64_t m, int64_t* __restrict__ counts,
+            const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand, int64_t cap,
+            const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
+{
+    extern __shared__ int32_t table[];  // kJoinTable slots
+    __shared__ int n_unique;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int64_t q = blockIdx.x; q < Q; q += gridDim.x) {
+        const bool skip = (d_n && q >= *d_n) || (d_flags && (*d_flags & 7));
+        if (skip) {
+            if (!kWrite && threadIdx.x == 0) counts[q] = 0;
+            continue;
+        }
+        if (kWrite && row_ptr[Q] > cap) {
+            if (threadIdx.x == 0 && d_flags) atomicOr(d_flags, 8);
+            return;
+        }
+        const uint32_t* qh = qhashes + q * K;
+        __syncthreads();
+        for (int i = threadIdx.x; i < kJoinTable; i += blockDim.x) table[i] = kNone;
+        if (threadIdx.x == 0) n_unique = 0;
+        __syncthreads();
+        for (int j = wid; j < bands; j += nw) {
+            const uint64_t key = band_key(qh, j, rows, T, lsh_seed);
+            if (key == PMH_INVALID_KEY) continue;
+            const uint32_t c = composite(key, j, band_bits);
+            int64_t lo = 0, hi = m;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (comp[mid] < c) lo = mid + 1;
+                else hi = mid;
+            }
+            for (int64_t base = lo;; base += 32) {
+                const int64_t e = base + lane;
+                const bool in = e < m && comp[e] == c;
+                if (!__any_sync(0xffffffffu, in)) break;
+                if (!in || skeys[e] != key) continue;
+                const int32_t p = ids[e];
+                if (!tuple_equal(qh, dbh + (int64_t)p * K, j, rows)) continue;
+                uint32_t h = slot_hash(p);
+                for (int probe = 0; probe < kJoinTable; ++probe, h = (h + 1) & (kJoinTable - 1)) {
+                    const int32_t old = atomicCAS(&table[h], kNone, p);
+                    if (old == kNone) {
+                        atomicAdd(&n_unique, 1);
+                        break;
+                    }
+                    if (old == p) break;
+                    if (n_unique > kJoinMaxUnique) break;  // the row falls back anyway
+                }
+            }
+        }
+        __syncthreads();
+        const int nu = n_unique;
+        if (nu > kJoinMaxUnique) {  // rare: merge the row with warp 0
+            if (wid == 0) {
+                int64_t cnt = merge_row(qh, K, bands, rows, T, lsh_seed, band_bits, comp, ids, skeys,
+                                        dbh, m, kWrite ? cand + row_ptr[q] : nullptr);
+                if (!kWrite && lane == 0) counts[q] = cnt;
+            }
+            continue;
+        }
+        if (!kWrite) {
+            if (threadIdx.x == 0) counts[q] = nu;
+            continue;
+        }
+        // sort the whole set; the nu ids come first, ascending
+        for (int k = 2; k <= kJoinTable; k <<= 1)
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int i = threadIdx.x; i < kJoinTable; i += blockDim.x) {
+                    const int l = i ^ jj;
+                    if (l > i) {
+                        const int32_t a = table[i], b = table[l];
+                        if ((a > b) == ((i & k) == 0)) {
+                            table[i] = b;
+                            table[l] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        int32_t* out = cand + row_ptr[q];
+        for (int i = threadIdx.x; i < nu; i += blockDim.x) out[i] = table[i];
+    }
 }
 
 }  // namespace
@@ -210,7 +373,8 @@ extern "C" int pmh_lsh_build(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
     if (cudaMalloc(&X->hashes, sizeof(uint32_t) * nn * params->K) != cudaSuccess ||
         cudaMalloc(&X->keys, sizeof(uint64_t) * nn * params->bands) != cudaSuccess ||
         cudaMalloc(&X->sorted_comp, sizeof(uint32_t) * ne) != cudaSuccess ||
-        cudaMalloc(&X->sorted_id, sizeof(int32_t) * ne) != cudaSuccess) {
+        cudaMalloc(&X->sorted_id, sizeof(int32_t) * ne) != cudaSuccess ||
+        cudaMalloc(&X->sorted_key, sizeof(uint64_t) * ne) != cudaSuccess) {
         cudaGetLastError();
         pmh_index_destroy(X);
         return pmh_set_error(PMH_ERR_NOMEM, "index allocation failed (n=%lld)", (long long)n);
@@ -230,6 +394,14 @@ extern "C" int pmh_lsh_build(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
             if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "fill: %s", cudaGetErrorString(e));
         }
         if (rc == PMH_OK) rc = pmh_radix_sort_u32(ctx, X->sorted_comp, X->sorted_id, entries, 32, s);
+        if (rc == PMH_OK) {
+            int blocks = (int)std::min<int64_t>((entries + 255) / 256, (int64_t)ctx->sm_count * 32);
+            gather_keys_kernel<<<blocks, 256, 0, s>>>(X->sorted_comp, X->sorted_id, X->keys, entries,
+                                                       (int)params->bands, bb, X->sorted_key);
+            g_pmh_launches.fetch_add(1);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "gather: %s", cudaGetErrorString(e));
+        }
     }
     if (rc != PMH_OK) {
         pmh_index_destroy(X);
@@ -248,6 +420,7 @@ extern "C" int pmh_index_destroy(pmh_index X)
     if (X->keys) cudaFree(X->keys);
     if (X->sorted_comp) cudaFree(X->sorted_comp);
     if (X->sorted_id) cudaFree(X->sorted_id);
+    if (X->sorted_key) cudaFree(X->sorted_key);
     delete X;
     return PMH_OK;
 }
@@ -259,18 +432,40 @@ int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* 
     if (Q <= 0) return PMH_OK;
     const pmh_params& P = X->params;
     const int64_t m = X->n * P.bands;
+    if (P.bands > 16) {  // many short bands: parallel walk + sort
+        const unsigned blocks = (unsigned)std::min<int64_t>(Q, (int64_t)X->ctx->sm_count * 3);
+        const size_t smem = sizeof(int32_t) * kJoinTable;
+        PMH_CUDA_TRY(cudaFuncSetAttribute(join_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        PMH_CUDA_TRY(cudaFuncSetAttribute(join_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+        if (write) {
+            join_kernel<true><<<blocks, kJoinThreads, smem, s>>>(
+                qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T, P.lsh_seed, X->band_bits,
+                X->sorted_comp, X->sorted_id, X->sorted_key, X->hashes, m, nullptr, row_ptr, cand, cap,
+                d_n, d_flags);
+            PMH_LAUNCHED("join_kernel<fill>");
+        } else {
+            join_kernel<false><<<blocks, kJoinThreads, smem, s>>>(
+                qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T, P.lsh_seed, X->band_bits,
+                X->sorted_comp, X->sorted_id, X->sorted_key, X->hashes, m, counts, nullptr, nullptr, 0,
+                d_n, d_flags);
+            PMH_LAUNCHED("join_kernel<count>");
+        }
+        return PMH_OK;
+    }
     const int wpb = 8;
     unsigned blocks = (unsigned)((Q + wpb - 1) / wpb);
     if (write) {
         query_kernel<true><<<blocks, wpb * 32, 0, s>>>(
             qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T, P.lsh_seed, X->band_bits,
-            X->sorted_comp, X->sorted_id, X->keys, X->hashes, m, nullptr, row_ptr, cand, cap, d_n,
+            X->sorted_comp, X->sorted_id, X->sorted_key, X->hashes, m, nullptr, row_ptr, cand, cap, d_n,
             d_flags);
         PMH_LAUNCHED("query_kernel<fill>");
     } else {
         query_kernel<false><<<blocks, wpb * 32, 0, s>>>(
             qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T, P.lsh_seed, X->band_bits,
-            X->sorted_comp, X->sorted_id, X->keys, X->hashes, m, counts, nullptr, nullptr, 0, d_n,
+            X->sorted_comp, X->sorted_id, X->sorted_key, X->hashes, m, counts, nullptr, nullptr, 0, d_n,
             d_flags);
         PMH_LAUNCHED("query_kernel<count>");
     }
@@ -306,4 +501,16 @@ extern "C" int pmh_lsh_query(pmh_ctx ctx, pmh_index X, const uint32_t* d_qhashes
     if (!d_cand) return pmh_set_error(PMH_ERR_ARG, "null candidate buffer");
     return pmh_launch_query(X, d_qhashes, Q, nullptr, nullptr, d_row_ptr, d_cand, cand_capacity,
                             nullptr, true, s);
+}
+
+extern "C" int pmh_lsh_query_fill(pmh_ctx ctx, pmh_index X, const uint32_t* d_qhashes, int64_t Q,
+                                  const int64_t* d_row_ptr, int32_t* d_cand, int64_t cand_capacity,
+                                  void* stream)
+{
+    PMH_TRY(pmh_check_device(ctx));
+    if (!X || !d_row_ptr || Q < 0 || (Q > 0 && (!d_qhashes || !d_cand)) || cand_capacity < 0)
+        return pmh_set_error(PMH_ERR_ARG, "bad arguments");
+    if (Q == 0) return PMH_OK;
+    return pmh_launch_query(X, d_qhashes, Q, nullptr, nullptr, d_row_ptr, d_cand, cand_capacity,
+                            nullptr, true, (cudaStream_t)stream);
 }

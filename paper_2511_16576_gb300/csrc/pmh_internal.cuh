@@ -84,6 +84,7 @@ struct pmh_polys_s {
     int4* bbox = nullptr;      // x0, y0, x1, y1 half-open, clipped to the domain
     int64_t* area2 = nullptr;  // twice the signed area
     int32_t max_n = 0;         // largest vertex count
+    float2* feat = nullptr;         // [n] log2(area) / 32, log2(n) / 16 (reranker inputs)
     SlabInfo* slab_info = nullptr;  // [n]
     int32_t* slab_ptr = nullptr;
     int32_t* slab_edges = nullptr;
@@ -103,6 +104,7 @@ struct pmh_index_s {
     uint64_t* keys = nullptr;       // [n][bands]
     uint32_t* sorted_comp = nullptr;  // [n * bands] composite (band, key) sort keys
     int32_t* sorted_id = nullptr;     // [n * bands]
+    uint64_t* sorted_key = nullptr;   // [n * bands] full band key of each sorted entry
 };
 
 // grow-only scratch buffer of the context
@@ -165,6 +167,11 @@ int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* 
 int pmh_launch_agree(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph, const int64_t* row_ptr,
                      const int32_t* cand, int64_t Q, int64_t cap, const pmh_params* P,
                      uint16_t* count, uint32_t* bandmask, const int* d_flags, cudaStream_t s);
+int pmh_launch_agree_features(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph,
+                              const int64_t* row_ptr, const int32_t* cand, int64_t Q, int64_t cap,
+                              const pmh_params* P, uint16_t* count, uint32_t* bandmask,
+                              uint16_t* feat, const float2* qfeat, const float2* pfeat,
+                              const int* d_flags, cudaStream_t s);
 int pmh_launch_topm(const int64_t* row_ptr, const int32_t* cand, const uint16_t* count,
                     const float* score, int64_t Q, int32_t m, int32_t* out_ids, int32_t* out_n,
                     const int* d_flags, cudaStream_t s);

@@ -5,7 +5,7 @@
 // refinement (A8) touches fewer of them.  Network 37 -> 64 -> 64 -> 1, ReLU,
 // ReLU, sigmoid, mean squared error against the exact Jaccard.
 //
-// Features (bf16, padded to 48 columns):
+// Features (bf16, padded to 48 columns; computed by the agreement kernel, A5):
 //   0..31  group-match bits: bit j = all K/32 hashes of group j agree (and are
 //          not the sentinel) -- the band-match pattern of a 32-band split;
 //   32     agreement fraction c / K (Theorem 1 estimate of J);
@@ -87,57 +87,6 @@ struct MlpSmem {
     float g3[kChunk];
     float gb1[kH], gb2[kH], gw3[kH], gb3, loss;
 };
-
-// features of pair e = (q, cand[e])
-__global__ void features_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ ph,
-                                const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cand,
-                                int64_t Q, int K, uint32_t T, const int64_t* __restrict__ q_area2,
-                                const int64_t* __restrict__ q_off, const int64_t* __restrict__ p_area2,
-                                const int64_t* __restrict__ p_off, __nv_bfloat16* __restrict__ feat)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t E = row_ptr[Q];
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int g = K / 32;  // hashes per group
-    for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < E; e += nwarps) {
-        int64_t lo = 0, hi = Q;
-        while (hi - lo > 1) {
-            int64_t mid = (lo + hi) >> 1;
-            if (row_ptr[mid] <= e) lo = mid;
-            else hi = mid;
-        }
-        const int64_t q = lo;
-        const int64_t p = cand[e];
-        const uint32_t* a = qh + q * K;
-        const uint32_t* b = ph + p * K;
-        // lane j handles group j
-        int agree = 0;
-        bool all = true;
-        for (int i = 0; i < g; ++i) {
-            uint32_t x = a[lane * g + i], y = b[lane * g + i];
-            bool eq = (x == y) & (x != T);
-            agree += eq;
-            all &= eq;
-        }
-        agree = __reduce_add_sync(0xffffffffu, agree);
-        __nv_bfloat16* f = feat + e * kInPad;
-        f[lane] = __float2bfloat16_rn(all ? 1.f : 0.f);
-        if (lane < kInPad - 32) {
-            float v = 0.f;
-            if (lane == 0) v = (float)agree / (float)K;
-            if (lane == 1 || lane == 2) {
-                long long a2 = lane == 1 ? q_area2[q] : p_area2[p];
-                double ar = 0.5 * (double)(a2 < 0 ? -a2 : a2);
-                v = (float)(log2(fmax(ar, 1.0)) / 32.0);
-            }
-            if (lane == 3 || lane == 4) {
-                int64_t n = lane == 3 ? q_off[q + 1] - q_off[q] : p_off[p + 1] - p_off[p];
-                v = (float)(log2((double)n) / 16.0);
-            }
-            f[32 + lane] = __float2bfloat16_rn(v);
-        }
-    }
-}
 
 // load the bf16 weights into shared memory (padding zeroed)
 __device__ void load_weights(MlpSmem& s, const __nv_bfloat16* __restrict__ w1b,
@@ -561,12 +510,9 @@ extern "C" int pmh_rerank_features(pmh_ctx ctx, pmh_polys queries, pmh_polys db,
         (Q > 0 && (!d_qhashes || !d_dbhashes || !d_row_ptr || !d_feat)))
         return pmh_set_error(PMH_ERR_ARG, "bad arguments (K must be a multiple of 32)");
     if (Q == 0) return PMH_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    features_kernel<<<ctx->sm_count * 8, 256, 0, s>>>(
-        d_qhashes, d_dbhashes, d_row_ptr, d_cand, Q, (int)params->K, params->T, queries->area2,
-        queries->offsets, db->area2, db->offsets, reinterpret_cast<__nv_bfloat16*>(d_feat));
-    PMH_LAUNCHED("features_kernel");
-    return PMH_OK;
+    return pmh_launch_agree_features(ctx, d_qhashes, d_dbhashes, d_row_ptr, d_cand, Q, INT64_MAX,
+                                     params, nullptr, nullptr, d_feat, queries->feat, db->feat,
+                                     nullptr, (cudaStream_t)stream);
 }
 
 static int mlp_launch(pmh_rerank r, bool train, const uint16_t* d_feat, const float* d_label,

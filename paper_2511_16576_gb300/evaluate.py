@@ -79,42 +79,61 @@ def recall_at_k(ann_ids: np.ndarray, ann_j: np.ndarray, truth: Truth, k: int = 1
 
 @dataclasses.dataclass
 class Searcher:
-    """The approximate search over one database index."""
+    """The approximate search over one database index.
+
+    Plain form: bucket candidates -> agreement counts -> top-m by count -> exact top-k.
+    Learned form: the top-`shortlist` candidates by count are rescored by the reranker and
+    the top-m by predicted Jaccard are refined."""
     ctx: B.Context
     index: B.Index
     params: B.Params
     dbp: B.Polys
     dbh: torch.Tensor
     reranker: B.Reranker | None = None
+    shortlist: int = 64
 
-    def query(self, qp: B.Polys, m: int, k: int = 10, learned: bool = False, stream=None):
+    def candidates(self, qp: B.Polys, stream=None):
         qh = B.minhash_sign(self.ctx, qp, self.params, stream=stream)
         row_ptr, cand = B.lsh_query(self.ctx, self.index, qh, stream=stream)
         count, _ = B.jaccard_estimate(self.ctx, qh, self.dbh, row_ptr, cand, self.params,
                                       bandmask=False, stream=stream)
-        score = None
+        return qh, row_ptr, cand, count
+
+    def shortlisted(self, qp: B.Polys, stream=None):
+        """(qh, CSR of the count shortlist, its features, total bucket candidates)."""
+        qh, row_ptr, cand, count = self.candidates(qp, stream)
+        ids1, nn1 = B.topm(self.ctx, row_ptr, cand, count, self.shortlist, stream=stream)
+        rp2, c2 = B.lists_to_csr(self.ctx, ids1, nn1, stream=stream)
+        feat = B.rerank_features(self.ctx, qp, self.dbp, qh, self.dbh, rp2, c2, self.params,
+                                 stream=stream)
+        return qh, rp2, c2, feat, int(cand.numel())
+
+    def query(self, qp: B.Polys, m: int, k: int = 10, learned: bool = False, stream=None):
         if learned:
-            feat = B.rerank_features(self.ctx, qp, self.dbp, qh, self.dbh, row_ptr, cand,
-                                     self.params, stream=stream)
+            qh, rp2, c2, feat, ncand = self.shortlisted(qp, stream)
             score = self.reranker.forward(feat, stream=stream)
-        ids, nn = B.topm(self.ctx, row_ptr, cand, count, m, score=score, stream=stream)
-        top_ids, top_j = B.refine_topk(self.ctx, qp, self.dbp, ids, nn, k, stream=stream)
-        return top_ids, top_j, int(cand.numel())
+            ids, nn = B.topm(self.ctx, rp2, c2, None, m, score=score, stream=stream)
+        else:
+            qh, row_ptr, cand, count = self.candidates(qp, stream)
+            ncand = int(cand.numel())
+            ids, nn = B.topm(self.ctx, row_ptr, cand, count, m, stream=stream)
+        top_ids, top_j = B.refine_topk(self.ctx, qp, self.dbp, ids, nn, min(k, m), stream=stream)
+        return top_ids, top_j, ncand
 
 
 def training_pairs(ctx: B.Context, searcher: Searcher, tp: B.Polys):
-    """Features and exact-Jaccard labels of every bucket candidate of the training queries."""
-    qh = B.minhash_sign(ctx, tp, searcher.params)
-    row_ptr, cand = B.lsh_query(ctx, searcher.index, qh)
-    feat = B.rerank_features(ctx, tp, searcher.dbp, qh, searcher.dbh, row_ptr, cand, searcher.params)
-    counts = (row_ptr[1:] - row_ptr[:-1])
-    qid = torch.repeat_interleave(torch.arange(tp.n, device=cand.device, dtype=torch.int32), counts)
-    label = B.pair_jaccard(ctx, tp, searcher.dbp, qid, cand).to(torch.float32)
-    return feat, label
+    """Features and exact-Jaccard labels of the shortlisted candidates of training queries."""
+    qh, rp2, c2, feat, _ = searcher.shortlisted(tp)
+    E = int(rp2[-1].item())
+    c2 = c2[:E]
+    counts = rp2[1:] - rp2[:-1]
+    qid = torch.repeat_interleave(torch.arange(tp.n, device=c2.device, dtype=torch.int32), counts)
+    label = B.pair_jaccard(ctx, tp, searcher.dbp, qid, c2).to(torch.float32)
+    return feat[:E].contiguous(), label
 
 
-def train_reranker(reranker: B.Reranker, feat: torch.Tensor, label: torch.Tensor, epochs: int = 4,
-                   batch: int = 8192, lr: float = 2e-3, seed: int = 0):
+def train_reranker(reranker: B.Reranker, feat: torch.Tensor, label: torch.Tensor, epochs: int = 8,
+                   batch: int = 4096, lr: float = 2e-3, seed: int = 0):
     """Minibatch Adam on the GPU; returns the mean loss of each epoch."""
     g = torch.Generator(device=feat.device)
     g.manual_seed(seed)
@@ -144,7 +163,7 @@ def timed(fn, stream=None):
     return out, e0.elapsed_time(e1) * 1e-3
 
 
-def sweep(searcher: Searcher, qp: B.Polys, truth: Truth, n_eval: int, ms=(10, 16, 32, 64, 128, 256, 512),
+def sweep(searcher: Searcher, qp: B.Polys, truth: Truth, n_eval: int, ms=(8, 10, 12, 16, 24, 32, 64),
           k: int = 10, learned: bool = False):
     """recall@k (first n_eval queries) and queries/s (whole batch) for each m."""
     rows = []
