@@ -185,9 +185,10 @@ def cpu_baseline(w, db, seconds_target=15.0, n_sample=None):
 def search_quality(args, w, B, ctx, db, qs, h, d_xy, d_off, q_xy, q_off, P):
     """queries/s at recall@10 >= 0.9, plain (agreement count) vs learned (reranker) ranking.
 
-    Runs after the timed region.  Candidates come from a one-hash-per-band index
-    (bands = K) of the same signatures, so that every polygon sharing one MinHash value
-    with the query is a candidate; the headline 16x8 banding is reported beside it."""
+    Runs after the timed region.  The same signatures are indexed with K x 1, K/2 x 2 and
+    K/4 x 4 bands (short bands make more polygons candidates) and with the workload's own
+    banding; for each shape the top-m sweep gives recall@10 and queries/s.  The best
+    queries/s reaching recall 0.9 is reported per form."""
     import torch
     from paper_2511_16576_gb300 import evaluate as ev
     from paper_2511_16576_gb300 import synth
@@ -201,16 +202,17 @@ def search_quality(args, w, B, ctx, db, qs, h, d_xy, d_off, q_xy, q_off, P):
     out = {"eval_queries": n_eval, "timed_queries": qs.n, "k": 10, "target_recall": 0.9,
            "bf_pairs_per_query": truth.pairs / n_eval, "bf_seconds_eval_queries": t_bf,
            "forms": {}}
-    P1 = B.make_params(w.K, w.K, w.T, w.seed, w.lsh_seed)
-    for label, params in (("bands_KxA", P1), ("bands_config", P)):
+    tq = synth.perturbed_queries(db, args.train_queries, w.query_seed + 1000)
+    tp = B.poly_upload(ctx, torch.from_numpy(tq.xy).to(dev), torch.from_numpy(tq.offsets).to(dev))
+    shapes = [b for b in (w.K, w.K // 2, w.K // 4) if b >= 1 and w.K % b == 0] + [w.bands]
+    for bands in shapes:
+        params = B.make_params(w.K, bands, w.T, w.seed, w.lsh_seed)
         index = B.lsh_build(ctx, h, params)
         s = ev.Searcher(ctx, index, params, dbp, h)
         key = f"{params.bands}x{params.rows}"
         plain = ev.sweep(s, qp, truth, n_eval, learned=False)
         res = {"bands": key, "plain_curve": plain, "plain": ev.best_at_recall(plain)}
-        if label == "bands_KxA":
-            tq = synth.perturbed_queries(db, args.train_queries, w.query_seed + 1000)
-            tp = B.poly_upload(ctx, torch.from_numpy(tq.xy).to(dev), torch.from_numpy(tq.offsets).to(dev))
+        if bands != w.bands:
             feat, lab = ev.training_pairs(ctx, s, tp)
             s.reranker = B.Reranker(ctx, seed=1)
             (losses, t_train) = ev.timed(lambda: ev.train_reranker(s.reranker, feat, lab))
@@ -219,9 +221,16 @@ def search_quality(args, w, B, ctx, db, qs, h, d_xy, d_off, q_xy, q_off, P):
                         "train_pairs": int(feat.shape[0]), "train_loss_per_epoch": losses,
                         "train_seconds": t_train})
             s.reranker.close()
-            tp.close()
         out["forms"][key] = res
         index.close()
+    tp.close()
+    for form in ("plain", "learned"):
+        best = [(f[form], k) for k, f in out["forms"].items() if f.get(form)]
+        if best:
+            r, k = max(best, key=lambda t: t[0]["qps"])
+            out[form] = {"bands": k, **r}
+        else:
+            out[form] = None
     qep.close()
     qp.close()
     dbp.close()

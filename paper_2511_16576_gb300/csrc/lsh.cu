@@ -187,11 +187,11 @@ __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, in
 // its lanes stride over the band's bucket (coalesced reads of the sorted
 // entries) and insert exact matches into a shared-memory open-addressing set,
 // which drops the duplicates (a candidate found in several bands).  The set is
-// then bitonic-sorted in place (empty slots sort last), which yields the same
-// ascending, duplicate-free row as the warp merge.  A row with more distinct
+// then compacted and bitonic-sorted, which yields the same ascending,
+// duplicate-free row as the warp merge.  A row with more distinct
 // candidates than the set can hold falls back to the warp merge (warp 0).
-constexpr int kJoinThreads = 256;
-constexpr int kJoinTable = 16384;            // shared set slots (64 KiB)
+constexpr int kJoinThreads = 512;
+constexpr int kJoinTable = 32768;            // shared set slots (128 KiB)
 constexpr int kJoinMaxUnique = kJoinTable / 2;
 
 __device__ int64_t merge_row(const uint32_t* __restrict__ qh, int K, int bands, int rows, uint32_t T,
@@ -238,7 +238,7 @@ __device__ int64_t merge_row(const uint32_t* __restrict__ qh, int K, int bands, 
 
 __device__ __forceinline__ uint32_t slot_hash(int32_t p)
 {
-    return ((uint32_t)p * 0x9E3779B1u) >> (32 - 14);  // 14 bits = log2(kJoinTable)
+    return ((uint32_t)p * 0x9E3779B1u) >> (32 - 15);  // 15 bits = log2(kJoinTable)
 }
 
 template <bool kWrite>
@@ -250,8 +250,9 @@ join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, i
             const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand, int64_t cap,
             const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
 {
-    extern __shared__ int32_t table[];  // kJoinTable slots
+    extern __shared__ int32_t table[];  // kJoinTable slots, then kJoinMaxUnique sorted ids
     __shared__ int n_unique;
+    __shared__ int wsum[kJoinThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     for (int64_t q = blockIdx.x; q < Q; q += gridDim.x) {
@@ -312,23 +313,44 @@ join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, i
             if (threadIdx.x == 0) counts[q] = nu;
             continue;
         }
-        // sort the whole set; the nu ids come first, ascending
-        for (int k = 2; k <= kJoinTable; k <<= 1)
+        // compact the occupied slots into buf (block scan over contiguous slot ranges),
+        // then sort only the next power of two above nu
+        int32_t* buf = table + kJoinTable;
+        constexpr int kPer = kJoinTable / kJoinThreads;
+        const int s0 = threadIdx.x * kPer;
+        int mine = 0;
+        for (int i = 0; i < kPer; ++i) mine += table[s0 + i] != kNone;
+        int x = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        int pos = x - mine;
+        for (int w = 0; w < wid; ++w) pos += wsum[w];
+        for (int i = 0; i < kPer; ++i)
+            if (table[s0 + i] != kNone) buf[pos++] = table[s0 + i];
+        int n2 = 1;
+        while (n2 < nu) n2 <<= 1;
+        for (int i = nu + threadIdx.x; i < n2; i += blockDim.x) buf[i] = kNone;
+        __syncthreads();
+        for (int k = 2; k <= n2; k <<= 1)
             for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                for (int i = threadIdx.x; i < kJoinTable; i += blockDim.x) {
+                for (int i = threadIdx.x; i < n2; i += blockDim.x) {
                     const int l = i ^ jj;
                     if (l > i) {
-                        const int32_t a = table[i], b = table[l];
+                        const int32_t a = buf[i], b = buf[l];
                         if ((a > b) == ((i & k) == 0)) {
-                            table[i] = b;
-                            table[l] = a;
+                            buf[i] = b;
+                            buf[l] = a;
                         }
                     }
                 }
                 __syncthreads();
             }
         int32_t* out = cand + row_ptr[q];
-        for (int i = threadIdx.x; i < nu; i += blockDim.x) out[i] = table[i];
+        for (int i = threadIdx.x; i < nu; i += blockDim.x) out[i] = buf[i];
     }
 }
 
@@ -433,8 +455,8 @@ int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* 
     const pmh_params& P = X->params;
     const int64_t m = X->n * P.bands;
     if (P.bands > 16) {  // many short bands: parallel walk + sort
-        const unsigned blocks = (unsigned)std::min<int64_t>(Q, (int64_t)X->ctx->sm_count * 3);
-        const size_t smem = sizeof(int32_t) * kJoinTable;
+        const unsigned blocks = (unsigned)std::min<int64_t>(Q, (int64_t)X->ctx->sm_count);
+        const size_t smem = sizeof(int32_t) * (kJoinTable + kJoinMaxUnique);
         PMH_CUDA_TRY(cudaFuncSetAttribute(join_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
         PMH_CUDA_TRY(cudaFuncSetAttribute(join_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
