@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=None, help="polygons in the CPU sample")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default sign variant")
     ap.add_argument("--no-search", action="store_true", help="skip the recall / queries-per-s sweep")
+    ap.add_argument("--no-stream-index", action="store_true",
+                    help="sign by walking every stream point (no stream index)")
     ap.add_argument("--eval-queries", type=int, default=1000,
                     help="queries whose recall@10 is checked against brute force")
     ap.add_argument("--train-queries", type=int, default=4000)
@@ -263,7 +265,8 @@ def main():
     db = synth.make_database(gen_w, args.n_polys)
     qs = synth.make_queries(gen_w, db, args.n_queries)
     N, Q, K = db.n, qs.n, w.K
-    P = B.make_params(K, w.bands, w.T, w.seed, w.lsh_seed)
+    P = B.make_params(K, w.bands, w.T, w.seed, w.lsh_seed,
+                      0 if args.no_stream_index else B.FLAG_STREAM_INDEX)
     ctx = B.Context(local)
     stream = torch.cuda.current_stream()
 

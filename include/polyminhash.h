@@ -69,7 +69,14 @@ typedef struct pmh_index_s* pmh_index;
  *             1 <= bands <= 128
  *   rows      r, must equal K / bands
  *   lsh_seed  seed of the band-key fingerprint
- *   flags     0 (reserved) */
+ *   flags     0 or PMH_FLAG_STREAM_INDEX */
+/* pmh_params.flags: sign through the stream index (same hashes, much less
+ * work for small polygons).  The first call with a given (seed, K) builds the
+ * index of the first 65,536 points of each stream, bucketed by cell of a
+ * 128 x 128 grid (K * 512 KiB of device memory, kept by the context; that
+ * call synchronises); later calls reuse it. */
+#define PMH_FLAG_STREAM_INDEX 1u
+
 typedef struct {
     uint64_t seed;
     uint32_t K;
@@ -131,6 +138,10 @@ int pmh_polys_destroy(pmh_polys polys);
  * Errors: PMH_ERR_ARG (null, bad K/T), PMH_ERR_CUDA. */
 int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* params,
                      uint32_t* d_hashes, void* stream);
+
+/* Build (or reuse) the context's stream index for params->seed and K ahead of
+ * the first indexed pmh_minhash_sign call.  Synchronises. */
+int pmh_stream_index_build(pmh_ctx ctx, const pmh_params* params, void* stream);
 
 /* A2 -- band keys (hashmap keys of Sec. 3.2 after Theorem 1, one per band).
  * Band j covers hashes j*r .. j*r+r-1; a = mix64(lsh_seed + (j+1)*G), then

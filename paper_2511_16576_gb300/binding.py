@@ -35,9 +35,12 @@ class Params(ctypes.Structure):
                 ("reserved", ctypes.c_uint32)]
 
 
+FLAG_STREAM_INDEX = 1
+
+
 def make_params(K: int, bands: int, T: int = 1 << 24, seed: int = 0x5EED,
-                lsh_seed: int = 0x15A) -> Params:
-    return Params(seed, K, T, bands, K // bands, lsh_seed, 0, 0)
+                lsh_seed: int = 0x15A, flags: int = 0) -> Params:
+    return Params(seed, K, T, bands, K // bands, lsh_seed, flags, 0)
 
 
 # entry points: name -> (restype, argtypes)
@@ -56,6 +59,7 @@ _SIGS = {
     "pmh_polys_destroy": (ctypes.c_int, [_P]),
     "pmh_minhash_sign": (ctypes.c_int, [_P, _P, ctypes.POINTER(Params), _P, _P]),
     "pmh_band_keys": (ctypes.c_int, [_P, _P, _i64, ctypes.POINTER(Params), _P, _P]),
+    "pmh_stream_index_build": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P]),
     "pmh_lsh_build": (ctypes.c_int, [_P, _P, _i64, ctypes.POINTER(Params), ctypes.POINTER(_P), _P]),
     "pmh_index_destroy": (ctypes.c_int, [_P]),
     "pmh_lsh_query": (ctypes.c_int, [_P, _P, _P, _i64, _P, _P, _i64, ctypes.POINTER(_i64), _P]),
@@ -256,6 +260,11 @@ def minhash_sign_noalloc(xy: torch.Tensor, offsets: torch.Tensor, params: Params
     _check(load().pmh_minhash_sign_noalloc(_ptr(xy), _ptr(offsets), n, xy.shape[0],
                                            ctypes.byref(params), _ptr(out), _stream(stream)))
     return out
+
+
+def stream_index_build(ctx: Context, params: Params, stream=None):
+    """Build the context's stream index for (seed, K) ahead of indexed signing."""
+    _check(load().pmh_stream_index_build(ctx.handle, ctypes.byref(params), _stream(stream)))
 
 
 def band_keys(ctx: Context, hashes: torch.Tensor, params: Params, out=None, stream=None):

@@ -110,6 +110,9 @@ extern "C" int pmh_destroy(pmh_ctx ctx)
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->d_tickets) cudaFree(ctx->d_tickets);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->sindex.cell_start) cudaFree(ctx->sindex.cell_start);
+    if (ctx->sindex.idx) cudaFree(ctx->sindex.idx);
+    if (ctx->sindex.pts) cudaFree(ctx->sindex.pts);
     delete ctx;
     return PMH_OK;
 }

@@ -53,6 +53,24 @@ enum ScratchSlot {
     SCR_COUNT
 };
 
+// first kStreamIndexPoints points of every hash's stream, bucketed by cell of a
+// 2^kStreamGridBits-square grid (stream_index.cu)
+constexpr int kStreamGridBits = 7;
+constexpr int kStreamIndexPoints = 65536;
+struct StreamIndex {
+    uint64_t seed = 0;
+    int K = 0;
+    uint32_t* cell_start = nullptr;  // [K * G * G + 1]
+    uint32_t* idx = nullptr;         // [K * M] stream index of each entry
+    uint32_t* pts = nullptr;         // [K * M] x | y << 16
+};
+struct StreamIndexView {
+    const uint32_t* cell_start;  // nullptr: no index
+    const uint32_t* idx;
+    const uint32_t* pts;
+    int M, gbits, shift;
+};
+
 struct pmh_ctx_s {
     int device = 0;
     int sm_count = 0;
@@ -62,7 +80,10 @@ struct pmh_ctx_s {
     size_t scratch_bytes[SCR_COUNT] = {};
     int64_t* h_pinned = nullptr;          // small pinned host buffer [64]
     int sign_variant = -1;                // autotuned signing kernel (-1 = default)
+    StreamIndex sindex;                   // cached stream index (PMH_FLAG_STREAM_INDEX)
 };
+
+int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, StreamIndexView* out);
 
 // per-polygon y-slab edge index (slabs.cu); S == 0 for polygons without one
 struct SlabInfo {
@@ -160,7 +181,8 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     const SlabInfo* slabs, const int32_t* slab_ptr, const int32_t* slab_edges,
                     const int32_t* order, const pmh_params* P, int64_t n_polys,
                     const int64_t* d_n, const int* d_flags, unsigned long long* ticket,
-                    uint32_t* out, cudaStream_t s);
+                    uint32_t* out, cudaStream_t s, const int64_t* area2 = nullptr,
+                    const StreamIndexView* sidx = nullptr);
 int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
                      int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
                      int* d_flags, bool write, cudaStream_t s);

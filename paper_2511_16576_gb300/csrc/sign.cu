@@ -100,12 +100,13 @@ struct SlabEdges {
 // lane per round: one round covers 32 * U consecutive stream indices.
 template <int U, class Inside>
 __device__ __forceinline__ uint32_t sign_one_t(const Inside& inside, int x0, int y0, uint32_t w,
-                                               uint32_t h, uint64_t sk, uint32_t T, int lane)
+                                               uint32_t h, uint64_t sk, uint32_t T, int lane,
+                                               uint32_t start = 0)
 {
     if (w == 0 || h == 0) return T;
-    uint64_t z = sk + (uint64_t)(lane + 1) * PMH_GAMMA;
+    uint64_t z = sk + (uint64_t)(start + lane + 1) * PMH_GAMMA;
     const uint64_t step = 32ull * PMH_GAMMA;
-    for (uint32_t i0 = 0; i0 < T; i0 += 32u * U) {
+    for (uint32_t i0 = start; i0 < T; i0 += 32u * U) {
         uint32_t pts[U];
         unsigned m = 0;
 #pragma unroll
@@ -141,19 +142,92 @@ __device__ __forceinline__ uint32_t sign_one(const int2* __restrict__ v, int n, 
     return sign_one_t<kU>(AllEdges{v, n}, x0, y0, w, h, sk, T, lane);
 }
 
-// the hashes k0 .. k0+31 of one polygon; lane j returns hash k0 + j
+// Indexed form of one hash: the stream points of index < lim that fall in the
+// bounding box are read from the cells under it (kCand at most, else the full
+// walk), visited in index order by repeated warp argmin and tested exactly; the
+// first inside is h_k.  With none inside, the walk continues from lim.
+constexpr int kCand = 64;
+
+template <int U, class Inside>
+__device__ uint32_t sign_one_indexed(const Inside& inside, const StreamIndexView& S, int k,
+                                     uint64_t sk, int4 bb, uint32_t w, uint32_t h, uint32_t lim,
+                                     uint32_t T, uint2* cbuf, int* ccount, int lane)
+{
+    lim = min(lim, T);
+    const int cx0 = bb.x >> S.shift, cx1 = (bb.z - 1) >> S.shift;
+    const int cy0 = bb.y >> S.shift, cy1 = (bb.w - 1) >> S.shift;
+    const int ncx = cx1 - cx0 + 1, C = ncx * (cy1 - cy0 + 1);
+    const uint32_t* cs = S.cell_start + ((int64_t)k << (2 * S.gbits));
+    if (lane == 0) *ccount = 0;
+    __syncwarp();
+    for (int c = lane; c < C; c += 32) {
+        const int cell = ((cy0 + c / ncx) << S.gbits) | (cx0 + c % ncx);
+        const uint32_t end = cs[cell + 1];
+        for (uint32_t e = cs[cell]; e < end; ++e) {
+            const uint32_t i = S.idx[e];
+            if (i >= lim) break;
+            const uint32_t r = S.pts[e];
+            if (((r & 0xFFFFu) - (uint32_t)bb.x) < w && ((r >> 16) - (uint32_t)bb.y) < h) {
+                const int slot = atomicAdd(ccount, 1);
+                if (slot < kCand) cbuf[slot] = make_uint2(i, r);
+            }
+        }
+    }
+    __syncwarp();
+    const int n = *ccount;
+    if (n > kCand) return sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, 0);
+    uint2 c0 = lane < n ? cbuf[lane] : make_uint2(0xFFFFFFFFu, 0u);
+    uint2 c1 = lane + 32 < n ? cbuf[lane + 32] : make_uint2(0xFFFFFFFFu, 0u);
+    for (int t = 0; t < n; ++t) {
+        const uint32_t best = __reduce_min_sync(0xffffffffu, min(c0.x, c1.x));
+        const unsigned who = __ballot_sync(0xffffffffu, c0.x == best || c1.x == best);
+        const int src = __ffs(who) - 1;
+        const uint32_t r = __shfl_sync(0xffffffffu, c0.x == best ? c0.y : c1.y, src);
+        if (inside((int)(r & 0xFFFFu), (int)(r >> 16), lane)) return best;
+        if (lane == src) {
+            if (c0.x == best) c0.x = 0xFFFFFFFFu;
+            else c1.x = 0xFFFFFFFFu;
+        }
+    }
+    if (lim >= T) return T;
+    return sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, lim);
+}
+
+// the hashes k0 .. k0+31 of one polygon; lane j returns hash k0 + j.  lim > 0
+// selects the indexed form (stream points below lim read from the index).
 template <int U, class Inside>
 __device__ __forceinline__ uint32_t sign_chunk(const Inside& inside, int4 bb, uint64_t seed, int k0,
-                                               int kend, uint32_t T, int lane)
+                                               int kend, uint32_t T, int lane,
+                                               const StreamIndexView& S, uint32_t lim,
+                                               uint2* cbuf, int* ccount)
 {
     const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
     uint32_t mine = T;
     for (int k = k0; k < kend; ++k) {
         uint64_t sk = pmh_mix64(seed + (uint64_t)(k + 1) * PMH_GAMMA);
-        uint32_t hk = sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane);
+        uint32_t hk = lim ? sign_one_indexed<U>(inside, S, k, sk, bb, w, h, lim, T, cbuf, ccount, lane)
+                          : sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane);
         if (lane == k - k0) mine = hk;
     }
     return mine;
+}
+
+// Cost model of the indexed form for one polygon: the walk examines about
+// 2^32 / area points per hash; the indexed form reads the cells under the
+// bounding box and about lim * bbox / 2^32 candidates, with lim = 8 * 2^32 /
+// area (a hit is then missed with probability ~e^-8 and the walk resumes at
+// lim).  Returns lim, or 0 to walk.
+__device__ __forceinline__ uint32_t indexed_limit(const StreamIndexView& S, int4 bb, long long area2)
+{
+    if (!S.cell_start || bb.z <= bb.x || bb.w <= bb.y) return 0;
+    const double area = 0.5 * (double)(area2 < 0 ? -area2 : area2);
+    const double walk = 4294967296.0 / fmax(area, 1.0);
+    const double cells = (double)(((bb.z - 1) >> S.shift) - (bb.x >> S.shift) + 1) *
+                         (double)(((bb.w - 1) >> S.shift) - (bb.y >> S.shift) + 1);
+    const double lim = fmin((double)S.M, 8.0 * walk + 256.0);
+    const double cand = lim * (double)(bb.z - bb.x) * (double)(bb.w - bb.y) / 4294967296.0;
+    if (cells * 16.0 + 64.0 >= walk || cand > 24.0) return 0;
+    return (uint32_t)lim;
 }
 
 template <int U, int W>
@@ -163,9 +237,12 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
             const int32_t* __restrict__ slab_ptr, const int32_t* __restrict__ slab_edges,
             const int32_t* __restrict__ order, uint64_t seed, int K, uint32_t T, int chunks,
             int64_t n_polys, const int64_t* __restrict__ d_n, const int* __restrict__ d_flags,
-            unsigned long long* __restrict__ ticket, uint32_t* __restrict__ out)
+            unsigned long long* __restrict__ ticket, uint32_t* __restrict__ out,
+            const int64_t* __restrict__ area2, StreamIndexView S)
 {
     __shared__ __align__(16) int2 sv[W][kSmemVerts];
+    __shared__ uint2 cbuf[W][kCand];
+    __shared__ int ccount[W];
     if (d_flags && *d_flags) return;  // the batch failed validation
     if (d_n) n_polys = min(n_polys, *d_n);
     const int64_t n_items = n_polys * chunks;
@@ -183,19 +260,22 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
         const int64_t b = off[p];
         const int n = (int)(off[p + 1] - b);
         const int4 bb = bbox[p];
+        const uint32_t lim = area2 ? indexed_limit(S, bb, area2[p]) : 0;
         uint32_t mine;
         if (n <= kSmemVerts) {
             // stage the vertices in this warp's shared-memory slice (coalesced 8-byte loads)
             for (int i = lane; i < n; i += 32) sv[wid][i] = xy[b + i];
             __syncwarp();
-            mine = sign_chunk<U>(AllEdges{sv[wid], n}, bb, seed, k0, kend, T, lane);
+            mine = sign_chunk<U>(AllEdges{sv[wid], n}, bb, seed, k0, kend, T, lane, S, lim,
+                                 cbuf[wid], &ccount[wid]);
         } else if (slabs && slabs[p].S > 0) {
             const SlabInfo si = slabs[p];
             mine = sign_chunk<U>(SlabEdges{xy + b, n, slab_ptr + si.slab_base,
                                            slab_edges + si.edge_base, si.slab_h, si.ymin},
-                                 bb, seed, k0, kend, T, lane);
+                                 bb, seed, k0, kend, T, lane, S, lim, cbuf[wid], &ccount[wid]);
         } else {
-            mine = sign_chunk<U>(AllEdges{xy + b, n}, bb, seed, k0, kend, T, lane);
+            mine = sign_chunk<U>(AllEdges{xy + b, n}, bb, seed, k0, kend, T, lane, S, lim,
+                                 cbuf[wid], &ccount[wid]);
         }
         if (k0 + lane < kend) out[p * (int64_t)K + k0 + lane] = mine;
         __syncwarp();
@@ -204,7 +284,8 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
 
 using SignFn = void (*)(const int2*, const int64_t*, const int4*, const SlabInfo*, const int32_t*,
                         const int32_t*, const int32_t*, uint64_t, int, uint32_t, int, int64_t,
-                        const int64_t*, const int*, unsigned long long*, uint32_t*);
+                        const int64_t*, const int*, unsigned long long*, uint32_t*, const int64_t*,
+                        StreamIndexView);
 struct SignVariant {
     int U, W;
     SignFn fn;
@@ -230,8 +311,10 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     const SlabInfo* slabs, const int32_t* slab_ptr, const int32_t* slab_edges,
                     const int32_t* order, const pmh_params* P, int64_t n_polys,
                     const int64_t* d_n, const int* d_flags, unsigned long long* ticket,
-                    uint32_t* out, cudaStream_t s)
+                    uint32_t* out, cudaStream_t s, const int64_t* area2,
+                    const StreamIndexView* sidx)
 {
+    const StreamIndexView S = sidx ? *sidx : StreamIndexView{nullptr, nullptr, nullptr, 0, 0, 0};
     if (n_polys <= 0) return PMH_OK;
     const SignVariant& v = kSignVariants[ctx->sign_variant >= 0 ? ctx->sign_variant : 0];
     const int chunks = (int)((P->K + 31) / 32);
@@ -243,7 +326,7 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
     PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
     v.fn<<<(int)blocks, v.W * 32, 0, s>>>(xy, off, bbox, slabs, slab_ptr, slab_edges, order,
                                           P->seed, (int)P->K, P->T, chunks, n_polys, d_n, d_flags,
-                                          ticket, out);
+                                          ticket, out, area2, S);
     PMH_LAUNCHED("sign_kernel");
     return PMH_OK;
 }
@@ -256,9 +339,13 @@ extern "C" int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* 
     if (!polys || (!d_hashes && polys->n > 0))
         return pmh_set_error(PMH_ERR_ARG, "null polygons or output");
     if (polys->n == 0) return PMH_OK;
+    StreamIndexView sidx;
+    const bool indexed = (params->flags & PMH_FLAG_STREAM_INDEX) != 0;
+    if (indexed) PMH_TRY(pmh_stream_index_get(ctx, params, (cudaStream_t)stream, &sidx));
     return pmh_launch_sign(ctx, polys->xy, polys->offsets, polys->bbox, polys->slab_info,
                            polys->slab_ptr, polys->slab_edges, polys->order, params, polys->n,
-                           nullptr, nullptr, ctx->d_tickets + 0, d_hashes, (cudaStream_t)stream);
+                           nullptr, nullptr, ctx->d_tickets + 0, d_hashes, (cudaStream_t)stream,
+                           polys->area2, indexed ? &sidx : nullptr);
 }
 
 extern "C" int pmh_sign_variant_info(int variant, int* points_per_lane, int* warps_per_block)
@@ -302,9 +389,14 @@ extern "C" int pmh_sign_autotune(pmh_ctx ctx, pmh_polys sample, const pmh_params
         float ms_v = 1e30f;
         for (int r = 0; r < 3 && rc == PMH_OK; ++r) {  // first run is a warm-up
             cudaEventRecord(e0, 0);
-            rc = pmh_launch_sign(ctx, sample->xy, sample->offsets, sample->bbox, sample->slab_info,
-                                 sample->slab_ptr, sample->slab_edges, sample->order, params,
-                                 sample->n, nullptr, nullptr, ctx->d_tickets + 1, out, 0);
+            StreamIndexView sidx;
+            const bool indexed = (params->flags & PMH_FLAG_STREAM_INDEX) != 0;
+            if (indexed) rc = pmh_stream_index_get(ctx, params, 0, &sidx);
+            if (rc == PMH_OK)
+                rc = pmh_launch_sign(ctx, sample->xy, sample->offsets, sample->bbox, sample->slab_info,
+                                     sample->slab_ptr, sample->slab_edges, sample->order, params,
+                                     sample->n, nullptr, nullptr, ctx->d_tickets + 1, out, 0,
+                                     sample->area2, indexed ? &sidx : nullptr);
             cudaEventRecord(e1, 0);
             if (cudaEventSynchronize(e1) != cudaSuccess)
                 rc = pmh_set_error(PMH_ERR_CUDA, "autotune run failed");

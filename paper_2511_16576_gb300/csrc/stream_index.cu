@@ -1,0 +1,154 @@
+// stream_index.cu -- the first M points of every hash's stream, bucketed by
+// lattice cell (used by the indexed signing path of A1).
+//
+// Every polygon draws from the same K point streams (Sec. 3.2: fixed seeds per
+// hash function), so the points themselves can be indexed once: for each hash
+// k the points i < M are sorted (stably) by their cell in a G x G grid over the
+// domain.  A polygon then reads only the cells under its bounding box, and in
+// each cell only the points below an index limit L; the smallest such index
+// whose point lies in the polygon is h_k exactly, because every point of the
+// stream with index < L that lies in the bounding box is in one of those
+// cells.  If no point below L hits, the ordinary walk continues from L.
+//
+// Layout (k-major): entry e of hash k lives in [cell_start[k*G*G + c],
+// cell_start[k*G*G + c + 1]) for its cell c, with idx[e] its stream index
+// (ascending within a cell) and pts[e] = x | y << 16.
+#include <algorithm>
+
+#include "pmh_internal.cuh"
+
+namespace {
+
+__global__ void stream_points_kernel(uint64_t seed, int K, int M, int shift, int gbits,
+                                     uint32_t* __restrict__ keys, int32_t* __restrict__ vals)
+{
+    const int64_t total = (int64_t)K * M;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t / M);
+        const int i = (int)(t - (int64_t)k * M);
+        const uint64_t sk = pmh_mix64(seed + (uint64_t)(k + 1) * PMH_GAMMA);
+        const uint32_t r = pmh_mix64_lo(sk + (uint64_t)(i + 1) * PMH_GAMMA);
+        const uint32_t x = r & 0xFFFFu, y = r >> 16;
+        const uint32_t cell = ((y >> shift) << gbits) | (x >> shift);
+        keys[t] = ((uint32_t)k << (2 * gbits)) | cell;
+        vals[t] = i;
+    }
+}
+
+__global__ void cell_count_kernel(const uint32_t* __restrict__ keys, int64_t n,
+                                  int64_t* __restrict__ counts)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&counts[keys[e]]), 1ull);
+}
+
+__global__ void finish_index_kernel(const uint32_t* __restrict__ keys, const int32_t* __restrict__ vals,
+                                    int64_t n, const int64_t* __restrict__ starts, int64_t n_cells,
+                                    uint64_t seed, int gbits, uint32_t* __restrict__ cell_start,
+                                    uint32_t* __restrict__ idx, uint32_t* __restrict__ pts)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(keys[e] >> (2 * gbits));
+        const int i = vals[e];
+        const uint64_t sk = pmh_mix64(seed + (uint64_t)(k + 1) * PMH_GAMMA);
+        pts[e] = pmh_mix64_lo(sk + (uint64_t)(i + 1) * PMH_GAMMA);
+        idx[e] = (uint32_t)i;
+    }
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= n_cells;
+         c += (int64_t)gridDim.x * blockDim.x)
+        cell_start[c] = (uint32_t)starts[c];
+}
+
+}  // namespace
+
+int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, StreamIndexView* out)
+{
+    StreamIndex& si = ctx->sindex;
+    const int gbits = kStreamGridBits, shift = 16 - kStreamGridBits;
+    const int M = kStreamIndexPoints;
+    if (si.cell_start && si.seed == P->seed && si.K == (int)P->K) {
+        *out = StreamIndexView{si.cell_start, si.idx, si.pts, M, gbits, shift};
+        return PMH_OK;
+    }
+    if (si.cell_start) {
+        cudaDeviceSynchronize();
+        cudaFree(si.cell_start);
+        cudaFree(si.idx);
+        cudaFree(si.pts);
+        si = StreamIndex();
+    }
+    const int64_t n = (int64_t)P->K * M;
+    const int64_t n_cells = (int64_t)P->K << (2 * gbits);
+    if (cudaMalloc(&si.cell_start, sizeof(uint32_t) * (n_cells + 1)) != cudaSuccess ||
+        cudaMalloc(&si.idx, sizeof(uint32_t) * n) != cudaSuccess ||
+        cudaMalloc(&si.pts, sizeof(uint32_t) * n) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(si.cell_start);
+        cudaFree(si.idx);
+        cudaFree(si.pts);
+        si = StreamIndex();
+        return pmh_set_error(PMH_ERR_NOMEM, "stream index allocation failed");
+    }
+    uint32_t* keys = nullptr;
+    int32_t* vals = nullptr;
+    int64_t* counts = nullptr;
+    if (cudaMalloc(&keys, sizeof(uint32_t) * n) != cudaSuccess ||
+        cudaMalloc(&vals, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMalloc(&counts, sizeof(int64_t) * (n_cells + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(keys);
+        cudaFree(vals);
+        return pmh_set_error(PMH_ERR_NOMEM, "stream index scratch allocation failed");
+    }
+    int rc = PMH_OK;
+    const int blocks = ctx->sm_count * 16;
+    stream_points_kernel<<<blocks, 256, 0, s>>>(P->seed, (int)P->K, M, shift, gbits, keys, vals);
+    g_pmh_launches.fetch_add(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "stream points: %s", cudaGetErrorString(e));
+    int key_bits = 2 * gbits;
+    while ((1ll << key_bits) < (int64_t)P->K << (2 * gbits)) ++key_bits;
+    if (rc == PMH_OK) rc = pmh_radix_sort_u32(ctx, keys, vals, n, key_bits, s);
+    if (rc == PMH_OK && cudaMemsetAsync(counts, 0, sizeof(int64_t) * (n_cells + 1), s) != cudaSuccess)
+        rc = pmh_set_error(PMH_ERR_CUDA, "memset failed");
+    if (rc == PMH_OK) {
+        cell_count_kernel<<<blocks, 256, 0, s>>>(keys, n, counts);
+        g_pmh_launches.fetch_add(1);
+        rc = pmh_exclusive_scan_i64(ctx, counts, counts, n_cells, s);
+    }
+    if (rc == PMH_OK) {
+        finish_index_kernel<<<blocks, 256, 0, s>>>(keys, vals, n, counts, n_cells, P->seed, gbits,
+                                                    si.cell_start, si.idx, si.pts);
+        g_pmh_launches.fetch_add(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "finish: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(keys);
+    cudaFree(vals);
+    cudaFree(counts);
+    if (rc == PMH_OK && e2 != cudaSuccess)
+        rc = pmh_set_error(PMH_ERR_CUDA, "stream index build: %s", cudaGetErrorString(e2));
+    if (rc != PMH_OK) {
+        cudaFree(si.cell_start);
+        cudaFree(si.idx);
+        cudaFree(si.pts);
+        si = StreamIndex();
+        return rc;
+    }
+    si.seed = P->seed;
+    si.K = (int)P->K;
+    *out = StreamIndexView{si.cell_start, si.idx, si.pts, M, gbits, shift};
+    return PMH_OK;
+}
+
+extern "C" int pmh_stream_index_build(pmh_ctx ctx, const pmh_params* params, void* stream)
+{
+    PMH_TRY(pmh_check_device(ctx));
+    PMH_TRY(pmh_check_params(params));
+    StreamIndexView v;
+    return pmh_stream_index_get(ctx, params, (cudaStream_t)stream, &v);
+}

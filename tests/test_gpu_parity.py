@@ -74,24 +74,30 @@ def test_upload_rejects_bad_input(B, ctx):
         upload(B, ctx, ps)
 
 
-def test_sign_small_bit_exact(B, ctx, orc, small):
+FLAGS = [0, 1]   # 1 = signing through the stream index
+
+
+@pytest.mark.parametrize("flags", FLAGS)
+def test_sign_small_bit_exact(B, ctx, orc, small, flags):
     w, db, qs = small
-    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed)
+    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed, flags)
     h = u32(B.minhash_sign(ctx, upload(B, ctx, db), P))
     ref = orc.sign(db.xy, db.offsets, w.seed, w.K, w.T, nthreads=8)
     assert np.array_equal(h, ref)
 
 
-@pytest.mark.parametrize("K,T", [(40, 1 << 24), (32, 100), (7, 3000), (64, 1)])
-def test_sign_ragged_K_and_cap(B, ctx, orc, K, T):
-    db = synth.star_polygons(300, 11, (3, 40), "uniform", (1e-3, 2e-2))
-    P = B.make_params(K, 1, T)
+@pytest.mark.parametrize("flags", FLAGS)
+@pytest.mark.parametrize("K,T", [(40, 1 << 24), (32, 100), (7, 3000), (64, 1), (32, 70000)])
+def test_sign_ragged_K_and_cap(B, ctx, orc, K, T, flags):
+    db = synth.star_polygons(300, 11, (3, 40), "loguniform", (2e-6, 2e-2))
+    P = B.make_params(K, 1, T, flags=flags)
     h = u32(B.minhash_sign(ctx, upload(B, ctx, db), P))
     ref = orc.sign(db.xy, db.offsets, SEED, K, T, nthreads=8)
     assert np.array_equal(h, ref)
 
 
-def test_sign_edge_cases(B, ctx, orc):
+@pytest.mark.parametrize("flags", FLAGS)
+def test_sign_edge_cases(B, ctx, orc, flags):
     polys = [
         [[0, 0], [65536, 0], [65536, 65536], [0, 65536]],          # covers the domain: all 0
         [[-100, -100], [70000, -50], [70000, 70000], [-90, 70000]],  # beyond the domain
@@ -104,19 +110,30 @@ def test_sign_edge_cases(B, ctx, orc):
     big = synth.star_polygons(1, 5, (2000, 2000), "uniform", (2e-3, 2e-3))
     polys.append(big.poly(0))
     ps = from_polys(polys)
+    # tiny polygons (indexed form, including walks resumed past the index) and a thin sliver
+    polys.append([[30000, 30000], [30040, 30000], [30040, 30030], [30000, 30030]])
+    polys.append([[100, 100], [160, 103], [120, 150]])
+    polys.append([[5000, 5000], [9000, 5001], [9000, 5003], [5000, 5002]])
+    ps = from_polys(polys)
     K, T = 64, 200000
-    P = B.make_params(K, 1, T)
+    P = B.make_params(K, 1, T, flags=flags)
     h = u32(B.minhash_sign(ctx, upload(B, ctx, ps), P))
     ref = orc.sign(ps.xy, ps.offsets, SEED, K, T)
     assert np.array_equal(h, ref)
     assert (h[0] == 0).all() and (h[2] == T).all()
 
 
-def test_sign_scale_workload_sampled(B, ctx, orc):
+@pytest.fixture(scope="module")
+def scale_db():
+    return synth.make_database(synth.WORKLOADS["scale"])
+
+
+@pytest.mark.parametrize("flags", FLAGS)
+def test_sign_scale_workload_sampled(B, ctx, orc, scale_db, flags):
     """The 1,000,000-polygon, K = 128 workload in the benchmark's launch, sampled rows."""
     w = synth.WORKLOADS["scale"]
-    db = synth.make_database(w)
-    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed)
+    db = scale_db
+    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed, flags)
     h = B.minhash_sign(ctx, upload(B, ctx, db), P)
     rng = np.random.default_rng(0)
     rows = np.sort(rng.choice(db.n, 96, replace=False))
@@ -290,11 +307,12 @@ def test_refine_topk_matches_oracle(B, ctx, orc, small):
         assert (top_ids[q, len(exp):] == -1).all()
 
 
-def test_sign_batching_workload_sampled(B, ctx, orc):
+@pytest.mark.parametrize("flags", FLAGS)
+def test_sign_batching_workload_sampled(B, ctx, orc, flags):
     """Fractal coastline-like polygons with 4..65,536 vertices (slab-index edge path), K = 256."""
     w = synth.WORKLOADS["batching"]
     db = synth.make_database(w, 600)
-    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed)
+    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed, flags)
     h = B.minhash_sign(ctx, upload(B, ctx, db), P)
     n = np.diff(db.offsets)
     order = np.argsort(n)
