@@ -28,10 +28,19 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# 32-bit integer operations the definition needs per stream point: 64-bit counter add (2),
-# two xor-shift rounds (4 + 4), two low-64-bit 64x64 multiplies (4 + 4), final xor-shift
-# of the low word (2), field extraction and half-open bbox test (6).
+# Algorithmic 32-bit integer operations of the signing kernel, per unit of work it
+# reports (pmh_sign_work):
+#  walked stream point: 64-bit counter add (2), two xor-shift rounds (4 + 4), two
+#    low-64-bit 64x64 multiplies (4 + 4), final xor-shift of the low word (2), field
+#    extraction and half-open bbox test (6) = 26;
+#  grid cell read by the indexed form: two offsets and the cell address = 8;
+#  stream-index entry read: index and point loads, limit compare, bbox test = 10;
+#  bbox candidate ordered (one warp argmin step) = 6;
+#  polygon edge tested: straddle test (3), two 32x32->64 products (4), difference (2),
+#    sign test and parity (3) = 12.
 INT_OPS_PER_POINT = 26
+SIGN_OP_WEIGHTS = {"walk_points": 26, "cells": 8, "index_entries": 10, "candidates": 6,
+                   "edge_tests": 12}
 
 
 def parse():
@@ -365,17 +374,25 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": ms_e2e}
 
-    # roofline of the dominant kernel: integer ops of the definition / sign kernel time
+    # roofline of the dominant kernel: its algorithmic integer ops (work units it reports,
+    # weighted as above) per launch / its CUDA-event time, against the measured peak
     hashes_np = h.cpu().numpy().view(np.uint32)
     G = algorithmic_points(hashes_np, w.T)
+    dbp_w = B.poly_upload(ctx, d_xy, d_off)
+    B.minhash_sign(ctx, dbp_w, P)          # one more database launch, untimed, to read its work
+    units = B.sign_work(ctx)
+    dbp_w.close()
+    ops = sum(SIGN_OP_WEIGHTS[k] * v for k, v in units.items())
     peak = B.probe_int_peak(ctx)
-    achieved = INT_OPS_PER_POINT * G / (sign_ms * 1e-3)
+    achieved = ops / (sign_ms * 1e-3)
     roofline = {"bound": "alu", "kernel": "sign_kernel", "achieved": achieved / 1e12,
                 "peak": peak / 1e12, "unit": "Tintop/s", "frac": achieved / peak,
-                "traffic": None, "points_per_launch": G,
-                "int_ops_per_point": INT_OPS_PER_POINT,
+                "traffic": None, "work_units_per_launch": units, "op_weights": SIGN_OP_WEIGHTS,
+                "int_ops_per_launch": ops,
                 "peak_source": "measured: pmh_probe_int_peak (integer mad/add/xor/shl mix, all SMs)",
-                "sign_ms": sign_ms, "points_per_s": G / (sign_ms * 1e-3)}
+                "sign_ms": sign_ms, "stream_points_resolved": G,
+                "stream_points_resolved_per_s": G / (sign_ms * 1e-3),
+                "walk_equivalent_tintops": INT_OPS_PER_POINT * G / (sign_ms * 1e-3) / 1e12}
 
     search = None
     if not args.no_search:

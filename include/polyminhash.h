@@ -143,6 +143,12 @@ int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* params,
  * the first indexed pmh_minhash_sign call.  Synchronises. */
 int pmh_stream_index_build(pmh_ctx ctx, const pmh_params* params, void* stream);
 
+/* Algorithmic work of the last pmh_minhash_sign call on this context
+ * (synchronises): h_counts[0] stream points examined by walks (up to each
+ * result), [1] grid cells read by the indexed form, [2] stream-index entries
+ * read, [3] bounding-box candidates ordered, [4] polygon edges tested. */
+int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts);
+
 /* A2 -- band keys (hashmap keys of Sec. 3.2 after Theorem 1, one per band).
  * Band j covers hashes j*r .. j*r+r-1; a = mix64(lsh_seed + (j+1)*G), then
  * a = mix64(a ^ h) for each of its r hashes; a band holding T has key

@@ -60,6 +60,7 @@ _SIGS = {
     "pmh_minhash_sign": (ctypes.c_int, [_P, _P, ctypes.POINTER(Params), _P, _P]),
     "pmh_band_keys": (ctypes.c_int, [_P, _P, _i64, ctypes.POINTER(Params), _P, _P]),
     "pmh_stream_index_build": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P]),
+    "pmh_sign_work": (ctypes.c_int, [_P, _P]),
     "pmh_lsh_build": (ctypes.c_int, [_P, _P, _i64, ctypes.POINTER(Params), ctypes.POINTER(_P), _P]),
     "pmh_index_destroy": (ctypes.c_int, [_P]),
     "pmh_lsh_query": (ctypes.c_int, [_P, _P, _P, _i64, _P, _P, _i64, ctypes.POINTER(_i64), _P]),
@@ -265,6 +266,16 @@ def minhash_sign_noalloc(xy: torch.Tensor, offsets: torch.Tensor, params: Params
 def stream_index_build(ctx: Context, params: Params, stream=None):
     """Build the context's stream index for (seed, K) ahead of indexed signing."""
     _check(load().pmh_stream_index_build(ctx.handle, ctypes.byref(params), _stream(stream)))
+
+
+def sign_work(ctx: Context) -> dict:
+    """Work units of the last signing call: walked points, cells, index entries,
+    bbox candidates, edge tests."""
+    import numpy as np
+    c = np.zeros(5, np.uint64)
+    _check(load().pmh_sign_work(ctx.handle, c.ctypes.data))
+    return dict(zip(("walk_points", "cells", "index_entries", "candidates", "edge_tests"),
+                    (int(v) for v in c)))
 
 
 def band_keys(ctx: Context, hashes: torch.Tensor, params: Params, out=None, stream=None):

@@ -111,8 +111,7 @@ extern "C" int pmh_destroy(pmh_ctx ctx)
     if (ctx->d_tickets) cudaFree(ctx->d_tickets);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->sindex.cell_start) cudaFree(ctx->sindex.cell_start);
-    if (ctx->sindex.idx) cudaFree(ctx->sindex.idx);
-    if (ctx->sindex.pts) cudaFree(ctx->sindex.pts);
+    if (ctx->sindex.ent) cudaFree(ctx->sindex.ent);
     delete ctx;
     return PMH_OK;
 }

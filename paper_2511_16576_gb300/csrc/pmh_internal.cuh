@@ -61,13 +61,11 @@ struct StreamIndex {
     uint64_t seed = 0;
     int K = 0;
     uint32_t* cell_start = nullptr;  // [K * G * G + 1]
-    uint32_t* idx = nullptr;         // [K * M] stream index of each entry
-    uint32_t* pts = nullptr;         // [K * M] x | y << 16
+    uint2* ent = nullptr;            // [K * M] (stream index, x | y << 16)
 };
 struct StreamIndexView {
     const uint32_t* cell_start;  // nullptr: no index
-    const uint32_t* idx;
-    const uint32_t* pts;
+    const uint2* ent;
     int M, gbits, shift;
 };
 

@@ -32,6 +32,7 @@ namespace {
 constexpr int kWarps = 8;        // warps per block
 constexpr int kSmemVerts = 256;  // vertices staged per warp (larger polygons read global)
 constexpr int kU = 4;            // points per lane per round
+constexpr int kWorkSlot = 8;     // context ticket slots 8..12: work counters of the last sign
 
 // Exact half-open membership of lattice point (px, py), warp-cooperative.
 // Edge a->b counts iff (ay > py) != (by > py) and the int64 cross product
@@ -52,15 +53,23 @@ __device__ __forceinline__ bool warp_inside(const int2* __restrict__ v, int n, i
     return __popc(__ballot_sync(0xffffffffu, par)) & 1;
 }
 
+// Algorithmic work of one warp (warp-uniform counts): stream points the walk
+// examined up to its result, grid cells and index entries read by the indexed
+// form, bbox candidates it ordered, and edges tested by the exact membership.
+struct Work {
+    unsigned long long walk = 0, cells = 0, entries = 0, cand = 0, edges = 0;
+};
+
 // Exact membership through the polygon's y-slab index: only the edges listed
 // for the slab holding py can straddle the line y = py.
 __device__ __forceinline__ bool warp_inside_slab(const int2* __restrict__ v, int n,
                                                  const int32_t* __restrict__ sp,
                                                  const int32_t* __restrict__ se, int slab_h,
-                                                 int ymin, int px, int py, int lane)
+                                                 int ymin, int px, int py, int lane, int& tested)
 {
     const int s = (py - ymin) / slab_h;
     const int lo = sp[s], hi = sp[s + 1];
+    tested = hi - lo;
     unsigned par = 0;
     for (int i = lo + lane; i < hi; i += 32) {
         int e = se[i];
@@ -78,8 +87,9 @@ __device__ __forceinline__ bool warp_inside_slab(const int2* __restrict__ v, int
 struct AllEdges {
     const int2* v;
     int n;
-    __device__ __forceinline__ bool operator()(int px, int py, int lane) const
+    __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
     {
+        w.edges += n;
         return warp_inside(v, n, px, py, lane);
     }
 };
@@ -90,20 +100,38 @@ struct SlabEdges {
     const int32_t* sp;
     const int32_t* se;
     int slab_h, ymin;
-    __device__ __forceinline__ bool operator()(int px, int py, int lane) const
+    __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
     {
-        return warp_inside_slab(v, n, sp, se, slab_h, ymin, px, py, lane);
+        int tested = 0;
+        const bool r = warp_inside_slab(v, n, sp, se, slab_h, ymin, px, py, lane, tested);
+        w.edges += tested;
+        return r;
     }
 };
+
+template <int U, class Inside>
+__device__ __forceinline__ uint32_t sign_walk(const Inside& inside, int x0, int y0, uint32_t w,
+                                              uint32_t h, uint64_t sk, uint32_t T, int lane,
+                                              Work& work, uint32_t start);
 
 // One hash of one polygon; every lane returns the same value.  U points per
 // lane per round: one round covers 32 * U consecutive stream indices.
 template <int U, class Inside>
 __device__ __forceinline__ uint32_t sign_one_t(const Inside& inside, int x0, int y0, uint32_t w,
                                                uint32_t h, uint64_t sk, uint32_t T, int lane,
-                                               uint32_t start = 0)
+                                               Work& work, uint32_t start = 0)
 {
     if (w == 0 || h == 0) return T;
+    const uint32_t r = sign_walk<U>(inside, x0, y0, w, h, sk, T, lane, work, start);
+    work.walk += (r < T ? r + 1 : T) - start;
+    return r;
+}
+
+template <int U, class Inside>
+__device__ __forceinline__ uint32_t sign_walk(const Inside& inside, int x0, int y0, uint32_t w,
+                                              uint32_t h, uint64_t sk, uint32_t T, int lane,
+                                              Work& work, uint32_t start)
+{
     uint64_t z = sk + (uint64_t)(start + lane + 1) * PMH_GAMMA;
     const uint64_t step = 32ull * PMH_GAMMA;
     for (uint32_t i0 = start; i0 < T; i0 += 32u * U) {
@@ -128,7 +156,7 @@ __device__ __forceinline__ uint32_t sign_one_t(const Inside& inside, int x0, int
                 uint32_t i = i0 + (uint32_t)(j * 32 + l);
                 if (i >= T) return T;
                 uint32_t r = __shfl_sync(0xffffffffu, pts[j], l);
-                if (inside((int)(r & 0xFFFFu), (int)(r >> 16), lane)) return i;
+                if (inside((int)(r & 0xFFFFu), (int)(r >> 16), lane, work)) return i;
             }
         }
     }
@@ -139,7 +167,8 @@ __device__ __forceinline__ uint32_t sign_one(const int2* __restrict__ v, int n, 
                                              uint32_t w, uint32_t h, uint64_t sk, uint32_t T,
                                              int lane)
 {
-    return sign_one_t<kU>(AllEdges{v, n}, x0, y0, w, h, sk, T, lane);
+    Work unused;
+    return sign_one_t<kU>(AllEdges{v, n}, x0, y0, w, h, sk, T, lane, unused);
 }
 
 // Indexed form of one hash: the stream points of index < lim that fall in the
@@ -151,7 +180,7 @@ constexpr int kCand = 64;
 template <int U, class Inside>
 __device__ uint32_t sign_one_indexed(const Inside& inside, const StreamIndexView& S, int k,
                                      uint64_t sk, int4 bb, uint32_t w, uint32_t h, uint32_t lim,
-                                     uint32_t T, uint2* cbuf, int* ccount, int lane)
+                                     uint32_t T, uint2* cbuf, int* ccount, int lane, Work& work)
 {
     lim = min(lim, T);
     const int cx0 = bb.x >> S.shift, cx1 = (bb.z - 1) >> S.shift;
@@ -160,22 +189,39 @@ __device__ uint32_t sign_one_indexed(const Inside& inside, const StreamIndexView
     const uint32_t* cs = S.cell_start + ((int64_t)k << (2 * S.gbits));
     if (lane == 0) *ccount = 0;
     __syncwarp();
+    int read = 0;
     for (int c = lane; c < C; c += 32) {
         const int cell = ((cy0 + c / ncx) << S.gbits) | (cx0 + c % ncx);
-        const uint32_t end = cs[cell + 1];
-        for (uint32_t e = cs[cell]; e < end; ++e) {
-            const uint32_t i = S.idx[e];
-            if (i >= lim) break;
-            const uint32_t r = S.pts[e];
-            if (((r & 0xFFFFu) - (uint32_t)bb.x) < w && ((r >> 16) - (uint32_t)bb.y) < h) {
-                const int slot = atomicAdd(ccount, 1);
-                if (slot < kCand) cbuf[slot] = make_uint2(i, r);
+        const uint32_t beg = cs[cell], end = cs[cell + 1];
+        // entries four at a time: independent 8-byte loads in flight together
+        for (uint32_t e = beg; e < end; e += 4) {
+            uint2 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) q[u] = e + u < end ? S.ent[e + u] : make_uint2(0xFFFFFFFFu, 0u);
+            bool stop = false;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (stop || e + u >= end) break;
+                ++read;
+                if (q[u].x >= lim) {
+                    stop = true;
+                    break;
+                }
+                const uint32_t r = q[u].y;
+                if (((r & 0xFFFFu) - (uint32_t)bb.x) < w && ((r >> 16) - (uint32_t)bb.y) < h) {
+                    const int slot = atomicAdd(ccount, 1);
+                    if (slot < kCand) cbuf[slot] = make_uint2(q[u].x, r);
+                }
             }
+            if (stop) break;
         }
     }
     __syncwarp();
     const int n = *ccount;
-    if (n > kCand) return sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, 0);
+    work.cells += C;
+    work.entries += __reduce_add_sync(0xffffffffu, read);
+    work.cand += min(n, kCand);
+    if (n > kCand) return sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, work, 0);
     uint2 c0 = lane < n ? cbuf[lane] : make_uint2(0xFFFFFFFFu, 0u);
     uint2 c1 = lane + 32 < n ? cbuf[lane + 32] : make_uint2(0xFFFFFFFFu, 0u);
     for (int t = 0; t < n; ++t) {
@@ -183,14 +229,14 @@ __device__ uint32_t sign_one_indexed(const Inside& inside, const StreamIndexView
         const unsigned who = __ballot_sync(0xffffffffu, c0.x == best || c1.x == best);
         const int src = __ffs(who) - 1;
         const uint32_t r = __shfl_sync(0xffffffffu, c0.x == best ? c0.y : c1.y, src);
-        if (inside((int)(r & 0xFFFFu), (int)(r >> 16), lane)) return best;
+        if (inside((int)(r & 0xFFFFu), (int)(r >> 16), lane, work)) return best;
         if (lane == src) {
             if (c0.x == best) c0.x = 0xFFFFFFFFu;
             else c1.x = 0xFFFFFFFFu;
         }
     }
     if (lim >= T) return T;
-    return sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, lim);
+    return sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, work, lim);
 }
 
 // the hashes k0 .. k0+31 of one polygon; lane j returns hash k0 + j.  lim > 0
@@ -199,24 +245,26 @@ template <int U, class Inside>
 __device__ __forceinline__ uint32_t sign_chunk(const Inside& inside, int4 bb, uint64_t seed, int k0,
                                                int kend, uint32_t T, int lane,
                                                const StreamIndexView& S, uint32_t lim,
-                                               uint2* cbuf, int* ccount)
+                                               uint2* cbuf, int* ccount, Work& work)
 {
     const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
     uint32_t mine = T;
     for (int k = k0; k < kend; ++k) {
         uint64_t sk = pmh_mix64(seed + (uint64_t)(k + 1) * PMH_GAMMA);
-        uint32_t hk = lim ? sign_one_indexed<U>(inside, S, k, sk, bb, w, h, lim, T, cbuf, ccount, lane)
-                          : sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane);
+        uint32_t hk = lim ? sign_one_indexed<U>(inside, S, k, sk, bb, w, h, lim, T, cbuf, ccount, lane,
+                                                work)
+                          : sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, work);
         if (lane == k - k0) mine = hk;
     }
     return mine;
 }
 
-// Cost model of the indexed form for one polygon: the walk examines about
-// 2^32 / area points per hash; the indexed form reads the cells under the
-// bounding box and about lim * bbox / 2^32 candidates, with lim = 8 * 2^32 /
-// area (a hit is then missed with probability ~e^-8 and the walk resumes at
-// lim).  Returns lim, or 0 to walk.
+// Cost model of the indexed form for one polygon, in warp instructions per
+// hash: the walk examines about 2^32 / area points, 128 per round of ~130
+// instructions; the indexed form reads the cells under the bounding box, 32 per
+// round of ~50 instructions, and orders about lim * bbox / 2^32 candidates,
+// with lim = 8 * 2^32 / area (a hit is then missed with probability ~e^-8 and
+// the walk resumes at lim).  Returns lim, or 0 to walk.
 __device__ __forceinline__ uint32_t indexed_limit(const StreamIndexView& S, int4 bb, long long area2)
 {
     if (!S.cell_start || bb.z <= bb.x || bb.w <= bb.y) return 0;
@@ -226,7 +274,9 @@ __device__ __forceinline__ uint32_t indexed_limit(const StreamIndexView& S, int4
                          (double)(((bb.w - 1) >> S.shift) - (bb.y >> S.shift) + 1);
     const double lim = fmin((double)S.M, 8.0 * walk + 256.0);
     const double cand = lim * (double)(bb.z - bb.x) * (double)(bb.w - bb.y) / 4294967296.0;
-    if (cells * 16.0 + 64.0 >= walk || cand > 24.0) return 0;
+    const double walk_cost = ceil(walk / 128.0) * 130.0;
+    const double index_cost = ceil(cells / 32.0) * 50.0 + 40.0;
+    if (index_cost >= walk_cost || cand > 24.0) return 0;
     return (uint32_t)lim;
 }
 
@@ -238,11 +288,16 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
             const int32_t* __restrict__ order, uint64_t seed, int K, uint32_t T, int chunks,
             int64_t n_polys, const int64_t* __restrict__ d_n, const int* __restrict__ d_flags,
             unsigned long long* __restrict__ ticket, uint32_t* __restrict__ out,
-            const int64_t* __restrict__ area2, StreamIndexView S)
+            const int64_t* __restrict__ area2, StreamIndexView S,
+            unsigned long long* __restrict__ work_out)
 {
     __shared__ __align__(16) int2 sv[W][kSmemVerts];
     __shared__ uint2 cbuf[W][kCand];
     __shared__ int ccount[W];
+    __shared__ unsigned long long wsum[5];
+    Work work;
+    if (threadIdx.x < 5) wsum[threadIdx.x] = 0;
+    __syncthreads();
     if (d_flags && *d_flags) return;  // the batch failed validation
     if (d_n) n_polys = min(n_polys, *d_n);
     const int64_t n_items = n_polys * chunks;
@@ -267,25 +322,36 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
             for (int i = lane; i < n; i += 32) sv[wid][i] = xy[b + i];
             __syncwarp();
             mine = sign_chunk<U>(AllEdges{sv[wid], n}, bb, seed, k0, kend, T, lane, S, lim,
-                                 cbuf[wid], &ccount[wid]);
+                                 cbuf[wid], &ccount[wid], work);
         } else if (slabs && slabs[p].S > 0) {
             const SlabInfo si = slabs[p];
             mine = sign_chunk<U>(SlabEdges{xy + b, n, slab_ptr + si.slab_base,
                                            slab_edges + si.edge_base, si.slab_h, si.ymin},
-                                 bb, seed, k0, kend, T, lane, S, lim, cbuf[wid], &ccount[wid]);
+                                 bb, seed, k0, kend, T, lane, S, lim, cbuf[wid], &ccount[wid], work);
         } else {
             mine = sign_chunk<U>(AllEdges{xy + b, n}, bb, seed, k0, kend, T, lane, S, lim,
-                                 cbuf[wid], &ccount[wid]);
+                                 cbuf[wid], &ccount[wid], work);
         }
         if (k0 + lane < kend) out[p * (int64_t)K + k0 + lane] = mine;
         __syncwarp();
+    }
+    if (work_out) {
+        if (lane == 0) {
+            atomicAdd(&wsum[0], work.walk);
+            atomicAdd(&wsum[1], work.cells);
+            atomicAdd(&wsum[2], work.entries);
+            atomicAdd(&wsum[3], work.cand);
+            atomicAdd(&wsum[4], work.edges);
+        }
+        __syncthreads();
+        if (threadIdx.x < 5) atomicAdd(&work_out[threadIdx.x], wsum[threadIdx.x]);
     }
 }
 
 using SignFn = void (*)(const int2*, const int64_t*, const int4*, const SlabInfo*, const int32_t*,
                         const int32_t*, const int32_t*, uint64_t, int, uint32_t, int, int64_t,
                         const int64_t*, const int*, unsigned long long*, uint32_t*, const int64_t*,
-                        StreamIndexView);
+                        StreamIndexView, unsigned long long*);
 struct SignVariant {
     int U, W;
     SignFn fn;
@@ -314,7 +380,7 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     uint32_t* out, cudaStream_t s, const int64_t* area2,
                     const StreamIndexView* sidx)
 {
-    const StreamIndexView S = sidx ? *sidx : StreamIndexView{nullptr, nullptr, nullptr, 0, 0, 0};
+    const StreamIndexView S = sidx ? *sidx : StreamIndexView{nullptr, nullptr, 0, 0, 0};
     if (n_polys <= 0) return PMH_OK;
     const SignVariant& v = kSignVariants[ctx->sign_variant >= 0 ? ctx->sign_variant : 0];
     const int chunks = (int)((P->K + 31) / 32);
@@ -324,9 +390,11 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
     int64_t blocks = (int64_t)ctx->sm_count * std::max(per_sm, 1);
     blocks = std::min<int64_t>(blocks, (n_items + v.W - 1) / v.W);
     PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
+    unsigned long long* work = d_n ? nullptr : ctx->d_tickets + kWorkSlot;
+    if (work) PMH_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long) * 5, s));
     v.fn<<<(int)blocks, v.W * 32, 0, s>>>(xy, off, bbox, slabs, slab_ptr, slab_edges, order,
                                           P->seed, (int)P->K, P->T, chunks, n_polys, d_n, d_flags,
-                                          ticket, out, area2, S);
+                                          ticket, out, area2, S, work);
     PMH_LAUNCHED("sign_kernel");
     return PMH_OK;
 }
@@ -346,6 +414,16 @@ extern "C" int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* 
                            polys->slab_ptr, polys->slab_edges, polys->order, params, polys->n,
                            nullptr, nullptr, ctx->d_tickets + 0, d_hashes, (cudaStream_t)stream,
                            polys->area2, indexed ? &sidx : nullptr);
+}
+
+extern "C" int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts)
+{
+    PMH_TRY(pmh_check_device(ctx));
+    if (!h_counts) return pmh_set_error(PMH_ERR_ARG, "null output");
+    PMH_CUDA_TRY(cudaDeviceSynchronize());
+    PMH_CUDA_TRY(cudaMemcpy(h_counts, ctx->d_tickets + kWorkSlot, sizeof(uint64_t) * 5,
+                            cudaMemcpyDeviceToHost));
+    return PMH_OK;
 }
 
 extern "C" int pmh_sign_variant_info(int variant, int* points_per_lane, int* warps_per_block)

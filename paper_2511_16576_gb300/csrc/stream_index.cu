@@ -11,8 +11,8 @@
 // cells.  If no point below L hits, the ordinary walk continues from L.
 //
 // Layout (k-major): entry e of hash k lives in [cell_start[k*G*G + c],
-// cell_start[k*G*G + c + 1]) for its cell c, with idx[e] its stream index
-// (ascending within a cell) and pts[e] = x | y << 16.
+// cell_start[k*G*G + c + 1]) for its cell c; ent[e] = (stream index, x | y << 16),
+// indices ascending within a cell, one 8-byte load per entry.
 #include <algorithm>
 
 #include "pmh_internal.cuh"
@@ -47,15 +47,14 @@ __global__ void cell_count_kernel(const uint32_t* __restrict__ keys, int64_t n,
 __global__ void finish_index_kernel(const uint32_t* __restrict__ keys, const int32_t* __restrict__ vals,
                                     int64_t n, const int64_t* __restrict__ starts, int64_t n_cells,
                                     uint64_t seed, int gbits, uint32_t* __restrict__ cell_start,
-                                    uint32_t* __restrict__ idx, uint32_t* __restrict__ pts)
+                                    uint2* __restrict__ ent)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(keys[e] >> (2 * gbits));
         const int i = vals[e];
         const uint64_t sk = pmh_mix64(seed + (uint64_t)(k + 1) * PMH_GAMMA);
-        pts[e] = pmh_mix64_lo(sk + (uint64_t)(i + 1) * PMH_GAMMA);
-        idx[e] = (uint32_t)i;
+        ent[e] = make_uint2((uint32_t)i, pmh_mix64_lo(sk + (uint64_t)(i + 1) * PMH_GAMMA));
     }
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= n_cells;
          c += (int64_t)gridDim.x * blockDim.x)
@@ -70,25 +69,22 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
     const int gbits = kStreamGridBits, shift = 16 - kStreamGridBits;
     const int M = kStreamIndexPoints;
     if (si.cell_start && si.seed == P->seed && si.K == (int)P->K) {
-        *out = StreamIndexView{si.cell_start, si.idx, si.pts, M, gbits, shift};
+        *out = StreamIndexView{si.cell_start, si.ent, M, gbits, shift};
         return PMH_OK;
     }
     if (si.cell_start) {
         cudaDeviceSynchronize();
         cudaFree(si.cell_start);
-        cudaFree(si.idx);
-        cudaFree(si.pts);
+        cudaFree(si.ent);
         si = StreamIndex();
     }
     const int64_t n = (int64_t)P->K * M;
     const int64_t n_cells = (int64_t)P->K << (2 * gbits);
     if (cudaMalloc(&si.cell_start, sizeof(uint32_t) * (n_cells + 1)) != cudaSuccess ||
-        cudaMalloc(&si.idx, sizeof(uint32_t) * n) != cudaSuccess ||
-        cudaMalloc(&si.pts, sizeof(uint32_t) * n) != cudaSuccess) {
+        cudaMalloc(&si.ent, sizeof(uint2) * n) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(si.cell_start);
-        cudaFree(si.idx);
-        cudaFree(si.pts);
+        cudaFree(si.ent);
         si = StreamIndex();
         return pmh_set_error(PMH_ERR_NOMEM, "stream index allocation failed");
     }
@@ -121,7 +117,7 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
     }
     if (rc == PMH_OK) {
         finish_index_kernel<<<blocks, 256, 0, s>>>(keys, vals, n, counts, n_cells, P->seed, gbits,
-                                                    si.cell_start, si.idx, si.pts);
+                                                    si.cell_start, si.ent);
         g_pmh_launches.fetch_add(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "finish: %s", cudaGetErrorString(e));
@@ -134,14 +130,13 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
         rc = pmh_set_error(PMH_ERR_CUDA, "stream index build: %s", cudaGetErrorString(e2));
     if (rc != PMH_OK) {
         cudaFree(si.cell_start);
-        cudaFree(si.idx);
-        cudaFree(si.pts);
+        cudaFree(si.ent);
         si = StreamIndex();
         return rc;
     }
     si.seed = P->seed;
     si.K = (int)P->K;
-    *out = StreamIndexView{si.cell_start, si.idx, si.pts, M, gbits, shift};
+    *out = StreamIndexView{si.cell_start, si.ent, M, gbits, shift};
     return PMH_OK;
 }
 
