@@ -120,10 +120,8 @@ class Clocks:
 
 
 def dist_setup(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2511_16576_gb300 import dist as D
+    return D.env()
 
 
 def algorithmic_points(hashes_np: np.ndarray, T: int) -> int:
@@ -270,7 +268,8 @@ def main():
 
     dev = torch.device("cuda", local)
     # every rank signs its own shard of the same size (weak scaling)
-    gen_w = w if rank == 0 else synth.Workload(**{**w.__dict__, "gen_seed": w.gen_seed + 1000 * rank})
+    from paper_2511_16576_gb300 import dist as D
+    gen_w = D.shard_workload(w, rank)
     db = synth.make_database(gen_w, args.n_polys)
     qs = synth.make_queries(gen_w, db, args.n_queries)
     N, Q, K = db.n, qs.n, w.K
@@ -352,11 +351,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         launches = B.launch_count() - l0
-        ms = t0.elapsed_time(t1) / steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = D.max_over_ranks(t0.elapsed_time(t1) / steps, dev)
         return ms, launches, out
 
     clocks = Clocks(local)
