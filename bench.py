@@ -37,10 +37,11 @@ sys.path.insert(0, ROOT)
 #  stream-index entry read: index and point loads, limit compare, bbox test = 10;
 #  bbox candidate ordered (one warp argmin step) = 6;
 #  polygon edge tested: straddle test (3), two 32x32->64 products (4), difference (2),
-#    sign test and parity (3) = 12.
+#    sign test and parity (3) = 12;
+#  candidate decided by the coverage mask: cell address and code lookup = 6.
 INT_OPS_PER_POINT = 26
 SIGN_OP_WEIGHTS = {"walk_points": 26, "cells": 8, "index_entries": 10, "candidates": 6,
-                   "edge_tests": 12}
+                   "edge_tests": 12, "mask_decisions": 6}
 
 
 def parse():
@@ -284,7 +285,7 @@ def main():
         sample = db.subset(np.linspace(0, db.n - 1, max(1, min(db.n, 20000)), dtype=np.int64))
         sp = B.poly_upload(ctx, torch.from_numpy(sample.xy).to(dev),
                            torch.from_numpy(sample.offsets).to(dev))
-        best, ms = B.sign_autotune(ctx, sp, P, cache_key=f"{w.name}:{N}")
+        best, ms = B.sign_autotune(ctx, sp, P, cache_key=f"{w.name}:{N}:flags{P.flags}")
         autotune = {"variant": best, "points_per_lane_x_warps": B.sign_variant_info(best),
                     "sample_ms": [round(t, 3) for t in ms]}
         sp.close()

@@ -69,13 +69,20 @@ typedef struct pmh_index_s* pmh_index;
  *             1 <= bands <= 128
  *   rows      r, must equal K / bands
  *   lsh_seed  seed of the band-key fingerprint
- *   flags     0 or PMH_FLAG_STREAM_INDEX */
+ *   flags     0 or PMH_FLAG_STREAM_INDEX | PMH_FLAG_COVERAGE_MASK */
 /* pmh_params.flags: sign through the stream index (same hashes, much less
  * work for small polygons).  The first call with a given (seed, K) builds the
  * index of the first 65,536 points of each stream, bucketed by cell of a
  * 128 x 128 grid (K * 512 KiB of device memory, kept by the context; that
  * call synchronises); later calls reuse it. */
 #define PMH_FLAG_STREAM_INDEX 1u
+/* pmh_params.flags: decide bounding-box candidates through a per-polygon
+ * 16 x 16 coverage mask where it can (cells no edge touches are wholly inside
+ * or outside), running the exact edge test only in boundary cells.  Same
+ * hashes.  The masks are built on the first such call for a polygon set
+ * (64 bytes per polygon of up to 256 vertices) and kept with it; they pay off
+ * when a set is signed more than once. */
+#define PMH_FLAG_COVERAGE_MASK 2u
 
 typedef struct {
     uint64_t seed;
@@ -146,7 +153,9 @@ int pmh_stream_index_build(pmh_ctx ctx, const pmh_params* params, void* stream);
 /* Algorithmic work of the last pmh_minhash_sign call on this context
  * (synchronises): h_counts[0] stream points examined by walks (up to each
  * result), [1] grid cells read by the indexed form, [2] stream-index entries
- * read, [3] bounding-box candidates ordered, [4] polygon edges tested. */
+ * read, [3] bounding-box candidates ordered, [4] polygon edges tested,
+ * [5] candidates decided by a polygon's coverage mask without edge tests
+ * (h_counts holds 6 values). */
 int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts);
 
 /* A2 -- band keys (hashmap keys of Sec. 3.2 after Theorem 1, one per band).

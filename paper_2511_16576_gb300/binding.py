@@ -36,6 +36,7 @@ class Params(ctypes.Structure):
 
 
 FLAG_STREAM_INDEX = 1
+FLAG_COVERAGE_MASK = 2
 
 
 def make_params(K: int, bands: int, T: int = 1 << 24, seed: int = 0x5EED,
@@ -272,10 +273,10 @@ def sign_work(ctx: Context) -> dict:
     """Work units of the last signing call: walked points, cells, index entries,
     bbox candidates, edge tests."""
     import numpy as np
-    c = np.zeros(5, np.uint64)
+    c = np.zeros(6, np.uint64)
     _check(load().pmh_sign_work(ctx.handle, c.ctypes.data))
-    return dict(zip(("walk_points", "cells", "index_entries", "candidates", "edge_tests"),
-                    (int(v) for v in c)))
+    return dict(zip(("walk_points", "cells", "index_entries", "candidates", "edge_tests",
+                     "mask_decisions"), (int(v) for v in c)))
 
 
 def band_keys(ctx: Context, hashes: torch.Tensor, params: Params, out=None, stream=None):

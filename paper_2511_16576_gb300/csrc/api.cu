@@ -311,7 +311,7 @@ extern "C" int pmh_polys_destroy(pmh_polys p)
     cudaSetDevice(p->device);
     if (p->xy || p->offsets || p->bbox || p->area2) cudaDeviceSynchronize();
     void* bufs[] = {p->xy, p->offsets, p->bbox, p->area2, p->feat, p->slab_info, p->slab_ptr,
-                    p->slab_edges, p->order};
+                    p->slab_edges, p->order, p->mask};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete p;

@@ -108,9 +108,21 @@ struct pmh_polys_s {
     int32_t* slab_ptr = nullptr;
     int32_t* slab_edges = nullptr;
     int32_t* order = nullptr;       // polygons by expected signing cost, largest first
+    uint32_t* mask = nullptr;       // [n][16] coverage masks
 };
 
 int pmh_build_slabs(pmh_polys P, cudaStream_t s);
+int pmh_build_masks(pmh_polys P, cudaStream_t s);
+
+// coverage masks (masks.cu): 16 x 16 cells of 2^cwl x 2^chl lattice units over the
+// clipped bounding box; 2 bits per cell (0 outside, 1 inside, 2 boundary)
+constexpr int kMaskMaxVerts = 256;
+__host__ __device__ __forceinline__ int mask_cell_log2(int w)
+{
+    int a = (w + 15) >> 4, l = 0;
+    while ((1 << l) < a) ++l;
+    return l;
+}
 int pmh_build_cost_order(pmh_polys P, cudaStream_t s);
 
 struct pmh_index_s {
@@ -180,7 +192,7 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     const int32_t* order, const pmh_params* P, int64_t n_polys,
                     const int64_t* d_n, const int* d_flags, unsigned long long* ticket,
                     uint32_t* out, cudaStream_t s, const int64_t* area2 = nullptr,
-                    const StreamIndexView* sidx = nullptr);
+                    const StreamIndexView* sidx = nullptr, const uint32_t* masks = nullptr);
 int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
                      int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
                      int* d_flags, bool write, cudaStream_t s);

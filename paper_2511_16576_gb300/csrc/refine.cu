@@ -7,24 +7,25 @@
 // F(t) = dy * (x0 t + dx t^2 / 2) (x dy integrated from the edge start to
 // parameter t), an edge that starts inside contributes nothing at t = 0, every
 // crossing where it enters the other polygon contributes -F(t), every exit
-// +F(t), and an edge that ends inside adds F(1).  So each (edge, edge) pair is
-// independent and a block sums them in any order.
+// +F(t), and an edge that ends inside adds F(1).  Every term is independent,
+// so one warp sums them for one pair in any order: each crossing of an A edge
+// with a B edge is met once and adds both edges' terms with one division, and
+// the "ends inside" state of an edge is the start state of the next edge.
 //
 // Degenerate contacts (a vertex on an edge, overlapping collinear edges,
 // identical polygons) are resolved by simulation of simplicity: A is taken as
 // shifted by (e1, e2), 0 < e2 << e1 infinitesimal.  Every predicate is then
 // decided exactly with int64 cross products (coordinates <= 2^20), and the
-// area of the shifted configuration tends to the exact one.  Crossing
-// parameters and the integrals are fp64 in coordinates relative to B's first
-// vertex.
+// area of the shifted configuration tends to the exact one.  The terms are
+// fp64 in coordinates relative to B's first vertex.  GB300's fp64 rate is low,
+// so the fp64 work is kept to the crossings (a few per edge) and one division
+// each.
 #include <algorithm>
 
 #include "pmh_internal.cuh"
 
 namespace {
 
-constexpr int kRefineThreads = 128;
-constexpr int kSmemVerts = 4096;  // both polygons staged when n_a + n_b fits
 
 __device__ __forceinline__ long long cross3(int2 o, int2 a, int2 b)
 {
@@ -51,99 +52,86 @@ __device__ __forceinline__ int side_of_point_to_shifted(int2 a, int2 b, int2 q)
     return dx > 0 ? -1 : 1;
 }
 
-__device__ __forceinline__ double Fint(double x0, double dx, double dy, double t)
-{
-    return dy * (x0 * t + 0.5 * dx * t * t);
-}
-
-__device__ __forceinline__ bool boxes_touch(int2 a, int2 b, int2 c, int2 d)
-{
-    return max(min(a.x, b.x), min(c.x, d.x)) <= min(max(a.x, b.x), max(c.x, d.x)) &&
-           max(min(a.y, b.y), min(c.y, d.y)) <= min(max(a.y, b.y), max(c.y, d.y));
-}
-
-__device__ double block_sum(double v, double* sh)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double t = 0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    return t;  // valid in thread 0
-}
-
-// area(A n B) for one pair, by the whole block; valid in thread 0
-__device__ double intersection_area(const int2* __restrict__ A, int na, int sA,
-                                    const int2* __restrict__ B, int nb, int sB, double* sh)
+// area(A n B) for one pair, by one warp; returned in every lane.
+//  * end terms: edge e_i of the shifted A ends inside B iff its end vertex
+//    a_{i+1} + e is inside B (the start state of the next edge), so each lane
+//    tests its vertices and adds F(1) of the edge that ends there -- no crossing
+//    parity per edge is needed; likewise for B's edges and A + e;
+//  * crossings: each (A edge, B edge) pair that crosses is visited by one lane,
+//    which adds both boundary terms with one division: with D = de x df,
+//    t = Nt / D on e and u = Nu / D on f (Nt, Nu, D exact integers),
+//    F_e(t) + F_f(u) = [dy Nt (x0e D + dx Nt / 2) +- ey Nu (x0f D + ex Nu / 2)] / D^2.
+__device__ double warp_intersection_area(const int2* __restrict__ A, int na, int sA,
+                                         const int2* __restrict__ B, int nb, int sB, int lane)
 {
     const int2 org = B[0];
     double acc = 0;
-    // pieces of A's (shifted) edges inside B
-    for (int i = threadIdx.x; i < na; i += blockDim.x) {
-        int2 a = A[i], b = A[i + 1 == na ? 0 : i + 1];
-        if (a.x == b.x && a.y == b.y) continue;
-        double x0 = (double)(a.x - org.x), dx = (double)(b.x - a.x), dy = (double)(b.y - a.y);
-        unsigned start_in = 0, ncross = 0;
-        double s = 0;
+    // end terms of A's edges: vertex a_i + e inside B closes edge i-1
+    for (int i = lane; i < na; i += 32) {
+        const int2 a = A[i];
+        unsigned in = 0;
         for (int j = 0; j < nb; ++j) {
-            int2 c = B[j], d = B[j + 1 == nb ? 0 : j + 1];
-            // a + e inside B: half-open crossing rule for the point a
+            const int2 c = B[j], d = B[j + 1 == nb ? 0 : j + 1];
             if ((c.y > a.y) != (d.y > a.y)) {
-                long long cr = cross3(c, d, a);
-                start_in ^= (cr != 0) & ((cr > 0) == (d.y > c.y));
+                const long long cr = cross3(c, d, a);
+                in ^= (cr != 0) & ((cr > 0) == (d.y > c.y));
             }
-            if (!boxes_touch(a, b, c, d) || (c.x == d.x && c.y == d.y)) continue;
-            int s1 = side_of_shifted_point(c, d, a), s2 = side_of_shifted_point(c, d, b);
-            if (s1 == s2) continue;
-            int s3 = side_of_point_to_shifted(a, b, c), s4 = side_of_point_to_shifted(a, b, d);
-            if (s3 == s4) continue;
-            double ex = (double)(d.x - c.x), ey = (double)(d.y - c.y);
-            double den = dx * ey - dy * ex;
-            double t = ((double)(c.x - a.x) * ey - (double)(c.y - a.y) * ex) / den;
-            t = fmin(fmax(t, 0.0), 1.0);
-            bool entering = (s2 > 0) == (sB > 0);
-            double f = Fint(x0, dx, dy, t);
-            s += entering ? -f : f;
-            ++ncross;
         }
-        if ((start_in ^ (ncross & 1u)) != 0) s += Fint(x0, dx, dy, 1.0);
-        acc += sA > 0 ? s : -s;
+        if (in) {
+            const int2 p = A[i == 0 ? na - 1 : i - 1];
+            const double x0 = (double)(p.x - org.x), dx = (double)(a.x - p.x), dy = (double)(a.y - p.y);
+            acc += (sA > 0 ? 1.0 : -1.0) * dy * (x0 + 0.5 * dx);
+        }
     }
-    // pieces of B's edges inside the shifted A
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        int2 c = B[j], d = B[j + 1 == nb ? 0 : j + 1];
-        if (c.x == d.x && c.y == d.y) continue;
-        double x0 = (double)(c.x - org.x), ex = (double)(d.x - c.x), ey = (double)(d.y - c.y);
-        unsigned start_in = 0, ncross = 0;
-        double s = 0;
+    // end terms of B's edges: vertex c_j - e inside A closes edge j-1
+    for (int j = lane; j < nb; j += 32) {
+        const int2 c = B[j];
+        unsigned in = 0;
         for (int i = 0; i < na; ++i) {
-            int2 a = A[i], b = A[i + 1 == na ? 0 : i + 1];
-            // c - e inside A
+            const int2 a = A[i], b = A[i + 1 == na ? 0 : i + 1];
             if ((a.y >= c.y) != (b.y >= c.y)) {
-                long long cr = cross3(a, b, c);
-                start_in ^= (cr == 0) | ((cr > 0) == (b.y > a.y));
+                const long long cr = cross3(a, b, c);
+                in ^= (cr == 0) | ((cr > 0) == (b.y > a.y));
             }
-            if (!boxes_touch(a, b, c, d) || (a.x == b.x && a.y == b.y)) continue;
-            int s1 = side_of_shifted_point(c, d, a), s2 = side_of_shifted_point(c, d, b);
-            if (s1 == s2) continue;
-            int s3 = side_of_point_to_shifted(a, b, c), s4 = side_of_point_to_shifted(a, b, d);
-            if (s3 == s4) continue;
-            double dx = (double)(b.x - a.x), dy = (double)(b.y - a.y);
-            double den = dx * ey - dy * ex;
-            double u = ((double)(c.x - a.x) * dy - (double)(c.y - a.y) * dx) / den;
-            u = fmin(fmax(u, 0.0), 1.0);
-            bool entering = (s4 > 0) == (sA > 0);
-            double f = Fint(x0, ex, ey, u);
-            s += entering ? -f : f;
-            ++ncross;
         }
-        if ((start_in ^ (ncross & 1u)) != 0) s += Fint(x0, ex, ey, 1.0);
-        acc += sB > 0 ? s : -s;
+        if (in) {
+            const int2 p = B[j == 0 ? nb - 1 : j - 1];
+            const double x0 = (double)(p.x - org.x), ex = (double)(c.x - p.x), ey = (double)(c.y - p.y);
+            acc += (sB > 0 ? 1.0 : -1.0) * ey * (x0 + 0.5 * ex);
+        }
     }
-    return block_sum(acc, sh);
+    // crossings
+    for (int i = lane; i < na; i += 32) {
+        const int2 a = A[i], b = A[i + 1 == na ? 0 : i + 1];
+        if (a.x == b.x && a.y == b.y) continue;
+        const int ax0 = min(a.x, b.x), ax1 = max(a.x, b.x), ay0 = min(a.y, b.y), ay1 = max(a.y, b.y);
+        const long long dx = b.x - a.x, dy = b.y - a.y;
+        for (int j = 0; j < nb; ++j) {
+            const int2 c = B[j], d = B[j + 1 == nb ? 0 : j + 1];
+            if (max(ax0, min(c.x, d.x)) > min(ax1, max(c.x, d.x)) ||
+                max(ay0, min(c.y, d.y)) > min(ay1, max(c.y, d.y)) || (c.x == d.x && c.y == d.y))
+                continue;
+            const int s1 = side_of_shifted_point(c, d, a), s2 = side_of_shifted_point(c, d, b);
+            if (s1 == s2) continue;
+            const int s3 = side_of_point_to_shifted(a, b, c), s4 = side_of_point_to_shifted(a, b, d);
+            if (s3 == s4) continue;
+            const long long ex = d.x - c.x, ey = d.y - c.y;
+            const long long D = dx * ey - dy * ex;
+            const long long Nt = (long long)(c.x - a.x) * ey - (long long)(c.y - a.y) * ex;
+            const long long Nu = (long long)(c.x - a.x) * dy - (long long)(c.y - a.y) * dx;
+            const double Dd = (double)D;
+            // A's edge: entering B flips the sign; B's edge: entering the shifted A
+            const double sa = (((s2 > 0) == (sB > 0)) ? -1.0 : 1.0) * (sA > 0 ? 1.0 : -1.0);
+            const double sb = (((s4 > 0) == (sA > 0)) ? -1.0 : 1.0) * (sB > 0 ? 1.0 : -1.0);
+            const double fa = (double)dy * (double)Nt *
+                              ((double)(a.x - org.x) * Dd + 0.5 * (double)dx * (double)Nt);
+            const double fb = (double)ey * (double)Nu *
+                              ((double)(c.x - org.x) * Dd + 0.5 * (double)ex * (double)Nu);
+            acc += (sa * fa + sb * fb) / (Dd * Dd);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
 }
 
 struct PairView {
@@ -166,35 +154,39 @@ __device__ __forceinline__ PairView view(const int2* xy, const int64_t* off, con
     return r;
 }
 
-// stage both polygons in shared memory when they fit, then compute J
-__device__ double pair_jaccard(PairView A, PairView B, int2* sv, double* sh)
+constexpr int kRefineWarps = 8;
+constexpr int kWarpVerts = 512;  // both polygons staged per warp when they fit
+
+// J of one pair by one warp (vertices staged in the warp's shared slice when they fit)
+__device__ double warp_pair_jaccard(PairView A, PairView B, int2* sv, int lane)
 {
     if (A.sgn == 0 || B.sgn == 0) return 0.0;
     const int2* a = A.v;
     const int2* b = B.v;
-    if (A.n + B.n <= kSmemVerts) {
-        for (int i = threadIdx.x; i < A.n; i += blockDim.x) sv[i] = A.v[i];
-        for (int i = threadIdx.x; i < B.n; i += blockDim.x) sv[A.n + i] = B.v[i];
-        __syncthreads();
+    if (A.n + B.n <= kWarpVerts) {
+        for (int i = lane; i < A.n; i += 32) sv[i] = A.v[i];
+        for (int i = lane; i < B.n; i += 32) sv[A.n + i] = B.v[i];
+        __syncwarp();
         a = sv;
         b = sv + A.n;
     }
-    double inter = intersection_area(a, A.n, A.sgn, b, B.n, B.sgn, sh);
-    __syncthreads();
-    double uni = A.area + B.area - inter;
+    const double inter = warp_intersection_area(a, A.n, A.sgn, b, B.n, B.sgn, lane);
+    __syncwarp();
+    const double uni = A.area + B.area - inter;
     return uni > 0 ? fmin(fmax(inter / uni, 0.0), 1.0) : 0.0;
 }
 
-__global__ void __launch_bounds__(kRefineThreads)
+__global__ void __launch_bounds__(kRefineWarps * 32)
 refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qoff,
                     const int64_t* __restrict__ qarea2, const int2* __restrict__ pxy,
                     const int64_t* __restrict__ poff, const int64_t* __restrict__ parea2,
                     const int32_t* __restrict__ ids, const int32_t* __restrict__ nlist, int m,
                     const int32_t* __restrict__ qid_list, int64_t n_pairs, double* __restrict__ out)
 {
-    __shared__ int2 sv[kSmemVerts];
-    __shared__ double sh[kRefineThreads / 32];
-    for (int64_t e = blockIdx.x; e < n_pairs; e += gridDim.x) {
+    __shared__ int2 sv[kRefineWarps][kWarpVerts];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * kRefineWarps;
+    for (int64_t e = (int64_t)blockIdx.x * kRefineWarps + wid; e < n_pairs; e += nw) {
         int64_t q;
         int32_t p;
         if (qid_list) {  // explicit pairs
@@ -202,16 +194,16 @@ refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qo
             p = ids[e];
         } else {         // top-m lists: pair e = (q, slot)
             q = e / m;
-            int slot = (int)(e - q * m);
+            const int slot = (int)(e - q * m);
             if (slot >= nlist[q]) {
-                if (threadIdx.x == 0) out[e] = -1.0;
+                if (lane == 0) out[e] = -1.0;
                 continue;
             }
             p = ids[e];
         }
-        double j = pair_jaccard(view(qxy, qoff, qarea2, q), view(pxy, poff, parea2, p), sv, sh);
-        if (threadIdx.x == 0) out[e] = j;
-        __syncthreads();
+        const double j = warp_pair_jaccard(view(qxy, qoff, qarea2, q), view(pxy, poff, parea2, p),
+                                           sv[wid], lane);
+        if (lane == 0) out[e] = j;
     }
 }
 
@@ -281,8 +273,9 @@ extern "C" int pmh_refine_topk(pmh_ctx ctx, pmh_polys queries, pmh_polys db, con
     double* jv = nullptr;
     PMH_TRY(pmh_scratch(ctx, SCR_REFINE, sizeof(double) * (size_t)(Q * m), (void**)&jv));
     int64_t n_pairs = Q * m;
-    int blocks = (int)std::min<int64_t>(n_pairs, (int64_t)ctx->sm_count * 16);
-    refine_pairs_kernel<<<blocks, kRefineThreads, 0, s>>>(
+    int blocks = (int)std::min<int64_t>((n_pairs + kRefineWarps - 1) / kRefineWarps,
+                                        (int64_t)ctx->sm_count * 8);
+    refine_pairs_kernel<<<blocks, kRefineWarps * 32, 0, s>>>(
         queries->xy, queries->offsets, queries->area2, db->xy, db->offsets, db->area2, d_ids, d_n, m,
         nullptr, n_pairs, jv);
     PMH_LAUNCHED("refine_pairs_kernel");
@@ -302,8 +295,9 @@ extern "C" int pmh_pair_jaccard(pmh_ctx ctx, pmh_polys queries, pmh_polys db, co
         return pmh_set_error(PMH_ERR_ARG, "bad arguments");
     if (n_pairs == 0) return PMH_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    int blocks = (int)std::min<int64_t>(n_pairs, (int64_t)ctx->sm_count * 16);
-    refine_pairs_kernel<<<blocks, kRefineThreads, 0, s>>>(
+    int blocks = (int)std::min<int64_t>((n_pairs + kRefineWarps - 1) / kRefineWarps,
+                                        (int64_t)ctx->sm_count * 8);
+    refine_pairs_kernel<<<blocks, kRefineWarps * 32, 0, s>>>(
         queries->xy, queries->offsets, queries->area2, db->xy, db->offsets, db->area2, d_pid,
         nullptr, 1, d_qid, n_pairs, d_j);
     PMH_LAUNCHED("refine_pairs_kernel");

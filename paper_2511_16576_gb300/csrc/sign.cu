@@ -32,7 +32,7 @@ namespace {
 constexpr int kWarps = 8;        // warps per block
 constexpr int kSmemVerts = 256;  // vertices staged per warp (larger polygons read global)
 constexpr int kU = 4;            // points per lane per round
-constexpr int kWorkSlot = 8;     // context ticket slots 8..12: work counters of the last sign
+constexpr int kWorkSlot = 8;     // context ticket slots 8..13: work counters of the last sign
 
 // Exact half-open membership of lattice point (px, py), warp-cooperative.
 // Edge a->b counts iff (ay > py) != (by > py) and the int64 cross product
@@ -57,7 +57,7 @@ __device__ __forceinline__ bool warp_inside(const int2* __restrict__ v, int n, i
 // examined up to its result, grid cells and index entries read by the indexed
 // form, bbox candidates it ordered, and edges tested by the exact membership.
 struct Work {
-    unsigned long long walk = 0, cells = 0, entries = 0, cand = 0, edges = 0;
+    unsigned long long walk = 0, cells = 0, entries = 0, cand = 0, edges = 0, masked = 0;
 };
 
 // Exact membership through the polygon's y-slab index: only the edges listed
@@ -113,6 +113,25 @@ template <int U, class Inside>
 __device__ __forceinline__ uint32_t sign_walk(const Inside& inside, int x0, int y0, uint32_t w,
                                               uint32_t h, uint64_t sk, uint32_t T, int lane,
                                               Work& work, uint32_t start);
+
+// Membership through the polygon's coverage mask first: a candidate in a cell
+// that no edge touches is decided by the cell's code; only boundary cells run
+// the exact test.
+template <class Inner>
+struct Masked {
+    Inner inner;
+    const uint32_t* m;  // 16 words (row j), 2 bits per cell
+    int x0, y0, cwl, chl;
+    __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
+    {
+        const uint32_t code = (m[(py - y0) >> chl] >> (2 * ((px - x0) >> cwl))) & 3u;
+        if (code != 2u) {
+            w.masked += 1;
+            return code == 1u;
+        }
+        return inner(px, py, lane, w);
+    }
+};
 
 // One hash of one polygon; every lane returns the same value.  U points per
 // lane per round: one round covers 32 * U consecutive stream indices.
@@ -171,72 +190,101 @@ __device__ __forceinline__ uint32_t sign_one(const int2* __restrict__ v, int n, 
     return sign_one_t<kU>(AllEdges{v, n}, x0, y0, w, h, sk, T, lane, unused);
 }
 
-// Indexed form of one hash: the stream points of index < lim that fall in the
-// bounding box are read from the cells under it (kCand at most, else the full
-// walk), visited in index order by repeated warp argmin and tested exactly; the
-// first inside is h_k.  With none inside, the walk continues from lim.
+// Indexed form: the stream points of index < lim that fall in the bounding box
+// are read from the cells under it (kCand per hash at most, else the full walk).
 constexpr int kCand = 64;
 
+// Indexed form of the hashes k0 .. kend-1, four at a time: each group of eight
+// lanes gathers one hash's candidates from the cells under the bounding box
+// (four independent chains of index reads in flight per warp), then the warp
+// resolves the four hashes one after the other: candidates in index order by
+// repeated warp argmin, exact test, walk resumed at lim if none is inside.
 template <int U, class Inside>
-__device__ uint32_t sign_one_indexed(const Inside& inside, const StreamIndexView& S, int k,
-                                     uint64_t sk, int4 bb, uint32_t w, uint32_t h, uint32_t lim,
-                                     uint32_t T, uint2* cbuf, int* ccount, int lane, Work& work)
+__device__ uint32_t sign_chunk_indexed(const Inside& inside, const StreamIndexView& S, int4 bb,
+                                       uint64_t seed, int k0, int kend, uint32_t T, uint32_t lim,
+                                       uint2* cbuf /* [4][kCand] */, int* ccount /* [4] */,
+                                       int lane, Work& work)
 {
+    const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
     lim = min(lim, T);
     const int cx0 = bb.x >> S.shift, cx1 = (bb.z - 1) >> S.shift;
     const int cy0 = bb.y >> S.shift, cy1 = (bb.w - 1) >> S.shift;
     const int ncx = cx1 - cx0 + 1, C = ncx * (cy1 - cy0 + 1);
-    const uint32_t* cs = S.cell_start + ((int64_t)k << (2 * S.gbits));
-    if (lane == 0) *ccount = 0;
-    __syncwarp();
-    int read = 0;
-    for (int c = lane; c < C; c += 32) {
-        const int cell = ((cy0 + c / ncx) << S.gbits) | (cx0 + c % ncx);
-        const uint32_t beg = cs[cell], end = cs[cell + 1];
-        // entries four at a time: independent 8-byte loads in flight together
-        for (uint32_t e = beg; e < end; e += 4) {
-            uint2 q[4];
+    const int g = lane >> 3, gl = lane & 7;
+    uint32_t mine = T;
+    for (int kb = k0; kb < kend; kb += 4) {
+        if (lane < 4) ccount[lane] = 0;
+        __syncwarp();
+        const int k = kb + g;
+        int read = 0;
+        if (k < kend) {
+            const uint32_t* cs = S.cell_start + ((int64_t)k << (2 * S.gbits));
+            uint2* cb = cbuf + g * kCand;
+            for (int c = gl; c < C; c += 8) {
+                const int cell = ((cy0 + c / ncx) << S.gbits) | (cx0 + c % ncx);
+                const uint32_t beg = cs[cell], end = cs[cell + 1];
+                for (uint32_t e = beg; e < end; e += 4) {
+                    uint2 q[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) q[u] = e + u < end ? S.ent[e + u] : make_uint2(0xFFFFFFFFu, 0u);
-            bool stop = false;
+                    for (int u = 0; u < 4; ++u)
+                        q[u] = e + u < end ? S.ent[e + u] : make_uint2(0xFFFFFFFFu, 0u);
+                    bool stop = false;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (stop || e + u >= end) break;
-                ++read;
-                if (q[u].x >= lim) {
-                    stop = true;
-                    break;
-                }
-                const uint32_t r = q[u].y;
-                if (((r & 0xFFFFu) - (uint32_t)bb.x) < w && ((r >> 16) - (uint32_t)bb.y) < h) {
-                    const int slot = atomicAdd(ccount, 1);
-                    if (slot < kCand) cbuf[slot] = make_uint2(q[u].x, r);
+                    for (int u = 0; u < 4; ++u) {
+                        if (stop || e + u >= end) break;
+                        ++read;
+                        if (q[u].x >= lim) {
+                            stop = true;
+                            break;
+                        }
+                        const uint32_t r = q[u].y;
+                        if (((r & 0xFFFFu) - (uint32_t)bb.x) < w && ((r >> 16) - (uint32_t)bb.y) < h) {
+                            const int slot = atomicAdd(&ccount[g], 1);
+                            if (slot < kCand) cb[slot] = make_uint2(q[u].x, r);
+                        }
+                    }
+                    if (stop) break;
                 }
             }
-            if (stop) break;
         }
-    }
-    __syncwarp();
-    const int n = *ccount;
-    work.cells += C;
-    work.entries += __reduce_add_sync(0xffffffffu, read);
-    work.cand += min(n, kCand);
-    if (n > kCand) return sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, work, 0);
-    uint2 c0 = lane < n ? cbuf[lane] : make_uint2(0xFFFFFFFFu, 0u);
-    uint2 c1 = lane + 32 < n ? cbuf[lane + 32] : make_uint2(0xFFFFFFFFu, 0u);
-    for (int t = 0; t < n; ++t) {
-        const uint32_t best = __reduce_min_sync(0xffffffffu, min(c0.x, c1.x));
-        const unsigned who = __ballot_sync(0xffffffffu, c0.x == best || c1.x == best);
-        const int src = __ffs(who) - 1;
-        const uint32_t r = __shfl_sync(0xffffffffu, c0.x == best ? c0.y : c1.y, src);
-        if (inside((int)(r & 0xFFFFu), (int)(r >> 16), lane, work)) return best;
-        if (lane == src) {
-            if (c0.x == best) c0.x = 0xFFFFFFFFu;
-            else c1.x = 0xFFFFFFFFu;
+        work.entries += __reduce_add_sync(0xffffffffu, read);
+        __syncwarp();
+        const int nk = min(4, kend - kb);
+        work.cells += (unsigned long long)C * nk;
+        for (int j = 0; j < nk; ++j) {
+            const int kk = kb + j;
+            const int n = ccount[j];
+            const uint64_t sk = pmh_mix64(seed + (uint64_t)(kk + 1) * PMH_GAMMA);
+            uint32_t hk = 0xFFFFFFFFu;
+            work.cand += min(n, kCand);
+            if (n > kCand) {
+                hk = sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, work, 0);
+            } else {
+                const uint2* cb = cbuf + j * kCand;
+                uint2 c0 = lane < n ? cb[lane] : make_uint2(0xFFFFFFFFu, 0u);
+                uint2 c1 = lane + 32 < n ? cb[lane + 32] : make_uint2(0xFFFFFFFFu, 0u);
+                for (int t = 0; t < n; ++t) {
+                    const uint32_t best = __reduce_min_sync(0xffffffffu, min(c0.x, c1.x));
+                    const unsigned who = __ballot_sync(0xffffffffu, c0.x == best || c1.x == best);
+                    const int src = __ffs(who) - 1;
+                    const uint32_t r = __shfl_sync(0xffffffffu, c0.x == best ? c0.y : c1.y, src);
+                    if (inside((int)(r & 0xFFFFu), (int)(r >> 16), lane, work)) {
+                        hk = best;
+                        break;
+                    }
+                    if (lane == src) {
+                        if (c0.x == best) c0.x = 0xFFFFFFFFu;
+                        else c1.x = 0xFFFFFFFFu;
+                    }
+                }
+                if (hk == 0xFFFFFFFFu)
+                    hk = lim >= T ? T : sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, work, lim);
+            }
+            if (lane == kk - k0) mine = hk;
         }
+        __syncwarp();
     }
-    if (lim >= T) return T;
-    return sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, work, lim);
+    return mine;
 }
 
 // the hashes k0 .. k0+31 of one polygon; lane j returns hash k0 + j.  lim > 0
@@ -247,13 +295,12 @@ __device__ __forceinline__ uint32_t sign_chunk(const Inside& inside, int4 bb, ui
                                                const StreamIndexView& S, uint32_t lim,
                                                uint2* cbuf, int* ccount, Work& work)
 {
+    if (lim) return sign_chunk_indexed<U>(inside, S, bb, seed, k0, kend, T, lim, cbuf, ccount, lane, work);
     const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
     uint32_t mine = T;
     for (int k = k0; k < kend; ++k) {
         uint64_t sk = pmh_mix64(seed + (uint64_t)(k + 1) * PMH_GAMMA);
-        uint32_t hk = lim ? sign_one_indexed<U>(inside, S, k, sk, bb, w, h, lim, T, cbuf, ccount, lane,
-                                                work)
-                          : sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, work);
+        uint32_t hk = sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, work);
         if (lane == k - k0) mine = hk;
     }
     return mine;
@@ -289,14 +336,15 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
             int64_t n_polys, const int64_t* __restrict__ d_n, const int* __restrict__ d_flags,
             unsigned long long* __restrict__ ticket, uint32_t* __restrict__ out,
             const int64_t* __restrict__ area2, StreamIndexView S,
-            unsigned long long* __restrict__ work_out)
+            unsigned long long* __restrict__ work_out, const uint32_t* __restrict__ masks)
 {
     __shared__ __align__(16) int2 sv[W][kSmemVerts];
-    __shared__ uint2 cbuf[W][kCand];
-    __shared__ int ccount[W];
-    __shared__ unsigned long long wsum[5];
+    __shared__ uint2 cbuf[W][4 * kCand];
+    __shared__ int ccount[W][4];
+    __shared__ uint32_t smask[W][16];
+    __shared__ unsigned long long wsum[6];
     Work work;
-    if (threadIdx.x < 5) wsum[threadIdx.x] = 0;
+    if (threadIdx.x < 6) wsum[threadIdx.x] = 0;
     __syncthreads();
     if (d_flags && *d_flags) return;  // the batch failed validation
     if (d_n) n_polys = min(n_polys, *d_n);
@@ -317,20 +365,28 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
         const int4 bb = bbox[p];
         const uint32_t lim = area2 ? indexed_limit(S, bb, area2[p]) : 0;
         uint32_t mine;
-        if (n <= kSmemVerts) {
+        if (n <= kSmemVerts && masks) {
+            // stage the vertices and the coverage mask in this warp's shared-memory slice
+            for (int i = lane; i < n; i += 32) sv[wid][i] = xy[b + i];
+            if (lane < 16) smask[wid][lane] = masks[p * 16 + lane];
+            __syncwarp();
+            const Masked<AllEdges> in{AllEdges{sv[wid], n}, smask[wid], bb.x, bb.y,
+                                      mask_cell_log2(bb.z - bb.x), mask_cell_log2(bb.w - bb.y)};
+            mine = sign_chunk<U>(in, bb, seed, k0, kend, T, lane, S, lim, cbuf[wid], ccount[wid], work);
+        } else if (n <= kSmemVerts) {
             // stage the vertices in this warp's shared-memory slice (coalesced 8-byte loads)
             for (int i = lane; i < n; i += 32) sv[wid][i] = xy[b + i];
             __syncwarp();
             mine = sign_chunk<U>(AllEdges{sv[wid], n}, bb, seed, k0, kend, T, lane, S, lim,
-                                 cbuf[wid], &ccount[wid], work);
+                                 cbuf[wid], ccount[wid], work);
         } else if (slabs && slabs[p].S > 0) {
             const SlabInfo si = slabs[p];
             mine = sign_chunk<U>(SlabEdges{xy + b, n, slab_ptr + si.slab_base,
                                            slab_edges + si.edge_base, si.slab_h, si.ymin},
-                                 bb, seed, k0, kend, T, lane, S, lim, cbuf[wid], &ccount[wid], work);
+                                 bb, seed, k0, kend, T, lane, S, lim, cbuf[wid], ccount[wid], work);
         } else {
             mine = sign_chunk<U>(AllEdges{xy + b, n}, bb, seed, k0, kend, T, lane, S, lim,
-                                 cbuf[wid], &ccount[wid], work);
+                                 cbuf[wid], ccount[wid], work);
         }
         if (k0 + lane < kend) out[p * (int64_t)K + k0 + lane] = mine;
         __syncwarp();
@@ -342,24 +398,26 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
             atomicAdd(&wsum[2], work.entries);
             atomicAdd(&wsum[3], work.cand);
             atomicAdd(&wsum[4], work.edges);
+            atomicAdd(&wsum[5], work.masked);
         }
         __syncthreads();
-        if (threadIdx.x < 5) atomicAdd(&work_out[threadIdx.x], wsum[threadIdx.x]);
+        if (threadIdx.x < 6) atomicAdd(&work_out[threadIdx.x], wsum[threadIdx.x]);
     }
 }
 
 using SignFn = void (*)(const int2*, const int64_t*, const int4*, const SlabInfo*, const int32_t*,
                         const int32_t*, const int32_t*, uint64_t, int, uint32_t, int, int64_t,
                         const int64_t*, const int*, unsigned long long*, uint32_t*, const int64_t*,
-                        StreamIndexView, unsigned long long*);
+                        StreamIndexView, unsigned long long*, const uint32_t*);
 struct SignVariant {
     int U, W;
     SignFn fn;
 };
 // index 0 is the default; the autotuner may pick any of them
+// (static shared memory per block stays below 48 KiB: 8 warps at most)
 const SignVariant kSignVariants[] = {
-    {4, 8, sign_kernel<4, 8>},  {2, 8, sign_kernel<2, 8>},   {8, 8, sign_kernel<8, 8>},
-    {4, 4, sign_kernel<4, 4>},  {4, 16, sign_kernel<4, 16>}, {2, 16, sign_kernel<2, 16>},
+    {4, 8, sign_kernel<4, 8>}, {2, 8, sign_kernel<2, 8>}, {8, 8, sign_kernel<8, 8>},
+    {4, 4, sign_kernel<4, 4>}, {2, 4, sign_kernel<2, 4>}, {1, 8, sign_kernel<1, 8>},
 };
 constexpr int kNumSignVariants = sizeof(kSignVariants) / sizeof(kSignVariants[0]);
 
@@ -378,7 +436,7 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     const int32_t* order, const pmh_params* P, int64_t n_polys,
                     const int64_t* d_n, const int* d_flags, unsigned long long* ticket,
                     uint32_t* out, cudaStream_t s, const int64_t* area2,
-                    const StreamIndexView* sidx)
+                    const StreamIndexView* sidx, const uint32_t* masks)
 {
     const StreamIndexView S = sidx ? *sidx : StreamIndexView{nullptr, nullptr, 0, 0, 0};
     if (n_polys <= 0) return PMH_OK;
@@ -391,10 +449,10 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
     blocks = std::min<int64_t>(blocks, (n_items + v.W - 1) / v.W);
     PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
     unsigned long long* work = d_n ? nullptr : ctx->d_tickets + kWorkSlot;
-    if (work) PMH_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long) * 5, s));
+    if (work) PMH_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long) * 6, s));
     v.fn<<<(int)blocks, v.W * 32, 0, s>>>(xy, off, bbox, slabs, slab_ptr, slab_edges, order,
                                           P->seed, (int)P->K, P->T, chunks, n_polys, d_n, d_flags,
-                                          ticket, out, area2, S, work);
+                                          ticket, out, area2, S, work, masks);
     PMH_LAUNCHED("sign_kernel");
     return PMH_OK;
 }
@@ -409,11 +467,13 @@ extern "C" int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* 
     if (polys->n == 0) return PMH_OK;
     StreamIndexView sidx;
     const bool indexed = (params->flags & PMH_FLAG_STREAM_INDEX) != 0;
+    const bool masked = (params->flags & PMH_FLAG_COVERAGE_MASK) != 0;
     if (indexed) PMH_TRY(pmh_stream_index_get(ctx, params, (cudaStream_t)stream, &sidx));
+    if (masked && !polys->mask) PMH_TRY(pmh_build_masks(polys, (cudaStream_t)stream));
     return pmh_launch_sign(ctx, polys->xy, polys->offsets, polys->bbox, polys->slab_info,
                            polys->slab_ptr, polys->slab_edges, polys->order, params, polys->n,
                            nullptr, nullptr, ctx->d_tickets + 0, d_hashes, (cudaStream_t)stream,
-                           polys->area2, indexed ? &sidx : nullptr);
+                           polys->area2, indexed ? &sidx : nullptr, masked ? polys->mask : nullptr);
 }
 
 extern "C" int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts)
@@ -421,7 +481,7 @@ extern "C" int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts)
     PMH_TRY(pmh_check_device(ctx));
     if (!h_counts) return pmh_set_error(PMH_ERR_ARG, "null output");
     PMH_CUDA_TRY(cudaDeviceSynchronize());
-    PMH_CUDA_TRY(cudaMemcpy(h_counts, ctx->d_tickets + kWorkSlot, sizeof(uint64_t) * 5,
+    PMH_CUDA_TRY(cudaMemcpy(h_counts, ctx->d_tickets + kWorkSlot, sizeof(uint64_t) * 6,
                             cudaMemcpyDeviceToHost));
     return PMH_OK;
 }
@@ -469,12 +529,15 @@ extern "C" int pmh_sign_autotune(pmh_ctx ctx, pmh_polys sample, const pmh_params
             cudaEventRecord(e0, 0);
             StreamIndexView sidx;
             const bool indexed = (params->flags & PMH_FLAG_STREAM_INDEX) != 0;
+            const bool masked = (params->flags & PMH_FLAG_COVERAGE_MASK) != 0;
             if (indexed) rc = pmh_stream_index_get(ctx, params, 0, &sidx);
+            if (rc == PMH_OK && masked && !sample->mask) rc = pmh_build_masks(sample, 0);
             if (rc == PMH_OK)
                 rc = pmh_launch_sign(ctx, sample->xy, sample->offsets, sample->bbox, sample->slab_info,
                                      sample->slab_ptr, sample->slab_edges, sample->order, params,
                                      sample->n, nullptr, nullptr, ctx->d_tickets + 1, out, 0,
-                                     sample->area2, indexed ? &sidx : nullptr);
+                                     sample->area2, indexed ? &sidx : nullptr,
+                                     masked ? sample->mask : nullptr);
             cudaEventRecord(e1, 0);
             if (cudaEventSynchronize(e1) != cudaSuccess)
                 rc = pmh_set_error(PMH_ERR_CUDA, "autotune run failed");

@@ -74,7 +74,7 @@ def test_upload_rejects_bad_input(B, ctx):
         upload(B, ctx, ps)
 
 
-FLAGS = [0, 1]   # 1 = signing through the stream index
+FLAGS = [0, 1, 3]   # 1 = signing through the stream index, 2 = through coverage masks
 
 
 @pytest.mark.parametrize("flags", FLAGS)
@@ -371,3 +371,18 @@ def test_bbox_join_and_brute_force_truth(B, ctx, orc, small):
             assert abs(truth.j[q, s] - jr) <= 1e-9 * jr + 1e-12
     # the exact search finds itself: recall of the truth against itself is 1
     assert ev.recall_at_k(truth.ids, truth.j, truth, 10) == 1.0
+
+
+def test_pair_jaccard_large_polygons(B, ctx, orc):
+    """Pairs too large for the warp's shared slice (global-memory path of the refinement)."""
+    big = synth.star_polygons(3, 23, (300, 1500), "uniform", (2e-3, 4e-3), fractal=True)
+    qs = synth.perturbed_queries(big, 3, 24)
+    dbp, qp = upload(B, ctx, big), upload(B, ctx, qs)
+    qid = np.array([0, 1, 2, 0], np.int32)
+    pid = np.array([int(qs.source[0]), int(qs.source[1]), int(qs.source[2]), 1], np.int32)
+    j = B.pair_jaccard(ctx, qp, dbp, torch.from_numpy(qid).to(DEV), torch.from_numpy(pid).to(DEV))
+    j = j.cpu().numpy()
+    for e in range(len(qid)):
+        ref = orc.jaccard(qs.poly(int(qid[e])), big.poly(int(pid[e])))
+        assert abs(j[e] - ref) <= 1e-9 * max(ref, 1e-300) + 1e-12, (e, j[e], ref)
+    assert j[0] > 0.5
