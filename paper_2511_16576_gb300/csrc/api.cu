@@ -110,7 +110,7 @@ extern "C" int pmh_destroy(pmh_ctx ctx)
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->d_tickets) cudaFree(ctx->d_tickets);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
-    if (ctx->sindex.cell_start) cudaFree(ctx->sindex.cell_start);
+    if (ctx->sindex.cell) cudaFree(ctx->sindex.cell);
     if (ctx->sindex.ent) cudaFree(ctx->sindex.ent);
     delete ctx;
     return PMH_OK;
@@ -311,7 +311,7 @@ extern "C" int pmh_polys_destroy(pmh_polys p)
     cudaSetDevice(p->device);
     if (p->xy || p->offsets || p->bbox || p->area2) cudaDeviceSynchronize();
     void* bufs[] = {p->xy, p->offsets, p->bbox, p->area2, p->feat, p->slab_info, p->slab_ptr,
-                    p->slab_edges, p->order, p->mask};
+                    p->slab_edges, p->order, p->order_cls, p->mask};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete p;

@@ -15,27 +15,9 @@
 // vertices) get a mask; the others keep the exact test for every candidate.
 #include <algorithm>
 
-#include "pmh_internal.cuh"
+#include "sign_common.cuh"
 
 namespace {
-
-__device__ __forceinline__ long long orient(int2 a, int2 b, long long px, long long py)
-{
-    return (long long)(b.x - a.x) * (py - a.y) - (long long)(b.y - a.y) * (px - a.x);
-}
-
-// does the closed segment a-b meet the closed rectangle [rx0, rx1] x [ry0, ry1]?
-__device__ __forceinline__ bool seg_meets_rect(int2 a, int2 b, long long rx0, long long ry0,
-                                               long long rx1, long long ry1)
-{
-    if (max(a.x, b.x) < rx0 || min(a.x, b.x) > rx1 || max(a.y, b.y) < ry0 || min(a.y, b.y) > ry1)
-        return false;
-    const long long o1 = orient(a, b, rx0, ry0), o2 = orient(a, b, rx1, ry0);
-    const long long o3 = orient(a, b, rx0, ry1), o4 = orient(a, b, rx1, ry1);
-    const bool all_pos = o1 > 0 && o2 > 0 && o3 > 0 && o4 > 0;
-    const bool all_neg = o1 < 0 && o2 < 0 && o3 < 0 && o4 < 0;
-    return !(all_pos || all_neg);
-}
 
 // exact half-open membership (same rule as the signing kernel), warp-cooperative
 __device__ __forceinline__ bool warp_member(const int2* __restrict__ v, int n, int px, int py, int lane)

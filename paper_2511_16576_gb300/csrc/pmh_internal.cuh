@@ -57,16 +57,51 @@ enum ScratchSlot {
 // 2^kStreamGridBits-square grid (stream_index.cu)
 constexpr int kStreamGridBits = 7;
 constexpr int kStreamIndexPoints = 65536;
+// polygons of at most this many vertices are staged in shared memory by the
+// signing kernels; larger ones are read through their y-slab edge index
+constexpr int kStagedMaxVerts = 256;
+
+// Cost model of the indexed form for one polygon (clipped box bb, twice its
+// area), in warp instructions per hash: the walk examines about 2^32 / area
+// points, 128 per round of ~130 instructions; the indexed form reads the cells
+// under the bounding box, 32 per round of ~50 instructions, and sees about
+// lim * bbox / 2^32 candidates, with lim = 8 * 2^32 / area (a hit is then
+// missed with probability ~e^-8 and the walk resumes at lim).  Returns lim, or
+// 0 to walk.  The same function decides the class of a polygon at upload and
+// the limit in the signing kernels.
+__host__ __device__ __forceinline__ uint32_t pmh_indexed_limit(int4 bb, long long area2)
+{
+    // single precision: the estimate only picks a form and a limit (any limit
+    // gives the exact result), and double precision is slow on this GPU
+    if (bb.z <= bb.x || bb.w <= bb.y) return 0;
+    const int shift = 16 - kStreamGridBits;
+    const float area = 0.5f * (float)(area2 < 0 ? -area2 : area2);
+    const float walk = 4294967296.0f / fmaxf(area, 1.0f);
+    const float cells = (float)((((bb.z - 1) >> shift) - (bb.x >> shift) + 1) *
+                                (((bb.w - 1) >> shift) - (bb.y >> shift) + 1));
+    const float lim = fminf((float)kStreamIndexPoints, 8.0f * walk + 256.0f);
+    const float cand = lim * ((float)(bb.z - bb.x) * (float)(bb.w - bb.y) * (1.0f / 4294967296.0f));
+    const float walk_cost = ceilf(walk * (1.0f / 128.0f)) * 130.0f;
+    const float index_cost = ceilf(cells * (1.0f / 32.0f)) * 50.0f + 40.0f;
+    if (index_cost >= walk_cost || cand > 24.0f) return 0;
+    return (uint32_t)lim;
+}
+
+// Cell record of the stream index: .x = first entry of the cell's list (the
+// list ends where the next record's starts), .y = six 5-bit counts, bits
+// [5t, 5t+5) = entries of the list with stream index below M >> t.
+constexpr int kRankLevels = 6;
 struct StreamIndex {
     uint64_t seed = 0;
     int K = 0;
-    uint32_t* cell_start = nullptr;  // [K * G * G + 1]
-    uint2* ent = nullptr;            // [K * M] (stream index, x | y << 16)
+    uint2* cell = nullptr;  // [K * G * G + 1] records
+    uint2* ent = nullptr;   // [K * M] (stream index, x | y << 16)
+    int ranked = 0;         // every list fits the 5-bit counts
 };
 struct StreamIndexView {
-    const uint32_t* cell_start;  // nullptr: no index
+    const uint2* cell;  // nullptr: no index
     const uint2* ent;
-    int M, gbits, shift;
+    int M, gbits, shift, ranked;
 };
 
 struct pmh_ctx_s {
@@ -108,6 +143,8 @@ struct pmh_polys_s {
     int32_t* slab_ptr = nullptr;
     int32_t* slab_edges = nullptr;
     int32_t* order = nullptr;       // polygons by expected signing cost, largest first
+    int32_t* order_cls = nullptr;   // the same, staged indexed-form polygons first
+    int64_t n_indexed = 0;          // number of those (<= kStagedMaxVerts vertices, pmh_indexed_limit > 0)
     uint32_t* mask = nullptr;       // [n][16] coverage masks
 };
 
@@ -192,7 +229,15 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     const int32_t* order, const pmh_params* P, int64_t n_polys,
                     const int64_t* d_n, const int* d_flags, unsigned long long* ticket,
                     uint32_t* out, cudaStream_t s, const int64_t* area2 = nullptr,
-                    const StreamIndexView* sidx = nullptr, const uint32_t* masks = nullptr);
+                    const StreamIndexView* sidx = nullptr, const uint32_t* masks = nullptr,
+                    const int32_t* order_cls = nullptr, int64_t n_indexed = 0);
+// indexed form of the staged polygons list[0 .. n_list) (sign_indexed.cu); ticket is
+// its own work-queue counter, work (optional) the six work counters
+int pmh_launch_sign_indexed(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4* bbox,
+                            const int64_t* area2, const int32_t* list, int64_t n_list,
+                            const pmh_params* P, const StreamIndexView& S,
+                            unsigned long long* ticket, uint32_t* out,
+                            unsigned long long* work, cudaStream_t s);
 int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
                      int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
                      int* d_flags, bool write, cudaStream_t s);

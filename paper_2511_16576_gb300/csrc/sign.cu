@@ -7,8 +7,10 @@
 // almost every point, and the exact point-in-polygon test runs ~2-3 times per
 // hash.  One warp owns a work item (polygon p, 32 consecutive hashes):
 //   * the polygon's vertices are staged once into the warp's shared-memory
-//     slice (polygons of more than 256 vertices are read from global memory
-//     through their y-slab edge index instead, see slabs.cu);
+//     slice and its edges binned into 32 horizontal slabs there, so that an
+//     exact test reads only the few edges whose y-range meets the point's slab
+//     (polygons of more than 256 vertices are read from global memory through
+//     their y-slab edge index instead, see slabs.cu);
 //   * per round every lane draws U points (indices i0 + j*32 + lane), so one
 //     round covers 32*U consecutive stream indices; the counter-based stream
 //     lets each lane jump straight to its own index;
@@ -27,160 +29,13 @@
 
 #include "pmh_internal.cuh"
 
+#include "sign_common.cuh"
+
 namespace {
 
 constexpr int kWarps = 8;        // warps per block
-constexpr int kSmemVerts = 256;  // vertices staged per warp (larger polygons read global)
 constexpr int kU = 4;            // points per lane per round
 constexpr int kWorkSlot = 8;     // context ticket slots 8..13: work counters of the last sign
-
-// Exact half-open membership of lattice point (px, py), warp-cooperative.
-// Edge a->b counts iff (ay > py) != (by > py) and the int64 cross product
-// (b - a) x (p - a) is non-zero with the sign of (by - ay).
-__device__ __forceinline__ bool warp_inside(const int2* __restrict__ v, int n, int px, int py,
-                                            int lane)
-{
-    unsigned par = 0;
-    for (int e = lane; e < n; e += 32) {
-        int2 a = v[e];
-        int2 b = v[e + 1 == n ? 0 : e + 1];
-        bool st = (a.y > py) != (b.y > py);
-        if (st) {
-            long long cr = (long long)(b.x - a.x) * (py - a.y) - (long long)(px - a.x) * (b.y - a.y);
-            par ^= (cr != 0) & ((cr > 0) == (b.y > a.y));
-        }
-    }
-    return __popc(__ballot_sync(0xffffffffu, par)) & 1;
-}
-
-// Algorithmic work of one warp (warp-uniform counts): stream points the walk
-// examined up to its result, grid cells and index entries read by the indexed
-// form, bbox candidates it ordered, and edges tested by the exact membership.
-struct Work {
-    unsigned long long walk = 0, cells = 0, entries = 0, cand = 0, edges = 0, masked = 0;
-};
-
-// Exact membership through the polygon's y-slab index: only the edges listed
-// for the slab holding py can straddle the line y = py.
-__device__ __forceinline__ bool warp_inside_slab(const int2* __restrict__ v, int n,
-                                                 const int32_t* __restrict__ sp,
-                                                 const int32_t* __restrict__ se, int slab_h,
-                                                 int ymin, int px, int py, int lane, int& tested)
-{
-    const int s = (py - ymin) / slab_h;
-    const int lo = sp[s], hi = sp[s + 1];
-    tested = hi - lo;
-    unsigned par = 0;
-    for (int i = lo + lane; i < hi; i += 32) {
-        int e = se[i];
-        int2 a = v[e];
-        int2 b = v[e + 1 == n ? 0 : e + 1];
-        bool st = (a.y > py) != (b.y > py);
-        if (st) {
-            long long cr = (long long)(b.x - a.x) * (py - a.y) - (long long)(px - a.x) * (b.y - a.y);
-            par ^= (cr != 0) & ((cr > 0) == (b.y > a.y));
-        }
-    }
-    return __popc(__ballot_sync(0xffffffffu, par)) & 1;
-}
-
-struct AllEdges {
-    const int2* v;
-    int n;
-    __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
-    {
-        w.edges += n;
-        return warp_inside(v, n, px, py, lane);
-    }
-};
-
-struct SlabEdges {
-    const int2* v;
-    int n;
-    const int32_t* sp;
-    const int32_t* se;
-    int slab_h, ymin;
-    __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
-    {
-        int tested = 0;
-        const bool r = warp_inside_slab(v, n, sp, se, slab_h, ymin, px, py, lane, tested);
-        w.edges += tested;
-        return r;
-    }
-};
-
-template <int U, class Inside>
-__device__ __forceinline__ uint32_t sign_walk(const Inside& inside, int x0, int y0, uint32_t w,
-                                              uint32_t h, uint64_t sk, uint32_t T, int lane,
-                                              Work& work, uint32_t start);
-
-// Membership through the polygon's coverage mask first: a candidate in a cell
-// that no edge touches is decided by the cell's code; only boundary cells run
-// the exact test.
-template <class Inner>
-struct Masked {
-    Inner inner;
-    const uint32_t* m;  // 16 words (row j), 2 bits per cell
-    int x0, y0, cwl, chl;
-    __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
-    {
-        const uint32_t code = (m[(py - y0) >> chl] >> (2 * ((px - x0) >> cwl))) & 3u;
-        if (code != 2u) {
-            w.masked += 1;
-            return code == 1u;
-        }
-        return inner(px, py, lane, w);
-    }
-};
-
-// One hash of one polygon; every lane returns the same value.  U points per
-// lane per round: one round covers 32 * U consecutive stream indices.
-template <int U, class Inside>
-__device__ __forceinline__ uint32_t sign_one_t(const Inside& inside, int x0, int y0, uint32_t w,
-                                               uint32_t h, uint64_t sk, uint32_t T, int lane,
-                                               Work& work, uint32_t start = 0)
-{
-    if (w == 0 || h == 0) return T;
-    const uint32_t r = sign_walk<U>(inside, x0, y0, w, h, sk, T, lane, work, start);
-    work.walk += (r < T ? r + 1 : T) - start;
-    return r;
-}
-
-template <int U, class Inside>
-__device__ __forceinline__ uint32_t sign_walk(const Inside& inside, int x0, int y0, uint32_t w,
-                                              uint32_t h, uint64_t sk, uint32_t T, int lane,
-                                              Work& work, uint32_t start)
-{
-    uint64_t z = sk + (uint64_t)(start + lane + 1) * PMH_GAMMA;
-    const uint64_t step = 32ull * PMH_GAMMA;
-    for (uint32_t i0 = start; i0 < T; i0 += 32u * U) {
-        uint32_t pts[U];
-        unsigned m = 0;
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-            uint32_t r = pmh_mix64_lo(z + (uint64_t)j * step);
-            pts[j] = r;
-            uint32_t dx = (r & 0xFFFFu) - (uint32_t)x0;
-            uint32_t dy = (r >> 16) - (uint32_t)y0;
-            m |= (unsigned)((dx < w) & (dy < h)) << j;
-        }
-        z += (uint64_t)U * step;
-        if (!__any_sync(0xffffffffu, m)) continue;
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-            unsigned b = __ballot_sync(0xffffffffu, (m >> j) & 1u);
-            while (b) {
-                int l = __ffs(b) - 1;
-                b &= b - 1;
-                uint32_t i = i0 + (uint32_t)(j * 32 + l);
-                if (i >= T) return T;
-                uint32_t r = __shfl_sync(0xffffffffu, pts[j], l);
-                if (inside((int)(r & 0xFFFFu), (int)(r >> 16), lane, work)) return i;
-            }
-        }
-    }
-    return T;
-}
 
 __device__ __forceinline__ uint32_t sign_one(const int2* __restrict__ v, int n, int x0, int y0,
                                              uint32_t w, uint32_t h, uint64_t sk, uint32_t T,
@@ -218,11 +73,11 @@ __device__ uint32_t sign_chunk_indexed(const Inside& inside, const StreamIndexVi
         const int k = kb + g;
         int read = 0;
         if (k < kend) {
-            const uint32_t* cs = S.cell_start + ((int64_t)k << (2 * S.gbits));
+            const uint2* cs = S.cell + ((int64_t)k << (2 * S.gbits));
             uint2* cb = cbuf + g * kCand;
             for (int c = gl; c < C; c += 8) {
                 const int cell = ((cy0 + c / ncx) << S.gbits) | (cx0 + c % ncx);
-                const uint32_t beg = cs[cell], end = cs[cell + 1];
+                const uint32_t beg = cs[cell].x, end = cs[cell + 1].x;
                 for (uint32_t e = beg; e < end; e += 4) {
                     uint2 q[4];
 #pragma unroll
@@ -258,7 +113,7 @@ __device__ uint32_t sign_chunk_indexed(const Inside& inside, const StreamIndexVi
             uint32_t hk = 0xFFFFFFFFu;
             work.cand += min(n, kCand);
             if (n > kCand) {
-                hk = sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, work, 0);
+                hk = sign_resume<U>(inside, bb.x, bb.y, w, h, sk, T, lane, &work, 0);
             } else {
                 const uint2* cb = cbuf + j * kCand;
                 uint2 c0 = lane < n ? cb[lane] : make_uint2(0xFFFFFFFFu, 0u);
@@ -278,7 +133,7 @@ __device__ uint32_t sign_chunk_indexed(const Inside& inside, const StreamIndexVi
                     }
                 }
                 if (hk == 0xFFFFFFFFu)
-                    hk = lim >= T ? T : sign_one_t<U>(inside, bb.x, bb.y, w, h, sk, T, lane, work, lim);
+                    hk = lim >= T ? T : sign_resume<U>(inside, bb.x, bb.y, w, h, sk, T, lane, &work, lim);
             }
             if (lane == kk - k0) mine = hk;
         }
@@ -290,12 +145,9 @@ __device__ uint32_t sign_chunk_indexed(const Inside& inside, const StreamIndexVi
 // the hashes k0 .. k0+31 of one polygon; lane j returns hash k0 + j.  lim > 0
 // selects the indexed form (stream points below lim read from the index).
 template <int U, class Inside>
-__device__ __forceinline__ uint32_t sign_chunk(const Inside& inside, int4 bb, uint64_t seed, int k0,
-                                               int kend, uint32_t T, int lane,
-                                               const StreamIndexView& S, uint32_t lim,
-                                               uint2* cbuf, int* ccount, Work& work)
+__device__ __forceinline__ uint32_t sign_chunk_walk(const Inside& inside, int4 bb, uint64_t seed,
+                                                    int k0, int kend, uint32_t T, int lane, Work& work)
 {
-    if (lim) return sign_chunk_indexed<U>(inside, S, bb, seed, k0, kend, T, lim, cbuf, ccount, lane, work);
     const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
     uint32_t mine = T;
     for (int k = k0; k < kend; ++k) {
@@ -306,29 +158,19 @@ __device__ __forceinline__ uint32_t sign_chunk(const Inside& inside, int4 bb, ui
     return mine;
 }
 
-// Cost model of the indexed form for one polygon, in warp instructions per
-// hash: the walk examines about 2^32 / area points, 128 per round of ~130
-// instructions; the indexed form reads the cells under the bounding box, 32 per
-// round of ~50 instructions, and orders about lim * bbox / 2^32 candidates,
-// with lim = 8 * 2^32 / area (a hit is then missed with probability ~e^-8 and
-// the walk resumes at lim).  Returns lim, or 0 to walk.
-__device__ __forceinline__ uint32_t indexed_limit(const StreamIndexView& S, int4 bb, long long area2)
+template <int U, class Inside>
+__device__ __forceinline__ uint32_t sign_chunk(const Inside& inside, int4 bb, uint64_t seed, int k0,
+                                               int kend, uint32_t T, int lane,
+                                               const StreamIndexView& S, uint32_t lim,
+                                               uint2* cbuf, int* ccount, Work& work)
 {
-    if (!S.cell_start || bb.z <= bb.x || bb.w <= bb.y) return 0;
-    const double area = 0.5 * (double)(area2 < 0 ? -area2 : area2);
-    const double walk = 4294967296.0 / fmax(area, 1.0);
-    const double cells = (double)(((bb.z - 1) >> S.shift) - (bb.x >> S.shift) + 1) *
-                         (double)(((bb.w - 1) >> S.shift) - (bb.y >> S.shift) + 1);
-    const double lim = fmin((double)S.M, 8.0 * walk + 256.0);
-    const double cand = lim * (double)(bb.z - bb.x) * (double)(bb.w - bb.y) / 4294967296.0;
-    const double walk_cost = ceil(walk / 128.0) * 130.0;
-    const double index_cost = ceil(cells / 32.0) * 50.0 + 40.0;
-    if (index_cost >= walk_cost || cand > 24.0) return 0;
-    return (uint32_t)lim;
+    if (lim) return sign_chunk_indexed<U>(inside, S, bb, seed, k0, kend, T, lim, cbuf, ccount, lane, work);
+    return sign_chunk_walk<U>(inside, bb, seed, k0, kend, T, lane, work);
 }
 
-template <int U, int W>
-__global__ void __launch_bounds__(W * 32)
+
+template <int U, int W, int MinBlocks>
+__global__ void __launch_bounds__(W * 32, MinBlocks)
 sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
             const int4* __restrict__ bbox, const SlabInfo* __restrict__ slabs,
             const int32_t* __restrict__ slab_ptr, const int32_t* __restrict__ slab_edges,
@@ -338,7 +180,10 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
             const int64_t* __restrict__ area2, StreamIndexView S,
             unsigned long long* __restrict__ work_out, const uint32_t* __restrict__ masks)
 {
-    __shared__ __align__(16) int2 sv[W][kSmemVerts];
+    __shared__ __align__(16) int2 sv[W][kSmemVerts + 1];
+    __shared__ uint8_t sid[W][kSlabCap];
+    __shared__ uint16_t sbeg[W][kSlabs + 1];
+    __shared__ int scnt[W][kSlabs];
     __shared__ uint2 cbuf[W][4 * kCand];
     __shared__ int ccount[W][4];
     __shared__ uint32_t smask[W][16];
@@ -363,22 +208,31 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
         const int64_t b = off[p];
         const int n = (int)(off[p + 1] - b);
         const int4 bb = bbox[p];
-        const uint32_t lim = area2 ? indexed_limit(S, bb, area2[p]) : 0;
+        // (staged polygons of the indexed form have their own kernel, sign_indexed.cu)
+        const uint32_t lim = area2 && S.cell && n > kSmemVerts ? pmh_indexed_limit(bb, area2[p]) : 0;
         uint32_t mine;
-        if (n <= kSmemVerts && masks) {
-            // stage the vertices and the coverage mask in this warp's shared-memory slice
+        if (n <= kSmemVerts) {
+            // stage the vertices (closed: v[n] = v[0]; coalesced 8-byte loads), the
+            // coverage mask if any, and the slab lists in this warp's shared-memory slice
             for (int i = lane; i < n; i += 32) sv[wid][i] = xy[b + i];
-            if (lane < 16) smask[wid][lane] = masks[p * 16 + lane];
+            if (lane == 0) sv[wid][n] = xy[b];
+            if (masks && lane < 16) smask[wid][lane] = masks[p * 16 + lane];
             __syncwarp();
-            const Masked<AllEdges> in{AllEdges{sv[wid], n}, smask[wid], bb.x, bb.y,
-                                      mask_cell_log2(bb.z - bb.x), mask_cell_log2(bb.w - bb.y)};
-            mine = sign_chunk<U>(in, bb, seed, k0, kend, T, lane, S, lim, cbuf[wid], ccount[wid], work);
-        } else if (n <= kSmemVerts) {
-            // stage the vertices in this warp's shared-memory slice (coalesced 8-byte loads)
-            for (int i = lane; i < n; i += 32) sv[wid][i] = xy[b + i];
-            __syncwarp();
-            mine = sign_chunk<U>(AllEdges{sv[wid], n}, bb, seed, k0, kend, T, lane, S, lim,
-                                 cbuf[wid], ccount[wid], work);
+            const int sh = staged_slab_shift(max(bb.w - bb.y, 1));
+            const bool staged = bb.w > bb.y && bb.z > bb.x &&
+                                build_staged_slabs(sv[wid], n, bb.y, sh, sid[wid], sbeg[wid], scnt[wid], lane);
+            const int cwl = mask_cell_log2(bb.z - bb.x), chl = mask_cell_log2(bb.w - bb.y);
+            if (staged) {
+                const StagedEdges st{sv[wid], sid[wid], sbeg[wid], bb.y, sh};
+                if (masks)
+                    mine = sign_chunk_walk<U>(Masked<StagedEdges>{st, smask[wid], bb.x, bb.y, cwl, chl}, bb,
+                                              seed, k0, kend, T, lane, work);
+                else
+                    mine = sign_chunk_walk<U>(st, bb, seed, k0, kend, T, lane, work);
+            } else {
+                // too many slab references (or an empty box): every edge, no mask
+                mine = sign_chunk_walk<U>(AllEdges{sv[wid], n}, bb, seed, k0, kend, T, lane, work);
+            }
         } else if (slabs && slabs[p].S > 0) {
             const SlabInfo si = slabs[p];
             mine = sign_chunk<U>(SlabEdges{xy + b, n, slab_ptr + si.slab_base,
@@ -392,6 +246,10 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
         __syncwarp();
     }
     if (work_out) {
+        unsigned long long le = work.lane_edges;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) le += __shfl_xor_sync(0xffffffffu, le, o);
+        work.edges += le;
         if (lane == 0) {
             atomicAdd(&wsum[0], work.walk);
             atomicAdd(&wsum[1], work.cells);
@@ -410,14 +268,16 @@ using SignFn = void (*)(const int2*, const int64_t*, const int4*, const SlabInfo
                         const int64_t*, const int*, unsigned long long*, uint32_t*, const int64_t*,
                         StreamIndexView, unsigned long long*, const uint32_t*);
 struct SignVariant {
-    int U, W;
+    int U, W, MinBlocks;
     SignFn fn;
 };
-// index 0 is the default; the autotuner may pick any of them
-// (static shared memory per block stays below 48 KiB: 8 warps at most)
+// index 0 is the default; the autotuner may pick any of them.  MinBlocks caps
+// the registers (65536 / (MinBlocks * W * 32)) so that more warps stay resident
+// to hide the latency of the index reads.  (Static shared memory per block
+// stays below 48 KiB: 8 warps at most.)
 const SignVariant kSignVariants[] = {
-    {4, 8, sign_kernel<4, 8>}, {2, 8, sign_kernel<2, 8>}, {8, 8, sign_kernel<8, 8>},
-    {4, 4, sign_kernel<4, 4>}, {2, 4, sign_kernel<2, 4>}, {1, 8, sign_kernel<1, 8>},
+    {4, 8, 3, sign_kernel<4, 8, 3>}, {4, 8, 4, sign_kernel<4, 8, 4>}, {4, 8, 2, sign_kernel<4, 8, 2>},
+    {2, 8, 3, sign_kernel<2, 8, 3>}, {2, 8, 4, sign_kernel<2, 8, 4>}, {8, 8, 3, sign_kernel<8, 8, 3>},
 };
 constexpr int kNumSignVariants = sizeof(kSignVariants) / sizeof(kSignVariants[0]);
 
@@ -436,10 +296,22 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     const int32_t* order, const pmh_params* P, int64_t n_polys,
                     const int64_t* d_n, const int* d_flags, unsigned long long* ticket,
                     uint32_t* out, cudaStream_t s, const int64_t* area2,
-                    const StreamIndexView* sidx, const uint32_t* masks)
+                    const StreamIndexView* sidx, const uint32_t* masks,
+                    const int32_t* order_cls, int64_t n_indexed)
 {
-    const StreamIndexView S = sidx ? *sidx : StreamIndexView{nullptr, nullptr, 0, 0, 0};
+    const StreamIndexView S = sidx ? *sidx : StreamIndexView{nullptr, nullptr, 0, 0, 0, 0};
     if (n_polys <= 0) return PMH_OK;
+    unsigned long long* work = d_n ? nullptr : ctx->d_tickets + kWorkSlot;
+    if (work) PMH_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long) * 6, s));
+    if (S.cell && S.ranked && order_cls && area2 && !d_n) {
+        // staged polygons of the indexed form (the first n_indexed of the class
+        // order) in their own kernel; the rest below, in cost order
+        PMH_TRY(pmh_launch_sign_indexed(ctx, xy, off, bbox, area2, order_cls, n_indexed, P, S,
+                                        ticket + 2, out, work, s));
+        order = order_cls + n_indexed;
+        n_polys -= n_indexed;
+        if (n_polys <= 0) return PMH_OK;
+    }
     const SignVariant& v = kSignVariants[ctx->sign_variant >= 0 ? ctx->sign_variant : 0];
     const int chunks = (int)((P->K + 31) / 32);
     const int64_t n_items = n_polys * chunks;
@@ -448,8 +320,6 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
     int64_t blocks = (int64_t)ctx->sm_count * std::max(per_sm, 1);
     blocks = std::min<int64_t>(blocks, (n_items + v.W - 1) / v.W);
     PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
-    unsigned long long* work = d_n ? nullptr : ctx->d_tickets + kWorkSlot;
-    if (work) PMH_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long) * 6, s));
     v.fn<<<(int)blocks, v.W * 32, 0, s>>>(xy, off, bbox, slabs, slab_ptr, slab_edges, order,
                                           P->seed, (int)P->K, P->T, chunks, n_polys, d_n, d_flags,
                                           ticket, out, area2, S, work, masks);
@@ -473,7 +343,8 @@ extern "C" int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* 
     return pmh_launch_sign(ctx, polys->xy, polys->offsets, polys->bbox, polys->slab_info,
                            polys->slab_ptr, polys->slab_edges, polys->order, params, polys->n,
                            nullptr, nullptr, ctx->d_tickets + 0, d_hashes, (cudaStream_t)stream,
-                           polys->area2, indexed ? &sidx : nullptr, masked ? polys->mask : nullptr);
+                           polys->area2, indexed ? &sidx : nullptr, masked ? polys->mask : nullptr,
+                           polys->order_cls, polys->n_indexed);
 }
 
 extern "C" int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts)
@@ -537,7 +408,8 @@ extern "C" int pmh_sign_autotune(pmh_ctx ctx, pmh_polys sample, const pmh_params
                                      sample->slab_ptr, sample->slab_edges, sample->order, params,
                                      sample->n, nullptr, nullptr, ctx->d_tickets + 1, out, 0,
                                      sample->area2, indexed ? &sidx : nullptr,
-                                     masked ? sample->mask : nullptr);
+                                     masked ? sample->mask : nullptr, sample->order_cls,
+                                     sample->n_indexed);
             cudaEventRecord(e1, 0);
             if (cudaEventSynchronize(e1) != cudaSuccess)
                 rc = pmh_set_error(PMH_ERR_CUDA, "autotune run failed");

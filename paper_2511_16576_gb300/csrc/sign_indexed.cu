@@ -1,0 +1,362 @@
+// sign_indexed.cu -- step A1 (Definition 2, Algorithm 1), indexed form for the
+// polygons staged in shared memory.
+//
+// h_k(P) = min{ i : point i of stream k lies in P } is found from the stream
+// index (stream_index.cu): every point of stream k with index below the limit
+// L that falls in P's bounding box sits in one of the grid cells under the box,
+// and a cell record tells how many of its points lie below each of six index
+// levels.  One warp owns one polygon and all of its hashes:
+//   * the vertices are staged once, their edges binned into y-slabs, and a
+//     32 x 32 coverage mask of the bounding box is built: a cell that no edge
+//     touches is wholly inside or wholly outside, decided by one exact test
+//     per run of such cells;
+//   * sixteen hashes at a time, the (hash, cell) pairs under the box are read
+//     one per lane, and the points they hold below the smallest level >= L are
+//     spread over the lanes by a warp scan (every lane loads one point, no
+//     lane walks a list).  A point in the box is classified by the mask: in an
+//     inside cell it is a hit and bounds the hash from above, in an outside
+//     cell it is dropped, in a boundary cell it is kept;
+//   * the kept points whose index is below their hash's smallest hit are
+//     queued and tested 32 at a time, one per lane (lane-local exact test over
+//     the slab's edges);
+//   * h_k is the smallest index that passed; a hash without one below L (or
+//     whose kept points overflowed) continues with the ordinary walk.
+// Every step is exact, so the result equals the definition bit for bit.
+#include <algorithm>
+
+#include "sign_common.cuh"
+
+namespace {
+
+static_assert(kStreamIndexPoints <= 65536, "point indices are packed in 16 bits");
+
+constexpr int kIdxWarps = 4;      // warps per block
+constexpr int kIdxMinBlocks = 8;  // resident blocks per SM the registers are sized for
+constexpr int kSub = 16;          // hashes gathered together
+constexpr int kMaskN = 32;        // coverage mask cells per side
+constexpr int kPool = 256;        // kept (boundary) points of one group of kSub hashes
+constexpr int kQueue = 64;        // exact-test queue (at most 31 + 32 entries)
+constexpr int kIdxU = 4;          // points per lane per round of a resumed walk
+
+struct IdxWarp {
+    int2 v[kSmemVerts + 1];  // vertices, v[n] = v[0]
+    uint8_t ids[kSlabCap];   // edges by slab
+    uint16_t beg[kSlabs + 1];
+    int cnt[kSlabs];
+    uint32_t bnd[kMaskN];    // bit i of row j: an edge touches cell (i, j)
+    uint32_t inb[kMaskN];    // bit i of row j: untouched cell (i, j) lies inside
+    uint32_t best[kSub];     // per hash: smallest inside index found
+    uint2 pool[kPool];       // (hash << 16 | index, x | y << 16)
+    uint2 queue[kQueue];
+    int npool;
+    uint32_t ovf;            // bit j: hash j lost kept points
+};
+
+__host__ __device__ __forceinline__ int mask32_log2(int w)
+{
+    int a = (w + kMaskN - 1) / kMaskN, l = 0;
+    while ((1 << l) < a) ++l;
+    return l;
+}
+
+// quotient a / b for 0 <= a < 2^22, 1 <= b, from a float reciprocal
+__device__ __forceinline__ int div_small(int a, int b, float inv)
+{
+    int q = (int)((float)a * inv);
+    if (q * b > a) --q;
+    else if ((q + 1) * b <= a) ++q;
+    return q;
+}
+
+// one slab holding every edge: the exact test then reads all n edges
+__device__ __forceinline__ int single_slab(IdxWarp& m, int n, int lane)
+{
+    for (int e = lane; e < n; e += 32) m.ids[e] = (uint8_t)e;
+    if (lane == 0) m.beg[0] = 0;
+    if (lane < kSlabs) m.beg[lane + 1] = (uint16_t)n;
+    __syncwarp();
+    return 16;
+}
+
+// 32 x 32 coverage mask over the clipped box bb: bnd marks the cells whose
+// closed rectangle, grown by one unit on its low sides, meets an edge; every
+// lattice point of another cell (under the half-open reading, the point
+// shifted up and right by an infinitesimal) shares the membership of the whole
+// rectangle, and so does a run of such cells in a row -- one exact test at the
+// run's first lattice point classifies it.
+__device__ __forceinline__ void build_mask(IdxWarp& m, int n, int4 bb, int cwl, int chl,
+                                           const StagedEdges& st, int lane, Work& work)
+{
+    m.bnd[lane] = 0;
+    __syncwarp();
+    for (int e = lane; e < n; e += 32) {
+        const int2 a = m.v[e], c = m.v[e + 1];
+        const int ix0 = max(0, ((min(a.x, c.x) - bb.x) >> cwl) - 1);
+        const int ix1 = min(kMaskN - 1, (max(a.x, c.x) + 1 - bb.x) >> cwl);
+        const int iy0 = max(0, ((min(a.y, c.y) - bb.y) >> chl) - 1);
+        const int iy1 = min(kMaskN - 1, (max(a.y, c.y) + 1 - bb.y) >> chl);
+        for (int j = iy0; j <= iy1; ++j)
+            for (int i = ix0; i <= ix1; ++i) {
+                const long long rx0 = (long long)bb.x + ((long long)i << cwl) - 1;
+                const long long rx1 = (long long)bb.x + ((long long)(i + 1) << cwl);
+                const long long ry0 = (long long)bb.y + ((long long)j << chl) - 1;
+                const long long ry1 = (long long)bb.y + ((long long)(j + 1) << chl);
+                if (seg_meets_rect(a, c, rx0, ry0, rx1, ry1)) atomicOr(&m.bnd[j], 1u << i);
+            }
+    }
+    __syncwarp();
+    // lane j classifies the untouched runs of row j (rows below the box's top
+    // only: the slab lists cover [bb.y, bb.w))
+    uint32_t word = 0;
+    if ((lane << chl) < bb.w - bb.y) {
+        uint32_t free_cells = ~m.bnd[lane];
+        while (free_cells) {
+            const int s = __ffs(free_cells) - 1;
+            const uint32_t rest = free_cells >> s;
+            const int len = rest == 0xFFFFFFFFu ? 32 : __ffs(~rest) - 1;
+            const uint32_t run = (len == 32 ? 0xFFFFFFFFu : ((1u << len) - 1u)) << s;
+            if (st.lane_inside(bb.x + (s << cwl), bb.y + (lane << chl), work)) word |= run;
+            free_cells &= ~run;
+        }
+    }
+    m.inb[lane] = word;
+    __syncwarp();
+}
+
+// Membership through the mask (warp-cooperative, for the resumed walk):
+// untouched cells by their code, boundary cells by the exact slab test.
+struct MaskedStaged {
+    const IdxWarp* m;
+    StagedEdges st;
+    int x0, y0, cwl, chl;
+    __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
+    {
+        const int i = (px - x0) >> cwl, j = (py - y0) >> chl;
+        if (!((m->bnd[j] >> i) & 1u)) {
+            w.masked += 1;
+            return (m->inb[j] >> i) & 1u;
+        }
+        return st(px, py, lane, w);
+    }
+};
+
+// exact tests of queue[0 .. count), one per lane; an inside point lowers its hash's result
+__device__ __forceinline__ void exact_batch(IdxWarp& m, int count, const StagedEdges& st, int lane,
+                                            Work& work)
+{
+    if (lane < count) {
+        const uint2 c = m.queue[lane];
+        const int kl = (int)(c.x >> 16);
+        const uint32_t idx = c.x & 0xFFFFu;
+        if (idx < m.best[kl] && st.lane_inside((int)(c.y & 0xFFFFu), (int)(c.y >> 16), work))
+            atomicMin(&m.best[kl], idx);
+    }
+    __syncwarp();
+}
+
+template <int W>
+__global__ void __launch_bounds__(W * 32, kIdxMinBlocks)
+sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
+                    const int4* __restrict__ bbox, const int64_t* __restrict__ area2,
+                    const int32_t* __restrict__ list, int64_t n_list, uint64_t seed, int K,
+                    uint32_t T, StreamIndexView S, unsigned long long* __restrict__ ticket,
+                    uint32_t* __restrict__ out, unsigned long long* __restrict__ work_out)
+{
+    __shared__ IdxWarp smem[W];
+    __shared__ unsigned long long wsum[6];
+    if (threadIdx.x < 6) wsum[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    IdxWarp& m = smem[threadIdx.x >> 5];
+    const unsigned full = 0xffffffffu;
+    Work work;  // warp-uniform counts (walks, warp-cooperative tests) and lane-local edge counts
+    unsigned long long lane_cells = 0, lane_read = 0, lane_cand = 0, lane_masked = 0;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(ticket, 1ull);
+        item = __shfl_sync(full, item, 0);
+        if ((int64_t)item >= n_list) break;
+        const int64_t p = list[item];
+        const int64_t b = off[p];
+        const int n = (int)(off[p + 1] - b);
+        const int4 bb = bbox[p];
+        const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
+        const uint32_t lim = min(pmh_indexed_limit(bb, area2[p]), T);
+        int lev = 0;  // smallest level M >> lev that is still >= lim
+        while (lev + 1 < kRankLevels && ((uint32_t)S.M >> (lev + 1)) >= lim) ++lev;
+
+        // stage the polygon, its slab lists and its coverage mask
+        for (int i = lane; i < n; i += 32) m.v[i] = xy[b + i];
+        if (lane == 0) m.v[n] = xy[b];
+        __syncwarp();
+        int sh = staged_slab_shift((int)h);
+        if (!build_staged_slabs(m.v, n, bb.y, sh, m.ids, m.beg, m.cnt, lane)) sh = single_slab(m, n, lane);
+        const StagedEdges st{m.v, m.ids, m.beg, bb.y, sh};
+        const int cwl = mask32_log2((int)w), chl = mask32_log2((int)h);
+        build_mask(m, n, bb, cwl, chl, st, lane, work);
+        const MaskedStaged walker{&m, st, bb.x, bb.y, cwl, chl};
+
+        // cells under the box, row-major; pair = hash * C + cell
+        const int cx0 = bb.x >> S.shift, cy0 = bb.y >> S.shift;
+        const int ncx = ((bb.z - 1) >> S.shift) - cx0 + 1;
+        const int C = ncx * (((bb.w - 1) >> S.shift) - cy0 + 1);
+        const float invC = 1.0f / (float)C, invX = 1.0f / (float)ncx;
+
+        for (int kc = 0; kc < K; kc += kSub) {
+            const int kn = min(kSub, K - kc);
+            if (lane < kSub) m.best[lane] = 0xFFFFFFFFu;
+            if (lane == 0) {
+                m.npool = 0;
+                m.ovf = 0;
+            }
+            __syncwarp();
+            const int npairs = lim > 0 ? kn * C : 0;
+            const uint2* rec = S.cell + ((int64_t)kc << (2 * S.gbits));
+            for (int p0 = 0; p0 < npairs; p0 += 32) {
+                // one (hash, cell) record per lane: its points below the level
+                const int pr = p0 + lane;
+                uint32_t first = 0, cnt = 0;
+                int hl = 0;
+                if (pr < npairs) {
+                    hl = div_small(pr, C, invC);
+                    const int c = pr - hl * C;
+                    const int cy = div_small(c, ncx, invX), cx = c - cy * ncx;
+                    const uint2 r = rec[((int64_t)hl << (2 * S.gbits)) + (((cy0 + cy) << S.gbits) | (cx0 + cx))];
+                    first = r.x;
+                    cnt = (r.y >> (5 * lev)) & 31u;
+                    ++lane_cells;
+                }
+                uint32_t incl = cnt;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t t = __shfl_up_sync(full, incl, d);
+                    if (lane >= d) incl += t;
+                }
+                const uint32_t excl = incl - cnt;
+                const int E = (int)__shfl_sync(full, incl, 31);
+                // spread the points over the lanes: point e belongs to the last
+                // lane whose exclusive offset is <= e
+                for (int e0 = 0; e0 < E; e0 += 32) {
+                    const uint32_t e = (uint32_t)(e0 + lane);
+                    int own = 0;
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1)
+                        if (__shfl_sync(full, excl, own + step) <= e) own += step;
+                    const uint32_t o_first = __shfl_sync(full, first, own);
+                    const uint32_t o_excl = __shfl_sync(full, excl, own);
+                    const int o_hl = __shfl_sync(full, hl, own);
+                    if ((int)e < E) {
+                        const uint2 q = S.ent[o_first + (e - o_excl)];
+                        ++lane_read;
+                        const uint32_t r = q.y;
+                        const uint32_t dx = (r & 0xFFFFu) - (uint32_t)bb.x;
+                        const uint32_t dy = (r >> 16) - (uint32_t)bb.y;
+                        if (q.x < lim && dx < w && dy < h) {
+                            ++lane_cand;
+                            const int i = (int)(dx >> cwl), j = (int)(dy >> chl);
+                            if ((m.bnd[j] >> i) & 1u) {
+                                const int slot = atomicAdd(&m.npool, 1);
+                                if (slot < kPool) m.pool[slot] = make_uint2(((uint32_t)o_hl << 16) | q.x, r);
+                                else atomicOr(&m.ovf, 1u << o_hl);
+                            } else {
+                                ++lane_masked;
+                                if ((m.inb[j] >> i) & 1u) atomicMin(&m.best[o_hl], q.x);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            // kept points below their hash's smallest hit go to the queue, tested 32 at a time
+            const int np = min(m.npool, kPool);
+            int nq = 0;  // warp-uniform queue length
+            for (int t0 = 0; t0 < np; t0 += 32) {
+                const int t = t0 + lane;
+                uint2 c = make_uint2(0u, 0u);
+                bool keep = false;
+                if (t < np) {
+                    c = m.pool[t];
+                    keep = (c.x & 0xFFFFu) < m.best[c.x >> 16];
+                }
+                const unsigned bal = __ballot_sync(full, keep);
+                if (keep) m.queue[nq + __popc(bal & pmh_lanemask_lt())] = c;
+                nq += __popc(bal);
+                __syncwarp();
+                if (nq >= 32) {
+                    exact_batch(m, 32, st, lane, work);
+                    nq -= 32;
+                    const uint2 rest = lane < nq ? m.queue[32 + lane] : make_uint2(0u, 0u);
+                    __syncwarp();
+                    if (lane < nq) m.queue[lane] = rest;
+                    __syncwarp();
+                }
+            }
+            if (nq > 0) exact_batch(m, nq, st, lane, work);
+
+            // hashes without an inside point below lim resume the walk there; one
+            // that lost kept points walks from the start
+            const uint32_t overs = m.ovf;
+            unsigned todo =
+                __ballot_sync(full, lane < kn && (((overs >> lane) & 1u) || m.best[lane] == 0xFFFFFFFFu));
+            while (todo) {
+                const int j = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const uint32_t start = ((overs >> j) & 1u) ? 0u : lim;
+                uint32_t hk = T;
+                if (start < T) {
+                    const uint64_t sk = pmh_mix64(seed + (uint64_t)(kc + j + 1) * PMH_GAMMA);
+                    hk = sign_one_t<kIdxU>(walker, bb.x, bb.y, w, h, sk, T, lane, work, start);
+                }
+                if (lane == 0) m.best[j] = hk;
+            }
+            __syncwarp();
+            if (lane < kn) out[p * (int64_t)K + kc + lane] = m.best[lane];
+            __syncwarp();
+        }
+    }
+    if (work_out) {
+        unsigned long long le = work.lane_edges, en = lane_read, ca = lane_cand, ma = lane_masked,
+                           ce = lane_cells;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            le += __shfl_xor_sync(full, le, o);
+            en += __shfl_xor_sync(full, en, o);
+            ca += __shfl_xor_sync(full, ca, o);
+            ma += __shfl_xor_sync(full, ma, o);
+            ce += __shfl_xor_sync(full, ce, o);
+        }
+        if (lane == 0) {
+            // Work's walk, edges and masked counts are warp-uniform; the gather's
+            // counts and the lane-local edge tests are per lane
+            atomicAdd(&wsum[0], work.walk);
+            atomicAdd(&wsum[1], ce);
+            atomicAdd(&wsum[2], en);
+            atomicAdd(&wsum[3], ca);
+            atomicAdd(&wsum[4], work.edges + le);
+            atomicAdd(&wsum[5], ma + work.masked);
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) atomicAdd(&work_out[threadIdx.x], wsum[threadIdx.x]);
+    }
+}
+
+}  // namespace
+
+int pmh_launch_sign_indexed(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4* bbox,
+                            const int64_t* area2, const int32_t* list, int64_t n_list,
+                            const pmh_params* P, const StreamIndexView& S,
+                            unsigned long long* ticket, uint32_t* out,
+                            unsigned long long* work, cudaStream_t s)
+{
+    if (n_list <= 0) return PMH_OK;
+    int per_sm = 0;
+    PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sign_indexed_kernel<kIdxWarps>,
+                                                               kIdxWarps * 32, 0));
+    int64_t blocks = (int64_t)ctx->sm_count * std::max(per_sm, 1);
+    blocks = std::min<int64_t>(blocks, (n_list + kIdxWarps - 1) / kIdxWarps);
+    PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
+    sign_indexed_kernel<kIdxWarps><<<(int)blocks, kIdxWarps * 32, 0, s>>>(
+        xy, off, bbox, area2, list, n_list, P->seed, (int)P->K, P->T, S, ticket, out, work);
+    PMH_LAUNCHED("sign_indexed_kernel");
+    return PMH_OK;
+}

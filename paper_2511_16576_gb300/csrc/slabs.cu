@@ -151,6 +151,47 @@ __global__ void cost_key_kernel(const int64_t* __restrict__ area2, int64_t n,
     }
 }
 
+// Morton code of a point of the 2^16 lattice (x bits at even positions)
+__device__ __forceinline__ uint32_t morton16(uint32_t x, uint32_t y)
+{
+    auto spread = [](uint32_t v) {
+        v &= 0xFFFFu;
+        v = (v | (v << 8)) & 0x00FF00FFu;
+        v = (v | (v << 4)) & 0x0F0F0F0Fu;
+        v = (v | (v << 2)) & 0x33333333u;
+        v = (v | (v << 1)) & 0x55555555u;
+        return v;
+    };
+    return spread(x) | (spread(y) << 1);
+}
+
+// class key: staged polygons of the indexed form first (class 0) in Morton
+// order of their box centres -- warps running at the same time then read
+// nearby cells of the stream index, which keeps them in L2 -- and the rest
+// (class 1) by decreasing expected cost; counts class 0 into *n_cls0
+__global__ void class_key_kernel(const int4* __restrict__ bbox, const int64_t* __restrict__ area2,
+                                 const int64_t* __restrict__ off, int64_t n,
+                                 uint32_t* __restrict__ keys, int32_t* __restrict__ ids,
+                                 unsigned long long* __restrict__ n_cls0)
+{
+    unsigned long long mine = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const long long a = area2[p];
+        const double aa = (double)(a < 0 ? -a : a);
+        const float cost = (float)(8589934592.0 / fmax(aa, 1.0));
+        const bool staged_indexed =
+            off[p + 1] - off[p] <= kStagedMaxVerts && pmh_indexed_limit(bbox[p], a) > 0;
+        const int4 bb = bbox[p];
+        const uint32_t cx = (uint32_t)min((bb.x + bb.z) >> 1, 65535);
+        const uint32_t cy = (uint32_t)min((bb.y + bb.w) >> 1, 65535);
+        keys[p] = staged_indexed ? (morton16(cx, cy) >> 1) : ((1u << 31) | (~__float_as_uint(cost) >> 1));
+        ids[p] = (int32_t)p;
+        mine += staged_indexed;
+    }
+    if (mine) atomicAdd(n_cls0, mine);
+}
+
 }  // namespace
 
 int pmh_build_slabs(pmh_polys P, cudaStream_t s)
@@ -221,7 +262,34 @@ int pmh_build_cost_order(pmh_polys P, cudaStream_t s)
     g_pmh_launches.fetch_add(1);
     int rc = e == cudaSuccess ? pmh_radix_sort_u32(ctx, keys, P->order, n, 32, s)
                               : pmh_set_error(PMH_ERR_CUDA, "cost key: %s", cudaGetErrorString(e));
-    cudaStreamSynchronize(s);
+    // the class order of the indexed form; the class-0 count follows the keys
+    if (rc == PMH_OK && cudaMalloc(&P->order_cls, sizeof(int32_t) * n) != cudaSuccess) {
+        cudaGetLastError();
+        rc = pmh_set_error(PMH_ERR_NOMEM, "class order allocation failed");
+    }
+    unsigned long long* n_cls0 = nullptr;
+    if (rc == PMH_OK && cudaMalloc(&n_cls0, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = pmh_set_error(PMH_ERR_NOMEM, "class count allocation failed");
+    }
+    if (rc == PMH_OK && cudaMemsetAsync(n_cls0, 0, sizeof(unsigned long long), s) != cudaSuccess)
+        rc = pmh_set_error(PMH_ERR_CUDA, "memset failed");
+    if (rc == PMH_OK) {
+        class_key_kernel<<<blocks, 256, 0, s>>>(P->bbox, P->area2, P->offsets, n, keys, P->order_cls, n_cls0);
+        g_pmh_launches.fetch_add(1);
+        e = cudaGetLastError();
+        rc = e == cudaSuccess ? pmh_radix_sort_u32(ctx, keys, P->order_cls, n, 32, s)
+                              : pmh_set_error(PMH_ERR_CUDA, "class key: %s", cudaGetErrorString(e));
+    }
+    if (rc == PMH_OK &&
+        cudaMemcpyAsync(ctx->h_pinned, n_cls0, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess)
+        rc = pmh_set_error(PMH_ERR_CUDA, "class count copy failed");
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    if (rc == PMH_OK && e2 != cudaSuccess)
+        rc = pmh_set_error(PMH_ERR_CUDA, "cost order: %s", cudaGetErrorString(e2));
+    if (rc == PMH_OK) P->n_indexed = ctx->h_pinned[0];
+    if (n_cls0) cudaFree(n_cls0);
     cudaFree(keys);
     return rc;
 }

@@ -10,9 +10,12 @@
 // stream with index < L that lies in the bounding box is in one of those
 // cells.  If no point below L hits, the ordinary walk continues from L.
 //
-// Layout (k-major): entry e of hash k lives in [cell_start[k*G*G + c],
-// cell_start[k*G*G + c + 1]) for its cell c; ent[e] = (stream index, x | y << 16),
-// indices ascending within a cell, one 8-byte load per entry.
+// Layout (k-major): entry e of hash k lives in [cell[k*G*G + c].x,
+// cell[k*G*G + c + 1].x) for its cell c; ent[e] = (stream index, x | y << 16),
+// indices ascending within a cell, one 8-byte load per entry.  cell[.].y holds
+// six 5-bit counts: the entries of the cell below M, M/2, ..., M/32, so that a
+// reader with limit L knows how many entries to read (those below the smallest
+// level >= L) without reading past them.
 #include <algorithm>
 
 #include "pmh_internal.cuh"
@@ -45,9 +48,7 @@ __global__ void cell_count_kernel(const uint32_t* __restrict__ keys, int64_t n,
 }
 
 __global__ void finish_index_kernel(const uint32_t* __restrict__ keys, const int32_t* __restrict__ vals,
-                                    int64_t n, const int64_t* __restrict__ starts, int64_t n_cells,
-                                    uint64_t seed, int gbits, uint32_t* __restrict__ cell_start,
-                                    uint2* __restrict__ ent)
+                                    int64_t n, uint64_t seed, int gbits, uint2* __restrict__ ent)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -56,9 +57,31 @@ __global__ void finish_index_kernel(const uint32_t* __restrict__ keys, const int
         const uint64_t sk = pmh_mix64(seed + (uint64_t)(k + 1) * PMH_GAMMA);
         ent[e] = make_uint2((uint32_t)i, pmh_mix64_lo(sk + (uint64_t)(i + 1) * PMH_GAMMA));
     }
+}
+
+// cell records: start and the rank counts of each level; *longest = longest list
+__global__ void cell_record_kernel(const int64_t* __restrict__ starts, int64_t n_cells,
+                                   const uint2* __restrict__ ent, int M, uint2* __restrict__ cell,
+                                   int* __restrict__ longest)
+{
+    int mine = 0;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= n_cells;
-         c += (int64_t)gridDim.x * blockDim.x)
-        cell_start[c] = (uint32_t)starts[c];
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = (uint32_t)starts[c];
+        uint32_t counts = 0;
+        if (c < n_cells) {
+            const uint32_t e = (uint32_t)starts[c + 1];
+            mine = max(mine, (int)(e - b));
+            for (int t = 0; t < kRankLevels; ++t) {
+                const uint32_t level = (uint32_t)M >> t;
+                uint32_t cnt = 0;
+                for (uint32_t i = b; i < e && ent[i].x < level; ++i) ++cnt;
+                counts |= min(cnt, 31u) << (5 * t);
+            }
+        }
+        cell[c] = make_uint2(b, counts);
+    }
+    if (mine) atomicMax(longest, mine);
 }
 
 }  // namespace
@@ -68,22 +91,22 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
     StreamIndex& si = ctx->sindex;
     const int gbits = kStreamGridBits, shift = 16 - kStreamGridBits;
     const int M = kStreamIndexPoints;
-    if (si.cell_start && si.seed == P->seed && si.K == (int)P->K) {
-        *out = StreamIndexView{si.cell_start, si.ent, M, gbits, shift};
+    if (si.cell && si.seed == P->seed && si.K == (int)P->K) {
+        *out = StreamIndexView{si.cell, si.ent, M, gbits, shift, si.ranked};
         return PMH_OK;
     }
-    if (si.cell_start) {
+    if (si.cell) {
         cudaDeviceSynchronize();
-        cudaFree(si.cell_start);
+        cudaFree(si.cell);
         cudaFree(si.ent);
         si = StreamIndex();
     }
     const int64_t n = (int64_t)P->K * M;
     const int64_t n_cells = (int64_t)P->K << (2 * gbits);
-    if (cudaMalloc(&si.cell_start, sizeof(uint32_t) * (n_cells + 1)) != cudaSuccess ||
+    if (cudaMalloc(&si.cell, sizeof(uint2) * (n_cells + 1)) != cudaSuccess ||
         cudaMalloc(&si.ent, sizeof(uint2) * n) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(si.cell_start);
+        cudaFree(si.cell);
         cudaFree(si.ent);
         si = StreamIndex();
         return pmh_set_error(PMH_ERR_NOMEM, "stream index allocation failed");
@@ -93,12 +116,13 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
     int64_t* counts = nullptr;
     if (cudaMalloc(&keys, sizeof(uint32_t) * n) != cudaSuccess ||
         cudaMalloc(&vals, sizeof(int32_t) * n) != cudaSuccess ||
-        cudaMalloc(&counts, sizeof(int64_t) * (n_cells + 1)) != cudaSuccess) {
+        cudaMalloc(&counts, sizeof(int64_t) * (n_cells + 2)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(keys);
         cudaFree(vals);
         return pmh_set_error(PMH_ERR_NOMEM, "stream index scratch allocation failed");
     }
+    int* longest = reinterpret_cast<int*>(counts + n_cells + 1);
     int rc = PMH_OK;
     const int blocks = ctx->sm_count * 16;
     stream_points_kernel<<<blocks, 256, 0, s>>>(P->seed, (int)P->K, M, shift, gbits, keys, vals);
@@ -108,7 +132,7 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
     int key_bits = 2 * gbits;
     while ((1ll << key_bits) < (int64_t)P->K << (2 * gbits)) ++key_bits;
     if (rc == PMH_OK) rc = pmh_radix_sort_u32(ctx, keys, vals, n, key_bits, s);
-    if (rc == PMH_OK && cudaMemsetAsync(counts, 0, sizeof(int64_t) * (n_cells + 1), s) != cudaSuccess)
+    if (rc == PMH_OK && cudaMemsetAsync(counts, 0, sizeof(int64_t) * (n_cells + 2), s) != cudaSuccess)
         rc = pmh_set_error(PMH_ERR_CUDA, "memset failed");
     if (rc == PMH_OK) {
         cell_count_kernel<<<blocks, 256, 0, s>>>(keys, n, counts);
@@ -116,27 +140,33 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
         rc = pmh_exclusive_scan_i64(ctx, counts, counts, n_cells, s);
     }
     if (rc == PMH_OK) {
-        finish_index_kernel<<<blocks, 256, 0, s>>>(keys, vals, n, counts, n_cells, P->seed, gbits,
-                                                    si.cell_start, si.ent);
+        finish_index_kernel<<<blocks, 256, 0, s>>>(keys, vals, n, P->seed, gbits, si.ent);
+        g_pmh_launches.fetch_add(1);
+        cell_record_kernel<<<blocks, 256, 0, s>>>(counts, n_cells, si.ent, M, si.cell, longest);
         g_pmh_launches.fetch_add(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "finish: %s", cudaGetErrorString(e));
     }
+    if (rc == PMH_OK && cudaMemcpyAsync(ctx->h_pinned, longest, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                            cudaSuccess)
+        rc = pmh_set_error(PMH_ERR_CUDA, "stream index: copy failed");
     cudaError_t e2 = cudaStreamSynchronize(s);
+    const int longest_list = rc == PMH_OK ? (int)*reinterpret_cast<int*>(ctx->h_pinned) : 0;
     cudaFree(keys);
     cudaFree(vals);
     cudaFree(counts);
     if (rc == PMH_OK && e2 != cudaSuccess)
         rc = pmh_set_error(PMH_ERR_CUDA, "stream index build: %s", cudaGetErrorString(e2));
     if (rc != PMH_OK) {
-        cudaFree(si.cell_start);
+        cudaFree(si.cell);
         cudaFree(si.ent);
         si = StreamIndex();
         return rc;
     }
     si.seed = P->seed;
     si.K = (int)P->K;
-    *out = StreamIndexView{si.cell_start, si.ent, M, gbits, shift};
+    si.ranked = longest_list <= 31;  // else the counts saturate: only the list ends are used
+    *out = StreamIndexView{si.cell, si.ent, M, gbits, shift, si.ranked};
     return PMH_OK;
 }
 

@@ -123,6 +123,35 @@ def test_sign_edge_cases(B, ctx, orc, flags):
     assert (h[0] == 0).all() and (h[2] == T).all()
 
 
+def comb(x0, y0, teeth, tw, gap, height, base):
+    """A comb: a bar of the given base height with `teeth` upward teeth (4 * teeth vertices)."""
+    xe = x0 + teeth * (tw + gap) - gap
+    pts = [[x0, y0], [xe, y0]]
+    for t in reversed(range(teeth)):
+        xl = x0 + t * (tw + gap)
+        pts += [[xl + tw, y0 + base + height], [xl, y0 + base + height]]
+        if t > 0:
+            pts += [[xl, y0 + base], [xl - gap, y0 + base]]
+    return pts
+
+
+@pytest.mark.parametrize("flags", FLAGS)
+def test_sign_indexed_form_paths(B, ctx, orc, flags):
+    """Small polygons signed through the stream index: a comb whose 240 vertices need
+    more slab references than a warp stages (one slab of every edge instead), more
+    hashes than one pass holds (K = 300), tiny boxes whose walks resume past the index,
+    and a cap below and above the index limit."""
+    polys = [comb(20000, 20000, 60, 10, 10, 1000, 50), comb(40000, 7000, 30, 12, 8, 400, 5)]
+    tiny = synth.star_polygons(40, 29, (3, 256), "loguniform", (1e-6, 3e-4))
+    polys += [tiny.poly(i) for i in range(tiny.n)]
+    ps = from_polys(polys)
+    for K, T in [(300, 1 << 24), (33, 5000), (64, 70000)]:
+        P = B.make_params(K, 1, T, flags=flags)
+        h = u32(B.minhash_sign(ctx, upload(B, ctx, ps), P))
+        ref = orc.sign(ps.xy, ps.offsets, SEED, K, T, nthreads=16)
+        assert np.array_equal(h, ref), (K, T)
+
+
 @pytest.fixture(scope="module")
 def scale_db():
     return synth.make_database(synth.WORKLOADS["scale"])
