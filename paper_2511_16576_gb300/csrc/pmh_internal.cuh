@@ -87,21 +87,24 @@ __host__ __device__ __forceinline__ uint32_t pmh_indexed_limit(int4 bb, long lon
     return (uint32_t)lim;
 }
 
-// Cell record of the stream index: .x = first entry of the cell's list (the
-// list ends where the next record's starts), .y = six 5-bit counts, bits
-// [5t, 5t+5) = entries of the list with stream index below M >> t.
+// Cell records of the stream index, cell-major: record (cell c, hash k) is
+// cell[c * K + k]; .x = first entry of the list of (k, c), which ends where
+// record (c + 1, k) starts (row c = G*G is the end of every hash's lists);
+// .y = six 5-bit counts, bits [5t, 5t+5) = entries of the list with stream
+// index below M >> t.  The records of one cell for consecutive hashes are
+// adjacent, so a warp reading one cell for sixteen hashes reads 128 bytes.
 constexpr int kRankLevels = 6;
 struct StreamIndex {
     uint64_t seed = 0;
     int K = 0;
-    uint2* cell = nullptr;  // [K * G * G + 1] records
+    uint2* cell = nullptr;  // [(G * G + 1) * K] records
     uint2* ent = nullptr;   // [K * M] (stream index, x | y << 16)
     int ranked = 0;         // every list fits the 5-bit counts
 };
 struct StreamIndexView {
     const uint2* cell;  // nullptr: no index
     const uint2* ent;
-    int M, gbits, shift, ranked;
+    int M, gbits, shift, ranked, K;
 };
 
 struct pmh_ctx_s {

@@ -73,11 +73,11 @@ __device__ uint32_t sign_chunk_indexed(const Inside& inside, const StreamIndexVi
         const int k = kb + g;
         int read = 0;
         if (k < kend) {
-            const uint2* cs = S.cell + ((int64_t)k << (2 * S.gbits));
+            const uint2* cs = S.cell + k;  // record of cell c: cs[c * K]
             uint2* cb = cbuf + g * kCand;
             for (int c = gl; c < C; c += 8) {
                 const int cell = ((cy0 + c / ncx) << S.gbits) | (cx0 + c % ncx);
-                const uint32_t beg = cs[cell].x, end = cs[cell + 1].x;
+                const uint32_t beg = cs[(int64_t)cell * S.K].x, end = cs[(int64_t)(cell + 1) * S.K].x;
                 for (uint32_t e = beg; e < end; e += 4) {
                     uint2 q[4];
 #pragma unroll
@@ -299,7 +299,7 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     const StreamIndexView* sidx, const uint32_t* masks,
                     const int32_t* order_cls, int64_t n_indexed)
 {
-    const StreamIndexView S = sidx ? *sidx : StreamIndexView{nullptr, nullptr, 0, 0, 0, 0};
+    const StreamIndexView S = sidx ? *sidx : StreamIndexView{nullptr, nullptr, 0, 0, 0, 0, 0};
     if (n_polys <= 0) return PMH_OK;
     unsigned long long* work = d_n ? nullptr : ctx->d_tickets + kWorkSlot;
     if (work) PMH_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long) * 6, s));

@@ -10,10 +10,11 @@
 //     32 x 32 coverage mask of the bounding box is built: a cell that no edge
 //     touches is wholly inside or wholly outside, decided by one exact test
 //     per run of such cells;
-//   * sixteen hashes at a time, the (hash, cell) pairs under the box are read
-//     one per lane, and the points they hold below the smallest level >= L are
-//     spread over the lanes by a warp scan (every lane loads one point, no
-//     lane walks a list).  A point in the box is classified by the mask: in an
+//   * sixteen hashes at a time, the (cell, hash) records under the box are
+//     read one per lane (two cells per round, adjacent records), and the
+//     points they hold below the smallest level >= L are spread over the lanes
+//     by a warp scan (every lane loads one point, no lane walks a list).  A
+//     point in the box is classified by the mask: in an
 //     inside cell it is a hit and bounds the hash from above, in an outside
 //     cell it is dropped, in a boundary cell it is kept;
 //   * the kept points whose index is below their hash's smallest hit are
@@ -59,15 +60,6 @@ __host__ __device__ __forceinline__ int mask32_log2(int w)
     return l;
 }
 
-// quotient a / b for 0 <= a < 2^22, 1 <= b, from a float reciprocal
-__device__ __forceinline__ int div_small(int a, int b, float inv)
-{
-    int q = (int)((float)a * inv);
-    if (q * b > a) --q;
-    else if ((q + 1) * b <= a) ++q;
-    return q;
-}
-
 // one slab holding every edge: the exact test then reads all n edges
 __device__ __forceinline__ int single_slab(IdxWarp& m, int n, int lane)
 {
@@ -78,46 +70,72 @@ __device__ __forceinline__ int single_slab(IdxWarp& m, int n, int lane)
     return 16;
 }
 
-// 32 x 32 coverage mask over the clipped box bb: bnd marks the cells whose
-// closed rectangle, grown by one unit on its low sides, meets an edge; every
-// lattice point of another cell (under the half-open reading, the point
-// shifted up and right by an infinitesimal) shares the membership of the whole
-// rectangle, and so does a run of such cells in a row -- one exact test at the
-// run's first lattice point classifies it.
+// 32 x 32 coverage mask over the clipped box bb (cell (i, j): lattice points
+// bb.x + [i*cw, (i+1)*cw) by bb.y + [j*ch, (j+1)*ch)).  bnd marks every cell
+// whose closed rectangle, grown by one unit on its low sides, meets an edge
+// (and possibly a few neighbours: the marking is conservative).  Every lattice
+// point of an unmarked cell (under the half-open reading, the point shifted up
+// and right by an infinitesimal) then shares the membership of the whole
+// rectangle.  Row j's unmarked cells are classified together from the edges
+// crossing the line y = bb.y + j*ch: a cell is inside iff an odd number of
+// crossings lies left of it.  A crossing lies in a marked cell of the row, at
+// least one unit left of or strictly right of every unmarked cell, so its
+// cell index -- computed in single precision, off by less than one unit --
+// never moves it across an unmarked cell, and the classification is exact.
 __device__ __forceinline__ void build_mask(IdxWarp& m, int n, int4 bb, int cwl, int chl,
                                            const StagedEdges& st, int lane, Work& work)
 {
     m.bnd[lane] = 0;
     __syncwarp();
+    const float inv_cw = 1.0f / (float)(1 << cwl);
+    const int ch = 1 << chl;
     for (int e = lane; e < n; e += 32) {
         const int2 a = m.v[e], c = m.v[e + 1];
-        const int ix0 = max(0, ((min(a.x, c.x) - bb.x) >> cwl) - 1);
-        const int ix1 = min(kMaskN - 1, (max(a.x, c.x) + 1 - bb.x) >> cwl);
-        const int iy0 = max(0, ((min(a.y, c.y) - bb.y) >> chl) - 1);
-        const int iy1 = min(kMaskN - 1, (max(a.y, c.y) + 1 - bb.y) >> chl);
-        for (int j = iy0; j <= iy1; ++j)
-            for (int i = ix0; i <= ix1; ++i) {
-                const long long rx0 = (long long)bb.x + ((long long)i << cwl) - 1;
-                const long long rx1 = (long long)bb.x + ((long long)(i + 1) << cwl);
-                const long long ry0 = (long long)bb.y + ((long long)j << chl) - 1;
-                const long long ry1 = (long long)bb.y + ((long long)(j + 1) << chl);
-                if (seg_meets_rect(a, c, rx0, ry0, rx1, ry1)) atomicOr(&m.bnd[j], 1u << i);
+        // rows whose grown band [j*ch - 1, (j+1)*ch] (relative) meets the edge's y-range
+        const int ylo = min(a.y, c.y) - bb.y, yhi = max(a.y, c.y) - bb.y;
+        const int j0 = max(0, ((ylo + ch - 1) >> chl) - 1);
+        const int j1 = min(kMaskN - 1, (yhi + 1) >> chl);
+        const float ax = (float)(a.x - bb.x), ay = (float)(a.y - bb.y);
+        const float dx = (float)(c.x - a.x);
+        const float inv_dy = c.y != a.y ? 1.0f / (float)(c.y - a.y) : 0.0f;
+        for (int j = j0; j <= j1; ++j) {
+            // the edge's x-range over the band (single precision, error < 1 unit)
+            float t0 = 0.0f, t1 = 1.0f;
+            if (c.y != a.y) {
+                t0 = fminf(fmaxf(((float)((j << chl) - 1) - ay) * inv_dy, 0.0f), 1.0f);
+                t1 = fminf(fmaxf(((float)((j + 1) << chl) - ay) * inv_dy, 0.0f), 1.0f);
             }
+            const float xa = ax + dx * t0, xb = ax + dx * t1;
+            // cells whose grown x-range [i*cw - 1, (i+1)*cw] meets it, one unit of margin
+            const int i0 = max(0, (int)ceilf((fminf(xa, xb) - 1.0f) * inv_cw) - 1);
+            const int i1 = min(kMaskN - 1, (int)floorf((fmaxf(xa, xb) + 2.0f) * inv_cw));
+            if (i0 <= i1) {
+                const uint32_t hi_bits = i1 == 31 ? 0xFFFFFFFFu : ((2u << i1) - 1u);
+                atomicOr(&m.bnd[j], hi_bits & ~((1u << i0) - 1u));
+            }
+        }
     }
     __syncwarp();
-    // lane j classifies the untouched runs of row j (rows below the box's top
-    // only: the slab lists cover [bb.y, bb.w))
+    // lane j: parity of the crossings of the line y = bb.y + j*ch left of each cell
+    // (rows below the box's top only: the slab lists cover [bb.y, bb.w))
     uint32_t word = 0;
     if ((lane << chl) < bb.w - bb.y) {
-        uint32_t free_cells = ~m.bnd[lane];
-        while (free_cells) {
-            const int s = __ffs(free_cells) - 1;
-            const uint32_t rest = free_cells >> s;
-            const int len = rest == 0xFFFFFFFFu ? 32 : __ffs(~rest) - 1;
-            const uint32_t run = (len == 32 ? 0xFFFFFFFFu : ((1u << len) - 1u)) << s;
-            if (st.lane_inside(bb.x + (s << cwl), bb.y + (lane << chl), work)) word |= run;
-            free_cells &= ~run;
+        const int py = bb.y + (lane << chl);
+        const int sl = (py - bb.y) >> st.sh;
+        const int lo = st.beg[sl], hi = st.beg[sl + 1];
+        uint32_t par = 0;
+        for (int t = lo; t < hi; ++t) {
+            const int e = st.ids[t];
+            const int2 a = m.v[e], b = m.v[e + 1];
+            if ((a.y > py) != (b.y > py)) {
+                const float x = (float)(a.x - bb.x) +
+                                (float)(b.x - a.x) * ((float)(py - a.y) / (float)(b.y - a.y));
+                const int ci = (int)floorf(x * inv_cw);
+                par ^= ci < 0 ? 0xFFFFFFFFu : (ci >= kMaskN - 1 ? 0u : (0xFFFFFFFFu << (ci + 1)));
+            }
         }
+        work.lane_edges += hi - lo;
+        word = par & ~m.bnd[lane];
     }
     m.inb[lane] = word;
     __syncwarp();
@@ -170,7 +188,7 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
     IdxWarp& m = smem[threadIdx.x >> 5];
     const unsigned full = 0xffffffffu;
     Work work;  // warp-uniform counts (walks, warp-cooperative tests) and lane-local edge counts
-    unsigned long long lane_cells = 0, lane_read = 0, lane_cand = 0, lane_masked = 0;
+    unsigned lane_cells = 0, lane_read = 0, lane_cand = 0, lane_masked = 0;
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(ticket, 1ull);
@@ -196,11 +214,12 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
         build_mask(m, n, bb, cwl, chl, st, lane, work);
         const MaskedStaged walker{&m, st, bb.x, bb.y, cwl, chl};
 
-        // cells under the box, row-major; pair = hash * C + cell
+        // cells under the box, row-major; a round reads two cells for the kSub
+        // hashes of a group (lane: hash lane & 15, cell 2 * round + lane / 16)
         const int cx0 = bb.x >> S.shift, cy0 = bb.y >> S.shift;
         const int ncx = ((bb.z - 1) >> S.shift) - cx0 + 1;
         const int C = ncx * (((bb.w - 1) >> S.shift) - cy0 + 1);
-        const float invC = 1.0f / (float)C, invX = 1.0f / (float)ncx;
+        const int hl = lane & (kSub - 1);
 
         for (int kc = 0; kc < K; kc += kSub) {
             const int kn = min(kSub, K - kc);
@@ -210,21 +229,28 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                 m.ovf = 0;
             }
             __syncwarp();
-            const int npairs = lim > 0 ? kn * C : 0;
-            const uint2* rec = S.cell + ((int64_t)kc << (2 * S.gbits));
-            for (int p0 = 0; p0 < npairs; p0 += 32) {
+            const uint2* rec = S.cell + kc + hl;
+            int cx = lane >> 4, cy = 0;
+            if (cx >= ncx) {
+                cx -= ncx;
+                ++cy;
+            }
+            for (int c0 = 0; lim > 0 && c0 < C; c0 += 2) {
                 // one (hash, cell) record per lane: its points below the level
-                const int pr = p0 + lane;
                 uint32_t first = 0, cnt = 0;
-                int hl = 0;
-                if (pr < npairs) {
-                    hl = div_small(pr, C, invC);
-                    const int c = pr - hl * C;
-                    const int cy = div_small(c, ncx, invX), cx = c - cy * ncx;
-                    const uint2 r = rec[((int64_t)hl << (2 * S.gbits)) + (((cy0 + cy) << S.gbits) | (cx0 + cx))];
+                if (c0 + (lane >> 4) < C && hl < kn) {
+                    const uint2 r = rec[(int64_t)(((cy0 + cy) << S.gbits) | (cx0 + cx)) * S.K];
                     first = r.x;
                     cnt = (r.y >> (5 * lev)) & 31u;
                     ++lane_cells;
+                }
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    cx += 1;
+                    if (cx >= ncx) {
+                        cx -= ncx;
+                        ++cy;
+                    }
                 }
                 uint32_t incl = cnt;
 #pragma unroll
@@ -244,7 +270,7 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                         if (__shfl_sync(full, excl, own + step) <= e) own += step;
                     const uint32_t o_first = __shfl_sync(full, first, own);
                     const uint32_t o_excl = __shfl_sync(full, excl, own);
-                    const int o_hl = __shfl_sync(full, hl, own);
+                    const int o_hl = own & (kSub - 1);
                     if ((int)e < E) {
                         const uint2 q = S.ent[o_first + (e - o_excl)];
                         ++lane_read;
@@ -316,7 +342,7 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
     }
     if (work_out) {
         unsigned long long le = work.lane_edges, en = lane_read, ca = lane_cand, ma = lane_masked,
-                           ce = lane_cells;
+                           ce = lane_cells;  // (the gather's 32-bit lane counts, widened)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             le += __shfl_xor_sync(full, le, o);

@@ -10,10 +10,10 @@
 // stream with index < L that lies in the bounding box is in one of those
 // cells.  If no point below L hits, the ordinary walk continues from L.
 //
-// Layout (k-major): entry e of hash k lives in [cell[k*G*G + c].x,
-// cell[k*G*G + c + 1].x) for its cell c; ent[e] = (stream index, x | y << 16),
-// indices ascending within a cell, one 8-byte load per entry.  cell[.].y holds
-// six 5-bit counts: the entries of the cell below M, M/2, ..., M/32, so that a
+// Layout: the entries are sorted by (hash k, cell c, stream index); entry e =
+// (stream index, x | y << 16), one 8-byte load.  The list of (k, c) is
+// [cell[c*K + k].x, cell[(c+1)*K + k].x) (cell-major records).  cell[.].y holds
+// six 5-bit counts: the entries of the list below M, M/2, ..., M/32, so that a
 // reader with limit L knows how many entries to read (those below the smallest
 // level >= L) without reading past them.
 #include <algorithm>
@@ -59,27 +59,29 @@ __global__ void finish_index_kernel(const uint32_t* __restrict__ keys, const int
     }
 }
 
-// cell records: start and the rank counts of each level; *longest = longest list
-__global__ void cell_record_kernel(const int64_t* __restrict__ starts, int64_t n_cells,
+// cell records (cell-major) from the k-major list starts: start and the rank
+// counts of each level; row G*G holds each hash's end.  *longest = longest list
+__global__ void cell_record_kernel(const int64_t* __restrict__ starts, int K, int gbits,
                                    const uint2* __restrict__ ent, int M, uint2* __restrict__ cell,
                                    int* __restrict__ longest)
 {
+    const int64_t GG = (int64_t)1 << (2 * gbits);
+    const int64_t n_cells = GG * K;
     int mine = 0;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= n_cells;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells;
          c += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t b = (uint32_t)starts[c];
+        const int64_t k = c >> (2 * gbits), cl = c & (GG - 1);
+        const uint32_t b = (uint32_t)starts[c], e = (uint32_t)starts[c + 1];
+        mine = max(mine, (int)(e - b));
         uint32_t counts = 0;
-        if (c < n_cells) {
-            const uint32_t e = (uint32_t)starts[c + 1];
-            mine = max(mine, (int)(e - b));
-            for (int t = 0; t < kRankLevels; ++t) {
-                const uint32_t level = (uint32_t)M >> t;
-                uint32_t cnt = 0;
-                for (uint32_t i = b; i < e && ent[i].x < level; ++i) ++cnt;
-                counts |= min(cnt, 31u) << (5 * t);
-            }
+        for (int t = 0; t < kRankLevels; ++t) {
+            const uint32_t level = (uint32_t)M >> t;
+            uint32_t cnt = 0;
+            for (uint32_t i = b; i < e && ent[i].x < level; ++i) ++cnt;
+            counts |= min(cnt, 31u) << (5 * t);
         }
-        cell[c] = make_uint2(b, counts);
+        cell[cl * K + k] = make_uint2(b, counts);
+        if (cl == GG - 1) cell[GG * K + k] = make_uint2(e, 0u);
     }
     if (mine) atomicMax(longest, mine);
 }
@@ -92,7 +94,7 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
     const int gbits = kStreamGridBits, shift = 16 - kStreamGridBits;
     const int M = kStreamIndexPoints;
     if (si.cell && si.seed == P->seed && si.K == (int)P->K) {
-        *out = StreamIndexView{si.cell, si.ent, M, gbits, shift, si.ranked};
+        *out = StreamIndexView{si.cell, si.ent, M, gbits, shift, si.ranked, si.K};
         return PMH_OK;
     }
     if (si.cell) {
@@ -103,7 +105,7 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
     }
     const int64_t n = (int64_t)P->K * M;
     const int64_t n_cells = (int64_t)P->K << (2 * gbits);
-    if (cudaMalloc(&si.cell, sizeof(uint2) * (n_cells + 1)) != cudaSuccess ||
+    if (cudaMalloc(&si.cell, sizeof(uint2) * (n_cells + P->K)) != cudaSuccess ||
         cudaMalloc(&si.ent, sizeof(uint2) * n) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(si.cell);
@@ -142,7 +144,7 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
     if (rc == PMH_OK) {
         finish_index_kernel<<<blocks, 256, 0, s>>>(keys, vals, n, P->seed, gbits, si.ent);
         g_pmh_launches.fetch_add(1);
-        cell_record_kernel<<<blocks, 256, 0, s>>>(counts, n_cells, si.ent, M, si.cell, longest);
+        cell_record_kernel<<<blocks, 256, 0, s>>>(counts, (int)P->K, gbits, si.ent, M, si.cell, longest);
         g_pmh_launches.fetch_add(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "finish: %s", cudaGetErrorString(e));
@@ -166,7 +168,7 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
     si.seed = P->seed;
     si.K = (int)P->K;
     si.ranked = longest_list <= 31;  // else the counts saturate: only the list ends are used
-    *out = StreamIndexView{si.cell, si.ent, M, gbits, shift, si.ranked};
+    *out = StreamIndexView{si.cell, si.ent, M, gbits, shift, si.ranked, si.K};
     return PMH_OK;
 }
 
