@@ -158,6 +158,21 @@ int pmh_stream_index_build(pmh_ctx ctx, const pmh_params* params, void* stream);
  * (h_counts holds 6 values). */
 int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts);
 
+/* Measurement support (no counterpart in the paper).  pmh_minhash_sign runs
+ * two kernels: the indexed form of the polygons staged in shared memory, then
+ * the walk (and the indexed form of larger polygons) for the rest.
+ * pmh_sign_timing(ctx, 1) makes later signing calls on this context record
+ * CUDA events before, between and after the two kernels on the caller's
+ * stream, without synchronising (0 stops it; at most 1024 calls are kept).
+ * pmh_sign_report (synchronises) returns h_ms[0] / h_ms[1] = mean
+ * milliseconds of the indexed / walk kernel over the calls recorded since the
+ * previous report, h_ms[2] = their number (h_ms holds 3 floats; NULL: skip;
+ * the recorded calls are then forgotten), and h_counts[0..5] / [6..11] = the
+ * six work counts of pmh_sign_work for each kernel alone in the last signing
+ * call (NULL: skip).  Errors: PMH_ERR_ARG (null context), PMH_ERR_CUDA. */
+int pmh_sign_timing(pmh_ctx ctx, int enable);
+int pmh_sign_report(pmh_ctx ctx, float* h_ms, uint64_t* h_counts);
+
 /* A2 -- band keys (hashmap keys of Sec. 3.2 after Theorem 1, one per band).
  * Band j covers hashes j*r .. j*r+r-1; a = mix64(lsh_seed + (j+1)*G), then
  * a = mix64(a ^ h) for each of its r hashes; a band holding T has key

@@ -62,6 +62,8 @@ _SIGS = {
     "pmh_band_keys": (ctypes.c_int, [_P, _P, _i64, ctypes.POINTER(Params), _P, _P]),
     "pmh_stream_index_build": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P]),
     "pmh_sign_work": (ctypes.c_int, [_P, _P]),
+    "pmh_sign_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pmh_sign_report": (ctypes.c_int, [_P, _P, _P]),
     "pmh_lsh_build": (ctypes.c_int, [_P, _P, _i64, ctypes.POINTER(Params), ctypes.POINTER(_P), _P]),
     "pmh_index_destroy": (ctypes.c_int, [_P]),
     "pmh_lsh_query": (ctypes.c_int, [_P, _P, _P, _i64, _P, _P, _i64, ctypes.POINTER(_i64), _P]),
@@ -277,6 +279,26 @@ def sign_work(ctx: Context) -> dict:
     _check(load().pmh_sign_work(ctx.handle, c.ctypes.data))
     return dict(zip(("walk_points", "cells", "index_entries", "candidates", "edge_tests",
                      "mask_decisions"), (int(v) for v in c)))
+
+
+WORK_KEYS = ("walk_points", "cells", "index_entries", "candidates", "edge_tests", "mask_decisions")
+
+
+def sign_timing(ctx: Context, enable: bool = True):
+    """Record per-kernel events in later signing calls (indexed kernel, walk kernel)."""
+    _check(load().pmh_sign_timing(ctx.handle, 1 if enable else 0))
+
+
+def sign_report(ctx: Context) -> dict:
+    """Mean per-kernel milliseconds over the signing calls recorded since the last
+    report, and the per-kernel work counts of the last signing call."""
+    import numpy as np
+    ms = np.zeros(3, np.float32)
+    c = np.zeros(12, np.uint64)
+    _check(load().pmh_sign_report(ctx.handle, ms.ctypes.data, c.ctypes.data))
+    return {"calls": int(ms[2]),
+            "indexed": {"ms": float(ms[0]), "work": dict(zip(WORK_KEYS, (int(v) for v in c[:6])))},
+            "walk": {"ms": float(ms[1]), "work": dict(zip(WORK_KEYS, (int(v) for v in c[6:])))}}
 
 
 def band_keys(ctx: Context, hashes: torch.Tensor, params: Params, out=None, stream=None):

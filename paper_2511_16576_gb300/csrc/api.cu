@@ -110,6 +110,7 @@ extern "C" int pmh_destroy(pmh_ctx ctx)
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->d_tickets) cudaFree(ctx->d_tickets);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    for (cudaEvent_t e : ctx->sign_ev) cudaEventDestroy(e);
     if (ctx->sindex.cell) cudaFree(ctx->sindex.cell);
     if (ctx->sindex.ent) cudaFree(ctx->sindex.ent);
     delete ctx;

@@ -8,6 +8,7 @@
 
 #include <atomic>
 #include <string>
+#include <vector>
 
 #include "../../include/polyminhash.h"
 
@@ -117,6 +118,9 @@ struct pmh_ctx_s {
     int64_t* h_pinned = nullptr;          // small pinned host buffer [64]
     int sign_variant = -1;                // autotuned signing kernel (-1 = default)
     StreamIndex sindex;                   // cached stream index (PMH_FLAG_STREAM_INDEX)
+    int sign_timing = 0;                  // record per-kernel events in pmh_minhash_sign
+    std::vector<cudaEvent_t> sign_ev;     // three per recorded call
+    size_t sign_ev_used = 0;
 };
 
 int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, StreamIndexView* out);

@@ -35,7 +35,8 @@ namespace {
 
 constexpr int kWarps = 8;        // warps per block
 constexpr int kU = 4;            // points per lane per round
-constexpr int kWorkSlot = 8;     // context ticket slots 8..13: work counters of the last sign
+constexpr int kWorkSlot = 8;     // context ticket slots 8..13: work counters of the walk kernel
+constexpr int kIdxWorkSlot = 16; // slots 16..21: work counters of the indexed kernel
 
 __device__ __forceinline__ uint32_t sign_one(const int2* __restrict__ v, int n, int x0, int y0,
                                              uint32_t w, uint32_t h, uint64_t sk, uint32_t T,
@@ -302,15 +303,35 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
     const StreamIndexView S = sidx ? *sidx : StreamIndexView{nullptr, nullptr, 0, 0, 0, 0, 0};
     if (n_polys <= 0) return PMH_OK;
     unsigned long long* work = d_n ? nullptr : ctx->d_tickets + kWorkSlot;
-    if (work) PMH_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long) * 6, s));
+    if (work) {
+        PMH_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long) * 6, s));
+        PMH_CUDA_TRY(cudaMemsetAsync(ctx->d_tickets + kIdxWorkSlot, 0, sizeof(unsigned long long) * 6, s));
+    }
+    const bool timed = ctx->sign_timing && !d_n && ctx->sign_ev_used + 3 <= 3 * 1024;
+    cudaEvent_t* ev = nullptr;
+    if (timed) {
+        while (ctx->sign_ev.size() < ctx->sign_ev_used + 3) {
+            cudaEvent_t e;
+            PMH_CUDA_TRY(cudaEventCreate(&e));
+            ctx->sign_ev.push_back(e);
+        }
+        ev = ctx->sign_ev.data() + ctx->sign_ev_used;
+        ctx->sign_ev_used += 3;
+        PMH_CUDA_TRY(cudaEventRecord(ev[0], s));
+    }
     if (S.cell && S.ranked && order_cls && area2 && !d_n) {
         // staged polygons of the indexed form (the first n_indexed of the class
         // order) in their own kernel; the rest below, in cost order
         PMH_TRY(pmh_launch_sign_indexed(ctx, xy, off, bbox, area2, order_cls, n_indexed, P, S,
-                                        ticket + 2, out, work, s));
+                                        ticket + 2, out, work ? ctx->d_tickets + kIdxWorkSlot : nullptr,
+                                        s));
         order = order_cls + n_indexed;
         n_polys -= n_indexed;
-        if (n_polys <= 0) return PMH_OK;
+    }
+    if (timed) PMH_CUDA_TRY(cudaEventRecord(ev[1], s));
+    if (n_polys <= 0) {
+        if (timed) PMH_CUDA_TRY(cudaEventRecord(ev[2], s));
+        return PMH_OK;
     }
     const SignVariant& v = kSignVariants[ctx->sign_variant >= 0 ? ctx->sign_variant : 0];
     const int chunks = (int)((P->K + 31) / 32);
@@ -324,6 +345,7 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                                           P->seed, (int)P->K, P->T, chunks, n_polys, d_n, d_flags,
                                           ticket, out, area2, S, work, masks);
     PMH_LAUNCHED("sign_kernel");
+    if (timed) PMH_CUDA_TRY(cudaEventRecord(ev[2], s));
     return PMH_OK;
 }
 
@@ -351,9 +373,48 @@ extern "C" int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts)
 {
     PMH_TRY(pmh_check_device(ctx));
     if (!h_counts) return pmh_set_error(PMH_ERR_ARG, "null output");
+    uint64_t both[12];
     PMH_CUDA_TRY(cudaDeviceSynchronize());
-    PMH_CUDA_TRY(cudaMemcpy(h_counts, ctx->d_tickets + kWorkSlot, sizeof(uint64_t) * 6,
+    PMH_CUDA_TRY(cudaMemcpy(both, ctx->d_tickets + kIdxWorkSlot, sizeof(uint64_t) * 6,
                             cudaMemcpyDeviceToHost));
+    PMH_CUDA_TRY(cudaMemcpy(both + 6, ctx->d_tickets + kWorkSlot, sizeof(uint64_t) * 6,
+                            cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 6; ++i) h_counts[i] = both[i] + both[6 + i];
+    return PMH_OK;
+}
+
+extern "C" int pmh_sign_timing(pmh_ctx ctx, int enable)
+{
+    if (!ctx) return pmh_set_error(PMH_ERR_ARG, "null context");
+    ctx->sign_timing = enable != 0;
+    return PMH_OK;
+}
+
+extern "C" int pmh_sign_report(pmh_ctx ctx, float* h_ms, uint64_t* h_counts)
+{
+    PMH_TRY(pmh_check_device(ctx));
+    PMH_CUDA_TRY(cudaDeviceSynchronize());
+    if (h_ms) {
+        double a = 0.0, b = 0.0;
+        const size_t calls = ctx->sign_ev_used / 3;
+        for (size_t c = 0; c < calls; ++c) {
+            float x = 0.0f, y = 0.0f;
+            PMH_CUDA_TRY(cudaEventElapsedTime(&x, ctx->sign_ev[3 * c], ctx->sign_ev[3 * c + 1]));
+            PMH_CUDA_TRY(cudaEventElapsedTime(&y, ctx->sign_ev[3 * c + 1], ctx->sign_ev[3 * c + 2]));
+            a += x;
+            b += y;
+        }
+        h_ms[0] = calls ? (float)(a / calls) : -1.0f;
+        h_ms[1] = calls ? (float)(b / calls) : -1.0f;
+        h_ms[2] = (float)calls;
+        ctx->sign_ev_used = 0;
+    }
+    if (h_counts) {
+        PMH_CUDA_TRY(cudaMemcpy(h_counts, ctx->d_tickets + kIdxWorkSlot, sizeof(uint64_t) * 6,
+                                cudaMemcpyDeviceToHost));
+        PMH_CUDA_TRY(cudaMemcpy(h_counts + 6, ctx->d_tickets + kWorkSlot, sizeof(uint64_t) * 6,
+                                cudaMemcpyDeviceToHost));
+    }
     return PMH_OK;
 }
 

@@ -235,6 +235,7 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                 cx -= ncx;
                 ++cy;
             }
+            if (lim > 0 && lane == 0) lane_cells += (unsigned)(C * kn);
             for (int c0 = 0; lim > 0 && c0 < C; c0 += 2) {
                 // one (hash, cell) record per lane: its points below the level
                 uint32_t first = 0, cnt = 0;
@@ -242,7 +243,6 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                     const uint2 r = rec[(int64_t)(((cy0 + cy) << S.gbits) | (cx0 + cx)) * S.K];
                     first = r.x;
                     cnt = (r.y >> (5 * lev)) & 31u;
-                    ++lane_cells;
                 }
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
@@ -260,6 +260,7 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                 }
                 const uint32_t excl = incl - cnt;
                 const int E = (int)__shfl_sync(full, incl, 31);
+                lane_read += lane == 0 ? (unsigned)E : 0u;
                 // spread the points over the lanes: point e belongs to the last
                 // lane whose exclusive offset is <= e
                 for (int e0 = 0; e0 < E; e0 += 32) {
@@ -273,7 +274,6 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                     const int o_hl = own & (kSub - 1);
                     if ((int)e < E) {
                         const uint2 q = S.ent[o_first + (e - o_excl)];
-                        ++lane_read;
                         const uint32_t r = q.y;
                         const uint32_t dx = (r & 0xFFFFu) - (uint32_t)bb.x;
                         const uint32_t dy = (r >> 16) - (uint32_t)bb.y;
