@@ -150,8 +150,10 @@ struct pmh_polys_s {
     int32_t* slab_ptr = nullptr;
     int32_t* slab_edges = nullptr;
     int32_t* order = nullptr;       // polygons by expected signing cost, largest first
-    int32_t* order_cls = nullptr;   // the same, staged indexed-form polygons first
-    int64_t n_indexed = 0;          // number of those (<= kStagedMaxVerts vertices, pmh_indexed_limit > 0)
+    int32_t* order_cls = nullptr;   // class order: staged indexed-form polygons (Morton order),
+                                    // staged walk-form polygons, the rest (each by cost)
+    int64_t n_indexed = 0;          // class 0: <= kStagedMaxVerts vertices, pmh_indexed_limit > 0
+    int64_t n_staged_walk = 0;      // class 1: <= kStagedMaxVerts vertices, walk form
     uint32_t* mask = nullptr;       // [n][16] coverage masks
 };
 
@@ -237,7 +239,14 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     const int64_t* d_n, const int* d_flags, unsigned long long* ticket,
                     uint32_t* out, cudaStream_t s, const int64_t* area2 = nullptr,
                     const StreamIndexView* sidx = nullptr, const uint32_t* masks = nullptr,
-                    const int32_t* order_cls = nullptr, int64_t n_indexed = 0);
+                    const int32_t* order_cls = nullptr, int64_t n_indexed = 0,
+                    int64_t n_staged_walk = 0);
+// walk form of the staged polygons list[0 .. n_list) (sign_indexed.cu; U = points
+// per lane per round: 2, 4 or 8)
+int pmh_launch_sign_walk_staged(pmh_ctx ctx, int U, const int2* xy, const int64_t* off,
+                                const int4* bbox, const int32_t* list, int64_t n_list,
+                                const pmh_params* P, unsigned long long* ticket, uint32_t* out,
+                                unsigned long long* work, cudaStream_t s);
 // indexed form of the staged polygons list[0 .. n_list) (sign_indexed.cu); ticket is
 // its own work-queue counter, work (optional) the six work counters
 int pmh_launch_sign_indexed(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4* bbox,

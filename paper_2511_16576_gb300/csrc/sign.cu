@@ -298,7 +298,7 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     const int64_t* d_n, const int* d_flags, unsigned long long* ticket,
                     uint32_t* out, cudaStream_t s, const int64_t* area2,
                     const StreamIndexView* sidx, const uint32_t* masks,
-                    const int32_t* order_cls, int64_t n_indexed)
+                    const int32_t* order_cls, int64_t n_indexed, int64_t n_staged_walk)
 {
     const StreamIndexView S = sidx ? *sidx : StreamIndexView{nullptr, nullptr, 0, 0, 0, 0, 0};
     if (n_polys <= 0) return PMH_OK;
@@ -327,6 +327,15 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                                         s));
         order = order_cls + n_indexed;
         n_polys -= n_indexed;
+        if (!masks) {
+            // staged polygons of the walk form in their own kernel (with the
+            // precomputed masks of PMH_FLAG_COVERAGE_MASK they stay below)
+            const int U = kSignVariants[ctx->sign_variant >= 0 ? ctx->sign_variant : 0].U;
+            PMH_TRY(pmh_launch_sign_walk_staged(ctx, U, xy, off, bbox, order, n_staged_walk, P, ticket + 4,
+                                                out, work, s));
+            order += n_staged_walk;
+            n_polys -= n_staged_walk;
+        }
     }
     if (timed) PMH_CUDA_TRY(cudaEventRecord(ev[1], s));
     if (n_polys <= 0) {
@@ -366,7 +375,7 @@ extern "C" int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* 
                            polys->slab_ptr, polys->slab_edges, polys->order, params, polys->n,
                            nullptr, nullptr, ctx->d_tickets + 0, d_hashes, (cudaStream_t)stream,
                            polys->area2, indexed ? &sidx : nullptr, masked ? polys->mask : nullptr,
-                           polys->order_cls, polys->n_indexed);
+                           polys->order_cls, polys->n_indexed, polys->n_staged_walk);
 }
 
 extern "C" int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts)
@@ -470,7 +479,7 @@ extern "C" int pmh_sign_autotune(pmh_ctx ctx, pmh_polys sample, const pmh_params
                                      sample->n, nullptr, nullptr, ctx->d_tickets + 1, out, 0,
                                      sample->area2, indexed ? &sidx : nullptr,
                                      masked ? sample->mask : nullptr, sample->order_cls,
-                                     sample->n_indexed);
+                                     sample->n_indexed, sample->n_staged_walk);
             cudaEventRecord(e1, 0);
             if (cudaEventSynchronize(e1) != cudaSuccess)
                 rc = pmh_set_error(PMH_ERR_CUDA, "autotune run failed");

@@ -53,6 +53,16 @@ struct IdxWarp {
     uint32_t ovf;            // bit j: hash j lost kept points
 };
 
+// the staged polygon, its slab lists and its mask: the state of the walk kernel
+struct WalkWarp {
+    int2 v[kSmemVerts + 1];
+    uint8_t ids[kSlabCap];
+    uint16_t beg[kSlabs + 1];
+    int cnt[kSlabs];
+    uint32_t bnd[kMaskN];
+    uint32_t inb[kMaskN];
+};
+
 __host__ __device__ __forceinline__ int mask32_log2(int w)
 {
     int a = (w + kMaskN - 1) / kMaskN, l = 0;
@@ -61,7 +71,8 @@ __host__ __device__ __forceinline__ int mask32_log2(int w)
 }
 
 // one slab holding every edge: the exact test then reads all n edges
-__device__ __forceinline__ int single_slab(IdxWarp& m, int n, int lane)
+template <class Warp>
+__device__ __forceinline__ int single_slab(Warp& m, int n, int lane)
 {
     for (int e = lane; e < n; e += 32) m.ids[e] = (uint8_t)e;
     if (lane == 0) m.beg[0] = 0;
@@ -82,7 +93,8 @@ __device__ __forceinline__ int single_slab(IdxWarp& m, int n, int lane)
 // least one unit left of or strictly right of every unmarked cell, so its
 // cell index -- computed in single precision, off by less than one unit --
 // never moves it across an unmarked cell, and the classification is exact.
-__device__ __forceinline__ void build_mask(IdxWarp& m, int n, int4 bb, int cwl, int chl,
+template <class Warp>
+__device__ __forceinline__ void build_mask(Warp& m, int n, int4 bb, int cwl, int chl,
                                            const StagedEdges& st, int lane, Work& work)
 {
     m.bnd[lane] = 0;
@@ -143,8 +155,9 @@ __device__ __forceinline__ void build_mask(IdxWarp& m, int n, int4 bb, int cwl, 
 
 // Membership through the mask (warp-cooperative, for the resumed walk):
 // untouched cells by their code, boundary cells by the exact slab test.
+template <class Warp>
 struct MaskedStaged {
-    const IdxWarp* m;
+    const Warp* m;
     StagedEdges st;
     int x0, y0, cwl, chl;
     __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
@@ -212,7 +225,7 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
         const StagedEdges st{m.v, m.ids, m.beg, bb.y, sh};
         const int cwl = mask32_log2((int)w), chl = mask32_log2((int)h);
         build_mask(m, n, bb, cwl, chl, st, lane, work);
-        const MaskedStaged walker{&m, st, bb.x, bb.y, cwl, chl};
+        const MaskedStaged<IdxWarp> walker{&m, st, bb.x, bb.y, cwl, chl};
 
         // cells under the box, row-major; a round reads two cells for the kSub
         // hashes of a group (lane: hash lane & 15, cell 2 * round + lane / 16)
@@ -236,14 +249,13 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                 ++cy;
             }
             if (lim > 0 && lane == 0) lane_cells += (unsigned)(C * kn);
+            // the records of the next round are loaded while this round's points are read
+            uint2 rnext = make_uint2(0u, 0u);
+            if (lim > 0 && (lane >> 4) < C && hl < kn)
+                rnext = rec[(int64_t)(((cy0 + cy) << S.gbits) | (cx0 + cx)) * S.K];
             for (int c0 = 0; lim > 0 && c0 < C; c0 += 2) {
                 // one (hash, cell) record per lane: its points below the level
-                uint32_t first = 0, cnt = 0;
-                if (c0 + (lane >> 4) < C && hl < kn) {
-                    const uint2 r = rec[(int64_t)(((cy0 + cy) << S.gbits) | (cx0 + cx)) * S.K];
-                    first = r.x;
-                    cnt = (r.y >> (5 * lev)) & 31u;
-                }
+                const uint2 r = rnext;
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                     cx += 1;
@@ -252,6 +264,10 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                         ++cy;
                     }
                 }
+                rnext = make_uint2(0u, 0u);
+                if (c0 + 2 + (lane >> 4) < C && hl < kn)
+                    rnext = rec[(int64_t)(((cy0 + cy) << S.gbits) | (cx0 + cx)) * S.K];
+                const uint32_t first = r.x, cnt = (r.y >> (5 * lev)) & 31u;
                 uint32_t incl = cnt;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
@@ -366,7 +382,95 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
     }
 }
 
+// Walk form (Algorithm 1 in warp rounds) for the staged polygons the cost model
+// leaves to the walk: one warp per polygon and all of its hashes; vertices,
+// slab lists and coverage mask staged once, so a box candidate of the walk is
+// decided by the mask or by one slab's edges.
+template <int U, int W>
+__global__ void __launch_bounds__(W * 32, kIdxMinBlocks)
+sign_walk_staged_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
+                        const int4* __restrict__ bbox, const int32_t* __restrict__ list,
+                        int64_t n_list, uint64_t seed, int K, uint32_t T,
+                        unsigned long long* __restrict__ ticket, uint32_t* __restrict__ out,
+                        unsigned long long* __restrict__ work_out)
+{
+    __shared__ WalkWarp smem[W];
+    __shared__ unsigned long long wsum[6];
+    if (threadIdx.x < 6) wsum[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    WalkWarp& m = smem[threadIdx.x >> 5];
+    const unsigned full = 0xffffffffu;
+    Work work;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(ticket, 1ull);
+        item = __shfl_sync(full, item, 0);
+        if ((int64_t)item >= n_list) break;
+        const int64_t p = list[item];
+        const int64_t b = off[p];
+        const int n = (int)(off[p + 1] - b);
+        const int4 bb = bbox[p];
+        const uint32_t w = (uint32_t)max(bb.z - bb.x, 0), h = (uint32_t)max(bb.w - bb.y, 0);
+        int sh = 16, cwl = 0, chl = 0;
+        if (w > 0 && h > 0) {
+            for (int i = lane; i < n; i += 32) m.v[i] = xy[b + i];
+            if (lane == 0) m.v[n] = xy[b];
+            __syncwarp();
+            sh = staged_slab_shift((int)h);
+            if (!build_staged_slabs(m.v, n, bb.y, sh, m.ids, m.beg, m.cnt, lane)) sh = single_slab(m, n, lane);
+            cwl = mask32_log2((int)w);
+            chl = mask32_log2((int)h);
+            build_mask(m, n, bb, cwl, chl, StagedEdges{m.v, m.ids, m.beg, bb.y, sh}, lane, work);
+        }
+        const MaskedStaged<WalkWarp> walker{&m, StagedEdges{m.v, m.ids, m.beg, bb.y, sh}, bb.x, bb.y, cwl, chl};
+        for (int k0 = 0; k0 < K; k0 += 32) {
+            const int kend = min(K, k0 + 32);
+            uint32_t mine = T;
+            for (int k = k0; k < kend; ++k) {
+                const uint64_t sk = pmh_mix64(seed + (uint64_t)(k + 1) * PMH_GAMMA);
+                const uint32_t hk = sign_one_t<U>(walker, bb.x, bb.y, w, h, sk, T, lane, work);
+                if (lane == k - k0) mine = hk;
+            }
+            if (k0 + lane < kend) out[p * (int64_t)K + k0 + lane] = mine;
+        }
+        __syncwarp();
+    }
+    if (work_out) {
+        unsigned long long le = work.lane_edges;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) le += __shfl_xor_sync(full, le, o);
+        if (lane == 0) {
+            atomicAdd(&wsum[0], work.walk);
+            atomicAdd(&wsum[3], work.cand);
+            atomicAdd(&wsum[4], work.edges + le);
+            atomicAdd(&wsum[5], work.masked);
+        }
+        __syncthreads();
+        if (threadIdx.x < 6) atomicAdd(&work_out[threadIdx.x], wsum[threadIdx.x]);
+    }
+}
+
 }  // namespace
+
+int pmh_launch_sign_walk_staged(pmh_ctx ctx, int U, const int2* xy, const int64_t* off,
+                                const int4* bbox, const int32_t* list, int64_t n_list,
+                                const pmh_params* P, unsigned long long* ticket, uint32_t* out,
+                                unsigned long long* work, cudaStream_t s)
+{
+    if (n_list <= 0) return PMH_OK;
+    auto fn = U <= 2 ? sign_walk_staged_kernel<2, kIdxWarps>
+            : U <= 4 ? sign_walk_staged_kernel<4, kIdxWarps> : sign_walk_staged_kernel<8, kIdxWarps>;
+    int per_sm = 0;
+    PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kIdxWarps * 32, 0));
+    int64_t blocks = (int64_t)ctx->sm_count * std::max(per_sm, 1);
+    blocks = std::min<int64_t>(blocks, (n_list + kIdxWarps - 1) / kIdxWarps);
+    PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
+    fn<<<(int)blocks, kIdxWarps * 32, 0, s>>>(xy, off, bbox, list, n_list, P->seed, (int)P->K, P->T,
+                                              ticket, out, work);
+    PMH_LAUNCHED("sign_walk_staged_kernel");
+    return PMH_OK;
+}
 
 int pmh_launch_sign_indexed(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4* bbox,
                             const int64_t* area2, const int32_t* list, int64_t n_list,

@@ -144,8 +144,8 @@ __global__ void cost_key_kernel(const int64_t* __restrict__ area2, int64_t n,
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         long long a = area2[p];
-        double aa = (double)(a < 0 ? -a : a);
-        float cost = (float)(8589934592.0 / fmax(aa, 1.0));
+        const float aa = (float)(a < 0 ? -a : a);
+        const float cost = 8589934592.0f / fmaxf(aa, 1.0f);
         keys[p] = ~__float_as_uint(cost);  // positive floats order like their bits
         ids[p] = (int32_t)p;
     }
@@ -167,29 +167,38 @@ __device__ __forceinline__ uint32_t morton16(uint32_t x, uint32_t y)
 
 // class key: staged polygons of the indexed form first (class 0) in Morton
 // order of their box centres -- warps running at the same time then read
-// nearby cells of the stream index, which keeps them in L2 -- and the rest
-// (class 1) by decreasing expected cost; counts class 0 into *n_cls0
+// nearby cells of the stream index, which keeps them in L2 -- then staged
+// polygons of the walk form (class 1) and the rest (class 2), each by
+// decreasing expected cost; counts classes 0 and 1 into n_cls[0], n_cls[1]
 __global__ void class_key_kernel(const int4* __restrict__ bbox, const int64_t* __restrict__ area2,
                                  const int64_t* __restrict__ off, int64_t n,
                                  uint32_t* __restrict__ keys, int32_t* __restrict__ ids,
-                                 unsigned long long* __restrict__ n_cls0)
+                                 unsigned long long* __restrict__ n_cls)
 {
-    unsigned long long mine = 0;
+    unsigned long long c0 = 0, c1 = 0;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const long long a = area2[p];
-        const double aa = (double)(a < 0 ? -a : a);
-        const float cost = (float)(8589934592.0 / fmax(aa, 1.0));
-        const bool staged_indexed =
-            off[p + 1] - off[p] <= kStagedMaxVerts && pmh_indexed_limit(bbox[p], a) > 0;
+        const float aa = (float)(a < 0 ? -a : a);
+        const float cost = 8589934592.0f / fmaxf(aa, 1.0f);
         const int4 bb = bbox[p];
-        const uint32_t cx = (uint32_t)min((bb.x + bb.z) >> 1, 65535);
-        const uint32_t cy = (uint32_t)min((bb.y + bb.w) >> 1, 65535);
-        keys[p] = staged_indexed ? (morton16(cx, cy) >> 1) : ((1u << 31) | (~__float_as_uint(cost) >> 1));
+        const bool staged = off[p + 1] - off[p] <= kStagedMaxVerts;
+        const int cls = !staged ? 2 : pmh_indexed_limit(bb, a) > 0 ? 0 : 1;
+        uint32_t key;
+        if (cls == 0) {
+            const uint32_t cx = (uint32_t)min((bb.x + bb.z) >> 1, 65535);
+            const uint32_t cy = (uint32_t)min((bb.y + bb.w) >> 1, 65535);
+            key = morton16(cx, cy) >> 2;
+        } else {
+            key = ((uint32_t)cls << 30) | (~__float_as_uint(cost) >> 2);
+        }
+        keys[p] = key;
         ids[p] = (int32_t)p;
-        mine += staged_indexed;
+        c0 += cls == 0;
+        c1 += cls == 1;
     }
-    if (mine) atomicAdd(n_cls0, mine);
+    if (c0) atomicAdd(&n_cls[0], c0);
+    if (c1) atomicAdd(&n_cls[1], c1);
 }
 
 }  // namespace
@@ -267,29 +276,32 @@ int pmh_build_cost_order(pmh_polys P, cudaStream_t s)
         cudaGetLastError();
         rc = pmh_set_error(PMH_ERR_NOMEM, "class order allocation failed");
     }
-    unsigned long long* n_cls0 = nullptr;
-    if (rc == PMH_OK && cudaMalloc(&n_cls0, sizeof(unsigned long long)) != cudaSuccess) {
+    unsigned long long* n_cls = nullptr;
+    if (rc == PMH_OK && cudaMalloc(&n_cls, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         rc = pmh_set_error(PMH_ERR_NOMEM, "class count allocation failed");
     }
-    if (rc == PMH_OK && cudaMemsetAsync(n_cls0, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    if (rc == PMH_OK && cudaMemsetAsync(n_cls, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess)
         rc = pmh_set_error(PMH_ERR_CUDA, "memset failed");
     if (rc == PMH_OK) {
-        class_key_kernel<<<blocks, 256, 0, s>>>(P->bbox, P->area2, P->offsets, n, keys, P->order_cls, n_cls0);
+        class_key_kernel<<<blocks, 256, 0, s>>>(P->bbox, P->area2, P->offsets, n, keys, P->order_cls, n_cls);
         g_pmh_launches.fetch_add(1);
         e = cudaGetLastError();
         rc = e == cudaSuccess ? pmh_radix_sort_u32(ctx, keys, P->order_cls, n, 32, s)
                               : pmh_set_error(PMH_ERR_CUDA, "class key: %s", cudaGetErrorString(e));
     }
     if (rc == PMH_OK &&
-        cudaMemcpyAsync(ctx->h_pinned, n_cls0, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) !=
+        cudaMemcpyAsync(ctx->h_pinned, n_cls, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) !=
             cudaSuccess)
         rc = pmh_set_error(PMH_ERR_CUDA, "class count copy failed");
     const cudaError_t e2 = cudaStreamSynchronize(s);
     if (rc == PMH_OK && e2 != cudaSuccess)
         rc = pmh_set_error(PMH_ERR_CUDA, "cost order: %s", cudaGetErrorString(e2));
-    if (rc == PMH_OK) P->n_indexed = ctx->h_pinned[0];
-    if (n_cls0) cudaFree(n_cls0);
+    if (rc == PMH_OK) {
+        P->n_indexed = ctx->h_pinned[0];
+        P->n_staged_walk = ctx->h_pinned[1];
+    }
+    if (n_cls) cudaFree(n_cls);
     cudaFree(keys);
     return rc;
 }
