@@ -112,6 +112,8 @@ extern "C" int pmh_destroy(pmh_ctx ctx)
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     for (cudaEvent_t e : ctx->sign_ev) cudaEventDestroy(e);
     if (ctx->sindex.cell) cudaFree(ctx->sindex.cell);
+    if (ctx->sindex.cell2) cudaFree(ctx->sindex.cell2);
+    if (ctx->sindex.ent2) cudaFree(ctx->sindex.ent2);
     if (ctx->sindex.ent) cudaFree(ctx->sindex.ent);
     delete ctx;
     return PMH_OK;

@@ -212,9 +212,22 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
         const int n = (int)(off[p + 1] - b);
         const int4 bb = bbox[p];
         const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
-        const uint32_t lim = min(pmh_indexed_limit(bb, area2[p]), T);
-        int lev = 0;  // smallest level M >> lev that is still >= lim
-        while (lev + 1 < kRankLevels && ((uint32_t)S.M >> (lev + 1)) >= lim) ++lev;
+        const PmhIndexPlan plan = pmh_index_plan(bb, area2[p]);
+        const uint32_t lim = min(plan.lim, T);
+        // grid level of the plan (the coarse one for boxes that span many fine cells)
+        const uint2* cells = S.cell;
+        const uint2* ents = S.ent;
+        int gb = S.gbits, shf = S.shift;
+        uint32_t Ml = (uint32_t)S.M;
+        if (plan.level == 1 && S.ranked2 && lim <= (uint32_t)S.M2) {
+            cells = S.cell2;
+            ents = S.ent2;
+            gb = S.gbits2;
+            shf = S.shift2;
+            Ml = (uint32_t)S.M2;
+        }
+        int lev = 0;  // smallest level Ml >> lev that is still >= lim
+        while (lev + 1 < kRankLevels && (Ml >> (lev + 1)) >= lim) ++lev;
 
         // stage the polygon, its slab lists and its coverage mask
         for (int i = lane; i < n; i += 32) m.v[i] = xy[b + i];
@@ -229,9 +242,9 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
 
         // cells under the box, row-major; a round reads two cells for the kSub
         // hashes of a group (lane: hash lane & 15, cell 2 * round + lane / 16)
-        const int cx0 = bb.x >> S.shift, cy0 = bb.y >> S.shift;
-        const int ncx = ((bb.z - 1) >> S.shift) - cx0 + 1;
-        const int C = ncx * (((bb.w - 1) >> S.shift) - cy0 + 1);
+        const int cx0 = bb.x >> shf, cy0 = bb.y >> shf;
+        const int ncx = ((bb.z - 1) >> shf) - cx0 + 1;
+        const int C = ncx * (((bb.w - 1) >> shf) - cy0 + 1);
         const int hl = lane & (kSub - 1);
 
         for (int kc = 0; kc < K; kc += kSub) {
@@ -242,7 +255,7 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                 m.ovf = 0;
             }
             __syncwarp();
-            const uint2* rec = S.cell + kc + hl;
+            const uint2* rec = cells + kc + hl;
             int cx = lane >> 4, cy = 0;
             if (cx >= ncx) {
                 cx -= ncx;
@@ -252,7 +265,7 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
             // the records of the next round are loaded while this round's points are read
             uint2 rnext = make_uint2(0u, 0u);
             if (lim > 0 && (lane >> 4) < C && hl < kn)
-                rnext = rec[(int64_t)(((cy0 + cy) << S.gbits) | (cx0 + cx)) * S.K];
+                rnext = rec[(int64_t)(((cy0 + cy) << gb) | (cx0 + cx)) * S.K];
             for (int c0 = 0; lim > 0 && c0 < C; c0 += 2) {
                 // one (hash, cell) record per lane: its points below the level
                 const uint2 r = rnext;
@@ -266,7 +279,7 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                 }
                 rnext = make_uint2(0u, 0u);
                 if (c0 + 2 + (lane >> 4) < C && hl < kn)
-                    rnext = rec[(int64_t)(((cy0 + cy) << S.gbits) | (cx0 + cx)) * S.K];
+                    rnext = rec[(int64_t)(((cy0 + cy) << gb) | (cx0 + cx)) * S.K];
                 const uint32_t first = r.x, cnt = (r.y >> (5 * lev)) & 31u;
                 uint32_t incl = cnt;
 #pragma unroll
@@ -289,7 +302,7 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                     const uint32_t o_excl = __shfl_sync(full, excl, own);
                     const int o_hl = own & (kSub - 1);
                     if ((int)e < E) {
-                        const uint2 q = S.ent[o_first + (e - o_excl)];
+                        const uint2 q = ents[o_first + (e - o_excl)];
                         const uint32_t r = q.y;
                         const uint32_t dx = (r & 0xFFFFu) - (uint32_t)bb.x;
                         const uint32_t dy = (r >> 16) - (uint32_t)bb.y;

@@ -183,7 +183,7 @@ __global__ void class_key_kernel(const int4* __restrict__ bbox, const int64_t* _
         const float cost = 8589934592.0f / fmaxf(aa, 1.0f);
         const int4 bb = bbox[p];
         const bool staged = off[p + 1] - off[p] <= kStagedMaxVerts;
-        const int cls = !staged ? 2 : pmh_indexed_limit(bb, a) > 0 ? 0 : 1;
+        const int cls = !staged ? 2 : pmh_index_plan(bb, a).lim > 0 ? 0 : 1;
         uint32_t key;
         if (cls == 0) {
             const uint32_t cx = (uint32_t)min((bb.x + bb.z) >> 1, 65535);

@@ -88,29 +88,20 @@ __global__ void cell_record_kernel(const int64_t* __restrict__ starts, int K, in
 
 }  // namespace
 
-int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, StreamIndexView* out)
+// One level: the first M points of every hash's stream on a 2^gbits-square grid.
+// Allocates *cell and *ent; on failure frees what it allocated.
+static int build_level(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, int M, int gbits,
+                       uint2** cell_out, uint2** ent_out, int* ranked)
 {
-    StreamIndex& si = ctx->sindex;
-    const int gbits = kStreamGridBits, shift = 16 - kStreamGridBits;
-    const int M = kStreamIndexPoints;
-    if (si.cell && si.seed == P->seed && si.K == (int)P->K) {
-        *out = StreamIndexView{si.cell, si.ent, M, gbits, shift, si.ranked, si.K};
-        return PMH_OK;
-    }
-    if (si.cell) {
-        cudaDeviceSynchronize();
-        cudaFree(si.cell);
-        cudaFree(si.ent);
-        si = StreamIndex();
-    }
+    const int shift = 16 - gbits;
     const int64_t n = (int64_t)P->K * M;
     const int64_t n_cells = (int64_t)P->K << (2 * gbits);
-    if (cudaMalloc(&si.cell, sizeof(uint2) * (n_cells + P->K)) != cudaSuccess ||
-        cudaMalloc(&si.ent, sizeof(uint2) * n) != cudaSuccess) {
+    uint2 *cell = nullptr, *ent = nullptr;
+    if (cudaMalloc(&cell, sizeof(uint2) * (n_cells + P->K)) != cudaSuccess ||
+        cudaMalloc(&ent, sizeof(uint2) * n) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(si.cell);
-        cudaFree(si.ent);
-        si = StreamIndex();
+        cudaFree(cell);
+        cudaFree(ent);
         return pmh_set_error(PMH_ERR_NOMEM, "stream index allocation failed");
     }
     uint32_t* keys = nullptr;
@@ -122,6 +113,8 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
         cudaGetLastError();
         cudaFree(keys);
         cudaFree(vals);
+        cudaFree(cell);
+        cudaFree(ent);
         return pmh_set_error(PMH_ERR_NOMEM, "stream index scratch allocation failed");
     }
     int* longest = reinterpret_cast<int*>(counts + n_cells + 1);
@@ -142,9 +135,9 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
         rc = pmh_exclusive_scan_i64(ctx, counts, counts, n_cells, s);
     }
     if (rc == PMH_OK) {
-        finish_index_kernel<<<blocks, 256, 0, s>>>(keys, vals, n, P->seed, gbits, si.ent);
+        finish_index_kernel<<<blocks, 256, 0, s>>>(keys, vals, n, P->seed, gbits, ent);
         g_pmh_launches.fetch_add(1);
-        cell_record_kernel<<<blocks, 256, 0, s>>>(counts, (int)P->K, gbits, si.ent, M, si.cell, longest);
+        cell_record_kernel<<<blocks, 256, 0, s>>>(counts, (int)P->K, gbits, ent, M, cell, longest);
         g_pmh_launches.fetch_add(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "finish: %s", cudaGetErrorString(e));
@@ -160,15 +153,53 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
     if (rc == PMH_OK && e2 != cudaSuccess)
         rc = pmh_set_error(PMH_ERR_CUDA, "stream index build: %s", cudaGetErrorString(e2));
     if (rc != PMH_OK) {
-        cudaFree(si.cell);
-        cudaFree(si.ent);
-        si = StreamIndex();
+        cudaFree(cell);
+        cudaFree(ent);
         return rc;
     }
-    si.seed = P->seed;
-    si.K = (int)P->K;
-    si.ranked = longest_list <= 31;  // else the counts saturate: only the list ends are used
-    *out = StreamIndexView{si.cell, si.ent, M, gbits, shift, si.ranked, si.K};
+    *cell_out = cell;
+    *ent_out = ent;
+    *ranked = longest_list <= 31;  // else the counts saturate: only the list ends are used
+    return PMH_OK;
+}
+
+static StreamIndexView view_of(const StreamIndex& si)
+{
+    return StreamIndexView{si.cell,  si.ent,  kStreamIndexPoints,  kStreamGridBits,  16 - kStreamGridBits,
+                           si.ranked, si.K,   si.cell2,            si.ent2,          kStreamIndexPoints2,
+                           kStreamGridBits2, 16 - kStreamGridBits2, si.ranked2};
+}
+
+int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, StreamIndexView* out)
+{
+    StreamIndex& si = ctx->sindex;
+    if (si.cell && si.seed == P->seed && si.K == (int)P->K) {
+        *out = view_of(si);
+        return PMH_OK;
+    }
+    if (si.cell) {
+        cudaDeviceSynchronize();
+        cudaFree(si.cell);
+        cudaFree(si.ent);
+        cudaFree(si.cell2);
+        cudaFree(si.ent2);
+        si = StreamIndex();
+    }
+    StreamIndex fresh;
+    int rc = build_level(ctx, P, s, kStreamIndexPoints, kStreamGridBits, &fresh.cell, &fresh.ent,
+                         &fresh.ranked);
+    if (rc == PMH_OK)
+        rc = build_level(ctx, P, s, kStreamIndexPoints2, kStreamGridBits2, &fresh.cell2, &fresh.ent2,
+                         &fresh.ranked2);
+    if (rc != PMH_OK) {
+        cudaFree(fresh.cell);
+        cudaFree(fresh.ent);
+        return rc;
+    }
+    fresh.seed = P->seed;
+    fresh.K = (int)P->K;
+    si = fresh;
+    *out = view_of(si);
     return PMH_OK;
 }
 
