@@ -9,7 +9,7 @@
 // crossing where it enters the other polygon contributes -F(t), every exit
 // +F(t), and an edge that ends inside adds F(1).  Every term is independent,
 // so one warp sums them for one pair in any order: each crossing of an A edge
-// with a B edge is met once and adds both edges' terms with one division, and
+// with a B edge is met once and adds both edges' terms with one reciprocal, and
 // the "ends inside" state of an edge is the start state of the next edge.
 //
 // Degenerate contacts (a vertex on an edge, overlapping collinear edges,
@@ -18,8 +18,8 @@
 // decided exactly with int64 cross products (coordinates <= 2^20), and the
 // area of the shifted configuration tends to the exact one.  The terms are
 // fp64 in coordinates relative to B's first vertex.  GB300's fp64 rate is low,
-// so the fp64 work is kept to the crossings (a few per edge) and one division
-// each.
+// so the fp64 work is kept to the crossings (a few per edge) and one Newton
+// reciprocal each.
 #include <algorithm>
 
 #include "pmh_internal.cuh"
@@ -52,15 +52,31 @@ __device__ __forceinline__ int side_of_point_to_shifted(int2 a, int2 b, int2 q)
     return dx > 0 ? -1 : 1;
 }
 
+// 1/D in double precision for an integer D != 0 (|D| < 2^44): a single-precision
+// reciprocal as the start, then two Newton steps y <- y + y(1 - D y), each of
+// which squares the relative error (2^-23 -> 2^-46 -> below double rounding).
+// Cheaper on this GPU's narrow fp64 pipe than a correctly rounded division;
+// the result is within a few units in the last place, far inside the 1e-9
+// relative tolerance of the refinement.
+__device__ __forceinline__ double recip(long long D)
+{
+    const double d = (double)D;
+    double y = (double)(1.0f / (float)d);
+    double e = fma(-d, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-d, y, 1.0);
+    return fma(y, e, y);
+}
+
 // area(A n B) for one pair, by one warp; returned in every lane.
 //  * end terms: edge e_i of the shifted A ends inside B iff its end vertex
 //    a_{i+1} + e is inside B (the start state of the next edge), so each lane
 //    tests its vertices and adds F(1) of the edge that ends there -- no crossing
 //    parity per edge is needed; likewise for B's edges and A + e;
 //  * crossings: each (A edge, B edge) pair that crosses is visited by one lane,
-//    which adds both boundary terms with one division: with D = de x df,
+//    which adds both boundary terms from one reciprocal: with D = de x df,
 //    t = Nt / D on e and u = Nu / D on f (Nt, Nu, D exact integers),
-//    F_e(t) + F_f(u) = [dy Nt (x0e D + dx Nt / 2) +- ey Nu (x0f D + ex Nu / 2)] / D^2.
+//    F_e(t) = dy t (x0e + dx t / 2) and F_f(u) = ey u (x0f + ex u / 2).
 __device__ double warp_intersection_area(const int2* __restrict__ A, int na, int sA,
                                          const int2* __restrict__ B, int nb, int sB, int lane)
 {
@@ -119,15 +135,14 @@ __device__ double warp_intersection_area(const int2* __restrict__ A, int na, int
             const long long D = dx * ey - dy * ex;
             const long long Nt = (long long)(c.x - a.x) * ey - (long long)(c.y - a.y) * ex;
             const long long Nu = (long long)(c.x - a.x) * dy - (long long)(c.y - a.y) * dx;
-            const double Dd = (double)D;
             // A's edge: entering B flips the sign; B's edge: entering the shifted A
             const double sa = (((s2 > 0) == (sB > 0)) ? -1.0 : 1.0) * (sA > 0 ? 1.0 : -1.0);
             const double sb = (((s4 > 0) == (sA > 0)) ? -1.0 : 1.0) * (sB > 0 ? 1.0 : -1.0);
-            const double fa = (double)dy * (double)Nt *
-                              ((double)(a.x - org.x) * Dd + 0.5 * (double)dx * (double)Nt);
-            const double fb = (double)ey * (double)Nu *
-                              ((double)(c.x - org.x) * Dd + 0.5 * (double)ex * (double)Nu);
-            acc += (sa * fa + sb * fb) / (Dd * Dd);
+            const double r = recip(D);  // D != 0: the edges cross at one point
+            const double t = (double)Nt * r, u = (double)Nu * r;
+            const double fa = (double)dy * t * ((double)(a.x - org.x) + 0.5 * (double)dx * t);
+            const double fb = (double)ey * u * ((double)(c.x - org.x) + 0.5 * (double)ex * u);
+            acc += sa * fa + sb * fb;
         }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

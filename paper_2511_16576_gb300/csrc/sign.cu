@@ -327,6 +327,7 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                                         s));
         order = order_cls + n_indexed;
         n_polys -= n_indexed;
+        if (timed) PMH_CUDA_TRY(cudaEventRecord(ev[1], s));
         if (!masks) {
             // staged polygons of the walk form in their own kernel (with the
             // precomputed masks of PMH_FLAG_COVERAGE_MASK they stay below)
@@ -336,8 +337,9 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
             order += n_staged_walk;
             n_polys -= n_staged_walk;
         }
+    } else if (timed) {
+        PMH_CUDA_TRY(cudaEventRecord(ev[1], s));
     }
-    if (timed) PMH_CUDA_TRY(cudaEventRecord(ev[1], s));
     if (n_polys <= 0) {
         if (timed) PMH_CUDA_TRY(cudaEventRecord(ev[2], s));
         return PMH_OK;

@@ -169,7 +169,7 @@ def test_sign_kernel_report(B, ctx):
     B.minhash_sign(ctx, dbp, P)
     rep = B.sign_report(ctx)
     assert rep["calls"] == 2 and torch.equal(h1, h2)
-    assert rep["indexed"]["ms"] > 0 and rep["walk"]["ms"] >= 0
+    assert rep["indexed"]["ms"] > 0 and rep["walk"]["ms"] > 0
     total = B.sign_work(ctx)
     for k, v in total.items():
         assert v == rep["indexed"]["work"][k] + rep["walk"]["work"][k], k
