@@ -111,10 +111,10 @@ extern "C" int pmh_destroy(pmh_ctx ctx)
     if (ctx->d_tickets) cudaFree(ctx->d_tickets);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     for (cudaEvent_t e : ctx->sign_ev) cudaEventDestroy(e);
-    if (ctx->sindex.cell) cudaFree(ctx->sindex.cell);
-    if (ctx->sindex.cell2) cudaFree(ctx->sindex.cell2);
-    if (ctx->sindex.ent2) cudaFree(ctx->sindex.ent2);
-    if (ctx->sindex.ent) cudaFree(ctx->sindex.ent);
+    for (int l = 0; l < kIndexLevels; ++l) {
+        if (ctx->sindex.cell[l]) cudaFree(ctx->sindex.cell[l]);
+        if (ctx->sindex.ent[l]) cudaFree(ctx->sindex.ent[l]);
+    }
     delete ctx;
     return PMH_OK;
 }

@@ -55,12 +55,14 @@ enum ScratchSlot {
 };
 
 // first kStreamIndexPoints points of every hash's stream, bucketed by cell of a
-// 2^kStreamGridBits-square grid (stream_index.cu); a coarse second level holds
-// the first kStreamIndexPoints2 points on a 2^kStreamGridBits2-square grid
+// 2^kStreamGridBits-square grid (stream_index.cu); coarser levels hold fewer
+// points on coarser grids (level l: 2^index_level_gbits(l) cells per side, the
+// first index_level_points(l) points)
 constexpr int kStreamGridBits = 7;
 constexpr int kStreamIndexPoints = 65536;
-constexpr int kStreamGridBits2 = 5;
-constexpr int kStreamIndexPoints2 = 8192;
+constexpr int kIndexLevels = 3;
+__host__ __device__ constexpr int index_level_gbits(int l) { return l == 0 ? 7 : l == 1 ? 6 : 5; }
+__host__ __device__ constexpr int index_level_points(int l) { return l == 0 ? 65536 : l == 1 ? 32768 : 8192; }
 // polygons of at most this many vertices are staged in shared memory by the
 // signing kernels; larger ones are read through their y-slab edge index
 constexpr int kStagedMaxVerts = 256;
@@ -99,65 +101,76 @@ __host__ __device__ __forceinline__ uint32_t pmh_indexed_limit(int4 bb, long lon
 // adjacent, so a warp reading one cell for sixteen hashes reads 128 bytes.
 constexpr int kRankLevels = 6;
 // Plan of the indexed form for a polygon staged in shared memory (sign_indexed.cu),
-// in estimated warp instructions per hash: the gather costs ~2.1 per cell record
-// and ~3.7 per point read (the points below the smallest rank level >= the limit
-// in the cells under the box), plus ~60 for the mask, exact tests and setup; the
-// walk costs ~45 per round of 64 points plus ~40.  The limit is lim = 8 * 2^32 /
-// area (a hit below it is missed with probability ~e^-8; the walk then resumes at
-// lim), and at most ~24 box points below lim are expected.  Returns lim (0 = walk)
-// and the grid level (0 fine, 1 coarse).  Any limit and level give the exact
-// result; the plan only picks the cheaper work.
+// in estimated warp instructions per hash.  The limit is lim = 8 * 2^32 / area (a
+// hit below it is missed with probability ~e^-8; the walk then resumes at lim),
+// and at most ~24 box points below lim are expected.  The gather first reads the
+// points below lim1 = 2.5 * 2^32 / area (an inside point exists there with
+// probability ~1 - e^-2.5); only the hashes without one read on up to lim.  On a
+// grid level holding at least lim points it costs ~4.9 per cell record under the
+// box and ~2.5 per first-pass point read (those below the smallest rank level >=
+// lim1 in those cells), plus ~60 for the mask, exact tests and setup; the walk
+// costs ~45 per round of 64 points plus ~40.  Returns lim (0 = walk), lim1 and
+// the cheapest level.  Any limit and level give the exact result; the plan only
+// picks the cheaper work.
 struct PmhIndexPlan {
     uint32_t lim;
     int level;
+    uint32_t lim1;  // bound of the first gather pass: ~2.5 expected first hits
 };
-__host__ __device__ __forceinline__ float pmh_level_cost(int4 bb, uint32_t lim, uint32_t M, int shift)
+__host__ __device__ __forceinline__ float pmh_level_cost(int4 bb, uint32_t lim1, uint32_t M, int shift)
 {
     const float C = (float)((((bb.z - 1) >> shift) - (bb.x >> shift) + 1) *
                             (((bb.w - 1) >> shift) - (bb.y >> shift) + 1));
     uint32_t lvl = M;
-    for (int t = 1; t < 6 && (M >> t) >= lim; ++t) lvl = M >> t;
+    for (int t = 1; t < 6 && (M >> t) >= lim1; ++t) lvl = M >> t;
     const float pts = (float)lvl * C * (float)(1u << (2 * shift)) * (1.0f / 4294967296.0f);
-    return 2.1f * C + 3.7f * pts;
+    return 4.9f * C + 2.5f * pts;
 }
 __host__ __device__ __forceinline__ PmhIndexPlan pmh_index_plan(int4 bb, long long area2)
 {
-    PmhIndexPlan plan{0u, 0};
+    PmhIndexPlan plan{0u, 0, 0u};
     if (bb.z <= bb.x || bb.w <= bb.y) return plan;
     const float area = 0.5f * (float)(area2 < 0 ? -area2 : area2);
     const float walk = 4294967296.0f / fmaxf(area, 1.0f);
     const float lim = fminf((float)kStreamIndexPoints, 8.0f * walk + 256.0f);
     const float cand = lim * ((float)(bb.z - bb.x) * (float)(bb.w - bb.y) * (1.0f / 4294967296.0f));
     if (cand > 24.0f) return plan;
-    const uint32_t L = (uint32_t)lim;
-    const float c1 = pmh_level_cost(bb, L, kStreamIndexPoints, 16 - kStreamGridBits);
-    const float c2 = L <= (uint32_t)kStreamIndexPoints2
-                         ? pmh_level_cost(bb, L, kStreamIndexPoints2, 16 - kStreamGridBits2)
-                         : 3.0e38f;
+    const uint32_t L = (uint32_t)lim, L1 = (uint32_t)fminf(lim, 2.5f * walk + 64.0f);
+    float best = 3.0e38f;
+    int level = 0;
+    for (int l = 0; l < kIndexLevels; ++l) {
+        if (L > (uint32_t)index_level_points(l)) continue;
+        const float c = pmh_level_cost(bb, L1, index_level_points(l), 16 - index_level_gbits(l));
+        if (c < best) {
+            best = c;
+            level = l;
+        }
+    }
     const float walk_cost = ceilf(walk * (1.0f / 64.0f)) * 45.0f + 40.0f;
-    if (fminf(c1, c2) + 60.0f >= walk_cost) return plan;
+    if (best + 60.0f >= walk_cost) return plan;
     plan.lim = L;
-    plan.level = c2 < c1 ? 1 : 0;
+    plan.level = level;
+    plan.lim1 = L1;
     return plan;
 }
 
 struct StreamIndex {
     uint64_t seed = 0;
     int K = 0;
-    uint2* cell = nullptr;   // [(G * G + 1) * K] records
-    uint2* ent = nullptr;    // [K * M] (stream index, x | y << 16)
-    int ranked = 0;          // every list fits the 5-bit counts
-    uint2* cell2 = nullptr;  // the coarse level: [(G2 * G2 + 1) * K] records
-    uint2* ent2 = nullptr;   // [K * M2]
-    int ranked2 = 0;
+    uint2* cell[kIndexLevels] = {};  // per level: [(G * G + 1) * K] records
+    uint2* ent[kIndexLevels] = {};   // per level: [K * M] (stream index, x | y << 16)
+    int ranked[kIndexLevels] = {};   // every list of the level fits the 5-bit counts
+};
+struct IndexLevelView {
+    const uint2* cell;
+    const uint2* ent;
+    int M, gbits, shift, ranked;
 };
 struct StreamIndexView {
-    const uint2* cell;  // nullptr: no index
+    const uint2* cell;  // level 0 (nullptr: no index)
     const uint2* ent;
     int M, gbits, shift, ranked, K;
-    const uint2* cell2;  // coarse level (same layout)
-    const uint2* ent2;
-    int M2, gbits2, shift2, ranked2;
+    IndexLevelView lv[kIndexLevels];
 };
 
 struct pmh_ctx_s {

@@ -214,20 +214,17 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
         const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
         const PmhIndexPlan plan = pmh_index_plan(bb, area2[p]);
         const uint32_t lim = min(plan.lim, T);
-        // grid level of the plan (the coarse one for boxes that span many fine cells)
-        const uint2* cells = S.cell;
-        const uint2* ents = S.ent;
-        int gb = S.gbits, shf = S.shift;
-        uint32_t Ml = (uint32_t)S.M;
-        if (plan.level == 1 && S.ranked2 && lim <= (uint32_t)S.M2) {
-            cells = S.cell2;
-            ents = S.ent2;
-            gb = S.gbits2;
-            shf = S.shift2;
-            Ml = (uint32_t)S.M2;
-        }
+        // grid level of the plan (coarser ones for boxes that span many fine cells)
+        const IndexLevelView& L =
+            S.lv[S.lv[plan.level].ranked && lim <= (uint32_t)S.lv[plan.level].M ? plan.level : 0];
+        const uint2* cells = L.cell;
+        const uint2* ents = L.ent;
+        const int gb = L.gbits, shf = L.shift;
+        const uint32_t Ml = (uint32_t)L.M;
         int lev = 0;  // smallest level Ml >> lev that is still >= lim
         while (lev + 1 < kRankLevels && (Ml >> (lev + 1)) >= lim) ++lev;
+        int lev1 = lev;  // smallest level >= the first pass's bound
+        while (lev1 + 1 < kRankLevels && (Ml >> (lev1 + 1)) >= plan.lim1) ++lev1;
 
         // stage the polygon, its slab lists and its coverage mask
         for (int i = lane; i < n; i += 32) m.v[i] = xy[b + i];
@@ -250,103 +247,114 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
         for (int kc = 0; kc < K; kc += kSub) {
             const int kn = min(kSub, K - kc);
             if (lane < kSub) m.best[lane] = 0xFFFFFFFFu;
-            if (lane == 0) {
-                m.npool = 0;
-                m.ovf = 0;
-            }
-            __syncwarp();
-            const uint2* rec = cells + kc + hl;
-            int cx = lane >> 4, cy = 0;
-            if (cx >= ncx) {
-                cx -= ncx;
-                ++cy;
-            }
-            if (lim > 0 && lane == 0) lane_cells += (unsigned)(C * kn);
-            // the records of the next round are loaded while this round's points are read
-            uint2 rnext = make_uint2(0u, 0u);
-            if (lim > 0 && (lane >> 4) < C && hl < kn)
-                rnext = rec[(int64_t)(((cy0 + cy) << gb) | (cx0 + cx)) * S.K];
-            for (int c0 = 0; lim > 0 && c0 < C; c0 += 2) {
-                // one (hash, cell) record per lane: its points below the level
-                const uint2 r = rnext;
+            if (lane == 0) m.ovf = 0;
+            // two passes over the cells: first the points below level lev1 (about
+            // 2.5x the expected first hit: most hashes find their answer there),
+            // then, for the hashes with no inside point yet, those up to level lev
+            uint32_t open = kn == 32 ? 0xFFFFFFFFu : ((1u << kn) - 1u);
+            for (int pass = 0; pass < 2 && lim > 0; ++pass) {
+                const int hi_lev = pass == 0 ? lev1 : lev;  // read entries below Ml >> hi_lev
+                const int lo_lev = pass == 0 ? -1 : lev1;   // ... skipping those below Ml >> lo_lev
+                if (pass == 1 && (lev1 == lev || open == 0)) break;
+                if (lane == 0) m.npool = 0;
+                __syncwarp();
+                const bool mine = hl < kn && ((open >> hl) & 1u);
+                const uint2* rec = cells + kc + hl;
+                int cx = lane >> 4, cy = 0;
+                if (cx >= ncx) {
+                    cx -= ncx;
+                    ++cy;
+                }
+                if (lane == 0) lane_cells += (unsigned)(C * __popc(open));
+                // the records of the next round are loaded while this round's points are read
+                uint2 rnext = make_uint2(0u, 0u);
+                if ((lane >> 4) < C && mine) rnext = rec[(int64_t)(((cy0 + cy) << gb) | (cx0 + cx)) * S.K];
+                for (int c0 = 0; c0 < C; c0 += 2) {
+                    // one (hash, cell) record per lane: its points between the levels
+                    const uint2 r = rnext;
 #pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    cx += 1;
-                    if (cx >= ncx) {
-                        cx -= ncx;
-                        ++cy;
+                    for (int t = 0; t < 2; ++t) {
+                        cx += 1;
+                        if (cx >= ncx) {
+                            cx -= ncx;
+                            ++cy;
+                        }
                     }
-                }
-                rnext = make_uint2(0u, 0u);
-                if (c0 + 2 + (lane >> 4) < C && hl < kn)
-                    rnext = rec[(int64_t)(((cy0 + cy) << gb) | (cx0 + cx)) * S.K];
-                const uint32_t first = r.x, cnt = (r.y >> (5 * lev)) & 31u;
-                uint32_t incl = cnt;
+                    rnext = make_uint2(0u, 0u);
+                    if (c0 + 2 + (lane >> 4) < C && mine)
+                        rnext = rec[(int64_t)(((cy0 + cy) << gb) | (cx0 + cx)) * S.K];
+                    const uint32_t below_lo = lo_lev < 0 ? 0u : (r.y >> (5 * lo_lev)) & 31u;
+                    const uint32_t first = r.x + below_lo, cnt = ((r.y >> (5 * hi_lev)) & 31u) - below_lo;
+                    uint32_t incl = cnt;
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t t = __shfl_up_sync(full, incl, d);
-                    if (lane >= d) incl += t;
-                }
-                const uint32_t excl = incl - cnt;
-                const int E = (int)__shfl_sync(full, incl, 31);
-                lane_read += lane == 0 ? (unsigned)E : 0u;
-                // spread the points over the lanes: point e belongs to the last
-                // lane whose exclusive offset is <= e
-                for (int e0 = 0; e0 < E; e0 += 32) {
-                    const uint32_t e = (uint32_t)(e0 + lane);
-                    int own = 0;
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint32_t t = __shfl_up_sync(full, incl, d);
+                        if (lane >= d) incl += t;
+                    }
+                    const uint32_t excl = incl - cnt;
+                    const int E = (int)__shfl_sync(full, incl, 31);
+                    lane_read += lane == 0 ? (unsigned)E : 0u;
+                    // spread the points over the lanes: point e belongs to the last
+                    // lane whose exclusive offset is <= e
+                    for (int e0 = 0; e0 < E; e0 += 32) {
+                        const uint32_t e = (uint32_t)(e0 + lane);
+                        int own = 0;
 #pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1)
-                        if (__shfl_sync(full, excl, own + step) <= e) own += step;
-                    const uint32_t o_first = __shfl_sync(full, first, own);
-                    const uint32_t o_excl = __shfl_sync(full, excl, own);
-                    const int o_hl = own & (kSub - 1);
-                    if ((int)e < E) {
-                        const uint2 q = ents[o_first + (e - o_excl)];
-                        const uint32_t r = q.y;
-                        const uint32_t dx = (r & 0xFFFFu) - (uint32_t)bb.x;
-                        const uint32_t dy = (r >> 16) - (uint32_t)bb.y;
-                        if (q.x < lim && dx < w && dy < h) {
-                            ++lane_cand;
-                            const int i = (int)(dx >> cwl), j = (int)(dy >> chl);
-                            if ((m.bnd[j] >> i) & 1u) {
-                                const int slot = atomicAdd(&m.npool, 1);
-                                if (slot < kPool) m.pool[slot] = make_uint2(((uint32_t)o_hl << 16) | q.x, r);
-                                else atomicOr(&m.ovf, 1u << o_hl);
-                            } else {
-                                ++lane_masked;
-                                if ((m.inb[j] >> i) & 1u) atomicMin(&m.best[o_hl], q.x);
+                        for (int step = 16; step >= 1; step >>= 1)
+                            if (__shfl_sync(full, excl, own + step) <= e) own += step;
+                        const uint32_t o_first = __shfl_sync(full, first, own);
+                        const uint32_t o_excl = __shfl_sync(full, excl, own);
+                        const int o_hl = own & (kSub - 1);
+                        if ((int)e < E) {
+                            const uint2 q = ents[o_first + (e - o_excl)];
+                            const uint32_t r = q.y;
+                            const uint32_t dx = (r & 0xFFFFu) - (uint32_t)bb.x;
+                            const uint32_t dy = (r >> 16) - (uint32_t)bb.y;
+                            if (q.x < lim && dx < w && dy < h) {
+                                ++lane_cand;
+                                const int i = (int)(dx >> cwl), j = (int)(dy >> chl);
+                                if ((m.bnd[j] >> i) & 1u) {
+                                    const int slot = atomicAdd(&m.npool, 1);
+                                    if (slot < kPool) m.pool[slot] = make_uint2(((uint32_t)o_hl << 16) | q.x, r);
+                                    else atomicOr(&m.ovf, 1u << o_hl);
+                                } else {
+                                    ++lane_masked;
+                                    if ((m.inb[j] >> i) & 1u) atomicMin(&m.best[o_hl], q.x);
+                                }
                             }
                         }
                     }
                 }
-            }
-            __syncwarp();
-            // kept points below their hash's smallest hit go to the queue, tested 32 at a time
-            const int np = min(m.npool, kPool);
-            int nq = 0;  // warp-uniform queue length
-            for (int t0 = 0; t0 < np; t0 += 32) {
-                const int t = t0 + lane;
-                uint2 c = make_uint2(0u, 0u);
-                bool keep = false;
-                if (t < np) {
-                    c = m.pool[t];
-                    keep = (c.x & 0xFFFFu) < m.best[c.x >> 16];
-                }
-                const unsigned bal = __ballot_sync(full, keep);
-                if (keep) m.queue[nq + __popc(bal & pmh_lanemask_lt())] = c;
-                nq += __popc(bal);
                 __syncwarp();
-                if (nq >= 32) {
-                    exact_batch(m, 32, st, lane, work);
-                    nq -= 32;
-                    const uint2 rest = lane < nq ? m.queue[32 + lane] : make_uint2(0u, 0u);
+                // kept points below their hash's smallest hit go to the queue, tested 32 at a time
+                const int np = min(m.npool, kPool);
+                int nq = 0;  // warp-uniform queue length
+                for (int t0 = 0; t0 < np; t0 += 32) {
+                    const int t = t0 + lane;
+                    uint2 c = make_uint2(0u, 0u);
+                    bool keep = false;
+                    if (t < np) {
+                        c = m.pool[t];
+                        keep = (c.x & 0xFFFFu) < m.best[c.x >> 16];
+                    }
+                    const unsigned bal = __ballot_sync(full, keep);
+                    if (keep) m.queue[nq + __popc(bal & pmh_lanemask_lt())] = c;
+                    nq += __popc(bal);
                     __syncwarp();
-                    if (lane < nq) m.queue[lane] = rest;
-                    __syncwarp();
+                    if (nq >= 32) {
+                        exact_batch(m, 32, st, lane, work);
+                        nq -= 32;
+                        const uint2 rest = lane < nq ? m.queue[32 + lane] : make_uint2(0u, 0u);
+                        __syncwarp();
+                        if (lane < nq) m.queue[lane] = rest;
+                        __syncwarp();
+                    }
                 }
+                if (nq > 0) exact_batch(m, nq, st, lane, work);
+                // a hash with an inside point below the first level is final (every point
+                // below it was examined); one that lost kept points walks from the start
+                open &= __ballot_sync(full, lane < kn && m.best[lane] == 0xFFFFFFFFu) & ~m.ovf;
             }
-            if (nq > 0) exact_batch(m, nq, st, lane, work);
 
             // hashes without an inside point below lim resume the walk there; one
             // that lost kept points walks from the start

@@ -165,35 +165,47 @@ static int build_level(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, int M, 
 
 static StreamIndexView view_of(const StreamIndex& si)
 {
-    return StreamIndexView{si.cell,  si.ent,  kStreamIndexPoints,  kStreamGridBits,  16 - kStreamGridBits,
-                           si.ranked, si.K,   si.cell2,            si.ent2,          kStreamIndexPoints2,
-                           kStreamGridBits2, 16 - kStreamGridBits2, si.ranked2};
+    StreamIndexView v{};
+    for (int l = 0; l < kIndexLevels; ++l)
+        v.lv[l] = IndexLevelView{si.cell[l], si.ent[l], index_level_points(l), index_level_gbits(l),
+                                 16 - index_level_gbits(l), si.ranked[l]};
+    v.cell = si.cell[0];
+    v.ent = si.ent[0];
+    v.M = index_level_points(0);
+    v.gbits = index_level_gbits(0);
+    v.shift = 16 - index_level_gbits(0);
+    v.ranked = si.ranked[0];
+    v.K = si.K;
+    return v;
+}
+
+static void free_index(StreamIndex& si)
+{
+    for (int l = 0; l < kIndexLevels; ++l) {
+        cudaFree(si.cell[l]);
+        cudaFree(si.ent[l]);
+    }
+    si = StreamIndex();
 }
 
 int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, StreamIndexView* out)
 {
     StreamIndex& si = ctx->sindex;
-    if (si.cell && si.seed == P->seed && si.K == (int)P->K) {
+    if (si.cell[0] && si.seed == P->seed && si.K == (int)P->K) {
         *out = view_of(si);
         return PMH_OK;
     }
-    if (si.cell) {
+    if (si.cell[0]) {
         cudaDeviceSynchronize();
-        cudaFree(si.cell);
-        cudaFree(si.ent);
-        cudaFree(si.cell2);
-        cudaFree(si.ent2);
-        si = StreamIndex();
+        free_index(si);
     }
     StreamIndex fresh;
-    int rc = build_level(ctx, P, s, kStreamIndexPoints, kStreamGridBits, &fresh.cell, &fresh.ent,
-                         &fresh.ranked);
-    if (rc == PMH_OK)
-        rc = build_level(ctx, P, s, kStreamIndexPoints2, kStreamGridBits2, &fresh.cell2, &fresh.ent2,
-                         &fresh.ranked2);
+    int rc = PMH_OK;
+    for (int l = 0; l < kIndexLevels && rc == PMH_OK; ++l)
+        rc = build_level(ctx, P, s, index_level_points(l), index_level_gbits(l), &fresh.cell[l],
+                         &fresh.ent[l], &fresh.ranked[l]);
     if (rc != PMH_OK) {
-        cudaFree(fresh.cell);
-        cudaFree(fresh.ent);
+        free_index(fresh);
         return rc;
     }
     fresh.seed = P->seed;

@@ -140,11 +140,11 @@ def test_sign_indexed_form_paths(B, ctx, orc, flags):
     """Polygons signed through the stream index: a comb whose 240 vertices need more
     slab references than a warp stages (one slab of every edge instead), more hashes
     than one pass holds (K = 300), tiny boxes whose walks resume past the index, boxes
-    on the coarse grid level, and caps below and above the index limit."""
+    on the coarser grid levels, and caps below and above the index limits."""
     polys = [comb(20000, 20000, 60, 10, 10, 1000, 50), comb(40000, 7000, 30, 12, 8, 400, 5)]
     tiny = synth.star_polygons(40, 29, (3, 256), "loguniform", (1e-6, 3e-4))
     polys += [tiny.poly(i) for i in range(tiny.n)]
-    # boxes that span many fine cells take the coarse grid level
+    # boxes that span many fine cells take the coarser grid levels
     mid = synth.star_polygons(30, 37, (16, 256), "loguniform", (2e-3, 8e-3))
     polys += [mid.poly(i) for i in range(mid.n)]
     ps = from_polys(polys)
