@@ -108,7 +108,7 @@ constexpr int kRankLevels = 6;
 // probability ~1 - e^-2.5); only the hashes without one read on up to lim.  On a
 // grid level holding at least lim points it costs ~4.9 per cell record under the
 // box and ~2.5 per first-pass point read (those below the smallest rank level >=
-// lim1 in those cells), plus ~60 for the mask, exact tests and setup; the walk
+// lim1 in those cells), plus ~20 for the mask, exact tests and setup; the walk
 // costs ~45 per round of 64 points plus ~40.  Returns lim (0 = walk), lim1 and
 // the cheapest level.  Any limit and level give the exact result; the plan only
 // picks the cheaper work.
@@ -147,7 +147,7 @@ __host__ __device__ __forceinline__ PmhIndexPlan pmh_index_plan(int4 bb, long lo
         }
     }
     const float walk_cost = ceilf(walk * (1.0f / 64.0f)) * 45.0f + 40.0f;
-    if (best + 60.0f >= walk_cost) return plan;
+    if (best + 20.0f >= walk_cost) return plan;
     plan.lim = L;
     plan.level = level;
     plan.lim1 = L1;

@@ -77,8 +77,35 @@ __device__ __forceinline__ double recip(long long D)
 //    which adds both boundary terms from one reciprocal: with D = de x df,
 //    t = Nt / D on e and u = Nu / D on f (Nt, Nu, D exact integers),
 //    F_e(t) = dy t (x0e + dx t / 2) and F_f(u) = ey u (x0f + ex u / 2).
+// boundary terms of one crossing, queued as (A edge i, B edge j): with
+// D = de x df, t = Nt / D on e and u = Nu / D on f (Nt, Nu, D exact integers),
+// F_e(t) = dy t (x0e + dx t / 2) and F_f(u) = ey u (x0f + ex u / 2), signed by
+// the direction of the crossing
+__device__ __forceinline__ double crossing_terms(const int2* __restrict__ A, int na, int sA,
+                                                 const int2* __restrict__ B, int nb, int sB,
+                                                 int2 org, uint2 ij)
+{
+    const int i = (int)ij.x, j = (int)ij.y;
+    const int2 a = A[i], b = A[i + 1 == na ? 0 : i + 1];
+    const int2 c = B[j], d = B[j + 1 == nb ? 0 : j + 1];
+    const int s2 = side_of_shifted_point(c, d, b), s4 = side_of_point_to_shifted(a, b, d);
+    const long long dx = b.x - a.x, dy = b.y - a.y, ex = d.x - c.x, ey = d.y - c.y;
+    const long long D = dx * ey - dy * ex;
+    const long long Nt = (long long)(c.x - a.x) * ey - (long long)(c.y - a.y) * ex;
+    const long long Nu = (long long)(c.x - a.x) * dy - (long long)(c.y - a.y) * dx;
+    // A's edge: entering B flips the sign; B's edge: entering the shifted A
+    const double sa = (((s2 > 0) == (sB > 0)) ? -1.0 : 1.0) * (sA > 0 ? 1.0 : -1.0);
+    const double sb = (((s4 > 0) == (sA > 0)) ? -1.0 : 1.0) * (sB > 0 ? 1.0 : -1.0);
+    const double r = recip(D);  // D != 0: the edges cross at one point
+    const double t = (double)Nt * r, u = (double)Nu * r;
+    const double fa = (double)dy * t * ((double)(a.x - org.x) + 0.5 * (double)dx * t);
+    const double fb = (double)ey * u * ((double)(c.x - org.x) + 0.5 * (double)ex * u);
+    return sa * fa + sb * fb;
+}
+
 __device__ double warp_intersection_area(const int2* __restrict__ A, int na, int sA,
-                                         const int2* __restrict__ B, int nb, int sB, int lane)
+                                         const int2* __restrict__ B, int nb, int sB,
+                                         uint2* cq /* [64] */, int lane)
 {
     const int2 org = B[0];
     double acc = 0;
@@ -116,35 +143,49 @@ __device__ double warp_intersection_area(const int2* __restrict__ A, int na, int
             acc += (sB > 0 ? 1.0 : -1.0) * ey * (x0 + 0.5 * ex);
         }
     }
-    // crossings
-    for (int i = lane; i < na; i += 32) {
-        const int2 a = A[i], b = A[i + 1 == na ? 0 : i + 1];
-        if (a.x == b.x && a.y == b.y) continue;
+    // crossings: the lanes find them with integer predicates only and queue them
+    // (edge indices); the fp64 terms are then evaluated 32 at a time, one
+    // crossing per lane, so the narrow fp64 pipe never runs a mostly idle warp
+    const unsigned full = 0xffffffffu;
+    int nq = 0;  // warp-uniform queue length (< 32 between iterations)
+    for (int i0 = 0; i0 < na; i0 += 32) {
+        const int i = i0 + lane;
+        int2 a = make_int2(0, 0), b = make_int2(0, 0);
+        bool live = i < na;
+        if (live) {
+            a = A[i];
+            b = A[i + 1 == na ? 0 : i + 1];
+            live = a.x != b.x || a.y != b.y;
+        }
         const int ax0 = min(a.x, b.x), ax1 = max(a.x, b.x), ay0 = min(a.y, b.y), ay1 = max(a.y, b.y);
-        const long long dx = b.x - a.x, dy = b.y - a.y;
         for (int j = 0; j < nb; ++j) {
-            const int2 c = B[j], d = B[j + 1 == nb ? 0 : j + 1];
-            if (max(ax0, min(c.x, d.x)) > min(ax1, max(c.x, d.x)) ||
-                max(ay0, min(c.y, d.y)) > min(ay1, max(c.y, d.y)) || (c.x == d.x && c.y == d.y))
-                continue;
-            const int s1 = side_of_shifted_point(c, d, a), s2 = side_of_shifted_point(c, d, b);
-            if (s1 == s2) continue;
-            const int s3 = side_of_point_to_shifted(a, b, c), s4 = side_of_point_to_shifted(a, b, d);
-            if (s3 == s4) continue;
-            const long long ex = d.x - c.x, ey = d.y - c.y;
-            const long long D = dx * ey - dy * ex;
-            const long long Nt = (long long)(c.x - a.x) * ey - (long long)(c.y - a.y) * ex;
-            const long long Nu = (long long)(c.x - a.x) * dy - (long long)(c.y - a.y) * dx;
-            // A's edge: entering B flips the sign; B's edge: entering the shifted A
-            const double sa = (((s2 > 0) == (sB > 0)) ? -1.0 : 1.0) * (sA > 0 ? 1.0 : -1.0);
-            const double sb = (((s4 > 0) == (sA > 0)) ? -1.0 : 1.0) * (sB > 0 ? 1.0 : -1.0);
-            const double r = recip(D);  // D != 0: the edges cross at one point
-            const double t = (double)Nt * r, u = (double)Nu * r;
-            const double fa = (double)dy * t * ((double)(a.x - org.x) + 0.5 * (double)dx * t);
-            const double fb = (double)ey * u * ((double)(c.x - org.x) + 0.5 * (double)ex * u);
-            acc += sa * fa + sb * fb;
+            bool hit = false;
+            if (live) {
+                const int2 c = B[j], d = B[j + 1 == nb ? 0 : j + 1];
+                if (!(max(ax0, min(c.x, d.x)) > min(ax1, max(c.x, d.x)) ||
+                      max(ay0, min(c.y, d.y)) > min(ay1, max(c.y, d.y)) || (c.x == d.x && c.y == d.y))) {
+                    hit = side_of_shifted_point(c, d, a) != side_of_shifted_point(c, d, b) &&
+                          side_of_point_to_shifted(a, b, c) != side_of_point_to_shifted(a, b, d);
+                }
+            }
+            const unsigned bal = __ballot_sync(full, hit);
+            if (bal) {
+                if (hit) cq[nq + __popc(bal & pmh_lanemask_lt())] = make_uint2((uint32_t)i, (uint32_t)j);
+                nq += __popc(bal);
+                __syncwarp();
+                if (nq >= 32) {
+                    acc += crossing_terms(A, na, sA, B, nb, sB, org, cq[lane]);
+                    nq -= 32;
+                    const uint2 rest = lane < nq ? cq[32 + lane] : make_uint2(0u, 0u);
+                    __syncwarp();
+                    if (lane < nq) cq[lane] = rest;
+                    __syncwarp();
+                }
+            }
         }
     }
+    if (lane < nq) acc += crossing_terms(A, na, sA, B, nb, sB, org, cq[lane]);
+    __syncwarp();
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     return acc;
 }
@@ -173,7 +214,7 @@ constexpr int kRefineWarps = 8;
 constexpr int kWarpVerts = 512;  // both polygons staged per warp when they fit
 
 // J of one pair by one warp (vertices staged in the warp's shared slice when they fit)
-__device__ double warp_pair_jaccard(PairView A, PairView B, int2* sv, int lane)
+__device__ double warp_pair_jaccard(PairView A, PairView B, int2* sv, uint2* cq, int lane)
 {
     if (A.sgn == 0 || B.sgn == 0) return 0.0;
     const int2* a = A.v;
@@ -185,7 +226,7 @@ __device__ double warp_pair_jaccard(PairView A, PairView B, int2* sv, int lane)
         a = sv;
         b = sv + A.n;
     }
-    const double inter = warp_intersection_area(a, A.n, A.sgn, b, B.n, B.sgn, lane);
+    const double inter = warp_intersection_area(a, A.n, A.sgn, b, B.n, B.sgn, cq, lane);
     __syncwarp();
     const double uni = A.area + B.area - inter;
     return uni > 0 ? fmin(fmax(inter / uni, 0.0), 1.0) : 0.0;
@@ -199,6 +240,7 @@ refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qo
                     const int32_t* __restrict__ qid_list, int64_t n_pairs, double* __restrict__ out)
 {
     __shared__ int2 sv[kRefineWarps][kWarpVerts];
+    __shared__ uint2 cq[kRefineWarps][64];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t nw = (int64_t)gridDim.x * kRefineWarps;
     for (int64_t e = (int64_t)blockIdx.x * kRefineWarps + wid; e < n_pairs; e += nw) {
@@ -217,7 +259,7 @@ refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qo
             p = ids[e];
         }
         const double j = warp_pair_jaccard(view(qxy, qoff, qarea2, q), view(pxy, poff, parea2, p),
-                                           sv[wid], lane);
+                                           sv[wid], cq[wid], lane);
         if (lane == 0) out[e] = j;
     }
 }
