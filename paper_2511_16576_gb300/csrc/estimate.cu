@@ -159,7 +159,10 @@ topm_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ can
     int kept = 0;
     for (int64_t base = b; base < e; base += kTopChunk) {
         int take = (int)(e - base < kTopChunk ? e - base : kTopChunk);
-        for (int i = threadIdx.x; i < cap; i += blockDim.x) {
+        // sort only the occupied prefix, rounded up to a power of two (most lists are short)
+        int sz = 2;
+        while (sz < kept + take) sz <<= 1;
+        for (int i = threadIdx.x; i < sz; i += blockDim.x) {
             uint64_t key = ~0ull;
             if (i >= kept && i < kept + take) {
                 int64_t idx = base + (i - kept);
@@ -171,7 +174,7 @@ topm_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ can
             s[i] = key;
         }
         __syncthreads();
-        bitonic_sort_u64(s, cap);
+        bitonic_sort_u64(s, sz);
         kept = min(m, kept + take);
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x)

@@ -21,6 +21,7 @@
 // so the fp64 work is kept to the crossings (a few per edge) and one Newton
 // reciprocal each.
 #include <algorithm>
+#include <climits>
 
 #include "pmh_internal.cuh"
 
@@ -190,6 +191,179 @@ __device__ double warp_intersection_area(const int2* __restrict__ A, int na, int
     return acc;
 }
 
+// y-slab lists of a staged ring v[0..n) (edge e = v[e] -> v[e+1 mod n]): edge e
+// is listed in every slab of [y0 + s*2^sh, y0 + (s+1)*2^sh) that its closed
+// y-range meets.  Returns false (warp-uniform) if more than kRefSlabCap
+// references would be needed.
+constexpr int kRefSlabs = 32;
+constexpr int kRefSlabCap = 1024;
+struct RefSlabs {
+    uint16_t ids[kRefSlabCap];
+    uint16_t beg[kRefSlabs + 1];
+    int cnt[kRefSlabs];
+    int y0, sh;
+};
+
+__device__ __forceinline__ bool build_ref_slabs(const int2* v, int n, RefSlabs& L, int lane)
+{
+    int y0 = INT_MAX, y1 = INT_MIN;
+    for (int e = lane; e < n; e += 32) {
+        y0 = min(y0, v[e].y);
+        y1 = max(y1, v[e].y);
+    }
+    y0 = __reduce_min_sync(0xffffffffu, y0);
+    y1 = __reduce_max_sync(0xffffffffu, y1);
+    int sh = 0;
+    while (((y1 - y0) >> sh) >= kRefSlabs) ++sh;
+    L.cnt[lane] = 0;
+    __syncwarp();
+    for (int e = lane; e < n; e += 32) {
+        const int2 a = v[e], b = v[e + 1 == n ? 0 : e + 1];
+        const int s0 = (min(a.y, b.y) - y0) >> sh, s1 = (max(a.y, b.y) - y0) >> sh;
+        for (int q = s0; q <= s1; ++q) atomicAdd(&L.cnt[q], 1);
+    }
+    __syncwarp();
+    const int c = L.cnt[lane];
+    int incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total > kRefSlabCap) return false;
+    L.beg[lane] = (uint16_t)(incl - c);
+    if (lane == 31) L.beg[kRefSlabs] = (uint16_t)total;
+    if (lane == 0) {
+        L.y0 = y0;
+        L.sh = sh;
+    }
+    __syncwarp();
+    L.cnt[lane] = incl - c;
+    __syncwarp();
+    for (int e = lane; e < n; e += 32) {
+        const int2 a = v[e], b = v[e + 1 == n ? 0 : e + 1];
+        const int s0 = (min(a.y, b.y) - y0) >> sh, s1 = (max(a.y, b.y) - y0) >> sh;
+        for (int q = s0; q <= s1; ++q) L.ids[atomicAdd(&L.cnt[q], 1)] = (uint16_t)e;
+    }
+    __syncwarp();
+    return true;
+}
+
+// area(A n B) as warp_intersection_area, for staged rings with slab lists: a
+// vertex test reads only the other ring's slab of the vertex's y, and an A edge
+// meets only the B edges listed in the slabs its y-range spans (each pair once:
+// in the first of those slabs that also lists the B edge).
+__device__ double warp_intersection_area_slabs(const int2* __restrict__ A, int na, int sA,
+                                               const RefSlabs& LA, const int2* __restrict__ B, int nb,
+                                               int sB, const RefSlabs& LB, uint2* cq, int lane)
+{
+    const int2 org = B[0];
+    const unsigned full = 0xffffffffu;
+    double acc = 0;
+    const int ya0 = LA.y0, ya1 = LA.y0 + (kRefSlabs << LA.sh) - 1;
+    const int yb0 = LB.y0, yb1 = LB.y0 + (kRefSlabs << LB.sh) - 1;
+    // end terms of A's edges: vertex a_i + e inside B closes edge i-1
+    for (int i = lane; i < na; i += 32) {
+        const int2 a = A[i];
+        unsigned in = 0;
+        if (a.y >= yb0 && a.y <= yb1) {
+            const int q = (a.y - yb0) >> LB.sh;
+            for (int k = LB.beg[q]; k < LB.beg[q + 1]; ++k) {
+                const int j = LB.ids[k];
+                const int2 c = B[j], d = B[j + 1 == nb ? 0 : j + 1];
+                if ((c.y > a.y) != (d.y > a.y)) {
+                    const long long cr = cross3(c, d, a);
+                    in ^= (cr != 0) & ((cr > 0) == (d.y > c.y));
+                }
+            }
+        }
+        if (in) {
+            const int2 p = A[i == 0 ? na - 1 : i - 1];
+            const double x0 = (double)(p.x - org.x), dx = (double)(a.x - p.x), dy = (double)(a.y - p.y);
+            acc += (sA > 0 ? 1.0 : -1.0) * dy * (x0 + 0.5 * dx);
+        }
+    }
+    // end terms of B's edges: vertex c_j - e inside A closes edge j-1
+    for (int j = lane; j < nb; j += 32) {
+        const int2 c = B[j];
+        unsigned in = 0;
+        if (c.y >= ya0 && c.y <= ya1) {
+            const int q = (c.y - ya0) >> LA.sh;
+            for (int k = LA.beg[q]; k < LA.beg[q + 1]; ++k) {
+                const int i = LA.ids[k];
+                const int2 a = A[i], b = A[i + 1 == na ? 0 : i + 1];
+                if ((a.y >= c.y) != (b.y >= c.y)) {
+                    const long long cr = cross3(a, b, c);
+                    in ^= (cr == 0) | ((cr > 0) == (b.y > a.y));
+                }
+            }
+        }
+        if (in) {
+            const int2 p = B[j == 0 ? nb - 1 : j - 1];
+            const double x0 = (double)(p.x - org.x), ex = (double)(c.x - p.x), ey = (double)(c.y - p.y);
+            acc += (sB > 0 ? 1.0 : -1.0) * ey * (x0 + 0.5 * ex);
+        }
+    }
+    // crossings, queued and evaluated 32 at a time as in warp_intersection_area
+    int nq = 0;
+    for (int i0 = 0; i0 < na; i0 += 32) {
+        const int i = i0 + lane;
+        int2 a = make_int2(0, 0), b = make_int2(0, 0);
+        int k0 = 0, cntk = 0, q0 = 0;
+        if (i < na) {
+            a = A[i];
+            b = A[i + 1 == na ? 0 : i + 1];
+            const int lo = min(a.y, b.y), hi = max(a.y, b.y);
+            if ((a.x != b.x || a.y != b.y) && hi >= yb0 && lo <= yb1) {
+                q0 = (max(lo, yb0) - yb0) >> LB.sh;
+                const int q1 = (min(hi, yb1) - yb0) >> LB.sh;
+                k0 = LB.beg[q0];
+                cntk = LB.beg[q1 + 1] - k0;
+            }
+        }
+        const int ax0 = min(a.x, b.x), ax1 = max(a.x, b.x), ay0 = min(a.y, b.y), ay1 = max(a.y, b.y);
+        const int steps = __reduce_max_sync(full, cntk);
+        int q = q0;  // slab of list position k0 + t
+        for (int t = 0; t < steps; ++t) {
+            bool hit = false;
+            int j = 0;
+            if (t < cntk) {
+                const int k = k0 + t;
+                while (k >= LB.beg[q + 1]) ++q;
+                j = LB.ids[k];
+                const int2 c = B[j], d = B[j + 1 == nb ? 0 : j + 1];
+                // this pair is visited once: in the first listed slab of both
+                const int first = max(q0, (min(c.y, d.y) - yb0) >> LB.sh);
+                if (q == first &&
+                    !(max(ax0, min(c.x, d.x)) > min(ax1, max(c.x, d.x)) ||
+                      max(ay0, min(c.y, d.y)) > min(ay1, max(c.y, d.y)) || (c.x == d.x && c.y == d.y))) {
+                    hit = side_of_shifted_point(c, d, a) != side_of_shifted_point(c, d, b) &&
+                          side_of_point_to_shifted(a, b, c) != side_of_point_to_shifted(a, b, d);
+                }
+            }
+            const unsigned bal = __ballot_sync(full, hit);
+            if (bal) {
+                if (hit) cq[nq + __popc(bal & pmh_lanemask_lt())] = make_uint2((uint32_t)i, (uint32_t)j);
+                nq += __popc(bal);
+                __syncwarp();
+                if (nq >= 32) {
+                    acc += crossing_terms(A, na, sA, B, nb, sB, org, cq[lane]);
+                    nq -= 32;
+                    const uint2 rest = lane < nq ? cq[32 + lane] : make_uint2(0u, 0u);
+                    __syncwarp();
+                    if (lane < nq) cq[lane] = rest;
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    if (lane < nq) acc += crossing_terms(A, na, sA, B, nb, sB, org, cq[lane]);
+    __syncwarp();
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(full, acc, o);
+    return acc;
+}
+
 struct PairView {
     const int2* v;
     int n;
@@ -210,23 +384,31 @@ __device__ __forceinline__ PairView view(const int2* xy, const int64_t* off, con
     return r;
 }
 
-constexpr int kRefineWarps = 8;
+constexpr int kRefineWarps = 4;
 constexpr int kWarpVerts = 512;  // both polygons staged per warp when they fit
 
-// J of one pair by one warp (vertices staged in the warp's shared slice when they fit)
-__device__ double warp_pair_jaccard(PairView A, PairView B, int2* sv, uint2* cq, int lane)
+// J of one pair by one warp (vertices staged in the warp's shared slice, with
+// y-slab lists, when they fit)
+__device__ double warp_pair_jaccard(PairView A, PairView B, int2* sv, uint2* cq, RefSlabs* L,
+                                    int lane)
 {
     if (A.sgn == 0 || B.sgn == 0) return 0.0;
     const int2* a = A.v;
     const int2* b = B.v;
+    double inter;
     if (A.n + B.n <= kWarpVerts) {
         for (int i = lane; i < A.n; i += 32) sv[i] = A.v[i];
         for (int i = lane; i < B.n; i += 32) sv[A.n + i] = B.v[i];
         __syncwarp();
         a = sv;
         b = sv + A.n;
+        if (build_ref_slabs(a, A.n, L[0], lane) && build_ref_slabs(b, B.n, L[1], lane))
+            inter = warp_intersection_area_slabs(a, A.n, A.sgn, L[0], b, B.n, B.sgn, L[1], cq, lane);
+        else
+            inter = warp_intersection_area(a, A.n, A.sgn, b, B.n, B.sgn, cq, lane);
+    } else {
+        inter = warp_intersection_area(a, A.n, A.sgn, b, B.n, B.sgn, cq, lane);
     }
-    const double inter = warp_intersection_area(a, A.n, A.sgn, b, B.n, B.sgn, cq, lane);
     __syncwarp();
     const double uni = A.area + B.area - inter;
     return uni > 0 ? fmin(fmax(inter / uni, 0.0), 1.0) : 0.0;
@@ -241,6 +423,7 @@ refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qo
 {
     __shared__ int2 sv[kRefineWarps][kWarpVerts];
     __shared__ uint2 cq[kRefineWarps][64];
+    __shared__ RefSlabs sl[kRefineWarps][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t nw = (int64_t)gridDim.x * kRefineWarps;
     for (int64_t e = (int64_t)blockIdx.x * kRefineWarps + wid; e < n_pairs; e += nw) {
@@ -259,7 +442,7 @@ refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qo
             p = ids[e];
         }
         const double j = warp_pair_jaccard(view(qxy, qoff, qarea2, q), view(pxy, poff, parea2, p),
-                                           sv[wid], cq[wid], lane);
+                                           sv[wid], cq[wid], sl[wid], lane);
         if (lane == 0) out[e] = j;
     }
 }
