@@ -419,14 +419,20 @@ refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qo
                     const int64_t* __restrict__ qarea2, const int2* __restrict__ pxy,
                     const int64_t* __restrict__ poff, const int64_t* __restrict__ parea2,
                     const int32_t* __restrict__ ids, const int32_t* __restrict__ nlist, int m,
-                    const int32_t* __restrict__ qid_list, int64_t n_pairs, double* __restrict__ out)
+                    const int32_t* __restrict__ qid_list, int64_t n_pairs, double* __restrict__ out,
+                    unsigned long long* __restrict__ ticket)
 {
     __shared__ int2 sv[kRefineWarps][kWarpVerts];
     __shared__ uint2 cq[kRefineWarps][64];
     __shared__ RefSlabs sl[kRefineWarps][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t nw = (int64_t)gridDim.x * kRefineWarps;
-    for (int64_t e = (int64_t)blockIdx.x * kRefineWarps + wid; e < n_pairs; e += nw) {
+    // persistent warps pull pairs from a ticket: pair costs differ by orders of
+    // magnitude (a query against its own source vs a neighbour it barely touches)
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1ull);
+        const int64_t e = (int64_t)__shfl_sync(0xffffffffu, t, 0);
+        if (e >= n_pairs) break;
         int64_t q;
         int32_t p;
         if (qid_list) {  // explicit pairs
@@ -500,6 +506,27 @@ __global__ void topk_by_j_kernel(const int32_t* __restrict__ ids, const int32_t*
 
 }  // namespace
 
+// persistent grid (SM count x resident blocks) over the pairs, with its ticket in
+// context slot kRefineTicket
+constexpr int kRefineTicket = 6;
+static int launch_refine(pmh_ctx ctx, pmh_polys queries, pmh_polys db, const int32_t* ids,
+                         const int32_t* nlist, int m, const int32_t* qid_list, int64_t n_pairs,
+                         double* out, cudaStream_t s)
+{
+    int per_sm = 0;
+    PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_pairs_kernel,
+                                                               kRefineWarps * 32, 0));
+    const int blocks = (int)std::min<int64_t>((n_pairs + kRefineWarps - 1) / kRefineWarps,
+                                              (int64_t)ctx->sm_count * std::max(per_sm, 1));
+    unsigned long long* ticket = ctx->d_tickets + kRefineTicket;
+    PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
+    refine_pairs_kernel<<<blocks, kRefineWarps * 32, 0, s>>>(
+        queries->xy, queries->offsets, queries->area2, db->xy, db->offsets, db->area2, ids, nlist, m,
+        qid_list, n_pairs, out, ticket);
+    PMH_LAUNCHED("refine_pairs_kernel");
+    return PMH_OK;
+}
+
 extern "C" int pmh_refine_topk(pmh_ctx ctx, pmh_polys queries, pmh_polys db, const int32_t* d_ids,
                                const int32_t* d_n, int64_t Q, int32_t m, int32_t k,
                                int32_t* d_top_ids, double* d_top_j, void* stream)
@@ -513,12 +540,7 @@ extern "C" int pmh_refine_topk(pmh_ctx ctx, pmh_polys queries, pmh_polys db, con
     double* jv = nullptr;
     PMH_TRY(pmh_scratch(ctx, SCR_REFINE, sizeof(double) * (size_t)(Q * m), (void**)&jv));
     int64_t n_pairs = Q * m;
-    int blocks = (int)std::min<int64_t>((n_pairs + kRefineWarps - 1) / kRefineWarps,
-                                        (int64_t)ctx->sm_count * 8);
-    refine_pairs_kernel<<<blocks, kRefineWarps * 32, 0, s>>>(
-        queries->xy, queries->offsets, queries->area2, db->xy, db->offsets, db->area2, d_ids, d_n, m,
-        nullptr, n_pairs, jv);
-    PMH_LAUNCHED("refine_pairs_kernel");
+    PMH_TRY(launch_refine(ctx, queries, db, d_ids, d_n, m, nullptr, n_pairs, jv, s));
     int cap = 1;
     while (cap < m) cap <<= 1;
     size_t smem = sizeof(JKey) * cap;
@@ -534,14 +556,7 @@ extern "C" int pmh_pair_jaccard(pmh_ctx ctx, pmh_polys queries, pmh_polys db, co
     if (!queries || !db || n_pairs < 0 || (n_pairs > 0 && (!d_qid || !d_pid || !d_j)))
         return pmh_set_error(PMH_ERR_ARG, "bad arguments");
     if (n_pairs == 0) return PMH_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    int blocks = (int)std::min<int64_t>((n_pairs + kRefineWarps - 1) / kRefineWarps,
-                                        (int64_t)ctx->sm_count * 8);
-    refine_pairs_kernel<<<blocks, kRefineWarps * 32, 0, s>>>(
-        queries->xy, queries->offsets, queries->area2, db->xy, db->offsets, db->area2, d_pid,
-        nullptr, 1, d_qid, n_pairs, d_j);
-    PMH_LAUNCHED("refine_pairs_kernel");
-    return PMH_OK;
+    return launch_refine(ctx, queries, db, d_pid, nullptr, 1, d_qid, n_pairs, d_j, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
