@@ -393,9 +393,15 @@ def main():
                           "achieved": ops / (kms * 1e-3) / 1e12 if kms > 0 else None,
                           "frac": ops / (kms * 1e-3) / peak if kms > 0 else None}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    # DRAM bytes (read + write) of one sign_indexed_kernel launch from an ncu capture on
+    # the 200,000-polygon slice of this workload (399.3 MB), scaled by polygons to the
+    # 1,000,000-polygon launch; other sizes and kernels: not measured
+    traffic = 5 * 399.3e6 if dom == "sign_indexed_kernel" and N == 1000000 and w.name == "scale" else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": kernels[dom]["achieved"],
                 "peak": peak / 1e12, "unit": "Tintop/s", "frac": kernels[dom]["frac"],
-                "traffic": None, "op_weights": SIGN_OP_WEIGHTS,
+                "traffic": traffic, "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                "of a 200,000-polygon launch x 5" if traffic else None,
+                "op_weights": SIGN_OP_WEIGHTS,
                 "peak_source": "measured: pmh_probe_int_peak (integer mad/add/xor/shl mix, all SMs)",
                 "kernels": kernels, "timed_launches": kernel_ms["calls"],
                 "sign_ms": sign_ms, "stream_points_resolved": G,
