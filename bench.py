@@ -131,6 +131,17 @@ def algorithmic_points(hashes_np: np.ndarray, T: int) -> int:
     return int(np.where(h < T, h + 1, T).sum())
 
 
+def arm_config(args, w, db, Q, world):
+    """The workload both arms report (the reference arm runs a sample of it)."""
+    return {"workload": f"{w.name}: {db.n} star polygons ({db.n_vertices} vertices), K={w.K}, "
+                        f"{w.bands}x{w.rows} bands, {Q} perturbed-copy queries, "
+                        f"top-{args.topm} refined to top-10",
+            "l2": (f"inputs larger than L2 ({db.xy.nbytes / 1e6:.0f} MB of vertices)"
+                   if db.xy.nbytes > 129e6 else
+                   f"inputs smaller than L2 ({db.xy.nbytes / 1e6:.0f} MB of vertices), L2 not flushed"),
+            "parallelism": f"{world} independent shard(s)"}
+
+
 def run_reference(args, w):
     """The oracle as it stands, on the host cores, on a bounded sample of the workload."""
     world, rank, _ = dist_setup(args)
@@ -160,8 +171,7 @@ def run_reference(args, w):
         "unit": "hashes/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"{w.name}: {w.n_polys} star polygons, K={w.K}, "
-                               f"{w.bands}x{w.rows} bands", "sample_polygons": n_sample},
+        "config": arm_config(args, w, db, args.n_queries or w.n_queries, world),
         "cpu_baseline": {"value": value, "unit": "hashes/s", "cores": cores, "kind": "oracle",
                          "sample": f"oracle sign + band keys of {n_sample} random polygons of the "
                                    f"{w.n_polys}-polygon workload per step"},
@@ -422,11 +432,7 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": f"{w.name}: {N} star polygons ({db.n_vertices} vertices), K={K}, "
-                               f"{w.bands}x{w.rows} bands, {Q} perturbed-copy queries, "
-                               f"top-{args.topm} refined to top-10",
-                   "l2": f"inputs larger than L2 ({db.xy.nbytes / 1e6:.0f} MB of vertices)",
-                   "parallelism": f"{world} independent shard(s)"},
+        "config": arm_config(args, w, db, Q, world),
         "sign_hashes_per_s": world * N * K / (sign_ms * 1e-3),
         "candidates_per_query": float(out[1].numel()) / Q,
         "roofline": roofline,
