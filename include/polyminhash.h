@@ -141,7 +141,11 @@ int pmh_polys_destroy(pmh_polys polys);
 
 /* A1 -- MinHash signatures (Definition 2, Algorithm 1; 0-based, cap T).
  *   d_hashes  uint32 [n_polys][K] row-major, written completely.
- * Hashes are exact: bit-identical to the definition above.
+ * Hashes are exact: bit-identical to the definition above.  The first call on
+ * a context with PMH_FLAG_STREAM_INDEX builds the stream index for (seed, K),
+ * and the first call on a polygon set without it builds the set's cost order;
+ * both synchronise the stream once.  Calls on one polygon set from several
+ * host threads at once must be serialised by the caller.
  * Errors: PMH_ERR_ARG (null, bad K/T), PMH_ERR_CUDA. */
 int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* params,
                      uint32_t* d_hashes, void* stream);

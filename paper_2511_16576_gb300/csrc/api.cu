@@ -268,7 +268,7 @@ static int upload_common(pmh_ctx ctx, const int32_t* xy, const int64_t* offsets,
             return fail(pmh_set_error(PMH_ERR_CUDA, "feature kernel: %s", cudaGetErrorString(e)));
     }
     int rc = pmh_build_slabs(P, s);
-    if (rc == PMH_OK) rc = pmh_build_cost_order(P, s);
+    if (rc == PMH_OK) rc = pmh_build_class_order(P, s);
     if (rc != PMH_OK) return fail(rc);
     *out = P;
     return PMH_OK;

@@ -214,7 +214,8 @@ struct pmh_polys_s {
     SlabInfo* slab_info = nullptr;  // [n]
     int32_t* slab_ptr = nullptr;
     int32_t* slab_edges = nullptr;
-    int32_t* order = nullptr;       // polygons by expected signing cost, largest first
+    int32_t* order = nullptr;       // polygons by expected signing cost, largest first (built
+                                    // on the first signing call without the stream index)
     int32_t* order_cls = nullptr;   // class order: staged indexed-form polygons (Morton order),
                                     // staged walk-form polygons, the rest (each by cost)
     int64_t n_indexed = 0;          // class 0: <= kStagedMaxVerts vertices, pmh_index_plan lim > 0
@@ -234,7 +235,8 @@ __host__ __device__ __forceinline__ int mask_cell_log2(int w)
     while ((1 << l) < a) ++l;
     return l;
 }
-int pmh_build_cost_order(pmh_polys P, cudaStream_t s);
+int pmh_build_cost_order(pmh_polys P, cudaStream_t s);   // P->order (walk form without the index)
+int pmh_build_class_order(pmh_polys P, cudaStream_t s);  // P->order_cls and the class counts
 
 struct pmh_index_s {
     pmh_ctx ctx = nullptr;

@@ -372,6 +372,7 @@ extern "C" int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* 
     const bool indexed = (params->flags & PMH_FLAG_STREAM_INDEX) != 0;
     const bool masked = (params->flags & PMH_FLAG_COVERAGE_MASK) != 0;
     if (indexed) PMH_TRY(pmh_stream_index_get(ctx, params, (cudaStream_t)stream, &sidx));
+    if ((!indexed || !sidx.ranked) && !polys->order) PMH_TRY(pmh_build_cost_order(polys, (cudaStream_t)stream));
     if (masked && !polys->mask) PMH_TRY(pmh_build_masks(polys, (cudaStream_t)stream));
     return pmh_launch_sign(ctx, polys->xy, polys->offsets, polys->bbox, polys->slab_info,
                            polys->slab_ptr, polys->slab_edges, polys->order, params, polys->n,
@@ -474,6 +475,7 @@ extern "C" int pmh_sign_autotune(pmh_ctx ctx, pmh_polys sample, const pmh_params
             const bool indexed = (params->flags & PMH_FLAG_STREAM_INDEX) != 0;
             const bool masked = (params->flags & PMH_FLAG_COVERAGE_MASK) != 0;
             if (indexed) rc = pmh_stream_index_get(ctx, params, 0, &sidx);
+            if (rc == PMH_OK && (!indexed || !sidx.ranked) && !sample->order) rc = pmh_build_cost_order(sample, 0);
             if (rc == PMH_OK && masked && !sample->mask) rc = pmh_build_masks(sample, 0);
             if (rc == PMH_OK)
                 rc = pmh_launch_sign(ctx, sample->xy, sample->offsets, sample->bbox, sample->slab_info,

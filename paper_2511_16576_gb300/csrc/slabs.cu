@@ -271,8 +271,32 @@ int pmh_build_cost_order(pmh_polys P, cudaStream_t s)
     g_pmh_launches.fetch_add(1);
     int rc = e == cudaSuccess ? pmh_radix_sort_u32(ctx, keys, P->order, n, 32, s)
                               : pmh_set_error(PMH_ERR_CUDA, "cost key: %s", cudaGetErrorString(e));
-    // the class order of the indexed form; the class-0 count follows the keys
-    if (rc == PMH_OK && cudaMalloc(&P->order_cls, sizeof(int32_t) * n) != cudaSuccess) {
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    if (rc == PMH_OK && e2 != cudaSuccess)
+        rc = pmh_set_error(PMH_ERR_CUDA, "cost order: %s", cudaGetErrorString(e2));
+    cudaFree(keys);
+    if (rc != PMH_OK) {
+        cudaFree(P->order);
+        P->order = nullptr;
+    }
+    return rc;
+}
+
+int pmh_build_class_order(pmh_polys P, cudaStream_t s)
+{
+    pmh_ctx ctx = P->ctx;
+    const int64_t n = P->n;
+    if (n == 0) return PMH_OK;
+    uint32_t* keys = nullptr;
+    if (cudaMalloc(&keys, sizeof(uint32_t) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return pmh_set_error(PMH_ERR_NOMEM, "class order allocation failed");
+    }
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)ctx->sm_count * 32);
+    cudaError_t e;
+    int rc = PMH_OK;
+    // the class order of the indexed form; the class counts follow the keys
+    if (cudaMalloc(&P->order_cls, sizeof(int32_t) * n) != cudaSuccess) {
         cudaGetLastError();
         rc = pmh_set_error(PMH_ERR_NOMEM, "class order allocation failed");
     }
@@ -296,7 +320,7 @@ int pmh_build_cost_order(pmh_polys P, cudaStream_t s)
         rc = pmh_set_error(PMH_ERR_CUDA, "class count copy failed");
     const cudaError_t e2 = cudaStreamSynchronize(s);
     if (rc == PMH_OK && e2 != cudaSuccess)
-        rc = pmh_set_error(PMH_ERR_CUDA, "cost order: %s", cudaGetErrorString(e2));
+        rc = pmh_set_error(PMH_ERR_CUDA, "class order: %s", cudaGetErrorString(e2));
     if (rc == PMH_OK) {
         P->n_indexed = ctx->h_pinned[0];
         P->n_staged_walk = ctx->h_pinned[1];
