@@ -131,6 +131,20 @@ def algorithmic_points(hashes_np: np.ndarray, T: int) -> int:
     return int(np.where(h < T, h + 1, T).sum())
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of this GPU pool (GB/s), if the peaks file is present."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    for key in ("hbm_gbs", "hbm_GBps", "hbm"):
+        if isinstance(d.get(key), (int, float)):
+            return float(d[key])
+    return None
+
+
 def arm_config(args, w, db, Q, world):
     """The workload both arms report (the reference arm runs a sample of it)."""
     return {"workload": f"{w.name}: {db.n} star polygons ({db.n_vertices} vertices), K={w.K}, "
@@ -414,6 +428,13 @@ def main():
                 "op_weights": SIGN_OP_WEIGHTS,
                 "peak_source": "measured: pmh_probe_int_peak (integer mad/add/xor/shl mix, all SMs)",
                 "kernels": kernels, "timed_launches": kernel_ms["calls"],
+                "edge_tests_per_s": sum(k["work_units_per_launch"]["edge_tests"] for k in kernels.values())
+                / (sign_ms * 1e-3),
+                # the vertex stream (8 B per vertex, staged once per polygon by the signing kernels)
+                # against the measured HBM copy bandwidth: far from being the bound
+                "vertex_stream_gbs": db.xy.nbytes / (sign_ms * 1e-3) / 1e9,
+                "vertex_stream_frac_of_hbm": db.xy.nbytes / (sign_ms * 1e-3) / 1e9 / hbm_peak_gbs()
+                if hbm_peak_gbs() else None,
                 "sign_ms": sign_ms, "stream_points_resolved": G,
                 "stream_points_resolved_per_s": G / (sign_ms * 1e-3),
                 "walk_equivalent_tintops": INT_OPS_PER_POINT * G / (sign_ms * 1e-3) / 1e12}
