@@ -300,7 +300,7 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     const StreamIndexView* sidx, const uint32_t* masks,
                     const int32_t* order_cls, int64_t n_indexed, int64_t n_staged_walk)
 {
-    const StreamIndexView S = sidx ? *sidx : StreamIndexView{nullptr, nullptr, 0, 0, 0, 0, 0};
+    const StreamIndexView S = sidx ? *sidx : StreamIndexView{};
     if (n_polys <= 0) return PMH_OK;
     unsigned long long* work = d_n ? nullptr : ctx->d_tickets + kWorkSlot;
     if (work) {
