@@ -64,6 +64,13 @@ def parse():
     ap.add_argument("--eval-queries", type=int, default=1000,
                     help="queries whose recall@10 is checked against brute force")
     ap.add_argument("--train-queries", type=int, default=4000)
+    ap.add_argument("--paper-sweep", action="store_true",
+                    help="paper-shaped centred sets, one hashmap keyed on m = 1..5 hashes (prints one "
+                         "JSON line with the table instead of the benchmark line)")
+    ap.add_argument("--paper-scale", type=float, default=1.0, help="fraction of the paper set sizes")
+    ap.add_argument("--paper-sets", default="n9,n12,n95",
+                    help="paper-shaped sets of the sweep (n319 needs an exhaustive search over "
+                         "319-vertex pairs: hours at full size)")
     return ap.parse_args()
 
 
@@ -129,6 +136,111 @@ def algorithmic_points(hashes_np: np.ndarray, T: int) -> int:
     """Stream points the definition examines: h + 1 for a hit, T for the sentinel."""
     h = hashes_np.astype(np.int64)
     return int(np.where(h < T, h + 1, T).sum())
+
+
+def paper_sweep(args):
+    """The paper's own configuration on paper-shaped sets (Sec. 3.1 centring and global MBR,
+    Sec. 5.2-5.3 single hashmap keyed on the m-hash code, every candidate refined): per set
+    and m = 1..5, the time to hash the database, to build and query the hashmap, to refine
+    all candidates exactly, the candidates per query (pruning) and recall@10 against the
+    exhaustive exact search over all polygons (they all overlap once centred)."""
+    import torch
+    from paper_2511_16576_gb300 import binding as B, synth, build as cuda_build
+    from paper_2511_16576_gb300 import evaluate as ev
+    cuda_build.build()
+    dev = torch.device("cuda", 0)
+    ctx = B.Context(0)
+    stream = torch.cuda.current_stream()
+    n_q, k = 100, 10
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    def top_k(qn, row_ptr, cand, j):
+        ids = np.full((qn, k), -1, np.int32)
+        jj = np.full((qn, k), -1.0)
+        n_pos = np.zeros(qn, np.int64)
+        rp = row_ptr.cpu().numpy()
+        cd = cand.cpu().numpy()
+        jv = j.cpu().numpy()
+        for q in range(qn):
+            sj, si = jv[rp[q]:rp[q + 1]], cd[rp[q]:rp[q + 1]]
+            pos = sj > 0
+            sj, si = sj[pos], si[pos]
+            o = np.lexsort((si, -sj))[:k]
+            ids[q, :len(o)], jj[q, :len(o)], n_pos[q] = si[o], sj[o], len(o)
+        return ids, jj, n_pos
+
+    def truth_top_k(qn, jv, n):
+        # exhaustive search: the 32 best of each query's row on the device, then the
+        # (J desc, id asc) order of those on the host
+        vals, idx = torch.topk(jv.view(qn, n), min(32, n), dim=1)
+        vals, idx = vals.cpu().numpy(), idx.cpu().numpy().astype(np.int32)
+        ids = np.full((qn, k), -1, np.int32)
+        jj = np.full((qn, k), -1.0)
+        n_pos = np.zeros(qn, np.int64)
+        for q in range(qn):
+            pos = vals[q] > 0
+            sj, si = vals[q][pos], idx[q][pos]
+            o = np.lexsort((si, -sj))[:k]
+            ids[q, :len(o)], jj[q, :len(o)], n_pos[q] = si[o], sj[o], len(o)
+        return ids, jj, n_pos
+
+    rows = []
+    for name in args.paper_sets.split(","):
+        n_full, mean_v = synth.PAPER_SETS[name]
+        n = max(1000, int(n_full * args.paper_scale))
+        db = synth.paper_shaped(n, mean_v, seed=7 + len(rows))
+        qs = synth.paper_queries(db, n_q, seed=107 + len(rows))
+        dbp = B.poly_upload(ctx, torch.from_numpy(db.xy).to(dev), torch.from_numpy(db.offsets).to(dev))
+        qp = B.poly_upload(ctx, torch.from_numpy(qs.xy).to(dev), torch.from_numpy(qs.offsets).to(dev))
+        # exhaustive exact search: every (query, polygon) pair, in chunks of queries
+        all_ids = torch.arange(db.n, dtype=torch.int32, device=dev)
+        t_ids, t_j, t_pos = [], [], []
+        bf_ms = 0.0
+        for q0 in range(0, n_q, 10):
+            qn = min(10, n_q - q0)
+            qid = torch.arange(q0, q0 + qn, dtype=torch.int32, device=dev).repeat_interleave(db.n)
+            cand = all_ids.repeat(qn)
+            jv, ms = timed(lambda: B.pair_jaccard(ctx, qp, dbp, qid, cand))
+            bf_ms += ms
+            a, b_, c_ = truth_top_k(qn, jv, db.n)
+            t_ids.append(a), t_j.append(b_), t_pos.append(c_)
+        truth = ev.Truth(np.concatenate(t_ids), np.concatenate(t_j), np.concatenate(t_pos), n_q * db.n)
+        for m in range(1, 6):
+            P = B.make_params(m, 1, 1 << 24, flags=B.FLAG_STREAM_INDEX)
+            B.minhash_sign(ctx, dbp, P)                       # builds the stream index for (seed, m)
+            h, hash_ms = timed(lambda: B.minhash_sign(ctx, dbp, P))
+            qh = B.minhash_sign(ctx, qp, P)
+
+            def hashmap():
+                index = B.lsh_build(ctx, h, P)
+                rp, cd = B.lsh_query(ctx, index, qh)
+                return index, rp, cd
+            (index, row_ptr, cand), map_ms = timed(hashmap)
+            index.close()
+            counts = (row_ptr[1:] - row_ptr[:-1])
+            qid = torch.repeat_interleave(torch.arange(n_q, dtype=torch.int32, device=dev), counts)
+            E = int(row_ptr[-1].item())
+            jv, ref_ms = timed(lambda: B.pair_jaccard(ctx, qp, dbp, qid, cand[:E]) if E else
+                               torch.zeros(0, dtype=torch.float64, device=dev))
+            ids, jj, _ = top_k(n_q, row_ptr, cand[:E], jv)
+            rows.append({"set": name, "polygons": db.n, "mean_vertices": db.n_vertices / db.n, "m": m,
+                         "hash_ms": hash_ms, "hashmap_ms": map_ms, "refine_ms": ref_ms,
+                         "candidates_per_query": E / n_q, "pruning": 1.0 - E / (n_q * db.n),
+                         "recall_at_10": ev.recall_at_k(ids, jj, truth, k),
+                         "brute_force_ms": bf_ms})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        qp.close()
+        dbp.close()
+    print(json.dumps({"paper_sweep": rows, "queries": n_q, "k": k, "scale": args.paper_scale}), flush=True)
+    ctx.close()
 
 
 def hbm_peak_gbs():
@@ -277,6 +389,9 @@ def main():
     w = synth.WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, w)
+        return
+    if args.paper_sweep:
+        paper_sweep(args)
         return
     assert args.warmup >= 3 or os.environ.get("PMH_BENCH_ALLOW_SHORT"), "warm-up >= 3"
 

@@ -258,6 +258,90 @@ def perturbed_queries(db: PolySet, n_queries: int, seed: int, max_rot_deg: float
 
 
 # ----------------------------------------------------------------------------
+# Paper-shaped sets (Sec. 3.1 preprocessing applied at generation time).
+# ----------------------------------------------------------------------------
+# Vertex-count means and sizes of the paper's four evaluation sets (Sec. 5.1, Table 1).
+PAPER_SETS = {"n9": (149_000, 9.26), "n12": (1_000_000, 12.0), "n95": (11_800, 95.4),
+              "n319": (300_000, 319.0)}
+
+
+def centroids(xy: np.ndarray, offsets: np.ndarray) -> np.ndarray:
+    """Area centroids [N, 2] (float64) of simple polygons given as float or int rings."""
+    x = xy[:, 0].astype(np.float64)
+    y = xy[:, 1].astype(np.float64)
+    n = np.diff(offsets)
+    pid = np.repeat(np.arange(len(n)), n)
+    nxt = np.arange(len(x)) + 1
+    nxt[offsets[1:] - 1] = offsets[:-1]
+    cr = x * y[nxt] - x[nxt] * y
+    a6 = 3.0 * np.bincount(pid, weights=cr, minlength=len(n))  # 6 * area
+    cx = np.bincount(pid, weights=(x + x[nxt]) * cr, minlength=len(n)) / a6
+    cy = np.bincount(pid, weights=(y + y[nxt]) * cr, minlength=len(n)) / a6
+    return np.stack([cx, cy], axis=1)
+
+
+def center_and_quantize(xy: np.ndarray, offsets: np.ndarray, mbr=None):
+    """Sec. 3.1 preprocessing: move every polygon's centroid to (0, 0), take the global
+    MBR of the moved polygons (or the given one), and map it onto the 2^16 lattice
+    domain (x and y scaled separately, so that a uniform point of the lattice is a
+    uniform point of the MBR).  Returns (int64 x, int64 y, the MBR, the lattice point
+    of (0, 0))."""
+    c = centroids(xy, offsets)
+    pid = np.repeat(np.arange(len(offsets) - 1), np.diff(offsets))
+    px = xy[:, 0].astype(np.float64) - c[pid, 0]
+    py = xy[:, 1].astype(np.float64) - c[pid, 1]
+    if mbr is None:
+        mbr = (px.min(), py.min(), px.max(), py.max())
+    x0, y0, x1, y1 = mbr
+    sx, sy = DOMAIN / (x1 - x0), DOMAIN / (y1 - y0)
+    qx = np.clip(np.rint((px - x0) * sx), 0, DOMAIN).astype(np.int64)
+    qy = np.clip(np.rint((py - y0) * sy), 0, DOMAIN).astype(np.int64)
+    origin = (int(np.rint(-x0 * sx)), int(np.rint(-y0 * sy)))
+    return qx, qy, mbr, origin
+
+
+def paper_shaped(n_polys: int, mean_vertices: float, seed: int, size_ratio: float = 30.0) -> PolySet:
+    """Polygons shaped like a paper evaluation set, centred and quantized onto the lattice.
+
+    Vertex counts are 3 + Poisson(mean - 3); radii log-uniform over a ``size_ratio`` span
+    (the largest polygons set the global MBR, the smallest are sparse in it); star
+    outlines (sorted uniform angles, radius jitter +-30%) in float coordinates, then
+    centred on their centroids and mapped onto the lattice by ``center_and_quantize``.
+    Every polygon is made star-shaped around the lattice image of (0, 0), so all of
+    them contain it, as centred polygons do."""
+    rng = np.random.default_rng(seed)
+    n = 3 + rng.poisson(max(mean_vertices - 3.0, 0.0), size=n_polys).astype(np.int64)
+    r = np.exp(rng.uniform(0.0, math.log(size_ratio), n_polys))
+    V = int(n.sum())
+    pid = np.repeat(np.arange(n_polys, dtype=np.int64), n)
+    offs = np.zeros(n_polys + 1, np.int64)
+    np.cumsum(n, out=offs[1:])
+    pos = np.arange(V, dtype=np.int64) - offs[pid]
+    ang = (pos + rng.uniform(0.05, 0.95, V)) * (2 * math.pi) / n[pid]   # stratified: star-shaped
+    rad = r[pid] * rng.uniform(0.7, 1.3, V)
+    fxy = np.stack([rad * np.cos(ang), rad * np.sin(ang)], axis=1)
+    qx, qy, mbr, origin = center_and_quantize(fxy, offs)
+    ox = np.full(n_polys, origin[0], np.int64)
+    oy = np.full(n_polys, origin[1], np.int64)
+    rbar = r * DOMAIN / (mbr[2] - mbr[0])
+    xy, offs2 = _make_star_shaped(qx, qy, pid, ox, oy, n_polys, rbar)
+    return PolySet(xy, offs2, np.stack([ox, oy], axis=1), rbar)
+
+
+def paper_queries(db: PolySet, n_queries: int, seed: int) -> PolySet:
+    """Perturbed copies of paper-shaped polygons, centred again on the common lattice
+    point (integer shift of each copy's centroid)."""
+    qs = perturbed_queries(db, n_queries, seed)
+    c = centroids(qs.xy, qs.offsets)
+    shift = np.rint(qs.centre - c).astype(np.int64)
+    pid = np.repeat(np.arange(qs.n), np.diff(qs.offsets))
+    x = np.clip(qs.xy[:, 0].astype(np.int64) + shift[pid, 0], 0, DOMAIN)
+    y = np.clip(qs.xy[:, 1].astype(np.int64) + shift[pid, 1], 0, DOMAIN)
+    xy, offs = _make_star_shaped(x, y, pid, qs.centre[:, 0], qs.centre[:, 1], qs.n, qs.rbar)
+    return PolySet(xy, offs, qs.centre, qs.rbar, qs.source)
+
+
+# ----------------------------------------------------------------------------
 # Named workloads (sizes of the five evaluation configurations).
 # ----------------------------------------------------------------------------
 @dataclasses.dataclass(frozen=True)
