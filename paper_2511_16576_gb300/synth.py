@@ -14,7 +14,12 @@ in for them with the shapes the workloads name:
 * fractal stars: the radius is a midpoint-displacement profile (coastline-like
   boundaries with up to 65,536 vertices);
 * queries: perturbed copies of database polygons (rotation, scale, vertex
-  jitter about the source centre).
+  jitter about the source centre);
+* paper-shaped sets: the vertex-count means and sizes of the paper's four
+  sets, prepared as Sec. 3.1 prepares data before hashing (centroid moved to
+  the origin, one global MBR mapped onto the lattice).  That preparation is
+  done here, at generation time, so that both sides receive the same lattice
+  polygons; the hashing itself (Sec. 3.2 on) is not in this module.
 
 Every polygon is rounded to int32 and then made strictly star-shaped around its
 (integer) centre by dropping any vertex v_i with (v_i - c) x (v_{i+1} - c) <= 0,
