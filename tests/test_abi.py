@@ -60,3 +60,44 @@ def test_params_struct_layout():
     assert ctypes.sizeof(binding.Params) == 40
     p = binding.make_params(128, 16)
     assert (p.K, p.bands, p.rows, p.T) == (128, 16, 8, 1 << 24)
+
+
+def test_header_layout_and_constants_match_the_binding(tmp_path):
+    """The header compiled by a plain C compiler: pmh_params field offsets and the
+    shared constants equal the binding's ctypes view of them."""
+    import shutil
+    import subprocess
+    from paper_2511_16576_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "polyminhash.h"
+int main(void) {
+    printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(pmh_params),
+           offsetof(pmh_params, seed), offsetof(pmh_params, K), offsetof(pmh_params, T),
+           offsetof(pmh_params, bands), offsetof(pmh_params, rows),
+           offsetof(pmh_params, lsh_seed), offsetof(pmh_params, flags),
+           offsetof(pmh_params, reserved));
+    printf("%d %d %d %d %d %u %u %d\n", PMH_SIGN_VARIANTS, PMH_RERANK_IN, PMH_RERANK_HIDDEN,
+           PMH_RERANK_PARAMS, PMH_NOALLOC_MAX_POLYS, PMH_FLAG_STREAM_INDEX,
+           PMH_FLAG_COVERAGE_MASK, PMH_ERR_CAPACITY);
+    return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    lines = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    sizes = [int(v) for v in lines[0].split()]
+    P = binding.Params
+    assert sizes[0] == ctypes.sizeof(P)
+    for off, (name, _) in zip(sizes[1:], P._fields_):
+        assert off == getattr(P, name).offset, name
+    consts = [int(v) for v in lines[1].split()]
+    assert consts == [binding.SIGN_VARIANTS, binding.RERANK_IN, binding.RERANK_HIDDEN,
+                      binding.RERANK_PARAMS, binding.NOALLOC_MAX_POLYS, binding.FLAG_STREAM_INDEX,
+                      binding.FLAG_COVERAGE_MASK, binding.PMH_ERR_CAPACITY]
