@@ -243,6 +243,17 @@ def paper_sweep(args):
     ctx.close()
 
 
+def nominal_int_peak(dev, clk):
+    """SMs x 128 integer lanes x the maximum SM clock, in T int-op/s (None if unknown)."""
+    try:
+        import torch
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = float(clk.get("sm_max_mhz") or 0.0) if isinstance(clk, dict) else 0.0
+        return sms * 128 * mhz * 1e6 / 1e12 if mhz > 0 else None
+    except Exception:  # measurement context only: never fail the benchmark line for it
+        return None
+
+
 def hbm_peak_gbs():
     """Measured HBM copy bandwidth of this GPU pool (GB/s), if the peaks file is present."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -542,6 +553,7 @@ def main():
                 "of a 200,000-polygon launch x 5" if traffic else None,
                 "op_weights": SIGN_OP_WEIGHTS,
                 "peak_source": "measured: pmh_probe_int_peak (integer mad/add/xor/shl mix, all SMs)",
+                "peak_nominal": nominal_int_peak(dev, clk),
                 "kernels": kernels, "timed_launches": kernel_ms["calls"],
                 "edge_tests_per_s": sum(k["work_units_per_launch"]["edge_tests"] for k in kernels.values())
                 / (sign_ms * 1e-3),
