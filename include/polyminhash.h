@@ -72,16 +72,20 @@ typedef struct pmh_index_s* pmh_index;
  *   flags     0 or PMH_FLAG_STREAM_INDEX | PMH_FLAG_COVERAGE_MASK */
 /* pmh_params.flags: sign through the stream index (same hashes, much less
  * work for small polygons).  The first call with a given (seed, K) builds the
- * index of the first 65,536 points of each stream, bucketed by cell of a
- * 128 x 128 grid (K * 512 KiB of device memory, kept by the context; that
- * call synchronises); later calls reuse it. */
+ * index of the first 65,536 / 32,768 / 8,192 points of each stream, bucketed by
+ * cell of a 128 x 128 / 64 x 64 / 32 x 32 grid (about K * 840 KiB of device
+ * memory, kept by the context; that call synchronises); later calls reuse it.
+ * Each polygon's form (index or walk) and grid level are planned at upload from
+ * its box and area. */
 #define PMH_FLAG_STREAM_INDEX 1u
-/* pmh_params.flags: decide bounding-box candidates through a per-polygon
- * 16 x 16 coverage mask where it can (cells no edge touches are wholly inside
- * or outside), running the exact edge test only in boundary cells.  Same
- * hashes.  The masks are built on the first such call for a polygon set
- * (64 bytes per polygon of up to 256 vertices) and kept with it; they pay off
- * when a set is signed more than once. */
+/* pmh_params.flags: decide bounding-box candidates of the walk through a
+ * precomputed per-polygon 16 x 16 coverage mask where it can (cells no edge
+ * touches are wholly inside or outside), running the exact edge test only in
+ * boundary cells.  Same hashes.  The masks are built on the first such call for
+ * a polygon set (64 bytes per polygon of up to 256 vertices) and kept with it.
+ * Without this flag the signing kernels for polygons of up to 256 vertices
+ * build a 32 x 32 mask in shared memory themselves; with it, those polygons that
+ * take the walk form use the precomputed mask instead. */
 #define PMH_FLAG_COVERAGE_MASK 2u
 
 typedef struct {
@@ -112,7 +116,8 @@ int pmh_destroy(pmh_ctx ctx);
 /* A0 -- upload polygons (Sec. 3.1 preprocessing: local MBRs).
  * Copies n_polys polygons into library-owned device memory and computes each
  * polygon's half-open bounding box clipped to the domain, twice its signed
- * area (exact int64 shoelace) and a work estimate.
+ * area (exact int64 shoelace), its signing plan (indexed or walk form, grid
+ * level) and the order in which the signing kernels take the polygons.
  *   d_xy       int32 [n_vertices][2], interleaved (x, y), device
  *   d_offsets  int64 [n_polys + 1], offsets[0] = 0, offsets[n_polys] =
  *              n_vertices, polygon p = vertices offsets[p] .. offsets[p+1]-1
