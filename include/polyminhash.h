@@ -73,7 +73,7 @@ typedef struct pmh_index_s* pmh_index;
 /* pmh_params.flags: sign through the stream index (same hashes, much less
  * work for small polygons).  The first call with a given (seed, K) builds the
  * index of the first 65,536 / 32,768 / 8,192 points of each stream, bucketed by
- * cell of a 128 x 128 / 64 x 64 / 32 x 32 grid (about K * 840 KiB of device
+ * cell of a 128 x 128 / 64 x 64 / 32 x 32 grid (about K * 1 MiB of device
  * memory, kept by the context; that call synchronises); later calls reuse it.
  * Each polygon's form (index or walk) and grid level are planned at upload from
  * its box and area. */
