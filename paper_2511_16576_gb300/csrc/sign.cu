@@ -24,6 +24,14 @@
 // SM count) in decreasing order of expected cost (2^32 / area per hash,
 // Theorem 2: E[h] = 1/S_p), which balances polygons whose work differs by
 // orders of magnitude.
+//
+// Which kernel signs which polygon: with the stream index, the polygons of at
+// most 256 vertices are planned at upload and signed by sign_indexed_kernel
+// (indexed form) and sign_walk_staged_kernel (walk form, sign_indexed.cu); this
+// file's sign_kernel takes the larger polygons (walk, or the indexed form of the
+// fine level through their slab index) and, without the stream index or with
+// precomputed coverage masks, every polygon.  pmh_launch_sign runs the kernels
+// one after the other on the caller's stream.
 #include <algorithm>
 #include <mutex>
 
