@@ -353,12 +353,18 @@ int pmh_rerank_adam_step(pmh_rerank r, float lr, float beta1, float beta2, float
  * PMH_NOALLOC_MAX_POLYS + 1 16-byte entries (4 MiB) that every GPU loading
  * the library holds until the process exits; n_polys above
  * PMH_NOALLOC_MAX_POLYS is rejected with PMH_ERR_RANGE before any GPU work.
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  Every call
- * shares the one array and clears its ticket and flags itself, so calls that
- * overlap on the GPU (two streams, two threads) race: serialise them.
- * Synchronises `stream` once to report validation failures, like
- * pmh_poly_upload, with the same error codes. */
+ * d_xy, d_offsets and d_hashes must be device (or managed) memory of the
+ * current device; host pointers and other GPUs' memory are refused with
+ * PMH_ERR_ARG before anything is launched.
+ * The first call on a device looks up the array's device address, once per
+ * device, and keeps it for the life of the process: after a
+ * cudaDeviceReset of that device the kept address is stale, so do not use
+ * this entry point across a device reset.  Every call shares the one array
+ * and clears its ticket and flags itself, so calls that overlap on the GPU
+ * (two streams, two threads) race: serialise them.  Every call synchronises
+ * `stream` once to read the validation word (the same error codes as
+ * pmh_poly_upload), so the entry point cannot be called while `stream` is
+ * being captured into a CUDA graph. */
 #define PMH_NOALLOC_MAX_POLYS 262144
 int pmh_minhash_sign_noalloc(const int32_t* d_xy, const int64_t* d_offsets, int64_t n_polys,
                              int64_t n_vertices, const pmh_params* params, uint32_t* d_hashes,

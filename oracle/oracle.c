@@ -8,7 +8,7 @@
  * Paper: "PolyMinHash: Efficient Area-Based MinHashing of Polygons for
  * Approximate Nearest Neighbor Search" (arXiv 2511.16576).
  *
- * Readings of the paper taken here (each is listed in the design notes):
+ * Readings of the paper taken where it is silent or ambiguous:
  *  R1  random points: the paper only asks for seeded uniform sampling over the
  *      global MBR (Sec. 3.2).  Stream k is the SplitMix64 generator (Steele, Lea
  *      & Flood, OOPSLA 2014) seeded with s_k, the (k+1)-th SplitMix64 output of

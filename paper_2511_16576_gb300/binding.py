@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpolyminhash.so")
 _lib = None
 
 PMH_OK = 0
+PMH_ERR_ARG = -1
 PMH_ERR_CAPACITY = -3
 INVALID_KEY = 0xFFFFFFFFFFFFFFFF
 
@@ -255,14 +256,33 @@ def minhash_sign_noalloc(xy: torch.Tensor, offsets: torch.Tensor, params: Params
 
     The library allocates nothing for this call (its scratch is a fixed device array of
     NOALLOC_MAX_POLYS bounding boxes); `out` is allocated here by torch only when the caller
-    does not pass one.  Calls that overlap on the GPU share that array and race.
+    does not pass one.  Calls that overlap on the GPU share that array and race.  The
+    arrays must be contiguous CUDA tensors on one device (xy int32 [V, 2], offsets int64
+    [N + 1], out int32 with at least N * K elements); the call runs on that device and, by
+    default, on its current stream.
     """
-    assert xy.dtype == torch.int32 and offsets.dtype == torch.int64
+    if not (isinstance(xy, torch.Tensor) and isinstance(offsets, torch.Tensor)):
+        raise PmhError(PMH_ERR_ARG, "xy and offsets must be torch tensors")
+    if xy.dtype != torch.int32 or offsets.dtype != torch.int64:
+        raise PmhError(PMH_ERR_ARG, "xy must be int32 and offsets int64")
+    if xy.dim() != 2 or xy.shape[1] != 2 or offsets.dim() != 1 or offsets.numel() < 1:
+        raise PmhError(PMH_ERR_ARG, "xy must be [V, 2] and offsets [N + 1]")
+    arrays = [xy, offsets] + ([out] if out is not None else [])
+    if not all(a.is_cuda for a in arrays):
+        raise PmhError(PMH_ERR_ARG, "xy, offsets and out must be CUDA tensors")
+    if len({a.device for a in arrays}) != 1:
+        raise PmhError(PMH_ERR_ARG, "xy, offsets and out must be on one device")
+    if not all(a.is_contiguous() for a in arrays):
+        raise PmhError(PMH_ERR_ARG, "xy, offsets and out must be contiguous")
     n = offsets.numel() - 1
-    if out is None:
-        out = torch.empty((n, params.K), dtype=torch.int32, device=xy.device)
-    _check(load().pmh_minhash_sign_noalloc(_ptr(xy), _ptr(offsets), n, xy.shape[0],
-                                           ctypes.byref(params), _ptr(out), _stream(stream)))
+    if out is not None and (out.dtype != torch.int32 or out.numel() < n * params.K):
+        raise PmhError(PMH_ERR_ARG, f"out must be int32 with at least {n * params.K} elements")
+    with torch.cuda.device(xy.device):
+        if out is None:
+            out = torch.empty((n, params.K), dtype=torch.int32, device=xy.device)
+        s = (stream if stream is not None else torch.cuda.current_stream(xy.device)).cuda_stream
+        _check(load().pmh_minhash_sign_noalloc(_ptr(xy), _ptr(offsets), n, xy.shape[0],
+                                               ctypes.byref(params), _ptr(out), s))
     return out
 
 

@@ -634,6 +634,25 @@ extern "C" int pmh_minhash_sign_noalloc(const int32_t* d_xy, const int64_t* d_of
     int dev = 0;
     PMH_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return pmh_set_error(PMH_ERR_ARG, "device %d out of range", dev);
+    // every array must be device (or managed) memory of the current device: a host
+    // pointer, or memory of another GPU, is refused before anything is launched
+    {
+        const void* arrays[3] = {d_xy, d_offsets, d_hashes};
+        const char* names[3] = {"d_xy", "d_offsets", "d_hashes"};
+        for (int a = 0; a < 3; ++a) {
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, arrays[a]) != cudaSuccess) {
+                cudaGetLastError();
+                return pmh_set_error(PMH_ERR_ARG, "%s is not a CUDA pointer", names[a]);
+            }
+            const bool on_device = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+            if (!on_device || (at.type == cudaMemoryTypeDevice && at.device != dev))
+                return pmh_set_error(PMH_ERR_ARG,
+                                     "%s must be device memory of the current device %d "
+                                     "(memory type %d, device %d)",
+                                     names[a], dev, (int)at.type, at.device);
+        }
+    }
     NoallocDevice nd;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
