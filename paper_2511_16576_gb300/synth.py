@@ -21,6 +21,10 @@ in for them with the shapes the workloads name:
   done here, at generation time, so that both sides receive the same lattice
   polygons; the hashing itself (Sec. 3.2 on) is not in this module.
 
+The per-vertex work (angles, radius profiles, rounding, the star-shape filter) runs
+in ``synth_gen.c`` on all host cores, with one PCG32 stream per polygon, so that a
+10,000,000-polygon set takes seconds; the per-polygon parameters are drawn here.
+
 Every polygon is rounded to int32 and then made strictly star-shaped around its
 (integer) centre by dropping any vertex v_i with (v_i - c) x (v_{i+1} - c) <= 0,
 which guarantees a simple polygon.  Layout: ``xy`` int32 [V, 2] interleaved,
@@ -28,12 +32,59 @@ which guarantees a simple polygon.  Layout: ``xy`` int32 [V, 2] interleaved,
 """
 from __future__ import annotations
 
+import ctypes
 import dataclasses
 import math
+import os
+import subprocess
+import threading
 
 import numpy as np
 
 DOMAIN = 65536
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_GEN_SRC = os.path.join(_HERE, "synth_gen.c")
+_GEN_LIB = os.path.join(_HERE, "_build", "libsynthgen.so")
+_gen_lock = threading.Lock()
+_gen = None
+
+
+def build_generator(force: bool = False) -> str:
+    """Compile the per-vertex generator (synth_gen.c, plain gcc) into _build/."""
+    os.makedirs(os.path.dirname(_GEN_LIB), exist_ok=True)
+    if force or not os.path.exists(_GEN_LIB) or \
+            os.path.getmtime(_GEN_LIB) < os.path.getmtime(_GEN_SRC):
+        tmp = _GEN_LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _GEN_SRC,
+                               "-lpthread", "-lm"])
+        os.replace(tmp, _GEN_LIB)
+    return _GEN_LIB
+
+
+def _lib():
+    global _gen
+    with _gen_lock:
+        if _gen is None:
+            lib = ctypes.CDLL(build_generator())
+            P, i64 = ctypes.c_void_p, ctypes.c_int64
+            lib.sg_star_vertices.argtypes = [i64, P, P, P, P, P, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_uint64, ctypes.c_int, P]
+            lib.sg_star_vertices.restype = None
+            lib.sg_star_filter.argtypes = [i64, P, P, P, P, P, ctypes.c_int, P]
+            lib.sg_star_filter.restype = None
+            lib.sg_compact.argtypes = [i64, P, P, P]
+            lib.sg_compact.restype = None
+            _gen = lib
+        return _gen
+
+
+def _threads() -> int:
+    return max(1, min(64, os.cpu_count() or 1))
+
+
+def _c(a: np.ndarray, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
 
 
 @dataclasses.dataclass
@@ -66,105 +117,38 @@ class PolySet:
                        None if self.source is None else self.source[ids])
 
 
-def _group_starts(pid: np.ndarray) -> np.ndarray:
-    """For a sorted group-id array, the index of the first element of each element's group."""
-    n = len(pid)
-    first = np.ones(n, bool)
-    first[1:] = pid[1:] != pid[:-1]
-    starts = np.nonzero(first)[0]
-    return starts[np.cumsum(first) - 1]
+def _filter_and_pack(xy: np.ndarray, offs0: np.ndarray, cx: np.ndarray, cy: np.ndarray,
+                     rbar: np.ndarray):
+    """Star-shape filter of every polygon in place (synth_gen.c), then pack the kept
+    vertices: returns (xy [V', 2] int32, offsets [N + 1] int64)."""
+    n_polys = len(offs0) - 1
+    lib = _lib()
+    cx, cy, rbar = _c(cx, np.int64), _c(cy, np.int64), _c(rbar, np.float64)
+    kept = np.zeros(n_polys, np.int64)
+    lib.sg_star_filter(n_polys, offs0.ctypes.data, xy.ctypes.data, cx.ctypes.data, cy.ctypes.data,
+                       rbar.ctypes.data, _threads(), kept.ctypes.data)
+    offs = np.zeros(n_polys + 1, np.int64)
+    np.cumsum(kept, out=offs[1:])
+    lib.sg_compact(n_polys, offs0.ctypes.data, offs.ctypes.data, xy.ctypes.data)
+    return xy[:offs[-1]], offs
 
 
 def _make_star_shaped(x: np.ndarray, y: np.ndarray, pid: np.ndarray, cx: np.ndarray,
                       cy: np.ndarray, n_polys: int, rbar: np.ndarray):
-    """Drop vertices until every edge turns strictly counter-clockwise around c."""
-    keep = np.ones(len(x), bool)
-    active = np.ones(len(x), bool)   # vertices of polygons that may still change
-    while True:
-        idx = np.nonzero(keep & active)[0]
-        if len(idx) == 0:
-            break
-        p = pid[idx]
-        start = _group_starts(p)
-        nxt = np.arange(len(idx)) + 1
-        last = np.ones(len(idx), bool)
-        last[:-1] = p[1:] != p[:-1]
-        nxt[last] = start[last]
-        ax = x[idx] - cx[p]
-        ay = y[idx] - cy[p]
-        bx = x[idx[nxt]] - cx[p]
-        by = y[idx[nxt]] - cy[p]
-        cross = ax * by - bx * ay
-        bad = cross <= 0
-        if not bad.any():
-            break
-        keep[idx[bad]] = False
-        changed = np.zeros(n_polys, bool)
-        changed[p[bad]] = True
-        active = changed[pid]
-    # polygons left with fewer than 3 vertices become a triangle around c
-    counts = np.bincount(pid[keep], minlength=n_polys)
-    small = np.nonzero(counts < 3)[0]
-    xs, ys, ps = [x[keep]], [y[keep]], [pid[keep]]
-    if len(small):
-        keep_small = np.isin(pid, small) & keep
-        xs, ys, ps = [x[keep & ~keep_small]], [y[keep & ~keep_small]], [pid[keep & ~keep_small]]
-        ang = np.array([0.0, 2 * math.pi / 3, 4 * math.pi / 3])
-        for s in small:
-            r = max(2.0, rbar[s])
-            tx = np.rint(cx[s] + r * np.cos(ang)).astype(np.int64)
-            ty = np.rint(cy[s] + r * np.sin(ang)).astype(np.int64)
-            xs.append(tx)
-            ys.append(ty)
-            ps.append(np.full(3, s, np.int64))
-    x = np.concatenate(xs)
-    y = np.concatenate(ys)
-    p = np.concatenate(ps)
-    order = np.argsort(p, kind="stable")
-    x, y, p = x[order], y[order], p[order]
-    offs = np.zeros(n_polys + 1, np.int64)
-    np.cumsum(np.bincount(p, minlength=n_polys), out=offs[1:])
+    """Drop vertices until every edge turns strictly counter-clockwise around c.
+
+    x, y: vertex coordinates grouped by polygon (pid sorted); polygons left with fewer
+    than 3 vertices become a triangle around c."""
+    offs0 = np.zeros(n_polys + 1, np.int64)
+    np.cumsum(np.bincount(pid, minlength=n_polys), out=offs0[1:])
     xy = np.empty((len(x), 2), np.int32)
     xy[:, 0] = x
     xy[:, 1] = y
-    return xy, offs
+    return _filter_and_pack(xy, offs0, cx, cy, rbar)
 
 
 def _loguniform(rng, lo, hi, size):
     return np.exp(rng.uniform(math.log(lo), math.log(hi), size))
-
-
-def _fractal_radius(rng, pid: np.ndarray, pos: np.ndarray, n: np.ndarray, amp0: float = 0.25,
-                    decay: float = 0.6) -> np.ndarray:
-    """Midpoint-displacement radius profile r(t) on t in [0,1), amplitude x decay per level.
-
-    Level l adds 2^l periodic control offsets; a vertex takes the linear interpolation of
-    each level's controls at its angle, so the sum is a periodic fractal profile.  A
-    polygon only receives the levels its own vertex count can resolve (2^l <= 2n).
-    """
-    t = pos / n[pid]
-    r = np.ones(len(pid))
-    levels = int(math.ceil(math.log2(max(int(n.max()), 2)))) + 1
-    amp = amp0
-    for lev in range(2, levels + 1):
-        m = 1 << lev
-        elig = np.nonzero(2 * n >= m)[0]
-        if len(elig) == 0:
-            break
-        row = np.full(len(n), -1, np.int64)
-        row[elig] = np.arange(len(elig))
-        ctrl = rng.uniform(-amp, amp, size=(len(elig), m))
-        sel = row[pid] >= 0
-        u = t[sel] * m
-        i0 = np.floor(u).astype(np.int64) % m
-        w = u - np.floor(u)
-        i1 = (i0 + 1) % m
-        rr = row[pid[sel]]
-        r[sel] += (1 - w) * ctrl[rr, i0] + w * ctrl[rr, i1]
-        amp *= decay
-        if amp < 1e-4:
-            break
-    return np.clip(r, 0.3, 1.6)
 
 
 def star_polygons(n_polys: int, seed: int, n_range=(8, 64), n_dist: str = "uniform",
@@ -197,37 +181,15 @@ def star_polygons(n_polys: int, seed: int, n_range=(8, 64), n_dist: str = "unifo
     margin = np.ceil(1.6 * rbar) + 2
     cx = np.rint(rng.uniform(margin, DOMAIN - margin)).astype(np.int64)
     cy = np.rint(rng.uniform(margin, DOMAIN - margin)).astype(np.int64)
-    V = int(n.sum())
-    pid = np.repeat(np.arange(n_polys, dtype=np.int64), n)
     offs0 = np.zeros(n_polys + 1, np.int64)
     np.cumsum(n, out=offs0[1:])
-    pos = np.arange(V, dtype=np.int64) - offs0[pid]
-    if fractal:
-        # equally spaced angles with a small jitter; radius from the fractal profile
-        ang = (pos + rng.uniform(0.1, 0.9, V)) * (2 * math.pi) / n[pid]
-        rad = rbar[pid] * _fractal_radius(rng, pid, pos.astype(np.float64), n.astype(np.float64))
-    else:
-        ang = rng.uniform(0.0, 2 * math.pi, V)
-        # sort angles within each polygon
-        order = np.lexsort((ang, pid))
-        ang = ang[order]
-        # a cyclic angular gap of pi or more would leave the centre outside the polygon;
-        # such polygons (rare for n >= 8) take stratified angles instead
-        nxt_ang = np.empty_like(ang)
-        nxt_ang[:-1] = ang[1:]
-        nxt_ang[offs0[1:] - 1] = ang[offs0[:-1]] + 2 * math.pi
-        gap = nxt_ang - ang
-        wide = np.zeros(n_polys, bool)
-        wide[pid[gap > 0.75 * math.pi]] = True
-        if wide.any():
-            sel = wide[pid]
-            ang[sel] = (pos[sel] + rng.uniform(0.0, 1.0, int(sel.sum()))) * (2 * math.pi) / n[pid[sel]]
-        rad = rbar[pid] * rng.uniform(1.0 - jitter, 1.0 + jitter, V)
-    x = np.rint(cx[pid] + rad * np.cos(ang)).astype(np.int64)
-    y = np.rint(cy[pid] + rad * np.sin(ang)).astype(np.int64)
-    np.clip(x, 0, DOMAIN, out=x)
-    np.clip(y, 0, DOMAIN, out=y)
-    xy, offs = _make_star_shaped(x, y, pid, cx, cy, n_polys, rbar)
+    # per-vertex work in C, one PCG32 stream per polygon seeded from this generator
+    vseed = int(rng.integers(0, 1 << 63))
+    xy = np.empty((int(offs0[-1]), 2), np.int32)
+    _lib().sg_star_vertices(n_polys, n.ctypes.data, offs0.ctypes.data, cx.ctypes.data,
+                            cy.ctypes.data, rbar.ctypes.data, float(jitter), int(fractal), vseed,
+                            _threads(), xy.ctypes.data)
+    xy, offs = _filter_and_pack(xy, offs0, cx, cy, rbar)
     centre = np.stack([cx, cy], axis=1)
     return PolySet(xy, offs, centre, rbar)
 
