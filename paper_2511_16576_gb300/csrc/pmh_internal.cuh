@@ -55,14 +55,25 @@ enum ScratchSlot {
 };
 
 // first kStreamIndexPoints points of every hash's stream, bucketed by cell of a
-// 2^kStreamGridBits-square grid (stream_index.cu); coarser levels hold fewer
-// points on coarser grids (level l: 2^index_level_gbits(l) cells per side, the
-// first index_level_points(l) points)
+// 2^kStreamGridBits-square grid (stream_index.cu); the other levels hold fewer
+// points on coarser grids or more points on a finer one (level l:
+// 2^index_level_gbits(l) cells per side, the first index_level_points(l)
+// points): 65,536 on 128^2, 32,768 on 64^2, 8,192 on 32^2 and 2^20 on 512^2
+// (about four points per (cell, hash) list on levels 0 and 3, eight on 1 and 2)
 constexpr int kStreamGridBits = 7;
 constexpr int kStreamIndexPoints = 65536;
-constexpr int kIndexLevels = 3;
-__host__ __device__ constexpr int index_level_gbits(int l) { return l == 0 ? 7 : l == 1 ? 6 : 5; }
-__host__ __device__ constexpr int index_level_points(int l) { return l == 0 ? 65536 : l == 1 ? 32768 : 8192; }
+constexpr int kIndexLevels = 4;
+constexpr int kIndexMaxPoints = 1 << 20;  // the deepest level
+__host__ __device__ constexpr int index_level_gbits(int l) { return l == 0 ? 7 : l == 1 ? 6 : l == 2 ? 5 : 9; }
+__host__ __device__ constexpr int index_level_points(int l)
+{
+    return l == 0 ? 65536 : l == 1 ? 32768 : l == 2 ? 8192 : kIndexMaxPoints;
+}
+// a level is built only if its entry offsets (K * points) fit in 31 bits
+__host__ __device__ constexpr bool index_level_fits(int l, int K)
+{
+    return (long long)K * index_level_points(l) <= (1ll << 31);
+}
 // polygons of at most this many vertices are staged in shared memory by the
 // signing kernels; larger ones are read through their y-slab edge index
 constexpr int kStagedMaxVerts = 256;
@@ -132,7 +143,7 @@ __host__ __device__ __forceinline__ PmhIndexPlan pmh_index_plan(int4 bb, long lo
     if (bb.z <= bb.x || bb.w <= bb.y) return plan;
     const float area = 0.5f * (float)(area2 < 0 ? -area2 : area2);
     const float walk = 4294967296.0f / fmaxf(area, 1.0f);
-    const float lim = fminf((float)kStreamIndexPoints, 8.0f * walk + 256.0f);
+    const float lim = fminf((float)kIndexMaxPoints, 8.0f * walk + 256.0f);
     const float cand = lim * ((float)(bb.z - bb.x) * (float)(bb.w - bb.y) * (1.0f / 4294967296.0f));
     if (cand > 24.0f) return plan;
     const uint32_t L = (uint32_t)lim, L1 = (uint32_t)fminf(lim, 2.5f * walk + 64.0f);

@@ -29,7 +29,10 @@
 
 namespace {
 
-static_assert(kStreamIndexPoints <= 65536, "point indices are packed in 16 bits");
+// a kept point is packed as (hash within the group << 20 | stream index)
+constexpr int kIdxBits = 20;
+constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
+static_assert(kIndexMaxPoints <= (1 << kIdxBits), "point indices are packed in 20 bits");
 
 constexpr int kIdxWarps = 4;      // warps per block
 constexpr int kIdxMinBlocks = 8;  // resident blocks per SM the registers are sized for
@@ -47,7 +50,7 @@ struct IdxWarp {
     uint32_t bnd[kMaskN];    // bit i of row j: an edge touches cell (i, j)
     uint32_t inb[kMaskN];    // bit i of row j: untouched cell (i, j) lies inside
     uint32_t best[kSub];     // per hash: smallest inside index found
-    uint2 pool[kPool];       // (hash << 16 | index, x | y << 16)
+    uint2 pool[kPool];       // (hash << 20 | index, x | y << 16)
     uint2 queue[kQueue];
     int npool;
     uint32_t ovf;            // bit j: hash j lost kept points
@@ -177,8 +180,8 @@ __device__ __forceinline__ void exact_batch(IdxWarp& m, int count, const StagedE
 {
     if (lane < count) {
         const uint2 c = m.queue[lane];
-        const int kl = (int)(c.x >> 16);
-        const uint32_t idx = c.x & 0xFFFFu;
+        const int kl = (int)(c.x >> kIdxBits);
+        const uint32_t idx = c.x & kIdxMask;
         if (idx < m.best[kl] && st.lane_inside((int)(c.y & 0xFFFFu), (int)(c.y >> 16), work))
             atomicMin(&m.best[kl], idx);
     }
@@ -213,10 +216,12 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
         const int4 bb = bbox[p];
         const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
         const PmhIndexPlan plan = pmh_index_plan(bb, area2[p]);
-        const uint32_t lim = min(plan.lim, T);
-        // grid level of the plan (coarser ones for boxes that span many fine cells)
+        uint32_t lim = min(plan.lim, T);
+        // grid level of the plan (coarser ones for boxes that span many fine cells, the
+        // deep level for long walks); level 0 if that level is not built
         const IndexLevelView& L =
             S.lv[S.lv[plan.level].ranked && lim <= (uint32_t)S.lv[plan.level].M ? plan.level : 0];
+        lim = min(lim, (uint32_t)L.M);  // every point below lim is in the level's lists
         const uint2* cells = L.cell;
         const uint2* ents = L.ent;
         const int gb = L.gbits, shf = L.shift;
@@ -315,7 +320,7 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                                 const int i = (int)(dx >> cwl), j = (int)(dy >> chl);
                                 if ((m.bnd[j] >> i) & 1u) {
                                     const int slot = atomicAdd(&m.npool, 1);
-                                    if (slot < kPool) m.pool[slot] = make_uint2(((uint32_t)o_hl << 16) | q.x, r);
+                                    if (slot < kPool) m.pool[slot] = make_uint2(((uint32_t)o_hl << kIdxBits) | q.x, r);
                                     else atomicOr(&m.ovf, 1u << o_hl);
                                 } else {
                                     ++lane_masked;
@@ -335,7 +340,7 @@ sign_indexed_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
                     bool keep = false;
                     if (t < np) {
                         c = m.pool[t];
-                        keep = (c.x & 0xFFFFu) < m.best[c.x >> 16];
+                        keep = (c.x & kIdxMask) < m.best[c.x >> kIdxBits];
                     }
                     const unsigned bal = __ballot_sync(full, keep);
                     if (keep) m.queue[nq + __popc(bal & pmh_lanemask_lt())] = c;

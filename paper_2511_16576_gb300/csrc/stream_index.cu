@@ -202,8 +202,9 @@ int pmh_stream_index_get(pmh_ctx ctx, const pmh_params* P, cudaStream_t s, Strea
     StreamIndex fresh;
     int rc = PMH_OK;
     for (int l = 0; l < kIndexLevels && rc == PMH_OK; ++l)
-        rc = build_level(ctx, P, s, index_level_points(l), index_level_gbits(l), &fresh.cell[l],
-                         &fresh.ent[l], &fresh.ranked[l]);
+        if (l == 0 || index_level_fits(l, (int)P->K))  // level 0 always fits (K <= 4096)
+            rc = build_level(ctx, P, s, index_level_points(l), index_level_gbits(l), &fresh.cell[l],
+                             &fresh.ent[l], &fresh.ranked[l]);
     if (rc != PMH_OK) {
         free_index(fresh);
         return rc;

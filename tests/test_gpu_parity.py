@@ -199,6 +199,31 @@ def test_sign_scale_workload_sampled(B, ctx, orc, scale_db, flags):
     assert int(torch.max(h.view(torch.int32))) < w.T
 
 
+def test_sign_combined_workload_sampled(B, ctx, orc):
+    """The 10,000,000-polygon, K = 128 workload (8-1,024 vertices, area fractions down to
+    1e-5, whose walks run past the shallow index levels into the deep one) in the
+    benchmark's launch: sampled rows of every size class bit-exact, and every hash below
+    the cap."""
+    w = synth.WORKLOADS["combined"]
+    db = synth.make_database(w)
+    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed, B.FLAG_STREAM_INDEX)
+    dbp = upload(B, ctx, db)
+    h = B.minhash_sign(ctx, dbp, P)
+    n = np.diff(db.offsets)
+    rng = np.random.default_rng(3)
+    # rows of each class: the smallest polygons (deep index level), staged ones, large ones
+    order = np.argsort(n, kind="stable")
+    rows = np.concatenate([order[:16], rng.choice(db.n, 32, replace=False), order[-16:],
+                           [0, db.n - 1]])
+    rows = np.unique(rows)
+    sub = db.subset(rows)
+    ref = orc.sign(sub.xy, sub.offsets, w.seed, w.K, w.T, nthreads=16)
+    assert np.array_equal(u32(h[torch.from_numpy(rows).to(DEV)]), ref)
+    assert int(torch.max(h.view(torch.int32))) < w.T
+    dbp.close()
+    del h
+
+
 def test_band_keys_bit_exact(B, ctx, orc):
     rng = np.random.default_rng(3)
     for K, b in ((32, 8), (128, 16), (256, 32), (128, 128)):
