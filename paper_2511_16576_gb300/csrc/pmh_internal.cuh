@@ -151,6 +151,8 @@ __host__ __device__ __forceinline__ PmhIndexPlan pmh_index_plan(int4 bb, long lo
     int level = 0;
     for (int l = 0; l < kIndexLevels; ++l) {
         if (L > (uint32_t)index_level_points(l)) continue;
+        // the deep level (larger than L2) only for limits the L2-resident levels cannot hold
+        if (index_level_points(l) > kStreamIndexPoints && L <= (uint32_t)kStreamIndexPoints) continue;
         const float c = pmh_level_cost(bb, L1, index_level_points(l), 16 - index_level_gbits(l));
         if (c < best) {
             best = c;
