@@ -535,7 +535,7 @@ def main():
     dbp_w.close()
     peak = B.probe_int_peak(ctx)
     kernels = {}
-    for name, kname in (("indexed", "sign_indexed_kernel"), ("walk", "sign_kernel")):
+    for name, kname in (("unified", "sign_unified_kernel"), ("walk", "sign_kernel")):
         units = per_kernel[name]["work"]
         ops = sum(SIGN_OP_WEIGHTS[k] * v for k, v in units.items())
         kms = kernel_ms[name]["ms"]
@@ -546,7 +546,7 @@ def main():
     # DRAM bytes (read + write) of one sign_indexed_kernel launch from an ncu capture on
     # the 200,000-polygon slice of this workload (399.3 MB), scaled by polygons to the
     # 1,000,000-polygon launch; other sizes and kernels: not measured
-    traffic = 5 * 399.3e6 if dom == "sign_indexed_kernel" and N == 1000000 and w.name == "scale" else None
+    traffic = 5 * 399.3e6 if dom == "sign_unified_kernel" and N == 1000000 and w.name == "scale" else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": kernels[dom]["achieved"],
                 "peak": peak / 1e12, "unit": "Tintop/s", "frac": kernels[dom]["frac"],
                 "traffic": traffic, "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum "

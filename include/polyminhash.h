@@ -167,18 +167,20 @@ int pmh_stream_index_build(pmh_ctx ctx, const pmh_params* params, void* stream);
  * (h_counts holds 6 values). */
 int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts);
 
-/* Measurement support (no counterpart in the paper).  pmh_minhash_sign runs
- * two kernels: the indexed form of the polygons staged in shared memory, then
- * the walk (and the indexed form of larger polygons) for the rest.
+/* Measurement support (no counterpart in the paper).  With the stream index,
+ * pmh_minhash_sign signs every polygon in one persistent launch (the unified
+ * kernel: indexed or walk form per polygon); without it, or with
+ * PMH_FLAG_COVERAGE_MASK, it runs the walk kernel over every polygon.
  * pmh_sign_timing(ctx, 1) makes later signing calls on this context record
- * CUDA events before, between and after the two kernels on the caller's
- * stream, without synchronising (0 stops it; at most 1024 calls are kept).
+ * CUDA events around each of the two on the caller's stream, without
+ * synchronising (0 stops it; at most 1024 calls are kept).
  * pmh_sign_report (synchronises) returns h_ms[0] / h_ms[1] = mean
- * milliseconds of the indexed / walk kernel over the calls recorded since the
- * previous report, h_ms[2] = their number (h_ms holds 3 floats; NULL: skip;
- * the recorded calls are then forgotten), and h_counts[0..5] / [6..11] = the
- * six work counts of pmh_sign_work for each kernel alone in the last signing
- * call (NULL: skip).  Errors: PMH_ERR_ARG (null context), PMH_ERR_CUDA. */
+ * milliseconds of the unified / walk kernel over the calls recorded since
+ * the previous report (0 for a kernel the calls did not run), h_ms[2] =
+ * their number (h_ms holds 3 floats; NULL: skip; the recorded calls are then
+ * forgotten), and h_counts[0..5] / [6..11] = the six work counts of
+ * pmh_sign_work for each kernel alone in the last signing call (NULL: skip).
+ * Errors: PMH_ERR_ARG (null context), PMH_ERR_CUDA. */
 int pmh_sign_timing(pmh_ctx ctx, int enable);
 int pmh_sign_report(pmh_ctx ctx, float* h_ms, uint64_t* h_counts);
 
@@ -271,32 +273,44 @@ int pmh_sign_variant_info(int variant, int* points_per_lane, int* warps_per_bloc
 
 /* A9 -- batching: the query pipeline as one CUDA graph.
  * pmh_qgraph_create captures, on buffers the graph owns, the chain
- * A0 prep -> A1 sign -> A4 join -> A5 agreement -> A6 top-m (m per query) for
- * batches of at most max_queries polygons holding at most max_vertices
- * vertices, against `index` (which must outlive the graph).  The signing
- * variant in force in ctx is baked in.
+ * A0 prep -> y-slab lists of the polygons above 256 vertices -> A1 sign (one
+ * launch of the unified kernel: through the stream index when the index's
+ * params carry PMH_FLAG_STREAM_INDEX, which this call builds if needed and
+ * which must not be rebuilt for other parameters while the graph lives) ->
+ * A4 join -> A5 agreement -> A6 top-m (m per query) and, if k > 0, A8 exact
+ * refinement of the top-m lists to the top-k by (J desc, id asc) against the
+ * polygon set `db` (which, like `index`, must outlive the graph), for batches
+ * of at most max_queries polygons holding at most max_vertices vertices.  The
+ * slab lists get fixed buffers (a table entry per slab, four list entries per
+ * vertex); a polygon whose lists do not fit is tested over all its edges.
+ * Synchronises; 0 <= k <= m <= 1024.
  * pmh_qgraph_run copies one batch (xy int32 [n_vertices][2], offsets int64
  * [n_queries + 1], HOST arrays if host_memory != 0, else device) into the
  * graph's inputs and replays the graph on `stream`: it neither allocates nor
- * synchronises.  Batches beyond the graph's sizes fail with PMH_ERR_RANGE.
+ * synchronises.  Batches beyond the graph's sizes fail with PMH_ERR_RANGE; a
+ * stream index rebuilt since the capture fails with PMH_ERR_STATE.
  * pmh_qgraph_outputs returns device pointers (owned by the graph, valid until
  * pmh_qgraph_destroy, rewritten by every run): hashes uint32 [max_queries][K],
  * row_ptr int64 [max_queries + 1], cand int32 [cand_capacity], count uint16
  * [cand_capacity], top_ids int32 [max_queries][m] (-1 padded), top_n int32
- * [max_queries]; rows past the batch are empty.
+ * [max_queries]; rows past the batch are empty.  pmh_qgraph_refined returns
+ * the refined top-k (int32 ids [max_queries][k], -1 padded; fp64 J, -1 in
+ * empty slots; rows past the batch are not written), PMH_ERR_STATE if k == 0.
  * pmh_qgraph_status synchronises `stream` and reports the last run's status
  * bits (1, 2, 4: invalid polygons -- offsets, fewer than 3 vertices,
  * coordinate range -- nothing computed; 8: more candidates than
- * cand_capacity, rows not written, agreement and top-m skipped) and its
- * candidate total. */
+ * cand_capacity, rows not written, agreement, top-m and refinement skipped)
+ * and its candidate total. */
 typedef struct pmh_qgraph_s* pmh_qgraph;
-int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, int64_t max_queries, int64_t max_vertices,
-                      int64_t cand_capacity, int32_t m, pmh_qgraph* out);
+int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, pmh_polys db, int64_t max_queries,
+                      int64_t max_vertices, int64_t cand_capacity, int32_t m, int32_t k,
+                      pmh_qgraph* out);
 int pmh_qgraph_run(pmh_qgraph graph, const int32_t* xy, const int64_t* offsets, int64_t n_queries,
                    int64_t n_vertices, int host_memory, void* stream);
 int pmh_qgraph_outputs(pmh_qgraph graph, uint32_t** d_hashes, int64_t** d_row_ptr,
                        int32_t** d_cand, uint16_t** d_count, int32_t** d_top_ids,
                        int32_t** d_top_n);
+int pmh_qgraph_refined(pmh_qgraph graph, int32_t** d_top_ids, double** d_top_j);
 int pmh_qgraph_status(pmh_qgraph graph, int* h_flags, int64_t* h_total, void* stream);
 int pmh_qgraph_destroy(pmh_qgraph graph);
 

@@ -84,7 +84,8 @@ _SIGS = {
     "pmh_sign_set_variant": (ctypes.c_int, [_P, ctypes.c_int]),
     "pmh_sign_variant_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_int)]),
-    "pmh_qgraph_create": (ctypes.c_int, [_P, _P, _i64, _i64, _i64, _i32, ctypes.POINTER(_P)]),
+    "pmh_qgraph_create": (ctypes.c_int, [_P, _P, _P, _i64, _i64, _i64, _i32, _i32, ctypes.POINTER(_P)]),
+    "pmh_qgraph_refined": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "pmh_qgraph_run": (ctypes.c_int, [_P, _P, _P, _i64, _i64, ctypes.c_int, _P]),
     "pmh_qgraph_outputs": (ctypes.c_int, [_P] + [ctypes.POINTER(_P)] * 6),
     "pmh_qgraph_status": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64), _P]),
@@ -305,7 +306,7 @@ WORK_KEYS = ("walk_points", "cells", "index_entries", "candidates", "edge_tests"
 
 
 def sign_timing(ctx: Context, enable: bool = True):
-    """Record per-kernel events in later signing calls (indexed kernel, walk kernel)."""
+    """Record per-kernel events in later signing calls (unified kernel, walk kernel)."""
     _check(load().pmh_sign_timing(ctx.handle, 1 if enable else 0))
 
 
@@ -317,7 +318,7 @@ def sign_report(ctx: Context) -> dict:
     c = np.zeros(12, np.uint64)
     _check(load().pmh_sign_report(ctx.handle, ms.ctypes.data, c.ctypes.data))
     return {"calls": int(ms[2]),
-            "indexed": {"ms": float(ms[0]), "work": dict(zip(WORK_KEYS, (int(v) for v in c[:6])))},
+            "unified": {"ms": float(ms[0]), "work": dict(zip(WORK_KEYS, (int(v) for v in c[:6])))},
             "walk": {"ms": float(ms[1]), "work": dict(zip(WORK_KEYS, (int(v) for v in c[6:])))}}
 
 
@@ -524,16 +525,19 @@ def _view(ptr, shape, typestr, device):
 
 
 class QueryGraph:
-    """A9: captured query pipeline (prep, sign, join, agreement, top-m) replayed per batch."""
+    """A9: captured query pipeline (prep, slab lists, sign, join, agreement, top-m and,
+    with a database polygon set and k > 0, exact refinement to the top-k) replayed per
+    batch."""
 
     def __init__(self, ctx: Context, index: Index, max_queries: int, max_vertices: int,
-                 cand_capacity: int, m: int):
+                 cand_capacity: int, m: int, db: "Polys | None" = None, k: int = 0):
         h = _P()
-        _check(load().pmh_qgraph_create(ctx.handle, index.handle, max_queries, max_vertices,
-                                        cand_capacity, m, ctypes.byref(h)))
-        self.ctx, self.index, self.handle = ctx, index, h
+        _check(load().pmh_qgraph_create(ctx.handle, index.handle, db.handle if db else None,
+                                        max_queries, max_vertices, cand_capacity, m, k,
+                                        ctypes.byref(h)))
+        self.ctx, self.index, self.db, self.handle = ctx, index, db, h
         ctx._adopt(self)
-        self.max_queries, self.m, self.K = max_queries, m, index.params.K
+        self.max_queries, self.m, self.k, self.K = max_queries, m, k, index.params.K
         ptrs = [_P() for _ in range(6)]
         _check(load().pmh_qgraph_outputs(h, *[ctypes.byref(p) for p in ptrs]))
         dev = torch.device("cuda", ctx.device)
@@ -544,6 +548,12 @@ class QueryGraph:
         self.count = _view(ptrs[3].value, (cand_capacity,), "<i2", dev)
         self.top_ids = _view(ptrs[4].value, (Q, m), "<i4", dev)
         self.top_n = _view(ptrs[5].value, (Q,), "<i4", dev)
+        self.ref_ids = self.ref_j = None
+        if k > 0:
+            ri, rj = _P(), _P()
+            _check(load().pmh_qgraph_refined(h, ctypes.byref(ri), ctypes.byref(rj)))
+            self.ref_ids = _view(ri.value, (Q, k), "<i4", dev)
+            self.ref_j = _view(rj.value, (Q, k), "<f8", dev)
 
     def run(self, xy, offsets, stream=None):
         """Replay on one batch: device tensors, or pinned/pageable CPU tensors / numpy arrays."""

@@ -1,15 +1,20 @@
 // graph.cu -- A9: the query pipeline captured once as a CUDA graph.
 //
 // For query batches of up to max_queries polygons (at most max_vertices
-// vertices in all), the steps prep (A0), sign (A1), bucket join (A4, count +
-// scan + fill), agreement (A5) and top-m (A6) are captured on fixed,
-// graph-owned buffers.  A replay copies the batch into the input buffers,
-// writes the batch size into a device word and launches the graph: no host
-// synchronisation, no allocation.  Data-dependent sizes stay on the device:
-// kernels read the batch size from the device word, the join writes its rows
-// only if the candidate total fits the capacity, and a device status word
-// records failures (bits 0-2 invalid polygons, bit 3 candidate overflow) which
-// make the later stages do nothing; pmh_qgraph_status reads it.
+// vertices in all), the steps prep (A0), y-slab edge lists of the polygons
+// above the staged size, sign (A1: one launch of the unified kernel, through
+// the stream index when the index's parameters ask for it), bucket join (A4,
+// count + scan + fill), agreement (A5), top-m (A6) and, with a database
+// polygon set, exact refinement of the top-m to the top-k (A8) are captured on
+// fixed, graph-owned buffers.  A replay copies the batch into the input
+// buffers, writes the batch size into a device word and launches the graph:
+// no host synchronisation, no allocation.  Data-dependent sizes stay on the
+// device: kernels read the batch size from the device word, the slab lists of
+// a polygon that does not fit the fixed buffers are left out (that polygon is
+// tested over all its edges), the join writes its rows only if the candidate
+// total fits the capacity, and a device status word records failures (bits
+// 0-2 invalid polygons, bit 3 candidate overflow) which make the later stages
+// do nothing; pmh_qgraph_status reads it.
 #include <algorithm>
 
 #include "pmh_internal.cuh"
@@ -18,24 +23,37 @@ struct pmh_qgraph_s {
     pmh_ctx ctx = nullptr;
     int device = 0;
     pmh_index index = nullptr;
+    pmh_polys db = nullptr;           // refinement target (nullptr: no refinement)
     pmh_params P{};
     int64_t maxQ = 0, maxV = 0, cap = 0;
-    int m = 0;
+    int m = 0, k = 0;
     int2* xy = nullptr;
     int64_t* off = nullptr;
     int4* bbox = nullptr;
     int64_t* area2 = nullptr;
     uint32_t* hashes = nullptr;
+    SlabInfo* slab_info = nullptr;    // y-slab lists of the batch's large polygons
+    int64_t* slab_sizes = nullptr;
+    int64_t* slab_sums = nullptr;
+    int32_t* slab_ptr = nullptr;
+    int32_t* slab_cursor = nullptr;
+    int32_t* slab_edges = nullptr;
+    int64_t cap_ptr = 0, cap_edges = 0;
     int64_t* counts = nullptr;
     int64_t* row_ptr = nullptr;
     int32_t* cand = nullptr;
     uint16_t* count16 = nullptr;
     int32_t* top_ids = nullptr;
     int32_t* top_n = nullptr;
+    double* jv = nullptr;             // exact J of the top-m lists
+    int32_t* ref_ids = nullptr;       // refined top-k
+    double* ref_j = nullptr;
     int* flags = nullptr;
     int64_t* d_n = nullptr;
-    unsigned long long* ticket = nullptr;
+    unsigned long long* ticket = nullptr;  // [2]: signing grid, refinement grid
     int64_t* scan_sums = nullptr;
+    const uint2* sidx_cell = nullptr;  // the stream index the graph captured (nullptr: none)
+    int64_t kernels = 0;               // kernel launches per replay
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -53,49 +71,77 @@ extern "C" int pmh_qgraph_destroy(pmh_qgraph g)
     cudaDeviceSynchronize();
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
-    void* bufs[] = {g->xy,     g->off,     g->bbox,    g->area2, g->hashes, g->counts,
-                    g->row_ptr, g->cand,   g->count16, g->top_ids, g->top_n, g->flags,
-                    g->d_n,    g->ticket, g->scan_sums};
+    void* bufs[] = {g->xy,        g->off,        g->bbox,       g->area2,     g->hashes,
+                    g->slab_info, g->slab_sizes, g->slab_sums,  g->slab_ptr,  g->slab_cursor,
+                    g->slab_edges, g->counts,    g->row_ptr,    g->cand,      g->count16,
+                    g->top_ids,   g->top_n,      g->jv,         g->ref_ids,   g->ref_j,
+                    g->flags,     g->d_n,        g->ticket,     g->scan_sums};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete g;
     return PMH_OK;
 }
 
-extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, int64_t max_queries,
-                                 int64_t max_vertices, int64_t cand_capacity, int32_t m,
+extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, pmh_polys db, int64_t max_queries,
+                                 int64_t max_vertices, int64_t cand_capacity, int32_t m, int32_t k,
                                  pmh_qgraph* out)
 {
     if (!out) return pmh_set_error(PMH_ERR_ARG, "null out");
     *out = nullptr;
     PMH_TRY(pmh_check_device(ctx));
     if (!index || max_queries < 1 || max_queries >= (1ll << 31) || max_vertices < 3 ||
-        cand_capacity < 1 || m < 1 || m > 1024)
-        return pmh_set_error(PMH_ERR_ARG, "bad graph sizes");
+        cand_capacity < 1 || m < 1 || m > 1024 || k < 0 || k > m || (k > 0 && !db))
+        return pmh_set_error(PMH_ERR_ARG, "bad graph sizes (0 <= k <= m <= 1024, k > 0 needs db)");
     pmh_qgraph g = new pmh_qgraph_s();
     g->ctx = ctx;
     g->device = ctx->device;
     g->index = index;
+    g->db = k > 0 ? db : nullptr;
     g->P = index->params;
     g->maxQ = max_queries;
     g->maxV = max_vertices;
     g->cap = cand_capacity;
     g->m = m;
+    g->k = k;
     const int64_t Q = max_queries, K = g->P.K;
+    // every large polygon has at most n / 4 slabs: the slab tables fit exactly; the
+    // edge lists get four entries per vertex (a polygon needing more is left out)
+    g->cap_ptr = max_vertices / 4 + Q + 1;
+    g->cap_edges = 4 * max_vertices;
+    // the stream index is built (or found) now: building it synchronises
+    StreamIndexView sidx{};
+    if (g->P.flags & PMH_FLAG_STREAM_INDEX) {
+        const int rc = pmh_stream_index_get(ctx, &g->P, nullptr, &sidx);
+        if (rc != PMH_OK) {
+            delete g;
+            return rc;
+        }
+        if (!sidx.ranked) sidx = StreamIndexView{};  // saturated lists: sign by walking
+        g->sidx_cell = sidx.cell;
+    }
     bool ok = cudaMalloc(&g->xy, sizeof(int2) * max_vertices) == cudaSuccess &&
               cudaMalloc(&g->off, sizeof(int64_t) * (Q + 1)) == cudaSuccess &&
               cudaMalloc(&g->bbox, sizeof(int4) * Q) == cudaSuccess &&
               cudaMalloc(&g->area2, sizeof(int64_t) * Q) == cudaSuccess &&
               cudaMalloc(&g->hashes, sizeof(uint32_t) * Q * K) == cudaSuccess &&
+              cudaMalloc(&g->slab_info, sizeof(SlabInfo) * Q) == cudaSuccess &&
+              cudaMalloc(&g->slab_sizes, sizeof(int64_t) * 2 * (Q + 1)) == cudaSuccess &&
+              cudaMalloc(&g->slab_sums, sizeof(int64_t) * 2 * pmh_scan_sums_size(Q)) == cudaSuccess &&
+              cudaMalloc(&g->slab_ptr, sizeof(int32_t) * g->cap_ptr) == cudaSuccess &&
+              cudaMalloc(&g->slab_cursor, sizeof(int32_t) * g->cap_ptr) == cudaSuccess &&
+              cudaMalloc(&g->slab_edges, sizeof(int32_t) * g->cap_edges) == cudaSuccess &&
               cudaMalloc(&g->counts, sizeof(int64_t) * Q) == cudaSuccess &&
               cudaMalloc(&g->row_ptr, sizeof(int64_t) * (Q + 1)) == cudaSuccess &&
               cudaMalloc(&g->cand, sizeof(int32_t) * cand_capacity) == cudaSuccess &&
               cudaMalloc(&g->count16, sizeof(uint16_t) * cand_capacity) == cudaSuccess &&
               cudaMalloc(&g->top_ids, sizeof(int32_t) * Q * m) == cudaSuccess &&
               cudaMalloc(&g->top_n, sizeof(int32_t) * Q) == cudaSuccess &&
+              (k == 0 || (cudaMalloc(&g->jv, sizeof(double) * Q * m) == cudaSuccess &&
+                          cudaMalloc(&g->ref_ids, sizeof(int32_t) * Q * k) == cudaSuccess &&
+                          cudaMalloc(&g->ref_j, sizeof(double) * Q * k) == cudaSuccess)) &&
               cudaMalloc(&g->flags, sizeof(int) * 4) == cudaSuccess &&
               cudaMalloc(&g->d_n, sizeof(int64_t)) == cudaSuccess &&
-              cudaMalloc(&g->ticket, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&g->ticket, 2 * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMalloc(&g->scan_sums, sizeof(int64_t) * pmh_scan_sums_size(Q)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -106,6 +152,8 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, int64_t max_queri
     cudaMemset(g->off, 0, sizeof(int64_t) * (Q + 1));
     cudaStream_t cs;
     PMH_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const int U = 4;  // points per lane per round of the walk form
+    const int64_t launches0 = g_pmh_launches.load();
     int rc = PMH_OK;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
@@ -115,8 +163,13 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, int64_t max_queri
         rc = pmh_launch_prep(ctx->sm_count, g->xy, g->off, Q, g->d_n, max_vertices, g->bbox, g->area2,
                              g->flags, cs);
     if (rc == PMH_OK)
-        rc = pmh_launch_sign(ctx, g->xy, g->off, g->bbox, nullptr, nullptr, nullptr, nullptr, &g->P,
-                             Q, g->d_n, g->flags, g->ticket, g->hashes, cs);
+        rc = pmh_launch_slabs_fixed(ctx, g->xy, g->off, Q, g->d_n, g->slab_info, g->slab_sizes,
+                                    g->slab_sums, g->slab_ptr, g->cap_ptr, g->slab_cursor, g->slab_edges,
+                                    g->cap_edges, cs);
+    if (rc == PMH_OK)
+        rc = pmh_launch_sign_unified(ctx, U, g->xy, g->off, g->bbox, g->area2, g->slab_info, g->slab_ptr,
+                                     g->slab_edges, nullptr, Q, Q, g->d_n, g->flags, &g->P, sidx,
+                                     g->ticket, g->hashes, nullptr, cs);
     if (rc == PMH_OK)
         rc = pmh_launch_query(index, g->hashes, Q, g->d_n, g->counts, nullptr, nullptr, 0, g->flags,
                               false, cs);
@@ -130,11 +183,16 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, int64_t max_queri
     if (rc == PMH_OK)
         rc = pmh_launch_topm(g->row_ptr, g->cand, g->count16, nullptr, Q, m, g->top_ids, g->top_n,
                              g->flags, cs);
+    if (rc == PMH_OK && k > 0)
+        rc = pmh_launch_refine_topk(ctx, g->xy, g->off, g->area2, db, g->top_ids, g->top_n, Q, g->d_n, m,
+                                    k, g->jv, g->ticket + 1, g->ref_ids, g->ref_j, cs);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(cs, &graph);
     if (rc == PMH_OK && e != cudaSuccess)
         rc = pmh_set_error(PMH_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
     g->graph = graph;
+    g->kernels = g_pmh_launches.load() - launches0;
+    g_pmh_launches.fetch_sub(g->kernels);  // captured, not launched: counted per replay
     if (rc == PMH_OK) {
         e = cudaGraphInstantiate(&g->exec, graph, 0);
         if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
@@ -155,6 +213,9 @@ extern "C" int pmh_qgraph_run(pmh_qgraph g, const int32_t* xy, const int64_t* of
 {
     if (!g) return pmh_set_error(PMH_ERR_ARG, "null graph");
     PMH_TRY(pmh_check_device(g->ctx));
+    if (g->sidx_cell && g->ctx->sindex.cell[0] != g->sidx_cell)
+        return pmh_set_error(PMH_ERR_STATE, "the context's stream index was rebuilt for other "
+                                            "parameters since the graph was captured: recreate the graph");
     if (n_queries < 0 || n_queries > g->maxQ || n_vertices < 0 || n_vertices > g->maxV ||
         (n_queries > 0 && (!xy || !offsets)))
         return pmh_set_error(PMH_ERR_RANGE, "batch of %lld queries / %lld vertices exceeds the "
@@ -168,7 +229,7 @@ extern "C" int pmh_qgraph_run(pmh_qgraph g, const int32_t* xy, const int64_t* of
     set_batch_kernel<<<1, 1, 0, s>>>(g->d_n, n_queries);
     PMH_LAUNCHED("set_batch_kernel");
     PMH_CUDA_TRY(cudaGraphLaunch(g->exec, s));
-    g_pmh_launches.fetch_add(9);  // kernels in the graph: prep, sign, 2 x join, 3 x scan, agree, top-m
+    g_pmh_launches.fetch_add(g->kernels);  // the kernels the graph holds
     return PMH_OK;
 }
 
@@ -183,6 +244,15 @@ extern "C" int pmh_qgraph_outputs(pmh_qgraph g, uint32_t** d_hashes, int64_t** d
     if (d_count) *d_count = g->count16;
     if (d_top_ids) *d_top_ids = g->top_ids;
     if (d_top_n) *d_top_n = g->top_n;
+    return PMH_OK;
+}
+
+extern "C" int pmh_qgraph_refined(pmh_qgraph g, int32_t** d_top_ids, double** d_top_j)
+{
+    if (!g) return pmh_set_error(PMH_ERR_ARG, "null graph");
+    if (g->k == 0) return pmh_set_error(PMH_ERR_STATE, "the graph was captured without refinement");
+    if (d_top_ids) *d_top_ids = g->ref_ids;
+    if (d_top_j) *d_top_j = g->ref_j;
     return PMH_OK;
 }
 

@@ -229,14 +229,19 @@ struct pmh_polys_s {
     int32_t* slab_edges = nullptr;
     int32_t* order = nullptr;       // polygons by expected signing cost, largest first (built
                                     // on the first signing call without the stream index)
-    int32_t* order_cls = nullptr;   // class order: staged indexed-form polygons (Morton order),
-                                    // staged walk-form polygons, the rest (each by cost)
+    int32_t* order_cls = nullptr;   // class order: polygons above kStagedMaxVerts vertices and
+                                    // staged walk-form polygons (each by cost), then staged
+                                    // indexed-form polygons (Morton order)
     int64_t n_indexed = 0;          // class 0: <= kStagedMaxVerts vertices, pmh_index_plan lim > 0
     int64_t n_staged_walk = 0;      // class 1: <= kStagedMaxVerts vertices, walk form
     uint32_t* mask = nullptr;       // [n][16] coverage masks
 };
 
 int pmh_build_slabs(pmh_polys P, cudaStream_t s);
+int pmh_launch_slabs_fixed(pmh_ctx ctx, const int2* xy, const int64_t* off, int64_t max_polys,
+                           const int64_t* d_n, SlabInfo* info, int64_t* sizes, int64_t* sums,
+                           int32_t* slab_ptr, int64_t cap_ptr, int32_t* cursor, int32_t* slab_edges,
+                           int64_t cap_edges, cudaStream_t s);
 int pmh_build_masks(pmh_polys P, cudaStream_t s);
 
 // coverage masks (masks.cu): 16 x 16 cells of 2^cwl x 2^chl lattice units over the
@@ -321,19 +326,19 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     const StreamIndexView* sidx = nullptr, const uint32_t* masks = nullptr,
                     const int32_t* order_cls = nullptr, int64_t n_indexed = 0,
                     int64_t n_staged_walk = 0);
-// walk form of the staged polygons list[0 .. n_list) (sign_indexed.cu; U = points
-// per lane per round: 2, 4 or 8)
-int pmh_launch_sign_walk_staged(pmh_ctx ctx, int U, const int2* xy, const int64_t* off,
-                                const int4* bbox, const int32_t* list, int64_t n_list,
-                                const pmh_params* P, unsigned long long* ticket, uint32_t* out,
-                                unsigned long long* work, cudaStream_t s);
-// indexed form of the staged polygons list[0 .. n_list) (sign_indexed.cu); ticket is
-// its own work-queue counter, work (optional) the six work counters
-int pmh_launch_sign_indexed(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4* bbox,
-                            const int64_t* area2, const int32_t* list, int64_t n_list,
-                            const pmh_params* P, const StreamIndexView& S,
-                            unsigned long long* ticket, uint32_t* out,
-                            unsigned long long* work, cudaStream_t s);
+// every polygon in one persistent launch (sign_unified.cu): slots list[0 ..
+// n_slots) (list nullptr: slot = polygon id), the first n_chunked as (polygon,
+// 32-hash chunk) items, the rest whole; d_n (optional) caps n_slots on the
+// device, d_flags (optional) skips a batch that failed validation; U = points
+// per lane per round of the walk form (2, 4 or 8); work (optional) the six
+// work counters
+int pmh_launch_sign_unified(pmh_ctx ctx, int U, const int2* xy, const int64_t* off,
+                            const int4* bbox, const int64_t* area2, const SlabInfo* slabs,
+                            const int32_t* slab_ptr, const int32_t* slab_edges, const int32_t* list,
+                            int64_t n_slots, int64_t n_chunked, const int64_t* d_n,
+                            const int* d_flags, const pmh_params* P, const StreamIndexView& S,
+                            unsigned long long* ticket, uint32_t* out, unsigned long long* work,
+                            cudaStream_t s);
 int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
                      int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
                      int* d_flags, bool write, cudaStream_t s);
@@ -345,6 +350,14 @@ int pmh_launch_agree_features(pmh_ctx ctx, const uint32_t* qh, const uint32_t* p
                               const pmh_params* P, uint16_t* count, uint32_t* bandmask,
                               uint16_t* feat, const float2* qfeat, const float2* pfeat,
                               const int* d_flags, cudaStream_t s);
+// exact refinement of fixed-width top-m lists (ids [Q][m], nlist [Q]) to the top-k by
+// (J desc, id asc) (refine.cu); jv: Q * m doubles of scratch; ticket: the grid's counter;
+// d_n (optional) caps Q on the device
+int pmh_launch_refine_topk(pmh_ctx ctx, const int2* qxy, const int64_t* qoff, const int64_t* qarea2,
+                           pmh_polys db, const int32_t* ids, const int32_t* nlist, int64_t Q,
+                           const int64_t* d_n, int32_t m, int32_t k, double* jv,
+                           unsigned long long* ticket, int32_t* top_ids, double* top_j,
+                           cudaStream_t s);
 int pmh_launch_topm(const int64_t* row_ptr, const int32_t* cand, const uint16_t* count,
                     const float* score, int64_t Q, int32_t m, int32_t* out_ids, int32_t* out_n,
                     const int* d_flags, cudaStream_t s);

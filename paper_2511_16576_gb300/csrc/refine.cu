@@ -420,12 +420,13 @@ refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qo
                     const int64_t* __restrict__ poff, const int64_t* __restrict__ parea2,
                     const int32_t* __restrict__ ids, const int32_t* __restrict__ nlist, int m,
                     const int32_t* __restrict__ qid_list, int64_t n_pairs, double* __restrict__ out,
-                    unsigned long long* __restrict__ ticket)
+                    unsigned long long* __restrict__ ticket, const int64_t* __restrict__ d_n)
 {
     __shared__ int2 sv[kRefineWarps][kWarpVerts];
     __shared__ uint2 cq[kRefineWarps][64];
     __shared__ RefSlabs sl[kRefineWarps][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (d_n && !qid_list) n_pairs = min(n_pairs, *d_n * (int64_t)m);  // lists of the live queries
     // persistent warps pull pairs from a ticket: pair costs differ by orders of
     // magnitude (a query against its own source vs a neighbour it barely touches)
     for (;;) {
@@ -465,10 +466,12 @@ __device__ __forceinline__ bool jkey_before(JKey a, JKey b)  // (J desc, id asc)
 
 __global__ void topk_by_j_kernel(const int32_t* __restrict__ ids, const int32_t* __restrict__ nlist,
                                  const double* __restrict__ jv, int m, int cap, int k,
-                                 int32_t* __restrict__ top_ids, double* __restrict__ top_j)
+                                 int32_t* __restrict__ top_ids, double* __restrict__ top_j,
+                                 const int64_t* __restrict__ d_n)
 {
     extern __shared__ JKey s[];
     const int64_t q = blockIdx.x;
+    if (d_n && q >= *d_n) return;  // past the live batch
     const int n = nlist[q];
     for (int i = threadIdx.x; i < cap; i += blockDim.x) {
         JKey x;
@@ -506,24 +509,41 @@ __global__ void topk_by_j_kernel(const int32_t* __restrict__ ids, const int32_t*
 
 }  // namespace
 
-// persistent grid (SM count x resident blocks) over the pairs, with its ticket in
-// context slot kRefineTicket
-constexpr int kRefineTicket = 6;
-static int launch_refine(pmh_ctx ctx, pmh_polys queries, pmh_polys db, const int32_t* ids,
-                         const int32_t* nlist, int m, const int32_t* qid_list, int64_t n_pairs,
-                         double* out, cudaStream_t s)
+// persistent grid (SM count x resident blocks) over the pairs
+static int launch_refine(pmh_ctx ctx, const int2* qxy, const int64_t* qoff, const int64_t* qarea2,
+                         pmh_polys db, const int32_t* ids, const int32_t* nlist, int m,
+                         const int32_t* qid_list, int64_t n_pairs, double* out,
+                         unsigned long long* ticket, const int64_t* d_n, cudaStream_t s)
 {
     int per_sm = 0;
     PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_pairs_kernel,
                                                                kRefineWarps * 32, 0));
     const int blocks = (int)std::min<int64_t>((n_pairs + kRefineWarps - 1) / kRefineWarps,
                                               (int64_t)ctx->sm_count * std::max(per_sm, 1));
-    unsigned long long* ticket = ctx->d_tickets + kRefineTicket;
     PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
     refine_pairs_kernel<<<blocks, kRefineWarps * 32, 0, s>>>(
-        queries->xy, queries->offsets, queries->area2, db->xy, db->offsets, db->area2, ids, nlist, m,
-        qid_list, n_pairs, out, ticket);
+        qxy, qoff, qarea2, db->xy, db->offsets, db->area2, ids, nlist, m, qid_list, n_pairs, out, ticket,
+        d_n);
     PMH_LAUNCHED("refine_pairs_kernel");
+    return PMH_OK;
+}
+
+// context ticket slot of the refinement grid
+constexpr int kRefineTicket = 6;
+
+int pmh_launch_refine_topk(pmh_ctx ctx, const int2* qxy, const int64_t* qoff, const int64_t* qarea2,
+                           pmh_polys db, const int32_t* ids, const int32_t* nlist, int64_t Q,
+                           const int64_t* d_n, int32_t m, int32_t k, double* jv,
+                           unsigned long long* ticket, int32_t* top_ids, double* top_j,
+                           cudaStream_t s)
+{
+    if (Q <= 0) return PMH_OK;
+    PMH_TRY(launch_refine(ctx, qxy, qoff, qarea2, db, ids, nlist, m, nullptr, Q * m, jv, ticket, d_n, s));
+    int cap = 1;
+    while (cap < m) cap <<= 1;
+    const size_t smem = sizeof(JKey) * cap;
+    topk_by_j_kernel<<<(unsigned)Q, 256, smem, s>>>(ids, nlist, jv, m, cap, k, top_ids, top_j, d_n);
+    PMH_LAUNCHED("topk_by_j_kernel");
     return PMH_OK;
 }
 
@@ -536,17 +556,11 @@ extern "C" int pmh_refine_topk(pmh_ctx ctx, pmh_polys queries, pmh_polys db, con
         (Q > 0 && (!d_ids || !d_n || !d_top_ids || !d_top_j)))
         return pmh_set_error(PMH_ERR_ARG, "bad arguments (1 <= k <= m <= 1024)");
     if (Q == 0) return PMH_OK;
-    cudaStream_t s = (cudaStream_t)stream;
     double* jv = nullptr;
     PMH_TRY(pmh_scratch(ctx, SCR_REFINE, sizeof(double) * (size_t)(Q * m), (void**)&jv));
-    int64_t n_pairs = Q * m;
-    PMH_TRY(launch_refine(ctx, queries, db, d_ids, d_n, m, nullptr, n_pairs, jv, s));
-    int cap = 1;
-    while (cap < m) cap <<= 1;
-    size_t smem = sizeof(JKey) * cap;
-    topk_by_j_kernel<<<(unsigned)Q, 256, smem, s>>>(d_ids, d_n, jv, m, cap, k, d_top_ids, d_top_j);
-    PMH_LAUNCHED("topk_by_j_kernel");
-    return PMH_OK;
+    return pmh_launch_refine_topk(ctx, queries->xy, queries->offsets, queries->area2, db, d_ids, d_n, Q,
+                                  nullptr, m, k, jv, ctx->d_tickets + kRefineTicket, d_top_ids, d_top_j,
+                                  (cudaStream_t)stream);
 }
 
 extern "C" int pmh_pair_jaccard(pmh_ctx ctx, pmh_polys queries, pmh_polys db, const int32_t* d_qid,
@@ -556,7 +570,8 @@ extern "C" int pmh_pair_jaccard(pmh_ctx ctx, pmh_polys queries, pmh_polys db, co
     if (!queries || !db || n_pairs < 0 || (n_pairs > 0 && (!d_qid || !d_pid || !d_j)))
         return pmh_set_error(PMH_ERR_ARG, "bad arguments");
     if (n_pairs == 0) return PMH_OK;
-    return launch_refine(ctx, queries, db, d_pid, nullptr, 1, d_qid, n_pairs, d_j, (cudaStream_t)stream);
+    return launch_refine(ctx, queries->xy, queries->offsets, queries->area2, db, d_pid, nullptr, 1, d_qid,
+                         n_pairs, d_j, ctx->d_tickets + kRefineTicket, nullptr, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------

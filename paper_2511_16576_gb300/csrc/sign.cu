@@ -25,13 +25,11 @@
 // Theorem 2: E[h] = 1/S_p), which balances polygons whose work differs by
 // orders of magnitude.
 //
-// Which kernel signs which polygon: with the stream index, the polygons of at
-// most 256 vertices are planned at upload and signed by sign_indexed_kernel
-// (indexed form) and sign_walk_staged_kernel (walk form, sign_indexed.cu); this
-// file's sign_kernel takes the larger polygons (walk, or the indexed form of the
-// fine level through their slab index) and, without the stream index or with
-// precomputed coverage masks, every polygon.  pmh_launch_sign runs the kernels
-// one after the other on the caller's stream.
+// Which kernel signs which polygon: with the stream index, every polygon is
+// signed by one launch of sign_unified_kernel (sign_unified.cu: indexed or walk
+// form as each polygon's plan says, staged or through its y-slab lists); this
+// file's sign_kernel signs without the stream index, with precomputed coverage
+// masks, and the batches of the captured query pipeline.
 #include <algorithm>
 #include <mutex>
 
@@ -44,7 +42,7 @@ namespace {
 constexpr int kWarps = 8;        // warps per block
 constexpr int kU = 4;            // points per lane per round
 constexpr int kWorkSlot = 8;     // context ticket slots 8..13: work counters of the walk kernel
-constexpr int kIdxWorkSlot = 16; // slots 16..21: work counters of the indexed kernel
+constexpr int kIdxWorkSlot = 16; // slots 16..21: work counters of the unified kernel
 
 __device__ __forceinline__ uint32_t sign_one(const int2* __restrict__ v, int n, int x0, int y0,
                                              uint32_t w, uint32_t h, uint64_t sk, uint32_t T,
@@ -327,27 +325,21 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
         ctx->sign_ev_used += 3;
         PMH_CUDA_TRY(cudaEventRecord(ev[0], s));
     }
-    if (S.cell && S.ranked && order_cls && area2 && !d_n) {
-        // staged polygons of the indexed form (the first n_indexed of the class
-        // order) in their own kernel; the rest below, in cost order
-        PMH_TRY(pmh_launch_sign_indexed(ctx, xy, off, bbox, area2, order_cls, n_indexed, P, S,
-                                        ticket + 2, out, work ? ctx->d_tickets + kIdxWorkSlot : nullptr,
-                                        s));
-        order = order_cls + n_indexed;
-        n_polys -= n_indexed;
-        if (timed) PMH_CUDA_TRY(cudaEventRecord(ev[1], s));
-        if (!masks) {
-            // staged polygons of the walk form in their own kernel (with the
-            // precomputed masks of PMH_FLAG_COVERAGE_MASK they stay below)
-            const int U = kSignVariants[ctx->sign_variant >= 0 ? ctx->sign_variant : 0].U;
-            PMH_TRY(pmh_launch_sign_walk_staged(ctx, U, xy, off, bbox, order, n_staged_walk, P, ticket + 4,
-                                                out, work, s));
-            order += n_staged_walk;
-            n_polys -= n_staged_walk;
+    if (S.cell && S.ranked && order_cls && area2 && !d_n && !masks) {
+        // every polygon in one launch: the class order puts the polygons above the
+        // staged size first (32-hash items), then the staged ones (whole polygons)
+        const int U = kSignVariants[ctx->sign_variant >= 0 ? ctx->sign_variant : 0].U;
+        const int64_t n_big = n_polys - n_indexed - n_staged_walk;
+        PMH_TRY(pmh_launch_sign_unified(ctx, U, xy, off, bbox, area2, slabs, slab_ptr, slab_edges,
+                                        order_cls, n_polys, n_big, nullptr, nullptr, P, S, ticket + 2,
+                                        out, work ? ctx->d_tickets + kIdxWorkSlot : nullptr, s));
+        if (timed) {
+            PMH_CUDA_TRY(cudaEventRecord(ev[1], s));
+            PMH_CUDA_TRY(cudaEventRecord(ev[2], s));
         }
-    } else if (timed) {
-        PMH_CUDA_TRY(cudaEventRecord(ev[1], s));
+        return PMH_OK;
     }
+    if (timed) PMH_CUDA_TRY(cudaEventRecord(ev[1], s));
     if (n_polys <= 0) {
         if (timed) PMH_CUDA_TRY(cudaEventRecord(ev[2], s));
         return PMH_OK;
@@ -380,7 +372,8 @@ extern "C" int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* 
     const bool indexed = (params->flags & PMH_FLAG_STREAM_INDEX) != 0;
     const bool masked = (params->flags & PMH_FLAG_COVERAGE_MASK) != 0;
     if (indexed) PMH_TRY(pmh_stream_index_get(ctx, params, (cudaStream_t)stream, &sidx));
-    if ((!indexed || !sidx.ranked) && !polys->order) PMH_TRY(pmh_build_cost_order(polys, (cudaStream_t)stream));
+    if ((!indexed || !sidx.ranked || masked) && !polys->order)
+        PMH_TRY(pmh_build_cost_order(polys, (cudaStream_t)stream));
     if (masked && !polys->mask) PMH_TRY(pmh_build_masks(polys, (cudaStream_t)stream));
     return pmh_launch_sign(ctx, polys->xy, polys->offsets, polys->bbox, polys->slab_info,
                            polys->slab_ptr, polys->slab_edges, polys->order, params, polys->n,
@@ -483,7 +476,8 @@ extern "C" int pmh_sign_autotune(pmh_ctx ctx, pmh_polys sample, const pmh_params
             const bool indexed = (params->flags & PMH_FLAG_STREAM_INDEX) != 0;
             const bool masked = (params->flags & PMH_FLAG_COVERAGE_MASK) != 0;
             if (indexed) rc = pmh_stream_index_get(ctx, params, 0, &sidx);
-            if (rc == PMH_OK && (!indexed || !sidx.ranked) && !sample->order) rc = pmh_build_cost_order(sample, 0);
+            if (rc == PMH_OK && (!indexed || !sidx.ranked || masked) && !sample->order)
+                rc = pmh_build_cost_order(sample, 0);
             if (rc == PMH_OK && masked && !sample->mask) rc = pmh_build_masks(sample, 0);
             if (rc == PMH_OK)
                 rc = pmh_launch_sign(ctx, sample->xy, sample->offsets, sample->bbox, sample->slab_info,

@@ -33,15 +33,18 @@ __device__ __forceinline__ int slab_count_for(int n, int height)
 
 // pass 1: sizes of every polygon's slab table and edge list
 __global__ void slab_size_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
-                                 int64_t n_polys, int min_verts, SlabInfo* __restrict__ info,
-                                 int64_t* __restrict__ ptr_sizes, int64_t* __restrict__ edge_sizes)
+                                 int64_t n_polys, const int64_t* __restrict__ d_n, int min_verts,
+                                 SlabInfo* __restrict__ info, int64_t* __restrict__ ptr_sizes,
+                                 int64_t* __restrict__ edge_sizes)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    // slots at or past the device-side count (d_n) get empty sizes
+    const int64_t n_live = d_n ? min(n_polys, *d_n) : n_polys;
     for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < n_polys;
          p += nwarps) {
-        const int64_t b = off[p];
-        const int n = (int)(off[p + 1] - b);
+        const int64_t b = p < n_live ? off[p] : 0;
+        const int n = p < n_live ? (int)(off[p + 1] - b) : 0;
         if (n <= min_verts) {
             if (lane == 0) {
                 info[p] = SlabInfo{0, 0, 0, 1, 0};
@@ -79,13 +82,15 @@ __global__ void slab_size_kernel(const int2* __restrict__ xy, const int64_t* __r
 
 // pass 2: per polygon (one warp) count, prefix-sum and fill the slab lists
 __global__ void slab_fill_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
-                                 int64_t n_polys, int min_verts, SlabInfo* __restrict__ info,
-                                 const int64_t* __restrict__ ptr_base,
+                                 int64_t n_polys, const int64_t* __restrict__ d_n, int min_verts,
+                                 SlabInfo* __restrict__ info, const int64_t* __restrict__ ptr_base,
                                  const int64_t* __restrict__ edge_base, int32_t* __restrict__ slab_ptr,
-                                 int32_t* __restrict__ cursor, int32_t* __restrict__ slab_edges)
+                                 int64_t cap_ptr, int32_t* __restrict__ cursor,
+                                 int32_t* __restrict__ slab_edges, int64_t cap_edges)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    if (d_n) n_polys = min(n_polys, *d_n);
     for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < n_polys;
          p += nwarps) {
         const int64_t b = off[p];
@@ -94,6 +99,11 @@ __global__ void slab_fill_kernel(const int2* __restrict__ xy, const int64_t* __r
         SlabInfo si = info[p];
         const int S = si.S, h = si.slab_h, y0 = si.ymin;
         const int64_t pb = ptr_base[p], eb = edge_base[p];
+        if (ptr_base[p + 1] > cap_ptr || edge_base[p + 1] > cap_edges) {
+            // the lists do not fit the fixed buffers: this polygon is tested over all its edges
+            if (lane == 0) info[p].S = 0;
+            continue;
+        }
         if (lane == 0) {
             info[p].slab_base = pb;
             info[p].edge_base = eb;
@@ -165,11 +175,13 @@ __device__ __forceinline__ uint32_t morton16(uint32_t x, uint32_t y)
     return spread(x) | (spread(y) << 1);
 }
 
-// class key: staged polygons of the indexed form first (class 0) in Morton
-// order of their box centres -- warps running at the same time then read
-// nearby cells of the stream index, which keeps them in L2 -- then staged
-// polygons of the walk form (class 1) and the rest (class 2), each by
-// decreasing expected cost; counts classes 0 and 1 into n_cls[0], n_cls[1]
+// class key: polygons of more than kStagedMaxVerts vertices (class 2) first,
+// by decreasing expected cost -- the signing launch splits them into 32-hash
+// items and starts the longest first -- then staged polygons of the walk form
+// (class 1), by decreasing expected cost, then staged polygons of the indexed
+// form (class 0) in Morton order of their box centres -- warps running at the
+// same time then read nearby cells of the stream index, which keeps them in
+// L2; counts classes 0 and 1 into n_cls[0], n_cls[1]
 __global__ void class_key_kernel(const int4* __restrict__ bbox, const int64_t* __restrict__ area2,
                                  const int64_t* __restrict__ off, int64_t n,
                                  uint32_t* __restrict__ keys, int32_t* __restrict__ ids,
@@ -188,9 +200,9 @@ __global__ void class_key_kernel(const int4* __restrict__ bbox, const int64_t* _
         if (cls == 0) {
             const uint32_t cx = (uint32_t)min((bb.x + bb.z) >> 1, 65535);
             const uint32_t cy = (uint32_t)min((bb.y + bb.w) >> 1, 65535);
-            key = morton16(cx, cy) >> 2;
+            key = (2u << 30) | (morton16(cx, cy) >> 2);
         } else {
-            key = ((uint32_t)cls << 30) | (~__float_as_uint(cost) >> 2);
+            key = ((uint32_t)(2 - cls) << 30) | (~__float_as_uint(cost) >> 2);
         }
         keys[p] = key;
         ids[p] = (int32_t)p;
@@ -221,7 +233,7 @@ int pmh_build_slabs(pmh_polys P, cudaStream_t s)
     int64_t* ptr_sizes = sizes;
     int64_t* edge_sizes = sizes + (n + 1);
     int blocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)ctx->sm_count * 16);
-    slab_size_kernel<<<blocks, 256, 0, s>>>(P->xy, P->offsets, n, kSlabMinVerts, P->slab_info,
+    slab_size_kernel<<<blocks, 256, 0, s>>>(P->xy, P->offsets, n, nullptr, kSlabMinVerts, P->slab_info,
                                             ptr_sizes, edge_sizes);
     PMH_LAUNCHED("slab_size_kernel");
     PMH_TRY(pmh_exclusive_scan_i64(ctx, ptr_sizes, ptr_sizes, n, s));
@@ -240,9 +252,9 @@ int pmh_build_slabs(pmh_polys P, cudaStream_t s)
         return pmh_set_error(PMH_ERR_NOMEM, "slab index allocation failed (%lld entries)",
                              (long long)n_edges);
     }
-    slab_fill_kernel<<<blocks, 256, 0, s>>>(P->xy, P->offsets, n, kSlabMinVerts, P->slab_info,
-                                            ptr_sizes, edge_sizes, P->slab_ptr, cursor,
-                                            P->slab_edges);
+    slab_fill_kernel<<<blocks, 256, 0, s>>>(P->xy, P->offsets, n, nullptr, kSlabMinVerts, P->slab_info,
+                                            ptr_sizes, edge_sizes, P->slab_ptr, INT64_MAX, cursor,
+                                            P->slab_edges, INT64_MAX);
     cudaError_t e = cudaGetLastError();
     g_pmh_launches.fetch_add(1);
     cudaError_t e2 = cudaStreamSynchronize(s);
@@ -328,4 +340,32 @@ int pmh_build_class_order(pmh_polys P, cudaStream_t s)
     if (n_cls) cudaFree(n_cls);
     cudaFree(keys);
     return rc;
+}
+
+// y-slab lists of a batch on fixed, caller-owned buffers, with no host
+// synchronisation (for a captured pipeline): sizes per slot (zero past *d_n),
+// two exclusive scans, and the lists of every polygon whose lists fit the
+// buffers (slab_ptr: cap_ptr entries; slab_edges: cap_edges entries); a polygon
+// whose lists do not fit gets S = 0 and is tested over all its edges.
+// sizes: 2 * (max_polys + 1) entries; sums: 2 * pmh_scan_sums_size(max_polys).
+int pmh_launch_slabs_fixed(pmh_ctx ctx, const int2* xy, const int64_t* off, int64_t max_polys,
+                           const int64_t* d_n, SlabInfo* info, int64_t* sizes, int64_t* sums,
+                           int32_t* slab_ptr, int64_t cap_ptr, int32_t* cursor, int32_t* slab_edges,
+                           int64_t cap_edges, cudaStream_t s)
+{
+    if (max_polys <= 0) return PMH_OK;
+    int64_t* ptr_sizes = sizes;
+    int64_t* edge_sizes = sizes + (max_polys + 1);
+    const int blocks = (int)std::min<int64_t>((max_polys + 7) / 8, (int64_t)ctx->sm_count * 16);
+    slab_size_kernel<<<blocks, 256, 0, s>>>(xy, off, max_polys, d_n, kSlabMinVerts, info, ptr_sizes,
+                                            edge_sizes);
+    PMH_LAUNCHED("slab_size_kernel");
+    PMH_TRY(pmh_exclusive_scan_i64(ctx, ptr_sizes, ptr_sizes, max_polys, s, sums));
+    PMH_TRY(pmh_exclusive_scan_i64(ctx, edge_sizes, edge_sizes, max_polys, s,
+                                   sums + pmh_scan_sums_size(max_polys)));
+    slab_fill_kernel<<<blocks, 256, 0, s>>>(xy, off, max_polys, d_n, kSlabMinVerts, info, ptr_sizes,
+                                            edge_sizes, slab_ptr, cap_ptr, cursor, slab_edges,
+                                            cap_edges);
+    PMH_LAUNCHED("slab_fill_kernel");
+    return PMH_OK;
 }

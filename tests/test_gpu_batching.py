@@ -125,3 +125,57 @@ def test_query_graph_overflow_invalid_and_recovery(B, ctx, small_index):
             g.run(big.xy, big.offsets)
     finally:
         g.close()
+
+
+def test_query_graph_indexed_large_polygons_refined(B, ctx, orc):
+    """The graph with the stream index, query polygons of every size class (staged ones,
+    fractal polygons of up to 3,000 vertices with slab lists, a comb whose slab lists do not
+    fit the graph's fixed buffers, two 5,000-6,000-vertex polygons signed without a
+    coverage mask) and exact refinement to the top-10: hashes equal the oracle's, the join,
+    counts and top-m equal the plain calls, and the refined top-10 equals pmh_refine_topk
+    on the same lists."""
+    from test_gpu_parity import comb
+    db = synth.star_polygons(3000, 41, (8, 3000), "loguniform", (1e-4, 2e-2), fractal=True,
+                             comonotone=True)
+    K, bands, m, k = 64, 16, 16, 10
+    P = B.make_params(K, bands, 1 << 24, flags=B.FLAG_STREAM_INDEX)
+    dbp = upload(B, ctx, db)
+    h = B.minhash_sign(ctx, dbp, P)
+    index = B.lsh_build(ctx, h, P)
+    qs = synth.perturbed_queries(db, 150, 77)
+    big = synth.star_polygons(2, 43, (5000, 6000), "uniform", (1e-2, 2e-2), fractal=True)
+    polys = [qs.poly(i) for i in range(qs.n)]
+    polys[5] = comb(5000, 5000, 500, 10, 10, 5000, 100)
+    polys[40], polys[41] = big.poly(0), big.poly(1)
+    allq = from_polys(polys)
+    g = B.QueryGraph(ctx, index, max_queries=160, max_vertices=allq.n_vertices,
+                     cand_capacity=2_000_000, m=m, db=dbp, k=k)
+    try:
+        for lo, n, host in ((0, 1, False), (0, 33, True), (33, 117, False), (0, 150, False),
+                            (3, 0, False)):
+            batch = allq.subset(np.arange(lo, lo + n))
+            if host:
+                g.run(batch.xy, batch.offsets)
+            else:
+                g.run(torch.from_numpy(batch.xy).to(DEV), torch.from_numpy(batch.offsets).to(DEV))
+            flags, total = g.status()
+            assert flags == 0
+            if n == 0:
+                assert total == 0
+                continue
+            qp = upload(B, ctx, batch)
+            qh, row_ptr, cand, count, ids, nn = plain_outputs(B, ctx, batch, P, h, index, m)
+            assert torch.equal(g.hashes[:n], qh)
+            assert np.array_equal(u32(qh), orc.sign(batch.xy, batch.offsets, P.seed, K, P.T,
+                                                   nthreads=16))
+            assert torch.equal(g.row_ptr[:n + 1], row_ptr) and total == cand.numel()
+            assert torch.equal(g.cand[:total], cand) and torch.equal(g.count[:total], count)
+            assert torch.equal(g.top_ids[:n], ids) and torch.equal(g.top_n[:n], nn)
+            ti, tj = B.refine_topk(ctx, qp, dbp, ids, nn, k)
+            assert torch.equal(g.ref_ids[:n], ti) and torch.equal(g.ref_j[:n], tj)
+            assert (ti[:, 0] >= 0).sum() > n // 2   # most queries find their source
+            qp.close()
+    finally:
+        g.close()
+        index.close()
+        dbp.close()

@@ -156,25 +156,29 @@ def test_sign_indexed_form_paths(B, ctx, orc, flags):
 
 
 def test_sign_kernel_report(B, ctx):
-    """Per-kernel events and work counts: the two signing kernels' counts add up to
-    pmh_sign_work, events cover exactly the calls made with timing on."""
-    db = synth.star_polygons(3000, 31, (16, 256), "loguniform", (1e-4, 1e-2))
-    P = B.make_params(64, 8, T24, flags=B.FLAG_STREAM_INDEX)
+    """Per-kernel events and work counts: with the stream index one launch (the unified
+    kernel) signs every polygon and its counts are pmh_sign_work's; without it the walk
+    kernel does; events cover exactly the calls made with timing on."""
+    db = synth.star_polygons(3000, 31, (16, 400), "loguniform", (1e-4, 1e-2))
     dbp = upload(B, ctx, db)
-    B.sign_report(ctx)
-    B.sign_timing(ctx, True)
-    h1 = B.minhash_sign(ctx, dbp, P)
-    h2 = B.minhash_sign(ctx, dbp, P)
-    B.sign_timing(ctx, False)
-    B.minhash_sign(ctx, dbp, P)
-    rep = B.sign_report(ctx)
-    assert rep["calls"] == 2 and torch.equal(h1, h2)
-    assert rep["indexed"]["ms"] > 0 and rep["walk"]["ms"] > 0
-    total = B.sign_work(ctx)
-    for k, v in total.items():
-        assert v == rep["indexed"]["work"][k] + rep["walk"]["work"][k], k
-    assert rep["indexed"]["work"]["cells"] > 0 and rep["walk"]["work"]["walk_points"] > 0
-    assert B.sign_report(ctx)["calls"] == 0
+    for flags, ran, idle in ((B.FLAG_STREAM_INDEX, "unified", "walk"), (0, "walk", "unified")):
+        P = B.make_params(64, 8, T24, flags=flags)
+        B.sign_report(ctx)
+        B.sign_timing(ctx, True)
+        h1 = B.minhash_sign(ctx, dbp, P)
+        h2 = B.minhash_sign(ctx, dbp, P)
+        B.sign_timing(ctx, False)
+        B.minhash_sign(ctx, dbp, P)
+        rep = B.sign_report(ctx)
+        assert rep["calls"] == 2 and torch.equal(h1, h2)
+        assert rep[ran]["ms"] > 0 and rep[idle]["ms"] < rep[ran]["ms"] * 0.05
+        total = B.sign_work(ctx)
+        for k, v in total.items():
+            assert v == rep[ran]["work"][k] and rep[idle]["work"][k] == 0, k
+        assert rep[ran]["work"]["walk_points"] > 0 and rep[ran]["work"]["edge_tests"] > 0
+        if flags:
+            assert rep[ran]["work"]["cells"] > 0 and rep[ran]["work"]["mask_decisions"] > 0
+        assert B.sign_report(ctx)["calls"] == 0
 
 
 @pytest.fixture(scope="module")
