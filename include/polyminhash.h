@@ -133,6 +133,17 @@ int pmh_poly_upload(pmh_ctx ctx, const int32_t* d_xy, const int64_t* d_offsets,
 int pmh_poly_upload_host(pmh_ctx ctx, const int32_t* h_xy, const int64_t* h_offsets,
                          int64_t n_polys, int64_t n_vertices, pmh_polys* out, void* stream);
 
+/* Upload new polygons into an existing set with the same n_polys and
+ * n_vertices (HOST arrays if host_memory != 0, else device), keeping the
+ * set's vertex, offset, box and area buffers -- so a query graph that
+ * refines against the set stays valid -- and rebuilding everything else as
+ * pmh_poly_upload does.  Synchronises `stream` before and after; work on other
+ * streams that reads the set meanwhile races.  Errors: as pmh_poly_upload,
+ * and PMH_ERR_ARG if the sizes differ from the set's; on a validation error
+ * the set holds the rejected data and must not be signed. */
+int pmh_poly_reload(pmh_polys polys, const int32_t* xy, const int64_t* offsets, int64_t n_polys,
+                    int64_t n_vertices, int host_memory, void* stream);
+
 /* Number of polygons and vertices of an uploaded set. */
 int pmh_polys_info(pmh_polys polys, int64_t* n_polys, int64_t* n_vertices);
 
@@ -198,6 +209,13 @@ int pmh_band_keys(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n, const pmh_pa
  * afterwards.  Errors: PMH_ERR_ARG, PMH_ERR_NOMEM, PMH_ERR_CUDA. */
 int pmh_lsh_build(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n, const pmh_params* params,
                   pmh_index* out, void* stream);
+/* Rebuild an index in place from n new signatures (n and the parameters of the
+ * index unchanged): the index keeps its buffers, so a query graph captured on
+ * it stays valid.  Enqueued on `stream`; a query on another stream that reads
+ * the index meanwhile races.  Errors: PMH_ERR_ARG (other context or size),
+ * PMH_ERR_CUDA. */
+int pmh_lsh_rebuild(pmh_ctx ctx, pmh_index index, const uint32_t* d_hashes, int64_t n,
+                    void* stream);
 int pmh_index_destroy(pmh_index index);
 
 /* A4 -- bucket join.  Candidates of query q: every database id p with some

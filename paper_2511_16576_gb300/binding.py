@@ -56,6 +56,7 @@ _SIGS = {
     "pmh_destroy": (ctypes.c_int, [_P]),
     "pmh_poly_upload": (ctypes.c_int, [_P, _P, _P, _i64, _i64, ctypes.POINTER(_P), _P]),
     "pmh_poly_upload_host": (ctypes.c_int, [_P, _P, _P, _i64, _i64, ctypes.POINTER(_P), _P]),
+    "pmh_poly_reload": (ctypes.c_int, [_P, _P, _P, _i64, _i64, ctypes.c_int, _P]),
     "pmh_polys_info": (ctypes.c_int, [_P, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "pmh_polys_prep": (ctypes.c_int, [_P, _P, _P, _P]),
     "pmh_polys_destroy": (ctypes.c_int, [_P]),
@@ -66,6 +67,7 @@ _SIGS = {
     "pmh_sign_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "pmh_sign_report": (ctypes.c_int, [_P, _P, _P]),
     "pmh_lsh_build": (ctypes.c_int, [_P, _P, _i64, ctypes.POINTER(Params), ctypes.POINTER(_P), _P]),
+    "pmh_lsh_rebuild": (ctypes.c_int, [_P, _P, _P, _i64, _P]),
     "pmh_index_destroy": (ctypes.c_int, [_P]),
     "pmh_lsh_query": (ctypes.c_int, [_P, _P, _P, _i64, _P, _P, _i64, ctypes.POINTER(_i64), _P]),
     "pmh_lsh_query_fill": (ctypes.c_int, [_P, _P, _P, _i64, _P, _P, _i64, _P]),
@@ -237,6 +239,15 @@ def poly_upload_pinned(ctx: Context, xy: torch.Tensor, offsets: torch.Tensor,
     return Polys(ctx, h)
 
 
+def poly_reload(polys: Polys, xy: torch.Tensor, offsets: torch.Tensor, stream=None):
+    """Upload new polygons (same counts) into an existing set, keeping its buffers: CUDA
+    tensors, or pinned CPU tensors."""
+    assert xy.dtype == torch.int32 and offsets.dtype == torch.int64
+    assert xy.is_contiguous() and offsets.is_contiguous() and xy.is_cuda == offsets.is_cuda
+    _check(load().pmh_poly_reload(polys.handle, _ptr(xy), _ptr(offsets), offsets.numel() - 1,
+                                  xy.shape[0], 0 if xy.is_cuda else 1, _stream(stream)))
+
+
 def minhash_sign(ctx: Context, polys: Polys, params: Params, out: torch.Tensor | None = None,
                  stream=None) -> torch.Tensor:
     """A1: uint32 hashes [N, K] (carried in an int32 tensor)."""
@@ -356,6 +367,12 @@ class Index:
 
 def lsh_build(ctx: Context, hashes: torch.Tensor, params: Params, stream=None) -> Index:
     return Index(ctx, hashes, params, stream)
+
+
+def lsh_rebuild(ctx: Context, index: Index, hashes: torch.Tensor, stream=None):
+    """A3 in place: rebuild `index` from new signatures of the same count."""
+    _check(load().pmh_lsh_rebuild(ctx.handle, index.handle, _ptr(hashes), hashes.shape[0],
+                                  _stream(stream)))
 
 
 def lsh_query(ctx: Context, index: Index, qhashes: torch.Tensor, capacity: int | None = None,

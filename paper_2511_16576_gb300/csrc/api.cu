@@ -204,6 +204,44 @@ __global__ void poly_feat_kernel(const int64_t* __restrict__ area2, const int64_
     }
 }
 
+// copy the arrays in, validate them and compute every per-polygon product (bbox,
+// 2 x area, reranker inputs, slab lists, class order) into P's buffers
+static int upload_fill(pmh_polys P, const int32_t* xy, const int64_t* offsets, bool host,
+                       cudaStream_t s)
+{
+    pmh_ctx ctx = P->ctx;
+    const int64_t n_polys = P->n, n_vertices = P->nv;
+    cudaMemcpyKind kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaSuccess;
+    if (n_vertices > 0) e = cudaMemcpyAsync(P->xy, xy, sizeof(int2) * n_vertices, kind, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P->offsets, offsets, sizeof(int64_t) * (n_polys + 1), kind, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return pmh_set_error(PMH_ERR_CUDA, "upload copy failed: %s", cudaGetErrorString(e));
+    // offsets[0] and offsets[n] are checked by the kernel through b/e bounds
+    if (n_polys > 0)
+        PMH_TRY(pmh_launch_prep(ctx->sm_count, P->xy, P->offsets, n_polys, nullptr, n_vertices, P->bbox,
+                                P->area2, ctx->d_status, s));
+    int st[2] = {0, 0};
+    e = cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return pmh_set_error(PMH_ERR_CUDA, "upload failed: %s", cudaGetErrorString(e));
+    memcpy(st, ctx->h_pinned, sizeof(st));
+    if (st[0] & 1) return pmh_set_error(PMH_ERR_RANGE, "offsets are not increasing / in range");
+    if (st[0] & 2) return pmh_set_error(PMH_ERR_RANGE, "a polygon has fewer than 3 vertices");
+    if (st[0] & 4) return pmh_set_error(PMH_ERR_RANGE, "a coordinate exceeds |2^20|");
+    P->max_n = st[1];
+    if (n_polys > 0) {
+        int blocks = (int)std::min<int64_t>((n_polys + 255) / 256, (int64_t)ctx->sm_count * 32);
+        poly_feat_kernel<<<blocks, 256, 0, s>>>(P->area2, P->offsets, n_polys, P->feat);
+        g_pmh_launches.fetch_add(1);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return pmh_set_error(PMH_ERR_CUDA, "feature kernel: %s", cudaGetErrorString(e));
+    }
+    PMH_TRY(pmh_build_slabs(P, s));
+    return pmh_build_class_order(P, s);
+}
+
 static int upload_common(pmh_ctx ctx, const int32_t* xy, const int64_t* offsets, int64_t n_polys,
                          int64_t n_vertices, bool host, pmh_polys* out, void* stream)
 {
@@ -214,64 +252,57 @@ static int upload_common(pmh_ctx ctx, const int32_t* xy, const int64_t* offsets,
         !offsets)
         return pmh_set_error(PMH_ERR_ARG, "bad polygon arguments (n_polys=%lld n_vertices=%lld)",
                              (long long)n_polys, (long long)n_vertices);
-    cudaStream_t s = (cudaStream_t)stream;
     pmh_polys P = new pmh_polys_s();
     P->ctx = ctx;
     P->device = ctx->device;
     P->n = n_polys;
     P->nv = n_vertices;
-    auto fail = [&](int code) {
-        pmh_polys_destroy(P);
-        return code;
-    };
+    const size_t np = (size_t)(n_polys > 0 ? n_polys : 1);
     if (cudaMalloc(&P->xy, sizeof(int2) * (size_t)(n_vertices > 0 ? n_vertices : 1)) != cudaSuccess ||
         cudaMalloc(&P->offsets, sizeof(int64_t) * (size_t)(n_polys + 1)) != cudaSuccess ||
-        cudaMalloc(&P->bbox, sizeof(int4) * (size_t)(n_polys > 0 ? n_polys : 1)) != cudaSuccess ||
-        cudaMalloc(&P->area2, sizeof(int64_t) * (size_t)(n_polys > 0 ? n_polys : 1)) != cudaSuccess) {
+        cudaMalloc(&P->bbox, sizeof(int4) * np) != cudaSuccess ||
+        cudaMalloc(&P->area2, sizeof(int64_t) * np) != cudaSuccess ||
+        cudaMalloc(&P->feat, sizeof(float2) * np) != cudaSuccess) {
         cudaGetLastError();
-        return fail(pmh_set_error(PMH_ERR_NOMEM, "polygon allocation failed (%lld vertices)",
-                                  (long long)n_vertices));
+        pmh_polys_destroy(P);
+        return pmh_set_error(PMH_ERR_NOMEM, "polygon allocation failed (%lld vertices)",
+                             (long long)n_vertices);
     }
-    cudaMemcpyKind kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-    cudaError_t e = cudaSuccess;
-    if (n_vertices > 0) e = cudaMemcpyAsync(P->xy, xy, sizeof(int2) * n_vertices, kind, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(P->offsets, offsets, sizeof(int64_t) * (n_polys + 1), kind, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, 2 * sizeof(int), s);
-    if (e != cudaSuccess)
-        return fail(pmh_set_error(PMH_ERR_CUDA, "upload copy failed: %s", cudaGetErrorString(e)));
-    // offsets[0] and offsets[n] are checked by the kernel through b/e bounds
-    if (n_polys > 0) {
-        int rc = pmh_launch_prep(ctx->sm_count, P->xy, P->offsets, n_polys, nullptr, n_vertices,
-                                 P->bbox, P->area2, ctx->d_status, s);
-        if (rc != PMH_OK) return fail(rc);
+    const int rc = upload_fill(P, xy, offsets, host, (cudaStream_t)stream);
+    if (rc != PMH_OK) {
+        pmh_polys_destroy(P);
+        return rc;
     }
-    int st[2] = {0, 0};
-    e = cudaMemcpyAsync(ctx->h_pinned, ctx->d_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess)
-        return fail(pmh_set_error(PMH_ERR_CUDA, "upload failed: %s", cudaGetErrorString(e)));
-    memcpy(st, ctx->h_pinned, sizeof(st));
-    if (st[0] & 1) return fail(pmh_set_error(PMH_ERR_RANGE, "offsets are not increasing / in range"));
-    if (st[0] & 2) return fail(pmh_set_error(PMH_ERR_RANGE, "a polygon has fewer than 3 vertices"));
-    if (st[0] & 4) return fail(pmh_set_error(PMH_ERR_RANGE, "a coordinate exceeds |2^20|"));
-    P->max_n = st[1];
-    if (cudaMalloc(&P->feat, sizeof(float2) * (size_t)(n_polys > 0 ? n_polys : 1)) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(pmh_set_error(PMH_ERR_NOMEM, "feature allocation failed"));
-    }
-    if (n_polys > 0) {
-        int blocks = (int)std::min<int64_t>((n_polys + 255) / 256, (int64_t)ctx->sm_count * 32);
-        poly_feat_kernel<<<blocks, 256, 0, s>>>(P->area2, P->offsets, n_polys, P->feat);
-        g_pmh_launches.fetch_add(1);
-        if ((e = cudaGetLastError()) != cudaSuccess)
-            return fail(pmh_set_error(PMH_ERR_CUDA, "feature kernel: %s", cudaGetErrorString(e)));
-    }
-    int rc = pmh_build_slabs(P, s);
-    if (rc == PMH_OK) rc = pmh_build_class_order(P, s);
-    if (rc != PMH_OK) return fail(rc);
     *out = P;
     return PMH_OK;
+}
+
+// the per-polygon products that a reload rebuilds (their sizes follow the data)
+static void free_derived(pmh_polys p)
+{
+    void* bufs[] = {p->slab_info, p->slab_ptr, p->slab_edges, p->order, p->order_cls, p->mask};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    p->slab_info = nullptr;
+    p->slab_ptr = p->slab_edges = nullptr;
+    p->order = p->order_cls = nullptr;
+    p->mask = nullptr;
+    p->n_indexed = p->n_staged_walk = 0;
+}
+
+extern "C" int pmh_poly_reload(pmh_polys polys, const int32_t* xy, const int64_t* offsets,
+                               int64_t n_polys, int64_t n_vertices, int host_memory, void* stream)
+{
+    if (!polys) return pmh_set_error(PMH_ERR_ARG, "null polygons");
+    PMH_TRY(pmh_check_device(polys->ctx));
+    if (n_polys != polys->n || n_vertices != polys->nv || (!xy && n_vertices > 0) || !offsets)
+        return pmh_set_error(PMH_ERR_ARG, "reload needs the set's own sizes (%lld polygons, %lld "
+                             "vertices; got %lld, %lld)", (long long)polys->n, (long long)polys->nv,
+                             (long long)n_polys, (long long)n_vertices);
+    cudaStream_t s = (cudaStream_t)stream;
+    PMH_CUDA_TRY(cudaStreamSynchronize(s));  // no kernel of this stream may still read the old data
+    free_derived(polys);
+    return upload_fill(polys, xy, offsets, host_memory != 0, s);
 }
 
 extern "C" int pmh_poly_upload(pmh_ctx ctx, const int32_t* d_xy, const int64_t* d_offsets,

@@ -372,6 +372,29 @@ extern "C" int pmh_band_keys(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
     return PMH_OK;
 }
 
+// hashes copied in, band keys, (band, key) entries radix-sorted with ids, full keys gathered
+static int index_fill(pmh_ctx ctx, pmh_index X, const uint32_t* d_hashes, cudaStream_t s)
+{
+    const int64_t n = X->n;
+    const pmh_params* params = &X->params;
+    const int bb = X->band_bits;
+    const int64_t entries = n * params->bands;
+    if (n == 0) return PMH_OK;
+    cudaError_t e = cudaMemcpyAsync(X->hashes, d_hashes, sizeof(uint32_t) * n * params->K,
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return pmh_set_error(PMH_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
+    PMH_TRY(pmh_band_keys(ctx, X->hashes, n, params, X->keys, s));
+    int blocks = (int)std::min<int64_t>((entries + 255) / 256, (int64_t)ctx->sm_count * 32);
+    fill_entries_kernel<<<blocks, 256, 0, s>>>(X->keys, n, (int)params->bands, bb, X->sorted_comp,
+                                                X->sorted_id);
+    PMH_LAUNCHED("fill_entries_kernel");
+    PMH_TRY(pmh_radix_sort_u32(ctx, X->sorted_comp, X->sorted_id, entries, 32, s));
+    gather_keys_kernel<<<blocks, 256, 0, s>>>(X->sorted_comp, X->sorted_id, X->keys, entries,
+                                               (int)params->bands, bb, X->sorted_key);
+    PMH_LAUNCHED("gather_keys_kernel");
+    return PMH_OK;
+}
+
 extern "C" int pmh_lsh_build(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
                              const pmh_params* params, pmh_index* out, void* stream)
 {
@@ -401,36 +424,23 @@ extern "C" int pmh_lsh_build(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
         pmh_index_destroy(X);
         return pmh_set_error(PMH_ERR_NOMEM, "index allocation failed (n=%lld)", (long long)n);
     }
-    int rc = PMH_OK;
-    if (n > 0) {
-        cudaError_t e = cudaMemcpyAsync(X->hashes, d_hashes, sizeof(uint32_t) * n * params->K,
-                                        cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
-        if (rc == PMH_OK) rc = pmh_band_keys(ctx, X->hashes, n, params, X->keys, stream);
-        if (rc == PMH_OK) {
-            int blocks = (int)std::min<int64_t>((entries + 255) / 256, (int64_t)ctx->sm_count * 32);
-            fill_entries_kernel<<<blocks, 256, 0, s>>>(X->keys, n, (int)params->bands, bb,
-                                                        X->sorted_comp, X->sorted_id);
-            g_pmh_launches.fetch_add(1);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "fill: %s", cudaGetErrorString(e));
-        }
-        if (rc == PMH_OK) rc = pmh_radix_sort_u32(ctx, X->sorted_comp, X->sorted_id, entries, 32, s);
-        if (rc == PMH_OK) {
-            int blocks = (int)std::min<int64_t>((entries + 255) / 256, (int64_t)ctx->sm_count * 32);
-            gather_keys_kernel<<<blocks, 256, 0, s>>>(X->sorted_comp, X->sorted_id, X->keys, entries,
-                                                       (int)params->bands, bb, X->sorted_key);
-            g_pmh_launches.fetch_add(1);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) rc = pmh_set_error(PMH_ERR_CUDA, "gather: %s", cudaGetErrorString(e));
-        }
-    }
+    int rc = index_fill(ctx, X, d_hashes, s);
     if (rc != PMH_OK) {
         pmh_index_destroy(X);
         return rc;
     }
     *out = X;
     return PMH_OK;
+}
+
+extern "C" int pmh_lsh_rebuild(pmh_ctx ctx, pmh_index index, const uint32_t* d_hashes, int64_t n,
+                               void* stream)
+{
+    PMH_TRY(pmh_check_device(ctx));
+    if (!index || index->ctx != ctx || n != index->n || (n > 0 && !d_hashes))
+        return pmh_set_error(PMH_ERR_ARG, "rebuild needs the index's own context and size (%lld)",
+                             index ? (long long)index->n : 0ll);
+    return index_fill(ctx, index, d_hashes, (cudaStream_t)stream);
 }
 
 extern "C" int pmh_index_destroy(pmh_index X)
