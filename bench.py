@@ -1,20 +1,28 @@
 """PolyMinHash benchmark: one step = one pass of the whole signature path over one batch.
 
-Step (device-resident inputs): upload + preprocessing of the database polygons (A0),
-MinHash signatures (A1), band keys + bucket index (A2, A3), the same for the query
-batch, bucket join (A4), agreement estimate (A5), top-m by agreement (A6), exact
-fp64 refinement to the top-10 (A8).  Workload: 1,000,000 star polygons (16-256 vertices,
-area fraction log-uniform 1e-4..1e-2), K = 128, 16 bands x 8 rows, 10,000 perturbed-copy
-queries, synthetic and seeded.
+Step (inputs resident in HBM when the timed region starts): the database polygons are
+loaded into the library's polygon set and prepared (A0: validation, boxes, areas, y-slab
+lists, signing plan), signed (A1: one persistent launch of the unified kernel through the
+stream index), their band keys and bucket index rebuilt (A2, A3); then the query set runs
+in batches of 4,096 through the captured query graph (A9): prep, signing, bucket join
+(A4), agreement (A5), a shortlist by agreement count rescored by the learned reranker
+(A7) to the top-m (A6), and exact fp64 refinement to the top-10 (A8).  Default workload:
+the combined configuration -- 10,000,000 star / fractal polygons with 8-1,024 vertices
+(16.7 GB of int32 vertices), area fractions log-uniform 1e-5..1e-2, K = 128, 16 bands x 8
+rows, 100,000 perturbed-copy queries -- synthetic and seeded.
 
 value = (N + Q) * K polygon-hashes per second of step time.  `e2e` is the same step
-through the C ABI from pinned HOST buffers (host-to-device copies and the device-to-host
-read of the top-10 inside the timed region).  `roofline` is the dominant kernel (A1
-signing) against the measured integer-ALU peak.
+from pinned HOST buffers (the database and every query batch copied to the device, the
+refined top-10 of every batch copied back, inside the timed region).  `roofline` is the
+dominant kernel (the signing launch) against the measured integer-ALU peak, with its L2
+and DRAM traffic from the committed ncu summary of the same kernel source.
+`search` (after the timed region) is queries/s at recall@10 >= 0.9 of the plain
+(agreement-count) and learned (reranker) forms, both through the graph, over band shapes.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -35,13 +43,17 @@ sys.path.insert(0, ROOT)
 #    extraction and half-open bbox test (6) = 26;
 #  grid cell read by the indexed form: two offsets and the cell address = 8;
 #  stream-index entry read: index and point loads, limit compare, bbox test = 10;
-#  bbox candidate ordered (one warp argmin step) = 6;
+#  bbox candidate classified = 6;
 #  polygon edge tested: straddle test (3), two 32x32->64 products (4), difference (2),
 #    sign test and parity (3) = 12;
 #  candidate decided by the coverage mask: cell address and code lookup = 6.
-INT_OPS_PER_POINT = 26
 SIGN_OP_WEIGHTS = {"walk_points": 26, "cells": 8, "index_entries": 10, "candidates": 6,
                    "edge_tests": 12, "mask_decisions": 6}
+# the signing kernel's sources: a profile summary applies only to the source it was taken on
+SIGN_SOURCES = ["paper_2511_16576_gb300/csrc/sign_unified.cu",
+                "paper_2511_16576_gb300/csrc/sign_common.cuh",
+                "paper_2511_16576_gb300/csrc/pmh_internal.cuh"]
+SIGN_PROFILE = "profiles/sign_unified_kernel_combined.md"
 
 
 def parse():
@@ -50,10 +62,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scale")
+    ap.add_argument("--workload", default="combined")
     ap.add_argument("--n-polys", type=int, default=None, help="override database size")
     ap.add_argument("--n-queries", type=int, default=None)
-    ap.add_argument("--topm", type=int, default=32)
+    ap.add_argument("--batch", type=int, default=4096, help="queries per graph replay")
+    ap.add_argument("--topm", type=int, default=32, help="candidates refined per query")
+    ap.add_argument("--shortlist", type=int, default=64, help="learned form: count shortlist")
+    ap.add_argument("--plain", action="store_true", help="time the plain form (no reranker)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=None, help="polygons in the CPU sample")
@@ -63,14 +78,15 @@ def parse():
                     help="sign by walking every stream point (no stream index)")
     ap.add_argument("--eval-queries", type=int, default=1000,
                     help="queries whose recall@10 is checked against brute force")
-    ap.add_argument("--train-queries", type=int, default=4000)
+    ap.add_argument("--train-queries", type=int, default=16000,
+                    help="training queries of the reranker (x shortlist pairs)")
     ap.add_argument("--paper-sweep", action="store_true",
                     help="paper-shaped centred sets, one hashmap keyed on m = 1..5 hashes (prints one "
                          "JSON line with the table instead of the benchmark line)")
     ap.add_argument("--paper-scale", type=float, default=1.0, help="fraction of the paper set sizes")
     ap.add_argument("--paper-sets", default="n9,n12,n95",
                     help="paper-shaped sets of the sweep (n319 needs an exhaustive search over "
-                         "319-vertex pairs: hours at full size)")
+                         "319-vertex pairs: run it with --paper-scale)")
     return ap.parse_args()
 
 
@@ -270,13 +286,16 @@ def hbm_peak_gbs():
 
 def arm_config(args, w, db, Q, world):
     """The workload both arms report (the reference arm runs a sample of it)."""
-    return {"workload": f"{w.name}: {db.n} star polygons ({db.n_vertices} vertices), K={w.K}, "
-                        f"{w.bands}x{w.rows} bands, {Q} perturbed-copy queries, "
-                        f"top-{args.topm} refined to top-10",
+    return {"workload": f"{w.name}: {db.n} {'fractal ' if w.fractal else ''}star polygons "
+                        f"({db.n_vertices} vertices, {w.n_range[0]}-{w.n_range[1]} per polygon), "
+                        f"K={w.K}, {w.bands}x{w.rows} bands, {Q} perturbed-copy queries in batches of "
+                        f"{args.batch}, {'plain' if args.plain else 'learned'} top-{args.topm} "
+                        f"refined to top-10",
             "l2": (f"inputs larger than L2 ({db.xy.nbytes / 1e6:.0f} MB of vertices)"
                    if db.xy.nbytes > 129e6 else
                    f"inputs smaller than L2 ({db.xy.nbytes / 1e6:.0f} MB of vertices), L2 not flushed"),
-            "parallelism": f"{world} independent shard(s)"}
+            "parallelism": f"{world} shard(s), one exchange of the query batches" if world > 1
+            else "1 GPU"}
 
 
 def run_reference(args, w):
@@ -339,48 +358,96 @@ def cpu_baseline(w, db, seconds_target=15.0, n_sample=None):
                       f"{db.n}-polygon workload ({dt:.1f} s, {cores} threads)"}
 
 
-def search_quality(args, w, B, ctx, db, qs, h, d_xy, d_off, q_xy, q_off, P):
-    """queries/s at recall@10 >= 0.9, plain (agreement count) vs learned (reranker) ranking.
+def sources_sha(paths) -> str:
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
-    Runs after the timed region.  The same signatures are indexed with K x 1, K/2 x 2 and
-    K/4 x 4 bands (short bands make more polygons candidates) and with the workload's own
-    banding; for each shape the top-m sweep gives recall@10 and queries/s.  The best
-    queries/s reaching recall 0.9 is reported per form."""
+
+def read_profile(path: str) -> dict:
+    """`key: value` lines of a committed ncu summary (empty if absent)."""
+    out = {}
+    try:
+        with open(os.path.join(ROOT, path)) as f:
+            for line in f:
+                line = line.strip().lstrip("-* ").strip("`")
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    out[k.strip()] = v.strip()
+    except OSError:
+        pass
+    return out
+
+
+def profiled_counters(polys_in_launch: int) -> dict | None:
+    """DRAM and L2 bytes and instructions per launch of the signing kernel, from the ncu
+    summary taken on this same kernel source (scaled by polygons to this launch), else None."""
+    p = read_profile(SIGN_PROFILE)
+    if not p or p.get("source_sha") != sources_sha(SIGN_SOURCES):
+        return None
+    try:
+        scale = polys_in_launch / float(p["launch_polygons"])
+        return {"dram_bytes": float(p["dram_bytes"]) * scale, "lts_bytes": float(p["lts_bytes"]) * scale,
+                "inst_executed": float(p["inst_executed"]) * scale,
+                "l2_throughput_pct": float(p["l2_throughput_pct"]),
+                "dram_throughput_pct": float(p["dram_throughput_pct"]),
+                "captured_on": p.get("workload"), "scale": scale}
+    except (KeyError, ValueError):
+        return None
+
+
+def search_quality(args, w, B, ctx, db, qs, h, dbp, q_xy, q_off, P):
+    """queries/s at recall@10 >= 0.9 of the plain (agreement count) and learned (reranker)
+    forms, both through the captured query graph in batches (after the timed region).
+
+    The database signatures are indexed with 64 x 2, 32 x 4 and the workload's 16 x 8
+    bands (short bands make more polygons candidates); for each shape the top-m sweep gives
+    recall@10 on the first eval queries (ground truth: the GPU brute force -- every
+    box-overlapping polygon, exact fp64 Jaccard) and queries/s over all queries; the
+    reranker is trained on the shortlists of separate training queries (GPU kernels, Adam)
+    for each shape.  The best queries/s reaching recall 0.9 is reported per form."""
     import torch
     from paper_2511_16576_gb300 import evaluate as ev
     from paper_2511_16576_gb300 import synth
-    dev = d_xy.device
-    dbp = B.poly_upload(ctx, d_xy, d_off)
-    qp = B.poly_upload(ctx, q_xy, q_off)
+    dev = q_xy.device
     n_eval = min(args.eval_queries, qs.n)
     qe = qs.subset(np.arange(n_eval))
     qep = B.poly_upload(ctx, torch.from_numpy(qe.xy).to(dev), torch.from_numpy(qe.offsets).to(dev))
     truth, t_bf = ev.timed(lambda: ev.brute_force_topk(ctx, qep, dbp, 10))
-    out = {"eval_queries": n_eval, "timed_queries": qs.n, "k": 10, "target_recall": 0.9,
-           "bf_pairs_per_query": truth.pairs / n_eval, "bf_seconds_eval_queries": t_bf,
-           "forms": {}}
+    qep.close()
+    qp = B.poly_upload(ctx, q_xy, q_off)
+    batches = ev.make_batches(q_xy, qs.offsets, args.batch)
     tq = synth.perturbed_queries(db, args.train_queries, w.query_seed + 1000)
     tp = B.poly_upload(ctx, torch.from_numpy(tq.xy).to(dev), torch.from_numpy(tq.offsets).to(dev))
-    shapes = [b for b in (w.K, w.K // 2, w.K // 4) if b >= 1 and w.K % b == 0] + [w.bands]
-    for bands in shapes:
-        params = B.make_params(w.K, bands, w.T, w.seed, w.lsh_seed)
+    out = {"eval_queries": n_eval, "timed_queries": qs.n, "batch": args.batch, "k": 10,
+           "target_recall": 0.9, "bf_pairs_per_query": truth.pairs / n_eval,
+           "bf_seconds_eval_queries": t_bf, "forms": {}}
+    ms = (10, 12, 14, 16, 18, 20, 22, 24, 28, 32)   # refined to the top-10: m >= 10
+    shapes = [b for b in (w.K // 2, w.K // 4, w.bands) if b >= 1 and w.K % b == 0]
+    for bands in dict.fromkeys(shapes):
+        params = B.make_params(w.K, bands, w.T, w.seed, w.lsh_seed, P.flags)
         index = B.lsh_build(ctx, h, params)
-        s = ev.Searcher(ctx, index, params, dbp, h)
+        cap = ev.batch_capacity(ctx, index, params, qp, args.batch)
         key = f"{params.bands}x{params.rows}"
-        plain = ev.sweep(s, qp, truth, n_eval, learned=False)
-        res = {"bands": key, "plain_curve": plain, "plain": ev.best_at_recall(plain)}
-        if bands != w.bands:
-            feat, lab = ev.training_pairs(ctx, s, tp)
-            s.reranker = B.Reranker(ctx, seed=1)
-            (losses, t_train) = ev.timed(lambda: ev.train_reranker(s.reranker, feat, lab))
-            learned = ev.sweep(s, qp, truth, n_eval, learned=True)
-            res.update({"learned_curve": learned, "learned": ev.best_at_recall(learned),
-                        "train_pairs": int(feat.shape[0]), "train_loss_per_epoch": losses,
-                        "train_seconds": t_train})
-            s.reranker.close()
-        out["forms"][key] = res
+        plain = ev.graph_sweep(ctx, index, dbp, batches, cap, truth, n_eval, ms)
+        s = ev.Searcher(ctx, index, params, dbp, h, shortlist=args.shortlist)
+        feat, lab = ev.training_pairs(ctx, s, tp)
+        rr = B.Reranker(ctx, seed=1)
+        (losses, t_train) = ev.timed(lambda: ev.train_reranker(rr, feat, lab, epochs=16))
+        learned = ev.graph_sweep(ctx, index, dbp, batches, cap, truth, n_eval, ms, rerank=rr,
+                                 shortlist=args.shortlist)
+        rr.close()
+        out["forms"][key] = {"bands": key, "candidates_per_query_cap": cap / args.batch,
+                             "plain_curve": plain, "plain": ev.best_at_recall(plain),
+                             "learned_curve": learned, "learned": ev.best_at_recall(learned),
+                             "train_pairs": int(feat.shape[0]), "train_loss_per_epoch": losses,
+                             "train_seconds": t_train}
+        del feat, lab
         index.close()
     tp.close()
+    qp.close()
     for form in ("plain", "learned"):
         best = [(f[form], k) for k, f in out["forms"].items() if f.get(form)]
         if best:
@@ -388,10 +455,27 @@ def search_quality(args, w, B, ctx, db, qs, h, d_xy, d_off, q_xy, q_off, P):
             out[form] = {"bands": k, **r}
         else:
             out[form] = None
-    qep.close()
-    qp.close()
-    dbp.close()
+    if out["plain"] and out["learned"]:
+        out["learned_over_plain_qps"] = out["learned"]["qps"] / out["plain"]["qps"]
     return out
+
+
+def train_for_step(args, w, B, ctx, db, dbp, h, index, P):
+    """The reranker of the timed step: trained (untimed) on the shortlists of separate
+    training queries at the step's own banding."""
+    import torch
+    from paper_2511_16576_gb300 import evaluate as ev
+    from paper_2511_16576_gb300 import synth
+    dev = torch.device("cuda", ctx.device)
+    n_train = min(args.train_queries, 8000)
+    tq = synth.perturbed_queries(db, n_train, w.query_seed + 2000)
+    tp = B.poly_upload(ctx, torch.from_numpy(tq.xy).to(dev), torch.from_numpy(tq.offsets).to(dev))
+    s = ev.Searcher(ctx, index, P, dbp, h, shortlist=args.shortlist)
+    feat, lab = ev.training_pairs(ctx, s, tp)
+    rr = B.Reranker(ctx, seed=1)
+    losses, secs = ev.timed(lambda: ev.train_reranker(rr, feat, lab, epochs=8))
+    tp.close()
+    return rr, {"pairs": int(feat.shape[0]), "loss_per_epoch": losses, "seconds": secs}
 
 
 def main():
@@ -415,23 +499,32 @@ def main():
         dist.init_process_group("nccl")
     from paper_2511_16576_gb300 import binding as B
     from paper_2511_16576_gb300 import build as cuda_build
+    from paper_2511_16576_gb300 import dist as D
+    from paper_2511_16576_gb300 import evaluate as ev
     cuda_build.build()
 
     dev = torch.device("cuda", local)
-    # every rank signs its own shard of the same size (weak scaling)
-    from paper_2511_16576_gb300 import dist as D
+    # every rank signs and indexes its own shard of the same size (weak scaling)
     gen_w = D.shard_workload(w, rank)
+    t_gen = time.perf_counter()
     db = synth.make_database(gen_w, args.n_polys)
     qs = synth.make_queries(gen_w, db, args.n_queries)
+    t_gen = time.perf_counter() - t_gen
     N, Q, K = db.n, qs.n, w.K
     P = B.make_params(K, w.bands, w.T, w.seed, w.lsh_seed,
                       0 if args.no_stream_index else B.FLAG_STREAM_INDEX)
     ctx = B.Context(local)
     stream = torch.cuda.current_stream()
 
+    # the stream index (once per seed and K), timed on its own
+    sidx_ms = None
+    if not args.no_stream_index:
+        _, t = ev.timed(lambda: B.stream_index_build(ctx, P))
+        sidx_ms = t * 1e3
+
     autotune = None
     if not args.no_autotune:
-        # pick the signing-kernel shape on a 2 % sample of the workload (cached per GPU/K/workload)
+        # the walk kernel's shape, picked on a 0.2 % sample of the workload (cached per GPU/K)
         sample = db.subset(np.linspace(0, db.n - 1, max(1, min(db.n, 20000)), dtype=np.int64))
         sp = B.poly_upload(ctx, torch.from_numpy(sample.xy).to(dev),
                            torch.from_numpy(sample.offsets).to(dev))
@@ -443,61 +536,87 @@ def main():
     d_xy = torch.from_numpy(db.xy).to(dev)
     d_off = torch.from_numpy(db.offsets).to(dev)
     q_xy = torch.from_numpy(qs.xy).to(dev)
-    q_off = torch.from_numpy(qs.offsets).to(dev)
-    ev = {}
+    # the library's polygon set, signatures and bucket index: built once, then reloaded
+    # and rebuilt in place by every step (the query graph is captured on them)
+    dbp = B.poly_upload(ctx, d_xy, d_off)
+    h = B.minhash_sign(ctx, dbp, P)
+    index = B.lsh_build(ctx, h, P)
+    qp_all = B.poly_upload(ctx, q_xy, torch.from_numpy(qs.offsets).to(dev))
+    cap = ev.batch_capacity(ctx, index, P, qp_all, args.batch)
+    qp_all.close()
+    rr, train = (None, None) if args.plain else train_for_step(args, w, B, ctx, db, dbp, h, index, P)
+    batches = ev.make_batches(q_xy, qs.offsets, args.batch)
+    # with several ranks every rank searches the query batches of all ranks (gathered) on its
+    # own shard, so its graph holds world x the batch
+    shard_base = int(D.shard_offsets(N, dev)[rank]) if world > 1 else 0
+    g = B.QueryGraph(ctx, index, world * args.batch, world * batches.max_vertices, world * cap,
+                     args.topm, db=dbp, k=10, rerank=rr, shortlist=args.shortlist)
+
+    def local_search(allq, k):
+        g.run(allq.xy, allq.offsets)
+        n = allq.n
+        return g.ref_ids[:n].to(torch.int64), g.ref_j[:n]
+
+    def query_pass(src, out_ids, out_j):
+        """Every query batch through the graph (one rank), or through the exchange."""
+        if world == 1:
+            ev.run_batches(g, src, out_ids, out_j)
+            return
+        q0 = 0
+        for xy, off, n in zip(src.xy, src.off, src.n):
+            xy, off = xy.to(dev, non_blocking=True), off.to(dev, non_blocking=True)
+            gid, gj = D.global_search(local_search, D.QueryBatch(None, xy, off), shard_base, 10)
+            out_ids[q0:q0 + n].copy_(gid, non_blocking=True)
+            out_j[q0:q0 + n].copy_(gj, non_blocking=True)
+            q0 += n
+    res_ids = torch.empty((Q, 10), dtype=torch.int32, device=dev)
+    res_j = torch.empty((Q, 10), dtype=torch.float64, device=dev)
+    ev_sign = []
 
     def step(host: bool, record: bool):
         if host:
-            dbp = B.poly_upload_pinned(ctx, h_xy, h_off)
+            B.poly_reload(dbp, h_xy, h_off)
         else:
-            dbp = B.poly_upload(ctx, d_xy, d_off)
+            B.poly_reload(dbp, d_xy, d_off)
         if record:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             B.sign_timing(ctx, True)   # per-kernel events inside the call, no host sync
-        h = B.minhash_sign(ctx, dbp, P)
+        B.minhash_sign(ctx, dbp, P, out=h)
         if record:
             B.sign_timing(ctx, False)
             e1.record(stream)
-            ev.setdefault("sign", []).append((e0, e1))
-        index = B.lsh_build(ctx, h, P)
-        qp = B.poly_upload_pinned(ctx, hq_xy, hq_off) if host else B.poly_upload(ctx, q_xy, q_off)
-        qh = B.minhash_sign(ctx, qp, P)
-        row_ptr, cand = B.lsh_query(ctx, index, qh)
-        count, _ = B.jaccard_estimate(ctx, qh, h, row_ptr, cand, P, bandmask=False)
-        ids, nn = B.topm(ctx, row_ptr, cand, count, args.topm)
-        top_ids, top_j = B.refine_topk(ctx, qp, dbp, ids, nn, 10)
-        out = (h, cand, top_ids, top_j)
+            ev_sign.append((e0, e1))
+        B.lsh_rebuild(ctx, index, h)
         if host:
-            res_ids.copy_(top_ids, non_blocking=True)
-            res_j.copy_(top_j, non_blocking=True)
-        index.close()
-        qp.close()
-        dbp.close()
-        return out
+            query_pass(hbatches, hres_ids, hres_j)
+        else:
+            query_pass(batches, res_ids, res_j)
 
-    h_xy = torch.from_numpy(db.xy).pin_memory()
-    h_off = torch.from_numpy(db.offsets).pin_memory()
-    hq_xy = torch.from_numpy(qs.xy).pin_memory()
-    hq_off = torch.from_numpy(qs.offsets).pin_memory()
-    res_ids = torch.empty((Q, 10), dtype=torch.int32).pin_memory()
-    res_j = torch.empty((Q, 10), dtype=torch.float64).pin_memory()
+    h_xy = h_off = hbatches = hres_ids = hres_j = None
+    if not args.no_e2e:
+        h_xy = torch.from_numpy(db.xy).pin_memory()
+        h_off = torch.from_numpy(db.offsets).pin_memory()
+        hbatches = ev.make_batches(torch.from_numpy(qs.xy).pin_memory(), qs.offsets, args.batch,
+                                   pinned=True)
+        hres_ids = torch.empty((Q, 10), dtype=torch.int32).pin_memory()
+        hres_j = torch.empty((Q, 10), dtype=torch.float64).pin_memory()
 
     def timed(host: bool, steps: int, warmup: int, record: bool):
         for _ in range(warmup):
-            out = step(host, False)
+            step(host, False)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        ev.clear()
+        ev_sign.clear()
         l0 = B.launch_count()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         for _ in range(steps):
-            out = step(host, record)
+            step(host, record)
         t1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -505,70 +624,87 @@ def main():
         torch.cuda.synchronize()
         launches = B.launch_count() - l0
         ms = D.max_over_ranks(t0.elapsed_time(t1) / steps, dev)
-        return ms, launches, out
+        return ms, launches
 
     clocks = Clocks(local)
     clocks.start()
     B.sign_report(ctx)                     # forget events of earlier calls
-    ms, launches, out = timed(False, args.steps, args.warmup, True)
+    ms, launches = timed(False, args.steps, args.warmup, True)
     clk = clocks.stop()
-    h = out[0]
-    sign_ms = float(np.mean([a.elapsed_time(b) for a, b in ev.get("sign", [])]))
+    flags = g.status()[0]
+    sign_ms = float(np.mean([a.elapsed_time(b) for a, b in ev_sign]))
     kernel_ms = B.sign_report(ctx)         # mean per-kernel times of the timed database launches
+    found = float((res_ids[:, 0] >= 0).float().mean())
     e2e = None
     if not args.no_e2e:
-        ms_e2e, _, _ = timed(True, args.steps, max(3, args.warmup // 2 + 1), False)
-        h2d = db.xy.nbytes + db.offsets.nbytes + qs.xy.nbytes + qs.offsets.nbytes
-        d2h = res_ids.numel() * 4 + res_j.numel() * 8
+        ms_e2e, _ = timed(True, args.steps, args.warmup, False)
+        h2d = db.xy.nbytes + db.offsets.nbytes + qs.xy.nbytes + 8 * (Q + len(batches.n))
+        d2h = hres_ids.numel() * 4 + hres_j.numel() * 8
         e2e = {"value": world * (N + Q) * K / (ms_e2e * 1e-3), "unit": "hashes/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": ms_e2e}
+        same = torch.equal(hres_ids, res_ids.cpu())
+        e2e["results_equal_device_run"] = bool(same)
 
     # roofline of the dominant kernel: its algorithmic integer ops (work units it reports,
     # weighted as above) per launch / its mean CUDA-event time over the timed database
-    # launches, against the measured peak
+    # launches, against the measured integer peak; L2 / DRAM traffic from the ncu summary
     hashes_np = h.cpu().numpy().view(np.uint32)
     G = algorithmic_points(hashes_np, w.T)
-    dbp_w = B.poly_upload(ctx, d_xy, d_off)
-    B.minhash_sign(ctx, dbp_w, P)          # one more database launch, untimed, to read its work
+    B.minhash_sign(ctx, dbp, P, out=h)     # one more database launch, untimed, to read its work
     per_kernel = B.sign_report(ctx)        # work counts are fixed by the input: same as timed
-    dbp_w.close()
     peak = B.probe_int_peak(ctx)
     kernels = {}
     for name, kname in (("unified", "sign_unified_kernel"), ("walk", "sign_kernel")):
         units = per_kernel[name]["work"]
         ops = sum(SIGN_OP_WEIGHTS[k] * v for k, v in units.items())
         kms = kernel_ms[name]["ms"]
+        if kms <= 0.01 and ops == 0:
+            continue
         kernels[kname] = {"ms": kms, "work_units_per_launch": units, "int_ops_per_launch": ops,
                           "achieved": ops / (kms * 1e-3) / 1e12 if kms > 0 else None,
                           "frac": ops / (kms * 1e-3) / peak if kms > 0 else None}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
-    # DRAM bytes (read + write) of one sign_indexed_kernel launch from an ncu capture on
-    # the 200,000-polygon slice of this workload (399.3 MB), scaled by polygons to the
-    # 1,000,000-polygon launch; other sizes and kernels: not measured
-    traffic = 5 * 399.3e6 if dom == "sign_unified_kernel" and N == 1000000 and w.name == "scale" else None
+    units = kernels[dom]["work_units_per_launch"]
+    gather_bytes = 8 * (units["cells"] + units["index_entries"])
+    prof = profiled_counters(N) if dom == "sign_unified_kernel" else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": kernels[dom]["achieved"],
                 "peak": peak / 1e12, "unit": "Tintop/s", "frac": kernels[dom]["frac"],
-                "traffic": traffic, "traffic_note": "ncu dram__bytes_read.sum + dram__bytes_write.sum "
-                "of a 200,000-polygon launch x 5" if traffic else None,
+                "traffic": prof["dram_bytes"] if prof else None,
+                "traffic_note": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel "
+                                 f"source on {prof['captured_on']}, x {prof['scale']:.2f} by polygons "
+                                 f"({SIGN_PROFILE})") if prof else
+                "no ncu summary of this kernel source: not measured",
                 "op_weights": SIGN_OP_WEIGHTS,
                 "peak_source": "measured: pmh_probe_int_peak (integer mad/add/xor/shl mix, all SMs)",
                 "peak_nominal": nominal_int_peak(dev, clk),
                 "kernels": kernels, "timed_launches": kernel_ms["calls"],
-                "edge_tests_per_s": sum(k["work_units_per_launch"]["edge_tests"] for k in kernels.values())
-                / (sign_ms * 1e-3),
-                # the vertex stream (8 B per vertex, staged once per polygon by the signing kernels)
-                # against the measured HBM copy bandwidth: far from being the bound
+                # the index gather: cell records and entries read (8 B each), against the L2
+                # sector bytes ncu counted for the launch
+                "l2_gather": {"algorithmic_bytes": gather_bytes,
+                              "lts_bytes": prof["lts_bytes"] if prof else None,
+                              "lts_over_algorithmic": prof["lts_bytes"] / gather_bytes
+                              if prof and gather_bytes else None,
+                              "l2_throughput_pct_of_peak": prof["l2_throughput_pct"] if prof else None},
+                "dram_throughput_pct_of_peak": prof["dram_throughput_pct"] if prof else None,
+                "warp_inst_per_hash": prof["inst_executed"] / (N * K) if prof else None,
+                "edge_tests_per_s": units["edge_tests"] / (kernels[dom]["ms"] * 1e-3),
+                # the vertex stream (8 B per vertex, staged once per polygon by the signing
+                # kernel) against the measured HBM copy bandwidth: far from being the bound
                 "vertex_stream_gbs": db.xy.nbytes / (sign_ms * 1e-3) / 1e9,
                 "vertex_stream_frac_of_hbm": db.xy.nbytes / (sign_ms * 1e-3) / 1e9 / hbm_peak_gbs()
                 if hbm_peak_gbs() else None,
                 "sign_ms": sign_ms, "stream_points_resolved": G,
-                "stream_points_resolved_per_s": G / (sign_ms * 1e-3),
-                "walk_equivalent_tintops": INT_OPS_PER_POINT * G / (sign_ms * 1e-3) / 1e12}
+                "stream_points_resolved_per_s": G / (sign_ms * 1e-3)}
 
+    print(json.dumps({"timed_ms_per_step": ms, "sign_ms": sign_ms, "e2e": e2e, "launches": launches,
+                      "graph_status_flags": flags, "queries_with_a_result": found,
+                      "unified_kernel_ms": kernels.get("sign_unified_kernel", {}).get("ms")}),
+          file=sys.stderr, flush=True)
     search = None
-    if not args.no_search:
-        search = search_quality(args, w, B, ctx, db, qs, h, d_xy, d_off, q_xy, q_off, P)
+    if not args.no_search and world == 1:
+        search = search_quality(args, w, B, ctx, db, qs, h, dbp, q_xy,
+                                torch.from_numpy(qs.offsets).to(dev), P)
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -582,17 +718,26 @@ def main():
         "data": "synthetic",
         "config": arm_config(args, w, db, Q, world),
         "sign_hashes_per_s": world * N * K / (sign_ms * 1e-3),
-        "candidates_per_query": float(out[1].numel()) / Q,
+        "stream_index_build_ms": sidx_ms,
+        "queries_per_s_in_step": world * Q / (ms * 1e-3),
+        "query_batches_per_step": len(batches.n),
+        "graph_status_flags": flags,
+        "queries_with_a_result": found,
+        "reranker_training": train,
         "roofline": roofline,
         "cpu_baseline": base,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "autotune": autotune,
         "search": search,
+        "generation_seconds": t_gen,
         "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    g.close()
+    if rr is not None:
+        rr.close()
     ctx.close()
     if world > 1:
         dist.destroy_process_group()

@@ -60,6 +60,7 @@ extern "C" {
 typedef struct pmh_ctx_s* pmh_ctx;
 typedef struct pmh_polys_s* pmh_polys;
 typedef struct pmh_index_s* pmh_index;
+typedef struct pmh_rerank_s* pmh_rerank;
 
 /* Signature and banding parameters.
  *   seed      global stream seed (Sec. 3.2: fixed seeds per hash function)
@@ -295,13 +296,17 @@ int pmh_sign_variant_info(int variant, int* points_per_lane, int* warps_per_bloc
  * launch of the unified kernel: through the stream index when the index's
  * params carry PMH_FLAG_STREAM_INDEX, which this call builds if needed and
  * which must not be rebuilt for other parameters while the graph lives) ->
- * A4 join -> A5 agreement -> A6 top-m (m per query) and, if k > 0, A8 exact
+ * A4 join -> A5 agreement -> A6 top-m per query -> (k > 0) A8 exact
  * refinement of the top-m lists to the top-k by (J desc, id asc) against the
- * polygon set `db` (which, like `index`, must outlive the graph), for batches
- * of at most max_queries polygons holding at most max_vertices vertices.  The
- * slab lists get fixed buffers (a table entry per slab, four list entries per
- * vertex); a polygon whose lists do not fit is tested over all its edges.
- * Synchronises; 0 <= k <= m <= 1024.
+ * polygon set cfg->db, for batches of at most max_queries polygons holding at
+ * most max_vertices vertices.  With cfg->rerank (A7, learned form) the top-m
+ * are the m best by the reranker's predicted Jaccard among the `shortlist`
+ * best by agreement count (m <= shortlist <= 1024, K a multiple of 32, db the
+ * polygon set `index` was built from); the reranker's weights are read at
+ * every replay, so later training is seen.  `index`, db and the reranker must
+ * outlive the graph.  The slab lists get fixed buffers (a table entry per
+ * slab, four list entries per vertex); a polygon whose lists do not fit is
+ * tested over all its edges.  Synchronises; 0 <= k <= m <= 1024.
  * pmh_qgraph_run copies one batch (xy int32 [n_vertices][2], offsets int64
  * [n_queries + 1], HOST arrays if host_memory != 0, else device) into the
  * graph's inputs and replays the graph on `stream`: it neither allocates nor
@@ -320,8 +325,16 @@ int pmh_sign_variant_info(int variant, int* points_per_lane, int* warps_per_bloc
  * cand_capacity, rows not written, agreement, top-m and refinement skipped)
  * and its candidate total. */
 typedef struct pmh_qgraph_s* pmh_qgraph;
-int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, pmh_polys db, int64_t max_queries,
-                      int64_t max_vertices, int64_t cand_capacity, int32_t m, int32_t k,
+typedef struct {
+    int64_t max_queries, max_vertices, cand_capacity;
+    int32_t m;           /* candidates per query kept for refinement (top-m) */
+    int32_t k;           /* refined top-k (0: no refinement) */
+    pmh_polys db;        /* the indexed polygon set (refinement, learned features) */
+    pmh_rerank rerank;   /* learned form (NULL: rank by agreement count) */
+    int32_t shortlist;   /* learned form: candidates by count rescored per query */
+    int32_t reserved;
+} pmh_qgraph_config;
+int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_config* cfg,
                       pmh_qgraph* out);
 int pmh_qgraph_run(pmh_qgraph graph, const int32_t* xy, const int64_t* offsets, int64_t n_queries,
                    int64_t n_vertices, int host_memory, void* stream);
@@ -332,27 +345,34 @@ int pmh_qgraph_refined(pmh_qgraph graph, int32_t** d_top_ids, double** d_top_j);
 int pmh_qgraph_status(pmh_qgraph graph, int* h_flags, int64_t* h_total, void* stream);
 int pmh_qgraph_destroy(pmh_qgraph graph);
 
-/* A7 -- learned reranker (not in the paper): an MLP 37 -> 64 -> 64 -> 1
+/* A7 -- learned reranker (not in the paper): an MLP 40 -> 64 -> 64 -> 1
  * (ReLU, ReLU, sigmoid) predicting the Jaccard similarity of a (query,
  * candidate) pair, trained on the GPU by mean squared error against exact
  * Jaccard.  bf16 weights and activations on the tensor cores, fp32
  * accumulation and fp32 master weights (Adam).
- * Packed parameter layout (PMH_RERANK_PARAMS floats): w1 [64][37] (out, in),
+ * Packed parameter layout (PMH_RERANK_PARAMS floats): w1 [64][40] (out, in),
  * b1 [64], w2 [64][64], b2 [64], w3 [64], b3 [1].
  * Features (pmh_rerank_features): bf16 [E][48] per CSR pair, columns
  *   0..31 group-match bits (group j = hashes j*K/32 .. (j+1)*K/32-1 all equal
  *          and not T), 32 agreement count / K, 33-34 log2(area) / 32 of query
- *          and candidate, 35-36 log2(vertex count) / 16, 37..47 zero.
+ *          and candidate, 35-36 log2(vertex count) / 16, 37 / 38 the number
+ *          of hashes with h_k(query) < h_k(candidate) / h_k(query) >
+ *          h_k(candidate), over K, 39 the upper bound m / (|q| + |p| - m) of
+ *          J with m = min(|q|, |p|, overlap area of the two bounding boxes),
+ *          40..47 zero.  By the min form of the hash (Theorem 1's proof),
+ *          h_k(q) < h_k(p) happens with probability area(q \ p) / area(q u p)
+ *          and h_k(q) > h_k(p) with area(p \ q) / area(q u p): with the exact
+ *          areas, the two counts sharpen the estimate of the overlap where the
+ *          areas differ; the bound is a geometric prior the hashes lack.
  *   K must be a multiple of 32.
  * pmh_rerank_forward writes a score in (0, 1) per feature row (feed it to
  * pmh_topm as d_score).  pmh_rerank_gradients computes the loss (mean over
  * n_rows) and the packed gradients of one batch into the reranker (and
  * copies them to d_grads / d_loss when not NULL); pmh_rerank_adam_step
  * applies them.  set/get move the packed fp32 master weights (synchronise). */
-#define PMH_RERANK_IN 37
+#define PMH_RERANK_IN 40
 #define PMH_RERANK_HIDDEN 64
-#define PMH_RERANK_PARAMS 6657
-typedef struct pmh_rerank_s* pmh_rerank;
+#define PMH_RERANK_PARAMS 6849
 int pmh_rerank_create(pmh_ctx ctx, pmh_rerank* out);
 int pmh_rerank_destroy(pmh_rerank r);
 int pmh_rerank_set_weights(pmh_rerank r, const float* h_params);

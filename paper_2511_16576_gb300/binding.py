@@ -36,6 +36,13 @@ class Params(ctypes.Structure):
                 ("reserved", ctypes.c_uint32)]
 
 
+class QGraphConfig(ctypes.Structure):
+    _fields_ = [("max_queries", ctypes.c_int64), ("max_vertices", ctypes.c_int64),
+                ("cand_capacity", ctypes.c_int64), ("m", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("db", ctypes.c_void_p), ("rerank", ctypes.c_void_p), ("shortlist", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 FLAG_STREAM_INDEX = 1
 FLAG_COVERAGE_MASK = 2
 
@@ -86,7 +93,7 @@ _SIGS = {
     "pmh_sign_set_variant": (ctypes.c_int, [_P, ctypes.c_int]),
     "pmh_sign_variant_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_int)]),
-    "pmh_qgraph_create": (ctypes.c_int, [_P, _P, _P, _i64, _i64, _i64, _i32, _i32, ctypes.POINTER(_P)]),
+    "pmh_qgraph_create": (ctypes.c_int, [_P, _P, ctypes.POINTER(QGraphConfig), ctypes.POINTER(_P)]),
     "pmh_qgraph_refined": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "pmh_qgraph_run": (ctypes.c_int, [_P, _P, _P, _i64, _i64, ctypes.c_int, _P]),
     "pmh_qgraph_outputs": (ctypes.c_int, [_P] + [ctypes.POINTER(_P)] * 6),
@@ -547,12 +554,14 @@ class QueryGraph:
     batch."""
 
     def __init__(self, ctx: Context, index: Index, max_queries: int, max_vertices: int,
-                 cand_capacity: int, m: int, db: "Polys | None" = None, k: int = 0):
+                 cand_capacity: int, m: int, db: "Polys | None" = None, k: int = 0,
+                 rerank: "Reranker | None" = None, shortlist: int = 64):
         h = _P()
-        _check(load().pmh_qgraph_create(ctx.handle, index.handle, db.handle if db else None,
-                                        max_queries, max_vertices, cand_capacity, m, k,
-                                        ctypes.byref(h)))
-        self.ctx, self.index, self.db, self.handle = ctx, index, db, h
+        cfg = QGraphConfig(max_queries, max_vertices, cand_capacity, m, k,
+                           db.handle if db else None, rerank.handle if rerank else None,
+                           shortlist if rerank else 0, 0)
+        _check(load().pmh_qgraph_create(ctx.handle, index.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self.ctx, self.index, self.db, self.rerank, self.handle = ctx, index, db, rerank, h
         ctx._adopt(self)
         self.max_queries, self.m, self.k, self.K = max_queries, m, k, index.params.K
         ptrs = [_P() for _ in range(6)]
@@ -609,7 +618,7 @@ class QueryGraph:
 
 
 # --------------------------------------------------------------------------- A7
-RERANK_IN, RERANK_HIDDEN, RERANK_PARAMS, RERANK_FEAT_COLS = 37, 64, 6657, 48
+RERANK_IN, RERANK_HIDDEN, RERANK_PARAMS, RERANK_FEAT_COLS = 40, 64, 6849, 48
 
 
 def unpack_params(flat):

@@ -191,10 +191,12 @@ int pmh_launch_prep(int sm_count, const int2* xy, const int64_t* off, int64_t n_
     return PMH_OK;
 }
 
-// per-polygon reranker inputs: log2(area) / 32 and log2(vertex count) / 16
+// per-polygon reranker inputs: log2(area) / 32 and log2(vertex count) / 16 (polygons
+// below the device-side count d_n, when given)
 __global__ void poly_feat_kernel(const int64_t* __restrict__ area2, const int64_t* __restrict__ off,
-                                 int64_t n, float2* __restrict__ out)
+                                 int64_t n, const int64_t* __restrict__ d_n, float2* __restrict__ out)
 {
+    if (d_n) n = min(n, *d_n);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const long long a2 = area2[p];
@@ -233,13 +235,23 @@ static int upload_fill(pmh_polys P, const int32_t* xy, const int64_t* offsets, b
     P->max_n = st[1];
     if (n_polys > 0) {
         int blocks = (int)std::min<int64_t>((n_polys + 255) / 256, (int64_t)ctx->sm_count * 32);
-        poly_feat_kernel<<<blocks, 256, 0, s>>>(P->area2, P->offsets, n_polys, P->feat);
+        poly_feat_kernel<<<blocks, 256, 0, s>>>(P->area2, P->offsets, n_polys, nullptr, P->feat);
         g_pmh_launches.fetch_add(1);
         if ((e = cudaGetLastError()) != cudaSuccess)
             return pmh_set_error(PMH_ERR_CUDA, "feature kernel: %s", cudaGetErrorString(e));
     }
     PMH_TRY(pmh_build_slabs(P, s));
     return pmh_build_class_order(P, s);
+}
+
+int pmh_launch_poly_feat(int sm_count, const int64_t* area2, const int64_t* off, int64_t n,
+                         const int64_t* d_n, float2* out, cudaStream_t s)
+{
+    if (n <= 0) return PMH_OK;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count * 32);
+    poly_feat_kernel<<<blocks, 256, 0, s>>>(area2, off, n, d_n, out);
+    PMH_LAUNCHED("poly_feat_kernel");
+    return PMH_OK;
 }
 
 static int upload_common(pmh_ctx ctx, const int32_t* xy, const int64_t* offsets, int64_t n_polys,

@@ -30,9 +30,8 @@ __global__ void __launch_bounds__(kAgreeWarps * 32)
 agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ ph,
                   const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cand, int64_t Q,
                   int64_t cap, int K, int bands, int rows, uint32_t T, uint16_t* __restrict__ count,
-                  uint32_t* __restrict__ bandmask, __nv_bfloat16* __restrict__ feat,
-                  const float2* __restrict__ qfeat, const float2* __restrict__ pfeat,
-                  const int* __restrict__ d_flags)
+                  uint32_t* __restrict__ bandmask, __nv_bfloat16* __restrict__ feat, FeatSrc qf,
+                  FeatSrc pf, const int* __restrict__ d_flags)
 {
     __shared__ __align__(16) uint32_t qs[kMaxK];
     __shared__ uint32_t eqbits[kAgreeWarps][kMaxK / 32];
@@ -47,7 +46,7 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
         for (int64_t x = b + wid; x < e; x += kAgreeWarps) {
             const int64_t p = cand[x];
             const uint32_t* bp = ph + p * K;
-            int c = 0;
+            int c = 0, lt = 0, gt = 0;  // lt / gt: hashes with h(q) < h(p) / h(q) > h(p)
             if ((K & 3) == 0) {
                 const uint4* a4 = reinterpret_cast<const uint4*>(qs);
                 const uint4* b4 = reinterpret_cast<const uint4*>(bp);
@@ -60,6 +59,10 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
                                ((unsigned)((u.y == v.y) & (u.y != T)) << 1) |
                                ((unsigned)((u.z == v.z) & (u.z != T)) << 2) |
                                ((unsigned)((u.w == v.w) & (u.w != T)) << 3);
+                        if (feat) {
+                            lt += (u.x < v.x) + (u.y < v.y) + (u.z < v.z) + (u.w < v.w);
+                            gt += (u.x > v.x) + (u.y > v.y) + (u.z > v.z) + (u.w > v.w);
+                        }
                     }
                     c += __popc(bits);
                     // hash 4i+t is bit (4i+t) % 32 of word i / 8: OR eight lanes' nibbles
@@ -75,11 +78,19 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
                     const bool eq = i < K && qs[i] == bp[i] && qs[i] != T;
                     const unsigned bal = __ballot_sync(0xffffffffu, eq);
                     c += eq;
+                    if (feat && i < K) {
+                        lt += qs[i] < bp[i];
+                        gt += qs[i] > bp[i];
+                    }
                     if (lane == 0) eqbits[wid][base / 32] = bal;
                 }
             }
             __syncwarp();
             c = __reduce_add_sync(0xffffffffu, c);
+            if (feat) {
+                lt = __reduce_add_sync(0xffffffffu, lt);
+                gt = __reduce_add_sync(0xffffffffu, gt);
+            }
             if (count && lane == 0) count[x] = (uint16_t)c;
             if (bandmask) {
                 bool all = lane < bands;
@@ -103,10 +114,25 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
                 if (lane < 16) {
                     float v = 0.f;
                     if (lane == 0) v = (float)c / (float)K;
-                    if (lane == 1) v = qfeat[q].x;
-                    if (lane == 2) v = pfeat[p].x;
-                    if (lane == 3) v = qfeat[q].y;
-                    if (lane == 4) v = pfeat[p].y;
+                    if (lane == 1) v = qf.feat[q].x;
+                    if (lane == 2) v = pf.feat[p].x;
+                    if (lane == 3) v = qf.feat[q].y;
+                    if (lane == 4) v = pf.feat[p].y;
+                    if (lane == 5) v = (float)lt / (float)K;
+                    if (lane == 6) v = (float)gt / (float)K;
+                    if (lane == 7) {
+                        // upper bound of J: the intersection is at most min(|q|, |p|, overlap of
+                        // the two bounding boxes)
+                        const int4 qb = qf.bbox[q], pb = pf.bbox[p];
+                        const float ow = (float)max(0, min(qb.z, pb.z) - max(qb.x, pb.x));
+                        const float oh = (float)max(0, min(qb.w, pb.w) - max(qb.y, pb.y));
+                        const long long qa = qf.area2[q], pa = pf.area2[p];
+                        const float a = 0.5f * (float)(qa < 0 ? -qa : qa);
+                        const float bq = 0.5f * (float)(pa < 0 ? -pa : pa);
+                        const float mn = fminf(fminf(a, bq), ow * oh);
+                        const float den = a + bq - mn;
+                        v = den > 0.f ? mn / den : 0.f;
+                    }
                     f[32 + lane] = __float2bfloat16_rn(v);
                 }
             }
@@ -182,18 +208,22 @@ topm_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ can
     if (threadIdx.x == 0) out_n[q] = kept;
 }
 
-// fixed-width lists (ids [Q][m], -1 padded, counts n[Q]) to compact CSR
-__global__ void list_counts_kernel(const int32_t* __restrict__ n, int64_t Q, int64_t* __restrict__ c)
+// fixed-width lists (ids [Q][m], -1 padded, counts n[Q]) to compact CSR; rows at or
+// past the device-side count d_n (optional) are empty
+__global__ void list_counts_kernel(const int32_t* __restrict__ n, int64_t Q,
+                                   const int64_t* __restrict__ d_n, int64_t* __restrict__ c)
 {
+    const int64_t live = d_n ? min(Q, *d_n) : Q;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < Q;
          q += (int64_t)gridDim.x * blockDim.x)
-        c[q] = n[q];
+        c[q] = q < live ? n[q] : 0;
 }
 
 __global__ void list_copy_kernel(const int32_t* __restrict__ ids, const int32_t* __restrict__ n,
-                                 int64_t Q, int m, const int64_t* __restrict__ row_ptr,
-                                 int32_t* __restrict__ cand)
+                                 int64_t Q, int m, const int64_t* __restrict__ d_n,
+                                 const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand)
 {
+    if (d_n) Q = min(Q, *d_n);
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < Q * m;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = t / m;
@@ -217,11 +247,19 @@ extern "C" int pmh_lists_to_csr(pmh_ctx ctx, const int32_t* d_ids, const int32_t
     }
     int64_t* counts = nullptr;
     PMH_TRY(pmh_scratch(ctx, SCR_QUERY, sizeof(int64_t) * (size_t)Q, (void**)&counts));
+    return pmh_launch_lists_to_csr(ctx, d_ids, d_n, Q, m, nullptr, counts, nullptr, d_row_ptr, d_cand, s);
+}
+
+int pmh_launch_lists_to_csr(pmh_ctx ctx, const int32_t* ids, const int32_t* n, int64_t Q, int32_t m,
+                            const int64_t* d_q, int64_t* counts, int64_t* sums, int64_t* row_ptr,
+                            int32_t* cand, cudaStream_t s)
+{
+    if (Q <= 0) return PMH_OK;
     const int blocks = (int)std::min<int64_t>((Q * m + 255) / 256, (int64_t)ctx->sm_count * 32);
-    list_counts_kernel<<<blocks, 256, 0, s>>>(d_n, Q, counts);
+    list_counts_kernel<<<blocks, 256, 0, s>>>(n, Q, d_q, counts);
     PMH_LAUNCHED("list_counts_kernel");
-    PMH_TRY(pmh_exclusive_scan_i64(ctx, counts, d_row_ptr, Q, s));
-    list_copy_kernel<<<blocks, 256, 0, s>>>(d_ids, d_n, Q, m, d_row_ptr, d_cand);
+    PMH_TRY(pmh_exclusive_scan_i64(ctx, counts, row_ptr, Q, s, sums));
+    list_copy_kernel<<<blocks, 256, 0, s>>>(ids, n, Q, m, d_q, row_ptr, cand);
     PMH_LAUNCHED("list_copy_kernel");
     return PMH_OK;
 }
@@ -231,20 +269,20 @@ int pmh_launch_agree(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph, const 
                      uint16_t* count, uint32_t* bandmask, const int* d_flags, cudaStream_t s)
 {
     return pmh_launch_agree_features(ctx, qh, ph, row_ptr, cand, Q, cap, P, count, bandmask, nullptr,
-                                     nullptr, nullptr, d_flags, s);
+                                     FeatSrc{}, FeatSrc{}, d_flags, s);
 }
 
 int pmh_launch_agree_features(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph,
                               const int64_t* row_ptr, const int32_t* cand, int64_t Q, int64_t cap,
                               const pmh_params* P, uint16_t* count, uint32_t* bandmask,
-                              uint16_t* feat, const float2* qfeat, const float2* pfeat,
-                              const int* d_flags, cudaStream_t s)
+                              uint16_t* feat, FeatSrc qf, FeatSrc pf, const int* d_flags,
+                              cudaStream_t s)
 {
     if (Q <= 0) return PMH_OK;
     const int blocks = (int)std::min<int64_t>(Q, (int64_t)ctx->sm_count * 16);
     agree_rows_kernel<<<blocks, kAgreeWarps * 32, 0, s>>>(
         qh, ph, row_ptr, cand, Q, cap, (int)P->K, (int)P->bands, (int)P->rows, P->T, count, bandmask,
-        reinterpret_cast<__nv_bfloat16*>(feat), qfeat, pfeat, d_flags);
+        reinterpret_cast<__nv_bfloat16*>(feat), qf, pf, d_flags);
     PMH_LAUNCHED("agree_rows_kernel");
     return PMH_OK;
 }

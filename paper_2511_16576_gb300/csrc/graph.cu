@@ -6,8 +6,10 @@
 // the stream index when the index's parameters ask for it), bucket join (A4,
 // count + scan + fill), agreement (A5), top-m (A6) and, with a database
 // polygon set, exact refinement of the top-m to the top-k (A8) are captured on
-// fixed, graph-owned buffers.  A replay copies the batch into the input
-// buffers, writes the batch size into a device word and launches the graph:
+// fixed, graph-owned buffers; with a reranker the top-m are chosen by its
+// predicted Jaccard among a shortlist by agreement count (A7, learned form).
+// A replay copies the batch into the input buffers, writes the batch size into
+// a device word and launches the graph:
 // no host synchronisation, no allocation.  Data-dependent sizes stay on the
 // device: kernels read the batch size from the device word, the slab lists of
 // a polygon that does not fit the fixed buffers are left out (that polygon is
@@ -45,6 +47,18 @@ struct pmh_qgraph_s {
     uint16_t* count16 = nullptr;
     int32_t* top_ids = nullptr;
     int32_t* top_n = nullptr;
+    // learned form: shortlist by count -> compact lists -> features -> scores
+    pmh_rerank rerank = nullptr;
+    int shortlist = 0;
+    int32_t* sl_ids = nullptr;
+    int32_t* sl_n = nullptr;
+    int64_t* sl_counts = nullptr;
+    int64_t* sl_sums = nullptr;
+    int64_t* sl_row_ptr = nullptr;
+    int32_t* sl_cand = nullptr;
+    float2* qfeat = nullptr;
+    uint16_t* feat = nullptr;
+    float* score = nullptr;
     double* jv = nullptr;             // exact J of the top-m lists
     int32_t* ref_ids = nullptr;       // refined top-k
     double* ref_j = nullptr;
@@ -75,28 +89,40 @@ extern "C" int pmh_qgraph_destroy(pmh_qgraph g)
                     g->slab_info, g->slab_sizes, g->slab_sums,  g->slab_ptr,  g->slab_cursor,
                     g->slab_edges, g->counts,    g->row_ptr,    g->cand,      g->count16,
                     g->top_ids,   g->top_n,      g->jv,         g->ref_ids,   g->ref_j,
-                    g->flags,     g->d_n,        g->ticket,     g->scan_sums};
+                    g->flags,     g->d_n,        g->ticket,     g->scan_sums, g->sl_ids,
+                    g->sl_n,      g->sl_counts,  g->sl_sums,    g->sl_row_ptr, g->sl_cand,
+                    g->qfeat,     g->feat,       g->score};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete g;
     return PMH_OK;
 }
 
-extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, pmh_polys db, int64_t max_queries,
-                                 int64_t max_vertices, int64_t cand_capacity, int32_t m, int32_t k,
+extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_config* cfg,
                                  pmh_qgraph* out)
 {
     if (!out) return pmh_set_error(PMH_ERR_ARG, "null out");
     *out = nullptr;
     PMH_TRY(pmh_check_device(ctx));
+    if (!cfg) return pmh_set_error(PMH_ERR_ARG, "null config");
+    const int64_t max_queries = cfg->max_queries, max_vertices = cfg->max_vertices;
+    const int64_t cand_capacity = cfg->cand_capacity;
+    const int32_t m = cfg->m, k = cfg->k, S = cfg->rerank ? cfg->shortlist : 0;
+    pmh_polys db = cfg->db;
     if (!index || max_queries < 1 || max_queries >= (1ll << 31) || max_vertices < 3 ||
-        cand_capacity < 1 || m < 1 || m > 1024 || k < 0 || k > m || (k > 0 && !db))
-        return pmh_set_error(PMH_ERR_ARG, "bad graph sizes (0 <= k <= m <= 1024, k > 0 needs db)");
+        cand_capacity < 1 || m < 1 || m > 1024 || k < 0 || k > m || ((k > 0 || cfg->rerank) && !db))
+        return pmh_set_error(PMH_ERR_ARG, "bad graph sizes (0 <= k <= m <= 1024; refinement and the "
+                                          "learned form need db)");
+    if (cfg->rerank && (S < m || S > 1024 || index->params.K % 32 != 0 || db->n != index->n))
+        return pmh_set_error(PMH_ERR_ARG, "learned form: m <= shortlist <= 1024, K a multiple of 32, "
+                                          "db the indexed set");
     pmh_qgraph g = new pmh_qgraph_s();
     g->ctx = ctx;
     g->device = ctx->device;
     g->index = index;
-    g->db = k > 0 ? db : nullptr;
+    g->db = db;
+    g->rerank = cfg->rerank;
+    g->shortlist = S;
     g->P = index->params;
     g->maxQ = max_queries;
     g->maxV = max_vertices;
@@ -136,6 +162,15 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, pmh_polys db, int
               cudaMalloc(&g->count16, sizeof(uint16_t) * cand_capacity) == cudaSuccess &&
               cudaMalloc(&g->top_ids, sizeof(int32_t) * Q * m) == cudaSuccess &&
               cudaMalloc(&g->top_n, sizeof(int32_t) * Q) == cudaSuccess &&
+              (S == 0 || (cudaMalloc(&g->sl_ids, sizeof(int32_t) * Q * S) == cudaSuccess &&
+                          cudaMalloc(&g->sl_n, sizeof(int32_t) * Q) == cudaSuccess &&
+                          cudaMalloc(&g->sl_counts, sizeof(int64_t) * Q) == cudaSuccess &&
+                          cudaMalloc(&g->sl_sums, sizeof(int64_t) * pmh_scan_sums_size(Q)) == cudaSuccess &&
+                          cudaMalloc(&g->sl_row_ptr, sizeof(int64_t) * (Q + 1)) == cudaSuccess &&
+                          cudaMalloc(&g->sl_cand, sizeof(int32_t) * Q * S) == cudaSuccess &&
+                          cudaMalloc(&g->qfeat, sizeof(float2) * Q) == cudaSuccess &&
+                          cudaMalloc(&g->feat, sizeof(uint16_t) * 48 * Q * S) == cudaSuccess &&
+                          cudaMalloc(&g->score, sizeof(float) * Q * S) == cudaSuccess)) &&
               (k == 0 || (cudaMalloc(&g->jv, sizeof(double) * Q * m) == cudaSuccess &&
                           cudaMalloc(&g->ref_ids, sizeof(int32_t) * Q * k) == cudaSuccess &&
                           cudaMalloc(&g->ref_j, sizeof(double) * Q * k) == cudaSuccess)) &&
@@ -180,9 +215,30 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, pmh_polys db, int
     if (rc == PMH_OK)
         rc = pmh_launch_agree(ctx, g->hashes, index->hashes, g->row_ptr, g->cand, Q, g->cap, &g->P,
                               g->count16, nullptr, g->flags, cs);
-    if (rc == PMH_OK)
+    if (rc == PMH_OK && S == 0)
         rc = pmh_launch_topm(g->row_ptr, g->cand, g->count16, nullptr, Q, m, g->top_ids, g->top_n,
                              g->flags, cs);
+    if (S > 0) {
+        // learned form (A7): the top-S by count, compacted, rescored by the MLP; the top-m by
+        // score go on to refinement
+        if (rc == PMH_OK)
+            rc = pmh_launch_topm(g->row_ptr, g->cand, g->count16, nullptr, Q, S, g->sl_ids, g->sl_n,
+                                 g->flags, cs);
+        if (rc == PMH_OK)
+            rc = pmh_launch_lists_to_csr(ctx, g->sl_ids, g->sl_n, Q, S, g->d_n, g->sl_counts, g->sl_sums,
+                                         g->sl_row_ptr, g->sl_cand, cs);
+        if (rc == PMH_OK)
+            rc = pmh_launch_poly_feat(ctx->sm_count, g->area2, g->off, Q, g->d_n, g->qfeat, cs);
+        if (rc == PMH_OK)
+            rc = pmh_launch_agree_features(ctx, g->hashes, index->hashes, g->sl_row_ptr, g->sl_cand, Q,
+                                           Q * S, &g->P, nullptr, nullptr, g->feat,
+                                           FeatSrc{g->qfeat, g->bbox, g->area2},
+                                           FeatSrc{db->feat, db->bbox, db->area2}, g->flags, cs);
+        if (rc == PMH_OK) rc = pmh_launch_rerank_forward(g->rerank, g->feat, Q * S, g->score, cs);
+        if (rc == PMH_OK)
+            rc = pmh_launch_topm(g->sl_row_ptr, g->sl_cand, nullptr, g->score, Q, m, g->top_ids, g->top_n,
+                                 g->flags, cs);
+    }
     if (rc == PMH_OK && k > 0)
         rc = pmh_launch_refine_topk(ctx, g->xy, g->off, g->area2, db, g->top_ids, g->top_n, Q, g->d_n, m,
                                     k, g->jv, g->ticket + 1, g->ref_ids, g->ref_j, cs);

@@ -345,11 +345,17 @@ int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* 
 int pmh_launch_agree(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph, const int64_t* row_ptr,
                      const int32_t* cand, int64_t Q, int64_t cap, const pmh_params* P,
                      uint16_t* count, uint32_t* bandmask, const int* d_flags, cudaStream_t s);
+// per-set inputs of the reranker's features: log features, boxes and twice the areas
+struct FeatSrc {
+    const float2* feat;
+    const int4* bbox;
+    const int64_t* area2;
+};
 int pmh_launch_agree_features(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph,
                               const int64_t* row_ptr, const int32_t* cand, int64_t Q, int64_t cap,
                               const pmh_params* P, uint16_t* count, uint32_t* bandmask,
-                              uint16_t* feat, const float2* qfeat, const float2* pfeat,
-                              const int* d_flags, cudaStream_t s);
+                              uint16_t* feat, FeatSrc qf, FeatSrc pf, const int* d_flags,
+                              cudaStream_t s);
 // exact refinement of fixed-width top-m lists (ids [Q][m], nlist [Q]) to the top-k by
 // (J desc, id asc) (refine.cu); jv: Q * m doubles of scratch; ticket: the grid's counter;
 // d_n (optional) caps Q on the device
@@ -358,6 +364,19 @@ int pmh_launch_refine_topk(pmh_ctx ctx, const int2* qxy, const int64_t* qoff, co
                            const int64_t* d_n, int32_t m, int32_t k, double* jv,
                            unsigned long long* ticket, int32_t* top_ids, double* top_j,
                            cudaStream_t s);
+// fixed-width lists ids [Q][m] with counts n [Q] to compact CSR (row_ptr [Q + 1], cand);
+// rows at or past *d_q (optional) are empty; counts: Q entries of scratch; sums: the
+// scan's partial sums (pmh_scan_sums_size(Q) entries; nullptr: context scratch)
+int pmh_launch_lists_to_csr(pmh_ctx ctx, const int32_t* ids, const int32_t* n, int64_t Q, int32_t m,
+                            const int64_t* d_q, int64_t* counts, int64_t* sums, int64_t* row_ptr,
+                            int32_t* cand, cudaStream_t s);
+// per-polygon reranker inputs (log2 area / 32, log2 vertex count / 16) of polygons
+// [0, n) (capped by *d_n when given)
+int pmh_launch_poly_feat(int sm_count, const int64_t* area2, const int64_t* off, int64_t n,
+                         const int64_t* d_n, float2* out, cudaStream_t s);
+// reranker scores of n feature rows (rerank.cu)
+int pmh_launch_rerank_forward(pmh_rerank r, const uint16_t* feat, int64_t n_rows, float* score,
+                              cudaStream_t s);
 int pmh_launch_topm(const int64_t* row_ptr, const int32_t* cand, const uint16_t* count,
                     const float* score, int64_t Q, int32_t m, int32_t* out_ids, int32_t* out_n,
                     const int* d_flags, cudaStream_t s);

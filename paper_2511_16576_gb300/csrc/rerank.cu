@@ -2,7 +2,7 @@
 //
 // A small MLP maps features of a (query, candidate) pair to a predicted
 // Jaccard similarity; candidates are then ordered by it (A6) so the exact
-// refinement (A8) touches fewer of them.  Network 37 -> 64 -> 64 -> 1, ReLU,
+// refinement (A8) touches fewer of them.  Network 40 -> 64 -> 64 -> 1, ReLU,
 // ReLU, sigmoid, mean squared error against the exact Jaccard.
 //
 // Features (bf16, padded to 48 columns; computed by the agreement kernel, A5):
@@ -10,7 +10,13 @@
 //          not the sentinel) -- the band-match pattern of a 32-band split;
 //   32     agreement fraction c / K (Theorem 1 estimate of J);
 //   33, 34 log2 of the query's and the candidate's area / 32;
-//   35, 36 log2 of the query's and the candidate's vertex count / 16.
+//   35, 36 log2 of the query's and the candidate's vertex count / 16;
+//   37, 38 fractions of hashes with h_k(q) < h_k(p) and h_k(q) > h_k(p): by the
+//          min form of the hash their expectations are area(q \ p) / area(q u p)
+//          and area(p \ q) / area(q u p), which, with the exact areas, sharpen
+//          the overlap estimate where the two areas differ;
+//   39     an upper bound of J: min(|q|, |p|, bounding-box overlap) over
+//          |q| + |p| minus that minimum (a geometric prior the hashes lack).
 //
 // GEMMs run on the tensor cores with mma.sync m16n8k16 (bf16 operands, fp32
 // accumulation).  One warp owns 16 rows; the accumulator fragment of one
@@ -29,7 +35,7 @@
 
 namespace {
 
-constexpr int kIn = PMH_RERANK_IN;      // 37
+constexpr int kIn = PMH_RERANK_IN;      // 40
 constexpr int kInPad = 48;
 constexpr int kH = PMH_RERANK_HIDDEN;   // 64
 constexpr int kWarpsMlp = 8;
@@ -511,8 +517,10 @@ extern "C" int pmh_rerank_features(pmh_ctx ctx, pmh_polys queries, pmh_polys db,
         return pmh_set_error(PMH_ERR_ARG, "bad arguments (K must be a multiple of 32)");
     if (Q == 0) return PMH_OK;
     return pmh_launch_agree_features(ctx, d_qhashes, d_dbhashes, d_row_ptr, d_cand, Q, INT64_MAX,
-                                     params, nullptr, nullptr, d_feat, queries->feat, db->feat,
-                                     nullptr, (cudaStream_t)stream);
+                                     params, nullptr, nullptr, d_feat,
+                                     FeatSrc{queries->feat, queries->bbox, queries->area2},
+                                     FeatSrc{db->feat, db->bbox, db->area2}, nullptr,
+                                     (cudaStream_t)stream);
 }
 
 static int mlp_launch(pmh_rerank r, bool train, const uint16_t* d_feat, const float* d_label,
@@ -527,6 +535,13 @@ static int mlp_launch(pmh_rerank r, bool train, const uint16_t* d_feat, const fl
         r->master, d_score, r->grads, r->loss);
     PMH_LAUNCHED(train ? "mlp_kernel<train>" : "mlp_kernel<forward>");
     return PMH_OK;
+}
+
+int pmh_launch_rerank_forward(pmh_rerank r, const uint16_t* feat, int64_t n_rows, float* score,
+                              cudaStream_t s)
+{
+    if (n_rows <= 0) return PMH_OK;
+    return mlp_launch(r, false, feat, nullptr, n_rows, score, s);
 }
 
 extern "C" int pmh_rerank_forward(pmh_rerank r, const uint16_t* d_feat, int64_t n_rows,

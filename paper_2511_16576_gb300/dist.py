@@ -87,8 +87,8 @@ def _all_gather_rows(t):
 
 @dataclasses.dataclass
 class QueryBatch:
-    """A batch of queries: signatures uint32 [Q, K] (in int32), vertices int32 [V, 2],
-    offsets int64 [Q + 1]."""
+    """A batch of queries: signatures uint32 [Q, K] (in int32; None when every shard signs
+    the gathered queries itself), vertices int32 [V, 2], offsets int64 [Q + 1]."""
     sig: "object"
     xy: "object"
     offsets: "object"
@@ -103,7 +103,7 @@ def gather_queries(qb: QueryBatch):
     this rank's own queries in it."""
     import torch
     import torch.distributed as dist
-    sigs = _all_gather_rows(qb.sig)
+    sigs = _all_gather_rows(qb.sig) if qb.sig is not None else None
     xys = _all_gather_rows(qb.xy)
     offs = _all_gather_rows(qb.offsets[1:] - qb.offsets[0])   # per-rank ends, from 0
     rank = dist.get_rank() if dist.is_initialized() else 0
@@ -115,7 +115,8 @@ def gather_queries(qb: QueryBatch):
             mine = (q0, q0 + o.shape[0])
         base += x.shape[0]
         q0 += o.shape[0]
-    return QueryBatch(torch.cat(sigs), torch.cat(xys), torch.cat(out_off)), mine
+    return QueryBatch(torch.cat(sigs) if sigs is not None else None, torch.cat(xys),
+                      torch.cat(out_off)), mine
 
 
 def merge_topk(j_parts, id_parts, k: int):

@@ -179,3 +179,84 @@ def sweep(searcher: Searcher, qp: B.Polys, truth: Truth, n_eval: int, ms=(8, 10,
 def best_at_recall(rows, target: float = 0.9):
     ok = [r for r in rows if r["recall"] >= target]
     return max(ok, key=lambda r: r["qps"]) if ok else None
+
+
+# ----------------------------------------------------------------------------
+# The batched search: queries in fixed-size batches through a captured graph (A9)
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class Batches:
+    """A query set cut into batches of at most `size` polygons (device tensors, offsets
+    rebased per batch), with the largest batch's vertex count."""
+    xy: list
+    off: list
+    n: list
+    size: int
+    max_vertices: int
+
+    @property
+    def total(self) -> int:
+        return int(sum(self.n))
+
+
+def make_batches(xy: torch.Tensor, offsets: np.ndarray, size: int, pinned: bool = False) -> Batches:
+    """Cut a query set (xy on the device or pinned host, offsets on the host) into batches."""
+    offsets = np.asarray(offsets, np.int64)
+    Q = len(offsets) - 1
+    xs, os_, ns = [], [], []
+    vmax = 3
+    for q0 in range(0, Q, size):
+        q1 = min(Q, q0 + size)
+        b, e = int(offsets[q0]), int(offsets[q1])
+        o = torch.from_numpy(offsets[q0:q1 + 1] - b)
+        o = o.pin_memory() if pinned else o.to(xy.device)
+        xs.append(xy[b:e])
+        os_.append(o)
+        ns.append(q1 - q0)
+        vmax = max(vmax, e - b)
+    return Batches(xs, os_, ns, size, vmax)
+
+
+def batch_capacity(ctx: B.Context, index: B.Index, params: B.Params, qp: B.Polys, size: int) -> int:
+    """Largest candidate total of any batch of `size` consecutive queries (plus a margin)."""
+    qh = B.minhash_sign(ctx, qp, params)
+    row_ptr, _ = B.lsh_query(ctx, index, qh)
+    rp = row_ptr.cpu().numpy()
+    ends = np.minimum(np.arange(0, qp.n, size) + size, qp.n)
+    per = rp[ends] - rp[np.arange(0, qp.n, size)]
+    return int(max(per.max() if len(per) else 1, 1) * 1.25) + 1024
+
+
+def run_batches(g: B.QueryGraph, batches: Batches, ids_out: torch.Tensor, j_out: torch.Tensor,
+                stream=None):
+    """Replay the graph on every batch; the refined top-k of batch b go to its rows of
+    ids_out / j_out (device or pinned host tensors, copied on the graph's stream)."""
+    q0 = 0
+    for xy, off, n in zip(batches.xy, batches.off, batches.n):
+        g.run(xy, off, stream=stream)
+        ids_out[q0:q0 + n].copy_(g.ref_ids[:n], non_blocking=True)
+        j_out[q0:q0 + n].copy_(g.ref_j[:n], non_blocking=True)
+        q0 += n
+
+
+def graph_sweep(ctx: B.Context, index: B.Index, dbp: B.Polys, batches: Batches, cap: int,
+                truth: Truth, n_eval: int, ms, k: int = 10, rerank: B.Reranker | None = None,
+                shortlist: int = 64):
+    """recall@k (first n_eval queries) and queries/s (all batches, graph replays) per m."""
+    dev = torch.device("cuda", ctx.device)
+    Q = batches.total
+    ids = torch.empty((Q, k), dtype=torch.int32, device=dev)
+    jj = torch.empty((Q, k), dtype=torch.float64, device=dev)
+    rows = []
+    for m in ms:
+        g = B.QueryGraph(ctx, index, batches.size, batches.max_vertices, cap, m, db=dbp, k=k,
+                         rerank=rerank, shortlist=max(shortlist, m))
+        try:
+            run_batches(g, batches, ids, jj)     # warm-up
+            flags = g.status()[0]
+            _, t = timed(lambda: run_batches(g, batches, ids, jj))
+        finally:
+            g.close()
+        r = recall_at_k(ids.cpu().numpy()[:n_eval], jj.cpu().numpy()[:n_eval], truth, k)
+        rows.append({"m": m, "recall": r, "qps": Q / t, "seconds": t, "flags": flags})
+    return rows

@@ -63,8 +63,8 @@ def test_params_struct_layout():
 
 
 def test_header_layout_and_constants_match_the_binding(tmp_path):
-    """The header compiled by a plain C compiler: pmh_params field offsets and the
-    shared constants equal the binding's ctypes view of them."""
+    """The header compiled by a plain C compiler: pmh_params and pmh_qgraph_config field
+    offsets and the shared constants equal the binding's ctypes view of them."""
     import shutil
     import subprocess
     from paper_2511_16576_gb300 import binding
@@ -82,6 +82,12 @@ int main(void) {
            offsetof(pmh_params, bands), offsetof(pmh_params, rows),
            offsetof(pmh_params, lsh_seed), offsetof(pmh_params, flags),
            offsetof(pmh_params, reserved));
+    printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(pmh_qgraph_config),
+           offsetof(pmh_qgraph_config, max_queries), offsetof(pmh_qgraph_config, max_vertices),
+           offsetof(pmh_qgraph_config, cand_capacity), offsetof(pmh_qgraph_config, m),
+           offsetof(pmh_qgraph_config, k), offsetof(pmh_qgraph_config, db),
+           offsetof(pmh_qgraph_config, rerank), offsetof(pmh_qgraph_config, shortlist),
+           offsetof(pmh_qgraph_config, reserved));
     printf("%d %d %d %d %d %u %u %d\n", PMH_SIGN_VARIANTS, PMH_RERANK_IN, PMH_RERANK_HIDDEN,
            PMH_RERANK_PARAMS, PMH_NOALLOC_MAX_POLYS, PMH_FLAG_STREAM_INDEX,
            PMH_FLAG_COVERAGE_MASK, PMH_ERR_CAPACITY);
@@ -97,7 +103,12 @@ int main(void) {
     assert sizes[0] == ctypes.sizeof(P)
     for off, (name, _) in zip(sizes[1:], P._fields_):
         assert off == getattr(P, name).offset, name
-    consts = [int(v) for v in lines[1].split()]
+    gsizes = [int(v) for v in lines[1].split()]
+    G = binding.QGraphConfig
+    assert gsizes[0] == ctypes.sizeof(G)
+    for off, (name, _) in zip(gsizes[1:], G._fields_):
+        assert off == getattr(G, name).offset, name
+    consts = [int(v) for v in lines[2].split()]
     assert consts == [binding.SIGN_VARIANTS, binding.RERANK_IN, binding.RERANK_HIDDEN,
                       binding.RERANK_PARAMS, binding.NOALLOC_MAX_POLYS, binding.FLAG_STREAM_INDEX,
                       binding.FLAG_COVERAGE_MASK, binding.PMH_ERR_CAPACITY]

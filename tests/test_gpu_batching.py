@@ -179,3 +179,78 @@ def test_query_graph_indexed_large_polygons_refined(B, ctx, orc):
         g.close()
         index.close()
         dbp.close()
+
+
+def test_query_graph_learned_form_matches_plain_calls(B, ctx, small_index):
+    """With a reranker the graph's top-m are the m best by predicted Jaccard among the
+    shortlist by agreement count: equal to the same chain of plain calls (shortlist top-S,
+    compact lists, features, forward, top-m by score, refinement)."""
+    w, db, qs, P, h, index = small_index
+    dbp = upload(B, ctx, db)
+    r = B.Reranker(ctx, seed=5)
+    m, S, k = 6, 16, 4
+    g = B.QueryGraph(ctx, index, max_queries=128, max_vertices=20000, cand_capacity=200000, m=m,
+                     db=dbp, k=k, rerank=r, shortlist=S)
+    try:
+        for lo, n in ((0, 1), (1, 90), (0, 128)):
+            batch = qs.subset(np.arange(lo, lo + n))
+            g.run(torch.from_numpy(batch.xy).to(DEV), torch.from_numpy(batch.offsets).to(DEV))
+            assert g.status()[0] == 0
+            qp = upload(B, ctx, batch)
+            qh, row_ptr, cand, count, _, _ = plain_outputs(B, ctx, batch, P, h, index, m)
+            ids1, nn1 = B.topm(ctx, row_ptr, cand, count, S)
+            rp2, c2 = B.lists_to_csr(ctx, ids1, nn1)
+            feat = B.rerank_features(ctx, qp, dbp, qh, h, rp2, c2, P)
+            score = r.forward(feat)
+            ids, nn = B.topm(ctx, rp2, c2, None, m, score=score)
+            assert torch.equal(g.top_ids[:n], ids) and torch.equal(g.top_n[:n], nn)
+            ti, tj = B.refine_topk(ctx, qp, dbp, ids, nn, k)
+            assert torch.equal(g.ref_ids[:n], ti) and torch.equal(g.ref_j[:n], tj)
+            qp.close()
+    finally:
+        g.close()
+        r.close()
+        dbp.close()
+
+
+def test_reload_and_rebuild_in_place_keep_a_graph_valid(B, ctx, orc):
+    """pmh_poly_reload and pmh_lsh_rebuild keep their buffers: a graph captured on the set
+    and its index answers for the new data exactly like a fresh upload and build."""
+    w = synth.WORKLOADS["small"]
+    a = synth.make_database(w)
+    # new data with a's vertex counts (a translated copy), so that it fits a's buffers
+    shift = np.array([137, -211])
+    b = synth.PolySet(a.xy + shift.astype(np.int32), a.offsets.copy(), a.centre + shift, a.rbar)
+    P = B.make_params(w.K, w.bands, w.T, w.seed, w.lsh_seed, B.FLAG_STREAM_INDEX)
+    qs = synth.make_queries(w, b, 60)
+    dbp = upload(B, ctx, a)
+    h = B.minhash_sign(ctx, dbp, P)
+    index = B.lsh_build(ctx, h, P)
+    g = B.QueryGraph(ctx, index, max_queries=64, max_vertices=10000, cand_capacity=100000, m=8,
+                     db=dbp, k=5)
+    try:
+        B.poly_reload(dbp, torch.from_numpy(b.xy).to(DEV), torch.from_numpy(b.offsets).to(DEV))
+        B.minhash_sign(ctx, dbp, P, out=h)
+        B.lsh_rebuild(ctx, index, h)
+        assert np.array_equal(u32(h), orc.sign(b.xy, b.offsets, w.seed, w.K, w.T, nthreads=8))
+        g.run(torch.from_numpy(qs.xy).to(DEV), torch.from_numpy(qs.offsets).to(DEV))
+        assert g.status()[0] == 0
+        fresh = upload(B, ctx, b)
+        h2 = B.minhash_sign(ctx, fresh, P)
+        index2 = B.lsh_build(ctx, h2, P)
+        qh, row_ptr, cand, count, ids, nn = plain_outputs(B, ctx, qs, P, h2, index2, 8)
+        assert torch.equal(g.top_ids[:qs.n], ids) and torch.equal(g.top_n[:qs.n], nn)
+        qp = upload(B, ctx, qs)
+        ti, tj = B.refine_topk(ctx, qp, fresh, ids, nn, 5)
+        assert torch.equal(g.ref_ids[:qs.n], ti) and torch.equal(g.ref_j[:qs.n], tj)
+        # the sizes must match the set's
+        with pytest.raises(B.PmhError):
+            B.poly_reload(dbp, torch.from_numpy(b.xy[:-1]).to(DEV),
+                          torch.from_numpy(b.offsets).to(DEV))
+        index2.close()
+        fresh.close()
+        qp.close()
+    finally:
+        g.close()
+        index.close()
+        dbp.close()

@@ -71,11 +71,21 @@ def test_features_match_oracle_values(B, ctx, orc, pairs):
             exp[34] = math.log2(max(abs(orc.area2(db.poly(p))) / 2, 1)) / 32
             exp[35] = math.log2(len(qs.poly(q))) / 16
             exp[36] = math.log2(len(db.poly(p))) / 16
+            exp[37] = (qh_ref[q] < h_ref[p]).sum() / K
+            exp[38] = (qh_ref[q] > h_ref[p]).sum() / K
+            qb, pb = orc.bbox(qs.poly(q)), orc.bbox(db.poly(p))
+            ov = max(0, min(qb[2], pb[2]) - max(qb[0], pb[0])) * max(0, min(qb[3], pb[3]) - max(qb[1], pb[1]))
+            a, b = abs(orc.area2(qs.poly(q))) / 2, abs(orc.area2(db.poly(p))) / 2
+            mn = min(a, b, ov)
+            exp[39] = mn / (a + b - mn) if a + b - mn > 0 else 0.0
             exp_b = np.array([orc.bf16_round(v) for v in exp])
             assert np.array_equal(got[e, :33], exp_b[:33]), e
             # log features: equal up to one bf16 step (the two log2 may round differently)
             assert np.all(np.abs(got[e, 33:37] - exp_b[33:37]) <= 2 ** -8 * np.abs(exp_b[33:37]) + 1e-12)
-            assert np.all(got[e, 37:] == 0)
+            assert np.array_equal(got[e, 37:39], exp_b[37:39]), e
+            # the bound is computed in fp32 on the GPU: equal up to one bf16 step
+            assert abs(got[e, 39] - exp_b[39]) <= 2 ** -8 * abs(exp_b[39]) + 1e-12, e
+            assert np.all(got[e, 40:] == 0)
 
 
 def random_features(rng, n):
@@ -83,12 +93,15 @@ def random_features(rng, n):
     f[:, :32] = rng.random((n, 32)) < 0.3
     f[:, 32] = rng.random(n)
     f[:, 33:37] = rng.uniform(0.2, 1.0, (n, 4))
+    f[:, 37] = rng.random(n) * (1 - f[:, 32])
+    f[:, 38] = 1 - f[:, 32] - f[:, 37]
+    f[:, 39] = np.minimum(1.0, f[:, 32] + rng.random(n) * 0.3)
     bits = (f.view(np.uint32) + 0x7FFF + ((f.view(np.uint32) >> 16) & 1)) >> 16   # to bf16 (RNE)
     return bits.astype(np.uint16).view(np.int16)
 
 
 def oracle_run(orc, B, feat_bits, label, flat, grads=True):
-    x = bf16_bits_to_float(feat_bits)[:, :37]
+    x = bf16_bits_to_float(feat_bits)[:, :B.RERANK_IN]
     w1, b1, w2, b2, w3, b3 = B.unpack_params(flat.astype(np.float64))
     return orc.mlp_forward_backward(x, label, w1, b1, w2, b2, w3, b3, grads=grads, bf16=True)
 

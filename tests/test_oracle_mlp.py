@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 
-def params(rng, d_in=37, d_h=64):
+def params(rng, d_in=40, d_h=64):
     return dict(
         w1=rng.normal(0, 1 / np.sqrt(d_in), (d_h, d_in)), b1=rng.normal(0, 0.1, d_h),
         w2=rng.normal(0, 1 / np.sqrt(d_h), (d_h, d_h)), b2=rng.normal(0, 0.1, d_h),
@@ -41,7 +41,7 @@ def test_finite_differences_exact_network(orc):
 def test_bf16_network_is_close_to_exact(orc):
     rng = np.random.default_rng(1)
     p = params(rng)
-    x = rng.normal(0, 1, (256, 37)).astype(np.float32)
+    x = rng.normal(0, 1, (256, 40)).astype(np.float32)
     y = rng.uniform(0, 1, 256).astype(np.float32)
     pe, le, ge = orc.mlp_forward_backward(x, y, **p, bf16=False)
     pb, lb, gb = orc.mlp_forward_backward(x, y, **p, bf16=True)
