@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--no-search", action="store_true", help="skip the recall / queries-per-s sweep")
     ap.add_argument("--no-stream-index", action="store_true",
                     help="sign by walking every stream point (no stream index)")
+    ap.add_argument("--cuda-profiler-range", action="store_true",
+                    help="bracket the device-input timed steps with cudaProfilerStart/Stop (for "
+                         "ncu --profile-from-start off)")
     ap.add_argument("--eval-queries", type=int, default=1000,
                     help="queries whose recall@10 is checked against brute force")
     ap.add_argument("--train-queries", type=int, default=16000,
@@ -612,13 +615,21 @@ def main():
         torch.cuda.synchronize()
         ev_sign.clear()
         l0 = B.launch_count()
+        # (for a launch list under ncu: skip this many launches, capture one step's worth)
+        print(json.dumps({"launches_before_timed": int(l0), "host_inputs": host}), file=sys.stderr,
+              flush=True)
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        profiled = args.cuda_profiler_range and not host
+        if profiled:
+            torch.cuda.profiler.start()
         t0.record(stream)
         for _ in range(steps):
             step(host, record)
         t1.record(stream)
         torch.cuda.synchronize()
+        if profiled:
+            torch.cuda.profiler.stop()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -698,9 +709,15 @@ def main():
                 "stream_points_resolved_per_s": G / (sign_ms * 1e-3)}
 
     print(json.dumps({"timed_ms_per_step": ms, "sign_ms": sign_ms, "e2e": e2e, "launches": launches,
+                      "launches_per_step": launches / args.steps,
                       "graph_status_flags": flags, "queries_with_a_result": found,
                       "unified_kernel_ms": kernels.get("sign_unified_kernel", {}).get("ms")}),
           file=sys.stderr, flush=True)
+    batch_sizes = None
+    if world == 1:
+        # graph replays per batch size (1 .. 4,096 uneven queries) beside the same steps as
+        # plain calls, both ranking by agreement count
+        batch_sizes = ev.batch_size_sweep(ctx, index, P, dbp, h, q_xy, qs.offsets, m=args.topm)
     search = None
     if not args.no_search and world == 1:
         search = search_quality(args, w, B, ctx, db, qs, h, dbp, q_xy,
@@ -729,6 +746,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": int(launches),
         "autotune": autotune,
+        "graph_batch_sizes": batch_sizes,
         "search": search,
         "generation_seconds": t_gen,
         "clocks": clk,

@@ -141,8 +141,12 @@ def _check(rc: int):
 
 
 def _ptr(t) -> int | None:
+    """Device address of a tensor; an empty view of an allocation passes its storage's
+    address (a zero-size tensor may report a null data pointer)."""
     if t is None:
         return None
+    if t.numel() == 0:
+        return t.untyped_storage().data_ptr() or None
     return t.data_ptr()
 
 

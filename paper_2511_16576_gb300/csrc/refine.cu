@@ -191,15 +191,16 @@ __device__ double warp_intersection_area(const int2* __restrict__ A, int na, int
     return acc;
 }
 
-// y-slab lists of a staged ring v[0..n) (edge e = v[e] -> v[e+1 mod n]): edge e
-// is listed in every slab of [y0 + s*2^sh, y0 + (s+1)*2^sh) that its closed
-// y-range meets.  Returns false (warp-uniform) if more than kRefSlabCap
-// references would be needed.
-constexpr int kRefSlabs = 32;
-constexpr int kRefSlabCap = 1024;
+// y-slab lists of a ring v[0..n) (staged in shared memory or read from global
+// memory; edge e = v[e] -> v[e+1 mod n]): edge e is listed in every slab of
+// [y0 + s*2^sh, y0 + (s+1)*2^sh) that its closed y-range meets, 64 slabs (two per
+// lane).  Returns false (warp-uniform) if more than kRefSlabCap references would
+// be needed.
+constexpr int kRefSlabs = 64;
+constexpr int kRefSlabCap = 2048;
 struct RefSlabs {
     uint16_t ids[kRefSlabCap];
-    uint16_t beg[kRefSlabs + 1];
+    uint16_t beg[kRefSlabs + 2];
     int cnt[kRefSlabs];
     int y0, sh;
 };
@@ -215,7 +216,8 @@ __device__ __forceinline__ bool build_ref_slabs(const int2* v, int n, RefSlabs& 
     y1 = __reduce_max_sync(0xffffffffu, y1);
     int sh = 0;
     while (((y1 - y0) >> sh) >= kRefSlabs) ++sh;
-    L.cnt[lane] = 0;
+    L.cnt[2 * lane] = 0;
+    L.cnt[2 * lane + 1] = 0;
     __syncwarp();
     for (int e = lane; e < n; e += 32) {
         const int2 a = v[e], b = v[e + 1 == n ? 0 : e + 1];
@@ -223,8 +225,8 @@ __device__ __forceinline__ bool build_ref_slabs(const int2* v, int n, RefSlabs& 
         for (int q = s0; q <= s1; ++q) atomicAdd(&L.cnt[q], 1);
     }
     __syncwarp();
-    const int c = L.cnt[lane];
-    int incl = c;
+    const int c0 = L.cnt[2 * lane], c1 = L.cnt[2 * lane + 1];
+    int incl = c0 + c1;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, incl, d);
@@ -232,14 +234,17 @@ __device__ __forceinline__ bool build_ref_slabs(const int2* v, int n, RefSlabs& 
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     if (total > kRefSlabCap) return false;
-    L.beg[lane] = (uint16_t)(incl - c);
+    const int excl = incl - c0 - c1;
+    L.beg[2 * lane] = (uint16_t)excl;
+    L.beg[2 * lane + 1] = (uint16_t)(excl + c0);
     if (lane == 31) L.beg[kRefSlabs] = (uint16_t)total;
     if (lane == 0) {
         L.y0 = y0;
         L.sh = sh;
     }
     __syncwarp();
-    L.cnt[lane] = incl - c;
+    L.cnt[2 * lane] = excl;
+    L.cnt[2 * lane + 1] = excl + c0;
     __syncwarp();
     for (int e = lane; e < n; e += 32) {
         const int2 a = v[e], b = v[e + 1 == n ? 0 : e + 1];
@@ -387,28 +392,33 @@ __device__ __forceinline__ PairView view(const int2* xy, const int64_t* off, con
 constexpr int kRefineWarps = 4;
 constexpr int kWarpVerts = 512;  // both polygons staged per warp when they fit
 
-// J of one pair by one warp (vertices staged in the warp's shared slice, with
-// y-slab lists, when they fit)
-__device__ double warp_pair_jaccard(PairView A, PairView B, int2* sv, uint2* cq, RefSlabs* L,
-                                    int lane)
+// one warp's shared slice: the staged rings, the crossing queue and both rings' slab lists
+struct RefWarp {
+    int2 sv[kWarpVerts];
+    uint2 cq[64];
+    RefSlabs sl[2];
+};
+
+// J of one pair by one warp: both rings staged in the warp's shared slice when they
+// fit, else read from global memory; y-slab lists of both rings when they fit their
+// capacity, else every edge pair
+__device__ double warp_pair_jaccard(PairView A, PairView B, RefWarp& w, int lane)
 {
     if (A.sgn == 0 || B.sgn == 0) return 0.0;
     const int2* a = A.v;
     const int2* b = B.v;
-    double inter;
     if (A.n + B.n <= kWarpVerts) {
-        for (int i = lane; i < A.n; i += 32) sv[i] = A.v[i];
-        for (int i = lane; i < B.n; i += 32) sv[A.n + i] = B.v[i];
+        for (int i = lane; i < A.n; i += 32) w.sv[i] = A.v[i];
+        for (int i = lane; i < B.n; i += 32) w.sv[A.n + i] = B.v[i];
         __syncwarp();
-        a = sv;
-        b = sv + A.n;
-        if (build_ref_slabs(a, A.n, L[0], lane) && build_ref_slabs(b, B.n, L[1], lane))
-            inter = warp_intersection_area_slabs(a, A.n, A.sgn, L[0], b, B.n, B.sgn, L[1], cq, lane);
-        else
-            inter = warp_intersection_area(a, A.n, A.sgn, b, B.n, B.sgn, cq, lane);
-    } else {
-        inter = warp_intersection_area(a, A.n, A.sgn, b, B.n, B.sgn, cq, lane);
+        a = w.sv;
+        b = w.sv + A.n;
     }
+    double inter;
+    if (build_ref_slabs(a, A.n, w.sl[0], lane) && build_ref_slabs(b, B.n, w.sl[1], lane))
+        inter = warp_intersection_area_slabs(a, A.n, A.sgn, w.sl[0], b, B.n, B.sgn, w.sl[1], w.cq, lane);
+    else
+        inter = warp_intersection_area(a, A.n, A.sgn, b, B.n, B.sgn, w.cq, lane);
     __syncwarp();
     const double uni = A.area + B.area - inter;
     return uni > 0 ? fmin(fmax(inter / uni, 0.0), 1.0) : 0.0;
@@ -422,10 +432,9 @@ refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qo
                     const int32_t* __restrict__ qid_list, int64_t n_pairs, double* __restrict__ out,
                     unsigned long long* __restrict__ ticket, const int64_t* __restrict__ d_n)
 {
-    __shared__ int2 sv[kRefineWarps][kWarpVerts];
-    __shared__ uint2 cq[kRefineWarps][64];
-    __shared__ RefSlabs sl[kRefineWarps][2];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    RefWarp& w = reinterpret_cast<RefWarp*>(smem_raw)[wid];
     if (d_n && !qid_list) n_pairs = min(n_pairs, *d_n * (int64_t)m);  // lists of the live queries
     // persistent warps pull pairs from a ticket: pair costs differ by orders of
     // magnitude (a query against its own source vs a neighbour it barely touches)
@@ -448,8 +457,7 @@ refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qo
             }
             p = ids[e];
         }
-        const double j = warp_pair_jaccard(view(qxy, qoff, qarea2, q), view(pxy, poff, parea2, p),
-                                           sv[wid], cq[wid], sl[wid], lane);
+        const double j = warp_pair_jaccard(view(qxy, qoff, qarea2, q), view(pxy, poff, parea2, p), w, lane);
         if (lane == 0) out[e] = j;
     }
 }
@@ -515,13 +523,16 @@ static int launch_refine(pmh_ctx ctx, const int2* qxy, const int64_t* qoff, cons
                          const int32_t* qid_list, int64_t n_pairs, double* out,
                          unsigned long long* ticket, const int64_t* d_n, cudaStream_t s)
 {
+    const size_t smem = sizeof(RefWarp) * kRefineWarps;
+    PMH_CUDA_TRY(cudaFuncSetAttribute(refine_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
     int per_sm = 0;
     PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_pairs_kernel,
-                                                               kRefineWarps * 32, 0));
+                                                               kRefineWarps * 32, smem));
     const int blocks = (int)std::min<int64_t>((n_pairs + kRefineWarps - 1) / kRefineWarps,
                                               (int64_t)ctx->sm_count * std::max(per_sm, 1));
     PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
-    refine_pairs_kernel<<<blocks, kRefineWarps * 32, 0, s>>>(
+    refine_pairs_kernel<<<blocks, kRefineWarps * 32, smem, s>>>(
         qxy, qoff, qarea2, db->xy, db->offsets, db->area2, ids, nlist, m, qid_list, n_pairs, out, ticket,
         d_n);
     PMH_LAUNCHED("refine_pairs_kernel");

@@ -260,3 +260,49 @@ def graph_sweep(ctx: B.Context, index: B.Index, dbp: B.Polys, batches: Batches, 
         r = recall_at_k(ids.cpu().numpy()[:n_eval], jj.cpu().numpy()[:n_eval], truth, k)
         rows.append({"m": m, "recall": r, "qps": Q / t, "seconds": t, "flags": flags})
     return rows
+
+
+def batch_size_sweep(ctx: B.Context, index: B.Index, params: B.Params, dbp: B.Polys,
+                     dbh: torch.Tensor, qs_xy: torch.Tensor, qs_offsets: np.ndarray,
+                     sizes=(1, 64, 1024, 4096), m: int = 32, k: int = 10,
+                     queries_per_size: int = 4096, rerank: B.Reranker | None = None,
+                     shortlist: int = 64):
+    """Per batch size: queries/s and mean milliseconds per batch of the captured graph
+    (replays, inputs on the device) beside the same steps as plain library calls (upload,
+    sign, join, agreement, top-m by count, refinement: several launches and host
+    synchronisations per batch), over the first `queries_per_size` queries."""
+    out = []
+    for size in sizes:
+        n_q = min(queries_per_size, len(qs_offsets) - 1)
+        n_q -= n_q % size if n_q >= size else 0
+        if n_q == 0:
+            continue
+        batches = make_batches(qs_xy, qs_offsets[:n_q + 1], size)
+        qp = B.poly_upload(ctx, qs_xy[:int(qs_offsets[n_q])], torch.from_numpy(qs_offsets[:n_q + 1]).to(qs_xy.device))
+        cap = batch_capacity(ctx, index, params, qp, size)
+        qp.close()
+        g = B.QueryGraph(ctx, index, size, batches.max_vertices, cap, m, db=dbp, k=k, rerank=rerank,
+                         shortlist=max(shortlist, m))
+        dev = qs_xy.device
+        ids = torch.empty((n_q, k), dtype=torch.int32, device=dev)
+        jj = torch.empty((n_q, k), dtype=torch.float64, device=dev)
+        run_batches(g, batches, ids, jj)
+        _, t_graph = timed(lambda: run_batches(g, batches, ids, jj))
+        g.close()
+
+        def plain():
+            for xy, off, n in zip(batches.xy, batches.off, batches.n):
+                qp = B.poly_upload(ctx, xy, off)
+                qh = B.minhash_sign(ctx, qp, params)
+                row_ptr, cand = B.lsh_query(ctx, index, qh)
+                count, _ = B.jaccard_estimate(ctx, qh, dbh, row_ptr, cand, params, bandmask=False)
+                tid, tn = B.topm(ctx, row_ptr, cand, count, m)
+                B.refine_topk(ctx, qp, dbp, tid, tn, k)
+                qp.close()
+        plain()
+        _, t_plain = timed(plain)
+        out.append({"batch": size, "queries": n_q, "graph_qps": n_q / t_graph,
+                    "graph_ms_per_batch": 1e3 * t_graph / len(batches.n),
+                    "plain_calls_qps": n_q / t_plain,
+                    "plain_calls_ms_per_batch": 1e3 * t_plain / len(batches.n)})
+    return out
