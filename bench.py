@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--n-queries", type=int, default=None)
     ap.add_argument("--batch", type=int, default=4096, help="queries per graph replay")
     ap.add_argument("--topm", type=int, default=32, help="candidates refined per query")
+    ap.add_argument("--refine-k", type=int, default=10,
+                    help="exact top-k of the refinement (0: the query graph stops at the top-m)")
     ap.add_argument("--shortlist", type=int, default=64, help="learned form: count shortlist")
     ap.add_argument("--plain", action="store_true", help="time the plain form (no reranker)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -81,6 +83,10 @@ def parse():
                          "ncu --profile-from-start off)")
     ap.add_argument("--eval-queries", type=int, default=1000,
                     help="queries whose recall@10 is checked against brute force")
+    ap.add_argument("--search-queries", type=int, default=5 * 4096,
+                    help="queries whose graph replays time the search's queries/s")
+    ap.add_argument("--search-max-candidates", type=float, default=5000.0,
+                    help="skip a band shape with more bucket candidates per query than this")
     ap.add_argument("--train-queries", type=int, default=16000,
                     help="training queries of the reranker (x shortlist pairs)")
     ap.add_argument("--paper-sweep", action="store_true",
@@ -293,7 +299,7 @@ def arm_config(args, w, db, Q, world):
                         f"({db.n_vertices} vertices, {w.n_range[0]}-{w.n_range[1]} per polygon), "
                         f"K={w.K}, {w.bands}x{w.rows} bands, {Q} perturbed-copy queries in batches of "
                         f"{args.batch}, {'plain' if args.plain else 'learned'} top-{args.topm} "
-                        f"refined to top-10",
+                        + (f"refined to top-{args.refine_k}" if args.refine_k > 0 else "lists (no refinement)"),
             "l2": (f"inputs larger than L2 ({db.xy.nbytes / 1e6:.0f} MB of vertices)"
                    if db.xy.nbytes > 129e6 else
                    f"inputs smaller than L2 ({db.xy.nbytes / 1e6:.0f} MB of vertices), L2 not flushed"),
@@ -420,11 +426,12 @@ def search_quality(args, w, B, ctx, db, qs, h, dbp, q_xy, q_off, P):
     qep = B.poly_upload(ctx, torch.from_numpy(qe.xy).to(dev), torch.from_numpy(qe.offsets).to(dev))
     truth, t_bf = ev.timed(lambda: ev.brute_force_topk(ctx, qep, dbp, 10))
     qep.close()
-    qp = B.poly_upload(ctx, q_xy, q_off)
-    batches = ev.make_batches(q_xy, qs.offsets, args.batch)
+    n_s = min(qs.n, max(args.search_queries, n_eval))
+    qp = B.poly_upload(ctx, q_xy[:int(qs.offsets[n_s])], q_off[:n_s + 1])
+    batches = ev.make_batches(q_xy, qs.offsets[:n_s + 1], args.batch)
     tq = synth.perturbed_queries(db, args.train_queries, w.query_seed + 1000)
     tp = B.poly_upload(ctx, torch.from_numpy(tq.xy).to(dev), torch.from_numpy(tq.offsets).to(dev))
-    out = {"eval_queries": n_eval, "timed_queries": qs.n, "batch": args.batch, "k": 10,
+    out = {"eval_queries": n_eval, "timed_queries": n_s, "batch": args.batch, "k": 10,
            "target_recall": 0.9, "bf_pairs_per_query": truth.pairs / n_eval,
            "bf_seconds_eval_queries": t_bf, "forms": {}}
     ms = (10, 12, 14, 16, 18, 20, 22, 24, 28, 32)   # refined to the top-10: m >= 10
@@ -434,6 +441,11 @@ def search_quality(args, w, B, ctx, db, qs, h, dbp, q_xy, q_off, P):
         index = B.lsh_build(ctx, h, params)
         cap = ev.batch_capacity(ctx, index, params, qp, args.batch)
         key = f"{params.bands}x{params.rows}"
+        if cap / args.batch > args.search_max_candidates * 1.25:
+            out["forms"][key] = {"bands": key, "skipped": f"{cap / args.batch / 1.25:.0f} bucket candidates "
+                                 f"per query in the largest batch (> {args.search_max_candidates:.0f})"}
+            index.close()
+            continue
         plain = ev.graph_sweep(ctx, index, dbp, batches, cap, truth, n_eval, ms)
         s = ev.Searcher(ctx, index, params, dbp, h, shortlist=args.shortlist)
         feat, lab = ev.training_pairs(ctx, s, tp)
@@ -552,8 +564,10 @@ def main():
     # with several ranks every rank searches the query batches of all ranks (gathered) on its
     # own shard, so its graph holds world x the batch
     shard_base = int(D.shard_offsets(N, dev)[rank]) if world > 1 else 0
+    kk = args.refine_k
     g = B.QueryGraph(ctx, index, world * args.batch, world * batches.max_vertices, world * cap,
-                     args.topm, db=dbp, k=10, rerank=rr, shortlist=args.shortlist)
+                     args.topm, db=dbp, k=kk, rerank=rr, shortlist=args.shortlist)
+    assert world == 1 or kk > 0, "the exchange merges refined top-k lists"
 
     def local_search(allq, k):
         g.run(allq.xy, allq.offsets)
@@ -568,12 +582,13 @@ def main():
         q0 = 0
         for xy, off, n in zip(src.xy, src.off, src.n):
             xy, off = xy.to(dev, non_blocking=True), off.to(dev, non_blocking=True)
-            gid, gj = D.global_search(local_search, D.QueryBatch(None, xy, off), shard_base, 10)
+            gid, gj = D.global_search(local_search, D.QueryBatch(None, xy, off), shard_base, kk)
             out_ids[q0:q0 + n].copy_(gid, non_blocking=True)
             out_j[q0:q0 + n].copy_(gj, non_blocking=True)
             q0 += n
-    res_ids = torch.empty((Q, 10), dtype=torch.int32, device=dev)
-    res_j = torch.empty((Q, 10), dtype=torch.float64, device=dev)
+    res_cols = kk if kk > 0 else args.topm   # refined top-k, else the top-m lists
+    res_ids = torch.empty((Q, res_cols), dtype=torch.int32, device=dev)
+    res_j = torch.empty((Q, res_cols), dtype=torch.float64, device=dev) if kk > 0 else None
     ev_sign = []
 
     def step(host: bool, record: bool):
@@ -603,8 +618,8 @@ def main():
         h_off = torch.from_numpy(db.offsets).pin_memory()
         hbatches = ev.make_batches(torch.from_numpy(qs.xy).pin_memory(), qs.offsets, args.batch,
                                    pinned=True)
-        hres_ids = torch.empty((Q, 10), dtype=torch.int32).pin_memory()
-        hres_j = torch.empty((Q, 10), dtype=torch.float64).pin_memory()
+        hres_ids = torch.empty((Q, res_cols), dtype=torch.int32).pin_memory()
+        hres_j = torch.empty((Q, res_cols), dtype=torch.float64).pin_memory() if kk > 0 else None
 
     def timed(host: bool, steps: int, warmup: int, record: bool):
         for _ in range(warmup):
@@ -640,6 +655,7 @@ def main():
     clocks = Clocks(local)
     clocks.start()
     B.sign_report(ctx)                     # forget events of earlier calls
+    B.sign_count_work(ctx, False)          # timed launches: the kernels without work counters
     ms, launches = timed(False, args.steps, args.warmup, True)
     clk = clocks.stop()
     flags = g.status()[0]
@@ -650,7 +666,7 @@ def main():
     if not args.no_e2e:
         ms_e2e, _ = timed(True, args.steps, args.warmup, False)
         h2d = db.xy.nbytes + db.offsets.nbytes + qs.xy.nbytes + 8 * (Q + len(batches.n))
-        d2h = hres_ids.numel() * 4 + hres_j.numel() * 8
+        d2h = hres_ids.numel() * 4 + (hres_j.numel() * 8 if hres_j is not None else 0)
         e2e = {"value": world * (N + Q) * K / (ms_e2e * 1e-3), "unit": "hashes/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": ms_e2e}
@@ -662,6 +678,7 @@ def main():
     # launches, against the measured integer peak; L2 / DRAM traffic from the ncu summary
     hashes_np = h.cpu().numpy().view(np.uint32)
     G = algorithmic_points(hashes_np, w.T)
+    B.sign_count_work(ctx, True)
     B.minhash_sign(ctx, dbp, P, out=h)     # one more database launch, untimed, to read its work
     per_kernel = B.sign_report(ctx)        # work counts are fixed by the input: same as timed
     peak = B.probe_int_peak(ctx)
@@ -717,7 +734,8 @@ def main():
     if world == 1:
         # graph replays per batch size (1 .. 4,096 uneven queries) beside the same steps as
         # plain calls, both ranking by agreement count
-        batch_sizes = ev.batch_size_sweep(ctx, index, P, dbp, h, q_xy, qs.offsets, m=args.topm)
+        batch_sizes = ev.batch_size_sweep(ctx, index, P, dbp, h, q_xy, qs.offsets, m=args.topm,
+                                          k=kk)
     search = None
     if not args.no_search and world == 1:
         search = search_quality(args, w, B, ctx, db, qs, h, dbp, q_xy,

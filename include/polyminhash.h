@@ -179,6 +179,12 @@ int pmh_stream_index_build(pmh_ctx ctx, const pmh_params* params, void* stream);
  * (h_counts holds 6 values). */
 int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts);
 
+/* Whether later signing calls on this context record those counts (1, the
+ * default) or run kernels built without the counters (0; pmh_sign_work and
+ * pmh_sign_report then return zeros for them).  The counters are measurement
+ * support only: the hashes are the same either way. */
+int pmh_sign_count_work(pmh_ctx ctx, int enable);
+
 /* Measurement support (no counterpart in the paper).  With the stream index,
  * pmh_minhash_sign signs every polygon in one persistent launch (the unified
  * kernel: indexed or walk form per polygon); without it, or with

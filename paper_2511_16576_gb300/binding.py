@@ -72,6 +72,7 @@ _SIGS = {
     "pmh_stream_index_build": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P]),
     "pmh_sign_work": (ctypes.c_int, [_P, _P]),
     "pmh_sign_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pmh_sign_count_work": (ctypes.c_int, [_P, ctypes.c_int]),
     "pmh_sign_report": (ctypes.c_int, [_P, _P, _P]),
     "pmh_lsh_build": (ctypes.c_int, [_P, _P, _i64, ctypes.POINTER(Params), ctypes.POINTER(_P), _P]),
     "pmh_lsh_rebuild": (ctypes.c_int, [_P, _P, _P, _i64, _P]),
@@ -325,6 +326,12 @@ def sign_work(ctx: Context) -> dict:
 
 
 WORK_KEYS = ("walk_points", "cells", "index_entries", "candidates", "edge_tests", "mask_decisions")
+
+
+def sign_count_work(ctx: Context, enable: bool = True):
+    """Record work counts in later signing calls (the default) or run the kernels built
+    without the counters (same hashes)."""
+    _check(load().pmh_sign_count_work(ctx.handle, 1 if enable else 0))
 
 
 def sign_timing(ctx: Context, enable: bool = True):

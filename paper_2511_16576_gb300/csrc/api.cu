@@ -299,7 +299,7 @@ static void free_derived(pmh_polys p)
     p->slab_ptr = p->slab_edges = nullptr;
     p->order = p->order_cls = nullptr;
     p->mask = nullptr;
-    p->n_indexed = p->n_staged_walk = 0;
+    p->n_indexed = p->n_whole_cost = 0;
 }
 
 extern "C" int pmh_poly_reload(pmh_polys polys, const int32_t* xy, const int64_t* offsets,

@@ -464,7 +464,10 @@ int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* 
     if (Q <= 0) return PMH_OK;
     const pmh_params& P = X->params;
     const int64_t m = X->n * P.bands;
-    if (P.bands > 16) {  // many short bands: parallel walk + sort
+    // sixteen bands or more: block per query, parallel bucket walks and a shared-memory
+    // set (rows of thousands of candidates occur on dense sets; the warp merge below
+    // would walk them one candidate at a time)
+    if (P.bands >= 16) {
         const unsigned blocks = (unsigned)std::min<int64_t>(Q, (int64_t)X->ctx->sm_count);
         const size_t smem = sizeof(int32_t) * (kJoinTable + kJoinMaxUnique);
         PMH_CUDA_TRY(cudaFuncSetAttribute(join_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

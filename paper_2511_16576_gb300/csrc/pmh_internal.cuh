@@ -77,6 +77,10 @@ __host__ __device__ constexpr bool index_level_fits(int l, int K)
 // polygons of at most this many vertices are staged in shared memory by the
 // signing kernels; larger ones are read through their y-slab edge index
 constexpr int kStagedMaxVerts = 256;
+// polygons above this many vertices are signed in (polygon, 32-hash chunk) items, so that
+// a few very large polygons spread over many warps; smaller ones are signed whole (the
+// staging, slab lists and coverage mask are then built once per polygon)
+constexpr int kChunkMinVerts = 4096;
 
 // Cost model of the indexed form for one polygon (clipped box bb, twice its
 // area), in warp instructions per hash: the walk examines about 2^32 / area
@@ -197,6 +201,7 @@ struct pmh_ctx_s {
     int sign_variant = -1;                // autotuned signing kernel (-1 = default)
     StreamIndex sindex;                   // cached stream index (PMH_FLAG_STREAM_INDEX)
     int sign_timing = 0;                  // record per-kernel events in pmh_minhash_sign
+    int sign_count = 1;                   // signing launches record their work counts
     std::vector<cudaEvent_t> sign_ev;     // three per recorded call
     size_t sign_ev_used = 0;
 };
@@ -229,11 +234,12 @@ struct pmh_polys_s {
     int32_t* slab_edges = nullptr;
     int32_t* order = nullptr;       // polygons by expected signing cost, largest first (built
                                     // on the first signing call without the stream index)
-    int32_t* order_cls = nullptr;   // class order: polygons above kStagedMaxVerts vertices and
-                                    // staged walk-form polygons (each by cost), then staged
-                                    // indexed-form polygons (Morton order)
+    int32_t* order_cls = nullptr;   // class order: polygons above kChunkMinVerts vertices, then
+                                    // the other polygons signed in cost order (staged walk-form
+                                    // ones and those above kStagedMaxVerts), each by cost, then
+                                    // staged indexed-form polygons (Morton order)
     int64_t n_indexed = 0;          // class 0: <= kStagedMaxVerts vertices, pmh_index_plan lim > 0
-    int64_t n_staged_walk = 0;      // class 1: <= kStagedMaxVerts vertices, walk form
+    int64_t n_whole_cost = 0;       // class 1: the rest up to kChunkMinVerts vertices
     uint32_t* mask = nullptr;       // [n][16] coverage masks
 };
 
@@ -325,7 +331,7 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     uint32_t* out, cudaStream_t s, const int64_t* area2 = nullptr,
                     const StreamIndexView* sidx = nullptr, const uint32_t* masks = nullptr,
                     const int32_t* order_cls = nullptr, int64_t n_indexed = 0,
-                    int64_t n_staged_walk = 0);
+                    int64_t n_whole_cost = 0);
 // every polygon in one persistent launch (sign_unified.cu): slots list[0 ..
 // n_slots) (list nullptr: slot = polygon id), the first n_chunked as (polygon,
 // 32-hash chunk) items, the rest whole; d_n (optional) caps n_slots on the

@@ -304,7 +304,7 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
                     const int64_t* d_n, const int* d_flags, unsigned long long* ticket,
                     uint32_t* out, cudaStream_t s, const int64_t* area2,
                     const StreamIndexView* sidx, const uint32_t* masks,
-                    const int32_t* order_cls, int64_t n_indexed, int64_t n_staged_walk)
+                    const int32_t* order_cls, int64_t n_indexed, int64_t n_whole_cost)
 {
     const StreamIndexView S = sidx ? *sidx : StreamIndexView{};
     if (n_polys <= 0) return PMH_OK;
@@ -312,6 +312,7 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
     if (work) {
         PMH_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(unsigned long long) * 6, s));
         PMH_CUDA_TRY(cudaMemsetAsync(ctx->d_tickets + kIdxWorkSlot, 0, sizeof(unsigned long long) * 6, s));
+        if (!ctx->sign_count) work = nullptr;  // counts stay zero: the counter-free kernels run
     }
     const bool timed = ctx->sign_timing && !d_n && ctx->sign_ev_used + 3 <= 3 * 1024;
     cudaEvent_t* ev = nullptr;
@@ -326,10 +327,10 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
         PMH_CUDA_TRY(cudaEventRecord(ev[0], s));
     }
     if (S.cell && S.ranked && order_cls && area2 && !d_n && !masks) {
-        // every polygon in one launch: the class order puts the polygons above the
-        // staged size first (32-hash items), then the staged ones (whole polygons)
+        // every polygon in one launch: the class order puts the polygons above
+        // kChunkMinVerts first (32-hash items), then the rest (whole polygons)
         const int U = kSignVariants[ctx->sign_variant >= 0 ? ctx->sign_variant : 0].U;
-        const int64_t n_big = n_polys - n_indexed - n_staged_walk;
+        const int64_t n_big = n_polys - n_indexed - n_whole_cost;
         PMH_TRY(pmh_launch_sign_unified(ctx, U, xy, off, bbox, area2, slabs, slab_ptr, slab_edges,
                                         order_cls, n_polys, n_big, nullptr, nullptr, P, S, ticket + 2,
                                         out, work ? ctx->d_tickets + kIdxWorkSlot : nullptr, s));
@@ -379,7 +380,7 @@ extern "C" int pmh_minhash_sign(pmh_ctx ctx, pmh_polys polys, const pmh_params* 
                            polys->slab_ptr, polys->slab_edges, polys->order, params, polys->n,
                            nullptr, nullptr, ctx->d_tickets + 0, d_hashes, (cudaStream_t)stream,
                            polys->area2, indexed ? &sidx : nullptr, masked ? polys->mask : nullptr,
-                           polys->order_cls, polys->n_indexed, polys->n_staged_walk);
+                           polys->order_cls, polys->n_indexed, polys->n_whole_cost);
 }
 
 extern "C" int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts)
@@ -393,6 +394,13 @@ extern "C" int pmh_sign_work(pmh_ctx ctx, uint64_t* h_counts)
     PMH_CUDA_TRY(cudaMemcpy(both + 6, ctx->d_tickets + kWorkSlot, sizeof(uint64_t) * 6,
                             cudaMemcpyDeviceToHost));
     for (int i = 0; i < 6; ++i) h_counts[i] = both[i] + both[6 + i];
+    return PMH_OK;
+}
+
+extern "C" int pmh_sign_count_work(pmh_ctx ctx, int enable)
+{
+    if (!ctx) return pmh_set_error(PMH_ERR_ARG, "null context");
+    ctx->sign_count = enable != 0;
     return PMH_OK;
 }
 
@@ -485,7 +493,7 @@ extern "C" int pmh_sign_autotune(pmh_ctx ctx, pmh_polys sample, const pmh_params
                                      sample->n, nullptr, nullptr, ctx->d_tickets + 1, out, 0,
                                      sample->area2, indexed ? &sidx : nullptr,
                                      masked ? sample->mask : nullptr, sample->order_cls,
-                                     sample->n_indexed, sample->n_staged_walk);
+                                     sample->n_indexed, sample->n_whole_cost);
             cudaEventRecord(e1, 0);
             if (cudaEventSynchronize(e1) != cudaSuccess)
                 rc = pmh_set_error(PMH_ERR_CUDA, "autotune run failed");

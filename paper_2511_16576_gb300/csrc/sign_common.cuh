@@ -53,6 +53,18 @@ struct Work {
     unsigned long long lane_edges = 0;  // per lane (lane-parallel tests), summed at the end
 };
 
+// The same counters compiled away, for launches that do not report their work: every
+// function below takes its counters as a template parameter W (Work or NoWork).
+struct Sink {
+    __device__ __forceinline__ Sink& operator+=(unsigned long long) { return *this; }
+    __device__ __forceinline__ Sink& operator++() { return *this; }
+    __device__ __forceinline__ Sink operator++(int) { return *this; }
+    __device__ __forceinline__ operator unsigned long long() const { return 0ull; }
+};
+struct NoWork {
+    Sink walk, cells, entries, cand, edges, masked, lane_edges;
+};
+
 // Exact membership through the polygon's y-slab index: only the edges listed
 // for the slab holding py can straddle the line y = py.
 __device__ __forceinline__ bool warp_inside_slab(const int2* __restrict__ v, int n,
@@ -80,7 +92,8 @@ __device__ __forceinline__ bool warp_inside_slab(const int2* __restrict__ v, int
 struct AllEdges {
     const int2* v;
     int n;
-    __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
+    template <class W>
+    __device__ __forceinline__ bool operator()(int px, int py, int lane, W& w) const
     {
         w.edges += n;
         return warp_inside(v, n, px, py, lane);
@@ -93,7 +106,8 @@ struct SlabEdges {
     const int32_t* sp;
     const int32_t* se;
     int slab_h, ymin;
-    __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
+    template <class W>
+    __device__ __forceinline__ bool operator()(int px, int py, int lane, W& w) const
     {
         int tested = 0;
         const bool r = warp_inside_slab(v, n, sp, se, slab_h, ymin, px, py, lane, tested);
@@ -113,7 +127,8 @@ struct StagedEdges {
     const uint8_t* ids;
     const uint16_t* beg;
     int y0, sh;
-    __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
+    template <class W>
+    __device__ __forceinline__ bool operator()(int px, int py, int lane, W& w) const
     {
         const int s = (py - y0) >> sh;
         const int lo = beg[s], hi = beg[s + 1];
@@ -125,7 +140,8 @@ struct StagedEdges {
         }
         return __popc(__ballot_sync(0xffffffffu, par)) & 1;
     }
-    __device__ __forceinline__ bool lane_inside(int px, int py, Work& w) const
+    template <class W>
+    __device__ __forceinline__ bool lane_inside(int px, int py, W& w) const
     {
         const int s = (py - y0) >> sh;
         const int lo = beg[s], hi = beg[s + 1];
@@ -191,10 +207,10 @@ __device__ __forceinline__ bool build_staged_slabs(const int2* v, int n, int y0,
     return true;
 }
 
-template <int U, class Inside>
+template <int U, class Inside, class W>
 __device__ __forceinline__ uint32_t sign_walk(const Inside& inside, int x0, int y0, uint32_t w,
                                               uint32_t h, uint64_t sk, uint32_t T, int lane,
-                                              Work& work, uint32_t start);
+                                              W& work, uint32_t start);
 
 // Membership through the polygon's coverage mask first: a candidate in a cell
 // that no edge touches is decided by the cell's code; only boundary cells run
@@ -204,7 +220,8 @@ struct Masked {
     Inner inner;
     const uint32_t* m;  // 16 words (row j), 2 bits per cell
     int x0, y0, cwl, chl;
-    __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
+    template <class W>
+    __device__ __forceinline__ bool operator()(int px, int py, int lane, W& w) const
     {
         const uint32_t code = (m[(py - y0) >> chl] >> (2 * ((px - x0) >> cwl))) & 3u;
         if (code != 2u) {
@@ -217,10 +234,10 @@ struct Masked {
 
 // One hash of one polygon; every lane returns the same value.  U points per
 // lane per round: one round covers 32 * U consecutive stream indices.
-template <int U, class Inside>
+template <int U, class Inside, class W>
 __device__ __forceinline__ uint32_t sign_one_t(const Inside& inside, int x0, int y0, uint32_t w,
                                                uint32_t h, uint64_t sk, uint32_t T, int lane,
-                                               Work& work, uint32_t start = 0)
+                                               W& work, uint32_t start = 0)
 {
     if (w == 0 || h == 0) return T;
     const uint32_t r = sign_walk<U>(inside, x0, y0, w, h, sk, T, lane, work, start);
@@ -228,10 +245,10 @@ __device__ __forceinline__ uint32_t sign_one_t(const Inside& inside, int x0, int
     return r;
 }
 
-template <int U, class Inside>
+template <int U, class Inside, class W>
 __device__ __forceinline__ uint32_t sign_walk(const Inside& inside, int x0, int y0, uint32_t w,
                                               uint32_t h, uint64_t sk, uint32_t T, int lane,
-                                              Work& work, uint32_t start)
+                                              W& work, uint32_t start)
 {
     uint64_t z = sk + (uint64_t)(start + lane + 1) * PMH_GAMMA;
     const uint64_t step = 32ull * PMH_GAMMA;
@@ -267,12 +284,12 @@ __device__ __forceinline__ uint32_t sign_walk(const Inside& inside, int x0, int 
 // The rare walks of the indexed form (a list that overflowed, or no inside
 // candidate below the index limit) are kept out of line, so that the registers
 // of the walk do not weigh on the gather and the lane-parallel tests.
-template <int U, class Inside>
+template <int U, class Inside, class W>
 __device__ __noinline__ uint32_t sign_resume(const Inside inside, int x0, int y0, uint32_t w,
                                              uint32_t h, uint64_t sk, uint32_t T, int lane,
-                                             Work* work, uint32_t start)
+                                             W* work, uint32_t start)
 {
-    Work local;
+    W local;
     const uint32_t r = sign_one_t<U>(inside, x0, y0, w, h, sk, T, lane, local, start);
     work->walk += local.walk;
     work->cand += local.cand;

@@ -27,14 +27,16 @@
 //
 // Work items come from one atomic ticket over a list of polygon slots: the
 // first n_chunked slots are split into (polygon, 32-hash chunk) items -- the
-// large polygons, whose walks and tests cost the most, first and by
-// decreasing cost -- and the remaining slots are whole polygons (all K
-// hashes, so that the staging and the mask are paid once per polygon).  A
+// very large polygons (above 4,096 vertices), whose walks and tests cost the
+// most, first and by decreasing cost -- and the remaining slots are whole
+// polygons (all K hashes, so that the staging and the mask are paid once per
+// polygon).  A
 // staged polygon met in a chunked slot is signed whole by its chunk 0 (its
 // other chunks return at once), so the captured query pipeline can hand in
 // every polygon as a chunked slot.  Every step is exact, so the result equals
 // the definition bit for bit.
 #include <algorithm>
+#include <type_traits>
 
 #include "sign_common.cuh"
 
@@ -110,8 +112,8 @@ struct GlobalSrc {
 };
 
 // exact half-open membership, one point per lane
-template <class Src>
-__device__ __forceinline__ bool lane_inside(const Src& s, int px, int py, Work& w)
+template <class Src, class W>
+__device__ __forceinline__ bool lane_inside(const Src& s, int px, int py, W& w)
 {
     int lo, hi;
     s.row(py, lo, hi);
@@ -125,8 +127,8 @@ __device__ __forceinline__ bool lane_inside(const Src& s, int px, int py, Work& 
 }
 
 // exact half-open membership, warp-cooperative (lanes split the row's edges)
-template <class Src>
-__device__ __forceinline__ bool warp_inside_src(const Src& s, int px, int py, int lane, Work& w)
+template <class Src, class W>
+__device__ __forceinline__ bool warp_inside_src(const Src& s, int px, int py, int lane, W& w)
 {
     int lo, hi;
     s.row(py, lo, hi);
@@ -169,9 +171,9 @@ __device__ __forceinline__ int single_slab(UniWarp& m, int n, int lane)
 // cell index -- computed in single precision, off by less than one unit --
 // never moves it across an unmarked cell, and the classification is exact.
 // Without a mask (use_mask false) every cell is a boundary cell.
-template <class Src>
+template <class Src, class W>
 __device__ __forceinline__ void build_mask(UniWarp& m, const Src& src, int n, int4 bb, int cwl,
-                                           int chl, bool use_mask, int lane, Work& work)
+                                           int chl, bool use_mask, int lane, W& work)
 {
     if (!use_mask) {
         m.bnd[lane] = 0xFFFFFFFFu;
@@ -242,7 +244,8 @@ struct MaskedWalker {
     const UniWarp* m;
     Src src;
     int x0, y0, cwl, chl;
-    __device__ __forceinline__ bool operator()(int px, int py, int lane, Work& w) const
+    template <class W>
+    __device__ __forceinline__ bool operator()(int px, int py, int lane, W& w) const
     {
         const int i = (px - x0) >> cwl, j = (py - y0) >> chl;
         if (!((m->bnd[j] >> i) & 1u)) {
@@ -254,9 +257,8 @@ struct MaskedWalker {
 };
 
 // exact tests of queue[0 .. count), one per lane; an inside point lowers its hash's result
-template <class Src>
-__device__ __forceinline__ void exact_batch(UniWarp& m, int count, const Src& src, int lane,
-                                            Work& work)
+template <class Src, class W>
+__device__ __forceinline__ void exact_batch(UniWarp& m, int count, const Src& src, int lane, W& work)
 {
     if (lane < count) {
         const uint2 c = m.queue[lane];
@@ -268,17 +270,20 @@ __device__ __forceinline__ void exact_batch(UniWarp& m, int count, const Src& sr
     __syncwarp();
 }
 
-// per-lane counts of the gather (widened at the end)
+// per-lane counts of the gather (widened at the end), and the same compiled away
 struct GatherCounts {
     unsigned cells = 0, read = 0, cand = 0, masked = 0;
 };
+struct NoGather {
+    Sink cells, read, cand, masked;
+};
 
 // Indexed form of hashes [k_begin, k_end) of polygon p (row `out` of the output).
-template <class Src>
+template <class Src, class W, class G>
 __device__ __forceinline__ void indexed_range(UniWarp& m, const Src& src, const StreamIndexView& S,
                                               PmhIndexPlan plan, int4 bb, uint64_t seed, uint32_t T,
                                               int k_begin, int k_end, uint32_t* __restrict__ out,
-                                              int lane, Work& work, GatherCounts& gc)
+                                              int lane, W& work, G& gc)
 {
     const unsigned full = 0xffffffffu;
     const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
@@ -441,10 +446,10 @@ __device__ __forceinline__ void indexed_range(UniWarp& m, const Src& src, const 
 }
 
 // Walk form of hashes [k_begin, k_end): lane j keeps hash k0 + j of each 32.
-template <int U, class Src>
+template <int U, class Src, class W>
 __device__ __forceinline__ void walk_range(const UniWarp& m, const Src& src, int4 bb, uint64_t seed,
                                            uint32_t T, int k_begin, int k_end,
-                                           uint32_t* __restrict__ out, int lane, Work& work)
+                                           uint32_t* __restrict__ out, int lane, W& work)
 {
     const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
     const MaskedWalker<Src> walker{&m, src, bb.x, bb.y, mask32_log2((int)w), mask32_log2((int)h)};
@@ -462,12 +467,12 @@ __device__ __forceinline__ void walk_range(const UniWarp& m, const Src& src, int
 
 // Walk form of a staged polygon, kept out of line so that its registers do not
 // weigh on the indexed form's gather (Work by pointer: a local copy inside).
-template <int U>
+template <int U, class W>
 __device__ __noinline__ void walk_staged(const UniWarp& m, StagedSrc src, int4 bb, uint64_t seed,
                                          uint32_t T, int k_begin, int k_end, uint32_t* out,
-                                         int lane, Work* work)
+                                         int lane, W* work)
 {
-    Work local;
+    W local;
     walk_range<U>(m, src, bb, seed, T, k_begin, k_end, out, lane, local);
     work->walk += local.walk;
     work->cand += local.cand;
@@ -478,14 +483,14 @@ __device__ __noinline__ void walk_staged(const UniWarp& m, StagedSrc src, int4 b
 
 // A polygon above the staged size (read from global memory): the mask, then the
 // planned form, out of line for the same reason.
-template <int U>
+template <int U, class W, class G>
 __device__ __noinline__ void sign_global(UniWarp& m, GlobalSrc src, int n, int4 bb, PmhIndexPlan plan,
                                          const StreamIndexView& S, uint64_t seed, uint32_t T,
-                                         int k_begin, int k_end, uint32_t* out, int lane, Work* work,
-                                         GatherCounts* gc)
+                                         int k_begin, int k_end, uint32_t* out, int lane, W* work,
+                                         G* gc)
 {
-    Work local;
-    GatherCounts g;
+    W local;
+    G g;
     build_mask(m, src, n, bb, mask32_log2(bb.z - bb.x), mask32_log2(bb.w - bb.y), n <= kMaskMaxEdges,
                lane, local);
     if (plan.lim > 0)
@@ -503,7 +508,7 @@ __device__ __noinline__ void sign_global(UniWarp& m, GlobalSrc src, int n, int4 
     gc->masked += g.masked;
 }
 
-template <int U>
+template <int U, bool kCount>
 __global__ void __launch_bounds__(kUniWarps * 32, kUniMinBlocks)
 sign_unified_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
                     const int4* __restrict__ bbox, const int64_t* __restrict__ area2,
@@ -521,8 +526,11 @@ sign_unified_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
     const int lane = threadIdx.x & 31;
     UniWarp& m = smem[threadIdx.x >> 5];
     const unsigned full = 0xffffffffu;
-    Work work;
-    GatherCounts gc;
+    // work counters only in launches that report them
+    using W = typename std::conditional<kCount, Work, NoWork>::type;
+    using G = typename std::conditional<kCount, GatherCounts, NoGather>::type;
+    W work;
+    G gc;
     const bool failed = d_flags && *d_flags;  // the batch failed validation
     if (d_n) n_slots = min(n_slots, *d_n);
     n_chunked = min(n_chunked, n_slots);
@@ -569,16 +577,16 @@ sign_unified_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
             if (plan.lim > 0)
                 indexed_range(m, src, S, plan, bb, seed, T, k_begin, k_end, row, lane, work, gc);
             else
-                walk_staged<U>(m, src, bb, seed, T, k_begin, k_end, row, lane, &work);
+                walk_staged<U, W>(m, src, bb, seed, T, k_begin, k_end, row, lane, &work);
         } else {
             const SlabInfo si = slabs ? slabs[p] : SlabInfo{0, 0, 0, 1, 0};
             const GlobalSrc src{xy + b, n, si.S > 0 ? slab_ptr + si.slab_base : nullptr,
                                 si.S > 0 ? slab_edges + si.edge_base : nullptr, si.slab_h, si.ymin};
-            sign_global<U>(m, src, n, bb, plan, S, seed, T, k_begin, k_end, row, lane, &work, &gc);
+            sign_global<U, W, G>(m, src, n, bb, plan, S, seed, T, k_begin, k_end, row, lane, &work, &gc);
         }
         __syncwarp();
     }
-    if (work_out) {
+    if (kCount && work_out) {
         unsigned long long le = work.lane_edges, en = gc.read, ca = gc.cand, ma = gc.masked,
                            ce = gc.cells;  // (the gather's 32-bit lane counts, widened)
 #pragma unroll
@@ -615,7 +623,10 @@ int pmh_launch_sign_unified(pmh_ctx ctx, int U, const int2* xy, const int64_t* o
                             cudaStream_t s)
 {
     if (n_slots <= 0) return PMH_OK;
-    auto fn = U <= 2 ? sign_unified_kernel<2> : U <= 4 ? sign_unified_kernel<4> : sign_unified_kernel<8>;
+    auto fn = work ? (U <= 2 ? sign_unified_kernel<2, true> : U <= 4 ? sign_unified_kernel<4, true>
+                                                             : sign_unified_kernel<8, true>)
+                   : (U <= 2 ? sign_unified_kernel<2, false> : U <= 4 ? sign_unified_kernel<4, false>
+                                                               : sign_unified_kernel<8, false>);
     int per_sm = 0;
     PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kUniWarps * 32, 0));
     const int chunks = (int)((P->K + 31) / 32);

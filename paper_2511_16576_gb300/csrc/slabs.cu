@@ -175,13 +175,14 @@ __device__ __forceinline__ uint32_t morton16(uint32_t x, uint32_t y)
     return spread(x) | (spread(y) << 1);
 }
 
-// class key: polygons of more than kStagedMaxVerts vertices (class 2) first,
-// by decreasing expected cost -- the signing launch splits them into 32-hash
-// items and starts the longest first -- then staged polygons of the walk form
-// (class 1), by decreasing expected cost, then staged polygons of the indexed
-// form (class 0) in Morton order of their box centres -- warps running at the
-// same time then read nearby cells of the stream index, which keeps them in
-// L2; counts classes 0 and 1 into n_cls[0], n_cls[1]
+// class key: polygons of more than kChunkMinVerts vertices (class 2) first, by
+// decreasing expected cost -- the signing launch splits them into 32-hash items
+// and starts the longest first -- then the staged polygons of the walk form and
+// the polygons above kStagedMaxVerts (class 1), by decreasing expected cost,
+// then staged polygons of the indexed form (class 0) in Morton order of their
+// box centres -- warps running at the same time then read nearby cells of the
+// stream index, which keeps them in L2; counts classes 0 and 1 into n_cls[0],
+// n_cls[1]
 __global__ void class_key_kernel(const int4* __restrict__ bbox, const int64_t* __restrict__ area2,
                                  const int64_t* __restrict__ off, int64_t n,
                                  uint32_t* __restrict__ keys, int32_t* __restrict__ ids,
@@ -194,8 +195,9 @@ __global__ void class_key_kernel(const int4* __restrict__ bbox, const int64_t* _
         const float aa = (float)(a < 0 ? -a : a);
         const float cost = 8589934592.0f / fmaxf(aa, 1.0f);
         const int4 bb = bbox[p];
-        const bool staged = off[p + 1] - off[p] <= kStagedMaxVerts;
-        const int cls = !staged ? 2 : pmh_index_plan(bb, a).lim > 0 ? 0 : 1;
+        const int64_t nv = off[p + 1] - off[p];
+        const int cls = nv > kChunkMinVerts ? 2
+                        : (nv > kStagedMaxVerts || pmh_index_plan(bb, a).lim == 0) ? 1 : 0;
         uint32_t key;
         if (cls == 0) {
             const uint32_t cx = (uint32_t)min((bb.x + bb.z) >> 1, 65535);
@@ -335,7 +337,7 @@ int pmh_build_class_order(pmh_polys P, cudaStream_t s)
         rc = pmh_set_error(PMH_ERR_CUDA, "class order: %s", cudaGetErrorString(e2));
     if (rc == PMH_OK) {
         P->n_indexed = ctx->h_pinned[0];
-        P->n_staged_walk = ctx->h_pinned[1];
+        P->n_whole_cost = ctx->h_pinned[1];
     }
     if (n_cls) cudaFree(n_cls);
     cudaFree(keys);

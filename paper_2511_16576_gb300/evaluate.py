@@ -227,15 +227,19 @@ def batch_capacity(ctx: B.Context, index: B.Index, params: B.Params, qp: B.Polys
     return int(max(per.max() if len(per) else 1, 1) * 1.25) + 1024
 
 
-def run_batches(g: B.QueryGraph, batches: Batches, ids_out: torch.Tensor, j_out: torch.Tensor,
+def run_batches(g: B.QueryGraph, batches: Batches, ids_out: torch.Tensor, j_out: torch.Tensor | None,
                 stream=None):
-    """Replay the graph on every batch; the refined top-k of batch b go to its rows of
-    ids_out / j_out (device or pinned host tensors, copied on the graph's stream)."""
+    """Replay the graph on every batch; the refined top-k of batch b (or, for a graph
+    without refinement, its top-m lists, with j_out None) go to its rows of ids_out /
+    j_out (device or pinned host tensors, copied on the graph's stream)."""
     q0 = 0
     for xy, off, n in zip(batches.xy, batches.off, batches.n):
         g.run(xy, off, stream=stream)
-        ids_out[q0:q0 + n].copy_(g.ref_ids[:n], non_blocking=True)
-        j_out[q0:q0 + n].copy_(g.ref_j[:n], non_blocking=True)
+        if g.k > 0:
+            ids_out[q0:q0 + n].copy_(g.ref_ids[:n], non_blocking=True)
+            j_out[q0:q0 + n].copy_(g.ref_j[:n], non_blocking=True)
+        else:
+            ids_out[q0:q0 + n].copy_(g.top_ids[:n], non_blocking=True)
         q0 += n
 
 
@@ -284,8 +288,8 @@ def batch_size_sweep(ctx: B.Context, index: B.Index, params: B.Params, dbp: B.Po
         g = B.QueryGraph(ctx, index, size, batches.max_vertices, cap, m, db=dbp, k=k, rerank=rerank,
                          shortlist=max(shortlist, m))
         dev = qs_xy.device
-        ids = torch.empty((n_q, k), dtype=torch.int32, device=dev)
-        jj = torch.empty((n_q, k), dtype=torch.float64, device=dev)
+        ids = torch.empty((n_q, k if k > 0 else m), dtype=torch.int32, device=dev)
+        jj = torch.empty((n_q, k), dtype=torch.float64, device=dev) if k > 0 else None
         run_batches(g, batches, ids, jj)
         _, t_graph = timed(lambda: run_batches(g, batches, ids, jj))
         g.close()
@@ -297,7 +301,8 @@ def batch_size_sweep(ctx: B.Context, index: B.Index, params: B.Params, dbp: B.Po
                 row_ptr, cand = B.lsh_query(ctx, index, qh)
                 count, _ = B.jaccard_estimate(ctx, qh, dbh, row_ptr, cand, params, bandmask=False)
                 tid, tn = B.topm(ctx, row_ptr, cand, count, m)
-                B.refine_topk(ctx, qp, dbp, tid, tn, k)
+                if k > 0:
+                    B.refine_topk(ctx, qp, dbp, tid, tn, k)
                 qp.close()
         plain()
         _, t_plain = timed(plain)
