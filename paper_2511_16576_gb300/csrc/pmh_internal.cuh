@@ -115,7 +115,7 @@ __host__ __device__ __forceinline__ uint32_t pmh_indexed_limit(int4 bb, long lon
 // index below M >> t.  The records of one cell for consecutive hashes are
 // adjacent, so a warp reading one cell for sixteen hashes reads 128 bytes.
 constexpr int kRankLevels = 6;
-// Plan of the indexed form for a polygon staged in shared memory (sign_indexed.cu),
+// Plan of the indexed form for a polygon (sign_unified.cu),
 // in estimated warp instructions per hash.  The limit is lim = 8 * 2^32 / area (a
 // hit below it is missed with probability ~e^-8; the walk then resumes at lim),
 // and at most ~24 box points below lim are expected.  The gather first reads the

@@ -215,16 +215,14 @@ sign_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
         const int64_t b = off[p];
         const int n = (int)(off[p + 1] - b);
         const int4 bb = bbox[p];
-        // (staged polygons of the indexed form have their own kernel, sign_indexed.cu)
+        // (with the stream index every polygon is signed by sign_unified.cu instead)
         const uint32_t lim = area2 && S.cell && n > kSmemVerts ? pmh_indexed_limit(bb, area2[p]) : 0;
         uint32_t mine;
         if (n <= kSmemVerts) {
-            // stage the vertices (closed: v[n] = v[0]; coalesced 8-byte loads), the
+            // stage the vertices (closed: v[n] = v[0]; cp.async 8-byte copies), the
             // coverage mask if any, and the slab lists in this warp's shared-memory slice
-            for (int i = lane; i < n; i += 32) sv[wid][i] = xy[b + i];
-            if (lane == 0) sv[wid][n] = xy[b];
             if (masks && lane < 16) smask[wid][lane] = masks[p * 16 + lane];
-            __syncwarp();
+            stage_vertices(sv[wid], xy + b, n, lane);
             const int sh = staged_slab_shift(max(bb.w - bb.y, 1));
             const bool staged = bb.w > bb.y && bb.z > bb.x &&
                                 build_staged_slabs(sv[wid], n, bb.y, sh, sid[wid], sbeg[wid], scnt[wid], lane);

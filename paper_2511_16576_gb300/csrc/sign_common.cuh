@@ -13,6 +13,20 @@ constexpr int kSlabs = 32;       // horizontal slabs of a staged polygon
 constexpr int kSlabCap = 512;    // (edge, slab) references of a staged polygon
 
 
+// Stage a polygon's n vertices into shared memory, closed (dst[n] = dst[0]), with
+// asynchronous 8-byte global-to-shared copies (cp.async: the data bypasses the
+// registers); the warp waits for its copies and synchronises before returning.
+__device__ __forceinline__ void stage_vertices(int2* dst, const int2* __restrict__ src, int n, int lane)
+{
+    for (int i = lane; i <= n; i += 32) {
+        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + i);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src + (i == n ? 0 : i))
+                     : "memory");
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncwarp();
+}
+
 // Parity contribution of edge a->b to the half-open crossing test of lattice
 // point (px, py): the edge counts iff it straddles y = py ((ay > py) != (by > py))
 // and the int64 cross product (b - a) x (p - a) is non-zero with the sign of

@@ -565,10 +565,8 @@ sign_unified_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
         // the form (indexed or walk) and grid level the polygon's cost model picks
         const PmhIndexPlan plan = (S.cell && area2) ? pmh_index_plan(bb, area2[p]) : PmhIndexPlan{0u, 0, 0u};
         if (staged) {
-            // stage the polygon (closed: v[n] = v[0]; coalesced 8-byte loads) and bin its edges
-            for (int i = lane; i < n; i += 32) m.v[i] = xy[b + i];
-            if (lane == 0) m.v[n] = xy[b];
-            __syncwarp();
+            // stage the polygon (closed: v[n] = v[0]; cp.async 8-byte copies) and bin its edges
+            stage_vertices(m.v, xy + b, n, lane);
             int sh = staged_slab_shift(bb.w - bb.y);
             if (!build_staged_slabs(m.v, n, bb.y, sh, m.ids, m.beg, m.cnt, lane)) sh = single_slab(m, n, lane);
             const StagedSrc src{m.v, m.ids, m.beg, bb.y, sh};
