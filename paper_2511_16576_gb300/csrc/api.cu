@@ -135,6 +135,7 @@ __global__ void prep_kernel(const int2* __restrict__ xy, const int64_t* __restri
     int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int LIM = 1 << 20;
+    int nmax = 0;  // largest vertex count of the warp's polygons (one atomic at the end)
     for (int64_t p = warp; p < n_polys; p += nwarps) {
         int64_t b = off[p], e = off[p + 1];
         int flags = 0;
@@ -151,15 +152,32 @@ __global__ void prep_kernel(const int2* __restrict__ xy, const int64_t* __restri
         }
         int x0 = INT_MAX, y0 = INT_MAX, x1 = INT_MIN, y1 = INT_MIN;
         long long a2 = 0;
-        for (int64_t i = lane; i < n; i += 32) {
-            int2 v = xy[b + i];
-            int2 w = xy[b + (i + 1 == n ? 0 : i + 1)];
-            if (v.x < -LIM || v.x > LIM || v.y < -LIM || v.y > LIM) flags |= 4;
-            x0 = min(x0, v.x);
-            x1 = max(x1, v.x);
-            y0 = min(y0, v.y);
-            y1 = max(y1, v.y);
-            a2 += (long long)v.x * w.y - (long long)w.x * v.y;
+        // four vertices per lane in flight; edge i's end vertex is lane + 1's vertex
+        // (a shuffle), lane 31 reads it
+        for (int64_t i0 = 0; i0 < n; i0 += 128) {
+            int2 v[4], w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + 32 * u + lane;
+                v[u] = i < n ? xy[b + i] : xy[b];
+                w[u] = lane == 31 && i < n ? xy[b + (i + 1 == n ? 0 : i + 1)] : v[u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t i = i0 + 32 * u + lane;
+                const int wx = __shfl_down_sync(0xffffffffu, v[u].x, 1);
+                const int wy = __shfl_down_sync(0xffffffffu, v[u].y, 1);
+                if (lane < 31) w[u] = make_int2(wx, wy);
+                if (i < n) {
+                    if (i + 1 == n) w[u] = xy[b];
+                    if (v[u].x < -LIM || v[u].x > LIM || v[u].y < -LIM || v[u].y > LIM) flags |= 4;
+                    x0 = min(x0, v[u].x);
+                    x1 = max(x1, v[u].x);
+                    y0 = min(y0, v[u].y);
+                    y1 = max(y1, v[u].y);
+                    a2 += (long long)v[u].x * w[u].y - (long long)w[u].x * v[u].y;
+                }
+            }
         }
         x0 = __reduce_min_sync(0xffffffffu, x0);
         y0 = __reduce_min_sync(0xffffffffu, y0);
@@ -175,9 +193,10 @@ __global__ void prep_kernel(const int2* __restrict__ xy, const int64_t* __restri
             if (cy1 < cy0) cy1 = cy0;
             bbox[p] = make_int4(cx0, cy0, cx1, cy1);
             area2[p] = a2;
-            atomicMax(&status[1], (int)(n < INT_MAX ? n : INT_MAX));
+            nmax = max(nmax, (int)(n < INT_MAX ? n : INT_MAX));
         }
     }
+    if (lane == 0 && nmax > 0) atomicMax(&status[1], nmax);
 }
 
 int pmh_launch_prep(int sm_count, const int2* xy, const int64_t* off, int64_t n_polys,

@@ -1,12 +1,13 @@
 // estimate.cu -- steps A5 (agreement estimate) and A6 (top-m selection).
 //
 // A5 follows Theorem 1: Pr[h_k(q) = h_k(p)] = J(q, p), so the fraction of
-// agreeing positions estimates J.  One block handles one query row: the
-// query's hashes sit in shared memory, each warp takes one candidate at a
-// time and reads its K hashes as 16-byte vectors (512 bytes per row at
-// K = 128); equality bits are gathered with shuffles, the count is a warp
-// reduction, and the band-match bits and the reranker's features (A7) come
-// from the same bits.
+// agreeing positions estimates J.  The candidate pairs of all rows are cut into
+// chunks of consecutive pairs that warps take in turn (rows range from a few
+// candidates to thousands, so a block per row would leave the grid waiting on
+// the longest); a warp reads both rows' K hashes as 16-byte vectors (512 bytes
+// per row at K = 128, the query's from L1/L2); equality bits are gathered with
+// shuffles, the count is a warp reduction, and the band-match bits and the
+// reranker's features (A7) come from the same bits.
 //
 // A6 sorts each candidate row by a 64-bit key in shared memory (bitonic),
 // keeping the first m: key = (K - count) << 32 | id for the plain form,
@@ -21,11 +22,12 @@ namespace {
 
 constexpr int kMaxK = 4096;
 constexpr int kAgreeWarps = 4;
+constexpr int kAgreeChunk = 16;  // consecutive pairs per warp turn
 
-// One block per query (its hashes staged in shared memory once), warps stride
-// over the query's candidate row.  Per pair: equality bits of the K hashes
-// (16-byte loads when K % 4 == 0), the count (warp sum), the full-match bits
-// of the first 32 bands and, optionally, the reranker's feature row.
+// Warps take chunks of kAgreeChunk consecutive pairs (the row of the first by
+// binary search over row_ptr, then stepping on).  Per pair: equality bits of the
+// K hashes (16-byte loads when K % 4 == 0), the count (warp sum), the full-match
+// bits of the first 32 bands and, optionally, the reranker's feature row.
 __global__ void __launch_bounds__(kAgreeWarps * 32)
 agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ ph,
                   const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cand, int64_t Q,
@@ -33,17 +35,24 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
                   uint32_t* __restrict__ bandmask, __nv_bfloat16* __restrict__ feat, FeatSrc qf,
                   FeatSrc pf, const int* __restrict__ d_flags)
 {
-    __shared__ __align__(16) uint32_t qs[kMaxK];
     __shared__ uint32_t eqbits[kAgreeWarps][kMaxK / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (d_flags && *d_flags) return;  // failed validation or candidate overflow
-    for (int64_t q = blockIdx.x; q < Q; q += gridDim.x) {
-        const int64_t b = min(row_ptr[q], cap), e = min(row_ptr[q + 1], cap);
-        if (b >= e) continue;
-        __syncthreads();
-        for (int i = threadIdx.x; i < K; i += blockDim.x) qs[i] = qh[q * K + i];
-        __syncthreads();
-        for (int64_t x = b + wid; x < e; x += kAgreeWarps) {
+    const int64_t total = min(row_ptr[Q], cap);
+    const int64_t nwarps = (int64_t)gridDim.x * kAgreeWarps;
+    for (int64_t ch = (int64_t)blockIdx.x * kAgreeWarps + wid; ch * kAgreeChunk < total; ch += nwarps) {
+        const int64_t x0 = ch * kAgreeChunk, x1 = min(x0 + kAgreeChunk, total);
+        // the row holding pair x0: the last q with row_ptr[q] <= x0
+        int64_t lo = 0, hi = Q;
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (row_ptr[mid] <= x0) lo = mid;
+            else hi = mid;
+        }
+        int64_t q = lo;
+        for (int64_t x = x0; x < x1; ++x) {
+            while (row_ptr[q + 1] <= x) ++q;
+            const uint32_t* qs = qh + q * K;
             const int64_t p = cand[x];
             const uint32_t* bp = ph + p * K;
             int c = 0, lt = 0, gt = 0;  // lt / gt: hashes with h(q) < h(p) / h(q) > h(p)
@@ -54,7 +63,7 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
                     const int i = base + lane;
                     unsigned bits = 0;
                     if (i < K / 4) {
-                        const uint4 u = a4[i], v = __ldg(b4 + i);
+                        const uint4 u = __ldg(a4 + i), v = __ldg(b4 + i);
                         bits = (unsigned)((u.x == v.x) & (u.x != T)) |
                                ((unsigned)((u.y == v.y) & (u.y != T)) << 1) |
                                ((unsigned)((u.z == v.z) & (u.z != T)) << 2) |
@@ -279,7 +288,7 @@ int pmh_launch_agree_features(pmh_ctx ctx, const uint32_t* qh, const uint32_t* p
                               cudaStream_t s)
 {
     if (Q <= 0) return PMH_OK;
-    const int blocks = (int)std::min<int64_t>(Q, (int64_t)ctx->sm_count * 16);
+    const int blocks = ctx->sm_count * 16;  // persistent: pair chunks are handed out in turn
     agree_rows_kernel<<<blocks, kAgreeWarps * 32, 0, s>>>(
         qh, ph, row_ptr, cand, Q, cap, (int)P->K, (int)P->bands, (int)P->rows, P->T, count, bandmask,
         reinterpret_cast<__nv_bfloat16*>(feat), qf, pf, d_flags);

@@ -240,7 +240,7 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_
                                  g->flags, cs);
     }
     if (rc == PMH_OK && k > 0)
-        rc = pmh_launch_refine_topk(ctx, g->xy, g->off, g->area2, db, g->top_ids, g->top_n, Q, g->d_n, m,
+        rc = pmh_launch_refine_topk(ctx, g->xy, g->off, g->area2, g->bbox, db, g->top_ids, g->top_n, Q, g->d_n, m,
                                     k, g->jv, g->ticket + 1, g->ref_ids, g->ref_j, cs);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(cs, &graph);

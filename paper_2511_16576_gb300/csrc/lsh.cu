@@ -5,8 +5,10 @@
 // Sec. 5.2; "2 hashmaps", Sec. 5.3).  Here one hashmap per band is a sorted
 // array: entry (band j, polygon p) gets a 32-bit composite sort key
 // (j in the top band_bits bits, the top bits of the 64-bit band key below),
-// stable-radix-sorted so that equal composites keep ascending ids.  A query
-// binary-searches its composite per band and walks the equal range, keeping
+// stable-radix-sorted so that equal composites keep ascending ids.  A
+// directory over the composites' top bits (about eight entries per slot)
+// bounds each lookup to one short range.  A query
+// binary-searches its composite there per band and walks the equal range, keeping
 // entries whose full 64-bit key AND r-tuple equal its own (exact bucket
 // membership).  The per-band id lists are ascending, so a warp merges them
 // (min over lanes) into the sorted, duplicate-free candidate row.
@@ -76,6 +78,39 @@ __global__ void gather_keys_kernel(const uint32_t* __restrict__ comp, const int3
     }
 }
 
+// The directory covers the composites of valid entries, [0, cmax) with
+// cmax = bands << (32 - band_bits) (invalid entries, all ones, sort last and are
+// never looked up): dir[s] = first sorted entry whose composite >> sh is >= s,
+// for s in [0, ceil(cmax / 2^sh)].  Thread e writes the slots after its predecessor's,
+// up to its own (thread m: up to the last), so every slot is written once; the
+// keys are uniform, so gaps are a slot or two (a band without one valid entry
+// leaves one thread a gap of 2^(32 - band_bits - sh) slots).
+__global__ void dir_kernel(const uint32_t* __restrict__ comp, int64_t m, int sh, int64_t cmax,
+                           int64_t* __restrict__ dir)
+{
+    const int64_t top = (cmax + (1ll << sh) - 1) >> sh;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e <= m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cs = e < m ? min((int64_t)comp[e], cmax) >> sh : top;
+        const int64_t ps = e == 0 ? 0 : (min((int64_t)comp[e - 1], cmax) >> sh) + 1;
+        for (int64_t s = ps; s <= cs; ++s) dir[s] = e;
+    }
+}
+
+// first sorted entry whose composite is >= c
+__device__ __forceinline__ int64_t comp_lower_bound(const uint32_t* __restrict__ comp,
+                                                    const int64_t* __restrict__ dir, int sh, uint32_t c)
+{
+    const uint32_t s = c >> sh;
+    int64_t lo = dir[s], hi = dir[s + 1];
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (comp[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 constexpr int kMaxBandsPerLane = 4;  // bands <= 128
 constexpr int32_t kNone = 0x7FFFFFFF;
 
@@ -125,7 +160,8 @@ __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, in
                              int rows, uint32_t T, uint64_t lsh_seed, int band_bits,
                              const uint32_t* __restrict__ comp, const int32_t* __restrict__ ids,
                              const uint64_t* __restrict__ skeys, const uint32_t* __restrict__ dbh,
-                             int64_t m, int64_t* __restrict__ counts,
+                             const int64_t* __restrict__ dir, int dsh, int64_t m,
+                             int64_t* __restrict__ counts,
                              const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand,
                              int64_t cap, const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
 {
@@ -156,14 +192,7 @@ __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, in
         if (key == PMH_INVALID_KEY) continue;
         cur[t].key = key;
         cur[t].comp = composite(key, j, band_bits);
-        // lower bound of comp in the sorted composite array
-        int64_t lo = 0, hi = m;
-        while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
-            if (comp[mid] < cur[t].comp) lo = mid + 1;
-            else hi = mid;
-        }
-        cur[t].cur = lo;
+        cur[t].cur = comp_lower_bound(comp, dir, dsh, cur[t].comp);
         advance(cur[t], comp, ids, skeys, dbh, qh, m, K, bands, rows);
     }
     int64_t out = kWrite ? row_ptr[q] : 0;
@@ -188,16 +217,26 @@ __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, in
 // entries) and insert exact matches into a shared-memory open-addressing set,
 // which drops the duplicates (a candidate found in several bands).  The set is
 // then compacted and bitonic-sorted, which yields the same ascending,
-// duplicate-free row as the warp merge.  A row with more distinct
-// candidates than the set can hold falls back to the warp merge (warp 0).
-constexpr int kJoinThreads = 512;
-constexpr int kJoinTable = 32768;            // shared set slots (128 KiB)
-constexpr int kJoinMaxUnique = kJoinTable / 2;
+// duplicate-free row as the warp merge.  Two set sizes: the small one (8,192
+// slots, several blocks per SM) takes every row of at most 4,096 distinct
+// candidates; a row that overflows it is marked (count -1) and counted again,
+// like every longer row filled, by the large one (32,768 slots, one block per
+// SM).  A row beyond even that falls back to the warp merge (warp 0).
+template <bool kBig>
+struct JoinShape {
+    static constexpr int kThreads = kBig ? 512 : 256;
+    static constexpr int kLog2Table = kBig ? 15 : 13;
+    static constexpr int kTable = 1 << kLog2Table;   // shared set slots
+    static constexpr int kMaxUnique = kTable / 2;    // load factor <= 1/2
+    static constexpr size_t kSmem = sizeof(int32_t) * (kTable + kMaxUnique);
+};
+constexpr int kSmallRowMax = JoinShape<false>::kMaxUnique;
 
 __device__ int64_t merge_row(const uint32_t* __restrict__ qh, int K, int bands, int rows, uint32_t T,
                              uint64_t lsh_seed, int band_bits, const uint32_t* __restrict__ comp,
                              const int32_t* __restrict__ ids, const uint64_t* __restrict__ skeys,
-                             const uint32_t* __restrict__ dbh, int64_t m, int32_t* __restrict__ out)
+                             const uint32_t* __restrict__ dbh, const int64_t* __restrict__ dir,
+                             int dsh, int64_t m, int32_t* __restrict__ out)
 {
     const int lane = threadIdx.x & 31;
     BandCursor cur[kMaxBandsPerLane];
@@ -211,13 +250,7 @@ __device__ int64_t merge_row(const uint32_t* __restrict__ qh, int K, int bands, 
         if (key == PMH_INVALID_KEY) continue;
         cur[t].key = key;
         cur[t].comp = composite(key, j, band_bits);
-        int64_t lo = 0, hi = m;
-        while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
-            if (comp[mid] < cur[t].comp) lo = mid + 1;
-            else hi = mid;
-        }
-        cur[t].cur = lo;
+        cur[t].cur = comp_lower_bound(comp, dir, dsh, cur[t].comp);
         advance(cur[t], comp, ids, skeys, dbh, qh, m, K, bands, rows);
     }
     int64_t cnt = 0;
@@ -236,35 +269,43 @@ __device__ int64_t merge_row(const uint32_t* __restrict__ qh, int K, int bands, 
     return cnt;
 }
 
+template <int kLog2>
 __device__ __forceinline__ uint32_t slot_hash(int32_t p)
 {
-    return ((uint32_t)p * 0x9E3779B1u) >> (32 - 15);  // 15 bits = log2(kJoinTable)
+    return ((uint32_t)p * 0x9E3779B1u) >> (32 - kLog2);
 }
 
-template <bool kWrite>
-__global__ void __launch_bounds__(kJoinThreads)
+template <bool kWrite, bool kBig>
+__global__ void __launch_bounds__(JoinShape<kBig>::kThreads)
 join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, int rows, uint32_t T,
             uint64_t lsh_seed, int band_bits, const uint32_t* __restrict__ comp,
             const int32_t* __restrict__ ids, const uint64_t* __restrict__ skeys,
-            const uint32_t* __restrict__ dbh, int64_t m, int64_t* __restrict__ counts,
+            const uint32_t* __restrict__ dbh, const int64_t* __restrict__ dir, int dsh, int64_t m,
+            int64_t* __restrict__ counts,
             const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand, int64_t cap,
             const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
 {
+    using S = JoinShape<kBig>;
+    constexpr int kJoinTable = S::kTable, kJoinMaxUnique = S::kMaxUnique;
     extern __shared__ int32_t table[];  // kJoinTable slots, then kJoinMaxUnique sorted ids
     __shared__ int n_unique;
-    __shared__ int wsum[kJoinThreads / 32];
+    __shared__ int wsum[S::kThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     for (int64_t q = blockIdx.x; q < Q; q += gridDim.x) {
         const bool skip = (d_n && q >= *d_n) || (d_flags && (*d_flags & 7));
         if (skip) {
-            if (!kWrite && threadIdx.x == 0) counts[q] = 0;
+            if (!kWrite && !kBig && threadIdx.x == 0) counts[q] = 0;
             continue;
         }
         if (kWrite && row_ptr[Q] > cap) {
             if (threadIdx.x == 0 && d_flags) atomicOr(d_flags, 8);
             return;
         }
+        // rows by size: the small set counts every row and fills the short ones; the
+        // large set counts the rows that overflowed the small one and fills the long ones
+        if (!kWrite && kBig && counts[q] >= 0) continue;
+        if (kWrite && ((row_ptr[q + 1] - row_ptr[q] > kSmallRowMax) != kBig)) continue;
         const uint32_t* qh = qhashes + q * K;
         __syncthreads();
         for (int i = threadIdx.x; i < kJoinTable; i += blockDim.x) table[i] = kNone;
@@ -274,12 +315,7 @@ join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, i
             const uint64_t key = band_key(qh, j, rows, T, lsh_seed);
             if (key == PMH_INVALID_KEY) continue;
             const uint32_t c = composite(key, j, band_bits);
-            int64_t lo = 0, hi = m;
-            while (lo < hi) {
-                int64_t mid = (lo + hi) >> 1;
-                if (comp[mid] < c) lo = mid + 1;
-                else hi = mid;
-            }
+            const int64_t lo = comp_lower_bound(comp, dir, dsh, c);
             for (int64_t base = lo;; base += 32) {
                 const int64_t e = base + lane;
                 const bool in = e < m && comp[e] == c;
@@ -287,7 +323,7 @@ join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, i
                 if (!in || skeys[e] != key) continue;
                 const int32_t p = ids[e];
                 if (!tuple_equal(qh, dbh + (int64_t)p * K, j, rows)) continue;
-                uint32_t h = slot_hash(p);
+                uint32_t h = slot_hash<S::kLog2Table>(p);
                 for (int probe = 0; probe < kJoinTable; ++probe, h = (h + 1) & (kJoinTable - 1)) {
                     const int32_t old = atomicCAS(&table[h], kNone, p);
                     if (old == kNone) {
@@ -301,10 +337,14 @@ join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, i
         }
         __syncthreads();
         const int nu = n_unique;
+        if (!kBig && nu > kJoinMaxUnique) {  // the large set counts this row again
+            if (threadIdx.x == 0) counts[q] = -1;
+            continue;
+        }
         if (nu > kJoinMaxUnique) {  // rare: merge the row with warp 0
             if (wid == 0) {
                 int64_t cnt = merge_row(qh, K, bands, rows, T, lsh_seed, band_bits, comp, ids, skeys,
-                                        dbh, m, kWrite ? cand + row_ptr[q] : nullptr);
+                                        dbh, dir, dsh, m, kWrite ? cand + row_ptr[q] : nullptr);
                 if (!kWrite && lane == 0) counts[q] = cnt;
             }
             continue;
@@ -316,7 +356,7 @@ join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, i
         // compact the occupied slots into buf (block scan over contiguous slot ranges),
         // then sort only the next power of two above nu
         int32_t* buf = table + kJoinTable;
-        constexpr int kPer = kJoinTable / kJoinThreads;
+        constexpr int kPer = kJoinTable / S::kThreads;
         const int s0 = threadIdx.x * kPer;
         int mine = 0;
         for (int i = 0; i < kPer; ++i) mine += table[s0 + i] != kNone;
@@ -372,6 +412,17 @@ extern "C" int pmh_band_keys(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
     return PMH_OK;
 }
 
+// end of the composites of valid entries (the directory's range), and the directory's
+// length (slots + 1)
+static int64_t dir_cmax(pmh_index X)
+{
+    return (int64_t)X->params.bands << (32 - X->band_bits);
+}
+static size_t dir_len(pmh_index X)
+{
+    return (size_t)((dir_cmax(X) + (1ll << X->dir_shift) - 1) >> X->dir_shift) + 1;
+}
+
 // hashes copied in, band keys, (band, key) entries radix-sorted with ids, full keys gathered
 static int index_fill(pmh_ctx ctx, pmh_index X, const uint32_t* d_hashes, cudaStream_t s)
 {
@@ -379,7 +430,10 @@ static int index_fill(pmh_ctx ctx, pmh_index X, const uint32_t* d_hashes, cudaSt
     const pmh_params* params = &X->params;
     const int bb = X->band_bits;
     const int64_t entries = n * params->bands;
-    if (n == 0) return PMH_OK;
+    if (n == 0) {
+        PMH_CUDA_TRY(cudaMemsetAsync(X->dir, 0, sizeof(int64_t) * dir_len(X), s));
+        return PMH_OK;
+    }
     cudaError_t e = cudaMemcpyAsync(X->hashes, d_hashes, sizeof(uint32_t) * n * params->K,
                                     cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return pmh_set_error(PMH_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
@@ -392,7 +446,18 @@ static int index_fill(pmh_ctx ctx, pmh_index X, const uint32_t* d_hashes, cudaSt
     gather_keys_kernel<<<blocks, 256, 0, s>>>(X->sorted_comp, X->sorted_id, X->keys, entries,
                                                (int)params->bands, bb, X->sorted_key);
     PMH_LAUNCHED("gather_keys_kernel");
+    const int dblocks = (int)std::min<int64_t>((entries + 256) / 256, (int64_t)ctx->sm_count * 32);
+    dir_kernel<<<dblocks, 256, 0, s>>>(X->sorted_comp, entries, X->dir_shift, dir_cmax(X), X->dir);
+    PMH_LAUNCHED("dir_kernel");
     return PMH_OK;
+}
+
+// directory shift: about eight sorted entries per slot over [0, cmax), at most 2^24 slots
+static int dir_shift_for(int64_t entries, int64_t cmax)
+{
+    int sh = 31;
+    while (sh > 0 && (cmax >> (sh - 1)) <= (int64_t)1 << 24 && (cmax >> (sh - 1)) * 8 <= entries) --sh;
+    return sh;
 }
 
 extern "C" int pmh_lsh_build(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
@@ -414,12 +479,14 @@ extern "C" int pmh_lsh_build(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
     while ((1u << bb) - 1 < params->bands) ++bb;  // band index < 2^bb - 1: comp never all ones
     X->band_bits = bb;
     const int64_t entries = n * params->bands;
+    X->dir_shift = dir_shift_for(entries, dir_cmax(X));
     const size_t nn = (size_t)std::max<int64_t>(n, 1), ne = (size_t)std::max<int64_t>(entries, 1);
     if (cudaMalloc(&X->hashes, sizeof(uint32_t) * nn * params->K) != cudaSuccess ||
         cudaMalloc(&X->keys, sizeof(uint64_t) * nn * params->bands) != cudaSuccess ||
         cudaMalloc(&X->sorted_comp, sizeof(uint32_t) * ne) != cudaSuccess ||
         cudaMalloc(&X->sorted_id, sizeof(int32_t) * ne) != cudaSuccess ||
-        cudaMalloc(&X->sorted_key, sizeof(uint64_t) * ne) != cudaSuccess) {
+        cudaMalloc(&X->sorted_key, sizeof(uint64_t) * ne) != cudaSuccess ||
+        cudaMalloc(&X->dir, sizeof(int64_t) * dir_len(X)) != cudaSuccess) {
         cudaGetLastError();
         pmh_index_destroy(X);
         return pmh_set_error(PMH_ERR_NOMEM, "index allocation failed (n=%lld)", (long long)n);
@@ -453,7 +520,33 @@ extern "C" int pmh_index_destroy(pmh_index X)
     if (X->sorted_comp) cudaFree(X->sorted_comp);
     if (X->sorted_id) cudaFree(X->sorted_id);
     if (X->sorted_key) cudaFree(X->sorted_key);
+    if (X->dir) cudaFree(X->dir);
     delete X;
+    return PMH_OK;
+}
+
+// one of the two block joins (both run: the large one after the small one)
+template <bool kBig>
+static int launch_join(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
+                       int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
+                       int* d_flags, bool write, cudaStream_t s)
+{
+    using S = JoinShape<kBig>;
+    const pmh_params& P = X->params;
+    const int64_t m = X->n * P.bands;
+    auto fn = write ? join_kernel<true, kBig> : join_kernel<false, kBig>;
+    PMH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem));
+    int per_sm = 1;
+    PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, S::kThreads, S::kSmem));
+    const unsigned blocks =
+        (unsigned)std::min<int64_t>(Q, (int64_t)X->ctx->sm_count * std::max(per_sm, 1));
+    fn<<<blocks, S::kThreads, S::kSmem, s>>>(qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T,
+                                            P.lsh_seed, X->band_bits, X->sorted_comp, X->sorted_id,
+                                            X->sorted_key, X->hashes, X->dir, X->dir_shift, m,
+                                            write ? nullptr : counts, write ? row_ptr : nullptr,
+                                            write ? cand : nullptr, write ? cap : 0, d_n, d_flags);
+    PMH_LAUNCHED(write ? (kBig ? "join_kernel<fill,large>" : "join_kernel<fill,small>")
+                       : (kBig ? "join_kernel<count,large>" : "join_kernel<count,small>"));
     return PMH_OK;
 }
 
@@ -468,39 +561,23 @@ int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* 
     // set (rows of thousands of candidates occur on dense sets; the warp merge below
     // would walk them one candidate at a time)
     if (P.bands >= 16) {
-        const unsigned blocks = (unsigned)std::min<int64_t>(Q, (int64_t)X->ctx->sm_count);
-        const size_t smem = sizeof(int32_t) * (kJoinTable + kJoinMaxUnique);
-        PMH_CUDA_TRY(cudaFuncSetAttribute(join_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-        PMH_CUDA_TRY(cudaFuncSetAttribute(join_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-        if (write) {
-            join_kernel<true><<<blocks, kJoinThreads, smem, s>>>(
-                qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T, P.lsh_seed, X->band_bits,
-                X->sorted_comp, X->sorted_id, X->sorted_key, X->hashes, m, nullptr, row_ptr, cand, cap,
-                d_n, d_flags);
-            PMH_LAUNCHED("join_kernel<fill>");
-        } else {
-            join_kernel<false><<<blocks, kJoinThreads, smem, s>>>(
-                qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T, P.lsh_seed, X->band_bits,
-                X->sorted_comp, X->sorted_id, X->sorted_key, X->hashes, m, counts, nullptr, nullptr, 0,
-                d_n, d_flags);
-            PMH_LAUNCHED("join_kernel<count>");
-        }
-        return PMH_OK;
+        PMH_TRY(launch_join<false>(X, qh, Q, d_n, counts, row_ptr, cand, cap, d_flags, write, s));
+        return launch_join<true>(X, qh, Q, d_n, counts, row_ptr, cand, cap, d_flags, write, s);
     }
     const int wpb = 8;
     unsigned blocks = (unsigned)((Q + wpb - 1) / wpb);
     if (write) {
         query_kernel<true><<<blocks, wpb * 32, 0, s>>>(
             qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T, P.lsh_seed, X->band_bits,
-            X->sorted_comp, X->sorted_id, X->sorted_key, X->hashes, m, nullptr, row_ptr, cand, cap, d_n,
+            X->sorted_comp, X->sorted_id, X->sorted_key, X->hashes, X->dir, X->dir_shift, m, nullptr,
+                row_ptr, cand, cap, d_n,
             d_flags);
         PMH_LAUNCHED("query_kernel<fill>");
     } else {
         query_kernel<false><<<blocks, wpb * 32, 0, s>>>(
             qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T, P.lsh_seed, X->band_bits,
-            X->sorted_comp, X->sorted_id, X->sorted_key, X->hashes, m, counts, nullptr, nullptr, 0, d_n,
+            X->sorted_comp, X->sorted_id, X->sorted_key, X->hashes, X->dir, X->dir_shift, m, counts,
+                nullptr, nullptr, 0, d_n,
             d_flags);
         PMH_LAUNCHED("query_kernel<count>");
     }

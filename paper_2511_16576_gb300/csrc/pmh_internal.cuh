@@ -273,6 +273,11 @@ struct pmh_index_s {
     uint32_t* sorted_comp = nullptr;  // [n * bands] composite (band, key) sort keys
     int32_t* sorted_id = nullptr;     // [n * bands]
     uint64_t* sorted_key = nullptr;   // [n * bands] full band key of each sorted entry
+    // directory of the sorted composites: dir[s] = first entry whose composite >> dir_shift
+    // is >= s, for s in [0, (bands << (32 - band_bits)) >> dir_shift] (a lower bound of a
+    // valid composite reads one short range)
+    int64_t* dir = nullptr;
+    int dir_shift = 32;
 };
 
 // grow-only scratch buffer of the context
@@ -366,7 +371,7 @@ int pmh_launch_agree_features(pmh_ctx ctx, const uint32_t* qh, const uint32_t* p
 // (J desc, id asc) (refine.cu); jv: Q * m doubles of scratch; ticket: the grid's counter;
 // d_n (optional) caps Q on the device
 int pmh_launch_refine_topk(pmh_ctx ctx, const int2* qxy, const int64_t* qoff, const int64_t* qarea2,
-                           pmh_polys db, const int32_t* ids, const int32_t* nlist, int64_t Q,
+                           const int4* qbox, pmh_polys db, const int32_t* ids, const int32_t* nlist, int64_t Q,
                            const int64_t* d_n, int32_t m, int32_t k, double* jv,
                            unsigned long long* ticket, int32_t* top_ids, double* top_j,
                            cudaStream_t s);

@@ -399,6 +399,16 @@ struct RefWarp {
     RefSlabs sl[2];
 };
 
+// n vertices to shared memory by asynchronous 8-byte copies (all in flight at once;
+// the caller waits)
+__device__ __forceinline__ void stage_ring(int2* dst, const int2* __restrict__ src, int n, int lane)
+{
+    for (int i = lane; i < n; i += 32) {
+        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + i);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src + i) : "memory");
+    }
+}
+
 // J of one pair by one warp: both rings staged in the warp's shared slice when they
 // fit, else read from global memory; y-slab lists of both rings when they fit their
 // capacity, else every edge pair
@@ -408,8 +418,9 @@ __device__ double warp_pair_jaccard(PairView A, PairView B, RefWarp& w, int lane
     const int2* a = A.v;
     const int2* b = B.v;
     if (A.n + B.n <= kWarpVerts) {
-        for (int i = lane; i < A.n; i += 32) w.sv[i] = A.v[i];
-        for (int i = lane; i < B.n; i += 32) w.sv[A.n + i] = B.v[i];
+        stage_ring(w.sv, A.v, A.n, lane);
+        stage_ring(w.sv + A.n, B.v, B.n, lane);
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
         __syncwarp();
         a = w.sv;
         b = w.sv + A.n;
@@ -426,8 +437,9 @@ __device__ double warp_pair_jaccard(PairView A, PairView B, RefWarp& w, int lane
 
 __global__ void __launch_bounds__(kRefineWarps * 32)
 refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qoff,
-                    const int64_t* __restrict__ qarea2, const int2* __restrict__ pxy,
-                    const int64_t* __restrict__ poff, const int64_t* __restrict__ parea2,
+                    const int64_t* __restrict__ qarea2, const int4* __restrict__ qbox,
+                    const int2* __restrict__ pxy, const int64_t* __restrict__ poff,
+                    const int64_t* __restrict__ parea2, const int4* __restrict__ pbox,
                     const int32_t* __restrict__ ids, const int32_t* __restrict__ nlist, int m,
                     const int32_t* __restrict__ qid_list, int64_t n_pairs, double* __restrict__ out,
                     unsigned long long* __restrict__ ticket, const int64_t* __restrict__ d_n)
@@ -457,7 +469,12 @@ refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qo
             }
             p = ids[e];
         }
-        const double j = warp_pair_jaccard(view(qxy, qoff, qarea2, q), view(pxy, poff, parea2, p), w, lane);
+        // bounding boxes (half-open lattice boxes) without a common interior point: an
+        // empty intersection, J = 0 exactly, as the full computation gives
+        const int4 a = qbox[q], b = pbox[p];
+        const bool apart = !(a.x < b.z && b.x < a.z && a.y < b.w && b.y < a.w);
+        const double j =
+            apart ? 0.0 : warp_pair_jaccard(view(qxy, qoff, qarea2, q), view(pxy, poff, parea2, p), w, lane);
         if (lane == 0) out[e] = j;
     }
 }
@@ -519,7 +536,7 @@ __global__ void topk_by_j_kernel(const int32_t* __restrict__ ids, const int32_t*
 
 // persistent grid (SM count x resident blocks) over the pairs
 static int launch_refine(pmh_ctx ctx, const int2* qxy, const int64_t* qoff, const int64_t* qarea2,
-                         pmh_polys db, const int32_t* ids, const int32_t* nlist, int m,
+                         const int4* qbox, pmh_polys db, const int32_t* ids, const int32_t* nlist, int m,
                          const int32_t* qid_list, int64_t n_pairs, double* out,
                          unsigned long long* ticket, const int64_t* d_n, cudaStream_t s)
 {
@@ -533,8 +550,8 @@ static int launch_refine(pmh_ctx ctx, const int2* qxy, const int64_t* qoff, cons
                                               (int64_t)ctx->sm_count * std::max(per_sm, 1));
     PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
     refine_pairs_kernel<<<blocks, kRefineWarps * 32, smem, s>>>(
-        qxy, qoff, qarea2, db->xy, db->offsets, db->area2, ids, nlist, m, qid_list, n_pairs, out, ticket,
-        d_n);
+        qxy, qoff, qarea2, qbox, db->xy, db->offsets, db->area2, db->bbox, ids, nlist, m, qid_list,
+        n_pairs, out, ticket, d_n);
     PMH_LAUNCHED("refine_pairs_kernel");
     return PMH_OK;
 }
@@ -543,13 +560,14 @@ static int launch_refine(pmh_ctx ctx, const int2* qxy, const int64_t* qoff, cons
 constexpr int kRefineTicket = 6;
 
 int pmh_launch_refine_topk(pmh_ctx ctx, const int2* qxy, const int64_t* qoff, const int64_t* qarea2,
-                           pmh_polys db, const int32_t* ids, const int32_t* nlist, int64_t Q,
+                           const int4* qbox, pmh_polys db, const int32_t* ids, const int32_t* nlist, int64_t Q,
                            const int64_t* d_n, int32_t m, int32_t k, double* jv,
                            unsigned long long* ticket, int32_t* top_ids, double* top_j,
                            cudaStream_t s)
 {
     if (Q <= 0) return PMH_OK;
-    PMH_TRY(launch_refine(ctx, qxy, qoff, qarea2, db, ids, nlist, m, nullptr, Q * m, jv, ticket, d_n, s));
+    PMH_TRY(launch_refine(ctx, qxy, qoff, qarea2, qbox, db, ids, nlist, m, nullptr, Q * m, jv, ticket, d_n,
+                          s));
     int cap = 1;
     while (cap < m) cap <<= 1;
     const size_t smem = sizeof(JKey) * cap;
@@ -569,7 +587,8 @@ extern "C" int pmh_refine_topk(pmh_ctx ctx, pmh_polys queries, pmh_polys db, con
     if (Q == 0) return PMH_OK;
     double* jv = nullptr;
     PMH_TRY(pmh_scratch(ctx, SCR_REFINE, sizeof(double) * (size_t)(Q * m), (void**)&jv));
-    return pmh_launch_refine_topk(ctx, queries->xy, queries->offsets, queries->area2, db, d_ids, d_n, Q,
+    return pmh_launch_refine_topk(ctx, queries->xy, queries->offsets, queries->area2, queries->bbox, db,
+                                  d_ids, d_n, Q,
                                   nullptr, m, k, jv, ctx->d_tickets + kRefineTicket, d_top_ids, d_top_j,
                                   (cudaStream_t)stream);
 }
@@ -581,8 +600,9 @@ extern "C" int pmh_pair_jaccard(pmh_ctx ctx, pmh_polys queries, pmh_polys db, co
     if (!queries || !db || n_pairs < 0 || (n_pairs > 0 && (!d_qid || !d_pid || !d_j)))
         return pmh_set_error(PMH_ERR_ARG, "bad arguments");
     if (n_pairs == 0) return PMH_OK;
-    return launch_refine(ctx, queries->xy, queries->offsets, queries->area2, db, d_pid, nullptr, 1, d_qid,
-                         n_pairs, d_j, ctx->d_tickets + kRefineTicket, nullptr, (cudaStream_t)stream);
+    return launch_refine(ctx, queries->xy, queries->offsets, queries->area2, queries->bbox, db, d_pid,
+                         nullptr, 1, d_qid, n_pairs, d_j, ctx->d_tickets + kRefineTicket, nullptr,
+                         (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------

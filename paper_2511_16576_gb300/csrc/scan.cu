@@ -98,7 +98,7 @@ __global__ void scan_apply_kernel(const int64_t* __restrict__ in, int64_t n,
 // ---------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 8;  // per lane
+constexpr int kSortItems = 16;  // per lane
 constexpr int kSortTile = kSortThreads * kSortItems;
 
 __global__ void __launch_bounds__(kSortThreads)
@@ -118,8 +118,11 @@ radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift, int64
         counts[(int64_t)d * n_tiles + blockIdx.x] = hist[d];
 }
 
-// Each warp owns kSortItems * 32 consecutive items of the tile, processed in
-// chunks of 32 consecutive items; ranks are stable (tile order preserved).
+// One tile per block.  Each warp owns kSortItems * 32 consecutive items of the
+// tile, processed in chunks of 32 consecutive items, and ranks them stably per
+// digit; the tile is then reordered by digit in shared memory (stable), and
+// written out in that order, so that consecutive threads store consecutive
+// positions of one digit's run instead of 32 scattered words.
 __global__ void __launch_bounds__(kSortThreads)
 radix_scatter_kernel(const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin,
                      uint32_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t n, int shift,
@@ -127,28 +130,38 @@ radix_scatter_kernel(const uint32_t* __restrict__ kin, const int32_t* __restrict
 {
     __shared__ int wcount[kSortWarps][256];
     __shared__ int64_t base_off[256];
+    __shared__ int tile_start[256];
+    __shared__ int wsum[kSortWarps];
+    __shared__ uint32_t sk[kSortTile];
+    __shared__ int32_t sv[kSortTile];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kSortWarps * 256; i += blockDim.x) (&wcount[0][0])[i] = 0;
     for (int d = threadIdx.x; d < 256; d += blockDim.x)
         base_off[d] = offsets[(int64_t)d * n_tiles + blockIdx.x];
     __syncthreads();
-    const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)wid * (kSortItems * 32);
+    const int64_t tbase = (int64_t)blockIdx.x * kSortTile;
+    const int tile_n = (int)(n - tbase < kSortTile ? n - tbase : kSortTile);
+    const int wbase = wid * (kSortItems * 32);
     uint32_t k[kSortItems];
     int32_t v[kSortItems];
     int rank[kSortItems];
 #pragma unroll
     for (int c = 0; c < kSortItems; ++c) {
-        int64_t idx = wbase + c * 32 + lane;
-        bool ok = idx < n;
-        k[c] = ok ? kin[idx] : 0;
-        v[c] = ok ? vin[idx] : 0;
-        unsigned d = (k[c] >> shift) & 0xFF;
-        unsigned act = __ballot_sync(0xffffffffu, ok);
-        unsigned peers = __match_any_sync(0xffffffffu, ok ? d : 0x100u + 0u) & act;
+        const int t = wbase + c * 32 + lane;
+        const bool ok = t < tile_n;
+        k[c] = ok ? kin[tbase + t] : 0;
+        v[c] = ok ? vin[tbase + t] : 0;
+    }
+#pragma unroll
+    for (int c = 0; c < kSortItems; ++c) {
+        const bool ok = wbase + c * 32 + lane < tile_n;
+        const unsigned d = (k[c] >> shift) & 0xFF;
+        const unsigned act = __ballot_sync(0xffffffffu, ok);
+        const unsigned peers = __match_any_sync(0xffffffffu, ok ? d : 0x100u) & act;
         int r = 0;
         if (ok) {
-            int before = __popc(peers & pmh_lanemask_lt());
-            int leader = __ffs(peers) - 1;
+            const int before = __popc(peers & pmh_lanemask_lt());
+            const int leader = __ffs(peers) - 1;
             int old = 0;
             if (lane == leader) {
                 old = wcount[wid][d];
@@ -161,25 +174,43 @@ radix_scatter_kernel(const uint32_t* __restrict__ kin, const int32_t* __restrict
         __syncwarp();
     }
     __syncthreads();
-    // exclusive prefix over warps per digit
-    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
-        int s = 0;
-        for (int w = 0; w < kSortWarps; ++w) {
-            int t = wcount[w][d];
-            wcount[w][d] = s;
-            s += t;
-        }
+    // per digit: exclusive prefix over warps, and the digit's total in the tile
+    const int dd = threadIdx.x;  // kSortThreads == 256 digits
+    int total = 0;
+    for (int w = 0; w < kSortWarps; ++w) {
+        const int t = wcount[w][dd];
+        wcount[w][dd] = total;
+        total += t;
     }
+    // exclusive prefix of the totals over digits: the digit runs' starts in the tile
+    int x = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    int pre = 0;
+    for (int w = 0; w < wid; ++w) pre += wsum[w];
+    tile_start[dd] = pre + x - total;
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < kSortItems; ++c) {
-        int64_t idx = wbase + c * 32 + lane;
-        if (idx < n) {
-            unsigned d = (k[c] >> shift) & 0xFF;
-            int64_t dst = base_off[d] + wcount[wid][d] + rank[c];
-            kout[dst] = k[c];
-            vout[dst] = v[c];
+        if (wbase + c * 32 + lane < tile_n) {
+            const unsigned d = (k[c] >> shift) & 0xFF;
+            const int pos = tile_start[d] + wcount[wid][d] + rank[c];
+            sk[pos] = k[c];
+            sv[pos] = v[c];
         }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < tile_n; j += kSortThreads) {
+        const uint32_t key = sk[j];
+        const unsigned d = (key >> shift) & 0xFF;
+        const int64_t dst = base_off[d] + (j - tile_start[d]);
+        kout[dst] = key;
+        vout[dst] = sv[j];
     }
 }
 

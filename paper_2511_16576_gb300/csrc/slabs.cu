@@ -54,10 +54,19 @@ __global__ void slab_size_kernel(const int2* __restrict__ xy, const int64_t* __r
             continue;
         }
         int y0 = 0x7fffffff, y1 = -0x7fffffff - 1;
-        for (int i = lane; i < n; i += 32) {
-            int y = xy[b + i].y;
-            y0 = min(y0, y);
-            y1 = max(y1, y);
+        // four loads in flight per lane
+        for (int i0 = 0; i0 < n; i0 += 128) {
+            int y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + 32 * u + lane;
+                y[u] = i < n ? xy[b + i].y : xy[b].y;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                y0 = min(y0, y[u]);
+                y1 = max(y1, y[u]);
+            }
         }
         y0 = __reduce_min_sync(0xffffffffu, y0);
         y1 = __reduce_max_sync(0xffffffffu, y1);
@@ -80,14 +89,19 @@ __global__ void slab_size_kernel(const int2* __restrict__ xy, const int64_t* __r
     }
 }
 
-// pass 2: per polygon (one warp) count, prefix-sum and fill the slab lists
-__global__ void slab_fill_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
+// pass 2: per polygon (one warp) count, prefix-sum and fill the slab lists; the
+// counters of a polygon of at most kFillSmemSlabs slabs live in the warp's shared
+// slice, larger ones in the global cursor array
+constexpr int kFillThreads = 256;
+constexpr int kFillSmemSlabs = 1024;
+__global__ void __launch_bounds__(kFillThreads) slab_fill_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
                                  int64_t n_polys, const int64_t* __restrict__ d_n, int min_verts,
                                  SlabInfo* __restrict__ info, const int64_t* __restrict__ ptr_base,
                                  const int64_t* __restrict__ edge_base, int32_t* __restrict__ slab_ptr,
                                  int64_t cap_ptr, int32_t* __restrict__ cursor,
                                  int32_t* __restrict__ slab_edges, int64_t cap_edges)
 {
+    __shared__ int scur[kFillThreads / 32][kFillSmemSlabs + 1];
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     if (d_n) n_polys = min(n_polys, *d_n);
@@ -109,7 +123,7 @@ __global__ void slab_fill_kernel(const int2* __restrict__ xy, const int64_t* __r
             info[p].edge_base = eb;
         }
         int32_t* sp = slab_ptr + pb;
-        int32_t* cur = cursor + pb;
+        int32_t* cur = S <= kFillSmemSlabs ? scur[threadIdx.x >> 5] : cursor + pb;
         for (int s = lane; s <= S; s += 32) cur[s] = 0;
         __syncwarp();
         for (int e = lane; e < n; e += 32) {

@@ -284,6 +284,55 @@ def test_query_capacity_and_empty(B, ctx, small):
     assert rp0.cpu().tolist() == [0] and c0.numel() == 0
 
 
+def disjoint_triple(ps):
+    """Three polygons with pairwise disjoint bounding boxes: no stream point lies in two of
+    them, so no hash (and no band) of one equals the other's."""
+    box = np.array([[p[:, 0].min(), p[:, 1].min(), p[:, 0].max(), p[:, 1].max()]
+                    for p in (ps.poly(i) for i in range(ps.n))])
+
+    def apart(i, j):
+        a, b = box[i], box[j]
+        return a[2] < b[0] or b[2] < a[0] or a[3] < b[1] or b[3] < a[1]
+    for i in range(ps.n):
+        for j in range(i + 1, ps.n):
+            if not apart(i, j):
+                continue
+            for k in range(j + 1, ps.n):
+                if apart(i, k) and apart(j, k):
+                    return i, j, k
+    raise AssertionError("no three disjoint polygons")
+
+
+@pytest.mark.parametrize("bands", [8, 16, 32])
+def test_candidates_of_long_rows_bit_exact(B, ctx, orc, bands):
+    """Candidate rows of every length the join meets: queries with 3,000, 6,000 and
+    20,000 exact duplicates in a database of 29,997 polygons -- rows of at most 3,997
+    (the small shared-memory set of 4,096 distinct candidates), of 6,000 to 6,997 (the
+    large set of 16,384) and above 20,000 (the warp merge) -- among ordinary rows;
+    bit-exact against the oracle's bucket definition."""
+    w = synth.WORKLOADS["small"]
+    base = synth.make_database(w)
+    a, b, c = disjoint_triple(base)
+    rest = np.setdiff1d(np.arange(base.n), [a, b, c])
+    ids = np.concatenate([np.full(3000, a), np.full(6000, b), np.full(20000, c), rest])
+    db, qs = base.subset(ids), base.subset(np.concatenate([[a, b, c], rest[:21]]))
+    K = 32
+    P = B.make_params(K, bands, w.T, w.seed, w.lsh_seed)
+    h_ref = orc.sign(db.xy, db.offsets, w.seed, K, w.T, nthreads=8)
+    qh_ref = orc.sign(qs.xy, qs.offsets, w.seed, K, w.T, nthreads=8)
+    h = B.minhash_sign(ctx, upload(B, ctx, db), P)
+    qh = B.minhash_sign(ctx, upload(B, ctx, qs), P)
+    assert np.array_equal(u32(h), h_ref) and np.array_equal(u32(qh), qh_ref)
+    index = B.lsh_build(ctx, h, P)
+    row_ptr, cand = B.lsh_query(ctx, index, qh)
+    rp_ref, cand_ref = orc.candidates(qh_ref, h_ref, bands, K // bands, w.T)
+    lens = np.diff(rp_ref)
+    assert 3000 <= lens[0] <= 3997 and 6000 <= lens[1] <= 6997 and lens[2] >= 20000
+    assert np.array_equal(row_ptr.cpu().numpy(), rp_ref)
+    assert np.array_equal(cand.cpu().numpy(), cand_ref)
+    index.close()
+
+
 def test_agreement_on_dense_pairs_with_sentinels(B, ctx, orc):
     rng = np.random.default_rng(9)
     for K, b in ((128, 16), (256, 32), (36, 4), (30, 5)):
@@ -369,11 +418,13 @@ def test_pair_jaccard_degenerate_contacts(B, ctx, orc):
         assert abs(j[e] - ref) <= 1e-12 + 1e-9 * ref, (e, j[e], ref)
 
 
-def test_refine_topk_matches_oracle(B, ctx, orc, small):
+@pytest.mark.parametrize("m,k", [(32, 10), (7, 3), (1, 1)])
+def test_refine_topk_matches_oracle(B, ctx, orc, small, m, k):
+    """Refined top-k of top-m lists (work items of a few list slots of one query: m = 7
+    leaves a short last item; lists shorter than m leave empty slots)."""
     w, db, qs = small
     P, dbp, qp, h, qh, index, row_ptr, cand = run_pipeline(B, ctx, w, db, qs, 32, 32, T24)
     count, _ = B.jaccard_estimate(ctx, qh, h, row_ptr, cand, P)
-    m, k = 32, 10
     ids, nn = B.topm(ctx, row_ptr, cand, count, m)
     top_ids, top_j = B.refine_topk(ctx, qp, dbp, ids, nn, k)
     ids, nn = ids.cpu().numpy(), nn.cpu().numpy()
