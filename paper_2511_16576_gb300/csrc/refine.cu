@@ -104,14 +104,17 @@ __device__ __forceinline__ double crossing_terms(const int2* __restrict__ A, int
     return sa * fa + sb * fb;
 }
 
+// One warp's part of area(A n B) for a pair worked on by two warps (wip = 0, 1):
+// the end terms of A's vertices (wip 0) or of B's (wip 1), and the crossings of
+// the A edges in the 32-edge groups of its parity; summed over the warp.
 __device__ double warp_intersection_area(const int2* __restrict__ A, int na, int sA,
                                          const int2* __restrict__ B, int nb, int sB,
-                                         uint2* cq /* [64] */, int lane)
+                                         uint2* cq /* [64] */, int lane, int wip)
 {
     const int2 org = B[0];
     double acc = 0;
     // end terms of A's edges: vertex a_i + e inside B closes edge i-1
-    for (int i = lane; i < na; i += 32) {
+    for (int i = wip == 0 ? lane : na; i < na; i += 32) {
         const int2 a = A[i];
         unsigned in = 0;
         for (int j = 0; j < nb; ++j) {
@@ -128,7 +131,7 @@ __device__ double warp_intersection_area(const int2* __restrict__ A, int na, int
         }
     }
     // end terms of B's edges: vertex c_j - e inside A closes edge j-1
-    for (int j = lane; j < nb; j += 32) {
+    for (int j = wip == 1 ? lane : nb; j < nb; j += 32) {
         const int2 c = B[j];
         unsigned in = 0;
         for (int i = 0; i < na; ++i) {
@@ -149,7 +152,7 @@ __device__ double warp_intersection_area(const int2* __restrict__ A, int na, int
     // crossing per lane, so the narrow fp64 pipe never runs a mostly idle warp
     const unsigned full = 0xffffffffu;
     int nq = 0;  // warp-uniform queue length (< 32 between iterations)
-    for (int i0 = 0; i0 < na; i0 += 32) {
+    for (int i0 = 32 * wip; i0 < na; i0 += 64) {
         const int i = i0 + lane;
         int2 a = make_int2(0, 0), b = make_int2(0, 0);
         bool live = i < na;
@@ -261,7 +264,7 @@ __device__ __forceinline__ bool build_ref_slabs(const int2* v, int n, RefSlabs& 
 // in the first of those slabs that also lists the B edge).
 __device__ double warp_intersection_area_slabs(const int2* __restrict__ A, int na, int sA,
                                                const RefSlabs& LA, const int2* __restrict__ B, int nb,
-                                               int sB, const RefSlabs& LB, uint2* cq, int lane)
+                                               int sB, const RefSlabs& LB, uint2* cq, int lane, int wip)
 {
     const int2 org = B[0];
     const unsigned full = 0xffffffffu;
@@ -269,7 +272,7 @@ __device__ double warp_intersection_area_slabs(const int2* __restrict__ A, int n
     const int ya0 = LA.y0, ya1 = LA.y0 + (kRefSlabs << LA.sh) - 1;
     const int yb0 = LB.y0, yb1 = LB.y0 + (kRefSlabs << LB.sh) - 1;
     // end terms of A's edges: vertex a_i + e inside B closes edge i-1
-    for (int i = lane; i < na; i += 32) {
+    for (int i = wip == 0 ? lane : na; i < na; i += 32) {
         const int2 a = A[i];
         unsigned in = 0;
         if (a.y >= yb0 && a.y <= yb1) {
@@ -290,7 +293,7 @@ __device__ double warp_intersection_area_slabs(const int2* __restrict__ A, int n
         }
     }
     // end terms of B's edges: vertex c_j - e inside A closes edge j-1
-    for (int j = lane; j < nb; j += 32) {
+    for (int j = wip == 1 ? lane : nb; j < nb; j += 32) {
         const int2 c = B[j];
         unsigned in = 0;
         if (c.y >= ya0 && c.y <= ya1) {
@@ -312,7 +315,7 @@ __device__ double warp_intersection_area_slabs(const int2* __restrict__ A, int n
     }
     // crossings, queued and evaluated 32 at a time as in warp_intersection_area
     int nq = 0;
-    for (int i0 = 0; i0 < na; i0 += 32) {
+    for (int i0 = 32 * wip; i0 < na; i0 += 64) {
         const int i = i0 + lane;
         int2 a = make_int2(0, 0), b = make_int2(0, 0);
         int k0 = 0, cntk = 0, q0 = 0;
@@ -389,53 +392,71 @@ __device__ __forceinline__ PairView view(const int2* xy, const int64_t* off, con
     return r;
 }
 
-constexpr int kRefineWarps = 4;
-constexpr int kWarpVerts = 512;  // both polygons staged per warp when they fit
+constexpr int kRefineWarps = 4;  // two pairs per block, two warps per pair
+constexpr int kWarpVerts = 512;  // both polygons staged per pair when they fit
 
-// one warp's shared slice: the staged rings, the crossing queue and both rings' slab lists
-struct RefWarp {
+// one pair's shared slice: the staged rings, a crossing queue per warp, both rings'
+// slab lists, and the two warps' partial sums
+struct RefPair {
     int2 sv[kWarpVerts];
-    uint2 cq[64];
+    uint2 cq[2][64];
     RefSlabs sl[2];
+    double part[2];
+    long long e;
+    int ok[2];
 };
 
-// n vertices to shared memory by asynchronous 8-byte copies (all in flight at once;
-// the caller waits)
-__device__ __forceinline__ void stage_ring(int2* dst, const int2* __restrict__ src, int n, int lane)
+// the named barrier of pair slot g (0 or 1) of the block (barrier 0 is __syncthreads;
+// immediate ids, so that the block holds three barriers)
+__device__ __forceinline__ void pair_sync(int g)
 {
-    for (int i = lane; i < n; i += 32) {
+    if (g == 0) asm volatile("bar.sync 1, 64;\n" ::: "memory");
+    else asm volatile("bar.sync 2, 64;\n" ::: "memory");
+}
+
+// n vertices to shared memory by asynchronous 8-byte copies, 64 threads striding
+// (the caller waits)
+__device__ __forceinline__ void stage_ring(int2* dst, const int2* __restrict__ src, int n, int t)
+{
+    for (int i = t; i < n; i += 64) {
         const unsigned d = (unsigned)__cvta_generic_to_shared(dst + i);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src + i) : "memory");
     }
 }
 
-// J of one pair by one warp: both rings staged in the warp's shared slice when they
-// fit, else read from global memory; y-slab lists of both rings when they fit their
-// capacity, else every edge pair
-__device__ double warp_pair_jaccard(PairView A, PairView B, RefWarp& w, int lane)
+// J of one pair by two warps (wip = 0, 1; every branch is uniform over both): both
+// rings staged in the pair's shared slice when they fit, else read from global
+// memory; warp 0 builds A's y-slab list and warp 1 B's, both when they fit their
+// capacity, else every edge pair; the area's terms split between the warps, summed
+// in a fixed order
+__device__ double pair_jaccard(PairView A, PairView B, RefPair& P, int wip, int lane, int g)
 {
     if (A.sgn == 0 || B.sgn == 0) return 0.0;
     const int2* a = A.v;
     const int2* b = B.v;
     if (A.n + B.n <= kWarpVerts) {
-        stage_ring(w.sv, A.v, A.n, lane);
-        stage_ring(w.sv + A.n, B.v, B.n, lane);
+        stage_ring(P.sv, A.v, A.n, 32 * wip + lane);
+        stage_ring(P.sv + A.n, B.v, B.n, 32 * wip + lane);
         asm volatile("cp.async.wait_all;\n" ::: "memory");
-        __syncwarp();
-        a = w.sv;
-        b = w.sv + A.n;
+        pair_sync(g);
+        a = P.sv;
+        b = P.sv + A.n;
     }
-    double inter;
-    if (build_ref_slabs(a, A.n, w.sl[0], lane) && build_ref_slabs(b, B.n, w.sl[1], lane))
-        inter = warp_intersection_area_slabs(a, A.n, A.sgn, w.sl[0], b, B.n, B.sgn, w.sl[1], w.cq, lane);
-    else
-        inter = warp_intersection_area(a, A.n, A.sgn, b, B.n, B.sgn, w.cq, lane);
-    __syncwarp();
+    const bool ok = build_ref_slabs(wip == 0 ? a : b, wip == 0 ? A.n : B.n, P.sl[wip], lane);
+    if (lane == 0) P.ok[wip] = ok;
+    pair_sync(g);
+    const double part =
+        P.ok[0] && P.ok[1]
+            ? warp_intersection_area_slabs(a, A.n, A.sgn, P.sl[0], b, B.n, B.sgn, P.sl[1], P.cq[wip], lane, wip)
+            : warp_intersection_area(a, A.n, A.sgn, b, B.n, B.sgn, P.cq[wip], lane, wip);
+    if (lane == 0) P.part[wip] = part;
+    pair_sync(g);
+    const double inter = P.part[0] + P.part[1];
     const double uni = A.area + B.area - inter;
     return uni > 0 ? fmin(fmax(inter / uni, 0.0), 1.0) : 0.0;
 }
 
-__global__ void __launch_bounds__(kRefineWarps * 32)
+__global__ void __launch_bounds__(kRefineWarps * 32, 7)
 refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qoff,
                     const int64_t* __restrict__ qarea2, const int4* __restrict__ qbox,
                     const int2* __restrict__ pxy, const int64_t* __restrict__ poff,
@@ -446,36 +467,39 @@ refine_pairs_kernel(const int2* __restrict__ qxy, const int64_t* __restrict__ qo
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    RefWarp& w = reinterpret_cast<RefWarp*>(smem_raw)[wid];
+    const int g = wid >> 1, wip = wid & 1;
+    RefPair& P = reinterpret_cast<RefPair*>(smem_raw)[g];
     if (d_n && !qid_list) n_pairs = min(n_pairs, *d_n * (int64_t)m);  // lists of the live queries
-    // persistent warps pull pairs from a ticket: pair costs differ by orders of
+    // persistent warp pairs pull pairs from a ticket: pair costs differ by orders of
     // magnitude (a query against its own source vs a neighbour it barely touches)
     for (;;) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(ticket, 1ull);
-        const int64_t e = (int64_t)__shfl_sync(0xffffffffu, t, 0);
-        if (e >= n_pairs) break;
+        if (wip == 0 && lane == 0) P.e = (long long)atomicAdd(ticket, 1ull);
+        pair_sync(g);
+        const int64_t e = P.e;
+        if (e >= n_pairs) break;  // the same for both warps
         int64_t q;
         int32_t p;
+        double j = -1.0;
+        bool live = true;
         if (qid_list) {  // explicit pairs
             q = qid_list[e];
             p = ids[e];
         } else {         // top-m lists: pair e = (q, slot)
             q = e / m;
             const int slot = (int)(e - q * m);
-            if (slot >= nlist[q]) {
-                if (lane == 0) out[e] = -1.0;
-                continue;
-            }
-            p = ids[e];
+            live = slot < nlist[q];
+            p = live ? ids[e] : 0;
         }
-        // bounding boxes (half-open lattice boxes) without a common interior point: an
-        // empty intersection, J = 0 exactly, as the full computation gives
-        const int4 a = qbox[q], b = pbox[p];
-        const bool apart = !(a.x < b.z && b.x < a.z && a.y < b.w && b.y < a.w);
-        const double j =
-            apart ? 0.0 : warp_pair_jaccard(view(qxy, qoff, qarea2, q), view(pxy, poff, parea2, p), w, lane);
-        if (lane == 0) out[e] = j;
+        if (live) {
+            // bounding boxes (half-open lattice boxes) without a common interior point:
+            // an empty intersection, J = 0 exactly, as the full computation gives
+            const int4 qa = qbox[q], pb = pbox[p];
+            const bool apart = !(qa.x < pb.z && pb.x < qa.z && qa.y < pb.w && pb.y < qa.w);
+            j = apart ? 0.0
+                      : pair_jaccard(view(qxy, qoff, qarea2, q), view(pxy, poff, parea2, p), P, wip, lane, g);
+        }
+        if (wip == 0 && lane == 0) out[e] = j;
+        pair_sync(g);  // the slice is free for the next pair
     }
 }
 
@@ -540,13 +564,13 @@ static int launch_refine(pmh_ctx ctx, const int2* qxy, const int64_t* qoff, cons
                          const int32_t* qid_list, int64_t n_pairs, double* out,
                          unsigned long long* ticket, const int64_t* d_n, cudaStream_t s)
 {
-    const size_t smem = sizeof(RefWarp) * kRefineWarps;
+    const size_t smem = sizeof(RefPair) * (kRefineWarps / 2);
     PMH_CUDA_TRY(cudaFuncSetAttribute(refine_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     int per_sm = 0;
     PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_pairs_kernel,
                                                                kRefineWarps * 32, smem));
-    const int blocks = (int)std::min<int64_t>((n_pairs + kRefineWarps - 1) / kRefineWarps,
+    const int blocks = (int)std::min<int64_t>((n_pairs + 1) / 2,
                                               (int64_t)ctx->sm_count * std::max(per_sm, 1));
     PMH_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
     refine_pairs_kernel<<<blocks, kRefineWarps * 32, smem, s>>>(
