@@ -328,8 +328,9 @@ int pmh_sign_variant_info(int variant, int* points_per_lane, int* warps_per_bloc
  * pmh_qgraph_status synchronises `stream` and reports the last run's status
  * bits (1, 2, 4: invalid polygons -- offsets, fewer than 3 vertices,
  * coordinate range -- nothing computed; 8: more candidates than
- * cand_capacity, rows not written, agreement, top-m and refinement skipped)
- * and its candidate total. */
+ * cand_capacity, rows not written, agreement, top-m and refinement skipped;
+ * 16: a bounded wait on the tensor cores in the reranker's forward pass ran
+ * out, scores not written) and its candidate total. */
 typedef struct pmh_qgraph_s* pmh_qgraph;
 typedef struct {
     int64_t max_queries, max_vertices, cand_capacity;
@@ -355,7 +356,9 @@ int pmh_qgraph_destroy(pmh_qgraph graph);
  * (ReLU, ReLU, sigmoid) predicting the Jaccard similarity of a (query,
  * candidate) pair, trained on the GPU by mean squared error against exact
  * Jaccard.  bf16 weights and activations on the tensor cores, fp32
- * accumulation and fp32 master weights (Adam).
+ * accumulation and fp32 master weights (Adam): the forward pass (scoring) as
+ * tcgen05 MMAs from shared memory into tensor-memory accumulators, training
+ * with mma.sync.
  * Packed parameter layout (PMH_RERANK_PARAMS floats): w1 [64][40] (out, in),
  * b1 [64], w2 [64][64], b2 [64], w3 [64], b3 [1].
  * Features (pmh_rerank_features): bf16 [E][48] per CSR pair, columns
@@ -372,7 +375,9 @@ int pmh_qgraph_destroy(pmh_qgraph graph);
  *          areas differ; the bound is a geometric prior the hashes lack.
  *   K must be a multiple of 32.
  * pmh_rerank_forward writes a score in (0, 1) per feature row (feed it to
- * pmh_topm as d_score).  pmh_rerank_gradients computes the loss (mean over
+ * pmh_topm as d_score); d_feat must be 16-byte aligned; it synchronises
+ * `stream` and returns PMH_ERR_CUDA if a bounded wait on the tensor cores ran
+ * out (scores not written).  pmh_rerank_gradients computes the loss (mean over
  * n_rows) and the packed gradients of one batch into the reranker (and
  * copies them to d_grads / d_loss when not NULL); pmh_rerank_adam_step
  * applies them.  set/get move the packed fp32 master weights (synchronise). */

@@ -234,7 +234,7 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_
                                            Q * S, &g->P, nullptr, nullptr, g->feat,
                                            FeatSrc{g->qfeat, g->bbox, g->area2},
                                            FeatSrc{db->feat, db->bbox, db->area2}, g->flags, cs);
-        if (rc == PMH_OK) rc = pmh_launch_rerank_forward(g->rerank, g->feat, Q * S, g->score, cs);
+        if (rc == PMH_OK) rc = pmh_launch_rerank_forward(g->rerank, g->feat, Q * S, g->score, g->flags, cs);
         if (rc == PMH_OK)
             rc = pmh_launch_topm(g->sl_row_ptr, g->sl_cand, nullptr, g->score, Q, m, g->top_ids, g->top_n,
                                  g->flags, cs);

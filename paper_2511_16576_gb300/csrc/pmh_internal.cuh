@@ -387,7 +387,7 @@ int pmh_launch_poly_feat(int sm_count, const int64_t* area2, const int64_t* off,
                          const int64_t* d_n, float2* out, cudaStream_t s);
 // reranker scores of n feature rows (rerank.cu)
 int pmh_launch_rerank_forward(pmh_rerank r, const uint16_t* feat, int64_t n_rows, float* score,
-                              cudaStream_t s);
+                              int* d_flags, cudaStream_t s);
 int pmh_launch_topm(const int64_t* row_ptr, const int32_t* cand, const uint16_t* count,
                     const float* score, int64_t Q, int32_t m, int32_t* out_ids, int32_t* out_n,
                     const int* d_flags, cudaStream_t s);

@@ -18,10 +18,13 @@
 //   39     an upper bound of J: min(|q|, |p|, bounding-box overlap) over
 //          |q| + |p| minus that minimum (a geometric prior the hashes lack).
 //
-// GEMMs run on the tensor cores with mma.sync m16n8k16 (bf16 operands, fp32
-// accumulation).  One warp owns 16 rows; the accumulator fragment of one
-// layer is, element for element, the A fragment of the next, so activations
-// stay in registers.  Training fuses forward and backward per 128-row chunk:
+// The forward pass (the scoring inside the query graph) runs on the
+// fifth-generation tensor cores: tcgen05 MMAs from shared-memory operands into
+// tensor-memory accumulators (mlp_tc_kernel, below).  Training runs its GEMMs
+// with mma.sync m16n8k16 (bf16 operands, fp32 accumulation): one warp owns 16
+// rows; the accumulator fragment of one layer is, element for element, the A
+// fragment of the next, so activations stay in registers.  Training fuses
+// forward and backward per 128-row chunk:
 // activations and back-propagated gradients go to shared memory, weight
 // gradients are tensor-core GEMMs over the chunk's rows (K = rows), kept in
 // registers across chunks and added to global memory once per CTA.  Operand
@@ -128,15 +131,13 @@ __device__ void load_weights(MlpSmem& s, const __nv_bfloat16* __restrict__ w1b,
     }
 }
 
-// Forward (kTrain = false: writes scores) or forward + backward (kTrain = true:
-// accumulates gradients of the mean squared error over n_total rows).
-template <bool kTrain>
+// Training pass: forward + backward, accumulating the gradients of the mean
+// squared error over n_total rows (the forward pass alone runs on tcgen05 below).
 __global__ void __launch_bounds__(kWarpsMlp * 32, 1)
-mlp_kernel(const __nv_bfloat16* __restrict__ feat, const float* __restrict__ label, int64_t n_rows,
-           int64_t n_total, const __nv_bfloat16* __restrict__ w1b,
-           const __nv_bfloat16* __restrict__ w2b, const __nv_bfloat16* __restrict__ w3b,
-           const float* __restrict__ master, float* __restrict__ score, float* __restrict__ grads,
-           float* __restrict__ loss_out)
+mlp_train_kernel(const __nv_bfloat16* __restrict__ feat, const float* __restrict__ label, int64_t n_rows,
+                 int64_t n_total, const __nv_bfloat16* __restrict__ w1b,
+                 const __nv_bfloat16* __restrict__ w2b, const __nv_bfloat16* __restrict__ w3b,
+                 const float* __restrict__ master, float* __restrict__ grads, float* __restrict__ loss_out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     MlpSmem& s = *reinterpret_cast<MlpSmem*>(smem_raw);
@@ -191,10 +192,8 @@ mlp_kernel(const __nv_bfloat16* __restrict__ feat, const float* __restrict__ lab
             uint32_t lo = pack2(h[0], h[1]), hi = pack2(h[2], h[3]);
             a2f[nt >> 1][(nt & 1) * 2 + 0] = lo;
             a2f[nt >> 1][(nt & 1) * 2 + 1] = hi;
-            if (kTrain) {
-                *reinterpret_cast<uint32_t*>(&s.h1[r0 + g][nt * 8 + 2 * t]) = lo;
-                *reinterpret_cast<uint32_t*>(&s.h1[r0 + g + 8][nt * 8 + 2 * t]) = hi;
-            }
+            *reinterpret_cast<uint32_t*>(&s.h1[r0 + g][nt * 8 + 2 * t]) = lo;
+            *reinterpret_cast<uint32_t*>(&s.h1[r0 + g + 8][nt * 8 + 2 * t]) = hi;
         }
         // ---- layer 2: [16 x 64] x [64 x 64]
         float acc2[8][4] = {};
@@ -233,14 +232,6 @@ mlp_kernel(const __nv_bfloat16* __restrict__ feat, const float* __restrict__ lab
         const int64_t rowA = base + r0 + g, rowB = rowA + 8;
         float pA = 1.f / (1.f + expf(-(acc3[0] + s.b3)));
         float pB = 1.f / (1.f + expf(-(acc3[2] + s.b3)));
-        if (!kTrain) {
-            if (t == 0) {
-                if (rowA < n_rows) score[rowA] = pA;
-                if (rowB < n_rows) score[rowB] = pB;
-            }
-            __syncthreads();
-            continue;
-        }
         // ---- backward
         if (t == 0) {
             float gA = 0.f, gB = 0.f, l = 0.f;
@@ -362,7 +353,6 @@ mlp_kernel(const __nv_bfloat16* __restrict__ feat, const float* __restrict__ lab
         }
         __syncthreads();
     }
-    if (!kTrain) return;
     // flush: this warp's weight-gradient slices and the CTA's small partials
     const int m0 = 16 * (wid >> 1);
 #pragma unroll
@@ -423,6 +413,226 @@ __global__ void refresh_bf16_kernel(const float* __restrict__ master, __nv_bfloa
         w3b[i] = __float2bfloat16_rn(master[OFF_W3 + i]);
 }
 
+// ---------------------------------------------------------------------------
+// Forward pass on the fifth-generation tensor cores (tcgen05, one CTA, no
+// cluster): tiles of 128 rows; layer 1 is [128 x 48] x [48 x 64] and layer 2
+// [128 x 64] x [64 x 64], each a chain of M=128, N=64, K=16 bf16 MMAs issued by
+// one thread with fp32 accumulators in tensor memory (columns 0..63 and
+// 64..127); the operands sit in shared memory in the canonical K-major layout
+// without swizzle (core matrices of 8 rows x 16 bytes; the 16-byte rows of one
+// core matrix are consecutive, core matrices adjacent in K are 128 bytes apart,
+// groups of 8 rows are K * 16 bytes apart).  Thread 32w + l owns row 32w + l of
+// the tile (tensor-memory lane 32w + l, which warp w may read): it adds the
+// bias, applies ReLU and rounds to bf16 after each layer, exactly where the
+// fp64 reference rounds, and computes layer 3 (64 -> 1) as a dot product.
+// Every wait on the tensor cores is bounded: a wait that runs out sets `err`
+// bit 16, the CTA stops, frees its tensor memory and returns.
+// ---------------------------------------------------------------------------
+constexpr int kTcRows = 128;
+constexpr int kTcThreads = 128;
+constexpr int kTcCols = 128;  // tensor-memory columns: two 64-column fp32 accumulators
+constexpr int kTcErr = 16;
+
+struct TcSmem {
+    __nv_bfloat16 x[kTcRows * kInPad];  // the tile's features (canonical layout)
+    __nv_bfloat16 h1[kTcRows * kH];     // layer-1 activations
+    __nv_bfloat16 w1[kH * kInPad];      // W1 [out][in] (B operand, K-major)
+    __nv_bfloat16 w2[kH * kH];          // W2 [out][in]
+    float b1[kH], b2[kH], w3[kH], b3;
+    unsigned long long mbar;
+    uint32_t tmem;
+    int stop;
+};
+
+// element offset of (row r, column k) in the canonical layout of a matrix with kd columns
+__device__ __forceinline__ int canon(int r, int k, int kd)
+{
+    return (r >> 3) * (kd * 8) + (k >> 3) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+// shared-memory matrix descriptor: start address, leading (K) and stride (8-row)
+// byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(const void* p, uint32_t lbo, uint32_t sbo)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    return (uint64_t)((a >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: fp32 accumulator, bf16 A and B, both K-major, N = 64, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kTcIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(unsigned long long* mbar)
+{
+    const uint32_t m = (uint32_t)__cvta_generic_to_shared(mbar);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(m)
+                 : "memory");
+}
+
+// bounded wait for the phase of parity `phase` of the barrier; false if it ran out
+__device__ __forceinline__ bool tc_wait(unsigned long long* mbar, uint32_t phase)
+{
+    const uint32_t m = (uint32_t)__cvta_generic_to_shared(mbar);
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(m), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// 16 consecutive fp32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+mlp_tc_kernel(const __nv_bfloat16* __restrict__ feat, int64_t n_rows, const __nv_bfloat16* __restrict__ w1b,
+              const __nv_bfloat16* __restrict__ w2b, const __nv_bfloat16* __restrict__ w3b,
+              const float* __restrict__ master, float* __restrict__ score, int* __restrict__ err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw);
+    const int tid = threadIdx.x, wid = tid >> 5;
+    for (int i = tid; i < kH * kInPad; i += kTcThreads) s.w1[canon(i / kInPad, i % kInPad, kInPad)] = w1b[i];
+    for (int i = tid; i < kH * kH; i += kTcThreads) s.w2[canon(i / kH, i % kH, kH)] = w2b[i];
+    for (int i = tid; i < kH; i += kTcThreads) {
+        s.b1[i] = master[OFF_B1 + i];
+        s.b2[i] = master[OFF_B2 + i];
+        s.w3[i] = __bfloat162float(w3b[i]);
+    }
+    if (tid == 0) {
+        s.b3 = master[OFF_B3];
+        s.stop = 0;
+        const uint32_t m = (uint32_t)__cvta_generic_to_shared(&s.mbar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(m) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (wid == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s.tmem);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s.tmem;
+    const uint32_t lane_base = (uint32_t)(32 * wid) << 16;  // this warp's tensor-memory lanes
+    uint32_t phase = 0;
+    for (int64_t base = (int64_t)blockIdx.x * kTcRows; base < n_rows; base += (int64_t)gridDim.x * kTcRows) {
+        // the tile's features (16-byte chunks; rows past n_rows are zero)
+        for (int i = tid; i < kTcRows * (kInPad / 8); i += kTcThreads) {
+            const int r = i / (kInPad / 8), kc = i % (kInPad / 8);
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (base + r < n_rows) v = *reinterpret_cast<const uint4*>(feat + (base + r) * kInPad + 8 * kc);
+            *reinterpret_cast<uint4*>(s.x + canon(r, 8 * kc, kInPad)) = v;
+        }
+        async_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // layer 1: three K = 16 steps (two core matrices each, 128 elements apart) into
+        // columns 0..63
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < kInPad / 16; ++kk)
+                tc_mma(tmem, tc_desc(s.x + 128 * kk, 128, kInPad * 16), tc_desc(s.w1 + 128 * kk, 128, kInPad * 16),
+                       kk > 0);
+            tc_commit(&s.mbar);
+        }
+        if (!tc_wait(&s.mbar, phase)) s.stop = 1;
+        phase ^= 1u;
+        tc_fence_after();
+        __syncthreads();
+        if (s.stop) break;
+        // epilogue 1: bias, ReLU, bf16, into the canonical layout of layer 2's A operand
+        const int row = tid;
+#pragma unroll
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            float z[16];
+            tc_ld16(tmem + lane_base + (uint32_t)c0, z);
+#pragma unroll
+            for (int j = 0; j < 16; j += 8) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float a = z[j + 2 * u] + s.b1[c0 + j + 2 * u];
+                    const float b = z[j + 2 * u + 1] + s.b1[c0 + j + 2 * u + 1];
+                    pk[u] = pack2(a > 0.f ? a : 0.f, b > 0.f ? b : 0.f);
+                }
+                *reinterpret_cast<uint4*>(s.h1 + canon(row, c0 + j, kH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+        async_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // layer 2: four K = 16 steps into columns 64..127
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < kH / 16; ++kk)
+                tc_mma(tmem + 64, tc_desc(s.h1 + 128 * kk, 128, kH * 16), tc_desc(s.w2 + 128 * kk, 128, kH * 16),
+                       kk > 0);
+            tc_commit(&s.mbar);
+        }
+        if (!tc_wait(&s.mbar, phase)) s.stop = 1;
+        phase ^= 1u;
+        tc_fence_after();
+        __syncthreads();
+        if (s.stop) break;
+        // epilogue 2: bias, ReLU, bf16 rounding, layer 3 and the sigmoid
+        float acc = 0.f;
+#pragma unroll
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            float z[16];
+            tc_ld16(tmem + lane_base + 64u + (uint32_t)c0, z);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float v = z[j] + s.b2[c0 + j];
+                acc += bfr(v > 0.f ? v : 0.f) * s.w3[c0 + j];
+            }
+        }
+        if (base + row < n_rows) score[base + row] = 1.f / (1.f + expf(-(acc + s.b3)));
+        tc_fence_before();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (wid == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols)
+                     : "memory");
+    if (tid == 0 && s.stop && err) atomicOr(err, kTcErr);
+}
+
 }  // namespace
 
 struct pmh_rerank_s {
@@ -436,6 +646,7 @@ struct pmh_rerank_s {
     __nv_bfloat16* w1b = nullptr;  // [64][48] bf16 operand copies
     __nv_bfloat16* w2b = nullptr;  // [64][64]
     __nv_bfloat16* w3b = nullptr;  // [64]
+    int* err = nullptr;            // tensor-core wait status of the public forward call
     int64_t steps = 0;
 };
 
@@ -444,7 +655,7 @@ extern "C" int pmh_rerank_destroy(pmh_rerank r)
     if (!r) return PMH_OK;
     cudaSetDevice(r->device);
     cudaDeviceSynchronize();
-    void* bufs[] = {r->master, r->m1, r->m2, r->grads, r->loss, r->w1b, r->w2b, r->w3b};
+    void* bufs[] = {r->master, r->m1, r->m2, r->grads, r->loss, r->w1b, r->w2b, r->w3b, r->err};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete r;
@@ -466,7 +677,8 @@ extern "C" int pmh_rerank_create(pmh_ctx ctx, pmh_rerank* out)
               cudaMalloc(&r->loss, sizeof(float)) == cudaSuccess &&
               cudaMalloc(&r->w1b, sizeof(__nv_bfloat16) * kH * kInPad) == cudaSuccess &&
               cudaMalloc(&r->w2b, sizeof(__nv_bfloat16) * kH * kH) == cudaSuccess &&
-              cudaMalloc(&r->w3b, sizeof(__nv_bfloat16) * kH) == cudaSuccess;
+              cudaMalloc(&r->w3b, sizeof(__nv_bfloat16) * kH) == cudaSuccess &&
+              cudaMalloc(&r->err, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         pmh_rerank_destroy(r);
@@ -475,6 +687,7 @@ extern "C" int pmh_rerank_create(pmh_ctx ctx, pmh_rerank* out)
     cudaMemset(r->master, 0, sizeof(float) * N_PARAMS);
     cudaMemset(r->m1, 0, sizeof(float) * N_PARAMS);
     cudaMemset(r->m2, 0, sizeof(float) * N_PARAMS);
+    cudaMemset(r->err, 0, sizeof(int));
     refresh_bf16_kernel<<<8, 256>>>(r->master, r->w1b, r->w2b, r->w3b);
     g_pmh_launches.fetch_add(1);
     PMH_CUDA_TRY(cudaDeviceSynchronize());
@@ -523,25 +736,38 @@ extern "C" int pmh_rerank_features(pmh_ctx ctx, pmh_polys queries, pmh_polys db,
                                      (cudaStream_t)stream);
 }
 
-static int mlp_launch(pmh_rerank r, bool train, const uint16_t* d_feat, const float* d_label,
-                      int64_t n, float* d_score, cudaStream_t s)
+// forward pass: the tensor-core kernel (a few CTAs per SM at most, so that their
+// tensor-memory allocations, 128 columns each, always fit the SM's 512)
+static int tc_forward(pmh_rerank r, const uint16_t* d_feat, int64_t n, float* d_score, int* err,
+                      cudaStream_t s)
+{
+    const size_t smem = std::max<size_t>(sizeof(TcSmem) + 1024, 60 * 1024);
+    PMH_CUDA_TRY(cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int blocks = (int)std::min<int64_t>((n + kTcRows - 1) / kTcRows, (int64_t)r->ctx->sm_count);
+    mlp_tc_kernel<<<std::max(blocks, 1), kTcThreads, smem, s>>>(
+        reinterpret_cast<const __nv_bfloat16*>(d_feat), n, r->w1b, r->w2b, r->w3b, r->master, d_score, err);
+    PMH_LAUNCHED("mlp_tc_kernel");
+    return PMH_OK;
+}
+
+static int train_launch(pmh_rerank r, const uint16_t* d_feat, const float* d_label, int64_t n,
+                        cudaStream_t s)
 {
     const size_t smem = sizeof(MlpSmem);
-    auto fn = train ? mlp_kernel<true> : mlp_kernel<false>;
-    PMH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PMH_CUDA_TRY(cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int blocks = (int)std::min<int64_t>((n + kChunk - 1) / kChunk, (int64_t)r->ctx->sm_count);
-    fn<<<std::max(blocks, 1), kWarpsMlp * 32, smem, s>>>(
+    mlp_train_kernel<<<std::max(blocks, 1), kWarpsMlp * 32, smem, s>>>(
         reinterpret_cast<const __nv_bfloat16*>(d_feat), d_label, n, n, r->w1b, r->w2b, r->w3b,
-        r->master, d_score, r->grads, r->loss);
-    PMH_LAUNCHED(train ? "mlp_kernel<train>" : "mlp_kernel<forward>");
+        r->master, r->grads, r->loss);
+    PMH_LAUNCHED("mlp_train_kernel");
     return PMH_OK;
 }
 
 int pmh_launch_rerank_forward(pmh_rerank r, const uint16_t* feat, int64_t n_rows, float* score,
-                              cudaStream_t s)
+                              int* d_flags, cudaStream_t s)
 {
     if (n_rows <= 0) return PMH_OK;
-    return mlp_launch(r, false, feat, nullptr, n_rows, score, s);
+    return tc_forward(r, feat, n_rows, score, d_flags, s);
 }
 
 extern "C" int pmh_rerank_forward(pmh_rerank r, const uint16_t* d_feat, int64_t n_rows,
@@ -549,9 +775,17 @@ extern "C" int pmh_rerank_forward(pmh_rerank r, const uint16_t* d_feat, int64_t 
 {
     if (!r || n_rows < 0 || (n_rows > 0 && (!d_feat || !d_score)))
         return pmh_set_error(PMH_ERR_ARG, "bad arguments");
+    if (((uintptr_t)d_feat & 15) != 0) return pmh_set_error(PMH_ERR_ARG, "features must be 16-byte aligned");
     PMH_TRY(pmh_check_device(r->ctx));
     if (n_rows == 0) return PMH_OK;
-    return mlp_launch(r, false, d_feat, nullptr, n_rows, d_score, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    PMH_CUDA_TRY(cudaMemsetAsync(r->err, 0, sizeof(int), s));
+    PMH_TRY(tc_forward(r, d_feat, n_rows, d_score, r->err, s));
+    int h_err = 0;
+    PMH_CUDA_TRY(cudaMemcpyAsync(&h_err, r->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PMH_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h_err) return pmh_set_error(PMH_ERR_CUDA, "a tensor-core wait of the forward pass ran out");
+    return PMH_OK;
 }
 
 extern "C" int pmh_rerank_gradients(pmh_rerank r, const uint16_t* d_feat, const float* d_label,
@@ -562,7 +796,7 @@ extern "C" int pmh_rerank_gradients(pmh_rerank r, const uint16_t* d_feat, const 
     cudaStream_t s = (cudaStream_t)stream;
     PMH_CUDA_TRY(cudaMemsetAsync(r->grads, 0, sizeof(float) * N_PARAMS, s));
     PMH_CUDA_TRY(cudaMemsetAsync(r->loss, 0, sizeof(float), s));
-    PMH_TRY(mlp_launch(r, true, d_feat, d_label, n_rows, nullptr, s));
+    PMH_TRY(train_launch(r, d_feat, d_label, n_rows, s));
     if (d_grads)
         PMH_CUDA_TRY(cudaMemcpyAsync(d_grads, r->grads, sizeof(float) * N_PARAMS,
                                      cudaMemcpyDeviceToDevice, s));
