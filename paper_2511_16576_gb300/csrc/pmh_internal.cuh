@@ -125,12 +125,13 @@ constexpr int kRankLevels = 6;
 // box and ~2.5 per first-pass point read (those below the smallest rank level >=
 // lim1 in those cells), plus ~20 for the mask, exact tests and setup; the walk
 // costs ~45 per round of 64 points plus ~40.  Returns lim (0 = walk), lim1 and
-// the cheapest level.  Any limit and level give the exact result; the plan only
-// picks the cheaper work.
+// the cheapest level for each pass.  Any limit and levels give the exact result;
+// the plan only picks the cheaper work.
 struct PmhIndexPlan {
     uint32_t lim;
-    int level;
+    int level;      // grid level holding every point below lim (the second pass)
     uint32_t lim1;  // bound of the first gather pass: ~2.5 expected first hits
+    int level1;     // grid level of the first pass (holding every point below lim1)
 };
 __host__ __device__ __forceinline__ float pmh_level_cost(int4 bb, uint32_t lim1, uint32_t M, int shift)
 {
@@ -143,7 +144,7 @@ __host__ __device__ __forceinline__ float pmh_level_cost(int4 bb, uint32_t lim1,
 }
 __host__ __device__ __forceinline__ PmhIndexPlan pmh_index_plan(int4 bb, long long area2)
 {
-    PmhIndexPlan plan{0u, 0, 0u};
+    PmhIndexPlan plan{0u, 0, 0u, 0};
     if (bb.z <= bb.x || bb.w <= bb.y) return plan;
     const float area = 0.5f * (float)(area2 < 0 ? -area2 : area2);
     const float walk = 4294967296.0f / fmaxf(area, 1.0f);
@@ -151,23 +152,31 @@ __host__ __device__ __forceinline__ PmhIndexPlan pmh_index_plan(int4 bb, long lo
     const float cand = lim * ((float)(bb.z - bb.x) * (float)(bb.w - bb.y) * (1.0f / 4294967296.0f));
     if (cand > 24.0f) return plan;
     const uint32_t L = (uint32_t)lim, L1 = (uint32_t)fminf(lim, 2.5f * walk + 64.0f);
-    float best = 3.0e38f;
-    int level = 0;
+    // the cheapest level holding every point below the bound: L for the second pass,
+    // L1 for the first (on a coarser shallow level the first pass reads a few cells
+    // where the deep level holding L would read many); the deep level (larger than
+    // L2) only for bounds the L2-resident levels cannot hold
+    float best = 3.0e38f, best1 = 3.0e38f;
+    int level = 0, level1 = 0;
     for (int l = 0; l < kIndexLevels; ++l) {
-        if (L > (uint32_t)index_level_points(l)) continue;
-        // the deep level (larger than L2) only for limits the L2-resident levels cannot hold
-        if (index_level_points(l) > kStreamIndexPoints && L <= (uint32_t)kStreamIndexPoints) continue;
-        const float c = pmh_level_cost(bb, L1, index_level_points(l), 16 - index_level_gbits(l));
-        if (c < best) {
+        const uint32_t M = (uint32_t)index_level_points(l);
+        const bool deep = M > (uint32_t)kStreamIndexPoints;
+        const float c = pmh_level_cost(bb, L1, M, 16 - index_level_gbits(l));
+        if (L <= M && !(deep && L <= (uint32_t)kStreamIndexPoints) && c < best) {
             best = c;
             level = l;
         }
+        if (L1 <= M && !(deep && L1 <= (uint32_t)kStreamIndexPoints) && c < best1) {
+            best1 = c;
+            level1 = l;
+        }
     }
     const float walk_cost = ceilf(walk * (1.0f / 64.0f)) * 45.0f + 40.0f;
-    if (best + 20.0f >= walk_cost) return plan;
+    if (best1 + 20.0f >= walk_cost) return plan;
     plan.lim = L;
     plan.level = level;
     plan.lim1 = L1;
+    plan.level1 = level1;
     return plan;
 }
 

@@ -289,26 +289,27 @@ __device__ __forceinline__ void indexed_range(UniWarp& m, const Src& src, const 
     const uint32_t w = (uint32_t)(bb.z - bb.x), h = (uint32_t)(bb.w - bb.y);
     const int cwl = mask32_log2((int)w), chl = mask32_log2((int)h);
     uint32_t lim = min(plan.lim, T);
-    // grid level of the plan (coarser ones for boxes that span many fine cells, the
-    // deep level for long walks); level 0 if that level is not built
-    const IndexLevelView& L =
-        S.lv[S.lv[plan.level].ranked && lim <= (uint32_t)S.lv[plan.level].M ? plan.level : 0];
-    lim = min(lim, (uint32_t)L.M);  // every point below lim is in the level's lists
-    const uint2* cells = L.cell;
-    const uint2* ents = L.ent;
-    const int gb = L.gbits, shf = L.shift;
-    const uint32_t Ml = (uint32_t)L.M;
-    int lev = 0;  // smallest level Ml >> lev that is still >= lim
-    while (lev + 1 < kRankLevels && (Ml >> (lev + 1)) >= lim) ++lev;
-    int lev1 = lev;  // smallest level >= the first pass's bound
-    while (lev1 + 1 < kRankLevels && (Ml >> (lev1 + 1)) >= plan.lim1) ++lev1;
+    // grid levels of the plan's two passes (coarser ones for boxes that span many
+    // fine cells, the deep level for long walks); level 0 (second pass) or the
+    // second pass's level (first pass) where that level is not built
+    const int l2 = S.lv[plan.level].ranked && lim <= (uint32_t)S.lv[plan.level].M ? plan.level : 0;
+    lim = min(lim, (uint32_t)S.lv[l2].M);  // every point below lim is in the level's lists
+    const uint32_t lim1 = min(plan.lim1, lim);
+    const int l1 = S.lv[plan.level1].ranked && lim1 <= (uint32_t)S.lv[plan.level1].M ? plan.level1 : l2;
+    // first pass: the points below bound1 = M1 >> lev1, the smallest rank level >= lim1
+    int lev1 = 0;
+    while (lev1 + 1 < kRankLevels && ((uint32_t)S.lv[l1].M >> (lev1 + 1)) >= lim1) ++lev1;
+    const uint32_t bound1 = (uint32_t)S.lv[l1].M >> lev1;
+    // second pass: up to M2 >> lev (the smallest rank level >= lim), skipping the
+    // points below bound1 when that is a rank level of its level (else reading
+    // them again: they are outside the polygon or above their hash's bound)
+    int lev = 0;
+    while (lev + 1 < kRankLevels && ((uint32_t)S.lv[l2].M >> (lev + 1)) >= lim) ++lev;
+    int lev_skip = -1;
+    for (int t = lev; t < kRankLevels; ++t)
+        if (((uint32_t)S.lv[l2].M >> t) == bound1) lev_skip = t;
+    const bool second = ((uint32_t)S.lv[l2].M >> lev) > bound1;
     const MaskedWalker<Src> walker{&m, src, bb.x, bb.y, cwl, chl};
-
-    // cells under the box, row-major; a round reads two cells for the kSub
-    // hashes of a group (lane: hash lane & 15, cell 2 * round + lane / 16)
-    const int cx0 = bb.x >> shf, cy0 = bb.y >> shf;
-    const int ncx = ((bb.z - 1) >> shf) - cx0 + 1;
-    const int C = ncx * (((bb.w - 1) >> shf) - cy0 + 1);
     const int hl = lane & (kSub - 1);
 
     for (int kc = k_begin; kc < k_end; kc += kSub) {
@@ -320,9 +321,19 @@ __device__ __forceinline__ void indexed_range(UniWarp& m, const Src& src, const 
         // then, for the hashes with no inside point yet, those up to level lev
         uint32_t open = kn == 32 ? 0xFFFFFFFFu : ((1u << kn) - 1u);
         for (int pass = 0; pass < 2 && lim > 0; ++pass) {
-            const int hi_lev = pass == 0 ? lev1 : lev;  // read entries below Ml >> hi_lev
-            const int lo_lev = pass == 0 ? -1 : lev1;   // ... skipping those below Ml >> lo_lev
-            if (pass == 1 && (lev1 == lev || open == 0)) break;
+            const int hi_lev = pass == 0 ? lev1 : lev;       // read entries below M >> hi_lev
+            const int lo_lev = pass == 0 ? -1 : lev_skip;    // ... skipping those below M >> lo_lev
+            if (pass == 1 && (!second || open == 0)) break;
+            // the pass's grid level: cells under the box, row-major; a round reads two
+            // cells for the kSub hashes of a group (lane: hash lane & 15, cell
+            // 2 * round + lane / 16)
+            const IndexLevelView& L = S.lv[pass == 0 ? l1 : l2];
+            const uint2* cells = L.cell;
+            const uint2* ents = L.ent;
+            const int gb = L.gbits, shf = L.shift;
+            const int cx0 = bb.x >> shf, cy0 = bb.y >> shf;
+            const int ncx = ((bb.z - 1) >> shf) - cx0 + 1;
+            const int C = ncx * (((bb.w - 1) >> shf) - cy0 + 1);
             if (lane == 0) m.npool = 0;
             __syncwarp();
             const bool mine = hl < kn && ((open >> hl) & 1u);
@@ -563,7 +574,7 @@ sign_unified_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
             continue;
         }
         // the form (indexed or walk) and grid level the polygon's cost model picks
-        const PmhIndexPlan plan = (S.cell && area2) ? pmh_index_plan(bb, area2[p]) : PmhIndexPlan{0u, 0, 0u};
+        const PmhIndexPlan plan = (S.cell && area2) ? pmh_index_plan(bb, area2[p]) : PmhIndexPlan{0u, 0, 0u, 0};
         if (staged) {
             // stage the polygon (closed: v[n] = v[0]; cp.async 8-byte copies) and bin its edges
             stage_vertices(m.v, xy + b, n, lane);
