@@ -31,6 +31,13 @@ __device__ __forceinline__ int slab_count_for(int n, int height)
     return min(s, 1 << 16);
 }
 
+// floor(x / h) by a multiply: with m = floor(2^40 / h) + 1 (slab_div_magic), x * m / 2^40
+// exceeds x / h by less than x / 2^40 < 2^-18 for x < 2^22, which is below the gap 1/h
+// between x / h and the next integer for every h < 2^18 (slab heights here are at most
+// 2^21 / 64 for polygons above 256 vertices, or 1), so the floor is exact
+__device__ __forceinline__ uint64_t slab_div_magic(int h) { return (1ull << 40) / (uint64_t)h + 1ull; }
+__device__ __forceinline__ int slab_div(int x, uint64_t m) { return (int)(((uint64_t)x * m) >> 40); }
+
 // pass 1: sizes of every polygon's slab table and edge list
 __global__ void slab_size_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
                                  int64_t n_polys, const int64_t* __restrict__ d_n, int min_verts,
@@ -73,12 +80,13 @@ __global__ void slab_size_kernel(const int2* __restrict__ xy, const int64_t* __r
         const int height = y1 - y0;
         const int S = slab_count_for(n, height);
         const int h = max((height + S - 1) / S, 1);
+        const uint64_t hm = slab_div_magic(h);
         long long entries = 0;
         for (int e = lane; e < n; e += 32) {
             int ay = xy[b + e].y, by = xy[b + (e + 1 == n ? 0 : e + 1)].y;
             if (ay == by) continue;
             int lo = min(ay, by) - y0, hi = max(ay, by) - 1 - y0;
-            entries += hi / h - lo / h + 1;
+            entries += slab_div(hi, hm) - slab_div(lo, hm) + 1;
         }
         for (int o = 16; o > 0; o >>= 1) entries += __shfl_xor_sync(0xffffffffu, entries, o);
         if (lane == 0) {
@@ -112,6 +120,7 @@ __global__ void __launch_bounds__(kFillThreads) slab_fill_kernel(const int2* __r
         if (n <= min_verts) continue;
         SlabInfo si = info[p];
         const int S = si.S, h = si.slab_h, y0 = si.ymin;
+        const uint64_t hm = slab_div_magic(h);
         const int64_t pb = ptr_base[p], eb = edge_base[p];
         if (ptr_base[p + 1] > cap_ptr || edge_base[p + 1] > cap_edges) {
             // the lists do not fit the fixed buffers: this polygon is tested over all its edges
@@ -129,7 +138,7 @@ __global__ void __launch_bounds__(kFillThreads) slab_fill_kernel(const int2* __r
         for (int e = lane; e < n; e += 32) {
             int ay = xy[b + e].y, by = xy[b + (e + 1 == n ? 0 : e + 1)].y;
             if (ay == by) continue;
-            int lo = (min(ay, by) - y0) / h, hi = (max(ay, by) - 1 - y0) / h;
+            int lo = slab_div(min(ay, by) - y0, hm), hi = slab_div(max(ay, by) - 1 - y0, hm);
             for (int s = lo; s <= hi; ++s) atomicAdd(&cur[s], 1);
         }
         __syncwarp();
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(kFillThreads) slab_fill_kernel(const int2* __r
         for (int e = lane; e < n; e += 32) {
             int ay = xy[b + e].y, by = xy[b + (e + 1 == n ? 0 : e + 1)].y;
             if (ay == by) continue;
-            int lo = (min(ay, by) - y0) / h, hi = (max(ay, by) - 1 - y0) / h;
+            int lo = slab_div(min(ay, by) - y0, hm), hi = slab_div(max(ay, by) - 1 - y0, hm);
             for (int s = lo; s <= hi; ++s) slab_edges[eb + atomicAdd(&cur[s], 1)] = e;
         }
         __syncwarp();
