@@ -393,7 +393,7 @@ __device__ __forceinline__ PairView view(const int2* xy, const int64_t* off, con
 }
 
 constexpr int kRefineWarps = 4;  // two pairs per block, two warps per pair
-constexpr int kWarpVerts = 512;  // both polygons staged per pair when they fit
+constexpr int kWarpVerts = 1024;  // vertices of a pair's staging slice
 
 // one pair's shared slice: the staged rings, a crossing queue per warp, both rings'
 // slab lists, and the two warps' partial sums
@@ -434,13 +434,18 @@ __device__ double pair_jaccard(PairView A, PairView B, RefPair& P, int wip, int 
     if (A.sgn == 0 || B.sgn == 0) return 0.0;
     const int2* a = A.v;
     const int2* b = B.v;
-    if (A.n + B.n <= kWarpVerts) {
-        stage_ring(P.sv, A.v, A.n, 32 * wip + lane);
-        stage_ring(P.sv + A.n, B.v, B.n, 32 * wip + lane);
+    // both rings staged when they fit the slice, else the one that fits (B first: its
+    // edges are the inner loop of two of the three passes), else neither
+    const bool sa = A.n + B.n <= kWarpVerts || (B.n > kWarpVerts && A.n <= kWarpVerts);
+    const bool sb = A.n + B.n <= kWarpVerts || B.n <= kWarpVerts;
+    if (sa || sb) {
+        const int boff = sa ? A.n : 0;
+        if (sa) stage_ring(P.sv, A.v, A.n, 32 * wip + lane);
+        if (sb) stage_ring(P.sv + boff, B.v, B.n, 32 * wip + lane);
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         pair_sync(g);
-        a = P.sv;
-        b = P.sv + A.n;
+        if (sa) a = P.sv;
+        if (sb) b = P.sv + boff;
     }
     const bool ok = build_ref_slabs(wip == 0 ? a : b, wip == 0 ? A.n : B.n, P.sl[wip], lane);
     if (lane == 0) P.ok[wip] = ok;
