@@ -42,6 +42,7 @@ struct pmh_qgraph_s {
     int32_t* slab_edges = nullptr;
     int64_t cap_ptr = 0, cap_edges = 0;
     int64_t* counts = nullptr;
+    int32_t* join_stage = nullptr;    // short join rows sorted by the count pass (nullable)
     int64_t* row_ptr = nullptr;
     int32_t* cand = nullptr;
     uint16_t* count16 = nullptr;
@@ -91,7 +92,7 @@ extern "C" int pmh_qgraph_destroy(pmh_qgraph g)
                     g->top_ids,   g->top_n,      g->jv,         g->ref_ids,   g->ref_j,
                     g->flags,     g->d_n,        g->ticket,     g->scan_sums, g->sl_ids,
                     g->sl_n,      g->sl_counts,  g->sl_sums,    g->sl_row_ptr, g->sl_cand,
-                    g->qfeat,     g->feat,       g->score};
+                    g->qfeat,     g->feat,       g->score,     g->join_stage};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete g;
@@ -157,6 +158,8 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_
               cudaMalloc(&g->slab_cursor, sizeof(int32_t) * g->cap_ptr) == cudaSuccess &&
               cudaMalloc(&g->slab_edges, sizeof(int32_t) * g->cap_edges) == cudaSuccess &&
               cudaMalloc(&g->counts, sizeof(int64_t) * Q) == cudaSuccess &&
+              (pmh_join_stage_ints(index, Q) == 0 ||
+               cudaMalloc(&g->join_stage, sizeof(int32_t) * pmh_join_stage_ints(index, Q)) == cudaSuccess) &&
               cudaMalloc(&g->row_ptr, sizeof(int64_t) * (Q + 1)) == cudaSuccess &&
               cudaMalloc(&g->cand, sizeof(int32_t) * cand_capacity) == cudaSuccess &&
               cudaMalloc(&g->count16, sizeof(uint16_t) * cand_capacity) == cudaSuccess &&
@@ -206,12 +209,12 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_
                                      g->slab_edges, nullptr, Q, Q, g->d_n, g->flags, &g->P, sidx,
                                      g->ticket, g->hashes, nullptr, cs);
     if (rc == PMH_OK)
-        rc = pmh_launch_query(index, g->hashes, Q, g->d_n, g->counts, nullptr, nullptr, 0, g->flags,
-                              false, cs);
+        rc = pmh_launch_query(index, g->hashes, Q, g->d_n, g->counts, nullptr, nullptr, 0, g->join_stage,
+                              g->flags, false, cs);
     if (rc == PMH_OK) rc = pmh_exclusive_scan_i64(ctx, g->counts, g->row_ptr, Q, cs, g->scan_sums);
     if (rc == PMH_OK)
         rc = pmh_launch_query(index, g->hashes, Q, g->d_n, nullptr, g->row_ptr, g->cand, g->cap,
-                              g->flags, true, cs);
+                              g->join_stage, g->flags, true, cs);
     if (rc == PMH_OK)
         rc = pmh_launch_agree(ctx, g->hashes, index->hashes, g->row_ptr, g->cand, Q, g->cap, &g->P,
                               g->count16, nullptr, g->flags, cs);

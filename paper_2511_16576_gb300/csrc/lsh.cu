@@ -9,9 +9,10 @@
 // directory over the composites' top bits (about eight entries per slot)
 // bounds each lookup to one short range.  A query
 // binary-searches its composite there per band and walks the equal range, keeping
-// entries whose full 64-bit key AND r-tuple equal its own (exact bucket
-// membership).  The per-band id lists are ascending, so a warp merges them
-// (min over lanes) into the sorted, duplicate-free candidate row.
+// the entries whose r-tuple equals its own (exact bucket membership; an entry of
+// another key shares the composite with probability ~n / 2^(32 - band_bits) per
+// lookup and costs one tuple read).  The per-band id lists are ascending, so a
+// warp merges them (min over lanes) into the sorted, duplicate-free candidate row.
 #include <algorithm>
 
 #include "pmh_internal.cuh"
@@ -50,31 +51,20 @@ __device__ __forceinline__ uint32_t composite(uint64_t key, int j, int band_bits
     return ((uint32_t)j << (32 - band_bits)) | (uint32_t)(key >> (32 + band_bits));
 }
 
-// entries in band-major order: e = j * n + p
-__global__ void fill_entries_kernel(const uint64_t* __restrict__ keys, int64_t n, int bands,
-                                    int band_bits, uint32_t* __restrict__ comp,
-                                    int32_t* __restrict__ ids)
+// entries in polygon-major order, e = p * bands + j (within one band, ascending ids:
+// the stable sort keeps them ascending inside a bucket), band keys computed from the
+// hashes in place
+__global__ void fill_entries_kernel(const uint32_t* __restrict__ hashes, int64_t n, int K, int bands,
+                                    int rows, uint32_t T, uint64_t lsh_seed, int band_bits,
+                                    uint32_t* __restrict__ comp, int32_t* __restrict__ ids)
 {
-    int64_t total = n * bands;
+    const int64_t total = n * bands;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int j = (int)(e / n);
-        int64_t p = e - (int64_t)j * n;
-        comp[e] = composite(keys[p * bands + j], j, band_bits);
+        const int64_t p = e / bands;
+        const int j = (int)(e - p * bands);
+        comp[e] = composite(band_key(hashes + p * K, j, rows, T, lsh_seed), j, band_bits);
         ids[e] = (int32_t)p;
-    }
-}
-
-// full 64-bit key of every sorted entry (band from the composite's top bits)
-__global__ void gather_keys_kernel(const uint32_t* __restrict__ comp, const int32_t* __restrict__ ids,
-                                   const uint64_t* __restrict__ keys, int64_t m, int bands,
-                                   int band_bits, uint64_t* __restrict__ out)
-{
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t c = comp[e];
-        out[e] = c == 0xFFFFFFFFu ? PMH_INVALID_KEY
-                                  : keys[(int64_t)ids[e] * bands + (int)(c >> (32 - band_bits))];
     }
 }
 
@@ -117,7 +107,6 @@ constexpr int32_t kNone = 0x7FFFFFFF;
 struct BandCursor {
     int64_t cur;
     uint32_t comp;
-    uint64_t key;
     int j;
     int32_t head;
 };
@@ -131,10 +120,11 @@ __device__ __forceinline__ bool tuple_equal(const uint32_t* __restrict__ a,
 }
 
 // advance c to the next entry of its band that is an exact bucket member: the
-// walk reads the sorted arrays sequentially; only a key match gathers the tuple
+// walk reads the sorted arrays sequentially and gathers the tuple of every entry
+// with the query's composite (the bucket's members, and the rare entries of other
+// keys sharing the composite's key bits)
 __device__ __forceinline__ void advance(BandCursor& c, const uint32_t* __restrict__ comp,
                                         const int32_t* __restrict__ ids,
-                                        const uint64_t* __restrict__ skeys,
                                         const uint32_t* __restrict__ dbh,
                                         const uint32_t* __restrict__ qh, int64_t m, int K,
                                         int bands, int rows)
@@ -142,7 +132,6 @@ __device__ __forceinline__ void advance(BandCursor& c, const uint32_t* __restric
     c.head = kNone;
     while (c.cur < m && comp[c.cur] == c.comp) {
         const int64_t e = c.cur++;
-        if (skeys[e] != c.key) continue;
         const int32_t p = ids[e];
         if (tuple_equal(qh, dbh + (int64_t)p * K, c.j, rows)) {
             c.head = p;
@@ -159,7 +148,7 @@ template <bool kWrite>
 __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands,
                              int rows, uint32_t T, uint64_t lsh_seed, int band_bits,
                              const uint32_t* __restrict__ comp, const int32_t* __restrict__ ids,
-                             const uint64_t* __restrict__ skeys, const uint32_t* __restrict__ dbh,
+                             const uint32_t* __restrict__ dbh,
                              const int64_t* __restrict__ dir, int dsh, int64_t m,
                              int64_t* __restrict__ counts,
                              const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand,
@@ -190,10 +179,9 @@ __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, in
         if (j >= bands) continue;
         uint64_t key = band_key(qh, j, rows, T, lsh_seed);
         if (key == PMH_INVALID_KEY) continue;
-        cur[t].key = key;
         cur[t].comp = composite(key, j, band_bits);
         cur[t].cur = comp_lower_bound(comp, dir, dsh, cur[t].comp);
-        advance(cur[t], comp, ids, skeys, dbh, qh, m, K, bands, rows);
+        advance(cur[t], comp, ids, dbh, qh, m, K, bands, rows);
     }
     int64_t out = kWrite ? row_ptr[q] : 0;
     int64_t cnt = 0;
@@ -207,7 +195,7 @@ __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, in
         ++cnt;
 #pragma unroll
         for (int t = 0; t < kMaxBandsPerLane; ++t)
-            if (cur[t].head == best) advance(cur[t], comp, ids, skeys, dbh, qh, m, K, bands, rows);
+            if (cur[t].head == best) advance(cur[t], comp, ids, dbh, qh, m, K, bands, rows);
     }
     if (!kWrite && lane == 0) counts[q] = cnt;
 }
@@ -221,7 +209,10 @@ __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, in
 // slots, several blocks per SM) takes every row of at most 4,096 distinct
 // candidates; a row that overflows it is marked (count -1) and counted again,
 // like every longer row filled, by the large one (32,768 slots, one block per
-// SM).  A row beyond even that falls back to the warp merge (warp 0).
+// SM).  A row beyond even that falls back to the warp merge (warp 0).  Given a
+// staging buffer (4,096 ids per query), the small set's count pass also writes
+// its sorted rows there, and the fill pass of those rows is a copy into place
+// (copy_rows_kernel) instead of a second join.
 template <bool kBig>
 struct JoinShape {
     static constexpr int kThreads = kBig ? 512 : 256;
@@ -234,8 +225,7 @@ constexpr int kSmallRowMax = JoinShape<false>::kMaxUnique;
 
 __device__ int64_t merge_row(const uint32_t* __restrict__ qh, int K, int bands, int rows, uint32_t T,
                              uint64_t lsh_seed, int band_bits, const uint32_t* __restrict__ comp,
-                             const int32_t* __restrict__ ids, const uint64_t* __restrict__ skeys,
-                             const uint32_t* __restrict__ dbh, const int64_t* __restrict__ dir,
+                             const int32_t* __restrict__ ids, const uint32_t* __restrict__ dbh, const int64_t* __restrict__ dir,
                              int dsh, int64_t m, int32_t* __restrict__ out)
 {
     const int lane = threadIdx.x & 31;
@@ -248,10 +238,9 @@ __device__ int64_t merge_row(const uint32_t* __restrict__ qh, int K, int bands, 
         if (j >= bands) continue;
         uint64_t key = band_key(qh, j, rows, T, lsh_seed);
         if (key == PMH_INVALID_KEY) continue;
-        cur[t].key = key;
         cur[t].comp = composite(key, j, band_bits);
         cur[t].cur = comp_lower_bound(comp, dir, dsh, cur[t].comp);
-        advance(cur[t], comp, ids, skeys, dbh, qh, m, K, bands, rows);
+        advance(cur[t], comp, ids, dbh, qh, m, K, bands, rows);
     }
     int64_t cnt = 0;
     for (;;) {
@@ -264,7 +253,7 @@ __device__ int64_t merge_row(const uint32_t* __restrict__ qh, int K, int bands, 
         ++cnt;
 #pragma unroll
         for (int t = 0; t < kMaxBandsPerLane; ++t)
-            if (cur[t].head == best) advance(cur[t], comp, ids, skeys, dbh, qh, m, K, bands, rows);
+            if (cur[t].head == best) advance(cur[t], comp, ids, dbh, qh, m, K, bands, rows);
     }
     return cnt;
 }
@@ -279,11 +268,10 @@ template <bool kWrite, bool kBig>
 __global__ void __launch_bounds__(JoinShape<kBig>::kThreads)
 join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, int rows, uint32_t T,
             uint64_t lsh_seed, int band_bits, const uint32_t* __restrict__ comp,
-            const int32_t* __restrict__ ids, const uint64_t* __restrict__ skeys,
-            const uint32_t* __restrict__ dbh, const int64_t* __restrict__ dir, int dsh, int64_t m,
-            int64_t* __restrict__ counts,
+            const int32_t* __restrict__ ids, const uint32_t* __restrict__ dbh,
+            const int64_t* __restrict__ dir, int dsh, int64_t m, int64_t* __restrict__ counts,
             const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand, int64_t cap,
-            const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
+            int32_t* __restrict__ stage, const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
 {
     using S = JoinShape<kBig>;
     constexpr int kJoinTable = S::kTable, kJoinMaxUnique = S::kMaxUnique;
@@ -320,7 +308,7 @@ join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, i
                 const int64_t e = base + lane;
                 const bool in = e < m && comp[e] == c;
                 if (!__any_sync(0xffffffffu, in)) break;
-                if (!in || skeys[e] != key) continue;
+                if (!in) continue;
                 const int32_t p = ids[e];
                 if (!tuple_equal(qh, dbh + (int64_t)p * K, j, rows)) continue;
                 uint32_t h = slot_hash<S::kLog2Table>(p);
@@ -343,7 +331,7 @@ join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, i
         }
         if (nu > kJoinMaxUnique) {  // rare: merge the row with warp 0
             if (wid == 0) {
-                int64_t cnt = merge_row(qh, K, bands, rows, T, lsh_seed, band_bits, comp, ids, skeys,
+                int64_t cnt = merge_row(qh, K, bands, rows, T, lsh_seed, band_bits, comp, ids,
                                         dbh, dir, dsh, m, kWrite ? cand + row_ptr[q] : nullptr);
                 if (!kWrite && lane == 0) counts[q] = cnt;
             }
@@ -351,7 +339,7 @@ join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, i
         }
         if (!kWrite) {
             if (threadIdx.x == 0) counts[q] = nu;
-            continue;
+            if (!stage) continue;  // (else the sorted row goes to the staging buffer)
         }
         // compact the occupied slots into buf (block scan over contiguous slot ranges),
         // then sort only the next power of two above nu
@@ -389,9 +377,29 @@ join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, i
                 }
                 __syncthreads();
             }
-        int32_t* out = cand + row_ptr[q];
+        int32_t* out = kWrite ? cand + row_ptr[q] : stage + q * (int64_t)kSmallRowMax;
         for (int i = threadIdx.x; i < nu; i += blockDim.x) out[i] = buf[i];
     }
+}
+
+// fill pass of the rows the small set counted and staged: a warp per query copies
+// its sorted row into place (longer rows are the large set's)
+__global__ void copy_rows_kernel(const int32_t* __restrict__ stage, int64_t Q,
+                                 const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand,
+                                 int64_t cap, const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= Q) return;
+    if ((d_n && q >= *d_n) || (d_flags && (*d_flags & 7))) return;
+    if (row_ptr[Q] > cap) {
+        if (lane == 0 && d_flags) atomicOr(d_flags, 8);
+        return;
+    }
+    const int64_t b = row_ptr[q], len = row_ptr[q + 1] - b;
+    if (len > kSmallRowMax) return;
+    const int32_t* src = stage + q * (int64_t)kSmallRowMax;
+    for (int64_t i = lane; i < len; i += 32) cand[b + i] = src[i];
 }
 
 }  // namespace
@@ -437,15 +445,12 @@ static int index_fill(pmh_ctx ctx, pmh_index X, const uint32_t* d_hashes, cudaSt
     cudaError_t e = cudaMemcpyAsync(X->hashes, d_hashes, sizeof(uint32_t) * n * params->K,
                                     cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return pmh_set_error(PMH_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
-    PMH_TRY(pmh_band_keys(ctx, X->hashes, n, params, X->keys, s));
     int blocks = (int)std::min<int64_t>((entries + 255) / 256, (int64_t)ctx->sm_count * 32);
-    fill_entries_kernel<<<blocks, 256, 0, s>>>(X->keys, n, (int)params->bands, bb, X->sorted_comp,
-                                                X->sorted_id);
+    fill_entries_kernel<<<blocks, 256, 0, s>>>(X->hashes, n, (int)params->K, (int)params->bands,
+                                                (int)params->rows, params->T, params->lsh_seed, bb,
+                                                X->sorted_comp, X->sorted_id);
     PMH_LAUNCHED("fill_entries_kernel");
     PMH_TRY(pmh_radix_sort_u32(ctx, X->sorted_comp, X->sorted_id, entries, 32, s));
-    gather_keys_kernel<<<blocks, 256, 0, s>>>(X->sorted_comp, X->sorted_id, X->keys, entries,
-                                               (int)params->bands, bb, X->sorted_key);
-    PMH_LAUNCHED("gather_keys_kernel");
     const int dblocks = (int)std::min<int64_t>((entries + 256) / 256, (int64_t)ctx->sm_count * 32);
     dir_kernel<<<dblocks, 256, 0, s>>>(X->sorted_comp, entries, X->dir_shift, dir_cmax(X), X->dir);
     PMH_LAUNCHED("dir_kernel");
@@ -482,10 +487,8 @@ extern "C" int pmh_lsh_build(pmh_ctx ctx, const uint32_t* d_hashes, int64_t n,
     X->dir_shift = dir_shift_for(entries, dir_cmax(X));
     const size_t nn = (size_t)std::max<int64_t>(n, 1), ne = (size_t)std::max<int64_t>(entries, 1);
     if (cudaMalloc(&X->hashes, sizeof(uint32_t) * nn * params->K) != cudaSuccess ||
-        cudaMalloc(&X->keys, sizeof(uint64_t) * nn * params->bands) != cudaSuccess ||
         cudaMalloc(&X->sorted_comp, sizeof(uint32_t) * ne) != cudaSuccess ||
         cudaMalloc(&X->sorted_id, sizeof(int32_t) * ne) != cudaSuccess ||
-        cudaMalloc(&X->sorted_key, sizeof(uint64_t) * ne) != cudaSuccess ||
         cudaMalloc(&X->dir, sizeof(int64_t) * dir_len(X)) != cudaSuccess) {
         cudaGetLastError();
         pmh_index_destroy(X);
@@ -516,10 +519,8 @@ extern "C" int pmh_index_destroy(pmh_index X)
     cudaSetDevice(X->device);
     cudaDeviceSynchronize();
     if (X->hashes) cudaFree(X->hashes);
-    if (X->keys) cudaFree(X->keys);
     if (X->sorted_comp) cudaFree(X->sorted_comp);
     if (X->sorted_id) cudaFree(X->sorted_id);
-    if (X->sorted_key) cudaFree(X->sorted_key);
     if (X->dir) cudaFree(X->dir);
     delete X;
     return PMH_OK;
@@ -529,7 +530,7 @@ extern "C" int pmh_index_destroy(pmh_index X)
 template <bool kBig>
 static int launch_join(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
                        int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
-                       int* d_flags, bool write, cudaStream_t s)
+                       int32_t* stage, int* d_flags, bool write, cudaStream_t s)
 {
     using S = JoinShape<kBig>;
     const pmh_params& P = X->params;
@@ -542,17 +543,23 @@ static int launch_join(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t
         (unsigned)std::min<int64_t>(Q, (int64_t)X->ctx->sm_count * std::max(per_sm, 1));
     fn<<<blocks, S::kThreads, S::kSmem, s>>>(qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T,
                                             P.lsh_seed, X->band_bits, X->sorted_comp, X->sorted_id,
-                                            X->sorted_key, X->hashes, X->dir, X->dir_shift, m,
+                                            X->hashes, X->dir, X->dir_shift, m,
                                             write ? nullptr : counts, write ? row_ptr : nullptr,
-                                            write ? cand : nullptr, write ? cap : 0, d_n, d_flags);
+                                            write ? cand : nullptr, write ? cap : 0,
+                                            kBig ? nullptr : stage, d_n, d_flags);
     PMH_LAUNCHED(write ? (kBig ? "join_kernel<fill,large>" : "join_kernel<fill,small>")
                        : (kBig ? "join_kernel<count,large>" : "join_kernel<count,small>"));
     return PMH_OK;
 }
 
+int64_t pmh_join_stage_ints(pmh_index X, int64_t Q)
+{
+    return X && X->params.bands >= 16 ? Q * (int64_t)kSmallRowMax : 0;
+}
+
 int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
                      int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
-                     int* d_flags, bool write, cudaStream_t s)
+                     int32_t* stage, int* d_flags, bool write, cudaStream_t s)
 {
     if (Q <= 0) return PMH_OK;
     const pmh_params& P = X->params;
@@ -561,22 +568,28 @@ int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* 
     // set (rows of thousands of candidates occur on dense sets; the warp merge below
     // would walk them one candidate at a time)
     if (P.bands >= 16) {
-        PMH_TRY(launch_join<false>(X, qh, Q, d_n, counts, row_ptr, cand, cap, d_flags, write, s));
-        return launch_join<true>(X, qh, Q, d_n, counts, row_ptr, cand, cap, d_flags, write, s);
+        if (write && stage) {  // the staged short rows: a copy into place
+            const unsigned cblocks = (unsigned)((Q + 7) / 8);
+            copy_rows_kernel<<<cblocks, 256, 0, s>>>(stage, Q, row_ptr, cand, cap, d_n, d_flags);
+            PMH_LAUNCHED("copy_rows_kernel");
+        } else {
+            PMH_TRY(launch_join<false>(X, qh, Q, d_n, counts, row_ptr, cand, cap, stage, d_flags, write, s));
+        }
+        return launch_join<true>(X, qh, Q, d_n, counts, row_ptr, cand, cap, nullptr, d_flags, write, s);
     }
     const int wpb = 8;
     unsigned blocks = (unsigned)((Q + wpb - 1) / wpb);
     if (write) {
         query_kernel<true><<<blocks, wpb * 32, 0, s>>>(
             qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T, P.lsh_seed, X->band_bits,
-            X->sorted_comp, X->sorted_id, X->sorted_key, X->hashes, X->dir, X->dir_shift, m, nullptr,
+            X->sorted_comp, X->sorted_id, X->hashes, X->dir, X->dir_shift, m, nullptr,
                 row_ptr, cand, cap, d_n,
             d_flags);
         PMH_LAUNCHED("query_kernel<fill>");
     } else {
         query_kernel<false><<<blocks, wpb * 32, 0, s>>>(
             qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T, P.lsh_seed, X->band_bits,
-            X->sorted_comp, X->sorted_id, X->sorted_key, X->hashes, X->dir, X->dir_shift, m, counts,
+            X->sorted_comp, X->sorted_id, X->hashes, X->dir, X->dir_shift, m, counts,
                 nullptr, nullptr, 0, d_n,
             d_flags);
         PMH_LAUNCHED("query_kernel<count>");
@@ -599,7 +612,13 @@ extern "C" int pmh_lsh_query(pmh_ctx ctx, pmh_index X, const uint32_t* d_qhashes
     }
     int64_t* counts = nullptr;
     PMH_TRY(pmh_scratch(ctx, SCR_QUERY, sizeof(int64_t) * (size_t)Q, (void**)&counts));
-    PMH_TRY(pmh_launch_query(X, d_qhashes, Q, nullptr, counts, nullptr, nullptr, 0, nullptr, false, s));
+    // the short rows staged by the count pass when the staging buffer stays modest
+    int32_t* stage = nullptr;
+    const int64_t stage_ints = pmh_join_stage_ints(X, Q);
+    if (stage_ints > 0 && stage_ints <= (64ll << 20))
+        PMH_TRY(pmh_scratch(ctx, SCR_JOIN, sizeof(int32_t) * (size_t)stage_ints, (void**)&stage));
+    PMH_TRY(pmh_launch_query(X, d_qhashes, Q, nullptr, counts, nullptr, nullptr, 0, stage, nullptr, false,
+                             s));
     PMH_TRY(pmh_exclusive_scan_i64(ctx, counts, d_row_ptr, Q, s));
     PMH_CUDA_TRY(cudaMemcpyAsync(ctx->h_pinned, d_row_ptr + Q, sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, s));
@@ -612,7 +631,7 @@ extern "C" int pmh_lsh_query(pmh_ctx ctx, pmh_index X, const uint32_t* d_qhashes
     if (total == 0) return PMH_OK;
     if (!d_cand) return pmh_set_error(PMH_ERR_ARG, "null candidate buffer");
     return pmh_launch_query(X, d_qhashes, Q, nullptr, nullptr, d_row_ptr, d_cand, cand_capacity,
-                            nullptr, true, s);
+                            stage, nullptr, true, s);
 }
 
 extern "C" int pmh_lsh_query_fill(pmh_ctx ctx, pmh_index X, const uint32_t* d_qhashes, int64_t Q,
@@ -624,5 +643,5 @@ extern "C" int pmh_lsh_query_fill(pmh_ctx ctx, pmh_index X, const uint32_t* d_qh
         return pmh_set_error(PMH_ERR_ARG, "bad arguments");
     if (Q == 0) return PMH_OK;
     return pmh_launch_query(X, d_qhashes, Q, nullptr, nullptr, d_row_ptr, d_cand, cand_capacity,
-                            nullptr, true, (cudaStream_t)stream);
+                            nullptr, nullptr, true, (cudaStream_t)stream);
 }

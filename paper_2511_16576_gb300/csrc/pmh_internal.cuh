@@ -51,6 +51,7 @@ enum ScratchSlot {
     SCR_QUERY,
     SCR_REFINE,
     SCR_MISC,
+    SCR_JOIN,
     SCR_COUNT
 };
 
@@ -278,13 +279,11 @@ struct pmh_index_s {
     pmh_params params{};
     int band_bits = 0;
     uint32_t* hashes = nullptr;     // [n][K]
-    uint64_t* keys = nullptr;       // [n][bands]
     uint32_t* sorted_comp = nullptr;  // [n * bands] composite (band, key) sort keys
     int32_t* sorted_id = nullptr;     // [n * bands]
-    uint64_t* sorted_key = nullptr;   // [n * bands] full band key of each sorted entry
     // directory of the sorted composites: dir[s] = first entry whose composite >> dir_shift
-    // is >= s, for s in [0, (bands << (32 - band_bits)) >> dir_shift] (a lower bound of a
-    // valid composite reads one short range)
+    // is >= s, for s in [0, ceil((bands << (32 - band_bits)) / 2^dir_shift)] (a lower bound
+    // of a valid composite reads one short range)
     int64_t* dir = nullptr;
     int dir_shift = 32;
 };
@@ -359,9 +358,13 @@ int pmh_launch_sign_unified(pmh_ctx ctx, int U, const int2* xy, const int64_t* o
                             const int* d_flags, const pmh_params* P, const StreamIndexView& S,
                             unsigned long long* ticket, uint32_t* out, unsigned long long* work,
                             cudaStream_t s);
+// bucket join (lsh.cu): the count pass (write false: counts) or the fill pass (write
+// true: the CSR rows); `stage` (nullable, pmh_join_stage_ints(X, Q) ints) lets the
+// count pass keep the short rows it sorted, so that the fill pass copies them
+int64_t pmh_join_stage_ints(pmh_index X, int64_t Q);
 int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
                      int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
-                     int* d_flags, bool write, cudaStream_t s);
+                     int32_t* stage, int* d_flags, bool write, cudaStream_t s);
 int pmh_launch_agree(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph, const int64_t* row_ptr,
                      const int32_t* cand, int64_t Q, int64_t cap, const pmh_params* P,
                      uint16_t* count, uint32_t* bandmask, const int* d_flags, cudaStream_t s);
