@@ -206,17 +206,23 @@ struct RefSlabs {
     uint16_t beg[kRefSlabs + 2];
     int cnt[kRefSlabs];
     int y0, sh;
+    int x0, x1;  // the ring's x-range
 };
 
 __device__ __forceinline__ bool build_ref_slabs(const int2* v, int n, RefSlabs& L, int lane)
 {
-    int y0 = INT_MAX, y1 = INT_MIN;
+    int y0 = INT_MAX, y1 = INT_MIN, x0 = INT_MAX, x1 = INT_MIN;
     for (int e = lane; e < n; e += 32) {
-        y0 = min(y0, v[e].y);
-        y1 = max(y1, v[e].y);
+        const int2 u = v[e];
+        y0 = min(y0, u.y);
+        y1 = max(y1, u.y);
+        x0 = min(x0, u.x);
+        x1 = max(x1, u.x);
     }
     y0 = __reduce_min_sync(0xffffffffu, y0);
     y1 = __reduce_max_sync(0xffffffffu, y1);
+    x0 = __reduce_min_sync(0xffffffffu, x0);
+    x1 = __reduce_max_sync(0xffffffffu, x1);
     int sh = 0;
     while (((y1 - y0) >> sh) >= kRefSlabs) ++sh;
     L.cnt[2 * lane] = 0;
@@ -244,6 +250,8 @@ __device__ __forceinline__ bool build_ref_slabs(const int2* v, int n, RefSlabs& 
     if (lane == 0) {
         L.y0 = y0;
         L.sh = sh;
+        L.x0 = x0;
+        L.x1 = x1;
     }
     __syncwarp();
     L.cnt[2 * lane] = excl;
@@ -271,11 +279,12 @@ __device__ double warp_intersection_area_slabs(const int2* __restrict__ A, int n
     double acc = 0;
     const int ya0 = LA.y0, ya1 = LA.y0 + (kRefSlabs << LA.sh) - 1;
     const int yb0 = LB.y0, yb1 = LB.y0 + (kRefSlabs << LB.sh) - 1;
-    // end terms of A's edges: vertex a_i + e inside B closes edge i-1
+    // end terms of A's edges: vertex a_i + e inside B closes edge i-1 (a vertex strictly
+    // left or right of B's x-range sees an even number of B's crossings: outside)
     for (int i = wip == 0 ? lane : na; i < na; i += 32) {
         const int2 a = A[i];
         unsigned in = 0;
-        if (a.y >= yb0 && a.y <= yb1) {
+        if (a.y >= yb0 && a.y <= yb1 && a.x >= LB.x0 && a.x <= LB.x1) {
             const int q = (a.y - yb0) >> LB.sh;
             for (int k = LB.beg[q]; k < LB.beg[q + 1]; ++k) {
                 const int j = LB.ids[k];
@@ -296,7 +305,7 @@ __device__ double warp_intersection_area_slabs(const int2* __restrict__ A, int n
     for (int j = wip == 1 ? lane : nb; j < nb; j += 32) {
         const int2 c = B[j];
         unsigned in = 0;
-        if (c.y >= ya0 && c.y <= ya1) {
+        if (c.y >= ya0 && c.y <= ya1 && c.x >= LA.x0 && c.x <= LA.x1) {
             const int q = (c.y - ya0) >> LA.sh;
             for (int k = LA.beg[q]; k < LA.beg[q + 1]; ++k) {
                 const int i = LA.ids[k];
@@ -323,7 +332,9 @@ __device__ double warp_intersection_area_slabs(const int2* __restrict__ A, int n
             a = A[i];
             b = A[i + 1 == na ? 0 : i + 1];
             const int lo = min(a.y, b.y), hi = max(a.y, b.y);
-            if ((a.x != b.x || a.y != b.y) && hi >= yb0 && lo <= yb1) {
+            // (an edge outside B's x-range meets no B edge)
+            if ((a.x != b.x || a.y != b.y) && hi >= yb0 && lo <= yb1 && max(a.x, b.x) >= LB.x0 &&
+                min(a.x, b.x) <= LB.x1) {
                 q0 = (max(lo, yb0) - yb0) >> LB.sh;
                 const int q1 = (min(hi, yb1) - yb0) >> LB.sh;
                 k0 = LB.beg[q0];
