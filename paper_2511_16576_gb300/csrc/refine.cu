@@ -196,10 +196,11 @@ __device__ double warp_intersection_area(const int2* __restrict__ A, int na, int
 
 // y-slab lists of a ring v[0..n) (staged in shared memory or read from global
 // memory; edge e = v[e] -> v[e+1 mod n]): edge e is listed in every slab of
-// [y0 + s*2^sh, y0 + (s+1)*2^sh) that its closed y-range meets, 64 slabs (two per
-// lane).  Returns false (warp-uniform) if more than kRefSlabCap references would
-// be needed.
-constexpr int kRefSlabs = 64;
+// [y0 + s*2^sh, y0 + (s+1)*2^sh) that its closed y-range meets, 128 slabs (four
+// per lane).  Returns false (warp-uniform) if more than kRefSlabCap references
+// would be needed.
+constexpr int kRefSlabs = 128;
+constexpr int kSlabsPerLane = kRefSlabs / 32;
 constexpr int kRefSlabCap = 2048;
 struct RefSlabs {
     uint16_t ids[kRefSlabCap];
@@ -225,8 +226,8 @@ __device__ __forceinline__ bool build_ref_slabs(const int2* v, int n, RefSlabs& 
     x1 = __reduce_max_sync(0xffffffffu, x1);
     int sh = 0;
     while (((y1 - y0) >> sh) >= kRefSlabs) ++sh;
-    L.cnt[2 * lane] = 0;
-    L.cnt[2 * lane + 1] = 0;
+#pragma unroll
+    for (int u = 0; u < kSlabsPerLane; ++u) L.cnt[kSlabsPerLane * lane + u] = 0;
     __syncwarp();
     for (int e = lane; e < n; e += 32) {
         const int2 a = v[e], b = v[e + 1 == n ? 0 : e + 1];
@@ -234,8 +235,13 @@ __device__ __forceinline__ bool build_ref_slabs(const int2* v, int n, RefSlabs& 
         for (int q = s0; q <= s1; ++q) atomicAdd(&L.cnt[q], 1);
     }
     __syncwarp();
-    const int c0 = L.cnt[2 * lane], c1 = L.cnt[2 * lane + 1];
-    int incl = c0 + c1;
+    int c[kSlabsPerLane], mine = 0;
+#pragma unroll
+    for (int u = 0; u < kSlabsPerLane; ++u) {
+        c[u] = L.cnt[kSlabsPerLane * lane + u];
+        mine += c[u];
+    }
+    int incl = mine;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, incl, d);
@@ -243,9 +249,15 @@ __device__ __forceinline__ bool build_ref_slabs(const int2* v, int n, RefSlabs& 
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     if (total > kRefSlabCap) return false;
-    const int excl = incl - c0 - c1;
-    L.beg[2 * lane] = (uint16_t)excl;
-    L.beg[2 * lane + 1] = (uint16_t)(excl + c0);
+    const int excl = incl - mine;
+    {
+        int run = excl;
+#pragma unroll
+        for (int u = 0; u < kSlabsPerLane; ++u) {
+            L.beg[kSlabsPerLane * lane + u] = (uint16_t)run;
+            run += c[u];
+        }
+    }
     if (lane == 31) L.beg[kRefSlabs] = (uint16_t)total;
     if (lane == 0) {
         L.y0 = y0;
@@ -254,8 +266,14 @@ __device__ __forceinline__ bool build_ref_slabs(const int2* v, int n, RefSlabs& 
         L.x1 = x1;
     }
     __syncwarp();
-    L.cnt[2 * lane] = excl;
-    L.cnt[2 * lane + 1] = excl + c0;
+    {
+        int run = excl;
+#pragma unroll
+        for (int u = 0; u < kSlabsPerLane; ++u) {
+            L.cnt[kSlabsPerLane * lane + u] = run;
+            run += c[u];
+        }
+    }
     __syncwarp();
     for (int e = lane; e < n; e += 32) {
         const int2 a = v[e], b = v[e + 1 == n ? 0 : e + 1];
@@ -404,7 +422,7 @@ __device__ __forceinline__ PairView view(const int2* xy, const int64_t* off, con
 }
 
 constexpr int kRefineWarps = 4;  // two pairs per block, two warps per pair
-constexpr int kWarpVerts = 1024;  // vertices of a pair's staging slice
+constexpr int kWarpVerts = 960;   // vertices of a pair's staging slice
 
 // one pair's shared slice: the staged rings, a crossing queue per warp, both rings'
 // slab lists, and the two warps' partial sums
