@@ -117,11 +117,11 @@ __host__ __device__ __forceinline__ uint32_t pmh_indexed_limit(int4 bb, long lon
 // adjacent, so a warp reading one cell for sixteen hashes reads 128 bytes.
 constexpr int kRankLevels = 6;
 // Plan of the indexed form for a polygon (sign_unified.cu),
-// in estimated warp instructions per hash.  The limit is lim = 8 * 2^32 / area (a
-// hit below it is missed with probability ~e^-8; the walk then resumes at lim),
+// in estimated warp instructions per hash.  The limit is lim = 11 * 2^32 / area (a
+// hit below it is missed with probability ~e^-11; the walk then resumes at lim),
 // and at most ~24 box points below lim are expected.  The gather first reads the
-// points below lim1 = 2.5 * 2^32 / area (an inside point exists there with
-// probability ~1 - e^-2.5); only the hashes without one read on up to lim.  On a
+// points below lim1 = 3.5 * 2^32 / area (an inside point exists there with
+// probability ~1 - e^-3.5); only the hashes without one read on up to lim.  On a
 // grid level holding at least lim points it costs ~4.9 per cell record under the
 // box and ~2.5 per first-pass point read (those below the smallest rank level >=
 // lim1 in those cells), plus ~20 for the mask, exact tests and setup; the walk
@@ -131,7 +131,7 @@ constexpr int kRankLevels = 6;
 struct PmhIndexPlan {
     uint32_t lim;
     int level;      // grid level holding every point below lim (the second pass)
-    uint32_t lim1;  // bound of the first gather pass: ~2.5 expected first hits
+    uint32_t lim1;  // bound of the first gather pass: ~3.5 expected first hits
     int level1;     // grid level of the first pass (holding every point below lim1)
 };
 __host__ __device__ __forceinline__ float pmh_level_cost(int4 bb, uint32_t lim1, uint32_t M, int shift)
@@ -149,10 +149,10 @@ __host__ __device__ __forceinline__ PmhIndexPlan pmh_index_plan(int4 bb, long lo
     if (bb.z <= bb.x || bb.w <= bb.y) return plan;
     const float area = 0.5f * (float)(area2 < 0 ? -area2 : area2);
     const float walk = 4294967296.0f / fmaxf(area, 1.0f);
-    const float lim = fminf((float)kIndexMaxPoints, 8.0f * walk + 256.0f);
+    const float lim = fminf((float)kIndexMaxPoints, 11.0f * walk + 256.0f);
     const float cand = lim * ((float)(bb.z - bb.x) * (float)(bb.w - bb.y) * (1.0f / 4294967296.0f));
     if (cand > 24.0f) return plan;
-    const uint32_t L = (uint32_t)lim, L1 = (uint32_t)fminf(lim, 2.5f * walk + 64.0f);
+    const uint32_t L = (uint32_t)lim, L1 = (uint32_t)fminf(lim, 3.5f * walk + 64.0f);
     // the cheapest level holding every point below the bound: L for the second pass,
     // L1 for the first (on a coarser shallow level the first pass reads a few cells
     // where the deep level holding L would read many); the deep level (larger than

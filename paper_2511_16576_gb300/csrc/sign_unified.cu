@@ -317,7 +317,7 @@ __device__ __forceinline__ void indexed_range(UniWarp& m, const Src& src, const 
         if (lane < kSub) m.best[lane] = 0xFFFFFFFFu;
         if (lane == 0) m.ovf = 0;
         // two passes over the cells: first the points below level lev1 (about
-        // 2.5x the expected first hit: most hashes find their answer there),
+        // 3.5x the expected first hit: most hashes find their answer there),
         // then, for the hashes with no inside point yet, those up to level lev
         uint32_t open = kn == 32 ? 0xFFFFFFFFu : ((1u << kn) - 1u);
         for (int pass = 0; pass < 2 && lim > 0; ++pass) {
