@@ -390,11 +390,14 @@ def read_profile(path: str) -> dict:
     return out
 
 
-def profiled_counters(polys_in_launch: int) -> dict | None:
+def profiled_counters(polys_in_launch: int, workload: str) -> dict | None:
     """DRAM and L2 bytes and instructions per launch of the signing kernel, from the ncu
-    summary taken on this same kernel source (scaled by polygons to this launch), else None."""
+    summary taken on this same kernel source and workload (scaled by polygons to this
+    launch), else None."""
     p = read_profile(SIGN_PROFILE)
     if not p or p.get("source_sha") != sources_sha(SIGN_SOURCES):
+        return None
+    if not str(p.get("workload", "")).startswith(workload):
         return None
     try:
         scale = polys_in_launch / float(p["launch_polygons"])
@@ -695,14 +698,14 @@ def main():
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     units = kernels[dom]["work_units_per_launch"]
     gather_bytes = 8 * (units["cells"] + units["index_entries"])
-    prof = profiled_counters(N) if dom == "sign_unified_kernel" else None
+    prof = profiled_counters(N, w.name) if dom == "sign_unified_kernel" else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": kernels[dom]["achieved"],
                 "peak": peak / 1e12, "unit": "Tintop/s", "frac": kernels[dom]["frac"],
                 "traffic": prof["dram_bytes"] if prof else None,
                 "traffic_note": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel "
                                  f"source on {prof['captured_on']}, x {prof['scale']:.2f} by polygons "
                                  f"({SIGN_PROFILE})") if prof else
-                "no ncu summary of this kernel source: not measured",
+                "no ncu summary of this kernel source on this workload: not measured",
                 "op_weights": SIGN_OP_WEIGHTS,
                 "peak_source": "measured: pmh_probe_int_peak (integer mad/add/xor/shl mix, all SMs)",
                 "peak_nominal": nominal_int_peak(dev, clk),

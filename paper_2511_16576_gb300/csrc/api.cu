@@ -125,7 +125,7 @@ extern "C" int pmh_destroy(pmh_ctx ctx)
 // status[0] |= 1 bad offsets, 2 < 3 vertices, 4 coordinate out of range;
 // status[1] = max vertex count.
 // ---------------------------------------------------------------------------
-__global__ void prep_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
+__global__ void __launch_bounds__(256, 6) prep_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
                             int64_t n_polys, const int64_t* __restrict__ d_n, int64_t n_vertices,
                             int4* __restrict__ bbox, int64_t* __restrict__ area2,
                             int* __restrict__ status)

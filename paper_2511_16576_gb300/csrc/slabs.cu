@@ -38,6 +38,28 @@ __device__ __forceinline__ int slab_count_for(int n, int height)
 __device__ __forceinline__ uint64_t slab_div_magic(int h) { return (1ull << 40) / (uint64_t)h + 1ull; }
 __device__ __forceinline__ int slab_div(int x, uint64_t m) { return (int)(((uint64_t)x * m) >> 40); }
 
+// y of the two end points of edges e0 + 32u + lane (u < 4) of the ring of n vertices at
+// xy + b, four loads in flight per lane: an edge's end vertex is the next lane's start
+// vertex (a shuffle); lane 31 and the closing edge read theirs
+__device__ __forceinline__ void edge_ys(const int2* __restrict__ xy, int64_t b, int n, int e0, int lane,
+                                        int (&ay)[4], int (&by)[4])
+{
+    int own[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int e = e0 + 32 * u + lane;
+        const bool edge_end = e < n && (lane == 31 || e + 1 == n);
+        ay[u] = e < n ? xy[b + e].y : 0;
+        own[u] = edge_end ? xy[b + (e + 1 == n ? 0 : e + 1)].y : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int e = e0 + 32 * u + lane;
+        const int nx = __shfl_down_sync(0xffffffffu, ay[u], 1);
+        by[u] = (lane == 31 || e + 1 == n) ? own[u] : nx;
+    }
+}
+
 // pass 1: sizes of every polygon's slab table and edge list
 __global__ void slab_size_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
                                  int64_t n_polys, const int64_t* __restrict__ d_n, int min_verts,
@@ -82,11 +104,15 @@ __global__ void slab_size_kernel(const int2* __restrict__ xy, const int64_t* __r
         const int h = max((height + S - 1) / S, 1);
         const uint64_t hm = slab_div_magic(h);
         long long entries = 0;
-        for (int e = lane; e < n; e += 32) {
-            int ay = xy[b + e].y, by = xy[b + (e + 1 == n ? 0 : e + 1)].y;
-            if (ay == by) continue;
-            int lo = min(ay, by) - y0, hi = max(ay, by) - 1 - y0;
-            entries += slab_div(hi, hm) - slab_div(lo, hm) + 1;
+        for (int e0 = 0; e0 < n; e0 += 128) {
+            int ay[4], by[4];
+            edge_ys(xy, b, n, e0, lane, ay, by);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (e0 + 32 * u + lane >= n || ay[u] == by[u]) continue;
+                const int lo = min(ay[u], by[u]) - y0, hi = max(ay[u], by[u]) - 1 - y0;
+                entries += slab_div(hi, hm) - slab_div(lo, hm) + 1;
+            }
         }
         for (int o = 16; o > 0; o >>= 1) entries += __shfl_xor_sync(0xffffffffu, entries, o);
         if (lane == 0) {
@@ -101,8 +127,8 @@ __global__ void slab_size_kernel(const int2* __restrict__ xy, const int64_t* __r
 // counters of a polygon of at most kFillSmemSlabs slabs live in the warp's shared
 // slice, larger ones in the global cursor array
 constexpr int kFillThreads = 256;
-constexpr int kFillSmemSlabs = 1024;
-__global__ void __launch_bounds__(kFillThreads) slab_fill_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
+constexpr int kFillSmemSlabs = 512;
+__global__ void __launch_bounds__(kFillThreads, 8) slab_fill_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
                                  int64_t n_polys, const int64_t* __restrict__ d_n, int min_verts,
                                  SlabInfo* __restrict__ info, const int64_t* __restrict__ ptr_base,
                                  const int64_t* __restrict__ edge_base, int32_t* __restrict__ slab_ptr,
@@ -135,11 +161,16 @@ __global__ void __launch_bounds__(kFillThreads) slab_fill_kernel(const int2* __r
         int32_t* cur = S <= kFillSmemSlabs ? scur[threadIdx.x >> 5] : cursor + pb;
         for (int s = lane; s <= S; s += 32) cur[s] = 0;
         __syncwarp();
-        for (int e = lane; e < n; e += 32) {
-            int ay = xy[b + e].y, by = xy[b + (e + 1 == n ? 0 : e + 1)].y;
-            if (ay == by) continue;
-            int lo = slab_div(min(ay, by) - y0, hm), hi = slab_div(max(ay, by) - 1 - y0, hm);
-            for (int s = lo; s <= hi; ++s) atomicAdd(&cur[s], 1);
+        for (int e0 = 0; e0 < n; e0 += 128) {
+            int ay[4], by[4];
+            edge_ys(xy, b, n, e0, lane, ay, by);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (e0 + 32 * u + lane >= n || ay[u] == by[u]) continue;
+                const int lo = slab_div(min(ay[u], by[u]) - y0, hm);
+                const int hi = slab_div(max(ay[u], by[u]) - 1 - y0, hm);
+                for (int s = lo; s <= hi; ++s) atomicAdd(&cur[s], 1);
+            }
         }
         __syncwarp();
         __threadfence_block();
@@ -159,11 +190,17 @@ __global__ void __launch_bounds__(kFillThreads) slab_fill_kernel(const int2* __r
         __syncwarp();
         for (int s = lane; s <= S; s += 32) cur[s] = sp[s];
         __syncwarp();
-        for (int e = lane; e < n; e += 32) {
-            int ay = xy[b + e].y, by = xy[b + (e + 1 == n ? 0 : e + 1)].y;
-            if (ay == by) continue;
-            int lo = slab_div(min(ay, by) - y0, hm), hi = slab_div(max(ay, by) - 1 - y0, hm);
-            for (int s = lo; s <= hi; ++s) slab_edges[eb + atomicAdd(&cur[s], 1)] = e;
+        for (int e0 = 0; e0 < n; e0 += 128) {
+            int ay[4], by[4];
+            edge_ys(xy, b, n, e0, lane, ay, by);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + 32 * u + lane;
+                if (e >= n || ay[u] == by[u]) continue;
+                const int lo = slab_div(min(ay[u], by[u]) - y0, hm);
+                const int hi = slab_div(max(ay[u], by[u]) - 1 - y0, hm);
+                for (int s = lo; s <= hi; ++s) slab_edges[eb + atomicAdd(&cur[s], 1)] = e;
+            }
         }
         __syncwarp();
     }
