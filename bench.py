@@ -437,7 +437,7 @@ def search_quality(args, w, B, ctx, db, qs, h, dbp, q_xy, q_off, P):
     out = {"eval_queries": n_eval, "timed_queries": n_s, "batch": args.batch, "k": 10,
            "target_recall": 0.9, "bf_pairs_per_query": truth.pairs / n_eval,
            "bf_seconds_eval_queries": t_bf, "forms": {}}
-    ms = (10, 12, 14, 16, 18, 20, 22, 24, 28, 32)   # refined to the top-10: m >= 10
+    ms = tuple(range(10, 25)) + (28, 32)   # refined to the top-10: m >= 10; every m to 24
     shapes = [b for b in (w.K // 2, w.K // 4, w.bands) if b >= 1 and w.K % b == 0]
     for bands in dict.fromkeys(shapes):
         params = B.make_params(w.K, bands, w.T, w.seed, w.lsh_seed, P.flags)

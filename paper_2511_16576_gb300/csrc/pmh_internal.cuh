@@ -119,7 +119,8 @@ constexpr int kRankLevels = 6;
 // Plan of the indexed form for a polygon (sign_unified.cu),
 // in estimated warp instructions per hash.  The limit is lim = 11 * 2^32 / area (a
 // hit below it is missed with probability ~e^-11; the walk then resumes at lim),
-// and at most ~24 box points below lim are expected.  The gather first reads the
+// capped at the shallow levels' 65,536 points where 8 * 2^32 / area fits there, and
+// at most ~24 box points below 8 * 2^32 / area are expected.  The gather first reads the
 // points below lim1 = 3.5 * 2^32 / area (an inside point exists there with
 // probability ~1 - e^-3.5); only the hashes without one read on up to lim.  On a
 // grid level holding at least lim points it costs ~4.9 per cell record under the
@@ -149,9 +150,13 @@ __host__ __device__ __forceinline__ PmhIndexPlan pmh_index_plan(int4 bb, long lo
     if (bb.z <= bb.x || bb.w <= bb.y) return plan;
     const float area = 0.5f * (float)(area2 < 0 ? -area2 : area2);
     const float walk = 4294967296.0f / fmaxf(area, 1.0f);
-    const float lim = fminf((float)kIndexMaxPoints, 11.0f * walk + 256.0f);
-    const float cand = lim * ((float)(bb.z - bb.x) * (float)(bb.w - bb.y) * (1.0f / 4294967296.0f));
-    if (cand > 24.0f) return plan;
+    // a polygon is indexed when ~24 box points lie below 8 expected first hits; its limit
+    // is 11 of them, but not past the shallow levels' 65,536 points when 8 fit there
+    const float lim8 = 8.0f * walk + 256.0f;
+    float lim = fminf((float)kIndexMaxPoints, 11.0f * walk + 256.0f);
+    if (lim8 <= (float)kStreamIndexPoints) lim = fminf(lim, (float)kStreamIndexPoints);
+    const float box = (float)(bb.z - bb.x) * (float)(bb.w - bb.y) * (1.0f / 4294967296.0f);
+    if (fminf((float)kIndexMaxPoints, lim8) * box > 24.0f) return plan;
     const uint32_t L = (uint32_t)lim, L1 = (uint32_t)fminf(lim, 3.5f * walk + 64.0f);
     // the cheapest level holding every point below the bound: L for the second pass,
     // L1 for the first (on a coarser shallow level the first pass reads a few cells
