@@ -206,7 +206,7 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_
                                     g->cap_edges, cs);
     if (rc == PMH_OK)
         rc = pmh_launch_sign_unified(ctx, U, g->xy, g->off, g->bbox, g->area2, g->slab_info, g->slab_ptr,
-                                     g->slab_edges, nullptr, Q, Q, g->d_n, g->flags, &g->P, sidx,
+                                     g->slab_edges, nullptr, Q, Q, 0, g->d_n, g->flags, &g->P, sidx,
                                      g->ticket, g->hashes, nullptr, cs);
     if (rc == PMH_OK)
         rc = pmh_launch_query(index, g->hashes, Q, g->d_n, g->counts, nullptr, nullptr, 0, g->join_stage,

@@ -355,14 +355,16 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
 // 32-hash chunk) items, the rest whole; d_n (optional) caps n_slots on the
 // device, d_flags (optional) skips a batch that failed validation; U = points
 // per lane per round of the walk form (2, 4 or 8); work (optional) the six
-// work counters
+// work counters.  The last n_indexed_tail slots of a class list (staged polygons
+// of the indexed form, the class order's last class) get a launch of their own
+// through a build of the kernel without the other paths.
 int pmh_launch_sign_unified(pmh_ctx ctx, int U, const int2* xy, const int64_t* off,
                             const int4* bbox, const int64_t* area2, const SlabInfo* slabs,
                             const int32_t* slab_ptr, const int32_t* slab_edges, const int32_t* list,
-                            int64_t n_slots, int64_t n_chunked, const int64_t* d_n,
-                            const int* d_flags, const pmh_params* P, const StreamIndexView& S,
-                            unsigned long long* ticket, uint32_t* out, unsigned long long* work,
-                            cudaStream_t s);
+                            int64_t n_slots, int64_t n_chunked, int64_t n_indexed_tail,
+                            const int64_t* d_n, const int* d_flags, const pmh_params* P,
+                            const StreamIndexView& S, unsigned long long* ticket, uint32_t* out,
+                            unsigned long long* work, cudaStream_t s);
 // bucket join (lsh.cu): the count pass (write false: counts) or the fill pass (write
 // true: the CSR rows); `stage` (nullable, pmh_join_stage_ints(X, Q) ints) lets the
 // count pass keep the short rows it sorted, so that the fill pass copies them

@@ -330,8 +330,8 @@ int pmh_launch_sign(pmh_ctx ctx, const int2* xy, const int64_t* off, const int4*
         const int U = kSignVariants[ctx->sign_variant >= 0 ? ctx->sign_variant : 0].U;
         const int64_t n_big = n_polys - n_indexed - n_whole_cost;
         PMH_TRY(pmh_launch_sign_unified(ctx, U, xy, off, bbox, area2, slabs, slab_ptr, slab_edges,
-                                        order_cls, n_polys, n_big, nullptr, nullptr, P, S, ticket + 2,
-                                        out, work ? ctx->d_tickets + kIdxWorkSlot : nullptr, s));
+                                        order_cls, n_polys, n_big, n_indexed, nullptr, nullptr, P, S,
+                                        ticket + 2, out, work ? ctx->d_tickets + kIdxWorkSlot : nullptr, s));
         if (timed) {
             PMH_CUDA_TRY(cudaEventRecord(ev[1], s));
             PMH_CUDA_TRY(cudaEventRecord(ev[2], s));

@@ -519,7 +519,11 @@ __device__ __noinline__ void sign_global(UniWarp& m, GlobalSrc src, int n, int4 
     gc->masked += g.masked;
 }
 
-template <int U, bool kCount>
+// kIndexedOnly: a launch over staged polygons of the indexed form only (the class
+// order's last class), compiled without the walk-form and large-polygon paths, so that
+// the gather keeps its values in registers (a fraction of the unified build's spills
+// and no call frames)
+template <int U, bool kCount, bool kIndexedOnly>
 __global__ void __launch_bounds__(kUniWarps * 32, kUniMinBlocks)
 sign_unified_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off,
                     const int4* __restrict__ bbox, const int64_t* __restrict__ area2,
@@ -583,11 +587,11 @@ sign_unified_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
             const StagedSrc src{m.v, m.ids, m.beg, bb.y, sh};
             build_mask(m, src, n, bb, mask32_log2(bb.z - bb.x), mask32_log2(bb.w - bb.y), true, lane,
                        work);
-            if (plan.lim > 0)
+            if (kIndexedOnly || plan.lim > 0)
                 indexed_range(m, src, S, plan, bb, seed, T, k_begin, k_end, row, lane, work, gc);
             else
                 walk_staged<U, W>(m, src, bb, seed, T, k_begin, k_end, row, lane, &work);
-        } else {
+        } else if (!kIndexedOnly) {
             const SlabInfo si = slabs ? slabs[p] : SlabInfo{0, 0, 0, 1, 0};
             const GlobalSrc src{xy + b, n, si.S > 0 ? slab_ptr + si.slab_base : nullptr,
                                 si.S > 0 ? slab_edges + si.edge_base : nullptr, si.slab_h, si.ymin};
@@ -623,19 +627,23 @@ sign_unified_kernel(const int2* __restrict__ xy, const int64_t* __restrict__ off
 
 }  // namespace
 
-int pmh_launch_sign_unified(pmh_ctx ctx, int U, const int2* xy, const int64_t* off,
-                            const int4* bbox, const int64_t* area2, const SlabInfo* slabs,
-                            const int32_t* slab_ptr, const int32_t* slab_edges, const int32_t* list,
-                            int64_t n_slots, int64_t n_chunked, const int64_t* d_n,
-                            const int* d_flags, const pmh_params* P, const StreamIndexView& S,
-                            unsigned long long* ticket, uint32_t* out, unsigned long long* work,
-                            cudaStream_t s)
+// one persistent launch over `n` slots of `list` (or slot order) with its own ticket
+template <bool kIndexedOnly>
+static int launch_unified(pmh_ctx ctx, int U, const int2* xy, const int64_t* off, const int4* bbox,
+                          const int64_t* area2, const SlabInfo* slabs, const int32_t* slab_ptr,
+                          const int32_t* slab_edges, const int32_t* list, int64_t n_slots,
+                          int64_t n_chunked, const int64_t* d_n, const int* d_flags, const pmh_params* P,
+                          const StreamIndexView& S, unsigned long long* ticket, uint32_t* out,
+                          unsigned long long* work, cudaStream_t s)
 {
-    if (n_slots <= 0) return PMH_OK;
-    auto fn = work ? (U <= 2 ? sign_unified_kernel<2, true> : U <= 4 ? sign_unified_kernel<4, true>
-                                                             : sign_unified_kernel<8, true>)
-                   : (U <= 2 ? sign_unified_kernel<2, false> : U <= 4 ? sign_unified_kernel<4, false>
-                                                               : sign_unified_kernel<8, false>);
+    auto fn = kIndexedOnly
+                  ? (work ? sign_unified_kernel<2, true, true> : sign_unified_kernel<2, false, true>)
+                  : work ? (U <= 2   ? sign_unified_kernel<2, true, false>
+                            : U <= 4 ? sign_unified_kernel<4, true, false>
+                                     : sign_unified_kernel<8, true, false>)
+                         : (U <= 2   ? sign_unified_kernel<2, false, false>
+                            : U <= 4 ? sign_unified_kernel<4, false, false>
+                                     : sign_unified_kernel<8, false, false>);
     int per_sm = 0;
     PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kUniWarps * 32, 0));
     const int chunks = (int)((P->K + 31) / 32);
@@ -646,6 +654,27 @@ int pmh_launch_sign_unified(pmh_ctx ctx, int U, const int2* xy, const int64_t* o
     fn<<<(int)blocks, kUniWarps * 32, 0, s>>>(xy, off, bbox, area2, slabs, slab_ptr, slab_edges, list,
                                               n_slots, n_chunked, d_n, d_flags, P->seed, (int)P->K,
                                               P->T, S, ticket, out, work);
-    PMH_LAUNCHED("sign_unified_kernel");
+    PMH_LAUNCHED(kIndexedOnly ? "sign_unified_kernel<indexed>" : "sign_unified_kernel");
+    return PMH_OK;
+}
+
+int pmh_launch_sign_unified(pmh_ctx ctx, int U, const int2* xy, const int64_t* off,
+                            const int4* bbox, const int64_t* area2, const SlabInfo* slabs,
+                            const int32_t* slab_ptr, const int32_t* slab_edges, const int32_t* list,
+                            int64_t n_slots, int64_t n_chunked, int64_t n_indexed_tail,
+                            const int64_t* d_n, const int* d_flags, const pmh_params* P,
+                            const StreamIndexView& S, unsigned long long* ticket, uint32_t* out,
+                            unsigned long long* work, cudaStream_t s)
+{
+    if (n_slots <= 0) return PMH_OK;
+    // the indexed class at the list's end goes to its own launch (needs the class list)
+    const int64_t tail = list && !d_n ? std::min(std::max<int64_t>(n_indexed_tail, 0), n_slots - n_chunked) : 0;
+    if (n_slots - tail > 0)
+        PMH_TRY(launch_unified<false>(ctx, U, xy, off, bbox, area2, slabs, slab_ptr, slab_edges, list,
+                                      n_slots - tail, n_chunked, d_n, d_flags, P, S, ticket, out, work, s));
+    if (tail > 0)
+        PMH_TRY(launch_unified<true>(ctx, U, xy, off, bbox, area2, slabs, slab_ptr, slab_edges,
+                                     list + (n_slots - tail), tail, 0, nullptr, d_flags, P, S, ticket, out,
+                                     work, s));
     return PMH_OK;
 }
