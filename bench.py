@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--refine-k", type=int, default=10,
                     help="exact top-k of the refinement (0: the query graph stops at the top-m)")
     ap.add_argument("--shortlist", type=int, default=64, help="learned form: count shortlist")
+    ap.add_argument("--search-shortlist", type=int, default=32,
+                    help="learned form in the recall / queries-per-s sweep: count shortlist")
     ap.add_argument("--plain", action="store_true", help="time the plain form (no reranker)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -450,12 +452,12 @@ def search_quality(args, w, B, ctx, db, qs, h, dbp, q_xy, q_off, P):
             index.close()
             continue
         plain = ev.graph_sweep(ctx, index, dbp, batches, cap, truth, n_eval, ms)
-        s = ev.Searcher(ctx, index, params, dbp, h, shortlist=args.shortlist)
+        s = ev.Searcher(ctx, index, params, dbp, h, shortlist=args.search_shortlist)
         feat, lab = ev.training_pairs(ctx, s, tp)
         rr = B.Reranker(ctx, seed=1)
         (losses, t_train) = ev.timed(lambda: ev.train_reranker(rr, feat, lab, epochs=16))
         learned = ev.graph_sweep(ctx, index, dbp, batches, cap, truth, n_eval, ms, rerank=rr,
-                                 shortlist=args.shortlist)
+                                 shortlist=args.search_shortlist)
         rr.close()
         out["forms"][key] = {"bands": key, "candidates_per_query_cap": cap / args.batch,
                              "plain_curve": plain, "plain": ev.best_at_recall(plain),
