@@ -89,8 +89,8 @@ def parse():
                     help="queries whose graph replays time the search's queries/s")
     ap.add_argument("--search-max-candidates", type=float, default=5000.0,
                     help="skip a band shape with more bucket candidates per query than this")
-    ap.add_argument("--train-queries", type=int, default=16000,
-                    help="training queries of the reranker (x shortlist pairs)")
+    ap.add_argument("--train-queries", type=int, default=24000,
+                    help="training queries of the search's reranker (x --shortlist pairs: ~1M)")
     ap.add_argument("--paper-sweep", action="store_true",
                     help="paper-shaped centred sets, one hashmap keyed on m = 1..5 hashes (prints one "
                          "JSON line with the table instead of the benchmark line)")
@@ -452,7 +452,9 @@ def search_quality(args, w, B, ctx, db, qs, h, dbp, q_xy, q_off, P):
             index.close()
             continue
         plain = ev.graph_sweep(ctx, index, dbp, batches, cap, truth, n_eval, ms)
-        s = ev.Searcher(ctx, index, params, dbp, h, shortlist=args.search_shortlist)
+        # trained on the wider count shortlist (more pairs per training query), used on the
+        # search's own
+        s = ev.Searcher(ctx, index, params, dbp, h, shortlist=max(args.shortlist, args.search_shortlist))
         feat, lab = ev.training_pairs(ctx, s, tp)
         rr = B.Reranker(ctx, seed=1)
         (losses, t_train) = ev.timed(lambda: ev.train_reranker(rr, feat, lab, epochs=16))

@@ -23,23 +23,29 @@ namespace {
 constexpr int kMaxK = 4096;
 constexpr int kAgreeWarps = 4;
 constexpr int kAgreeChunk = 16;  // consecutive pairs per warp turn
+constexpr int kAgreeGroup = 4;   // pairs compared at a time (their loads in flight together)
 
 // Warps take chunks of kAgreeChunk consecutive pairs (the row of the first by
-// binary search over row_ptr, then stepping on).  Per pair: equality bits of the
-// K hashes (16-byte loads when K % 4 == 0), the count (warp sum), the full-match
-// bits of the first 32 bands and, optionally, the reranker's feature row.
-__global__ void __launch_bounds__(kAgreeWarps * 32)
+// binary search over row_ptr, then stepping on), four pairs at a time.  Per pair:
+// equality bits of the K hashes (16-byte loads when K % 4 == 0), the count (warp
+// sum), the full-match bits of the first 32 bands and, optionally, the reranker's
+// feature row.
+__global__ void __launch_bounds__(kAgreeWarps * 32, 6)
 agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ ph,
                   const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cand, int64_t Q,
                   int64_t cap, int K, int bands, int rows, uint32_t T, uint16_t* __restrict__ count,
                   uint32_t* __restrict__ bandmask, __nv_bfloat16* __restrict__ feat, FeatSrc qf,
                   FeatSrc pf, const int* __restrict__ d_flags)
 {
-    __shared__ uint32_t eqbits[kAgreeWarps][kMaxK / 32];
+    __shared__ uint32_t eqbits[kAgreeWarps][kAgreeGroup][kMaxK / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (d_flags && *d_flags) return;  // failed validation or candidate overflow
     const int64_t total = min(row_ptr[Q], cap);
     const int64_t nwarps = (int64_t)gridDim.x * kAgreeWarps;
+    const int K4 = K / 4;
+    // equality words in shared memory: for the band bits, and for the features' groups
+    // unless K = 128 (then lane l holds group l's four hashes)
+    const bool need_eq = bandmask || (feat && K != 128);
     for (int64_t ch = (int64_t)blockIdx.x * kAgreeWarps + wid; ch * kAgreeChunk < total; ch += nwarps) {
         const int64_t x0 = ch * kAgreeChunk, x1 = min(x0 + kAgreeChunk, total);
         // the row holding pair x0: the last q with row_ptr[q] <= x0
@@ -50,99 +56,118 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
             else hi = mid;
         }
         int64_t q = lo;
-        for (int64_t x = x0; x < x1; ++x) {
-            while (row_ptr[q + 1] <= x) ++q;
-            const uint32_t* qs = qh + q * K;
-            const int64_t p = cand[x];
-            const uint32_t* bp = ph + p * K;
-            int c = 0, lt = 0, gt = 0;  // lt / gt: hashes with h(q) < h(p) / h(q) > h(p)
+        for (int64_t x = x0; x < x1; x += kAgreeGroup) {
+            int64_t qq[kAgreeGroup], pp[kAgreeGroup];
+            bool ok[kAgreeGroup];
+#pragma unroll
+            for (int t = 0; t < kAgreeGroup; ++t) {
+                ok[t] = x + t < x1;
+                if (ok[t])
+                    while (row_ptr[q + 1] <= x + t) ++q;
+                qq[t] = q;
+                pp[t] = ok[t] ? cand[x + t] : 0;
+            }
+            // lt / gt: hashes with h(q) < h(p) / h(q) > h(p); grp: K = 128, lane l's four
+            // hashes (group l of the features' 32-group split) all equal
+            int c[kAgreeGroup] = {0, 0, 0, 0}, lt[kAgreeGroup] = {0, 0, 0, 0}, gt[kAgreeGroup] = {0, 0, 0, 0};
+            bool grp[kAgreeGroup] = {false, false, false, false};
             if ((K & 3) == 0) {
-                const uint4* a4 = reinterpret_cast<const uint4*>(qs);
-                const uint4* b4 = reinterpret_cast<const uint4*>(bp);
-                for (int base = 0; base < K / 4; base += 32) {
+                for (int base = 0; base < K4; base += 32) {
                     const int i = base + lane;
-                    unsigned bits = 0;
-                    if (i < K / 4) {
-                        const uint4 u = __ldg(a4 + i), v = __ldg(b4 + i);
-                        bits = (unsigned)((u.x == v.x) & (u.x != T)) |
-                               ((unsigned)((u.y == v.y) & (u.y != T)) << 1) |
-                               ((unsigned)((u.z == v.z) & (u.z != T)) << 2) |
-                               ((unsigned)((u.w == v.w) & (u.w != T)) << 3);
-                        if (feat) {
-                            lt += (u.x < v.x) + (u.y < v.y) + (u.z < v.z) + (u.w < v.w);
-                            gt += (u.x > v.x) + (u.y > v.y) + (u.z > v.z) + (u.w > v.w);
+                    uint4 u[kAgreeGroup], v[kAgreeGroup];
+#pragma unroll
+                    for (int t = 0; t < kAgreeGroup; ++t) {
+                        u[t] = v[t] = make_uint4(0u, 0u, 0u, 0u);
+                        if (ok[t] && i < K4) {
+                            u[t] = __ldg(reinterpret_cast<const uint4*>(qh + qq[t] * K) + i);
+                            v[t] = __ldg(reinterpret_cast<const uint4*>(ph + pp[t] * K) + i);
                         }
                     }
-                    c += __popc(bits);
-                    // hash 4i+t is bit (4i+t) % 32 of word i / 8: OR eight lanes' nibbles
-                    unsigned w0 = bits << ((lane & 7) * 4);
-                    w0 |= __shfl_xor_sync(0xffffffffu, w0, 1);
-                    w0 |= __shfl_xor_sync(0xffffffffu, w0, 2);
-                    w0 |= __shfl_xor_sync(0xffffffffu, w0, 4);
-                    if ((lane & 7) == 0 && i < K / 4) eqbits[wid][i >> 3] = w0;
+#pragma unroll
+                    for (int t = 0; t < kAgreeGroup; ++t) {
+                        unsigned bits = 0;
+                        if (i < K4) {
+                            bits = (unsigned)((u[t].x == v[t].x) & (u[t].x != T)) |
+                                   ((unsigned)((u[t].y == v[t].y) & (u[t].y != T)) << 1) |
+                                   ((unsigned)((u[t].z == v[t].z) & (u[t].z != T)) << 2) |
+                                   ((unsigned)((u[t].w == v[t].w) & (u[t].w != T)) << 3);
+                            if (feat) {
+                                lt[t] += (u[t].x < v[t].x) + (u[t].y < v[t].y) + (u[t].z < v[t].z) +
+                                         (u[t].w < v[t].w);
+                                gt[t] += (u[t].x > v[t].x) + (u[t].y > v[t].y) + (u[t].z > v[t].z) +
+                                         (u[t].w > v[t].w);
+                            }
+                        }
+                        c[t] += __popc(bits);
+                        grp[t] = bits == 0xFu;
+                        if (need_eq) {
+                            // hash 4i+e is bit (4i+e) % 32 of word i / 8: OR eight lanes' nibbles
+                            unsigned w0 = bits << ((lane & 7) * 4);
+                            w0 |= __shfl_xor_sync(0xffffffffu, w0, 1);
+                            w0 |= __shfl_xor_sync(0xffffffffu, w0, 2);
+                            w0 |= __shfl_xor_sync(0xffffffffu, w0, 4);
+                            if ((lane & 7) == 0 && i < K4) eqbits[wid][t][i >> 3] = w0;
+                        }
+                    }
                 }
             } else {
                 for (int base = 0; base < K; base += 32) {
                     const int i = base + lane;
-                    const bool eq = i < K && qs[i] == bp[i] && qs[i] != T;
-                    const unsigned bal = __ballot_sync(0xffffffffu, eq);
-                    c += eq;
-                    if (feat && i < K) {
-                        lt += qs[i] < bp[i];
-                        gt += qs[i] > bp[i];
+#pragma unroll
+                    for (int t = 0; t < kAgreeGroup; ++t) {
+                        const bool in = ok[t] && i < K;
+                        const uint32_t a = in ? qh[qq[t] * K + i] : 0u, b = in ? ph[pp[t] * K + i] : 0u;
+                        const bool eq = in && a == b && a != T;
+                        const unsigned bal = __ballot_sync(0xffffffffu, eq);
+                        c[t] += eq;
+                        if (feat && in) {
+                            lt[t] += a < b;
+                            gt[t] += a > b;
+                        }
+                        if (lane == 0) eqbits[wid][t][base / 32] = bal;
                     }
-                    if (lane == 0) eqbits[wid][base / 32] = bal;
                 }
             }
             __syncwarp();
-            c = __reduce_add_sync(0xffffffffu, c);
-            if (feat) {
-                lt = __reduce_add_sync(0xffffffffu, lt);
-                gt = __reduce_add_sync(0xffffffffu, gt);
-            }
-            if (count && lane == 0) count[x] = (uint16_t)c;
-            if (bandmask) {
-                bool all = lane < bands;
-                for (int t = 0; t < rows && all; ++t) {
-                    const int k = lane * rows + t;
-                    all = (eqbits[wid][k >> 5] >> (k & 31)) & 1u;
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, all);
-                if (lane == 0) bandmask[x] = m;
-            }
-            if (feat) {
-                // group j = hashes j*g .. j*g+g-1 (g = K / 32) all equal
-                const int g = K / 32;
-                bool all = true;
-                for (int t = 0; t < g && all; ++t) {
-                    const int k = lane * g + t;
-                    all = (eqbits[wid][k >> 5] >> (k & 31)) & 1u;
-                }
-                __nv_bfloat16* f = feat + x * 48;
-                f[lane] = __float2bfloat16_rn(all ? 1.f : 0.f);
-                if (lane < 16) {
-                    float v = 0.f;
-                    if (lane == 0) v = (float)c / (float)K;
-                    if (lane == 1) v = qf.feat[q].x;
-                    if (lane == 2) v = pf.feat[p].x;
-                    if (lane == 3) v = qf.feat[q].y;
-                    if (lane == 4) v = pf.feat[p].y;
-                    if (lane == 5) v = (float)lt / (float)K;
-                    if (lane == 6) v = (float)gt / (float)K;
-                    if (lane == 7) {
-                        // upper bound of J: the intersection is at most min(|q|, |p|, overlap of
-                        // the two bounding boxes)
-                        const int4 qb = qf.bbox[q], pb = pf.bbox[p];
-                        const float ow = (float)max(0, min(qb.z, pb.z) - max(qb.x, pb.x));
-                        const float oh = (float)max(0, min(qb.w, pb.w) - max(qb.y, pb.y));
-                        const long long qa = qf.area2[q], pa = pf.area2[p];
-                        const float a = 0.5f * (float)(qa < 0 ? -qa : qa);
-                        const float bq = 0.5f * (float)(pa < 0 ? -pa : pa);
-                        const float mn = fminf(fminf(a, bq), ow * oh);
-                        const float den = a + bq - mn;
-                        v = den > 0.f ? mn / den : 0.f;
+#pragma unroll
+            for (int t = 0; t < kAgreeGroup; ++t) {
+                if (!ok[t]) continue;  // warp-uniform
+                const int64_t xt = x + t;
+                int ct, ltt = 0, gtt = 0;
+                if (feat && K < 1024) {  // the three counts in one sum (10 bits each)
+                    const int sum = __reduce_add_sync(0xffffffffu, c[t] | (lt[t] << 10) | (gt[t] << 20));
+                    ct = sum & 1023;
+                    ltt = (sum >> 10) & 1023;
+                    gtt = sum >> 20;
+                } else {
+                    ct = __reduce_add_sync(0xffffffffu, c[t]);
+                    if (feat) {
+                        ltt = __reduce_add_sync(0xffffffffu, lt[t]);
+                        gtt = __reduce_add_sync(0xffffffffu, gt[t]);
                     }
-                    f[32 + lane] = __float2bfloat16_rn(v);
+                }
+                if (count && lane == 0) count[xt] = (uint16_t)ct;
+                if (bandmask) {
+                    bool all = lane < bands;
+                    for (int r = 0; r < rows && all; ++r) {
+                        const int k = lane * rows + r;
+                        all = (eqbits[wid][t][k >> 5] >> (k & 31)) & 1u;
+                    }
+                    const unsigned mb = __ballot_sync(0xffffffffu, all);
+                    if (lane == 0) bandmask[xt] = mb;
+                }
+                if (feat) {
+                    float flo, fhi;
+                    if (K == 128) {
+                        flo = grp[t] ? 1.f : 0.f;
+                        fhi = pmh_feature_col(lane, K, ct, ltt, gtt, pmh_feat_pair(qf, pf, qq[t], pp[t]));
+                    } else {
+                        pmh_feature_values(eqbits[wid][t], K, ct, ltt, gtt, pmh_feat_pair(qf, pf, qq[t], pp[t]),
+                                           lane, flo, fhi);
+                    }
+                    __nv_bfloat16* f = feat + xt * 48;
+                    f[lane] = __float2bfloat16_rn(flo);
+                    if (lane < 16) f[32 + lane] = __float2bfloat16_rn(fhi);
                 }
             }
             __syncwarp();
@@ -180,19 +205,82 @@ __device__ void bitonic_sort_u64(uint64_t* s, int n /* power of two */)
     }
 }
 
-// one block per query; running top-m kept in s[0..m), new chunk appended
+// one block per query.  Count form: a histogram of the row's counts (0..K) gives
+// the largest threshold c* with at least m pairs of count >= c*; every key of
+// those pairs is gathered and sorted, and the first m kept -- the m best keys
+// (count desc, id asc) all have count >= c*, so the list is the full sort's.  A
+// row whose gathered set would pass kSelMax (a long tie at c*), and the score
+// form, take the merge form: the running top-m kept in s[0..m), each new chunk
+// of the row appended and sorted with it.
+constexpr int kSelMax = 2048;
+
 __global__ void __launch_bounds__(kTopThreads)
 topm_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cand,
             const uint16_t* __restrict__ count, const float* __restrict__ score, int K, int m,
-            int cap /* power of two >= m + kTopChunk */, int32_t* __restrict__ out_ids,
+            int cap /* power of two >= max(m + kTopChunk, kSelMax) */, int32_t* __restrict__ out_ids,
             int32_t* __restrict__ out_n, const int* __restrict__ d_flags)
 {
-    extern __shared__ uint64_t s[];
+    extern __shared__ uint64_t s[];  // cap keys, then (count form) K + 1 histogram bins
+    __shared__ int sel_c, sel_total, sel_n;
     const int64_t q = blockIdx.x;
     const bool failed = d_flags && *d_flags;
     const int64_t b = failed ? 0 : row_ptr[q], e = failed ? 0 : row_ptr[q + 1];
     int kept = 0;
-    for (int64_t base = b; base < e; base += kTopChunk) {
+    bool merged = true;
+    if (!score && e - b > m) {
+        int* hist = reinterpret_cast<int*>(s + cap);
+        for (int i = threadIdx.x; i <= K; i += blockDim.x) hist[i] = 0;
+        if (threadIdx.x == 0) {  // (the warp below always finds the threshold)
+            sel_c = 0;
+            sel_total = (int)min(e - b, (int64_t)INT32_MAX);
+            sel_n = 0;
+        }
+        __syncthreads();
+        for (int64_t x = b + threadIdx.x; x < e; x += blockDim.x) atomicAdd(&hist[min((int)count[x], K)], 1);
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // lane l sums bins [l*seg, (l+1)*seg); suffix sums over the lanes find the
+            // lane holding c*, which then walks its bins downwards
+            const int lane = threadIdx.x, seg = (K + 32) / 32;
+            const int lo = lane * seg, hi = min(lo + seg, K + 1);
+            int mine = 0;
+            for (int c = lo; c < hi; ++c) mine += hist[c];
+            int suf = mine;  // bins >= lo
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_down_sync(0xffffffffu, suf, o);
+                if (lane + o < 32) suf += y;
+            }
+            const int above = suf - mine;  // bins >= hi
+            if (above < m && suf >= m) {
+                int acc = above, c = hi - 1;
+                for (; c >= lo; --c) {
+                    acc += hist[c];
+                    if (acc >= m) break;
+                }
+                sel_c = c;
+                sel_total = acc;
+            }
+        }
+        __syncthreads();
+        const int cstar = sel_c, total = sel_total;
+        if (total <= kSelMax) {
+            merged = false;
+            for (int64_t x = b + threadIdx.x; x < e; x += blockDim.x) {
+                const int c = min((int)count[x], K);
+                if (c >= cstar) {
+                    const int pos = atomicAdd(&sel_n, 1);
+                    if (pos < total) s[pos] = ((uint64_t)(uint32_t)(K - c) << 32) | (uint32_t)cand[x];
+                }
+            }
+            int sz = 2;
+            while (sz < total) sz <<= 1;
+            for (int i = total + threadIdx.x; i < sz; i += blockDim.x) s[i] = ~0ull;
+            __syncthreads();
+            bitonic_sort_u64(s, sz);
+            kept = m;
+        }
+    }
+    for (int64_t base = b; merged && base < e; base += kTopChunk) {
         int take = (int)(e - base < kTopChunk ? e - base : kTopChunk);
         // sort only the occupied prefix, rounded up to a power of two (most lists are short)
         int sz = 2;
@@ -201,7 +289,7 @@ topm_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ can
             uint64_t key = ~0ull;
             if (i >= kept && i < kept + take) {
                 int64_t idx = base + (i - kept);
-                uint32_t hi = score ? ~f2ord(score[idx]) : (uint32_t)(K - (int)count[idx]);
+                uint32_t hi = score ? ~f2ord(score[idx]) : (uint32_t)(K - min((int)count[idx], K));
                 key = ((uint64_t)hi << 32) | (uint32_t)cand[idx];
             } else if (i < kept) {
                 key = s[i];
@@ -297,16 +385,17 @@ int pmh_launch_agree_features(pmh_ctx ctx, const uint32_t* qh, const uint32_t* p
 }
 
 int pmh_launch_topm(const int64_t* row_ptr, const int32_t* cand, const uint16_t* count,
-                    const float* score, int64_t Q, int32_t m, int32_t* out_ids, int32_t* out_n,
+                    const float* score, int64_t Q, int32_t m, int K, int32_t* out_ids, int32_t* out_n,
                     const int* d_flags, cudaStream_t s)
 {
     if (Q <= 0) return PMH_OK;
     int cap = 1;
-    while (cap < m + kTopChunk) cap <<= 1;
-    size_t smem = sizeof(uint64_t) * cap;
+    while (cap < m + kTopChunk || cap < kSelMax) cap <<= 1;
+    const int kb = (K > 0 && K <= kMaxK) ? K : kMaxK;  // counts are <= K
+    const size_t smem = sizeof(uint64_t) * cap + sizeof(int) * (size_t)(kb + 1);
     PMH_CUDA_TRY(cudaFuncSetAttribute(topm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-    topm_kernel<<<(unsigned)Q, kTopThreads, smem, s>>>(row_ptr, cand, count, score, 4096, m, cap,
+    topm_kernel<<<(unsigned)Q, kTopThreads, smem, s>>>(row_ptr, cand, count, score, kb, m, cap,
                                                        out_ids, out_n, d_flags);
     PMH_LAUNCHED("topm_kernel");
     return PMH_OK;
@@ -334,6 +423,6 @@ extern "C" int pmh_topm(pmh_ctx ctx, const int64_t* d_row_ptr, const int32_t* d_
         (!d_count && !d_score))
         return pmh_set_error(PMH_ERR_ARG, "bad arguments (m in [1,1024])");
     if (Q > 0x7FFFFFFF) return pmh_set_error(PMH_ERR_ARG, "too many queries");
-    return pmh_launch_topm(d_row_ptr, d_cand, d_count, d_score, Q, m, d_out_ids, d_out_n, nullptr,
+    return pmh_launch_topm(d_row_ptr, d_cand, d_count, d_score, Q, m, 0, d_out_ids, d_out_n, nullptr,
                            (cudaStream_t)stream);
 }

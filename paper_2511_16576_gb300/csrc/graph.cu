@@ -42,7 +42,7 @@ struct pmh_qgraph_s {
     int32_t* slab_edges = nullptr;
     int64_t cap_ptr = 0, cap_edges = 0;
     int64_t* counts = nullptr;
-    int32_t* join_stage = nullptr;    // short join rows sorted by the count pass (nullable)
+    void* join_stage = nullptr;       // join rows sorted by the count pass (nullable): a pool of cap ids
     int64_t* row_ptr = nullptr;
     int32_t* cand = nullptr;
     uint16_t* count16 = nullptr;
@@ -158,8 +158,8 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_
               cudaMalloc(&g->slab_cursor, sizeof(int32_t) * g->cap_ptr) == cudaSuccess &&
               cudaMalloc(&g->slab_edges, sizeof(int32_t) * g->cap_edges) == cudaSuccess &&
               cudaMalloc(&g->counts, sizeof(int64_t) * Q) == cudaSuccess &&
-              (pmh_join_stage_ints(index, Q) == 0 ||
-               cudaMalloc(&g->join_stage, sizeof(int32_t) * pmh_join_stage_ints(index, Q)) == cudaSuccess) &&
+              (index->params.bands < 16 ||
+               cudaMalloc(&g->join_stage, pmh_join_stage_bytes(Q, g->cap)) == cudaSuccess) &&
               cudaMalloc(&g->row_ptr, sizeof(int64_t) * (Q + 1)) == cudaSuccess &&
               cudaMalloc(&g->cand, sizeof(int32_t) * cand_capacity) == cudaSuccess &&
               cudaMalloc(&g->count16, sizeof(uint16_t) * cand_capacity) == cudaSuccess &&
@@ -210,37 +210,45 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_
                                      g->ticket, g->hashes, nullptr, cs);
     if (rc == PMH_OK)
         rc = pmh_launch_query(index, g->hashes, Q, g->d_n, g->counts, nullptr, nullptr, 0, g->join_stage,
-                              g->flags, false, cs);
+                              g->cap, g->flags, false, cs);
     if (rc == PMH_OK) rc = pmh_exclusive_scan_i64(ctx, g->counts, g->row_ptr, Q, cs, g->scan_sums);
     if (rc == PMH_OK)
         rc = pmh_launch_query(index, g->hashes, Q, g->d_n, nullptr, g->row_ptr, g->cand, g->cap,
-                              g->join_stage, g->flags, true, cs);
+                              g->join_stage, g->cap, g->flags, true, cs);
     if (rc == PMH_OK)
         rc = pmh_launch_agree(ctx, g->hashes, index->hashes, g->row_ptr, g->cand, Q, g->cap, &g->P,
                               g->count16, nullptr, g->flags, cs);
     if (rc == PMH_OK && S == 0)
-        rc = pmh_launch_topm(g->row_ptr, g->cand, g->count16, nullptr, Q, m, g->top_ids, g->top_n,
+        rc = pmh_launch_topm(g->row_ptr, g->cand, g->count16, nullptr, Q, m, K, g->top_ids, g->top_n,
                              g->flags, cs);
     if (S > 0) {
-        // learned form (A7): the top-S by count, compacted, rescored by the MLP; the top-m by
-        // score go on to refinement
+        // learned form (A7): the top-S by count rescored by the MLP; the top-m by score go on
+        // to refinement
         if (rc == PMH_OK)
-            rc = pmh_launch_topm(g->row_ptr, g->cand, g->count16, nullptr, Q, S, g->sl_ids, g->sl_n,
+            rc = pmh_launch_topm(g->row_ptr, g->cand, g->count16, nullptr, Q, S, K, g->sl_ids, g->sl_n,
                                  g->flags, cs);
-        if (rc == PMH_OK)
-            rc = pmh_launch_lists_to_csr(ctx, g->sl_ids, g->sl_n, Q, S, g->d_n, g->sl_counts, g->sl_sums,
-                                         g->sl_row_ptr, g->sl_cand, cs);
         if (rc == PMH_OK)
             rc = pmh_launch_poly_feat(ctx->sm_count, g->area2, g->off, Q, g->d_n, g->qfeat, cs);
-        if (rc == PMH_OK)
-            rc = pmh_launch_agree_features(ctx, g->hashes, index->hashes, g->sl_row_ptr, g->sl_cand, Q,
-                                           Q * S, &g->P, nullptr, nullptr, g->feat,
-                                           FeatSrc{g->qfeat, g->bbox, g->area2},
-                                           FeatSrc{db->feat, db->bbox, db->area2}, g->flags, cs);
-        if (rc == PMH_OK) rc = pmh_launch_rerank_forward(g->rerank, g->feat, Q * S, g->score, g->flags, cs);
-        if (rc == PMH_OK)
-            rc = pmh_launch_topm(g->sl_row_ptr, g->sl_cand, nullptr, g->score, Q, m, g->top_ids, g->top_n,
-                                 g->flags, cs);
+        const FeatSrc qf{g->qfeat, g->bbox, g->area2}, pf{db->feat, db->bbox, db->area2};
+        if (pmh_rerank_select_fits(S, (int)K)) {
+            // features, scores and the top-m by score in one launch
+            if (rc == PMH_OK)
+                rc = pmh_launch_rerank_select(g->rerank, g->hashes, index->hashes, g->sl_ids, g->sl_n, Q,
+                                              g->d_n, S, m, &g->P, qf, pf, g->top_ids, g->top_n, g->flags, cs);
+        } else {
+            // other shortlist lengths: compact lists, feature rows, forward pass, top-m
+            if (rc == PMH_OK)
+                rc = pmh_launch_lists_to_csr(ctx, g->sl_ids, g->sl_n, Q, S, g->d_n, g->sl_counts, g->sl_sums,
+                                             g->sl_row_ptr, g->sl_cand, cs);
+            if (rc == PMH_OK)
+                rc = pmh_launch_agree_features(ctx, g->hashes, index->hashes, g->sl_row_ptr, g->sl_cand, Q,
+                                               Q * S, &g->P, nullptr, nullptr, g->feat, qf, pf, g->flags, cs);
+            if (rc == PMH_OK)
+                rc = pmh_launch_rerank_forward(g->rerank, g->feat, Q * S, g->score, g->flags, cs);
+            if (rc == PMH_OK)
+                rc = pmh_launch_topm(g->sl_row_ptr, g->sl_cand, nullptr, g->score, Q, m, 0, g->top_ids,
+                                     g->top_n, g->flags, cs);
+        }
     }
     if (rc == PMH_OK && k > 0)
         rc = pmh_launch_refine_topk(ctx, g->xy, g->off, g->area2, g->bbox, db, g->top_ids, g->top_n, Q, g->d_n, m,

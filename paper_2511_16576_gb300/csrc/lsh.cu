@@ -202,26 +202,36 @@ __global__ void query_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, in
 
 // Many-band join: one block per query.  Each warp takes one band at a time;
 // its lanes stride over the band's bucket (coalesced reads of the sorted
-// entries) and insert exact matches into a shared-memory open-addressing set,
-// which drops the duplicates (a candidate found in several bands).  The set is
-// then compacted and bitonic-sorted, which yields the same ascending,
-// duplicate-free row as the warp merge.  Two set sizes: the small one (8,192
-// slots, several blocks per SM) takes every row of at most 4,096 distinct
-// candidates; a row that overflows it is marked (count -1) and counted again,
-// like every longer row filled, by the large one (32,768 slots, one block per
-// SM).  A row beyond even that falls back to the warp merge (warp 0).  Given a
-// staging buffer (4,096 ids per query), the small set's count pass also writes
-// its sorted rows there, and the fill pass of those rows is a copy into place
-// (copy_rows_kernel) instead of a second join.
+// entries, the next 32 read while the current ones are checked) and insert
+// exact matches into a shared-memory open-addressing set, which drops the
+// duplicates (a candidate found in several bands).  The set is then compacted
+// and bitonic-sorted, which yields the same ascending, duplicate-free row as the
+// warp merge.  Two set sizes: the small one (8,192 slots, several blocks per SM)
+// takes every row of at most 4,096 distinct candidates; a row that overflows it
+// stops walking, is marked (count -1) and counted again, like every longer row
+// filled, by the large one (32,768 slots, one block of 1,024 threads per SM).
+// A row beyond even that falls back to the warp merge (warp 0).  With a staging
+// pool, the count pass also writes each sorted row there (a slice reserved by an
+// atomic cursor; a row that no longer fits is left unstaged) and the fill pass
+// copies the staged rows into place (copy_rows_kernel) and joins only the rest.
 template <bool kBig>
 struct JoinShape {
-    static constexpr int kThreads = kBig ? 512 : 256;
+    static constexpr int kThreads = kBig ? 1024 : 256;
     static constexpr int kLog2Table = kBig ? 15 : 13;
     static constexpr int kTable = 1 << kLog2Table;   // shared set slots
     static constexpr int kMaxUnique = kTable / 2;    // load factor <= 1/2
     static constexpr size_t kSmem = sizeof(int32_t) * (kTable + kMaxUnique);
 };
 constexpr int kSmallRowMax = JoinShape<false>::kMaxUnique;
+
+// where the count pass leaves its sorted rows: pool slices handed out by cursor;
+// where[q] = offset of row q's slice, -1 if the row is not staged
+struct JoinStage {
+    int32_t* pool = nullptr;
+    int64_t pool_ints = 0;
+    unsigned long long* cursor = nullptr;
+    int64_t* where = nullptr;
+};
 
 __device__ int64_t merge_row(const uint32_t* __restrict__ qh, int K, int bands, int rows, uint32_t T,
                              uint64_t lsh_seed, int band_bits, const uint32_t* __restrict__ comp,
@@ -264,26 +274,208 @@ __device__ __forceinline__ uint32_t slot_hash(int32_t p)
     return ((uint32_t)p * 0x9E3779B1u) >> (32 - kLog2);
 }
 
+// candidate p's tuple of band j equals the query's, both tuples read at once (16-byte
+// loads for 4 or 8 rows when vec: K % 4 == 0)
+__device__ __forceinline__ bool tuple_match2(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ dbrow,
+                                             int j, int rows, bool vec)
+{
+    const uint32_t* a = qh + j * rows;
+    const uint32_t* b = dbrow + j * rows;
+    if (vec && rows == 4) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(a)), v = __ldg(reinterpret_cast<const uint4*>(b));
+        return u.x == v.x && u.y == v.y && u.z == v.z && u.w == v.w;
+    }
+    if (vec && rows == 8) {
+        const uint4 u0 = __ldg(reinterpret_cast<const uint4*>(a)), v0 = __ldg(reinterpret_cast<const uint4*>(b));
+        const uint4 u1 = __ldg(reinterpret_cast<const uint4*>(a) + 1), v1 = __ldg(reinterpret_cast<const uint4*>(b) + 1);
+        return u0.x == v0.x && u0.y == v0.y && u0.z == v0.z && u0.w == v0.w && u1.x == v1.x && u1.y == v1.y &&
+               u1.z == v1.z && u1.w == v1.w;
+    }
+    if (rows <= 8) {
+        uint32_t u[8], v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            u[t] = t < rows ? __ldg(a + t) : 0u;
+            v[t] = t < rows ? __ldg(b + t) : 0u;
+        }
+        bool eq = true;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) eq &= u[t] == v[t];
+        return eq;
+    }
+    return tuple_equal(qh, dbrow, j, rows);
+}
+
+// per-band state of a block's walk (bands <= 128)
+struct JoinBands {
+    int64_t lo[kMaxBandsPerLane * 32];   // first entry of the band's composite
+    int64_t off[kMaxBandsPerLane * 32 + 1];  // prefix of the bands' entry counts
+};
+
+// The set's walk over the query's bands, keeping the exact bucket members with ids in
+// [id_lo, id_hi); returns the number of distinct ids inserted (more than kMaxUnique:
+// the walk stopped early).  The equal-composite range of every band is found first
+// (a thread per band: two directory lookups); the ranges' entries, concatenated, are
+// then split evenly over the block's warps, 32 consecutive entries at a time, two
+// chunks in flight per warp -- one band's bucket of thousands of entries no longer
+// keeps one warp busy while the others wait.  Block-wide; starts and ends with a
+// barrier.
+template <bool kBig>
+__device__ int join_walk(const uint32_t* __restrict__ qh, int K, int bands, int rows, uint32_t T,
+                         uint64_t lsh_seed, int band_bits, const uint32_t* __restrict__ comp,
+                         const int32_t* __restrict__ ids, const uint32_t* __restrict__ dbh,
+                         const int64_t* __restrict__ dir, int dsh, int64_t m, int32_t id_lo, int32_t id_hi,
+                         int32_t* table, int* n_unique, JoinBands& jb)
+{
+    using S = JoinShape<kBig>;
+    constexpr int kJoinTable = S::kTable, kJoinMaxUnique = S::kMaxUnique;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    volatile int* nu_v = n_unique;
+    const bool vec = (K & 3) == 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kJoinTable; i += blockDim.x) table[i] = kNone;
+    if (threadIdx.x == 0) *n_unique = 0;
+    for (int j = threadIdx.x; j < bands; j += blockDim.x) {
+        const uint64_t key = band_key(qh, j, rows, T, lsh_seed);
+        int64_t lo = 0, n = 0;
+        if (key != PMH_INVALID_KEY) {
+            const uint32_t c = composite(key, j, band_bits);
+            lo = comp_lower_bound(comp, dir, dsh, c);
+            const int64_t hi = c == 0xFFFFFFFFu ? m : comp_lower_bound(comp, dir, dsh, c + 1);
+            n = hi - lo;
+        }
+        jb.lo[j] = lo;
+        jb.off[j + 1] = n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        jb.off[0] = 0;
+        for (int j = 0; j < bands; ++j) {
+            acc += jb.off[j + 1];
+            jb.off[j + 1] = acc;
+        }
+    }
+    __syncthreads();
+    const int64_t total = jb.off[bands];
+    for (int64_t g0 = (int64_t)wid * 64; g0 < total; g0 += (int64_t)nw * 64) {
+        if (__shfl_sync(0xffffffffu, *nu_v, 0) > kJoinMaxUnique) break;  // falls back anyway
+        // two chunks of 32 entries: each lane's band by bisection over the prefix
+        int jj[2];
+        int32_t pp[2];
+        bool in[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t g = g0 + 32 * u + lane;
+            in[u] = g < total;
+            int lo = 0, hi = bands;  // last j with off[j] <= g
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (jb.off[mid] <= g) lo = mid;
+                else hi = mid;
+            }
+            jj[u] = lo;
+            pp[u] = in[u] ? ids[jb.lo[lo] + (g - jb.off[lo])] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int32_t pe = pp[u];
+            if (in[u] && pe >= id_lo && pe < id_hi && tuple_match2(qh, dbh + (int64_t)pe * K, jj[u], rows, vec)) {
+                uint32_t h = slot_hash<S::kLog2Table>(pe);
+                for (int probe = 0; probe < kJoinTable; ++probe, h = (h + 1) & (kJoinTable - 1)) {
+                    const int32_t old = atomicCAS(&table[h], kNone, pe);
+                    if (old == kNone) {
+                        atomicAdd(n_unique, 1);
+                        break;
+                    }
+                    if (old == pe) break;
+                    if (*nu_v > kJoinMaxUnique) break;  // the set falls back anyway
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return *n_unique;
+}
+
+// the set's nu ids, ascending, to out (compaction by a block scan over contiguous
+// slot ranges into buf, then a bitonic sort of the next power of two above nu)
+template <bool kBig>
+__device__ void join_emit(int32_t* table, int nu, int* wsum, int32_t* __restrict__ out)
+{
+    using S = JoinShape<kBig>;
+    constexpr int kJoinTable = S::kTable;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t* buf = table + kJoinTable;
+    constexpr int kPer = kJoinTable / S::kThreads;
+    const int s0 = threadIdx.x * kPer;
+    int mine = 0;
+    for (int i = 0; i < kPer; ++i) mine += table[s0 + i] != kNone;
+    int x = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    int pos = x - mine;
+    for (int w = 0; w < wid; ++w) pos += wsum[w];
+    for (int i = 0; i < kPer; ++i)
+        if (table[s0 + i] != kNone) buf[pos++] = table[s0 + i];
+    int n2 = 1;
+    while (n2 < nu) n2 <<= 1;
+    for (int i = nu + threadIdx.x; i < n2; i += blockDim.x) buf[i] = kNone;
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int l = i ^ jj;
+                if (l > i) {
+                    const int32_t a = buf[i], b = buf[l];
+                    if ((a > b) == ((i & k) == 0)) {
+                        buf[i] = b;
+                        buf[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) out[i] = buf[i];
+    __syncthreads();
+}
+
+// A row of more distinct candidates than the large set holds is joined in id-range
+// passes: pass r keeps the ids in [r N / P, (r + 1) N / P), so the passes' sorted
+// outputs concatenate to the sorted row; P doubles until every pass fits (beyond
+// kMaxPasses the row takes the warp merge).  Such rows are not staged: the count
+// pass records -P in where[q] (-2 kMaxPasses for a merged row) and the fill pass
+// joins them again the same way.
+constexpr int kMaxPasses = 64;
+
 template <bool kWrite, bool kBig>
 __global__ void __launch_bounds__(JoinShape<kBig>::kThreads)
 join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, int rows, uint32_t T,
             uint64_t lsh_seed, int band_bits, const uint32_t* __restrict__ comp,
             const int32_t* __restrict__ ids, const uint32_t* __restrict__ dbh,
-            const int64_t* __restrict__ dir, int dsh, int64_t m, int64_t* __restrict__ counts,
+            const int64_t* __restrict__ dir, int dsh, int64_t m, int64_t n_db, int64_t* __restrict__ counts,
             const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand, int64_t cap,
-            int32_t* __restrict__ stage, const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
+            JoinStage st, const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
 {
     using S = JoinShape<kBig>;
-    constexpr int kJoinTable = S::kTable, kJoinMaxUnique = S::kMaxUnique;
+    constexpr int kJoinMaxUnique = S::kMaxUnique;
     extern __shared__ int32_t table[];  // kJoinTable slots, then kJoinMaxUnique sorted ids
     __shared__ int n_unique;
+    __shared__ long long stage_off;
     __shared__ int wsum[S::kThreads / 32];
+    __shared__ JoinBands jb;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
     for (int64_t q = blockIdx.x; q < Q; q += gridDim.x) {
         const bool skip = (d_n && q >= *d_n) || (d_flags && (*d_flags & 7));
         if (skip) {
-            if (!kWrite && !kBig && threadIdx.x == 0) counts[q] = 0;
+            if (!kWrite && !kBig && threadIdx.x == 0) {
+                counts[q] = 0;
+                if (st.where) st.where[q] = -1;
+            }
             continue;
         }
         if (kWrite && row_ptr[Q] > cap) {
@@ -291,115 +483,115 @@ join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, i
             return;
         }
         // rows by size: the small set counts every row and fills the short ones; the
-        // large set counts the rows that overflowed the small one and fills the long ones
+        // large set counts the rows that overflowed the small one and fills the long ones;
+        // staged rows are copied instead
         if (!kWrite && kBig && counts[q] >= 0) continue;
         if (kWrite && ((row_ptr[q + 1] - row_ptr[q] > kSmallRowMax) != kBig)) continue;
+        int passes = 1;
+        if (kWrite && st.where) {
+            const int64_t w = st.where[q];
+            if (w >= 0) continue;
+            passes = (int)max((int64_t)1, -w);
+        }
         const uint32_t* qh = qhashes + q * K;
-        __syncthreads();
-        for (int i = threadIdx.x; i < kJoinTable; i += blockDim.x) table[i] = kNone;
-        if (threadIdx.x == 0) n_unique = 0;
-        __syncthreads();
-        for (int j = wid; j < bands; j += nw) {
-            const uint64_t key = band_key(qh, j, rows, T, lsh_seed);
-            if (key == PMH_INVALID_KEY) continue;
-            const uint32_t c = composite(key, j, band_bits);
-            const int64_t lo = comp_lower_bound(comp, dir, dsh, c);
-            for (int64_t base = lo;; base += 32) {
-                const int64_t e = base + lane;
-                const bool in = e < m && comp[e] == c;
-                if (!__any_sync(0xffffffffu, in)) break;
-                if (!in) continue;
-                const int32_t p = ids[e];
-                if (!tuple_equal(qh, dbh + (int64_t)p * K, j, rows)) continue;
-                uint32_t h = slot_hash<S::kLog2Table>(p);
-                for (int probe = 0; probe < kJoinTable; ++probe, h = (h + 1) & (kJoinTable - 1)) {
-                    const int32_t old = atomicCAS(&table[h], kNone, p);
-                    if (old == kNone) {
-                        atomicAdd(&n_unique, 1);
-                        break;
-                    }
-                    if (old == p) break;
-                    if (n_unique > kJoinMaxUnique) break;  // the row falls back anyway
+        int64_t total = 0;
+        bool merged = passes > kMaxPasses;
+        while (!merged) {  // passes over id ranges (one, unless the row overflows the large set)
+            bool over = false;
+            total = 0;
+            for (int r = 0; r < passes; ++r) {
+                const int32_t lo = (int32_t)(n_db * r / passes), hi = (int32_t)(n_db * (r + 1) / passes);
+                const int nu = join_walk<kBig>(qh, K, bands, rows, T, lsh_seed, band_bits, comp, ids, dbh, dir,
+                                               dsh, m, lo, hi, table, &n_unique, jb);
+                if (nu > kJoinMaxUnique) {
+                    over = true;
+                    break;
                 }
-            }
-        }
-        __syncthreads();
-        const int nu = n_unique;
-        if (!kBig && nu > kJoinMaxUnique) {  // the large set counts this row again
-            if (threadIdx.x == 0) counts[q] = -1;
-            continue;
-        }
-        if (nu > kJoinMaxUnique) {  // rare: merge the row with warp 0
-            if (wid == 0) {
-                int64_t cnt = merge_row(qh, K, bands, rows, T, lsh_seed, band_bits, comp, ids,
-                                        dbh, dir, dsh, m, kWrite ? cand + row_ptr[q] : nullptr);
-                if (!kWrite && lane == 0) counts[q] = cnt;
-            }
-            continue;
-        }
-        if (!kWrite) {
-            if (threadIdx.x == 0) counts[q] = nu;
-            if (!stage) continue;  // (else the sorted row goes to the staging buffer)
-        }
-        // compact the occupied slots into buf (block scan over contiguous slot ranges),
-        // then sort only the next power of two above nu
-        int32_t* buf = table + kJoinTable;
-        constexpr int kPer = kJoinTable / S::kThreads;
-        const int s0 = threadIdx.x * kPer;
-        int mine = 0;
-        for (int i = 0; i < kPer; ++i) mine += table[s0 + i] != kNone;
-        int x = mine;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[wid] = x;
-        __syncthreads();
-        int pos = x - mine;
-        for (int w = 0; w < wid; ++w) pos += wsum[w];
-        for (int i = 0; i < kPer; ++i)
-            if (table[s0 + i] != kNone) buf[pos++] = table[s0 + i];
-        int n2 = 1;
-        while (n2 < nu) n2 <<= 1;
-        for (int i = nu + threadIdx.x; i < n2; i += blockDim.x) buf[i] = kNone;
-        __syncthreads();
-        for (int k = 2; k <= n2; k <<= 1)
-            for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-                    const int l = i ^ jj;
-                    if (l > i) {
-                        const int32_t a = buf[i], b = buf[l];
-                        if ((a > b) == ((i & k) == 0)) {
-                            buf[i] = b;
-                            buf[l] = a;
+                int32_t* out = nullptr;
+                if (kWrite) {
+                    out = cand + row_ptr[q] + total;
+                } else if (passes == 1) {
+                    // the count pass stages a one-pass row when the pool has room
+                    if (threadIdx.x == 0) {
+                        long long off = -1;
+                        if (st.pool && st.where) {
+                            const unsigned long long o = atomicAdd(st.cursor, (unsigned long long)nu);
+                            if ((long long)(o + (unsigned long long)nu) <= st.pool_ints) off = (long long)o;
                         }
+                        stage_off = off;
                     }
+                    __syncthreads();
+                    if (stage_off >= 0) out = st.pool + stage_off;
                 }
-                __syncthreads();
+                if (out) join_emit<kBig>(table, nu, wsum, out);
+                total += nu;
             }
-        int32_t* out = kWrite ? cand + row_ptr[q] : stage + q * (int64_t)kSmallRowMax;
-        for (int i = threadIdx.x; i < nu; i += blockDim.x) out[i] = buf[i];
+            if (!over) break;
+            if (!kBig) break;  // the large set takes the row
+            passes *= 2;
+            if (passes > kMaxPasses) {
+                merged = true;
+                break;
+            }
+        }
+        if (!kBig && n_unique > kJoinMaxUnique) {
+            // the small set overflowed: the large set counts this row again
+            if (threadIdx.x == 0) {
+                counts[q] = -1;
+                if (st.where) st.where[q] = -1;
+            }
+            continue;
+        }
+        if (merged) {  // beyond the id-range passes: merge the row with warp 0 (never staged)
+            if (wid == 0) {
+                const int64_t cnt = merge_row(qh, K, bands, rows, T, lsh_seed, band_bits, comp, ids, dbh, dir,
+                                              dsh, m, kWrite ? cand + row_ptr[q] : nullptr);
+                if (!kWrite && lane == 0) {
+                    counts[q] = cnt;
+                    if (st.where) st.where[q] = -2 * (int64_t)kMaxPasses;
+                }
+            }
+            continue;
+        }
+        if (!kWrite && threadIdx.x == 0) {
+            counts[q] = total;
+            if (st.where) st.where[q] = passes > 1 ? -(int64_t)passes : (long long)stage_off;
+        }
     }
 }
 
-// fill pass of the rows the small set counted and staged: a warp per query copies
-// its sorted row into place (longer rows are the large set's)
-__global__ void copy_rows_kernel(const int32_t* __restrict__ stage, int64_t Q,
-                                 const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand,
-                                 int64_t cap, const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
+// fill pass of the staged rows: a block per row copies its pool slice into place
+// (four independent loads per thread in flight)
+__global__ void __launch_bounds__(256)
+copy_rows_kernel(JoinStage st, int64_t Q, const int64_t* __restrict__ row_ptr, int32_t* __restrict__ cand,
+                 int64_t cap, const int64_t* __restrict__ d_n, int* __restrict__ d_flags)
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (q >= Q) return;
-    if ((d_n && q >= *d_n) || (d_flags && (*d_flags & 7))) return;
+    if (d_flags && (*d_flags & 7)) return;
     if (row_ptr[Q] > cap) {
-        if (lane == 0 && d_flags) atomicOr(d_flags, 8);
+        if (blockIdx.x == 0 && threadIdx.x == 0 && d_flags) atomicOr(d_flags, 8);
         return;
     }
-    const int64_t b = row_ptr[q], len = row_ptr[q + 1] - b;
-    if (len > kSmallRowMax) return;
-    const int32_t* src = stage + q * (int64_t)kSmallRowMax;
-    for (int64_t i = lane; i < len; i += 32) cand[b + i] = src[i];
+    const int64_t live = d_n ? min(Q, *d_n) : Q;
+    for (int64_t q = blockIdx.x; q < live; q += gridDim.x) {
+        const int64_t off = st.where[q];
+        if (off < 0) continue;
+        const int64_t b = row_ptr[q], len = row_ptr[q + 1] - b;
+        const int32_t* src = st.pool + off;
+        int32_t* dst = cand + b;
+        for (int64_t i = threadIdx.x; i < len; i += 4 * blockDim.x) {
+            int32_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t k = i + (int64_t)u * blockDim.x;
+                v[u] = k < len ? src[k] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t k = i + (int64_t)u * blockDim.x;
+                if (k < len) dst[k] = v[u];
+            }
+        }
+    }
 }
 
 }  // namespace
@@ -530,7 +722,7 @@ extern "C" int pmh_index_destroy(pmh_index X)
 template <bool kBig>
 static int launch_join(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
                        int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
-                       int32_t* stage, int* d_flags, bool write, cudaStream_t s)
+                       const JoinStage& st, int* d_flags, bool write, cudaStream_t s)
 {
     using S = JoinShape<kBig>;
     const pmh_params& P = X->params;
@@ -543,23 +735,35 @@ static int launch_join(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t
         (unsigned)std::min<int64_t>(Q, (int64_t)X->ctx->sm_count * std::max(per_sm, 1));
     fn<<<blocks, S::kThreads, S::kSmem, s>>>(qh, Q, (int)P.K, (int)P.bands, (int)P.rows, P.T,
                                             P.lsh_seed, X->band_bits, X->sorted_comp, X->sorted_id,
-                                            X->hashes, X->dir, X->dir_shift, m,
+                                            X->hashes, X->dir, X->dir_shift, m, X->n,
                                             write ? nullptr : counts, write ? row_ptr : nullptr,
-                                            write ? cand : nullptr, write ? cap : 0,
-                                            kBig ? nullptr : stage, d_n, d_flags);
+                                            write ? cand : nullptr, write ? cap : 0, st, d_n, d_flags);
     PMH_LAUNCHED(write ? (kBig ? "join_kernel<fill,large>" : "join_kernel<fill,small>")
                        : (kBig ? "join_kernel<count,large>" : "join_kernel<count,small>"));
     return PMH_OK;
 }
 
-int64_t pmh_join_stage_ints(pmh_index X, int64_t Q)
+size_t pmh_join_stage_bytes(int64_t Q, int64_t pool_ints)
 {
-    return X && X->params.bands >= 16 ? Q * (int64_t)kSmallRowMax : 0;
+    return 16 + sizeof(int64_t) * (size_t)Q + sizeof(int32_t) * (size_t)pool_ints;
+}
+
+// cursor (16 bytes), where [Q], pool [pool_ints] laid out in one buffer
+static JoinStage stage_view(void* buf, int64_t Q, int64_t pool_ints)
+{
+    JoinStage st;
+    if (!buf) return st;
+    char* c = static_cast<char*>(buf);
+    st.cursor = reinterpret_cast<unsigned long long*>(c);
+    st.where = reinterpret_cast<int64_t*>(c + 16);
+    st.pool = reinterpret_cast<int32_t*>(c + 16 + sizeof(int64_t) * (size_t)Q);
+    st.pool_ints = pool_ints;
+    return st;
 }
 
 int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
                      int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
-                     int32_t* stage, int* d_flags, bool write, cudaStream_t s)
+                     void* stage, int64_t pool_ints, int* d_flags, bool write, cudaStream_t s)
 {
     if (Q <= 0) return PMH_OK;
     const pmh_params& P = X->params;
@@ -568,14 +772,18 @@ int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* 
     // set (rows of thousands of candidates occur on dense sets; the warp merge below
     // would walk them one candidate at a time)
     if (P.bands >= 16) {
-        if (write && stage) {  // the staged short rows: a copy into place
-            const unsigned cblocks = (unsigned)((Q + 7) / 8);
-            copy_rows_kernel<<<cblocks, 256, 0, s>>>(stage, Q, row_ptr, cand, cap, d_n, d_flags);
-            PMH_LAUNCHED("copy_rows_kernel");
-        } else {
-            PMH_TRY(launch_join<false>(X, qh, Q, d_n, counts, row_ptr, cand, cap, stage, d_flags, write, s));
+        const JoinStage st = stage_view(stage, Q, pool_ints);
+        if (write) {
+            if (st.where) {  // the staged rows: a copy into place
+                const unsigned cblocks = (unsigned)std::min<int64_t>(Q, (int64_t)X->ctx->sm_count * 8);
+                copy_rows_kernel<<<cblocks, 256, 0, s>>>(st, Q, row_ptr, cand, cap, d_n, d_flags);
+                PMH_LAUNCHED("copy_rows_kernel");
+            }
+        } else if (st.cursor) {
+            PMH_CUDA_TRY(cudaMemsetAsync(st.cursor, 0, sizeof(unsigned long long), s));
         }
-        return launch_join<true>(X, qh, Q, d_n, counts, row_ptr, cand, cap, nullptr, d_flags, write, s);
+        PMH_TRY(launch_join<false>(X, qh, Q, d_n, counts, row_ptr, cand, cap, st, d_flags, write, s));
+        return launch_join<true>(X, qh, Q, d_n, counts, row_ptr, cand, cap, st, d_flags, write, s);
     }
     const int wpb = 8;
     unsigned blocks = (unsigned)((Q + wpb - 1) / wpb);
@@ -612,13 +820,16 @@ extern "C" int pmh_lsh_query(pmh_ctx ctx, pmh_index X, const uint32_t* d_qhashes
     }
     int64_t* counts = nullptr;
     PMH_TRY(pmh_scratch(ctx, SCR_QUERY, sizeof(int64_t) * (size_t)Q, (void**)&counts));
-    // the short rows staged by the count pass when the staging buffer stays modest
-    int32_t* stage = nullptr;
-    const int64_t stage_ints = pmh_join_stage_ints(X, Q);
-    if (stage_ints > 0 && stage_ints <= (64ll << 20))
-        PMH_TRY(pmh_scratch(ctx, SCR_JOIN, sizeof(int32_t) * (size_t)stage_ints, (void**)&stage));
-    PMH_TRY(pmh_launch_query(X, d_qhashes, Q, nullptr, counts, nullptr, nullptr, 0, stage, nullptr, false,
-                             s));
+    // the count pass stages its sorted rows in a pool of up to 4,096 ids per query
+    // (at most 64M ids); rows past the pool are joined again by the fill pass
+    void* stage = nullptr;
+    int64_t pool_ints = 0;
+    if (X->params.bands >= 16) {
+        pool_ints = std::min<int64_t>(Q * 4096, 64ll << 20);
+        PMH_TRY(pmh_scratch(ctx, SCR_JOIN, pmh_join_stage_bytes(Q, pool_ints), &stage));
+    }
+    PMH_TRY(pmh_launch_query(X, d_qhashes, Q, nullptr, counts, nullptr, nullptr, 0, stage, pool_ints,
+                             nullptr, false, s));
     PMH_TRY(pmh_exclusive_scan_i64(ctx, counts, d_row_ptr, Q, s));
     PMH_CUDA_TRY(cudaMemcpyAsync(ctx->h_pinned, d_row_ptr + Q, sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, s));
@@ -631,7 +842,7 @@ extern "C" int pmh_lsh_query(pmh_ctx ctx, pmh_index X, const uint32_t* d_qhashes
     if (total == 0) return PMH_OK;
     if (!d_cand) return pmh_set_error(PMH_ERR_ARG, "null candidate buffer");
     return pmh_launch_query(X, d_qhashes, Q, nullptr, nullptr, d_row_ptr, d_cand, cand_capacity,
-                            stage, nullptr, true, s);
+                            stage, pool_ints, nullptr, true, s);
 }
 
 extern "C" int pmh_lsh_query_fill(pmh_ctx ctx, pmh_index X, const uint32_t* d_qhashes, int64_t Q,
@@ -643,5 +854,5 @@ extern "C" int pmh_lsh_query_fill(pmh_ctx ctx, pmh_index X, const uint32_t* d_qh
         return pmh_set_error(PMH_ERR_ARG, "bad arguments");
     if (Q == 0) return PMH_OK;
     return pmh_launch_query(X, d_qhashes, Q, nullptr, nullptr, d_row_ptr, d_cand, cand_capacity,
-                            nullptr, nullptr, true, (cudaStream_t)stream);
+                            nullptr, 0, nullptr, true, (cudaStream_t)stream);
 }

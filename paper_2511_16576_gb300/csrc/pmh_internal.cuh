@@ -366,12 +366,14 @@ int pmh_launch_sign_unified(pmh_ctx ctx, int U, const int2* xy, const int64_t* o
                             const StreamIndexView& S, unsigned long long* ticket, uint32_t* out,
                             unsigned long long* work, cudaStream_t s);
 // bucket join (lsh.cu): the count pass (write false: counts) or the fill pass (write
-// true: the CSR rows); `stage` (nullable, pmh_join_stage_ints(X, Q) ints) lets the
-// count pass keep the short rows it sorted, so that the fill pass copies them
-int64_t pmh_join_stage_ints(pmh_index X, int64_t Q);
+// true: the CSR rows).  `stage` (nullable, pmh_join_stage_bytes(Q, pool_ints) bytes,
+// the same buffer for both passes, 16-byte aligned) lets the count pass keep the rows
+// it sorted, up to pool_ints ids in all, so that the fill pass copies them; the fill
+// pass of a call whose count pass had no stage gets none either
+size_t pmh_join_stage_bytes(int64_t Q, int64_t pool_ints);
 int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* d_n,
                      int64_t* counts, const int64_t* row_ptr, int32_t* cand, int64_t cap,
-                     int32_t* stage, int* d_flags, bool write, cudaStream_t s);
+                     void* stage, int64_t pool_ints, int* d_flags, bool write, cudaStream_t s);
 int pmh_launch_agree(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph, const int64_t* row_ptr,
                      const int32_t* cand, int64_t Q, int64_t cap, const pmh_params* P,
                      uint16_t* count, uint32_t* bandmask, const int* d_flags, cudaStream_t s);
@@ -381,6 +383,65 @@ struct FeatSrc {
     const int4* bbox;
     const int64_t* area2;
 };
+
+// a pair's per-polygon inputs of its feature row
+struct FeatPair {
+    float2 qf, pf;       // (log2 area / 32, log2 vertex count / 16)
+    int4 qb, pb;         // bounding boxes
+    long long qa2, pa2;  // twice the signed areas
+};
+__device__ __forceinline__ FeatPair pmh_feat_pair(const FeatSrc& qf, const FeatSrc& pf, int64_t q, int64_t p)
+{
+    return FeatPair{qf.feat[q], pf.feat[p], qf.bbox[q], pf.bbox[p], qf.area2[q], pf.area2[p]};
+}
+
+// Column 32 + col (col < 16) of the reranker's feature row of a pair (A7) from its
+// comparison counts over the K hashes -- c equal (and not the sentinel), lt / gt
+// lower / higher than the candidate's -- and the two polygons' inputs; 40..47 are
+// zero.  Every kernel that writes feature rows takes these values from here, so all
+// feed the network the same bf16 values.
+__device__ __forceinline__ float pmh_feature_col(int col, int K, int c, int lt, int gt, const FeatPair& in)
+{
+    switch (col) {
+    case 0: return (float)c / (float)K;
+    case 1: return in.qf.x;
+    case 2: return in.pf.x;
+    case 3: return in.qf.y;
+    case 4: return in.pf.y;
+    case 5: return (float)lt / (float)K;
+    case 6: return (float)gt / (float)K;
+    case 7: {
+        // upper bound of J: the intersection is at most min(|q|, |p|, overlap of the
+        // two bounding boxes)
+        const int4 qb = in.qb, pb = in.pb;
+        const float ow = (float)max(0, min(qb.z, pb.z) - max(qb.x, pb.x));
+        const float oh = (float)max(0, min(qb.w, pb.w) - max(qb.y, pb.y));
+        const long long qa = in.qa2, pa = in.pa2;
+        const float a = 0.5f * (float)(qa < 0 ? -qa : qa);
+        const float bq = 0.5f * (float)(pa < 0 ? -pa : pa);
+        const float mn = fminf(fminf(a, bq), ow * oh);
+        const float den = a + bq - mn;
+        return den > 0.f ? mn / den : 0.f;
+    }
+    default: return 0.f;
+    }
+}
+
+// The feature row of a pair, one warp per pair: eq = K / 32 equality words (bit
+// k % 32 of word k / 32 set iff h_k(q) = h_k(p) != T).  Lane l returns column l
+// (all K / 32 hashes of group l equal) in lo and, for l < 16, column 32 + l in hi.
+__device__ __forceinline__ void pmh_feature_values(const uint32_t* eq, int K, int c, int lt, int gt,
+                                                   const FeatPair& in, int lane, float& lo, float& hi)
+{
+    const int g = K / 32;
+    bool all = true;
+    for (int t = 0; t < g && all; ++t) {
+        const int k = lane * g + t;
+        all = (eq[k >> 5] >> (k & 31)) & 1u;
+    }
+    lo = all ? 1.f : 0.f;
+    hi = pmh_feature_col(lane, K, c, lt, gt, in);
+}
 int pmh_launch_agree_features(pmh_ctx ctx, const uint32_t* qh, const uint32_t* ph,
                               const int64_t* row_ptr, const int32_t* cand, int64_t Q, int64_t cap,
                               const pmh_params* P, uint16_t* count, uint32_t* bandmask,
@@ -407,8 +468,17 @@ int pmh_launch_poly_feat(int sm_count, const int64_t* area2, const int64_t* off,
 // reranker scores of n feature rows (rerank.cu)
 int pmh_launch_rerank_forward(pmh_rerank r, const uint16_t* feat, int64_t n_rows, float* score,
                               int* d_flags, cudaStream_t s);
+// the learned form's features, scores and top-m in one launch (rerank.cu): shortlist
+// ids [Q][S] / counts n[Q] (top-S by count) to ids [Q][m] (-1 padded) and counts
+// [Q] by (predicted Jaccard desc, id asc); S must divide 128 (S >= 4), K % 32 == 0
+bool pmh_rerank_select_fits(int S, int K);
+int pmh_launch_rerank_select(pmh_rerank r, const uint32_t* qh, const uint32_t* ph, const int32_t* sl_ids,
+                             const int32_t* sl_n, int64_t Q, const int64_t* d_n, int S, int m,
+                             const pmh_params* P, FeatSrc qf, FeatSrc pf, int32_t* out_ids, int32_t* out_n,
+                             int* d_flags, cudaStream_t s);
+// top-m per row (estimate.cu); K bounds the counts (0: up to 4,096)
 int pmh_launch_topm(const int64_t* row_ptr, const int32_t* cand, const uint16_t* count,
-                    const float* score, int64_t Q, int32_t m, int32_t* out_ids, int32_t* out_n,
+                    const float* score, int64_t Q, int32_t m, int K, int32_t* out_ids, int32_t* out_n,
                     const int* d_flags, cudaStream_t s);
 
 // signing kernel variants (points per lane per round x warps per block)

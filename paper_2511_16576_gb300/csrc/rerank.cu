@@ -513,13 +513,11 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
-mlp_tc_kernel(const __nv_bfloat16* __restrict__ feat, int64_t n_rows, const __nv_bfloat16* __restrict__ w1b,
-              const __nv_bfloat16* __restrict__ w2b, const __nv_bfloat16* __restrict__ w3b,
-              const float* __restrict__ master, float* __restrict__ score, int* __restrict__ err)
+// weights into shared memory, the barrier, the tensor-memory allocation
+__device__ uint32_t tc_setup(TcSmem& s, const __nv_bfloat16* __restrict__ w1b,
+                             const __nv_bfloat16* __restrict__ w2b, const __nv_bfloat16* __restrict__ w3b,
+                             const float* __restrict__ master)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw);
     const int tid = threadIdx.x, wid = tid >> 5;
     for (int i = tid; i < kH * kInPad; i += kTcThreads) s.w1[canon(i / kInPad, i % kInPad, kInPad)] = w1b[i];
     for (int i = tid; i < kH * kH; i += kTcThreads) s.w2[canon(i / kH, i % kH, kH)] = w2b[i];
@@ -545,8 +543,107 @@ mlp_tc_kernel(const __nv_bfloat16* __restrict__ feat, int64_t n_rows, const __nv
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = s.tmem;
+    return s.tmem;
+}
+
+// The network on the tile's features in s.x (written by the CTA's threads just
+// before): thread t returns the predicted Jaccard of row t.  False when a wait on
+// the tensor cores ran out (s.stop set; the caller leaves its loop).
+__device__ bool tc_tile(TcSmem& s, uint32_t tmem, uint32_t& phase, float& out)
+{
+    const int tid = threadIdx.x, wid = tid >> 5;
     const uint32_t lane_base = (uint32_t)(32 * wid) << 16;  // this warp's tensor-memory lanes
+    async_proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // layer 1: three K = 16 steps (two core matrices each, 128 elements apart) into
+    // columns 0..63
+    if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < kInPad / 16; ++kk)
+            tc_mma(tmem, tc_desc(s.x + 128 * kk, 128, kInPad * 16), tc_desc(s.w1 + 128 * kk, 128, kInPad * 16),
+                   kk > 0);
+        tc_commit(&s.mbar);
+    }
+    if (!tc_wait(&s.mbar, phase)) s.stop = 1;
+    phase ^= 1u;
+    tc_fence_after();
+    __syncthreads();
+    if (s.stop) return false;
+    // epilogue 1: bias, ReLU, bf16, into the canonical layout of layer 2's A operand
+    const int row = tid;
+#pragma unroll
+    for (int c0 = 0; c0 < kH; c0 += 16) {
+        float z[16];
+        tc_ld16(tmem + lane_base + (uint32_t)c0, z);
+#pragma unroll
+        for (int j = 0; j < 16; j += 8) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float a = z[j + 2 * u] + s.b1[c0 + j + 2 * u];
+                const float b = z[j + 2 * u + 1] + s.b1[c0 + j + 2 * u + 1];
+                pk[u] = pack2(a > 0.f ? a : 0.f, b > 0.f ? b : 0.f);
+            }
+            *reinterpret_cast<uint4*>(s.h1 + canon(row, c0 + j, kH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+    }
+    async_proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // layer 2: four K = 16 steps into columns 64..127
+    if (tid == 0) {
+#pragma unroll
+        for (int kk = 0; kk < kH / 16; ++kk)
+            tc_mma(tmem + 64, tc_desc(s.h1 + 128 * kk, 128, kH * 16), tc_desc(s.w2 + 128 * kk, 128, kH * 16),
+                   kk > 0);
+        tc_commit(&s.mbar);
+    }
+    if (!tc_wait(&s.mbar, phase)) s.stop = 1;
+    phase ^= 1u;
+    tc_fence_after();
+    __syncthreads();
+    if (s.stop) return false;
+    // epilogue 2: bias, ReLU, bf16 rounding, layer 3 and the sigmoid
+    float acc = 0.f;
+#pragma unroll
+    for (int c0 = 0; c0 < kH; c0 += 16) {
+        float z[16];
+        tc_ld16(tmem + lane_base + 64u + (uint32_t)c0, z);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float v = z[j] + s.b2[c0 + j];
+            acc += bfr(v > 0.f ? v : 0.f) * s.w3[c0 + j];
+        }
+    }
+    out = 1.f / (1.f + expf(-(acc + s.b3)));
+    tc_fence_before();
+    return true;
+}
+
+// the tensor memory back; a wait that ran out reports error bit 16
+__device__ void tc_teardown(TcSmem& s, uint32_t tmem, int* err)
+{
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols)
+                     : "memory");
+    if (threadIdx.x == 0 && s.stop && err) atomicOr(err, kTcErr);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+mlp_tc_kernel(const __nv_bfloat16* __restrict__ feat, int64_t n_rows, const __nv_bfloat16* __restrict__ w1b,
+              const __nv_bfloat16* __restrict__ w2b, const __nv_bfloat16* __restrict__ w3b,
+              const float* __restrict__ master, float* __restrict__ score, int* __restrict__ err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TcSmem& s = *reinterpret_cast<TcSmem*>(smem_raw);
+    const int tid = threadIdx.x;
+    const uint32_t tmem = tc_setup(s, w1b, w2b, w3b, master);
     uint32_t phase = 0;
     for (int64_t base = (int64_t)blockIdx.x * kTcRows; base < n_rows; base += (int64_t)gridDim.x * kTcRows) {
         // the tile's features (16-byte chunks; rows past n_rows are zero)
@@ -556,81 +653,189 @@ mlp_tc_kernel(const __nv_bfloat16* __restrict__ feat, int64_t n_rows, const __nv
             if (base + r < n_rows) v = *reinterpret_cast<const uint4*>(feat + (base + r) * kInPad + 8 * kc);
             *reinterpret_cast<uint4*>(s.x + canon(r, 8 * kc, kInPad)) = v;
         }
-        async_proxy_fence();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        // layer 1: three K = 16 steps (two core matrices each, 128 elements apart) into
-        // columns 0..63
-        if (tid == 0) {
-#pragma unroll
-            for (int kk = 0; kk < kInPad / 16; ++kk)
-                tc_mma(tmem, tc_desc(s.x + 128 * kk, 128, kInPad * 16), tc_desc(s.w1 + 128 * kk, 128, kInPad * 16),
-                       kk > 0);
-            tc_commit(&s.mbar);
-        }
-        if (!tc_wait(&s.mbar, phase)) s.stop = 1;
-        phase ^= 1u;
-        tc_fence_after();
-        __syncthreads();
-        if (s.stop) break;
-        // epilogue 1: bias, ReLU, bf16, into the canonical layout of layer 2's A operand
-        const int row = tid;
-#pragma unroll
-        for (int c0 = 0; c0 < kH; c0 += 16) {
-            float z[16];
-            tc_ld16(tmem + lane_base + (uint32_t)c0, z);
-#pragma unroll
-            for (int j = 0; j < 16; j += 8) {
-                uint32_t pk[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float a = z[j + 2 * u] + s.b1[c0 + j + 2 * u];
-                    const float b = z[j + 2 * u + 1] + s.b1[c0 + j + 2 * u + 1];
-                    pk[u] = pack2(a > 0.f ? a : 0.f, b > 0.f ? b : 0.f);
-                }
-                *reinterpret_cast<uint4*>(s.h1 + canon(row, c0 + j, kH)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            }
-        }
-        async_proxy_fence();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-        // layer 2: four K = 16 steps into columns 64..127
-        if (tid == 0) {
-#pragma unroll
-            for (int kk = 0; kk < kH / 16; ++kk)
-                tc_mma(tmem + 64, tc_desc(s.h1 + 128 * kk, 128, kH * 16), tc_desc(s.w2 + 128 * kk, 128, kH * 16),
-                       kk > 0);
-            tc_commit(&s.mbar);
-        }
-        if (!tc_wait(&s.mbar, phase)) s.stop = 1;
-        phase ^= 1u;
-        tc_fence_after();
-        __syncthreads();
-        if (s.stop) break;
-        // epilogue 2: bias, ReLU, bf16 rounding, layer 3 and the sigmoid
-        float acc = 0.f;
-#pragma unroll
-        for (int c0 = 0; c0 < kH; c0 += 16) {
-            float z[16];
-            tc_ld16(tmem + lane_base + 64u + (uint32_t)c0, z);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float v = z[j] + s.b2[c0 + j];
-                acc += bfr(v > 0.f ? v : 0.f) * s.w3[c0 + j];
-            }
-        }
-        if (base + row < n_rows) score[base + row] = 1.f / (1.f + expf(-(acc + s.b3)));
-        tc_fence_before();
+        float y;
+        if (!tc_tile(s, tmem, phase, y)) break;
+        if (base + tid < n_rows) score[base + tid] = y;
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (wid == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTcCols)
-                     : "memory");
-    if (tid == 0 && s.stop && err) atomicOr(err, kTcErr);
+    tc_teardown(s, tmem, err);
+}
+
+// ---------------------------------------------------------------------------
+// Learned selection in one launch (the query graph's A7 and final A6 step).  A
+// CTA takes 128 shortlist rows at a time -- 128 / S queries of S rows (the
+// top-S by agreement count, ids [Q][S] and counts n[Q]) -- and
+//  1. computes their feature rows straight into the tile's shared-memory
+//     operand: each lane reads its row's id and polygon inputs, then each warp
+//     compares eight pairs at a time (eight 16-byte loads of candidate hashes in
+//     flight per lane) and takes the values from pmh_feature_values, as the
+//     agreement kernel does;
+//  2. scores them with the network on the tensor cores (tc_tile);
+//  3. ranks each query's S scores (key = ~orderable(score) << 32 | id, as the
+//     top-m kernel orders them) and writes the first m ids, -1 padded, and
+//     min(m, n) -- the list the separate feature, forward and top-m launches give.
+// Queries at or past *d_n, or all of them after a failed validation, get empty
+// lists.  Needs K % 32 == 0 and S in {4, 8, .., 128} dividing 128.
+// ---------------------------------------------------------------------------
+constexpr int kSelPairs = 8;  // pairs compared at a time by a warp
+
+// orderable float bits: larger float -> larger unsigned (the top-m kernel's order)
+__device__ __forceinline__ uint32_t f2ord_sel(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+struct SelSmem {
+    TcSmem tc;
+    uint32_t eq[kTcThreads / 32][kSelPairs][4096 / 32];  // equality words, K <= 4096
+    FeatPair fp[kTcThreads / 32][32];                     // each warp's rows' polygon inputs
+    float score[kTcRows];
+};
+
+template <bool kOneQuery>  // S % kSelPairs == 0: the pairs compared together share their query
+__global__ void __launch_bounds__(kTcThreads, 1)
+rerank_select_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ ph,
+                     const int32_t* __restrict__ sl_ids, const int32_t* __restrict__ sl_n, int64_t Q,
+                     const int64_t* __restrict__ d_n, int S, int m, int K, uint32_t T, FeatSrc qf, FeatSrc pf,
+                     const __nv_bfloat16* __restrict__ w1b, const __nv_bfloat16* __restrict__ w2b,
+                     const __nv_bfloat16* __restrict__ w3b, const float* __restrict__ master,
+                     int32_t* __restrict__ out_ids, int32_t* __restrict__ out_n, const int* __restrict__ d_flags,
+                     int* __restrict__ err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SelSmem& ss = *reinterpret_cast<SelSmem*>(smem_raw);
+    TcSmem& s = ss.tc;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t tmem = tc_setup(s, w1b, w2b, w3b, master);
+    const bool failed = d_flags && *d_flags;
+    const int64_t live = failed ? 0 : (d_n ? min(Q, *d_n) : Q);
+    const int G = kTcRows / S;  // queries per tile
+    const int64_t tiles = (Q + G - 1) / G;
+    const int K4 = K / 4;
+    uint32_t phase = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t q0 = tile * G;
+        // 1. feature rows 32 * wid .. 32 * wid + 31: each lane first reads its own row's
+        //    candidate id and polygon inputs (one round of loads for the warp's rows), then
+        //    the warp compares the rows' hashes eight pairs at a time
+        const int rl = 32 * wid + lane;
+        const int64_t ql = q0 + rl / S;
+        const int nql = ql < live ? sl_n[ql] : 0;
+        const bool okl = rl % S < nql;
+        const int32_t pl = okl ? sl_ids[ql * S + rl % S] : 0;
+        if (okl) ss.fp[wid][lane] = pmh_feat_pair(qf, pf, ql, pl);
+        __syncwarp();
+        for (int j0 = 0; j0 < 32; j0 += kSelPairs) {
+            int64_t q[kSelPairs], p[kSelPairs];
+            bool ok[kSelPairs];
+#pragma unroll
+            for (int t = 0; t < kSelPairs; ++t) {
+                q[t] = q0 + (32 * wid + j0 + t) / S;
+                p[t] = __shfl_sync(0xffffffffu, pl, j0 + t);
+                ok[t] = __shfl_sync(0xffffffffu, (int)okl, j0 + t) != 0;
+            }
+            int c[kSelPairs], lt[kSelPairs], gt[kSelPairs];
+            bool grp[kSelPairs];  // K = 128: lane l's four hashes (group l) all equal
+#pragma unroll
+            for (int t = 0; t < kSelPairs; ++t) {
+                c[t] = lt[t] = gt[t] = 0;
+                grp[t] = false;
+            }
+            if (__any_sync(0xffffffffu, okl && lane >= j0 && lane < j0 + kSelPairs)) {
+                for (int base = 0; base < K4; base += 32) {
+                    const int i = base + lane;
+                    constexpr int kU = kOneQuery ? 1 : kSelPairs;  // query rows read
+                    uint4 u[kU], v[kSelPairs];
+#pragma unroll
+                    for (int t = 0; t < kU; ++t) {
+                        u[t] = make_uint4(0u, 0u, 0u, 0u);
+                        if ((kOneQuery || ok[t]) && i < K4) u[t] = __ldg(reinterpret_cast<const uint4*>(qh + q[t] * K) + i);
+                    }
+#pragma unroll
+                    for (int t = 0; t < kSelPairs; ++t) {
+                        v[t] = make_uint4(0u, 0u, 0u, 0u);
+                        if (ok[t] && i < K4) v[t] = __ldg(reinterpret_cast<const uint4*>(ph + p[t] * K) + i);
+                    }
+#pragma unroll
+                    for (int t = 0; t < kSelPairs; ++t) {
+                        const uint4 a = u[kOneQuery ? 0 : t], b = v[t];
+                        unsigned bits = 0;
+                        if (i < K4) {
+                            bits = (unsigned)((a.x == b.x) & (a.x != T)) | ((unsigned)((a.y == b.y) & (a.y != T)) << 1) |
+                                   ((unsigned)((a.z == b.z) & (a.z != T)) << 2) |
+                                   ((unsigned)((a.w == b.w) & (a.w != T)) << 3);
+                            lt[t] += (a.x < b.x) + (a.y < b.y) + (a.z < b.z) + (a.w < b.w);
+                            gt[t] += (a.x > b.x) + (a.y > b.y) + (a.z > b.z) + (a.w > b.w);
+                        }
+                        c[t] += __popc(bits);
+                        grp[t] = bits == 0xFu;
+                        if (K != 128) {
+                            // hash 4i+e is bit (4i+e) % 32 of word i / 8: OR eight lanes' nibbles
+                            unsigned w0 = bits << ((lane & 7) * 4);
+                            w0 |= __shfl_xor_sync(0xffffffffu, w0, 1);
+                            w0 |= __shfl_xor_sync(0xffffffffu, w0, 2);
+                            w0 |= __shfl_xor_sync(0xffffffffu, w0, 4);
+                            if ((lane & 7) == 0 && i < K4) ss.eq[wid][t][i >> 3] = w0;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < kSelPairs; ++t) {
+                const int r = 32 * wid + j0 + t;
+                float lo = 0.f, hi = 0.f;
+                if (ok[t]) {  // warp-uniform
+                    int ct, lt_t, gt_t;
+                    if (K < 1024) {  // the three counts in one sum (10 bits each)
+                        const int sum = __reduce_add_sync(0xffffffffu, c[t] | (lt[t] << 10) | (gt[t] << 20));
+                        ct = sum & 1023;
+                        lt_t = (sum >> 10) & 1023;
+                        gt_t = sum >> 20;
+                    } else {
+                        ct = __reduce_add_sync(0xffffffffu, c[t]);
+                        lt_t = __reduce_add_sync(0xffffffffu, lt[t]);
+                        gt_t = __reduce_add_sync(0xffffffffu, gt[t]);
+                    }
+                    if (K == 128) {
+                        lo = grp[t] ? 1.f : 0.f;
+                        hi = pmh_feature_col(lane, K, ct, lt_t, gt_t, ss.fp[wid][j0 + t]);
+                    } else {
+                        pmh_feature_values(ss.eq[wid][t], K, ct, lt_t, gt_t, ss.fp[wid][j0 + t], lane, lo, hi);
+                    }
+                }
+                s.x[canon(r, lane, kInPad)] = __float2bfloat16_rn(lo);
+                if (lane < 16) s.x[canon(r, 32 + lane, kInPad)] = __float2bfloat16_rn(hi);
+            }
+            __syncwarp();
+        }
+        // 2. the network
+        float y;
+        if (!tc_tile(s, tmem, phase, y)) break;
+        ss.score[tid] = y;
+        __syncthreads();
+        // 3. each query's top m by (score desc, id asc): a pair's rank is the number of
+        //    the query's keys below its own (ids within a list are distinct)
+        for (int gq = wid; gq < G; gq += kTcThreads / 32) {
+            const int64_t q = q0 + gq;
+            if (q >= Q) continue;
+            const int nq = q < live ? sl_n[q] : 0;
+            const int kept = min(m, nq);
+            const float* sc = ss.score + gq * S;
+            const int32_t* ids = sl_ids + q * S;
+            for (int i = lane; i < nq; i += 32) {
+                const uint64_t ki = ((uint64_t)~f2ord_sel(sc[i]) << 32) | (uint32_t)ids[i];
+                int rank = 0;
+                for (int j = 0; j < nq; ++j)
+                    rank += (((uint64_t)~f2ord_sel(sc[j]) << 32) | (uint32_t)ids[j]) < ki;
+                if (rank < m) out_ids[q * m + rank] = ids[i];
+            }
+            for (int i = kept + lane; i < m; i += 32) out_ids[q * m + i] = -1;
+            if (lane == 0) out_n[q] = kept;
+        }
+        __syncthreads();
+    }
+    tc_teardown(s, tmem, err);
 }
 
 }  // namespace
@@ -768,6 +973,33 @@ int pmh_launch_rerank_forward(pmh_rerank r, const uint16_t* feat, int64_t n_rows
 {
     if (n_rows <= 0) return PMH_OK;
     return tc_forward(r, feat, n_rows, score, d_flags, s);
+}
+
+bool pmh_rerank_select_fits(int S, int K) { return S >= 4 && S <= kTcRows && kTcRows % S == 0 && K % 32 == 0 && K <= 4096; }
+
+int pmh_launch_rerank_select(pmh_rerank r, const uint32_t* qh, const uint32_t* ph, const int32_t* sl_ids,
+                             const int32_t* sl_n, int64_t Q, const int64_t* d_n, int S, int m,
+                             const pmh_params* P, FeatSrc qf, FeatSrc pf, int32_t* out_ids, int32_t* out_n,
+                             int* d_flags, cudaStream_t s)
+{
+    if (Q <= 0) return PMH_OK;
+    if (!pmh_rerank_select_fits(S, (int)P->K) || m < 1)
+        return pmh_set_error(PMH_ERR_ARG, "fused selection: S must divide 128 (S >= 4), K a multiple of 32");
+    // at most three CTAs per SM (shared memory), so their tensor-memory allocations
+    // (128 columns each) always fit the SM's 512
+    const size_t smem = std::max<size_t>(sizeof(SelSmem) + 1024, 60 * 1024);
+    auto fn = S % kSelPairs == 0 ? rerank_select_kernel<true> : rerank_select_kernel<false>;
+    PMH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 1;
+    PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTcThreads, smem));
+    const int64_t G = kTcRows / S, tiles = (Q + G - 1) / G;
+    const int blocks =
+        (int)std::min<int64_t>(tiles, (int64_t)std::min(std::max(per_sm, 1), 3) * r->ctx->sm_count);
+    fn<<<std::max(blocks, 1), kTcThreads, smem, s>>>(qh, ph, sl_ids, sl_n, Q, d_n, S, m, (int)P->K, P->T, qf, pf,
+                                                      r->w1b, r->w2b, r->w3b, r->master, out_ids, out_n, d_flags,
+                                                      d_flags);
+    PMH_LAUNCHED("rerank_select_kernel");
+    return PMH_OK;
 }
 
 extern "C" int pmh_rerank_forward(pmh_rerank r, const uint16_t* d_feat, int64_t n_rows,

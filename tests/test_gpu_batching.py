@@ -61,6 +61,19 @@ def small_index(B, ctx):
     return w, db, qs, P, h, index
 
 
+@pytest.fixture(scope="module")
+def small_index_k128(B, ctx):
+    """The small workload signed with K = 128 in 16 bands of 8 (the feature rows' fast
+    group bits: one lane's four hashes per group; the block join)."""
+    w = synth.WORKLOADS["small"]
+    db = synth.make_database(w)
+    qs = synth.make_queries(w, db, 300)
+    P = B.make_params(128, 16, w.T, w.seed, w.lsh_seed)
+    h = B.minhash_sign(ctx, upload(B, ctx, db), P)
+    index = B.lsh_build(ctx, h, P)
+    return w, db, qs, P, h, index
+
+
 def plain_outputs(B, ctx, qs, P, h, index, m):
     qh = B.minhash_sign(ctx, upload(B, ctx, qs), P)
     row_ptr, cand = B.lsh_query(ctx, index, qh)
@@ -181,14 +194,20 @@ def test_query_graph_indexed_large_polygons_refined(B, ctx, orc):
         dbp.close()
 
 
-def test_query_graph_learned_form_matches_plain_calls(B, ctx, small_index):
+@pytest.mark.parametrize("which,m,S", [("small_index", 6, 16), ("small_index", 6, 24), ("small_index", 10, 32),
+                                       ("small_index", 32, 32), ("small_index", 4, 4),
+                                       ("small_index_k128", 10, 32), ("small_index_k128", 6, 24),
+                                       ("small_index_k128", 4, 4), ("small_index_k128", 17, 64)])
+def test_query_graph_learned_form_matches_plain_calls(B, ctx, request, which, m, S):
     """With a reranker the graph's top-m are the m best by predicted Jaccard among the
     shortlist by agreement count: equal to the same chain of plain calls (shortlist top-S,
-    compact lists, features, forward, top-m by score, refinement)."""
-    w, db, qs, P, h, index = small_index
+    compact lists, features, forward, top-m by score, refinement).  Shortlists dividing
+    128 take the graph's fused selection launch (features, tcgen05 scores and ranking in
+    one kernel), S = 24 the separate launches; K = 32 and K = 128 (its fast group bits)."""
+    w, db, qs, P, h, index = request.getfixturevalue(which)
     dbp = upload(B, ctx, db)
     r = B.Reranker(ctx, seed=5)
-    m, S, k = 6, 16, 4
+    k = 4
     g = B.QueryGraph(ctx, index, max_queries=128, max_vertices=20000, cand_capacity=200000, m=m,
                      db=dbp, k=k, rerank=r, shortlist=S)
     try:

@@ -308,8 +308,11 @@ def test_candidates_of_long_rows_bit_exact(B, ctx, orc, bands):
     """Candidate rows of every length the join meets: queries with 3,000, 6,000 and
     20,000 exact duplicates in a database of 29,997 polygons -- rows of at most 3,997
     (the small shared-memory set of 4,096 distinct candidates), of 6,000 to 6,997 (the
-    large set of 16,384) and above 20,000 (the warp merge) -- among ordinary rows;
-    bit-exact against the oracle's bucket definition."""
+    large set of 16,384) and above 20,000 (two id-range passes of the large set) --
+    among ordinary rows; bit-exact against the oracle's bucket definition.  Three
+    fills: a second call that counts again and joins every row (no capacity given),
+    the staged rows copied into place (capacity given), and a lone 6,000-row query
+    whose row does not fit the staging pool (4,096 ids per query) and is joined again."""
     w = synth.WORKLOADS["small"]
     base = synth.make_database(w)
     a, b, c = disjoint_triple(base)
@@ -330,6 +333,21 @@ def test_candidates_of_long_rows_bit_exact(B, ctx, orc, bands):
     assert 3000 <= lens[0] <= 3997 and 6000 <= lens[1] <= 6997 and lens[2] >= 20000
     assert np.array_equal(row_ptr.cpu().numpy(), rp_ref)
     assert np.array_equal(cand.cpu().numpy(), cand_ref)
+    row_ptr, cand = B.lsh_query(ctx, index, qh, capacity=int(rp_ref[-1]))
+    assert np.array_equal(row_ptr.cpu().numpy(), rp_ref)
+    assert np.array_equal(cand.cpu().numpy(), cand_ref)
+    if bands >= 16:
+        row_ptr, cand = B.lsh_query(ctx, index, qh[1:2].contiguous(), capacity=int(lens[1]))
+        assert np.array_equal(cand.cpu().numpy(), cand_ref[rp_ref[1]:rp_ref[2]])
+        # the query graph: its staging pool holds the candidate capacity
+        g = B.QueryGraph(ctx, index, qs.n, qs.xy.shape[0], int(rp_ref[-1]) + 1024, 8)
+        try:
+            g.run(torch.from_numpy(qs.xy).to(DEV), torch.from_numpy(qs.offsets).to(DEV))
+            assert g.status()[0] == 0
+            assert np.array_equal(g.row_ptr[:qs.n + 1].cpu().numpy(), rp_ref)
+            assert np.array_equal(g.cand[:int(rp_ref[-1])].cpu().numpy(), cand_ref)
+        finally:
+            g.close()
     index.close()
 
 
@@ -354,12 +372,23 @@ def test_agreement_on_dense_pairs_with_sentinels(B, ctx, orc):
 
 def test_topm_large_rows_and_scores(B, ctx):
     rng = np.random.default_rng(4)
-    lens = [0, 1, 7, 3000, 5000]
+    # rows 5..8 for the count form's threshold selection: one long tie (every count
+    # equal: the gathered set passes 2,048 and the row takes the merge form), mostly
+    # zero counts (the threshold is 0 for large m), counts up to 4,096, and a tie at
+    # the threshold that still fits the gathered set
+    lens = [0, 1, 7, 3000, 5000, 6000, 4000, 2500, 2300]
     row_ptr = np.zeros(len(lens) + 1, np.int64)
     row_ptr[1:] = np.cumsum(lens)
     E = int(row_ptr[-1])
     cand = rng.integers(0, 1 << 30, E).astype(np.int32)
     count = rng.integers(0, 40, E).astype(np.uint16)
+    r = lambda q: slice(row_ptr[q], row_ptr[q + 1])
+    count[r(5)] = 7
+    count[r(6)] = 0
+    count[r(6)][rng.choice(4000, 30, replace=False)] = rng.integers(1, 128, 30).astype(np.uint16)
+    count[r(7)] = rng.integers(0, 4097, 2500).astype(np.uint16)
+    count[r(8)] = np.where(rng.random(2300) < 0.5, 3, rng.integers(0, 3, 2300)).astype(np.uint16)
+    count[r(8)][:5] = 9
     score = rng.random(E).astype(np.float32)
     score[::5] = score[1::5][: len(score[::5])] if E > 5 else score[::5]
     t = lambda a: torch.from_numpy(a).to(DEV)

@@ -36,12 +36,10 @@ def bf16_bits_to_float(bits: np.ndarray) -> np.ndarray:
     return (bits.astype(np.uint16).astype(np.uint32) << 16).view(np.float32)
 
 
-@pytest.fixture(scope="module")
-def pairs(B, ctx, orc):
+def feature_pairs(B, ctx, K, bands):
     w = synth.WORKLOADS["small"]
     db = synth.make_database(w)
     qs = synth.make_queries(w, db)
-    K, bands = 64, 64          # one-hash bands: many candidates per query
     P = B.make_params(K, bands, w.T, w.seed, w.lsh_seed)
     dbp, qp = upload(B, ctx, db), upload(B, ctx, qs)
     h = B.minhash_sign(ctx, dbp, P)
@@ -52,9 +50,16 @@ def pairs(B, ctx, orc):
     return w, db, qs, P, dbp, qp, h, qh, row_ptr, cand, feat
 
 
-def test_features_match_oracle_values(B, ctx, orc, pairs):
-    w, db, qs, P, dbp, qp, h, qh, row_ptr, cand, feat = pairs
-    K = P.K
+@pytest.fixture(scope="module")
+def pairs(B, ctx):
+    return feature_pairs(B, ctx, 64, 64)   # one-hash bands: many candidates per query
+
+
+@pytest.mark.parametrize("K,bands", [(64, 64), (128, 64)])
+def test_features_match_oracle_values(B, ctx, orc, pairs, K, bands):
+    """Feature rows against a recomputation from oracle hashes and areas; K = 128 takes
+    the kernel's path where one lane holds a group's four hashes."""
+    w, db, qs, P, dbp, qp, h, qh, row_ptr, cand, feat = pairs if K == 64 else feature_pairs(B, ctx, K, bands)
     qh_ref = orc.sign(qs.xy, qs.offsets, w.seed, K, w.T, nthreads=8)
     h_ref = orc.sign(db.xy, db.offsets, w.seed, K, w.T, nthreads=8)
     rp, cd = row_ptr.cpu().numpy(), cand.cpu().numpy()
