@@ -229,7 +229,7 @@ constexpr int kSmallRowMax = JoinShape<false>::kMaxUnique;
 struct JoinStage {
     int32_t* pool = nullptr;
     int64_t pool_ints = 0;
-    unsigned long long* cursor = nullptr;
+    unsigned long long* cursor = nullptr;  // [0]: pool ids handed out, [1]: large-set row ticket
     int64_t* where = nullptr;
 };
 
@@ -377,6 +377,7 @@ __device__ int join_walk(const uint32_t* __restrict__ qh, int K, int bands, int 
             jj[u] = lo;
             pp[u] = in[u] ? ids[jb.lo[lo] + (g - jb.off[lo])] : 0;
         }
+        int added = 0;  // the warp's new ids, added to the set's count once per chunk pair
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int32_t pe = pp[u];
@@ -385,7 +386,7 @@ __device__ int join_walk(const uint32_t* __restrict__ qh, int K, int bands, int 
                 for (int probe = 0; probe < kJoinTable; ++probe, h = (h + 1) & (kJoinTable - 1)) {
                     const int32_t old = atomicCAS(&table[h], kNone, pe);
                     if (old == kNone) {
-                        atomicAdd(n_unique, 1);
+                        ++added;
                         break;
                     }
                     if (old == pe) break;
@@ -393,6 +394,8 @@ __device__ int join_walk(const uint32_t* __restrict__ qh, int K, int bands, int 
                 }
             }
         }
+        added = __reduce_add_sync(0xffffffffu, added);
+        if (lane == 0 && added) atomicAdd(n_unique, added);
     }
     __syncthreads();
     return *n_unique;
@@ -468,8 +471,19 @@ join_kernel(const uint32_t* __restrict__ qhashes, int64_t Q, int K, int bands, i
     __shared__ long long stage_off;
     __shared__ int wsum[S::kThreads / 32];
     __shared__ JoinBands jb;
+    __shared__ long long next_q;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int64_t q = blockIdx.x; q < Q; q += gridDim.x) {
+    // the large set's count pass takes rows from a ticket (its rows' sizes vary several
+    // times over); the other passes step through the rows
+    unsigned long long* ticket = (!kWrite && kBig && st.cursor) ? st.cursor + 1 : nullptr;
+    for (int64_t q = blockIdx.x;; q += gridDim.x) {
+        if (ticket) {
+            __syncthreads();
+            if (threadIdx.x == 0) next_q = (long long)atomicAdd(ticket, 1ull);
+            __syncthreads();
+            q = next_q;
+        }
+        if (q >= Q) break;
         const bool skip = (d_n && q >= *d_n) || (d_flags && (*d_flags & 7));
         if (skip) {
             if (!kWrite && !kBig && threadIdx.x == 0) {
@@ -748,7 +762,7 @@ size_t pmh_join_stage_bytes(int64_t Q, int64_t pool_ints)
     return 16 + sizeof(int64_t) * (size_t)Q + sizeof(int32_t) * (size_t)pool_ints;
 }
 
-// cursor (16 bytes), where [Q], pool [pool_ints] laid out in one buffer
+// cursor and ticket (16 bytes), where [Q], pool [pool_ints] laid out in one buffer
 static JoinStage stage_view(void* buf, int64_t Q, int64_t pool_ints)
 {
     JoinStage st;
@@ -779,8 +793,8 @@ int pmh_launch_query(pmh_index X, const uint32_t* qh, int64_t Q, const int64_t* 
                 copy_rows_kernel<<<cblocks, 256, 0, s>>>(st, Q, row_ptr, cand, cap, d_n, d_flags);
                 PMH_LAUNCHED("copy_rows_kernel");
             }
-        } else if (st.cursor) {
-            PMH_CUDA_TRY(cudaMemsetAsync(st.cursor, 0, sizeof(unsigned long long), s));
+        } else if (st.cursor) {  // the pool cursor and the large set's row ticket
+            PMH_CUDA_TRY(cudaMemsetAsync(st.cursor, 0, 2 * sizeof(unsigned long long), s));
         }
         PMH_TRY(launch_join<false>(X, qh, Q, d_n, counts, row_ptr, cand, cap, st, d_flags, write, s));
         return launch_join<true>(X, qh, Q, d_n, counts, row_ptr, cand, cap, st, d_flags, write, s);

@@ -519,8 +519,16 @@ __device__ uint32_t tc_setup(TcSmem& s, const __nv_bfloat16* __restrict__ w1b,
                              const float* __restrict__ master)
 {
     const int tid = threadIdx.x, wid = tid >> 5;
-    for (int i = tid; i < kH * kInPad; i += kTcThreads) s.w1[canon(i / kInPad, i % kInPad, kInPad)] = w1b[i];
-    for (int i = tid; i < kH * kH; i += kTcThreads) s.w2[canon(i / kH, i % kH, kH)] = w2b[i];
+    // eight consecutive inputs of an output row are 16 contiguous bytes on both sides
+    for (int i = tid; i < kH * kInPad / 8; i += kTcThreads) {
+        const int o = i / (kInPad / 8), c = 8 * (i % (kInPad / 8));
+        *reinterpret_cast<uint4*>(s.w1 + canon(o, c, kInPad)) =
+            __ldg(reinterpret_cast<const uint4*>(w1b + o * kInPad + c));
+    }
+    for (int i = tid; i < kH * kH / 8; i += kTcThreads) {
+        const int o = i / (kH / 8), c = 8 * (i % (kH / 8));
+        *reinterpret_cast<uint4*>(s.w2 + canon(o, c, kH)) = __ldg(reinterpret_cast<const uint4*>(w2b + o * kH + c));
+    }
     for (int i = tid; i < kH; i += kTcThreads) {
         s.b1[i] = master[OFF_B1 + i];
         s.b2[i] = master[OFF_B2 + i];
