@@ -22,11 +22,13 @@ namespace {
 
 constexpr int kMaxK = 4096;
 constexpr int kAgreeWarps = 4;
-constexpr int kAgreeChunk = 16;  // consecutive pairs per warp turn
+constexpr int kAgreeChunk = 64;  // consecutive pairs per warp turn
 constexpr int kAgreeGroup = 4;   // pairs compared at a time (their loads in flight together)
 
 // Warps take chunks of kAgreeChunk consecutive pairs (the row of the first by
-// binary search over row_ptr, then stepping on), four pairs at a time.  Per pair:
+// binary search over row_ptr); 32 pairs at a time each lane reads one pair's
+// candidate id and steps its row on from there, and the warp then compares the
+// pairs four at a time (ids and rows by shuffle).  Per pair:
 // equality bits of the K hashes (16-byte loads when K % 4 == 0), the count (warp
 // sum), the full-match bits of the first 32 bands and, optionally, the reranker's
 // feature row.
@@ -55,122 +57,131 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
             if (row_ptr[mid] <= x0) lo = mid;
             else hi = mid;
         }
-        int64_t q = lo;
-        for (int64_t x = x0; x < x1; x += kAgreeGroup) {
-            int64_t qq[kAgreeGroup], pp[kAgreeGroup];
-            bool ok[kAgreeGroup];
-#pragma unroll
-            for (int t = 0; t < kAgreeGroup; ++t) {
-                ok[t] = x + t < x1;
-                if (ok[t])
-                    while (row_ptr[q + 1] <= x + t) ++q;
-                qq[t] = q;
-                pp[t] = ok[t] ? cand[x + t] : 0;
+        const int64_t q0 = lo;
+        for (int64_t xb = x0; xb < x1; xb += 32) {
+            const int nvalid = (int)min((int64_t)32, x1 - xb);
+            const int64_t xl = xb + lane;
+            int64_t ql = q0;
+            int32_t pl = 0;
+            if (lane < nvalid) {
+                while (row_ptr[ql + 1] <= xl) ++ql;
+                pl = cand[xl];
             }
-            // lt / gt: hashes with h(q) < h(p) / h(q) > h(p); grp: K = 128, lane l's four
-            // hashes (group l of the features' 32-group split) all equal
-            int c[kAgreeGroup] = {0, 0, 0, 0}, lt[kAgreeGroup] = {0, 0, 0, 0}, gt[kAgreeGroup] = {0, 0, 0, 0};
-            bool grp[kAgreeGroup] = {false, false, false, false};
-            if ((K & 3) == 0) {
-                for (int base = 0; base < K4; base += 32) {
-                    const int i = base + lane;
-                    uint4 u[kAgreeGroup], v[kAgreeGroup];
-#pragma unroll
-                    for (int t = 0; t < kAgreeGroup; ++t) {
-                        u[t] = v[t] = make_uint4(0u, 0u, 0u, 0u);
-                        if (ok[t] && i < K4) {
-                            u[t] = __ldg(reinterpret_cast<const uint4*>(qh + qq[t] * K) + i);
-                            v[t] = __ldg(reinterpret_cast<const uint4*>(ph + pp[t] * K) + i);
-                        }
-                    }
-#pragma unroll
-                    for (int t = 0; t < kAgreeGroup; ++t) {
-                        unsigned bits = 0;
-                        if (i < K4) {
-                            bits = (unsigned)((u[t].x == v[t].x) & (u[t].x != T)) |
-                                   ((unsigned)((u[t].y == v[t].y) & (u[t].y != T)) << 1) |
-                                   ((unsigned)((u[t].z == v[t].z) & (u[t].z != T)) << 2) |
-                                   ((unsigned)((u[t].w == v[t].w) & (u[t].w != T)) << 3);
-                            if (feat) {
-                                lt[t] += (u[t].x < v[t].x) + (u[t].y < v[t].y) + (u[t].z < v[t].z) +
-                                         (u[t].w < v[t].w);
-                                gt[t] += (u[t].x > v[t].x) + (u[t].y > v[t].y) + (u[t].z > v[t].z) +
-                                         (u[t].w > v[t].w);
+            for (int t0 = 0; t0 < nvalid; t0 += kAgreeGroup) {
+                const int64_t x = xb + t0;
+                int64_t qq[kAgreeGroup], pp[kAgreeGroup];
+                bool ok[kAgreeGroup];
+    #pragma unroll
+                for (int t = 0; t < kAgreeGroup; ++t) {
+                    ok[t] = t0 + t < nvalid;
+                    qq[t] = __shfl_sync(0xffffffffu, ql, (t0 + t) & 31);
+                    pp[t] = __shfl_sync(0xffffffffu, pl, (t0 + t) & 31);
+                }
+                // lt / gt: hashes with h(q) < h(p) / h(q) > h(p); grp: K = 128, lane l's four
+                // hashes (group l of the features' 32-group split) all equal
+                int c[kAgreeGroup] = {0, 0, 0, 0}, lt[kAgreeGroup] = {0, 0, 0, 0}, gt[kAgreeGroup] = {0, 0, 0, 0};
+                bool grp[kAgreeGroup] = {false, false, false, false};
+                if ((K & 3) == 0) {
+                    for (int base = 0; base < K4; base += 32) {
+                        const int i = base + lane;
+                        uint4 u[kAgreeGroup], v[kAgreeGroup];
+    #pragma unroll
+                        for (int t = 0; t < kAgreeGroup; ++t) {
+                            u[t] = v[t] = make_uint4(0u, 0u, 0u, 0u);
+                            if (ok[t] && i < K4) {
+                                u[t] = __ldg(reinterpret_cast<const uint4*>(qh + qq[t] * K) + i);
+                                v[t] = __ldg(reinterpret_cast<const uint4*>(ph + pp[t] * K) + i);
                             }
                         }
-                        c[t] += __popc(bits);
-                        grp[t] = bits == 0xFu;
-                        if (need_eq) {
-                            // hash 4i+e is bit (4i+e) % 32 of word i / 8: OR eight lanes' nibbles
-                            unsigned w0 = bits << ((lane & 7) * 4);
-                            w0 |= __shfl_xor_sync(0xffffffffu, w0, 1);
-                            w0 |= __shfl_xor_sync(0xffffffffu, w0, 2);
-                            w0 |= __shfl_xor_sync(0xffffffffu, w0, 4);
-                            if ((lane & 7) == 0 && i < K4) eqbits[wid][t][i >> 3] = w0;
+    #pragma unroll
+                        for (int t = 0; t < kAgreeGroup; ++t) {
+                            unsigned bits = 0;
+                            if (i < K4) {
+                                bits = (unsigned)((u[t].x == v[t].x) & (u[t].x != T)) |
+                                       ((unsigned)((u[t].y == v[t].y) & (u[t].y != T)) << 1) |
+                                       ((unsigned)((u[t].z == v[t].z) & (u[t].z != T)) << 2) |
+                                       ((unsigned)((u[t].w == v[t].w) & (u[t].w != T)) << 3);
+                                if (feat) {
+                                    lt[t] += (u[t].x < v[t].x) + (u[t].y < v[t].y) + (u[t].z < v[t].z) +
+                                             (u[t].w < v[t].w);
+                                    gt[t] += (u[t].x > v[t].x) + (u[t].y > v[t].y) + (u[t].z > v[t].z) +
+                                             (u[t].w > v[t].w);
+                                }
+                            }
+                            c[t] += __popc(bits);
+                            grp[t] = bits == 0xFu;
+                            if (need_eq) {
+                                // hash 4i+e is bit (4i+e) % 32 of word i / 8: OR eight lanes' nibbles
+                                unsigned w0 = bits << ((lane & 7) * 4);
+                                w0 |= __shfl_xor_sync(0xffffffffu, w0, 1);
+                                w0 |= __shfl_xor_sync(0xffffffffu, w0, 2);
+                                w0 |= __shfl_xor_sync(0xffffffffu, w0, 4);
+                                if ((lane & 7) == 0 && i < K4) eqbits[wid][t][i >> 3] = w0;
+                            }
                         }
                     }
-                }
-            } else {
-                for (int base = 0; base < K; base += 32) {
-                    const int i = base + lane;
-#pragma unroll
-                    for (int t = 0; t < kAgreeGroup; ++t) {
-                        const bool in = ok[t] && i < K;
-                        const uint32_t a = in ? qh[qq[t] * K + i] : 0u, b = in ? ph[pp[t] * K + i] : 0u;
-                        const bool eq = in && a == b && a != T;
-                        const unsigned bal = __ballot_sync(0xffffffffu, eq);
-                        c[t] += eq;
-                        if (feat && in) {
-                            lt[t] += a < b;
-                            gt[t] += a > b;
-                        }
-                        if (lane == 0) eqbits[wid][t][base / 32] = bal;
-                    }
-                }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int t = 0; t < kAgreeGroup; ++t) {
-                if (!ok[t]) continue;  // warp-uniform
-                const int64_t xt = x + t;
-                int ct, ltt = 0, gtt = 0;
-                if (feat && K < 1024) {  // the three counts in one sum (10 bits each)
-                    const int sum = __reduce_add_sync(0xffffffffu, c[t] | (lt[t] << 10) | (gt[t] << 20));
-                    ct = sum & 1023;
-                    ltt = (sum >> 10) & 1023;
-                    gtt = sum >> 20;
                 } else {
-                    ct = __reduce_add_sync(0xffffffffu, c[t]);
-                    if (feat) {
-                        ltt = __reduce_add_sync(0xffffffffu, lt[t]);
-                        gtt = __reduce_add_sync(0xffffffffu, gt[t]);
+                    for (int base = 0; base < K; base += 32) {
+                        const int i = base + lane;
+    #pragma unroll
+                        for (int t = 0; t < kAgreeGroup; ++t) {
+                            const bool in = ok[t] && i < K;
+                            const uint32_t a = in ? qh[qq[t] * K + i] : 0u, b = in ? ph[pp[t] * K + i] : 0u;
+                            const bool eq = in && a == b && a != T;
+                            const unsigned bal = __ballot_sync(0xffffffffu, eq);
+                            c[t] += eq;
+                            if (feat && in) {
+                                lt[t] += a < b;
+                                gt[t] += a > b;
+                            }
+                            if (lane == 0) eqbits[wid][t][base / 32] = bal;
+                        }
                     }
                 }
-                if (count && lane == 0) count[xt] = (uint16_t)ct;
-                if (bandmask) {
-                    bool all = lane < bands;
-                    for (int r = 0; r < rows && all; ++r) {
-                        const int k = lane * rows + r;
-                        all = (eqbits[wid][t][k >> 5] >> (k & 31)) & 1u;
-                    }
-                    const unsigned mb = __ballot_sync(0xffffffffu, all);
-                    if (lane == 0) bandmask[xt] = mb;
-                }
-                if (feat) {
-                    float flo, fhi;
-                    if (K == 128) {
-                        flo = grp[t] ? 1.f : 0.f;
-                        fhi = pmh_feature_col(lane, K, ct, ltt, gtt, pmh_feat_pair(qf, pf, qq[t], pp[t]));
+                __syncwarp();
+    #pragma unroll
+                for (int t = 0; t < kAgreeGroup; ++t) {
+                    if (!ok[t]) continue;  // warp-uniform
+                    const int64_t xt = x + t;
+                    int ct, ltt = 0, gtt = 0;
+                    if (feat && K < 1024) {  // the three counts in one sum (10 bits each)
+                        const int sum = __reduce_add_sync(0xffffffffu, c[t] | (lt[t] << 10) | (gt[t] << 20));
+                        ct = sum & 1023;
+                        ltt = (sum >> 10) & 1023;
+                        gtt = sum >> 20;
                     } else {
-                        pmh_feature_values(eqbits[wid][t], K, ct, ltt, gtt, pmh_feat_pair(qf, pf, qq[t], pp[t]),
-                                           lane, flo, fhi);
+                        ct = __reduce_add_sync(0xffffffffu, c[t]);
+                        if (feat) {
+                            ltt = __reduce_add_sync(0xffffffffu, lt[t]);
+                            gtt = __reduce_add_sync(0xffffffffu, gt[t]);
+                        }
                     }
-                    __nv_bfloat16* f = feat + xt * 48;
-                    f[lane] = __float2bfloat16_rn(flo);
-                    if (lane < 16) f[32 + lane] = __float2bfloat16_rn(fhi);
+                    if (count && lane == 0) count[xt] = (uint16_t)ct;
+                    if (bandmask) {
+                        bool all = lane < bands;
+                        for (int r = 0; r < rows && all; ++r) {
+                            const int k = lane * rows + r;
+                            all = (eqbits[wid][t][k >> 5] >> (k & 31)) & 1u;
+                        }
+                        const unsigned mb = __ballot_sync(0xffffffffu, all);
+                        if (lane == 0) bandmask[xt] = mb;
+                    }
+                    if (feat) {
+                        float flo, fhi;
+                        if (K == 128) {
+                            flo = grp[t] ? 1.f : 0.f;
+                            fhi = pmh_feature_col(lane, K, ct, ltt, gtt, pmh_feat_pair(qf, pf, qq[t], pp[t]));
+                        } else {
+                            pmh_feature_values(eqbits[wid][t], K, ct, ltt, gtt, pmh_feat_pair(qf, pf, qq[t], pp[t]),
+                                               lane, flo, fhi);
+                        }
+                        __nv_bfloat16* f = feat + xt * 48;
+                        f[lane] = __float2bfloat16_rn(flo);
+                        if (lane < 16) f[32 + lane] = __float2bfloat16_rn(fhi);
+                    }
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
 }
