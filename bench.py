@@ -457,7 +457,9 @@ def search_quality(args, w, B, ctx, db, qs, h, dbp, q_xy, q_off, P):
         s = ev.Searcher(ctx, index, params, dbp, h, shortlist=max(args.shortlist, args.search_shortlist))
         feat, lab = ev.training_pairs(ctx, s, tp)
         rr = B.Reranker(ctx, seed=1)
-        (losses, t_train) = ev.timed(lambda: ev.train_reranker(rr, feat, lab, epochs=16))
+        # 24 epochs at the default rate, then 8 at a quarter of it (the same Adam moments)
+        (losses, t_train) = ev.timed(lambda: ev.train_reranker(rr, feat, lab, epochs=24) +
+                                     ev.train_reranker(rr, feat, lab, epochs=8, lr=5e-4, seed=1))
         learned = ev.graph_sweep(ctx, index, dbp, batches, cap, truth, n_eval, ms, rerank=rr,
                                  shortlist=args.search_shortlist)
         rr.close()

@@ -339,8 +339,14 @@ typedef struct {
     pmh_polys db;        /* the indexed polygon set (refinement, learned features) */
     pmh_rerank rerank;   /* learned form (NULL: rank by agreement count) */
     int32_t shortlist;   /* learned form: candidates by count rescored per query */
-    int32_t reserved;
+    int32_t options;     /* bit 0: learned form in one fused launch (PMH_QGRAPH_FUSED_SELECT) */
 } pmh_qgraph_config;
+/* options bit 0 (learned form, shortlist dividing 128, K a multiple of 32 up to
+ * 4,096): features, scores and the top-m by score in one launch instead of four
+ * (feature rows, forward pass, top-m, with the lists compacted first); the same
+ * lists either way.  Off by default: on the 10M combined workload the separate
+ * launches are the faster form. */
+#define PMH_QGRAPH_FUSED_SELECT 1
 int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_config* cfg,
                       pmh_qgraph* out);
 int pmh_qgraph_run(pmh_qgraph graph, const int32_t* xy, const int64_t* offsets, int64_t n_queries,

@@ -40,7 +40,10 @@ class QGraphConfig(ctypes.Structure):
     _fields_ = [("max_queries", ctypes.c_int64), ("max_vertices", ctypes.c_int64),
                 ("cand_capacity", ctypes.c_int64), ("m", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("db", ctypes.c_void_p), ("rerank", ctypes.c_void_p), ("shortlist", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("options", ctypes.c_int32)]
+
+
+QGRAPH_FUSED_SELECT = 1
 
 
 FLAG_STREAM_INDEX = 1
@@ -566,11 +569,11 @@ class QueryGraph:
 
     def __init__(self, ctx: Context, index: Index, max_queries: int, max_vertices: int,
                  cand_capacity: int, m: int, db: "Polys | None" = None, k: int = 0,
-                 rerank: "Reranker | None" = None, shortlist: int = 64):
+                 rerank: "Reranker | None" = None, shortlist: int = 64, fused_select: bool = False):
         h = _P()
         cfg = QGraphConfig(max_queries, max_vertices, cand_capacity, m, k,
                            db.handle if db else None, rerank.handle if rerank else None,
-                           shortlist if rerank else 0, 0)
+                           shortlist if rerank else 0, QGRAPH_FUSED_SELECT if fused_select else 0)
         _check(load().pmh_qgraph_create(ctx.handle, index.handle, ctypes.byref(cfg), ctypes.byref(h)))
         self.ctx, self.index, self.db, self.rerank, self.handle = ctx, index, db, rerank, h
         ctx._adopt(self)

@@ -32,6 +32,7 @@ constexpr int kAgreeGroup = 4;   // pairs compared at a time (their loads in fli
 // equality bits of the K hashes (16-byte loads when K % 4 == 0), the count (warp
 // sum), the full-match bits of the first 32 bands and, optionally, the reranker's
 // feature row.
+template <bool kFeat>  // feature rows written (a build without their work for the counts alone)
 __global__ void __launch_bounds__(kAgreeWarps * 32, 6)
 agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ ph,
                   const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ cand, int64_t Q,
@@ -47,7 +48,7 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
     const int K4 = K / 4;
     // equality words in shared memory: for the band bits, and for the features' groups
     // unless K = 128 (then lane l holds group l's four hashes)
-    const bool need_eq = bandmask || (feat && K != 128);
+    const bool need_eq = bandmask || (kFeat && K != 128);
     for (int64_t ch = (int64_t)blockIdx.x * kAgreeWarps + wid; ch * kAgreeChunk < total; ch += nwarps) {
         const int64_t x0 = ch * kAgreeChunk, x1 = min(x0 + kAgreeChunk, total);
         // the row holding pair x0: the last q with row_ptr[q] <= x0
@@ -101,7 +102,7 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
                                        ((unsigned)((u[t].y == v[t].y) & (u[t].y != T)) << 1) |
                                        ((unsigned)((u[t].z == v[t].z) & (u[t].z != T)) << 2) |
                                        ((unsigned)((u[t].w == v[t].w) & (u[t].w != T)) << 3);
-                                if (feat) {
+                                if (kFeat) {
                                     lt[t] += (u[t].x < v[t].x) + (u[t].y < v[t].y) + (u[t].z < v[t].z) +
                                              (u[t].w < v[t].w);
                                     gt[t] += (u[t].x > v[t].x) + (u[t].y > v[t].y) + (u[t].z > v[t].z) +
@@ -130,7 +131,7 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
                             const bool eq = in && a == b && a != T;
                             const unsigned bal = __ballot_sync(0xffffffffu, eq);
                             c[t] += eq;
-                            if (feat && in) {
+                            if (kFeat && in) {
                                 lt[t] += a < b;
                                 gt[t] += a > b;
                             }
@@ -144,14 +145,14 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
                     if (!ok[t]) continue;  // warp-uniform
                     const int64_t xt = x + t;
                     int ct, ltt = 0, gtt = 0;
-                    if (feat && K < 1024) {  // the three counts in one sum (10 bits each)
+                    if (kFeat && K < 1024) {  // the three counts in one sum (10 bits each)
                         const int sum = __reduce_add_sync(0xffffffffu, c[t] | (lt[t] << 10) | (gt[t] << 20));
                         ct = sum & 1023;
                         ltt = (sum >> 10) & 1023;
                         gtt = sum >> 20;
                     } else {
                         ct = __reduce_add_sync(0xffffffffu, c[t]);
-                        if (feat) {
+                        if (kFeat) {
                             ltt = __reduce_add_sync(0xffffffffu, lt[t]);
                             gtt = __reduce_add_sync(0xffffffffu, gt[t]);
                         }
@@ -166,7 +167,7 @@ agree_rows_kernel(const uint32_t* __restrict__ qh, const uint32_t* __restrict__ 
                         const unsigned mb = __ballot_sync(0xffffffffu, all);
                         if (lane == 0) bandmask[xt] = mb;
                     }
-                    if (feat) {
+                    if (kFeat) {
                         float flo, fhi;
                         if (K == 128) {
                             flo = grp[t] ? 1.f : 0.f;
@@ -388,9 +389,10 @@ int pmh_launch_agree_features(pmh_ctx ctx, const uint32_t* qh, const uint32_t* p
 {
     if (Q <= 0) return PMH_OK;
     const int blocks = ctx->sm_count * 16;  // persistent: pair chunks are handed out in turn
-    agree_rows_kernel<<<blocks, kAgreeWarps * 32, 0, s>>>(
-        qh, ph, row_ptr, cand, Q, cap, (int)P->K, (int)P->bands, (int)P->rows, P->T, count, bandmask,
-        reinterpret_cast<__nv_bfloat16*>(feat), qf, pf, d_flags);
+    auto fn = feat ? agree_rows_kernel<true> : agree_rows_kernel<false>;
+    fn<<<blocks, kAgreeWarps * 32, 0, s>>>(qh, ph, row_ptr, cand, Q, cap, (int)P->K, (int)P->bands, (int)P->rows,
+                                           P->T, count, bandmask, reinterpret_cast<__nv_bfloat16*>(feat), qf,
+                                           pf, d_flags);
     PMH_LAUNCHED("agree_rows_kernel");
     return PMH_OK;
 }

@@ -51,6 +51,7 @@ struct pmh_qgraph_s {
     // learned form: shortlist by count -> compact lists -> features -> scores
     pmh_rerank rerank = nullptr;
     int shortlist = 0;
+    bool fused_select = false;  // features, scores and top-m in one launch
     int32_t* sl_ids = nullptr;
     int32_t* sl_n = nullptr;
     int64_t* sl_counts = nullptr;
@@ -117,6 +118,11 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_
     if (cfg->rerank && (S < m || S > 1024 || index->params.K % 32 != 0 || db->n != index->n))
         return pmh_set_error(PMH_ERR_ARG, "learned form: m <= shortlist <= 1024, K a multiple of 32, "
                                           "db the indexed set");
+    if (cfg->options & ~PMH_QGRAPH_FUSED_SELECT) return pmh_set_error(PMH_ERR_ARG, "unknown graph options");
+    if (cfg->rerank && (cfg->options & PMH_QGRAPH_FUSED_SELECT) &&
+        !pmh_rerank_select_fits(S, (int)index->params.K))
+        return pmh_set_error(PMH_ERR_ARG, "fused selection: the shortlist must divide 128 (at least 4), K a "
+                                          "multiple of 32 up to 4,096");
     pmh_qgraph g = new pmh_qgraph_s();
     g->ctx = ctx;
     g->device = ctx->device;
@@ -124,6 +130,7 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_
     g->db = db;
     g->rerank = cfg->rerank;
     g->shortlist = S;
+    g->fused_select = cfg->rerank && (cfg->options & PMH_QGRAPH_FUSED_SELECT);
     g->P = index->params;
     g->maxQ = max_queries;
     g->maxV = max_vertices;
@@ -230,7 +237,7 @@ extern "C" int pmh_qgraph_create(pmh_ctx ctx, pmh_index index, const pmh_qgraph_
         if (rc == PMH_OK)
             rc = pmh_launch_poly_feat(ctx->sm_count, g->area2, g->off, Q, g->d_n, g->qfeat, cs);
         const FeatSrc qf{g->qfeat, g->bbox, g->area2}, pf{db->feat, db->bbox, db->area2};
-        if (pmh_rerank_select_fits(S, (int)K)) {
+        if (g->fused_select) {
             // features, scores and the top-m by score in one launch
             if (rc == PMH_OK)
                 rc = pmh_launch_rerank_select(g->rerank, g->hashes, index->hashes, g->sl_ids, g->sl_n, Q,

@@ -998,6 +998,8 @@ int pmh_launch_rerank_select(pmh_rerank r, const uint32_t* qh, const uint32_t* p
     const size_t smem = std::max<size_t>(sizeof(SelSmem) + 1024, 60 * 1024);
     auto fn = S % kSelPairs == 0 ? rerank_select_kernel<true> : rerank_select_kernel<false>;
     PMH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the whole carveout as shared memory, so that three CTAs fit an SM
+    PMH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     int per_sm = 1;
     PMH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTcThreads, smem));
     const int64_t G = kTcRows / S, tiles = (Q + G - 1) / G;

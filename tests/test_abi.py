@@ -87,10 +87,10 @@ int main(void) {
            offsetof(pmh_qgraph_config, cand_capacity), offsetof(pmh_qgraph_config, m),
            offsetof(pmh_qgraph_config, k), offsetof(pmh_qgraph_config, db),
            offsetof(pmh_qgraph_config, rerank), offsetof(pmh_qgraph_config, shortlist),
-           offsetof(pmh_qgraph_config, reserved));
-    printf("%d %d %d %d %d %u %u %d\n", PMH_SIGN_VARIANTS, PMH_RERANK_IN, PMH_RERANK_HIDDEN,
+           offsetof(pmh_qgraph_config, options));
+    printf("%d %d %d %d %d %u %u %d %d\n", PMH_SIGN_VARIANTS, PMH_RERANK_IN, PMH_RERANK_HIDDEN,
            PMH_RERANK_PARAMS, PMH_NOALLOC_MAX_POLYS, PMH_FLAG_STREAM_INDEX,
-           PMH_FLAG_COVERAGE_MASK, PMH_ERR_CAPACITY);
+           PMH_FLAG_COVERAGE_MASK, PMH_ERR_CAPACITY, PMH_QGRAPH_FUSED_SELECT);
     return 0;
 }
 ''')
@@ -111,4 +111,4 @@ int main(void) {
     consts = [int(v) for v in lines[2].split()]
     assert consts == [binding.SIGN_VARIANTS, binding.RERANK_IN, binding.RERANK_HIDDEN,
                       binding.RERANK_PARAMS, binding.NOALLOC_MAX_POLYS, binding.FLAG_STREAM_INDEX,
-                      binding.FLAG_COVERAGE_MASK, binding.PMH_ERR_CAPACITY]
+                      binding.FLAG_COVERAGE_MASK, binding.PMH_ERR_CAPACITY, binding.QGRAPH_FUSED_SELECT]

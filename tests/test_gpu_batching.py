@@ -194,22 +194,23 @@ def test_query_graph_indexed_large_polygons_refined(B, ctx, orc):
         dbp.close()
 
 
-@pytest.mark.parametrize("which,m,S", [("small_index", 6, 16), ("small_index", 6, 24), ("small_index", 10, 32),
-                                       ("small_index", 32, 32), ("small_index", 4, 4),
-                                       ("small_index_k128", 10, 32), ("small_index_k128", 6, 24),
-                                       ("small_index_k128", 4, 4), ("small_index_k128", 17, 64)])
-def test_query_graph_learned_form_matches_plain_calls(B, ctx, request, which, m, S):
+@pytest.mark.parametrize("which,m,S,fused", [("small_index", 6, 16, True), ("small_index", 6, 24, False),
+                                             ("small_index", 10, 32, True), ("small_index", 10, 32, False),
+                                             ("small_index", 32, 32, True), ("small_index", 4, 4, True),
+                                             ("small_index_k128", 10, 32, True), ("small_index_k128", 10, 32, False),
+                                             ("small_index_k128", 4, 4, True), ("small_index_k128", 17, 64, True)])
+def test_query_graph_learned_form_matches_plain_calls(B, ctx, request, which, m, S, fused):
     """With a reranker the graph's top-m are the m best by predicted Jaccard among the
     shortlist by agreement count: equal to the same chain of plain calls (shortlist top-S,
-    compact lists, features, forward, top-m by score, refinement).  Shortlists dividing
-    128 take the graph's fused selection launch (features, tcgen05 scores and ranking in
-    one kernel), S = 24 the separate launches; K = 32 and K = 128 (its fast group bits)."""
+    compact lists, features, forward, top-m by score, refinement): the graph's separate
+    launches, and its fused selection launch (features, tcgen05 scores and ranking in one
+    kernel; shortlists dividing 128); K = 32 and K = 128 (its fast group bits)."""
     w, db, qs, P, h, index = request.getfixturevalue(which)
     dbp = upload(B, ctx, db)
     r = B.Reranker(ctx, seed=5)
     k = 4
     g = B.QueryGraph(ctx, index, max_queries=128, max_vertices=20000, cand_capacity=200000, m=m,
-                     db=dbp, k=k, rerank=r, shortlist=S)
+                     db=dbp, k=k, rerank=r, shortlist=S, fused_select=fused)
     try:
         for lo, n in ((0, 1), (1, 90), (0, 128)):
             batch = qs.subset(np.arange(lo, lo + n))
@@ -228,6 +229,21 @@ def test_query_graph_learned_form_matches_plain_calls(B, ctx, request, which, m,
             qp.close()
     finally:
         g.close()
+        r.close()
+        dbp.close()
+
+
+def test_query_graph_fused_select_needs_a_dividing_shortlist(B, ctx, small_index):
+    """The fused selection takes 128 / S whole queries per tile: other shortlists are
+    refused before anything is allocated."""
+    w, db, qs, P, h, index = small_index
+    dbp = upload(B, ctx, db)
+    r = B.Reranker(ctx, seed=5)
+    try:
+        with pytest.raises(B.PmhError):
+            B.QueryGraph(ctx, index, max_queries=16, max_vertices=5000, cand_capacity=10000, m=6, db=dbp, k=4,
+                         rerank=r, shortlist=24, fused_select=True)
+    finally:
         r.close()
         dbp.close()
 
