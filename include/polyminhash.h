@@ -73,9 +73,10 @@ typedef struct pmh_rerank_s* pmh_rerank;
  *   flags     0 or PMH_FLAG_STREAM_INDEX | PMH_FLAG_COVERAGE_MASK */
 /* pmh_params.flags: sign through the stream index (same hashes, much less
  * work for small polygons).  The first call with a given (seed, K) builds the
- * index of the first 65,536 / 32,768 / 8,192 points of each stream, bucketed by
- * cell of a 128 x 128 / 64 x 64 / 32 x 32 grid (about K * 1 MiB of device
- * memory, kept by the context; that call synchronises); later calls reuse it.
+ * index of the first 65,536 / 32,768 / 8,192 / 1,048,576 points of each stream,
+ * bucketed by cell of a 128 x 128 / 64 x 64 / 32 x 32 / 512 x 512 grid (8 bytes
+ * per point and per (cell, hash) record: about K * 11.5 MB of device memory,
+ * kept by the context; that call synchronises); later calls reuse it.
  * Each polygon's form (index or walk) and grid level are planned at upload from
  * its box and area. */
 #define PMH_FLAG_STREAM_INDEX 1u
@@ -232,7 +233,10 @@ int pmh_index_destroy(pmh_index index);
  *   h_total   (host) receives the number of candidates over all queries.
  * Synchronises `stream` once (to learn the total).  With cand_capacity <
  * total, d_cand is left unwritten, d_row_ptr is still written, and the call
- * returns PMH_ERR_CAPACITY: call again with a larger buffer. */
+ * returns PMH_ERR_CAPACITY: call again with a larger buffer.  From 16 bands the
+ * counting pass keeps its sorted rows in context scratch (8 bytes per query and
+ * up to 4,096 ids per query, at most 64M ids) and the filling pass copies them;
+ * rows past that pool are joined again.  Errors also: PMH_ERR_NOMEM (scratch). */
 int pmh_lsh_query(pmh_ctx ctx, pmh_index index, const uint32_t* d_qhashes, int64_t Q,
                   int64_t* d_row_ptr, int32_t* d_cand, int64_t cand_capacity, int64_t* h_total,
                   void* stream);
@@ -258,7 +262,9 @@ int pmh_jaccard_estimate(pmh_ctx ctx, const uint32_t* d_qhashes, const uint32_t*
 
 /* A6 -- top-m of every candidate row.  Order: (count desc, id asc), or with
  * d_score != NULL (float per pair, e.g. a learned Jaccard) (score desc, id
- * asc).  d_out_ids int32 [Q][m] (-1 padded), d_out_n int32 [Q]. 1 <= m <= 1024. */
+ * asc).  d_out_ids int32 [Q][m] (-1 padded), d_out_n int32 [Q]. 1 <= m <= 1024.
+ * Counts are agreement counts (at most K <= 4,096); a larger count ranks as
+ * 4,096.  Does not synchronise. */
 int pmh_topm(pmh_ctx ctx, const int64_t* d_row_ptr, const int32_t* d_cand,
              const uint16_t* d_count, const float* d_score, int64_t Q, int32_t m,
              int32_t* d_out_ids, int32_t* d_out_n, void* stream);
